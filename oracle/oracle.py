@@ -1,0 +1,296 @@
+"""ctypes front end of the C oracle (``iga_oracle.c``) plus the oracle's own Newton.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Every function follows a
+passage of the PetIGA paper, cited where it is defined in ``iga_oracle.c``:
+
+* ``open_uniform_knots``      -- open knot vector with interior knots repeated
+  p-k times for continuity C^k (Sec. 2.1, 2.4; PetIGA's default space is the
+  uniform, maximally smooth one, Sec. 3.2).
+* ``Problem``                 -- the discretisation (Sec. 2.2-2.3) and the Bratu
+  parameters (Sec. 3.1).
+* ``residual``/``jacobian``   -- Algorithm 3 (Sec. 2.7) with Eq. (residual) and
+  Eq. (jacobian).
+* ``pattern``                 -- Algorithm 2 (Sec. 2.5).
+* ``newton``                  -- Newton's method on R(U) = 0 (Sec. 3.1), each
+  linear system solved exactly by a sparse LU (a library primitive).
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "iga_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+
+def build(force=False):
+    """Compile the C oracle with gcc (plain -O2, no fast-math, single thread)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("p", ctypes.c_int * 3),
+        ("m", ctypes.c_int * 3),
+        ("U", ctypes.c_void_p * 3),
+        ("q", ctypes.c_int * 3),
+        ("ctrl", ctypes.c_void_p),
+        ("weights", ctypes.c_void_p),
+        ("lam", ctypes.c_double),
+        ("log_kappa", ctypes.c_void_p),
+        ("bnd", (ctypes.c_int * 2) * 3),
+        ("bval", (ctypes.c_double * 2) * 3),
+        ("source", ctypes.c_int),
+    ]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        P = ctypes.POINTER(_Problem)
+        vp, i64 = ctypes.c_void_p, ctypes.c_int64
+        L.or_bspline.restype = ctypes.c_double
+        L.or_bspline.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_double]
+        L.or_bspline_der.restype = ctypes.c_double
+        L.or_bspline_der.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_double]
+        L.or_gauss_legendre.argtypes = [ctypes.c_int, vp, vp]
+        L.or_spans.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
+        L.or_stencil.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp]
+        L.or_num_dofs.restype = i64
+        L.or_num_dofs.argtypes = [P]
+        L.or_pattern.restype = i64
+        L.or_pattern.argtypes = [P, vp, vp]
+        L.or_pattern_dense_from_elements.argtypes = [P, vp]
+        L.or_residual.argtypes = [P, vp, vp]
+        L.or_jacobian.argtypes = [P, vp, vp, vp, vp]
+        L.or_residual_rows.argtypes = [P, vp, i64, vp, vp]
+        L.or_jacobian_rows.argtypes = [P, vp, i64, vp, vp, vp, vp]
+        L.or_dense_bruteforce.argtypes = [P, vp, vp, vp, ctypes.c_int]
+        L.or_l2_error_sq.restype = ctypes.c_double
+        L.or_l2_error_sq.argtypes = [P, vp]
+        L.or_map_point.argtypes = [P, vp, vp, vp]
+        L.or_is_dirichlet.argtypes = [P, i64]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data if a is not None else None
+
+
+def open_uniform_knots(nel, p, k=None):
+    """Open knot vector on [0, 1] with nel uniform spans, p+1 end knots and every
+    interior knot repeated p-k times (continuity C^k; default k = p-1)."""
+    if k is None or k < 0:
+        k = p - 1
+    mult = p - k
+    U = [0.0] * (p + 1)
+    for e in range(1, nel):
+        U += [e / nel] * mult
+    U += [1.0] * (p + 1)
+    return np.asarray(U, dtype=np.float64)
+
+
+def gauss_legendre(q):
+    x = np.zeros(q)
+    w = np.zeros(q)
+    rc = lib().or_gauss_legendre(q, _ptr(x), _ptr(w))
+    assert rc == 0
+    return x, w
+
+
+def bspline(i, p, U, xi):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    return lib().or_bspline(i, p, _ptr(U), float(xi))
+
+
+def bspline_der(i, p, U, xi):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    return lib().or_bspline_der(i, p, _ptr(U), float(xi))
+
+
+def stencil(i, p, U):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    l = ctypes.c_int()
+    r = ctypes.c_int()
+    lib().or_stencil(i, p, _ptr(U), ctypes.byref(l), ctypes.byref(r))
+    return l.value, r.value
+
+
+class Problem:
+    """A scalar Bratu problem on a tensor-product NURBS space.
+
+    knots: list of per-direction knot vectors; degrees: list of p; quad: list of
+    Gauss points per direction (default p+1); ctrl: (N, dim) control points or
+    None (identity map); weights: (N,) or None; lam: lambda; log_kappa: (N,) or
+    None; dirichlet: dict {(axis, side): value}.
+    """
+
+    def __init__(self, knots, degrees, quad=None, ctrl=None, weights=None, lam=1.0,
+                 log_kappa=None, dirichlet=None, source=False):
+        dim = len(knots)
+        self.dim = dim
+        self.knots = [np.ascontiguousarray(k, dtype=np.float64) for k in knots]
+        self.degrees = list(degrees)
+        self.quad = list(quad) if quad is not None else [p + 1 for p in degrees]
+        self.n = [len(k) - p - 1 for k, p in zip(self.knots, self.degrees)]
+        self.N = int(np.prod(self.n))
+        self.ctrl = None if ctrl is None else np.ascontiguousarray(ctrl, dtype=np.float64).reshape(self.N, dim)
+        self.weights = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64).reshape(self.N)
+        self.lam = float(lam)
+        self.log_kappa = None if log_kappa is None else np.ascontiguousarray(log_kappa, dtype=np.float64).reshape(self.N)
+        self.dirichlet = dict(dirichlet or {})
+        self.source = bool(source)
+        self._pat = None
+
+    def _c(self):
+        s = _Problem()
+        s.dim = self.dim
+        for d in range(self.dim):
+            s.p[d] = self.degrees[d]
+            s.m[d] = len(self.knots[d])
+            s.U[d] = self.knots[d].ctypes.data
+            s.q[d] = self.quad[d]
+        s.ctrl = _ptr(self.ctrl)
+        s.weights = _ptr(self.weights)
+        s.lam = self.lam
+        s.log_kappa = _ptr(self.log_kappa)
+        for (ax, side), v in self.dirichlet.items():
+            s.bnd[ax][side] = 1
+            s.bval[ax][side] = float(v)
+        s.source = 1 if self.source else 0
+        return s
+
+    # -- Sec. 2.5 Algorithm 2 -------------------------------------------------
+    def pattern(self):
+        if self._pat is None:
+            c = self._c()
+            rowptr = np.zeros(self.N + 1, dtype=np.int64)
+            nnz = lib().or_pattern(ctypes.byref(c), _ptr(rowptr), None)
+            assert nnz >= 0
+            colidx = np.zeros(nnz, dtype=np.int32)
+            lib().or_pattern(ctypes.byref(c), _ptr(rowptr), _ptr(colidx))
+            self._pat = (rowptr, colidx)
+        return self._pat
+
+    def pattern_dense_from_elements(self):
+        c = self._c()
+        mark = np.zeros((self.N, self.N), dtype=np.uint8)
+        rc = lib().or_pattern_dense_from_elements(ctypes.byref(c), _ptr(mark))
+        assert rc == 0
+        return mark
+
+    def is_dirichlet(self, A):
+        c = self._c()
+        return bool(lib().or_is_dirichlet(ctypes.byref(c), int(A)))
+
+    # -- Sec. 2.7 Algorithm 3 ----------------------------------------------------
+    def residual(self, U):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        F = np.zeros(self.N)
+        c = self._c()
+        rc = lib().or_residual(ctypes.byref(c), _ptr(U), _ptr(F))
+        if rc:
+            raise RuntimeError("or_residual failed: %d" % rc)
+        return F
+
+    def jacobian(self, U):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        rowptr, colidx = self.pattern()
+        vals = np.zeros(len(colidx))
+        c = self._c()
+        rc = lib().or_jacobian(ctypes.byref(c), _ptr(U), _ptr(rowptr), _ptr(colidx), _ptr(vals))
+        if rc:
+            raise RuntimeError("or_jacobian failed: %d" % rc)
+        return vals
+
+    def jacobian_csr(self, U):
+        import scipy.sparse as sp
+        rowptr, colidx = self.pattern()
+        return sp.csr_matrix((self.jacobian(U), colidx, rowptr), shape=(self.N, self.N))
+
+    def residual_rows(self, U, rows):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        out = np.zeros(len(rows))
+        c = self._c()
+        rc = lib().or_residual_rows(ctypes.byref(c), _ptr(U), len(rows), _ptr(rows), _ptr(out))
+        if rc:
+            raise RuntimeError("or_residual_rows failed: %d" % rc)
+        return out
+
+    def jacobian_rows(self, U, rows):
+        """Values of the selected CSR rows, concatenated in the order of rows."""
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        rowptr, colidx = self.pattern()
+        total = int(sum(rowptr[r + 1] - rowptr[r] for r in rows))
+        out = np.zeros(total)
+        c = self._c()
+        rc = lib().or_jacobian_rows(ctypes.byref(c), _ptr(U), len(rows), _ptr(rows), _ptr(rowptr),
+                                    _ptr(colidx), _ptr(out))
+        if rc:
+            raise RuntimeError("or_jacobian_rows failed: %d" % rc)
+        return out
+
+    def dense_bruteforce(self, U, fix=True):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        F = np.zeros(self.N)
+        J = np.zeros((self.N, self.N))
+        c = self._c()
+        rc = lib().or_dense_bruteforce(ctypes.byref(c), _ptr(U), _ptr(F), _ptr(J), 1 if fix else 0)
+        if rc:
+            raise RuntimeError("or_dense_bruteforce failed: %d" % rc)
+        return F, J
+
+    def l2_error(self, U):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        c = self._c()
+        return float(np.sqrt(lib().or_l2_error_sq(ctypes.byref(c), _ptr(U))))
+
+    def map_point(self, xi):
+        xi = np.ascontiguousarray(list(xi) + [0.0] * (3 - len(xi)), dtype=np.float64)
+        x = np.zeros(3)
+        det = ctypes.c_double()
+        c = self._c()
+        rc = lib().or_map_point(ctypes.byref(c), _ptr(xi), _ptr(x), ctypes.byref(det))
+        assert rc == 0
+        return x[: self.dim], det.value
+
+    def dirichlet_mask(self):
+        m = np.zeros(self.N, dtype=bool)
+        if not self.dirichlet:
+            return m
+        idx = np.indices(self.n[::-1]).reshape(self.dim, -1)[::-1]  # idx[d] = i_d of natural A
+        for (ax, side) in self.dirichlet:
+            m |= idx[ax] == (0 if side == 0 else self.n[ax] - 1)
+        return m
+
+
+def newton(prob, U0, atol=1e-10, max_it=50):
+    """Newton's method on R(U) = 0 (Sec. 3.1): J(U_k) dU = -R(U_k), U_{k+1} = U_k + dU,
+    with each linear system solved exactly by sparse LU.  Returns (U, history)."""
+    import scipy.sparse.linalg as spla
+    U = np.array(U0, dtype=np.float64)
+    hist = []
+    for _ in range(max_it + 1):
+        F = prob.residual(U)
+        nf = float(np.linalg.norm(F))
+        hist.append(nf)
+        if nf <= atol or not np.isfinite(nf):
+            break
+        J = prob.jacobian_csr(U)
+        U = U + spla.spsolve(J.tocsc(), -F)
+    return U, hist

@@ -1,0 +1,386 @@
+"""Pins for the oracle against what the paper and the mathematics fix (CPU only).
+
+Each test names the passage or property it pins.  A plausible mistake in the
+oracle -- a dropped rational term, a wrong sign in Eq. (3), a wrong index in the
+element-to-global map, a wrong quadrature weight -- fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+from paper_1305_4452_gb300 import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def dirichlet_all(dim, value=0.0):
+    return {(a, s): value for a in range(dim) for s in range(2)}
+
+
+# ---------------------------------------------------------------- Sec. 2.9 GL
+
+@pytest.mark.parametrize("q", [1, 2, 3, 4, 5, 7, 10])
+def test_gauss_legendre_exactness(q):
+    x, w = O.gauss_legendre(q)
+    assert abs(w.sum() - 2.0) < 1e-14
+    assert np.all(np.diff(x) > 0) and np.allclose(x, -x[::-1], atol=1e-15)
+    for k in range(2 * q):
+        exact = 0.0 if k % 2 else 2.0 / (k + 1)
+        assert abs(np.dot(w, x ** k) - exact) < 2e-14, (q, k)
+    # degree 2q is not integrated exactly (the rule is not over-claimed)
+    assert abs(np.dot(w, x ** (2 * q)) - 2.0 / (2 * q + 1)) > 1e-6
+
+
+# ---------------------------------------------------------- Sec. 2.1 B-splines
+
+KNOTS = [
+    (2, O.open_uniform_knots(5, 2)),
+    (3, O.open_uniform_knots(6, 3)),
+    (3, np.array([0, 0, 0, 0, 2, 4, 4, 6, 6, 6, 8, 8, 8, 8], float) / 8.0),  # Sec. 2.5 figure
+    (4, O.open_uniform_knots(4, 4, 2)),
+    (1, O.open_uniform_knots(7, 1)),
+]
+
+
+@pytest.mark.parametrize("p,U", KNOTS)
+def test_partition_of_unity_and_derivative_sum(p, U):
+    n = len(U) - p - 1
+    rng = np.random.default_rng(1)
+    for xi in rng.random(25) * 0.999999:
+        vals = np.array([O.bspline(i, p, U, xi) for i in range(n)])
+        ders = np.array([O.bspline_der(i, p, U, xi) for i in range(n)])
+        assert abs(vals.sum() - 1.0) < 1e-15 * 4
+        assert np.all(vals >= 0.0)
+        # Eq. (3) with the sign that differentiating Eq. (2) gives; a "+" fails here
+        assert abs(ders.sum()) < 1e-12 * max(1.0, np.abs(ders).max())
+        # support [U_i, U_{i+p+1})
+        for i in range(n):
+            if not (U[i] <= xi < U[i + p + 1]):
+                assert vals[i] == 0.0
+
+
+@pytest.mark.parametrize("p,U", KNOTS)
+def test_derivative_matches_central_difference(p, U):
+    n = len(U) - p - 1
+    h = 1e-6
+    for xi in [0.123, 0.377, 0.61, 0.905]:
+        for i in range(n):
+            fd = (O.bspline(i, p, U, xi + h) - O.bspline(i, p, U, xi - h)) / (2 * h)
+            assert abs(fd - O.bspline_der(i, p, U, xi)) < 1e-6 * (1 + abs(fd))
+
+
+def test_bernstein_special_case():
+    # one span, open knots: the B-splines are the Bernstein polynomials
+    U = np.array([0, 0, 0, 1, 1, 1], float)
+    for xi in [0.1, 0.5, 0.73]:
+        ref = [(1 - xi) ** 2, 2 * xi * (1 - xi), xi ** 2]
+        dref = [-2 * (1 - xi), 2 - 4 * xi, 2 * xi]
+        for i in range(3):
+            assert abs(O.bspline(i, 2, U, xi) - ref[i]) < 1e-15
+            assert abs(O.bspline_der(i, 2, U, xi) - dref[i]) < 1e-14
+
+
+def test_polynomial_reproduction_by_blossom():
+    # x^2 = sum_i c_i B_{i,p}(x) with c_i the blossom of x^2 at (U_{i+1},...,U_{i+p});
+    # x = sum_i g_i B_{i,p} with g_i the Greville abscissae (linear precision)
+    for p, U in [(2, O.open_uniform_knots(5, 2)), (3, O.open_uniform_knots(4, 3, 1)), (4, O.open_uniform_knots(3, 4))]:
+        n = len(U) - p - 1
+        c = []
+        for i in range(n):
+            t = U[i + 1: i + p + 1]
+            s = sum(t[a] * t[b] for a in range(p) for b in range(a + 1, p))
+            c.append(2.0 * s / (p * (p - 1)))
+        g = [np.mean(U[i + 1: i + p + 1]) for i in range(n)]
+        for xi in [0.05, 0.31, 0.5, 0.88]:
+            B = [O.bspline(i, p, U, xi) for i in range(n)]
+            assert abs(np.dot(c, B) - xi * xi) < 1e-14
+            assert abs(np.dot(g, B) - xi) < 1e-14
+
+
+# ------------------------------------------------------------- Sec. 2.5 Alg. 2
+
+@pytest.mark.parametrize("p,U", KNOTS)
+def test_stencil_matches_support_overlap(p, U):
+    n = len(U) - p - 1
+    for i in range(n):
+        l, r = O.stencil(i, p, U)
+        overl = [j for j in range(n) if max(U[i], U[j]) < min(U[i + p + 1], U[j + p + 1])]
+        assert (l, r) == (min(overl), max(overl)), (i, l, r, overl)
+
+
+@pytest.mark.parametrize("dim,p,nel,k", [(2, 2, 4, 1), (2, 3, 3, 1), (3, 2, 2, 1), (2, 1, 5, 0), (2, 3, 3, 2)])
+def test_pattern_two_constructions_agree(dim, p, nel, k):
+    U = O.open_uniform_knots(nel, p, k)
+    P = O.Problem([U] * dim, [p] * dim)
+    rowptr, colidx = P.pattern()
+    mark = P.pattern_dense_from_elements()
+    dense = np.zeros((P.N, P.N), np.uint8)
+    rows = np.repeat(np.arange(P.N), np.diff(rowptr))
+    dense[rows, colidx] = 1
+    assert np.array_equal(dense, mark)
+    for A in range(P.N):
+        assert np.all(np.diff(colidx[rowptr[A]:rowptr[A + 1]]) > 0)
+
+
+def test_pattern_counts_of_the_configs():
+    # n = nel + p functions per direction at maximal continuity; counted nnz
+    U = O.open_uniform_knots(16, 2)
+    P = O.Problem([U, U], [2, 2])
+    rowptr, colidx = P.pattern()
+    assert P.N == 324 and len(colidx) == 7056
+    U3 = O.open_uniform_knots(8, 3)
+    P3 = O.Problem([U3] * 3, [3] * 3)
+    n1 = sum(min(i, 3) + min(10 - i, 3) + 1 for i in range(11))
+    assert len(P3.pattern()[1]) == n1 ** 3
+
+
+# ------------------------------------------------- Sec. 3 / App. B: the residual
+
+def integral_1d(U, p):
+    n = len(U) - p - 1
+    return np.array([(U[i + p + 1] - U[i]) / (p + 1) for i in range(n)])
+
+
+@pytest.mark.parametrize("dim,p,nel,lam", [(2, 2, 6, 1.0), (2, 3, 5, 2.5), (3, 2, 3, 2.0)])
+def test_residual_at_zero_is_minus_lambda_times_basis_integrals(dim, p, nel, lam):
+    U = O.open_uniform_knots(nel, p)
+    P = O.Problem([U] * dim, [p] * dim, lam=lam, dirichlet=dirichlet_all(dim))
+    F = P.residual(np.zeros(P.N))
+    I1 = integral_1d(U, p)
+    ref = -lam * I1
+    for _ in range(dim - 1):
+        ref = np.kron(I1, ref)
+    ref[P.dirichlet_mask()] = 0.0
+    assert np.abs(F - ref).max() < 1e-15
+
+
+def read_trace():
+    rows = []
+    with open(os.path.join(HERE, "golden", "bratu_appB_trace.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                it, v = line.split()
+                rows.append(float(v))
+    return rows
+
+
+def test_appendix_b_initial_residual_norm():
+    trace = read_trace()
+    U = O.open_uniform_knots(128, 2)
+    P = O.Problem([U, U], [2, 2], lam=6.80, dirichlet=dirichlet_all(2))
+    assert P.N == 130 * 130
+    F = P.residual(np.zeros(P.N))
+    assert abs(np.linalg.norm(F) - trace[0]) <= 1e-12 * trace[0]
+
+
+@pytest.mark.slow
+def test_appendix_b_newton_trace():
+    # exact-solve Newton follows the printed trace to the accuracy of PETSc's CG
+    trace = read_trace()
+    U = O.open_uniform_knots(128, 2)
+    P = O.Problem([U, U], [2, 2], lam=6.80, dirichlet=dirichlet_all(2))
+    _, hist = O.newton(P, np.zeros(P.N))
+    assert len(hist) == len(trace)
+    for k in range(1, 5):
+        assert abs(hist[k] - trace[k]) < 1e-5 * trace[k], (k, hist[k], trace[k])
+    for k in (5, 6):
+        assert abs(hist[k] - trace[k]) < 1e-4 * trace[k]
+    assert hist[-1] <= 1e-10
+
+
+# ----------------------------------------------------- closed-form Jacobian rows
+
+def test_jacobian_at_zero_matches_kronecker_closed_form():
+    # uniform quadratic C1: 1D mass row h/120 [1,26,66,26,1], stiffness 1/(6h) [-1,-2,6,-2,-1];
+    # at U = 0 on the identity map, J = K x M + M x K - lambda M x M
+    nel, lam = 10, 1.7
+    h = 1.0 / nel
+    m1 = h / 120.0 * np.array([1, 26, 66, 26, 1.0])
+    k1 = 1.0 / (6.0 * h) * np.array([-1, -2, 6, -2, -1.0])
+    U = O.open_uniform_knots(nel, 2)
+    P = O.Problem([U, U], [2, 2], lam=lam)
+    J = P.jacobian_csr(np.zeros(P.N)).toarray()
+    n = nel + 2
+    for i in range(4, n - 4):
+        for j in range(4, n - 4):
+            A = i + n * j
+            for a in range(-2, 3):
+                for b in range(-2, 3):
+                    B = (i + a) + n * (j + b)
+                    ref = k1[a + 2] * m1[b + 2] + m1[a + 2] * k1[b + 2] - lam * m1[a + 2] * m1[b + 2]
+                    assert abs(J[A, B] - ref) < 1e-14 * (1 + abs(ref))
+
+
+def test_stiffness_annihilates_constants_and_mass_total_is_area():
+    kn, ctrl, w = W.quarter_annulus(3, 3)
+    P0 = O.Problem(kn, [3] * 3, quad=[8] * 3, ctrl=ctrl, weights=w, lam=0.0)
+    P1 = O.Problem(kn, [3] * 3, quad=[8] * 3, ctrl=ctrl, weights=w, lam=1.0)
+    Z = np.zeros(P0.N)
+    K = P0.jacobian_csr(Z)
+    M = K - P1.jacobian_csr(Z)
+    assert np.abs(K @ np.ones(P0.N)).max() < 1e-14 * abs(K).max()
+    assert abs(M.sum() - 3.0 * math.pi / 4.0) < 1e-13
+    # the unit cube
+    U = O.open_uniform_knots(3, 2)
+    Q0 = O.Problem([U] * 3, [2] * 3, lam=0.0)
+    Q1 = O.Problem([U] * 3, [2] * 3, lam=1.0)
+    Z = np.zeros(Q0.N)
+    assert abs((Q0.jacobian_csr(Z) - Q1.jacobian_csr(Z)).sum() - 1.0) < 1e-14
+
+
+def test_laplacian_of_reproduced_quadratic():
+    # u = x^2 + y^2 is reproduced exactly (blossom coefficients); with lambda = 0 an
+    # interior row is (grad N_A, grad u) = -(N_A, lap u) = -4 int N_A
+    nel, p = 7, 2
+    U = O.open_uniform_knots(nel, p)
+    n = nel + p
+    c = np.array([U[i + 1] * U[i + 2] for i in range(n)])  # blossom of x^2, p = 2
+    Uc = (c[None, :] + c[:, None]).reshape(-1)  # natural order: x fastest
+    P = O.Problem([U, U], [p, p], lam=0.0)
+    F = P.residual(Uc)
+    I1 = integral_1d(U, p)
+    for i in range(p + 1, n - p - 1):
+        for j in range(p + 1, n - p - 1):
+            assert abs(F[i + n * j] - (-4.0 * I1[i] * I1[j])) < 1e-14
+
+
+# ------------------------------------------------- brute force and consistency
+
+def random_nurbs_2d(nel0, nel1, p, seed):
+    kn, ctrl, w = W.quarter_annulus((nel0, nel1, 1), p)
+    n0, n1 = len(kn[0]) - p - 1, len(kn[1]) - p - 1
+    # take the z = 0 layer as a planar rational geometry
+    ctrl2 = ctrl.reshape(-1, n1, n0, 3)[0, :, :, :2].reshape(-1, 2)
+    w2 = w.reshape(-1, n1, n0)[0].reshape(-1)
+    return kn[:2], ctrl2, w2
+
+
+@pytest.mark.parametrize("case", ["identity2d", "nurbs2d", "identity3d", "kappa2d"])
+def test_element_assembly_equals_global_bruteforce(case):
+    if case == "identity2d":
+        U = O.open_uniform_knots(2, 2)
+        P = O.Problem([U, U], [2, 2], lam=1.3, dirichlet=dirichlet_all(2))
+    elif case == "nurbs2d":
+        kn, c, w = random_nurbs_2d(2, 2, 3, 0)
+        P = O.Problem(kn, [3, 3], ctrl=c, weights=w, lam=2.0, dirichlet=dirichlet_all(2))
+    elif case == "identity3d":
+        U = O.open_uniform_knots(2, 2)
+        P = O.Problem([U] * 3, [2] * 3, lam=2.0, dirichlet=dirichlet_all(3))
+    else:
+        U = O.open_uniform_knots(2, 2)
+        lk = W.uniform(9, 16, -0.5, 0.5)
+        P = O.Problem([U, U], [2, 2], lam=1.0, log_kappa=lk, dirichlet=dirichlet_all(2))
+    Uc = W.uniform(5, P.N, -0.3, 0.3)
+    F = P.residual(Uc)
+    J = P.jacobian_csr(Uc).toarray()
+    Fb, Jb = P.dense_bruteforce(Uc, fix=True)
+    assert np.abs(F - Fb).max() < 1e-14 * max(1.0, np.abs(Fb).max())
+    assert np.abs(J - Jb).max() < 1e-14 * max(1.0, np.abs(Jb).max())
+
+
+@pytest.mark.parametrize("case", ["nurbs2d", "kappa2d"])
+def test_jacobian_is_derivative_of_residual(case):
+    if case == "nurbs2d":
+        kn, c, w = random_nurbs_2d(3, 2, 2, 0)
+        P = O.Problem(kn, [2, 2], ctrl=c, weights=w, lam=2.0, dirichlet=dirichlet_all(2))
+    else:
+        U = O.open_uniform_knots(3, 2)
+        lk = W.uniform(3, 25, -0.5, 0.5)
+        P = O.Problem([U, U], [2, 2], lam=1.0, log_kappa=lk)
+    Uc = W.interior_field(P.n, 7, -0.5, 0.5)
+    J = P.jacobian_csr(Uc).toarray()
+    h = 1e-6
+    for B in range(P.N):
+        e = np.zeros(P.N)
+        e[B] = h
+        col = (P.residual(Uc + e) - P.residual(Uc - e)) / (2 * h)
+        mask = np.ones(P.N, bool)
+        if P.dirichlet:
+            # boundary columns are zeroed on purpose (symmetric Dirichlet reading)
+            if P.dirichlet_mask()[B]:
+                continue
+        assert np.abs(col[mask] - J[mask, B]).max() < 1e-7 * max(1.0, np.abs(J).max())
+
+
+def test_jacobian_symmetric_on_nurbs():
+    kn, c, w = random_nurbs_2d(3, 3, 3, 0)
+    P = O.Problem(kn, [3, 3], ctrl=c, weights=w, lam=2.0, dirichlet=dirichlet_all(2))
+    J = P.jacobian_csr(W.interior_field(P.n, 3)).toarray()
+    assert np.abs(J - J.T).max() < 1e-15 * 8 * np.abs(J).max()
+
+
+def test_greville_geometry_equals_identity_map():
+    # linear precision: control points at the Greville abscissae give x = xi, so the
+    # general rational/geometry path must reproduce the identity-map assembly
+    p, nel = 3, 3
+    U = O.open_uniform_knots(nel, p, 1)
+    g = np.array([np.mean(U[i + 1:i + p + 1]) for i in range(len(U) - p - 1)])
+    n = len(g)
+    ctrl = np.stack(np.meshgrid(g, g, indexing="xy"), -1).reshape(-1, 2)
+    Pi = O.Problem([U, U], [p, p], lam=1.5, dirichlet=dirichlet_all(2))
+    Pg = O.Problem([U, U], [p, p], ctrl=ctrl, weights=np.ones(n * n), lam=1.5, dirichlet=dirichlet_all(2))
+    Uc = W.interior_field([n, n], 11)
+    assert np.abs(Pi.residual(Uc) - Pg.residual(Uc)).max() < 1e-15
+    assert np.abs(Pi.jacobian(Uc) - Pg.jacobian(Uc)).max() < 1e-13
+
+
+def test_annulus_geometry():
+    kn, ctrl, w = W.quarter_annulus(5, 3)
+    assert [len(k) - 4 for k in kn] == [8, 8, 8]
+    P = O.Problem(kn, [3] * 3, ctrl=ctrl, weights=w)
+    rng = np.random.default_rng(3)
+    for xi in rng.random((30, 3)):
+        x, det = P.map_point(xi)
+        assert abs(math.hypot(x[0], x[1]) - (1.0 + xi[0])) < 1e-14
+        assert abs(x[2] - xi[2]) < 1e-15
+        assert det > 0
+    # corners of the angular range
+    x, _ = P.map_point([0.0, 0.0, 0.0])
+    assert np.allclose(x, [1, 0, 0], atol=1e-15)
+    x, _ = P.map_point([1.0, 1.0, 1.0])
+    assert np.allclose(x, [0, 2, 1], atol=1e-14)
+
+
+def test_dirichlet_rows_and_columns():
+    U = O.open_uniform_knots(3, 2)
+    P = O.Problem([U, U], [2, 2], lam=1.0, dirichlet={(0, 0): 0.5, (1, 1): -0.25})
+    Uc = W.uniform(4, P.N, -1, 1)
+    F = P.residual(Uc)
+    J = P.jacobian_csr(Uc).toarray()
+    n = 5
+    for A in range(P.N):
+        i, j = A % n, A // n
+        on = i == 0 or j == n - 1
+        if on:
+            g = -0.25 if j == n - 1 else 0.5
+            assert F[A] == Uc[A] - g
+            assert J[A, A] == 1.0 and np.count_nonzero(J[A]) == 1
+            assert np.count_nonzero(J[:, A]) == 1
+
+
+@pytest.mark.slow
+def test_l2_convergence_rate():
+    # manufactured u* = sin(pi x) sin(pi y): ||u_h - u*||_L2 = O(h^{p+1})
+    for p in (2, 3):
+        errs, hs = [], []
+        for nel in (8, 16, 32):
+            U = O.open_uniform_knots(nel, p)
+            P = O.Problem([U, U], [p, p], lam=1.0, dirichlet=dirichlet_all(2), source=True)
+            Uh, hist = O.newton(P, np.zeros(P.N))
+            assert hist[-1] < 1e-10
+            errs.append(P.l2_error(Uh))
+            hs.append(1.0 / nel)
+        slope = np.polyfit(np.log(hs), np.log(errs), 1)[0]
+        assert abs(slope - (p + 1)) < 0.2, (p, slope, errs)
+
+
+def test_lambda_beyond_fold_does_not_converge():
+    # no solution exists above lambda_max = 6.80812 (Sec. 3.1)
+    U = O.open_uniform_knots(16, 2)
+    P = O.Problem([U, U], [2, 2], lam=7.5, dirichlet=dirichlet_all(2))
+    _, hist = O.newton(P, np.zeros(P.N), max_it=30)
+    assert not (hist[-1] <= 1e-10)
