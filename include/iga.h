@@ -1,0 +1,174 @@
+/*
+ * iga.h -- C ABI of the GB300 isogeometric Bratu library (libiga.so).
+ *
+ * The library assembles, on one GPU, the residual vector and Jacobian matrix of
+ * the Galerkin weak form of the Bratu problem
+ *      -div(kappa grad u) - lambda exp(u) = 0,  u = g on the boundary,
+ * on a tensor-product NURBS space, and drives a Newton-Krylov solve.  It follows
+ * the PetIGA paper (Dalcin, Collier, Vignal, Cortes, Calo):
+ *   - B-spline bases (Sec. 2.1, Eqs. 1-3), tensor products (Sec. 2.2, Eq. 5),
+ *     NURBS bases and derivatives (Sec. 2.3, Eqs. 6-7, drational);
+ *   - the CSR adjacency pattern from BasisStencil (Sec. 2.5, Algorithm 2);
+ *   - element-by-element Gauss-Legendre assembly (Sec. 2.7, Algorithm 3);
+ *   - the geometry map, its inverse and spatial gradients (Appendix A);
+ *   - the Bratu residual and Jacobian (Sec. 3.1, Eqs. residual and jacobian),
+ *     with kappa = 1 unless a log-kappa field is given (an extension);
+ *   - the problem set-up calls of Sec. 3.2 (IGASetDim/SetDof/SetFromOptions/
+ *     SetUp, IGASetBoundaryValue, IGASetFormFunction/Jacobian, SNESSolve).
+ *
+ * Conventions shared by every call:
+ *   - Natural ordering (Sec. 2.2): the control variable of tensor index
+ *     (i0, i1, i2) is A = i0 + n0*(i1 + n1*i2); rows and columns of the Jacobian
+ *     use the same numbering.
+ *   - Every compute call is asynchronous on the CUDA stream given to iga_create
+ *     (NULL = the legacy default stream) unless stated otherwise.  Pointers
+ *     documented as "device" must be device (or managed) memory of the current
+ *     device; the library never frees caller memory.
+ *   - No call throws; each returns an iga_status.  IGA_EINVAL means the
+ *     arguments were rejected before any work was queued; nothing was written.
+ *     iga_last_error() gives a one-line reason.
+ *   - Results are deterministic: the kernels use no floating-point atomics and
+ *     every sum is taken in a fixed order, so two calls with the same input give
+ *     bit-identical output.
+ */
+#ifndef IGA_H
+#define IGA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct iga_s *iga_t;
+
+typedef enum {
+  IGA_OK = 0,
+  IGA_EINVAL = 1,    /* invalid argument or unsupported discretisation */
+  IGA_ENOMEM = 2,    /* device allocation failed */
+  IGA_ECUDA = 3,     /* a CUDA runtime call failed */
+  IGA_ENOCONV = 4,   /* Newton did not reach the tolerance within its cap */
+  IGA_EDIVERGED = 5, /* line search failed or the residual grew without bound */
+  IGA_ETIMEOUT = 6,  /* a bounded device-side wait gave up */
+  IGA_ENAN = 7       /* a NaN or Inf appeared in the input or in the iterates */
+} iga_status;
+
+typedef enum {
+  IGA_FP64 = 0,     /* FP64 element arithmetic, FP64 values (double *) */
+  IGA_JAC_TF32 = 1, /* element contraction with TF32 operands, FP32 accumulate; float * values */
+  IGA_JAC_BF16 = 2  /* element contraction with BF16 operands, FP32 accumulate; float * values */
+} iga_precision;
+
+/* Discretisation (the IGASetDim / IGASetFromOptions data of Sec. 3.2).
+ *  dim            2 or 3 (Sec. 3.2 IGASetDim); one scalar field (IGASetDof = 1).
+ *  degree[d]      polynomial degree p, 1..4, equal in every direction.
+ *  nel[d]         elements per direction (used when knots[d] == NULL).
+ *  continuity[d]  inter-element continuity k, 0..p-1; -1 means p-1 (the default
+ *                 space of Sec. 3.2 is C^{p-1}).  Used when knots[d] == NULL.
+ *  knots[d]       explicit open knot vector of nknots[d] entries (host memory),
+ *                 non-decreasing, p+1 repeated end knots; NULL: uniform on [0,1].
+ *  quad[d]        Gauss-Legendre points per direction; 0 means p+1 (the rule of
+ *                 Sec. 5 and App. C); only p+1 is supported.
+ *  ctrl           host array N*dim of physical control points (natural order,
+ *                 coordinates contiguous), or NULL for the identity map x = xi.
+ *  weights        host array N of rational weights, or NULL for all ones. */
+typedef struct {
+  int dim;
+  int degree[3];
+  int nel[3];
+  int continuity[3];
+  const double *knots[3];
+  int nknots[3];
+  int quad[3];
+  const double *ctrl;
+  const double *weights;
+} iga_desc;
+
+/* Problem parameters: lambda of Eq. (strong), and an optional host array of N
+ * log-kappa coefficients (kappa = exp(sum logkappa_A N_A); NULL: kappa = 1). */
+typedef struct {
+  double lambda;
+  const double *log_kappa;
+} iga_bratu;
+
+/* Create a discretisation (IGACreate + IGASetUp of Sec. 3.2): validates the
+ * description, builds knot vectors, Gauss rules and 1D basis tables, the CSR
+ * pattern (Algorithm 2), and the per-quadrature-point geometry factors on the
+ * device.  `stream` is a cudaStream_t (NULL: default stream); all library-owned
+ * device memory is allocated here with cudaMalloc and freed by iga_destroy.
+ * Synchronises the stream before returning.  On failure *out is NULL. */
+iga_status iga_create(const iga_desc *desc, const iga_bratu *bratu, void *stream, iga_t *out);
+
+/* IGASetBoundaryValue(iga, axis, side, 0, value) of Sec. 3.2: Dirichlet value on
+ * the face `side` (0 = left, 1 = right) of parametric direction `axis`.  Rows of
+ * boundary control variables become F_A = U_A - value and identity rows of the
+ * Jacobian, with the column zeroed in the other rows (symmetric form).  When
+ * faces meet, the face set later in the order (axis 0 side 0, axis 0 side 1,
+ * axis 1 side 0, ...) gives the value. */
+iga_status iga_set_boundary_value(iga_t iga, int axis, int side, double value);
+
+/* Change lambda after creation (used by the batched and learned-start drivers). */
+iga_status iga_set_lambda(iga_t iga, double lambda);
+
+/* Sizes and the device CSR pattern (library-owned, valid until iga_destroy):
+ * rowptr int64[n+1], colidx int32[nnz], columns ascending within each row,
+ * every BasisStencil entry present (explicit zeros included). */
+iga_status iga_get_pattern(iga_t iga, int64_t *n, int64_t *nnz, const int64_t **rowptr,
+                           const int32_t **colidx);
+
+/* Residual F(U) of Eq. (residual), Algorithm 3, FP64.  U and F: device double[n],
+ * caller-owned, must not overlap.  Dirichlet rows as set by iga_set_boundary_value. */
+iga_status iga_form_residual(iga_t iga, const double *U, double *F);
+
+/* Jacobian J(U) of Eq. (jacobian) into CSR values on the library's pattern.
+ * vals: device memory, caller-owned, nnz entries of double (IGA_FP64) or float
+ * (IGA_JAC_TF32, IGA_JAC_BF16). */
+iga_status iga_form_jacobian(iga_t iga, const double *U, void *vals, iga_precision prec);
+
+/* Newton-Krylov options (SNESSolve of Sec. 3.2; -snes_atol, -ksp_* analogues). */
+typedef struct {
+  double atol;         /* stop when ||F||_2 <= atol (default 1e-10) */
+  int max_newton;      /* Newton iteration cap (default 50) */
+  int gmres_restart;   /* GMRES(m) restart length (default 60) */
+  int max_krylov;      /* Krylov iteration cap per Newton step (default 4000) */
+  double krylov_rtol;  /* forcing term cap; the solve uses min(krylov_rtol, ||F_k||) (default 1e-2) */
+  iga_precision jac;   /* Jacobian precision used to steer Newton (default IGA_FP64) */
+  int reuse_stiffness; /* 1: assemble the U-independent part of J once per solve and add
+                          the reaction term each step (default 1); 0: full assembly each step */
+} iga_newton_opts;
+
+typedef struct {
+  int newton_its;         /* Newton steps taken */
+  int krylov_its;         /* total Krylov iterations */
+  double fnorm0, fnorm;   /* ||F(U_0)||_2 and ||F(U_final)||_2 */
+  double fnorm_hist[64];  /* ||F||_2 after each step (index 0 = initial) */
+  iga_status status;      /* IGA_OK when ||F|| <= atol */
+} iga_newton_report;
+
+/* Fill opts with the defaults above. */
+void iga_newton_defaults(iga_newton_opts *opts);
+
+/* Solve F(U) = 0 by Newton with GMRES(m) + Jacobi (right preconditioning) on
+ * the device, starting from U (device double[n], in/out).  Each step solves
+ * J(U_k) dU = -F(U_k) to the forcing tolerance and backtracks (halving, at most
+ * 10 times) until ||F|| decreases.  Synchronises the stream; fills *report
+ * (may be NULL).  Returns report->status. */
+iga_status iga_solve_newton(iga_t iga, double *U, const iga_newton_opts *opts,
+                            iga_newton_report *report);
+
+/* Same as iga_solve_newton with U in HOST memory: copies U to the device, solves,
+ * copies the solution back. */
+iga_status iga_solve_newton_host(iga_t iga, double *U_host, const iga_newton_opts *opts,
+                                 iga_newton_report *report);
+
+/* Release every library-owned device buffer.  NULL is accepted. */
+void iga_destroy(iga_t iga);
+
+/* One-line description of the last error on this handle (or of the last failed
+ * iga_create when iga == NULL).  Never NULL. */
+const char *iga_last_error(iga_t iga);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IGA_H */

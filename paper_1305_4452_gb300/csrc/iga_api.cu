@@ -1,0 +1,403 @@
+// C ABI of libiga (declared in include/iga.h): creation, residual and Jacobian
+// assembly, and the device Newton-Krylov driver (SNESSolve analogue, Sec. 3.2).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "iga_internal.h"
+
+static thread_local std::string g_create_err;
+
+#define CK(call)                                                                 \
+  do {                                                                           \
+    cudaError_t ce_ = (call);                                                    \
+    if (ce_ != cudaSuccess) {                                                    \
+      h->err = iga_format("%s: %s", #call, cudaGetErrorString(ce_));             \
+      return (ce_ == cudaErrorMemoryAllocation) ? IGA_ENOMEM : IGA_ECUDA;        \
+    }                                                                            \
+  } while (0)
+
+template <typename T>
+static cudaError_t upload(T **dst, const std::vector<T> &src) {
+  *dst = nullptr;
+  if (src.empty()) return cudaSuccess;
+  cudaError_t ce = cudaMalloc((void **)dst, src.size() * sizeof(T));
+  if (ce) return ce;
+  return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+static void free_dir(DirDev &d) {
+  void *ps[] = {d.first, d.tab, d.wq, d.l, d.r, d.pair_off, d.pair_i, d.pair_j, d.pair_x0,
+                d.pair_np, d.pair_po, d.pair_val, d.pair_val_f, d.node_e0, d.node_ne};
+  for (void *p : ps)
+    if (p) cudaFree(p);
+  memset(&d, 0, sizeof d);
+}
+
+static void release(iga_s *h) {
+  for (int ax = 0; ax < 3; ax++) free_dir(h->ddev[ax]);
+  void *ps[] = {h->rowptr, h->colidx, h->weights, h->geom, h->Fe, h->Q00, h->T1, h->T2, h->Kstiff, h->Kstiff_f,
+                h->Mred, h->Mred_f, h->J64, h->J32, h->wk, h->V, h->red, h->ctl, h->Uhost_dev};
+  for (void *p : ps)
+    if (p) cudaFree(p);
+  if (h->ctl_host) cudaFreeHost(h->ctl_host);
+}
+
+static iga_status upload_dir(iga_s *h, int ax) {
+  Dir &D = h->dir[ax];
+  DirDev &d = h->ddev[ax];
+  memset(&d, 0, sizeof d);
+  d.p = D.p; d.q = D.q; d.nel = D.nel; d.n = D.n; d.np = D.npairs(); d.X = D.X();
+  if (ax >= h->dim) return IGA_OK;
+  CK(upload(&d.first, D.first));
+  CK(upload(&d.tab, D.tab));
+  CK(upload(&d.wq, D.wq));
+  CK(upload(&d.l, D.l));
+  CK(upload(&d.r, D.r));
+  CK(upload(&d.pair_off, D.pair_off));
+  CK(upload(&d.pair_i, D.pair_i));
+  CK(upload(&d.pair_j, D.pair_j));
+  CK(upload(&d.pair_x0, D.pair_x0));
+  CK(upload(&d.pair_np, D.pair_np));
+  CK(upload(&d.pair_po, D.pair_po));
+  CK(upload(&d.pair_val, D.pair_val));
+  std::vector<float> pf(D.pair_val.begin(), D.pair_val.end());
+  CK(upload(&d.pair_val_f, pf));
+  CK(upload(&d.node_e0, D.node_e0));
+  CK(upload(&d.node_ne, D.node_ne));
+  return IGA_OK;
+}
+
+static iga_status create_impl(iga_s *h, const iga_desc *d, const iga_bratu *b) {
+  iga_status st = iga_build_dirs(h, d);
+  if (st != IGA_OK) return st;
+  h->lambda = b ? b->lambda : 0.0;
+  if (!isfinite(h->lambda)) {
+    h->err = "lambda must be finite";
+    return IGA_EINVAL;
+  }
+  h->gl = geom_layout(h->dim);
+  h->has_geom = d->ctrl != nullptr;
+  h->has_w = d->weights != nullptr;
+  h->has_kappa = b && b->log_kappa;
+  const int64_t N = h->N;
+  if (h->has_w)
+    for (int64_t A = 0; A < N; A++)
+      if (!(d->weights[A] > 0.0) || !isfinite(d->weights[A])) {
+        h->err = iga_format("weight %lld must be positive and finite", (long long)A);
+        return IGA_EINVAL;
+      }
+  if (h->has_geom)
+    for (int64_t k = 0; k < N * h->dim; k++)
+      if (!isfinite(d->ctrl[k])) {
+        h->err = "control points must be finite";
+        return IGA_EINVAL;
+      }
+  if (h->has_kappa)
+    for (int64_t A = 0; A < N; A++)
+      if (!isfinite(b->log_kappa[A])) {
+        h->err = "log-kappa coefficients must be finite";
+        return IGA_EINVAL;
+      }
+  for (int ax = 0; ax < 3; ax++) {
+    st = upload_dir(h, ax);
+    if (st != IGA_OK) return st;
+  }
+  // CSR pattern (Sec. 2.5)
+  std::vector<int64_t> rowptr;
+  iga_rowptr(h, rowptr);
+  h->nnz = rowptr[N];
+  CK(upload(&h->rowptr, rowptr));
+  CK(cudaMalloc((void **)&h->colidx, (size_t)h->nnz * sizeof(int32_t)));
+  CK(launch_colidx(h));
+  // weights, geometry factors
+  if (h->has_w) {
+    CK(cudaMalloc((void **)&h->weights, N * sizeof(double)));
+    CK(cudaMemcpy(h->weights, d->weights, N * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  int nq = (h->dim == 3) ? h->q * h->q * h->q : h->q * h->q;
+  int nen = (h->dim == 3) ? (h->p + 1) * (h->p + 1) * (h->p + 1) : (h->p + 1) * (h->p + 1);
+  CK(cudaMalloc((void **)&h->geom, (size_t)h->nelem * h->gl.nf * nq * sizeof(double)));
+  double *ctrl_dev = nullptr, *logk_dev = nullptr;
+  if (h->has_geom) {
+    CK(cudaMalloc((void **)&ctrl_dev, (size_t)N * h->dim * sizeof(double)));
+    CK(cudaMemcpy(ctrl_dev, d->ctrl, (size_t)N * h->dim * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  if (h->has_kappa) {
+    CK(cudaMalloc((void **)&logk_dev, N * sizeof(double)));
+    CK(cudaMemcpy(logk_dev, b->log_kappa, N * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  cudaError_t ge = launch_geometry(h, ctrl_dev, logk_dev);
+  if (ctrl_dev) cudaFree(ctrl_dev);
+  if (logk_dev) cudaFree(logk_dev);
+  if (ge == cudaErrorInvalidValue) {
+    h->err = "geometry map has a non-positive Jacobian determinant at a Gauss point";
+    return IGA_EINVAL;
+  }
+  CK(ge);
+  CK(cudaMalloc((void **)&h->Fe, (size_t)h->nelem * nen * sizeof(double)));
+  CK(cudaMalloc((void **)&h->Q00, (size_t)h->nelem * nq * sizeof(double)));
+  // stage intermediates (sized for FP64)
+  const Dir &D0 = h->dir[0], &D1 = h->dir[1], &D2 = h->dir[2];
+  int ng1 = (h->dim == 3) ? 9 : 4, ng2 = 4;
+  h->T1_bytes = (size_t)ng1 * D0.npairs() * D1.X() * (h->dim == 3 ? D2.X() : 1) * sizeof(double);
+  CK(cudaMalloc(&h->T1, h->T1_bytes));
+  if (h->dim == 3) {
+    h->T2_bytes = (size_t)ng2 * D0.npairs() * D1.npairs() * D2.X() * sizeof(double);
+    CK(cudaMalloc(&h->T2, h->T2_bytes));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return IGA_OK;
+}
+
+extern "C" iga_status iga_create(const iga_desc *d, const iga_bratu *b, void *stream, iga_t *out) {
+  if (!out) return IGA_EINVAL;
+  *out = nullptr;
+  if (!d) {
+    g_create_err = "desc is NULL";
+    return IGA_EINVAL;
+  }
+  iga_s *h = new iga_s();
+  h->stream = (cudaStream_t)stream;
+  iga_status st = create_impl(h, d, b);
+  if (st != IGA_OK) {
+    g_create_err = h->err;
+    release(h);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return IGA_OK;
+}
+
+extern "C" void iga_destroy(iga_t h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  release(h);
+  delete h;
+}
+
+extern "C" const char *iga_last_error(iga_t h) {
+  if (!h) return g_create_err.c_str();
+  return h->err.c_str();
+}
+
+extern "C" iga_status iga_set_boundary_value(iga_t h, int axis, int side, double value) {
+  if (!h) return IGA_EINVAL;
+  if (axis < 0 || axis >= h->dim || side < 0 || side > 1 || !isfinite(value)) {
+    h->err = iga_format("bad boundary (axis %d, side %d)", axis, side);
+    return IGA_EINVAL;
+  }
+  h->bnd.flag[axis][side] = 1;
+  h->bnd.val[axis][side] = value;
+  h->K_valid = false;
+  return IGA_OK;
+}
+
+extern "C" iga_status iga_set_lambda(iga_t h, double lambda) {
+  if (!h || !isfinite(lambda)) return IGA_EINVAL;
+  h->lambda = lambda;
+  return IGA_OK;
+}
+
+extern "C" iga_status iga_get_pattern(iga_t h, int64_t *n, int64_t *nnz, const int64_t **rowptr, const int32_t **colidx) {
+  if (!h) return IGA_EINVAL;
+  if (n) *n = h->N;
+  if (nnz) *nnz = h->nnz;
+  if (rowptr) *rowptr = h->rowptr;
+  if (colidx) *colidx = h->colidx;
+  return IGA_OK;
+}
+
+extern "C" iga_status iga_form_residual(iga_t h, const double *U, double *F) {
+  if (!h) return IGA_EINVAL;
+  if (!U || !F || U == F) {
+    h->err = "U and F must be distinct non-NULL device pointers";
+    return IGA_EINVAL;
+  }
+  CK(launch_residual(h, U, F));
+  return IGA_OK;
+}
+
+extern "C" iga_status iga_form_jacobian(iga_t h, const double *U, void *vals, iga_precision prec) {
+  if (!h) return IGA_EINVAL;
+  if (!U || !vals) {
+    h->err = "U and vals must be non-NULL device pointers";
+    return IGA_EINVAL;
+  }
+  if (prec == IGA_FP64) {
+    CK(launch_jacobian64(h, U, (double *)vals, 0));
+  } else if (prec == IGA_JAC_TF32 || prec == IGA_JAC_BF16) {
+    CK(launch_jacobian32(h, U, (float *)vals, 0, (int)prec));
+  } else {
+    h->err = "unknown precision";
+    return IGA_EINVAL;
+  }
+  return IGA_OK;
+}
+
+extern "C" void iga_newton_defaults(iga_newton_opts *o) {
+  if (!o) return;
+  o->atol = 1e-10;
+  o->max_newton = 50;
+  o->gmres_restart = 60;
+  o->max_krylov = 4000;
+  o->krylov_rtol = 1e-2;
+  o->jac = IGA_FP64;
+  o->reuse_stiffness = 1;
+}
+
+// ---- small vector kernels of the Newton driver ----
+__global__ static void k_axpby(const double *__restrict__ x, double a, const double *__restrict__ y, double *__restrict__ out,
+                               int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = x[i] + a * y[i];
+}
+__global__ static void k_neg(const double *__restrict__ x, double *__restrict__ y, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) y[i] = -x[i];
+}
+
+static iga_status ensure_workspace(iga_s *h, int m, bool f32) {
+  const int64_t N = h->N;
+  if (!h->wk) CK(cudaMalloc((void **)&h->wk, (size_t)(8 * N + 64 + 2 * 1025) * sizeof(double)));
+  if (!h->ctl_host) CK(cudaMallocHost((void **)&h->ctl_host, 16 * sizeof(double)));
+  if (h->V_m != m) {
+    if (h->V) cudaFree(h->V);
+    if (h->red) cudaFree(h->red);
+    if (h->ctl) cudaFree(h->ctl);
+    h->V = nullptr; h->red = nullptr; h->ctl = nullptr;
+    CK(cudaMalloc((void **)&h->V, (size_t)(m + 1) * N * sizeof(double)));
+    CK(cudaMalloc((void **)&h->red, (size_t)(m + 2) * 304 * sizeof(double)));
+    CK(cudaMalloc((void **)&h->ctl, (size_t)((m + 1) * m + 4 * m + 16) * sizeof(double)));
+    h->V_m = m;
+  }
+  if (!f32 && !h->J64) CK(cudaMalloc((void **)&h->J64, h->nnz * sizeof(double)));
+  if (f32 && !h->J32) CK(cudaMalloc((void **)&h->J32, h->nnz * sizeof(float)));
+  return IGA_OK;
+}
+
+static iga_status norm_host(iga_s *h, const double *x, double *out) {
+  double *scal = h->wk + 8 * h->N;
+  CK(launch_norm2(h, x, scal));
+  CK(cudaMemcpyAsync(h->ctl_host + 8, scal, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *out = sqrt(h->ctl_host[8]);
+  return IGA_OK;
+}
+
+// Assemble the Newton Jacobian at U into h->J64 / h->J32.
+static iga_status newton_jacobian(iga_s *h, const double *U, bool f32, bool reuse) {
+  if (!reuse) {
+    if (f32) CK(launch_jacobian32(h, U, h->J32, 0, 1));
+    else CK(launch_jacobian64(h, U, h->J64, 0));
+    return IGA_OK;
+  }
+  if (f32) {
+    if (!h->Kstiff_f) CK(cudaMalloc((void **)&h->Kstiff_f, h->nnz * sizeof(float)));
+    if (!h->Mred_f) CK(cudaMalloc((void **)&h->Mred_f, h->nnz * sizeof(float)));
+    if (!h->K_valid_f) { CK(launch_jacobian32(h, nullptr, h->Kstiff_f, 1, 1)); h->K_valid_f = true; }
+    CK(launch_jacobian32(h, U, h->Mred_f, 2, 1));
+    CK(launch_combine32(h, h->Kstiff_f, h->Mred_f, h->J32));
+  } else {
+    if (!h->Kstiff) CK(cudaMalloc((void **)&h->Kstiff, h->nnz * sizeof(double)));
+    if (!h->Mred) CK(cudaMalloc((void **)&h->Mred, h->nnz * sizeof(double)));
+    if (!h->K_valid) { CK(launch_jacobian64(h, nullptr, h->Kstiff, 1)); h->K_valid = true; }
+    CK(launch_jacobian64(h, U, h->Mred, 2));
+    CK(launch_combine64(h, h->Kstiff, h->Mred, h->J64));
+  }
+  return IGA_OK;
+}
+
+extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts *opts_in, iga_newton_report *rep) {
+  if (!h) return IGA_EINVAL;
+  iga_newton_opts o;
+  iga_newton_defaults(&o);
+  if (opts_in) o = *opts_in;
+  if (!U || o.gmres_restart < 1 || o.gmres_restart > 1000 || o.max_newton < 0 || !(o.atol >= 0.0) ||
+      (o.jac != IGA_FP64 && o.jac != IGA_JAC_TF32 && o.jac != IGA_JAC_BF16)) {
+    h->err = "bad Newton options or NULL U";
+    return IGA_EINVAL;
+  }
+  iga_newton_report R;
+  memset(&R, 0, sizeof R);
+  R.status = IGA_ENOCONV;
+  const bool f32 = o.jac != IGA_FP64;
+  iga_status st = ensure_workspace(h, o.gmres_restart, f32);
+  if (st != IGA_OK) return st;
+  const int64_t N = h->N;
+  double *F = h->wk, *dU = h->wk + N, *Ut = h->wk + 2 * N, *Ft = h->wk + 3 * N;
+  int eg = (int)((N + 255) / 256);
+  if (eg > 608) eg = 608;
+  // stiffness part is rebuilt once per solve (reuse across Newton steps only)
+  h->K_valid = false;
+  h->K_valid_f = false;
+  CK(launch_residual(h, U, F));
+  double fn;
+  st = norm_host(h, F, &fn);
+  if (st != IGA_OK) return st;
+  R.fnorm0 = fn;
+  R.fnorm_hist[0] = fn;
+  int k = 0;
+  for (;;) {
+    if (!isfinite(fn)) { R.status = IGA_ENAN; break; }
+    if (fn <= o.atol) { R.status = IGA_OK; break; }
+    if (k >= o.max_newton) { R.status = IGA_ENOCONV; break; }
+    st = newton_jacobian(h, U, f32, o.reuse_stiffness != 0);
+    if (st != IGA_OK) return st;
+    k_neg<<<eg, 256, 0, h->stream>>>(F, Ft, N);
+    double rtol = o.krylov_rtol < fn ? o.krylov_rtol : fn;
+    double tol_abs = rtol * fn;
+    if (tol_abs < 1e-14 * fn) tol_abs = 1e-14 * fn;
+    int its = 0;
+    cudaError_t ce = cudaSuccess;
+    int grc = gmres_solve(h, f32 ? (const void *)h->J32 : (const void *)h->J64, f32, Ft, dU, tol_abs,
+                          o.gmres_restart, o.max_krylov, &its, &ce);
+    if (grc < 0) {
+      h->err = iga_format("GMRES: %s", cudaGetErrorString(ce));
+      return IGA_ECUDA;
+    }
+    R.krylov_its += its;
+    // backtracking on ||F||: halve the step until the norm decreases
+    double alpha = 1.0, ft = 0.0;
+    bool ok = false;
+    for (int ls = 0; ls <= 10; ls++) {
+      k_axpby<<<eg, 256, 0, h->stream>>>(U, alpha, dU, Ut, N);
+      CK(launch_residual(h, Ut, Ft));
+      st = norm_host(h, Ft, &ft);
+      if (st != IGA_OK) return st;
+      if (isfinite(ft) && ft < fn) { ok = true; break; }
+      alpha *= 0.5;
+    }
+    k++;
+    if (!ok) {
+      R.status = isfinite(ft) ? IGA_EDIVERGED : IGA_ENAN;
+      if (k < 64) R.fnorm_hist[k] = fn;
+      break;
+    }
+    CK(cudaMemcpyAsync(U, Ut, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(F, Ft, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    fn = ft;
+    if (k < 64) R.fnorm_hist[k] = fn;
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  R.newton_its = k;
+  R.fnorm = fn;
+  if (rep) *rep = R;
+  if (R.status != IGA_OK) h->err = iga_format("Newton stopped after %d steps with ||F|| = %.3e", k, fn);
+  return R.status;
+}
+
+extern "C" iga_status iga_solve_newton_host(iga_t h, double *U_host, const iga_newton_opts *opts, iga_newton_report *rep) {
+  if (!h || !U_host) return IGA_EINVAL;
+  if (!h->Uhost_dev) CK(cudaMalloc((void **)&h->Uhost_dev, h->N * sizeof(double)));
+  CK(cudaMemcpyAsync(h->Uhost_dev, U_host, h->N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  iga_status st = iga_solve_newton(h, h->Uhost_dev, opts, rep);
+  if (st == IGA_EINVAL || st == IGA_ECUDA || st == IGA_ENOMEM) return st;
+  CK(cudaMemcpyAsync(U_host, h->Uhost_dev, h->N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return st;
+}

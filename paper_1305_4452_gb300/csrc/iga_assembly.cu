@@ -1,0 +1,895 @@
+// Assembly kernels of libiga for sm_103a.
+//
+// Residual (Sec. 2.7 Algorithm 3 with Eq. residual): one fused kernel per
+// element tile -- gather U_e, sum-factorised interpolation of u~ and grad u~ to
+// the Gauss points, the Bratu integrand with the cached geometry factors, and
+// the transposed sum-factorised test-function contraction -- writes F_e; a
+// gather kernel adds the element vectors of each control variable in a fixed
+// order (no atomics) and applies the Dirichlet rows.
+//
+// Jacobian (Eq. jacobian): the element integrals are written as one symmetric
+// 4x4 (3x3 in 2D) coefficient field Q_{mu nu} per Gauss point contracted with
+// tensor products of 1D basis functions and derivatives.  Because every
+// Jacobian entry J_AB is a sum over the Gauss points shared by the supports of
+// A and B, the contraction is done direction by direction over the whole mesh
+// ("global" sum factorisation): stage 1 contracts axis 0 into 1D function pairs
+// (i0, j0), stage 2 axis 1, stage 3 axis 2, which writes each CSR entry exactly
+// once.  Terms whose remaining directions share a derivative pattern are merged
+// after each stage (16 -> 9 -> 4 -> 1 in 3D).  Every sum runs in a fixed order.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "iga_internal.h"
+
+DirArgs dir_args(const DirDev &d) {
+  DirArgs a;
+  a.p = d.p; a.q = d.q; a.nel = d.nel; a.n = d.n; a.np = d.np; a.X = d.X;
+  a.first = d.first; a.tab = d.tab; a.wq = d.wq; a.l = d.l; a.r = d.r;
+  a.pair_off = d.pair_off; a.pair_i = d.pair_i; a.pair_j = d.pair_j;
+  a.pair_x0 = d.pair_x0; a.pair_np = d.pair_np; a.pair_po = d.pair_po;
+  a.pair_val = d.pair_val; a.pair_val_f = d.pair_val_f;
+  a.node_e0 = d.node_e0; a.node_ne = d.node_ne;
+  return a;
+}
+
+template <int DIM> __host__ __device__ constexpr int ipow(int b) { return DIM == 2 ? b * b : b * b * b; }
+
+// ---------------------------------------------------------------------------
+// Geometry factors (Sec. 2.3 Eqs. 6-7, drational; Appendix A Eqs. identity,
+// dspatial): one thread per (element, Gauss point).  Run once per iga_create.
+// ---------------------------------------------------------------------------
+template <int DIM, int P>
+__global__ void __launch_bounds__(128) k_geometry(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ ctrl,
+                                                  const double *__restrict__ wts, const double *__restrict__ logk,
+                                                  GeomLayout gl, double *__restrict__ geom, int64_t nelem,
+                                                  int *__restrict__ err) {
+  constexpr int N1 = P + 1, Q = P + 1, NQ = ipow<DIM>(Q), NEN = ipow<DIM>(N1);
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nelem * NQ) return;
+  int64_t e = t / NQ;
+  int qp = (int)(t % NQ);
+  int g0 = qp % Q, g1 = (qp / Q) % Q, g2 = (DIM == 3) ? qp / (Q * Q) : 0;
+  int e0 = (int)(e % d0.nel), e1 = (int)((e / d0.nel) % d1.nel), e2 = (DIM == 3) ? (int)(e / ((int64_t)d0.nel * d1.nel)) : 0;
+  const double *T0 = d0.tab + ((size_t)e0 * Q + g0) * N1 * 2;
+  const double *T1 = d1.tab + ((size_t)e1 * Q + g1) * N1 * 2;
+  const double *T2 = (DIM == 3) ? d2.tab + ((size_t)e2 * Q + g2) * N1 * 2 : nullptr;
+  int f0 = d0.first[e0], f1 = d1.first[e1], f2 = (DIM == 3) ? d2.first[e2] : 0;
+  double W = 0.0, Wd[3] = {0.0, 0.0, 0.0}, Pc[3] = {0, 0, 0}, Pd[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, L = 0.0;
+  for (int a = 0; a < NEN; a++) {
+    int a0 = a % N1, a1 = (a / N1) % N1, a2 = (DIM == 3) ? a / (N1 * N1) : 0;
+    double b0 = T0[a0 * 2], db0 = T0[a0 * 2 + 1], b1 = T1[a1 * 2], db1 = T1[a1 * 2 + 1];
+    double b2 = (DIM == 3) ? T2[a2 * 2] : 1.0, db2 = (DIM == 3) ? T2[a2 * 2 + 1] : 0.0;
+    int64_t G = (f0 + a0) + (int64_t)d0.n * ((f1 + a1) + (int64_t)d1.n * (f2 + a2));
+    double M = b0 * b1 * b2;
+    double dM[3] = {db0 * b1 * b2, b0 * db1 * b2, b0 * b1 * db2};
+    double w = wts ? wts[G] : 1.0;
+    W += w * M;
+    for (int al = 0; al < DIM; al++) Wd[al] += w * dM[al];
+    if (ctrl)
+      for (int i = 0; i < DIM; i++) {
+        double xw = w * ctrl[G * DIM + i];
+        Pc[i] += xw * M;
+        for (int al = 0; al < DIM; al++) Pd[i][al] += xw * dM[al];
+      }
+    if (logk) L += w * logk[G] * M;
+  }
+  double invW = 1.0 / W;
+  double F[3][3];
+  for (int i = 0; i < DIM; i++)
+    for (int al = 0; al < DIM; al++)
+      F[i][al] = ctrl ? (Pd[i][al] - Pc[i] * invW * Wd[al]) * invW : (i == al ? 1.0 : 0.0);
+  double det, X[3][3];  // X[alpha][i] = xi_{alpha,i}
+  if (DIM == 2) {
+    det = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+    double id = 1.0 / det;
+    X[0][0] = F[1][1] * id; X[0][1] = -F[0][1] * id;
+    X[1][0] = -F[1][0] * id; X[1][1] = F[0][0] * id;
+  } else {
+    double c00 = F[1][1] * F[2][2] - F[1][2] * F[2][1];
+    double c01 = F[1][2] * F[2][0] - F[1][0] * F[2][2];
+    double c02 = F[1][0] * F[2][1] - F[1][1] * F[2][0];
+    det = F[0][0] * c00 + F[0][1] * c01 + F[0][2] * c02;
+    double id = 1.0 / det;
+    X[0][0] = c00 * id; X[1][0] = c01 * id; X[2][0] = c02 * id;
+    X[0][1] = (F[0][2] * F[2][1] - F[0][1] * F[2][2]) * id;
+    X[1][1] = (F[0][0] * F[2][2] - F[0][2] * F[2][0]) * id;
+    X[2][1] = (F[0][1] * F[2][0] - F[0][0] * F[2][1]) * id;
+    X[0][2] = (F[0][1] * F[1][2] - F[0][2] * F[1][1]) * id;
+    X[1][2] = (F[0][2] * F[1][0] - F[0][0] * F[1][2]) * id;
+    X[2][2] = (F[0][0] * F[1][1] - F[0][1] * F[1][0]) * id;
+  }
+  if (!(det > 0.0)) atomicExch(err, 1);  // inverted or degenerate geometry (status only)
+  double wq = d0.wq[(size_t)e0 * Q + g0] * d1.wq[(size_t)e1 * Q + g1] * ((DIM == 3) ? d2.wq[(size_t)e2 * Q + g2] : 1.0);
+  double jw = det * wq;
+  double kappa = logk ? exp(L * invW) : 1.0;
+  double g[3] = {Wd[0] * invW, Wd[1] * invW, Wd[2] * invW};
+  double S[3][3];
+  double sc = kappa * jw * invW * invW;
+  for (int al = 0; al < DIM; al++)
+    for (int be = 0; be < DIM; be++) {
+      double c = 0.0;
+      for (int i = 0; i < DIM; i++) c += X[al][i] * X[be][i];
+      S[al][be] = sc * c;
+    }
+  double *rec = geom + (size_t)e * gl.nf * NQ + qp;
+  rec[gl.invW * NQ] = invW;
+  for (int al = 0; al < DIM; al++) rec[(gl.g + al) * NQ] = g[al];
+  if (DIM == 2) {
+    rec[(gl.S + 0) * NQ] = S[0][0]; rec[(gl.S + 1) * NQ] = S[1][1]; rec[(gl.S + 2) * NQ] = S[0][1];
+  } else {
+    rec[(gl.S + 0) * NQ] = S[0][0]; rec[(gl.S + 1) * NQ] = S[1][1]; rec[(gl.S + 2) * NQ] = S[2][2];
+    rec[(gl.S + 3) * NQ] = S[0][1]; rec[(gl.S + 4) * NQ] = S[0][2]; rec[(gl.S + 5) * NQ] = S[1][2];
+  }
+  rec[gl.jwW * NQ] = jw * invW;
+  double gSg = 0.0;
+  for (int al = 0; al < DIM; al++) {
+    double sg = 0.0;
+    for (int be = 0; be < DIM; be++) sg += S[al][be] * g[be];
+    rec[(gl.Sg + al) * NQ] = sg;
+    gSg += g[al] * sg;
+  }
+  rec[gl.gSg * NQ] = gSg;
+  rec[gl.jwW2 * NQ] = jw * invW * invW;
+}
+
+// ---------------------------------------------------------------------------
+// Residual element kernel.  NE elements per CTA; all stages in shared memory.
+// ---------------------------------------------------------------------------
+template <int DIM, int P>
+struct ResSmem {
+  static constexpr int N1 = P + 1, Q = P + 1;
+  static constexpr int NEN = ipow<DIM>(N1), NQ = ipow<DIM>(Q);
+  static constexpr int TAB = DIM * Q * N1 * 2;
+  // per-element scratch: coefficients, two stage buffers of the largest size
+  static constexpr int BUF = (DIM == 3) ? 4 * NQ : 4 * NQ;
+  static constexpr int PER = TAB + NEN + 2 * BUF;
+};
+
+template <int DIM, int P, int NE>
+__global__ void __launch_bounds__(128) k_residual(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ U,
+                                                  const double *__restrict__ wts, const double *__restrict__ geom,
+                                                  GeomLayout gl, double lambda, double *__restrict__ Fe, int64_t nelem) {
+  using SM = ResSmem<DIM, P>;
+  constexpr int N1 = SM::N1, Q = SM::Q, NEN = SM::NEN, NQ = SM::NQ;
+  extern __shared__ double smem[];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int64_t ebase = (int64_t)blockIdx.x * NE;
+  // ---- load tables and gather w_A U_A (Algorithm 3: U_e <- U) ----
+  for (int idx = tid; idx < NE * (SM::TAB + NEN); idx += nt) {
+    int le = idx / (SM::TAB + NEN), k = idx % (SM::TAB + NEN);
+    int64_t e = ebase + le;
+    double *base = smem + (size_t)le * SM::PER;
+    if (e >= nelem) { base[k] = 0.0; continue; }
+    int e0 = (int)(e % d0.nel), e1 = (int)((e / d0.nel) % d1.nel), e2 = (DIM == 3) ? (int)(e / ((int64_t)d0.nel * d1.nel)) : 0;
+    if (k < SM::TAB) {
+      int ax = k / (Q * N1 * 2), r = k % (Q * N1 * 2);
+      const DirArgs &d = ax == 0 ? d0 : (ax == 1 ? d1 : d2);
+      int ee = ax == 0 ? e0 : (ax == 1 ? e1 : e2);
+      base[k] = d.tab[(size_t)ee * Q * N1 * 2 + r];
+    } else {
+      int a = k - SM::TAB;
+      int a0 = a % N1, a1 = (a / N1) % N1, a2 = (DIM == 3) ? a / (N1 * N1) : 0;
+      int64_t G = (d0.first[e0] + a0) + (int64_t)d0.n * ((d1.first[e1] + a1) + (int64_t)d1.n * ((DIM == 3 ? d2.first[e2] : 0) + a2));
+      base[k] = U[G] * (wts ? wts[G] : 1.0);
+    }
+  }
+  __syncthreads();
+  // B(ax, g, a, s) from the element's tables
+#define TB(base, ax, g, a, s) (base)[(((ax) * Q + (g)) * N1 + (a)) * 2 + (s)]
+  if (DIM == 3) {
+    // buffers: X = base + TAB + NEN (size 4*NQ), Y = X + BUF
+    // S1: T_s[a2][a1][g0] (s = 0,1) -> X[s][a2][a1][g0]
+    for (int idx = tid; idx < NE * 2 * N1 * N1 * Q; idx += nt) {
+      int le = idx / (2 * N1 * N1 * Q), k = idx % (2 * N1 * N1 * Q);
+      int s = k / (N1 * N1 * Q), r = k % (N1 * N1 * Q);
+      int a2 = r / (N1 * Q), a1 = (r / Q) % N1, g0 = r % Q;
+      double *base = smem + (size_t)le * SM::PER;
+      const double *C = base + SM::TAB;
+      double acc = 0.0;
+#pragma unroll
+      for (int a0 = 0; a0 < N1; a0++) acc = fma(TB(base, 0, g0, a0, s), C[(a2 * N1 + a1) * N1 + a0], acc);
+      (base + SM::TAB + NEN)[k] = acc;
+    }
+    __syncthreads();
+    // S2: V_{st}[a2][g1][g0] for (s,t) in {(0,0),(1,0),(0,1)} -> Y[c][a2][g1][g0]
+    for (int idx = tid; idx < NE * 3 * N1 * Q * Q; idx += nt) {
+      int le = idx / (3 * N1 * Q * Q), k = idx % (3 * N1 * Q * Q);
+      int c = k / (N1 * Q * Q), r = k % (N1 * Q * Q);
+      int a2 = r / (Q * Q), g1 = (r / Q) % Q, g0 = r % Q;
+      int s = (c == 1), t = (c == 2);
+      double *base = smem + (size_t)le * SM::PER;
+      const double *X = base + SM::TAB + NEN;
+      double acc = 0.0;
+#pragma unroll
+      for (int a1 = 0; a1 < N1; a1++) acc = fma(TB(base, 1, g1, a1, t), X[s * N1 * N1 * Q + (a2 * N1 + a1) * Q + g0], acc);
+      (base + SM::TAB + NEN + SM::BUF)[k] = acc;
+    }
+    __syncthreads();
+    // S3: u, d0, d1, d2 at [g2][g1][g0] -> X[k][qp]
+    for (int idx = tid; idx < NE * 4 * NQ; idx += nt) {
+      int le = idx / (4 * NQ), k = idx % (4 * NQ);
+      int c = k / NQ, qp = k % NQ;
+      int g2 = qp / (Q * Q), g1 = (qp / Q) % Q, g0 = qp % Q;
+      int src = (c == 1) ? 1 : (c == 2 ? 2 : 0), t = (c == 3);
+      double *base = smem + (size_t)le * SM::PER;
+      const double *Y = base + SM::TAB + NEN + SM::BUF;
+      double acc = 0.0;
+#pragma unroll
+      for (int a2 = 0; a2 < N1; a2++) acc = fma(TB(base, 2, g2, a2, t), Y[src * N1 * Q * Q + (a2 * Q + g1) * Q + g0], acc);
+      (base + SM::TAB + NEN)[k] = acc;
+    }
+    __syncthreads();
+  } else {
+    // S1: T_s[a1][g0] -> Y[s][a1][g0]
+    for (int idx = tid; idx < NE * 2 * N1 * Q; idx += nt) {
+      int le = idx / (2 * N1 * Q), k = idx % (2 * N1 * Q);
+      int s = k / (N1 * Q), r = k % (N1 * Q);
+      int a1 = r / Q, g0 = r % Q;
+      double *base = smem + (size_t)le * SM::PER;
+      const double *C = base + SM::TAB;
+      double acc = 0.0;
+#pragma unroll
+      for (int a0 = 0; a0 < N1; a0++) acc = fma(TB(base, 0, g0, a0, s), C[a1 * N1 + a0], acc);
+      (base + SM::TAB + NEN + SM::BUF)[k] = acc;
+    }
+    __syncthreads();
+    // S2: u, d0, d1 at [g1][g0] -> X[k][qp]
+    for (int idx = tid; idx < NE * 3 * NQ; idx += nt) {
+      int le = idx / (3 * NQ), k = idx % (3 * NQ);
+      int c = k / NQ, qp = k % NQ;
+      int g1 = qp / Q, g0 = qp % Q;
+      int src = (c == 1), t = (c == 2);
+      double *base = smem + (size_t)le * SM::PER;
+      const double *Y = base + SM::TAB + NEN + SM::BUF;
+      double acc = 0.0;
+#pragma unroll
+      for (int a1 = 0; a1 < N1; a1++) acc = fma(TB(base, 1, g1, a1, t), Y[src * N1 * Q + a1 * Q + g0], acc);
+      (base + SM::TAB + NEN)[k] = acc;
+    }
+    __syncthreads();
+  }
+  // ---- pointwise Bratu integrand at each Gauss point (Eq. residual) ----
+  for (int idx = tid; idx < NE * NQ; idx += nt) {
+    int le = idx / NQ, qp = idx % NQ;
+    int64_t e = ebase + le;
+    double *base = smem + (size_t)le * SM::PER;
+    double *X = base + SM::TAB + NEN;
+    if (e >= nelem) {
+      for (int c = 0; c <= DIM; c++) X[c * NQ + qp] = 0.0;
+      continue;
+    }
+    const double *rec = geom + (size_t)e * gl.nf * NQ + qp;
+    double ut = X[qp];
+    double r[3];
+    for (int a = 0; a < DIM; a++) r[a] = X[(1 + a) * NQ + qp] - ut * rec[(gl.g + a) * NQ];
+    double v[3];
+    if (DIM == 2) {
+      double s00 = rec[(gl.S + 0) * NQ], s11 = rec[(gl.S + 1) * NQ], s01 = rec[(gl.S + 2) * NQ];
+      v[0] = s00 * r[0] + s01 * r[1];
+      v[1] = s01 * r[0] + s11 * r[1];
+    } else {
+      double s00 = rec[(gl.S + 0) * NQ], s11 = rec[(gl.S + 1) * NQ], s22 = rec[(gl.S + 2) * NQ];
+      double s01 = rec[(gl.S + 3) * NQ], s02 = rec[(gl.S + 4) * NQ], s12 = rec[(gl.S + 5) * NQ];
+      v[0] = s00 * r[0] + s01 * r[1] + s02 * r[2];
+      v[1] = s01 * r[0] + s11 * r[1] + s12 * r[2];
+      v[2] = s02 * r[0] + s12 * r[1] + s22 * r[2];
+    }
+    double u = ut * rec[gl.invW * NQ];
+    double s = -rec[gl.jwW * NQ] * lambda * exp(u);
+    for (int a = 0; a < DIM; a++) s -= rec[(gl.g + a) * NQ] * v[a];
+    X[qp] = s;
+    for (int a = 0; a < DIM; a++) X[(1 + a) * NQ + qp] = v[a];
+  }
+  __syncthreads();
+  if (DIM == 3) {
+    // B3: Y00 = sum_g2 B2 s + B2' v2; Y10 = sum B2 v0; Y01 = sum B2 v1 -> Y[c][a2][g1][g0]
+    for (int idx = tid; idx < NE * 3 * N1 * Q * Q; idx += nt) {
+      int le = idx / (3 * N1 * Q * Q), k = idx % (3 * N1 * Q * Q);
+      int c = k / (N1 * Q * Q), r = k % (N1 * Q * Q);
+      int a2 = r / (Q * Q), g1 = (r / Q) % Q, g0 = r % Q;
+      double *base = smem + (size_t)le * SM::PER;
+      const double *X = base + SM::TAB + NEN;
+      double acc = 0.0;
+      int src = (c == 0) ? 0 : (c == 1 ? 1 : 2);
+#pragma unroll
+      for (int g2 = 0; g2 < Q; g2++) {
+        int qp = (g2 * Q + g1) * Q + g0;
+        acc = fma(TB(base, 2, g2, a2, 0), X[src * NQ + qp], acc);
+        if (c == 0) acc = fma(TB(base, 2, g2, a2, 1), X[3 * NQ + qp], acc);
+      }
+      (base + SM::TAB + NEN + SM::BUF)[k] = acc;
+    }
+    __syncthreads();
+    // B2: Z0 = sum_g1 B1 Y00 + B1' Y01; Z1 = sum B1 Y10 -> X[c][a2][a1][g0]
+    for (int idx = tid; idx < NE * 2 * N1 * N1 * Q; idx += nt) {
+      int le = idx / (2 * N1 * N1 * Q), k = idx % (2 * N1 * N1 * Q);
+      int c = k / (N1 * N1 * Q), r = k % (N1 * N1 * Q);
+      int a2 = r / (N1 * Q), a1 = (r / Q) % N1, g0 = r % Q;
+      double *base = smem + (size_t)le * SM::PER;
+      const double *Y = base + SM::TAB + NEN + SM::BUF;
+      double acc = 0.0;
+#pragma unroll
+      for (int g1 = 0; g1 < Q; g1++) {
+        int o = (a2 * Q + g1) * Q + g0;
+        if (c == 0) {
+          acc = fma(TB(base, 1, g1, a1, 0), Y[0 * N1 * Q * Q + o], acc);
+          acc = fma(TB(base, 1, g1, a1, 1), Y[2 * N1 * Q * Q + o], acc);
+        } else {
+          acc = fma(TB(base, 1, g1, a1, 0), Y[1 * N1 * Q * Q + o], acc);
+        }
+      }
+      (base + SM::TAB + NEN)[k] = acc;
+    }
+    __syncthreads();
+    // B1: F[a2][a1][a0] = sum_g0 B0 Z0 + B0' Z1, times w_A
+    for (int idx = tid; idx < NE * NEN; idx += nt) {
+      int le = idx / NEN, a = idx % NEN;
+      int64_t e = ebase + le;
+      if (e >= nelem) continue;
+      int a0 = a % N1, a1 = (a / N1) % N1, a2 = a / (N1 * N1);
+      double *base = smem + (size_t)le * SM::PER;
+      const double *Z = base + SM::TAB + NEN;
+      double acc = 0.0;
+#pragma unroll
+      for (int g0 = 0; g0 < Q; g0++) {
+        int o = (a2 * N1 + a1) * Q + g0;
+        acc = fma(TB(base, 0, g0, a0, 0), Z[o], acc);
+        acc = fma(TB(base, 0, g0, a0, 1), Z[N1 * N1 * Q + o], acc);
+      }
+      if (wts) {
+        int e0 = (int)(e % d0.nel), e1 = (int)((e / d0.nel) % d1.nel), e2 = (int)(e / ((int64_t)d0.nel * d1.nel));
+        int64_t G = (d0.first[e0] + a0) + (int64_t)d0.n * ((d1.first[e1] + a1) + (int64_t)d1.n * (d2.first[e2] + a2));
+        acc *= wts[G];
+      }
+      Fe[(size_t)e * NEN + a] = acc;
+    }
+  } else {
+    // B2: Z0[a1][g0] = sum_g1 B1 s + B1' v1; Z1 = sum B1 v0 -> Y[c][a1][g0]
+    for (int idx = tid; idx < NE * 2 * N1 * Q; idx += nt) {
+      int le = idx / (2 * N1 * Q), k = idx % (2 * N1 * Q);
+      int c = k / (N1 * Q), r = k % (N1 * Q);
+      int a1 = r / Q, g0 = r % Q;
+      double *base = smem + (size_t)le * SM::PER;
+      const double *X = base + SM::TAB + NEN;
+      double acc = 0.0;
+#pragma unroll
+      for (int g1 = 0; g1 < Q; g1++) {
+        int qp = g1 * Q + g0;
+        if (c == 0) {
+          acc = fma(TB(base, 1, g1, a1, 0), X[qp], acc);
+          acc = fma(TB(base, 1, g1, a1, 1), X[2 * NQ + qp], acc);
+        } else {
+          acc = fma(TB(base, 1, g1, a1, 0), X[NQ + qp], acc);
+        }
+      }
+      (base + SM::TAB + NEN + SM::BUF)[k] = acc;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < NE * NEN; idx += nt) {
+      int le = idx / NEN, a = idx % NEN;
+      int64_t e = ebase + le;
+      if (e >= nelem) continue;
+      int a0 = a % N1, a1 = a / N1;
+      double *base = smem + (size_t)le * SM::PER;
+      const double *Z = base + SM::TAB + NEN + SM::BUF;
+      double acc = 0.0;
+#pragma unroll
+      for (int g0 = 0; g0 < Q; g0++) {
+        acc = fma(TB(base, 0, g0, a0, 0), Z[a1 * Q + g0], acc);
+        acc = fma(TB(base, 0, g0, a0, 1), Z[N1 * Q + a1 * Q + g0], acc);
+      }
+      if (wts) {
+        int e0 = (int)(e % d0.nel), e1 = (int)(e / d0.nel);
+        int64_t G = (d0.first[e0] + a0) + (int64_t)d0.n * (d1.first[e1] + a1);
+        acc *= wts[G];
+      }
+      Fe[(size_t)e * NEN + a] = acc;
+    }
+  }
+#undef TB
+}
+
+// Gather F_A = sum of the element vectors of the elements containing A
+// (Algorithm 3: F_e -> F), fixed order e2, e1, e0 ascending; Dirichlet rows.
+template <int DIM>
+__global__ void k_gather_residual(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ Fe,
+                                  const double *__restrict__ U, BndArgs bnd, double *__restrict__ F, int64_t N, int N1) {
+  int64_t A = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (A >= N) return;
+  int i0 = (int)(A % d0.n), i1 = (int)((A / d0.n) % d1.n), i2 = (DIM == 3) ? (int)(A / ((int64_t)d0.n * d1.n)) : 0;
+  int NEN = (DIM == 3) ? N1 * N1 * N1 : N1 * N1;
+  double acc = 0.0;
+  int lo2 = (DIM == 3) ? d2.node_e0[i2] : 0, hi2 = (DIM == 3) ? lo2 + d2.node_ne[i2] : 1;
+  for (int e2 = lo2; e2 < hi2; e2++) {
+    int a2 = (DIM == 3) ? i2 - d2.first[e2] : 0;
+    for (int e1 = d1.node_e0[i1]; e1 < d1.node_e0[i1] + d1.node_ne[i1]; e1++) {
+      int a1 = i1 - d1.first[e1];
+      for (int e0 = d0.node_e0[i0]; e0 < d0.node_e0[i0] + d0.node_ne[i0]; e0++) {
+        int a0 = i0 - d0.first[e0];
+        int64_t e = e0 + (int64_t)d0.nel * (e1 + (int64_t)d1.nel * e2);
+        acc += Fe[(size_t)e * NEN + (a2 * N1 + a1) * N1 + a0];
+      }
+    }
+  }
+  // Dirichlet rows: F_A = U_A - g (face order decides the value at edges)
+  int idx[3] = {i0, i1, i2};
+  int nn[3] = {d0.n, d1.n, d2.n};
+  bool on = false;
+  double g = 0.0;
+  for (int ax = 0; ax < DIM; ax++) {
+    if (bnd.flag[ax][0] && idx[ax] == 0) { on = true; g = bnd.val[ax][0]; }
+    if (bnd.flag[ax][1] && idx[ax] == nn[ax] - 1) { on = true; g = bnd.val[ax][1]; }
+  }
+  F[A] = on ? U[A] - g : acc;
+}
+
+// ---------------------------------------------------------------------------
+// Q_00 at the Gauss points: sum-factorised value-only interpolation of u~,
+// then Q00 = cs * g^T S g - cr * jw/W^2 * lambda * exp(u~/W).
+// ---------------------------------------------------------------------------
+template <int DIM, int P, int NE>
+__global__ void __launch_bounds__(128) k_q00(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ U,
+                                             const double *__restrict__ wts, const double *__restrict__ geom, GeomLayout gl,
+                                             double lambda, double cs, double cr, double *__restrict__ Q00, int64_t nelem) {
+  using SM = ResSmem<DIM, P>;
+  constexpr int N1 = SM::N1, Q = SM::Q, NEN = SM::NEN, NQ = SM::NQ;
+  extern __shared__ double smem[];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int64_t ebase = (int64_t)blockIdx.x * NE;
+  for (int idx = tid; idx < NE * (SM::TAB + NEN); idx += nt) {
+    int le = idx / (SM::TAB + NEN), k = idx % (SM::TAB + NEN);
+    int64_t e = ebase + le;
+    double *base = smem + (size_t)le * SM::PER;
+    if (e >= nelem) { base[k] = 0.0; continue; }
+    int e0 = (int)(e % d0.nel), e1 = (int)((e / d0.nel) % d1.nel), e2 = (DIM == 3) ? (int)(e / ((int64_t)d0.nel * d1.nel)) : 0;
+    if (k < SM::TAB) {
+      int ax = k / (Q * N1 * 2), r = k % (Q * N1 * 2);
+      const DirArgs &d = ax == 0 ? d0 : (ax == 1 ? d1 : d2);
+      int ee = ax == 0 ? e0 : (ax == 1 ? e1 : e2);
+      base[k] = d.tab[(size_t)ee * Q * N1 * 2 + r];
+    } else {
+      int a = k - SM::TAB;
+      int a0 = a % N1, a1 = (a / N1) % N1, a2 = (DIM == 3) ? a / (N1 * N1) : 0;
+      int64_t G = (d0.first[e0] + a0) + (int64_t)d0.n * ((d1.first[e1] + a1) + (int64_t)d1.n * ((DIM == 3 ? d2.first[e2] : 0) + a2));
+      base[k] = U ? U[G] * (wts ? wts[G] : 1.0) : 0.0;
+    }
+  }
+  __syncthreads();
+#define TB(base, ax, g, a) (base)[(((ax) * Q + (g)) * N1 + (a)) * 2]
+  // contract axis 0, then 1, then 2 (values only)
+  if (DIM == 3) {
+    for (int idx = tid; idx < NE * N1 * N1 * Q; idx += nt) {
+      int le = idx / (N1 * N1 * Q), r = idx % (N1 * N1 * Q);
+      int a2 = r / (N1 * Q), a1 = (r / Q) % N1, g0 = r % Q;
+      double *base = smem + (size_t)le * SM::PER;
+      const double *C = base + SM::TAB;
+      double acc = 0.0;
+#pragma unroll
+      for (int a0 = 0; a0 < N1; a0++) acc = fma(TB(base, 0, g0, a0), C[(a2 * N1 + a1) * N1 + a0], acc);
+      (base + SM::TAB + NEN)[r] = acc;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < NE * N1 * Q * Q; idx += nt) {
+      int le = idx / (N1 * Q * Q), r = idx % (N1 * Q * Q);
+      int a2 = r / (Q * Q), g1 = (r / Q) % Q, g0 = r % Q;
+      double *base = smem + (size_t)le * SM::PER;
+      const double *X = base + SM::TAB + NEN;
+      double acc = 0.0;
+#pragma unroll
+      for (int a1 = 0; a1 < N1; a1++) acc = fma(TB(base, 1, g1, a1), X[(a2 * N1 + a1) * Q + g0], acc);
+      (base + SM::TAB + NEN + SM::BUF)[r] = acc;
+    }
+    __syncthreads();
+  } else {
+    for (int idx = tid; idx < NE * N1 * Q; idx += nt) {
+      int le = idx / (N1 * Q), r = idx % (N1 * Q);
+      int a1 = r / Q, g0 = r % Q;
+      double *base = smem + (size_t)le * SM::PER;
+      const double *C = base + SM::TAB;
+      double acc = 0.0;
+#pragma unroll
+      for (int a0 = 0; a0 < N1; a0++) acc = fma(TB(base, 0, g0, a0), C[a1 * N1 + a0], acc);
+      (base + SM::TAB + NEN + SM::BUF)[r] = acc;
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < NE * NQ; idx += nt) {
+    int le = idx / NQ, qp = idx % NQ;
+    int64_t e = ebase + le;
+    if (e >= nelem) continue;
+    double *base = smem + (size_t)le * SM::PER;
+    const double *Y = base + SM::TAB + NEN + SM::BUF;
+    double ut = 0.0;
+    if (DIM == 3) {
+      int g2 = qp / (Q * Q), g1 = (qp / Q) % Q, g0 = qp % Q;
+#pragma unroll
+      for (int a2 = 0; a2 < N1; a2++) ut = fma(TB(base, 2, g2, a2), Y[(a2 * Q + g1) * Q + g0], ut);
+    } else {
+      int g1 = qp / Q, g0 = qp % Q;
+#pragma unroll
+      for (int a1 = 0; a1 < N1; a1++) ut = fma(TB(base, 1, g1, a1), Y[a1 * Q + g0], ut);
+    }
+    const double *rec = geom + (size_t)e * gl.nf * NQ + qp;
+    double v = 0.0;
+    if (cs != 0.0) v = cs * rec[gl.gSg * NQ];
+    if (cr != 0.0) v -= cr * rec[gl.jwW2 * NQ] * lambda * exp(ut * rec[gl.invW * NQ]);
+    Q00[(size_t)e * NQ + qp] = v;
+  }
+#undef TB
+}
+
+// ---------------------------------------------------------------------------
+// Global sum-factorised Jacobian stages.
+// ---------------------------------------------------------------------------
+// A term of stage 1: Q field slot, sign, axis-0 pattern, output group.
+struct S1Term { int slot; int sign; int pat; int grp; };
+struct S1Terms { int n, ngrp, nslot; S1Term t[16]; int slot_field[10]; };  // slot_field: record field (-1 = Q00)
+struct SNTerm { int in; int pat; int out; };
+struct SNTerms { int n, nout; SNTerm t[9]; };
+
+// pattern code: (s,t) -> s + 2t ; s = derivative order of the test function, t of the trial
+static int patcode(int s, int t) { return s + 2 * t; }
+
+// Build the term lists of the three (3D) or two (2D) stages for a mode.
+// mode 0 = full Jacobian, 1 = stiffness only (Q00 = g^T S g), 2 = reaction only (Q00 only).
+struct StagePlan { S1Terms s1; SNTerms s2; SNTerms s3; };
+
+static StagePlan make_plan(int dim, const GeomLayout &gl, int mode) {
+  StagePlan P{};
+  int ns = dim * (dim + 1) / 2;
+  // slots: 0 = Q00, 1..ns = S, ns+1..ns+dim = Sg
+  P.s1.nslot = (mode == 2) ? 1 : 1 + ns + dim;
+  P.s1.slot_field[0] = -1;
+  for (int k = 0; k < ns; k++) P.s1.slot_field[1 + k] = gl.S + k;
+  for (int k = 0; k < dim; k++) P.s1.slot_field[1 + ns + k] = gl.Sg + k;
+  auto sidx = [&](int a, int b) {
+    if (a == b) return a;
+    if (a > b) { int t = a; a = b; b = t; }
+    if (dim == 2) return 2;
+    return (a == 0 && b == 1) ? 3 : ((a == 0 && b == 2) ? 4 : 5);
+  };
+  // keys of the groups after stage 1: (pattern axis1, pattern axis2)
+  int keys1[16], nk1 = 0;
+  auto key1_index = [&](int key) {
+    for (int i = 0; i < nk1; i++)
+      if (keys1[i] == key) return i;
+    keys1[nk1] = key;
+    return nk1++;
+  };
+  int nmu = dim + 1;
+  for (int mu = 0; mu < nmu; mu++)
+    for (int nu = 0; nu < nmu; nu++) {
+      if (mode == 2 && (mu != 0 || nu != 0)) continue;
+      int pat[3];
+      for (int ax = 0; ax < 3; ax++) pat[ax] = patcode(mu == ax + 1, nu == ax + 1);
+      S1Term T;
+      if (mu == 0 && nu == 0) { T.slot = 0; T.sign = 1; }
+      else if (mu == 0 || nu == 0) { T.slot = 1 + ns + (mu + nu - 1); T.sign = -1; }
+      else { T.slot = 1 + sidx(mu - 1, nu - 1); T.sign = 1; }
+      T.pat = pat[0];
+      int key = (dim == 3) ? pat[1] + 4 * pat[2] : pat[1];
+      T.grp = key1_index(key);
+      P.s1.t[P.s1.n++] = T;
+    }
+  P.s1.ngrp = nk1;
+  if (dim == 2) {
+    // final stage over axis 1: each group contracted with its axis-1 pattern
+    P.s2.nout = 1;
+    for (int i = 0; i < nk1; i++) P.s2.t[P.s2.n++] = SNTerm{i, keys1[i], 0};
+  } else {
+    int keys2[4], nk2 = 0;
+    for (int i = 0; i < nk1; i++) {
+      int pat1 = keys1[i] % 4, pat2 = keys1[i] / 4;
+      int o = -1;
+      for (int k = 0; k < nk2; k++)
+        if (keys2[k] == pat2) o = k;
+      if (o < 0) { keys2[nk2] = pat2; o = nk2++; }
+      P.s2.t[P.s2.n++] = SNTerm{i, pat1, o};
+    }
+    P.s2.nout = nk2;
+    P.s3.nout = 1;
+    for (int k = 0; k < nk2; k++) P.s3.t[P.s3.n++] = SNTerm{k, keys2[k], 0};
+  }
+  return P;
+}
+
+// Stage 1: contract axis 0 of the Q fields along one Gauss line (x1, x2).
+// out[grp][x2][x1][pi0] (3D) or out[grp][x1][pi0] (2D).
+template <typename T, int DIM, int P>
+__global__ void __launch_bounds__(256) k_stage1(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ geom,
+                                                const double *__restrict__ Q00, GeomLayout gl, S1Terms terms,
+                                                T *__restrict__ out) {
+  constexpr int Q = P + 1, NQ = ipow<DIM>(Q);
+  extern __shared__ double line[];  // [nslot][X0]
+  const int X0 = d0.X;
+  const int x1 = blockIdx.x, x2 = blockIdx.y;
+  const int e1 = x1 / Q, g1 = x1 % Q, e2 = x2 / Q, g2 = x2 % Q;
+  for (int idx = threadIdx.x; idx < terms.nslot * X0; idx += blockDim.x) {
+    int s = idx / X0, x0 = idx % X0;
+    int e0 = x0 / Q, g0 = x0 % Q;
+    int64_t e = e0 + (int64_t)d0.nel * (e1 + (int64_t)d1.nel * e2);
+    int qp = g0 + Q * (g1 + Q * g2);
+    int f = terms.slot_field[s];
+    line[idx] = (f < 0) ? Q00[(size_t)e * NQ + qp] : geom[((size_t)e * gl.nf + f) * NQ + qp];
+  }
+  __syncthreads();
+  const size_t plane = (size_t)d0.np * d1.X * (DIM == 3 ? d2.X : 1);
+  const size_t lineoff = ((size_t)x2 * d1.X + x1) * d0.np;
+  for (int pi = threadIdx.x; pi < d0.np; pi += blockDim.x) {
+    double acc[9];
+#pragma unroll
+    for (int g = 0; g < 9; g++) acc[g] = 0.0;
+    const int x0 = d0.pair_x0[pi], np = d0.pair_np[pi];
+    const double *pv = d0.pair_val + (size_t)d0.pair_po[pi] * 4;
+    for (int k = 0; k < np; k++) {
+      const double *pk = pv + 4 * k;
+#pragma unroll 1
+      for (int t = 0; t < terms.n; t++) {
+        const S1Term tt = terms.t[t];
+        double q = line[tt.slot * X0 + x0 + k];
+        double pr = pk[tt.pat];
+        if (tt.sign < 0) pr = -pr;
+        acc[tt.grp] = fma(pr, q, acc[tt.grp]);
+      }
+    }
+    for (int g = 0; g < terms.ngrp; g++) out[g * plane + lineoff + pi] = (T)acc[g];
+  }
+}
+
+// Stage 2 (3D): contract axis 1.  in[g1][x2][x1][pi0] -> out[g2][x2][pi1][pi0].
+template <typename T>
+__global__ void __launch_bounds__(128) k_stage2(DirArgs d0, DirArgs d1, DirArgs d2, SNTerms terms,
+                                                const T *__restrict__ in, T *__restrict__ out, int chunk) {
+  const int pi0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int x2 = blockIdx.z;
+  const int pa = blockIdx.y * chunk, pb = min(pa + chunk, d1.np);
+  if (pi0 >= d0.np) return;
+  const size_t inplane = (size_t)d0.np * d1.X * d2.X;
+  const size_t outplane = (size_t)d0.np * d1.np * d2.X;
+  for (int pi1 = pa; pi1 < pb; pi1++) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const int xs = d1.pair_x0[pi1], np = d1.pair_np[pi1];
+    const double *pv = d1.pair_val + (size_t)d1.pair_po[pi1] * 4;
+    for (int k = 0; k < np; k++) {
+      const size_t o = ((size_t)x2 * d1.X + xs + k) * d0.np + pi0;
+#pragma unroll 1
+      for (int t = 0; t < terms.n; t++) {
+        const SNTerm tt = terms.t[t];
+        acc[tt.out] = fma(pv[4 * k + tt.pat], (double)in[tt.in * inplane + o], acc[tt.out]);
+      }
+    }
+    for (int g = 0; g < terms.nout; g++) out[g * outplane + ((size_t)x2 * d1.np + pi1) * d0.np + pi0] = (T)acc[g];
+  }
+}
+
+// Position of the entry (A, B) in the CSR values, and Dirichlet handling.
+struct CsrArgs {
+  const int64_t *rowptr;
+  const double *wts;  // rational weights (J_AB carries w_A w_B) or null
+  BndArgs bnd;
+};
+
+__device__ __forceinline__ bool on_dirichlet(const BndArgs &b, int dim, const int *i, const int *n) {
+  bool on = false;
+  for (int ax = 0; ax < dim; ax++) {
+    if (b.flag[ax][0] && i[ax] == 0) on = true;
+    if (b.flag[ax][1] && i[ax] == n[ax] - 1) on = true;
+  }
+  return on;
+}
+
+// Final stage.  3D: contract axis 2 of in[g2][x2][pi1][pi0]; 2D: contract axis 1
+// of in[g1][x1][pi0].  Writes every CSR entry once; Dirichlet rows/columns fixed.
+template <typename T, typename V, int DIM>
+__global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d2, SNTerms terms, const T *__restrict__ in,
+                                               CsrArgs csr, V *__restrict__ vals, int chunk, int fix) {
+  const int pi0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pi0 >= d0.np) return;
+  const DirArgs &dl = (DIM == 3) ? d2 : d1;   // the axis contracted here
+  const int pmid = (DIM == 3) ? blockIdx.z : 0;  // pi1 in 3D
+  const int pa = blockIdx.y * chunk, pb = min(pa + chunk, dl.np);
+  const size_t plane = (DIM == 3) ? (size_t)d0.np * d1.np * d2.X : (size_t)d0.np * d1.X;
+  const int i0 = d0.pair_i[pi0], j0 = d0.pair_j[pi0];
+  const int o0 = pi0 - d0.pair_off[i0], w0 = d0.r[i0] - d0.l[i0] + 1;
+  int i1 = 0, j1 = 0, o1 = 0, w1 = 1;
+  if (DIM == 3) {
+    i1 = d1.pair_i[pmid]; j1 = d1.pair_j[pmid];
+    o1 = pmid - d1.pair_off[i1]; w1 = d1.r[i1] - d1.l[i1] + 1;
+  }
+  for (int pl = pa; pl < pb; pl++) {
+    double acc = 0.0;
+    const int xs = dl.pair_x0[pl], np = dl.pair_np[pl];
+    const double *pv = dl.pair_val + (size_t)dl.pair_po[pl] * 4;
+    for (int k = 0; k < np; k++) {
+      size_t o = (DIM == 3) ? (((size_t)(xs + k) * d1.np + pmid) * d0.np + pi0) : ((size_t)(xs + k) * d0.np + pi0);
+#pragma unroll 1
+      for (int t = 0; t < terms.n; t++) acc = fma(pv[4 * k + terms.t[t].pat], (double)in[terms.t[t].in * plane + o], acc);
+    }
+    const int il = dl.pair_i[pl], jl = dl.pair_j[pl];
+    const int ol = pl - dl.pair_off[il];
+    int I[3], J[3], n[3] = {d0.n, d1.n, d2.n};
+    int64_t A, B, pos;
+    if (DIM == 3) {
+      I[0] = i0; I[1] = i1; I[2] = il; J[0] = j0; J[1] = j1; J[2] = jl;
+      A = i0 + (int64_t)d0.n * (i1 + (int64_t)d1.n * il);
+      B = j0 + (int64_t)d0.n * (j1 + (int64_t)d1.n * jl);
+      pos = csr.rowptr[A] + ((int64_t)ol * w1 + o1) * w0 + o0;
+    } else {
+      I[0] = i0; I[1] = il; J[0] = j0; J[1] = jl;
+      A = i0 + (int64_t)d0.n * il;
+      B = j0 + (int64_t)d0.n * jl;
+      pos = csr.rowptr[A] + (int64_t)ol * w0 + o0;
+    }
+    if (csr.wts) acc *= csr.wts[A] * csr.wts[B];
+    // fix 1: identity row and zero column (full or stiffness Jacobian);
+    // fix 2: zero row and column (the reaction part added to a fixed stiffness)
+    if (fix) {
+      bool ra = on_dirichlet(csr.bnd, DIM, I, n), cb = on_dirichlet(csr.bnd, DIM, J, n);
+      if (ra) acc = (fix == 1 && A == B) ? 1.0 : 0.0;
+      else if (cb) acc = 0.0;
+    }
+    vals[pos] = (V)acc;
+  }
+}
+
+// Column indices of the CSR pattern (Sec. 2.5): row A lists the lexicographic
+// product of the BasisStencil ranges, axis 0 fastest, so columns ascend.
+__global__ void k_colidx(DirArgs d0, DirArgs d1, DirArgs d2, int dim, const int64_t *__restrict__ rowptr,
+                         int32_t *__restrict__ colidx, int64_t N) {
+  int64_t A = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (A >= N) return;
+  int i0 = (int)(A % d0.n), i1 = (int)((A / d0.n) % d1.n), i2 = (dim == 3) ? (int)(A / ((int64_t)d0.n * d1.n)) : 0;
+  int64_t k = rowptr[A];
+  int l2 = dim == 3 ? d2.l[i2] : 0, r2 = dim == 3 ? d2.r[i2] : 0;
+  for (int j2 = l2; j2 <= r2; j2++)
+    for (int j1 = d1.l[i1]; j1 <= d1.r[i1]; j1++)
+      for (int j0 = d0.l[i0]; j0 <= d0.r[i0]; j0++)
+        colidx[k++] = (int32_t)(j0 + (int64_t)d0.n * (j1 + (int64_t)d1.n * j2));
+}
+
+// J = K + M: add the reaction-only values (on the same CSR layout) to the cached
+// stiffness; Dirichlet rows/columns were fixed in both with fix = 1 / 0.
+template <typename V>
+__global__ void k_combine(const V *__restrict__ K, const V *__restrict__ M, V *__restrict__ J, int64_t nnz) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < nnz) J[k] = K[k] + M[k];
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+#define DISPATCH_DP(DIM_, P_, CALL)                         \
+  do {                                                      \
+    if ((DIM_) == 2) {                                      \
+      switch (P_) {                                         \
+        case 1: { constexpr int D = 2, PP = 1; CALL; } break; \
+        case 2: { constexpr int D = 2, PP = 2; CALL; } break; \
+        case 3: { constexpr int D = 2, PP = 3; CALL; } break; \
+        case 4: { constexpr int D = 2, PP = 4; CALL; } break; \
+      }                                                     \
+    } else {                                                \
+      switch (P_) {                                         \
+        case 1: { constexpr int D = 3, PP = 1; CALL; } break; \
+        case 2: { constexpr int D = 3, PP = 2; CALL; } break; \
+        case 3: { constexpr int D = 3, PP = 3; CALL; } break; \
+        case 4: { constexpr int D = 3, PP = 4; CALL; } break; \
+      }                                                     \
+    }                                                       \
+  } while (0)
+
+cudaError_t launch_geometry(iga_s *h, const double *ctrl_dev, const double *logk_dev) {
+  int *err = nullptr;
+  cudaError_t ce = cudaMallocAsync((void **)&err, sizeof(int), h->stream);
+  if (ce) return ce;
+  cudaMemsetAsync(err, 0, sizeof(int), h->stream);
+  DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
+  int NQ = (h->dim == 3) ? h->q * h->q * h->q : h->q * h->q;
+  int64_t tot = h->nelem * NQ;
+  unsigned grid = (unsigned)((tot + 127) / 128);
+  DISPATCH_DP(h->dim, h->p, (k_geometry<D, PP><<<grid, 128, 0, h->stream>>>(a0, a1, a2, ctrl_dev, h->weights, logk_dev, h->gl, h->geom, h->nelem, err)));
+  int herr = 0;
+  cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  ce = cudaStreamSynchronize(h->stream);
+  cudaFreeAsync(err, h->stream);
+  if (ce) return ce;
+  if (herr) return cudaErrorInvalidValue;  // det <= 0 somewhere: reported as EINVAL by the caller
+  return cudaGetLastError();
+}
+
+template <int DIM, int P>
+static size_t res_smem(int NE) { return (size_t)NE * ResSmem<DIM, P>::PER * sizeof(double); }
+
+cudaError_t launch_residual(iga_s *h, const double *U, double *F) {
+  DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
+  constexpr int NE = 4;
+  unsigned grid = (unsigned)((h->nelem + NE - 1) / NE);
+  DISPATCH_DP(h->dim, h->p, ({
+    size_t sm = res_smem<D, PP>(NE);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_residual<D, PP, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_residual<D, PP, NE><<<grid, 128, sm, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, h->lambda, h->Fe, h->nelem);
+  }));
+  unsigned g2 = (unsigned)((h->N + 255) / 256);
+  if (h->dim == 3)
+    k_gather_residual<3><<<g2, 256, 0, h->stream>>>(a0, a1, a2, h->Fe, U, h->bnd, F, h->N, h->p + 1);
+  else
+    k_gather_residual<2><<<g2, 256, 0, h->stream>>>(a0, a1, a2, h->Fe, U, h->bnd, F, h->N, h->p + 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_q00(iga_s *h, const double *U, double cs, double cr) {
+  DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
+  constexpr int NE = 4;
+  unsigned grid = (unsigned)((h->nelem + NE - 1) / NE);
+  DISPATCH_DP(h->dim, h->p, ({
+    size_t sm = res_smem<D, PP>(NE);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_q00<D, PP, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_q00<D, PP, NE><<<grid, 128, sm, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, h->lambda, cs, cr, h->Q00, h->nelem);
+  }));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_q00(iga_s *h, const double *U, double lambda_scale) { return launch_q00(h, U, 1.0, lambda_scale); }
+
+template <typename T, typename V>
+static cudaError_t jacobian_stages(iga_s *h, V *vals, int mode, int fix) {
+  DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
+  StagePlan plan = make_plan(h->dim, h->gl, mode);
+  T *T1 = (T *)h->T1, *T2 = (T *)h->T2;
+  // stage 1
+  {
+    dim3 grid(a1.X, h->dim == 3 ? a2.X : 1);
+    size_t sm = (size_t)plan.s1.nslot * a0.X * sizeof(double);
+    DISPATCH_DP(h->dim, h->p, ({
+      if (sm > 48 * 1024) cudaFuncSetAttribute(k_stage1<T, D, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_stage1<T, D, PP><<<grid, 256, sm, h->stream>>>(a0, a1, a2, h->geom, h->Q00, h->gl, plan.s1, T1);
+    }));
+  }
+  CsrArgs csr{h->rowptr, h->weights, h->bnd};
+  const int chunk = 8;
+  if (h->dim == 3) {
+    dim3 g2((a0.np + 127) / 128, (a1.np + chunk - 1) / chunk, a2.X);
+    k_stage2<T><<<g2, 128, 0, h->stream>>>(a0, a1, a2, plan.s2, T1, T2, chunk);
+    dim3 g3((a0.np + 127) / 128, (a2.np + chunk - 1) / chunk, a1.np);
+    k_final<T, V, 3><<<g3, 128, 0, h->stream>>>(a0, a1, a2, plan.s3, T2, csr, vals, chunk, fix);
+  } else {
+    dim3 g3((a0.np + 127) / 128, (a1.np + chunk - 1) / chunk, 1);
+    k_final<T, V, 2><<<g3, 128, 0, h->stream>>>(a0, a1, a2, plan.s2, T1, csr, vals, chunk, fix);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobian64(iga_s *h, const double *U, double *vals, int mode) {
+  // mode 0: full; 1: stiffness only (U ignored); 2: reaction only (no Dirichlet fix)
+  double cs = (mode == 2) ? 0.0 : 1.0, cr = (mode == 1) ? 0.0 : 1.0;
+  cudaError_t ce = launch_q00(h, U, cs, cr);
+  if (ce) return ce;
+  return jacobian_stages<double, double>(h, vals, mode, mode == 2 ? 2 : 1);
+}
+
+cudaError_t launch_jacobian32(iga_s *h, const double *U, float *vals, int mode, int opmode) {
+  (void)opmode;
+  double cs = (mode == 2) ? 0.0 : 1.0, cr = (mode == 1) ? 0.0 : 1.0;
+  cudaError_t ce = launch_q00(h, U, cs, cr);
+  if (ce) return ce;
+  return jacobian_stages<float, float>(h, vals, mode, mode == 2 ? 2 : 1);
+}
+
+cudaError_t launch_combine64(iga_s *h, const double *K, const double *M, double *vals) {
+  unsigned g = (unsigned)((h->nnz + 255) / 256);
+  k_combine<double><<<g, 256, 0, h->stream>>>(K, M, vals, h->nnz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine32(iga_s *h, const float *K, const float *M, float *vals) {
+  unsigned g = (unsigned)((h->nnz + 255) / 256);
+  k_combine<float><<<g, 256, 0, h->stream>>>(K, M, vals, h->nnz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colidx(iga_s *h) {
+  DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
+  unsigned g = (unsigned)((h->N + 255) / 256);
+  k_colidx<<<g, 256, 0, h->stream>>>(a0, a1, a2, h->dim, h->rowptr, h->colidx, h->N);
+  return cudaGetLastError();
+}

@@ -1,0 +1,156 @@
+// Internal state and kernel interfaces of libiga (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/iga.h"
+
+#define IGA_MAXP 4                 // largest supported degree
+#define IGA_MAXN (IGA_MAXP + 1)    // largest number of nonzero 1D functions per element
+#define IGA_MAXQ (IGA_MAXP + 1)    // largest Gauss rule (q = p + 1)
+
+// Number of per-quadrature-point geometry fields (see GeomField) for each dimension.
+#define IGA_NGF2 11
+#define IGA_NGF3 16
+
+// Geometry factor record, one set per quadrature point, element-major layout
+// G[e][field][qp].  With W = sum w_A M_A, g = grad_xi W / W, C = Xi Xi^T
+// (Xi = inverse of dx/dxi), jw = det(dx/dxi) * (Gauss weight) * prod(span/2):
+//   invW            1 / W
+//   g[a]            grad_xi W / W
+//   S[ab]           kappa * jw * C / W^2   (symmetric; 2D: 00,11,01; 3D: 00,11,22,01,02,12)
+//   jwW             jw / W
+//   Sg[a]           (S g)_a
+//   gSg             g^T S g
+//   jwW2            jw / W^2
+// These turn the rational-basis integrands into polynomial-basis contractions:
+//   F_A = w_A sum_q [ grad M_A . v + M_A s ],  v = S (grad ũ - ũ g),  s = -g.v - jwW lambda e^u
+//   J_AB = w_A w_B sum_q sum_{mu,nu} Q_{mu nu} D_mu M_A D_nu M_B, with
+//   Q_00 = gSg - jwW2 lambda e^u, Q_0a = -Sg_a, Q_ab = S_ab
+// where ũ = sum (w_A U_A) M_A and u = ũ / W.
+struct GeomLayout {
+  int nf;      // number of fields
+  int invW, g, S, jwW, Sg, gSg, jwW2;  // field offsets
+};
+
+GeomLayout geom_layout(int dim);
+
+struct Dir {
+  int p = 0, q = 0, nel = 0, n = 0;
+  std::vector<double> knots;
+  std::vector<int> first;      // [nel] first nonzero function of each element (span - p)
+  std::vector<double> tab;     // [nel][q][p+1][2]: B, dB/dxi at the Gauss points
+  std::vector<double> wq;      // [nel][q]: Gauss weight * span/2
+  std::vector<int> l, r;       // [n] BasisStencil range
+  std::vector<int> pair_off;   // [n+1] first pair of each function
+  std::vector<int> pair_j;     // [P] second function of each pair
+  std::vector<int> pair_i;     // [P] first function of each pair
+  std::vector<int> pair_x0;    // [P] first Gauss point (global index) of the overlap
+  std::vector<int> pair_np;    // [P] number of Gauss points in the overlap
+  std::vector<int> pair_po;    // [P] offset into pair_val (in points)
+  std::vector<double> pair_val;// [sum np][4]: B_i B_j, B'_i B_j, B_i B'_j, B'_i B'_j
+  std::vector<int> node_e0;    // [n] first element containing the function
+  std::vector<int> node_ne;    // [n] number of elements containing it
+  int npairs() const { return (int)pair_j.size(); }
+  int X() const { return nel * q; }
+};
+
+// Device copies of the per-direction data.
+struct DirDev {
+  int p, q, nel, n, np, X;
+  int *first;
+  double *tab;
+  double *wq;
+  int *l, *r;
+  int *pair_off, *pair_i, *pair_j, *pair_x0, *pair_np, *pair_po;
+  double *pair_val;
+  float *pair_val_f;  // FP32 copy for the mixed-precision stages
+  int *node_e0, *node_ne;
+};
+
+struct DirArgs {  // passed by value to kernels
+  int p, q, nel, n, np, X;
+  const int *first;
+  const double *tab;
+  const double *wq;
+  const int *l, *r;
+  const int *pair_off, *pair_i, *pair_j, *pair_x0, *pair_np, *pair_po;
+  const double *pair_val;
+  const float *pair_val_f;
+  const int *node_e0, *node_ne;
+};
+
+struct BndArgs {
+  int flag[3][2];
+  double val[3][2];
+};
+
+struct iga_s {
+  int dim = 0, p = 0, q = 0;
+  int64_t N = 0, nnz = 0, nelem = 0, nqp = 0;
+  Dir dir[3];
+  DirDev ddev[3];
+  cudaStream_t stream = nullptr;
+  double lambda = 0.0;
+  bool has_geom = false, has_w = false, has_kappa = false;
+  BndArgs bnd{};
+  GeomLayout gl{};
+  std::string err;
+
+  // device buffers owned by the library
+  int64_t *rowptr = nullptr;
+  int32_t *colidx = nullptr;
+  double *weights = nullptr;   // [N] or null
+  double *geom = nullptr;      // [nelem][nf][nq]
+  double *Fe = nullptr;        // [nelem][nen] element residuals
+  double *Q00 = nullptr;       // [nelem][nq]
+  void *T1 = nullptr;          // stage-1 intermediate
+  void *T2 = nullptr;          // stage-2 intermediate (3D)
+  size_t T1_bytes = 0, T2_bytes = 0;
+  double *Kstiff = nullptr;    // U-independent part of J (Newton reuse), nnz doubles
+  float *Kstiff_f = nullptr;   // FP32 copy for mixed Newton
+  double *Mred = nullptr;      // reaction-only contraction on the CSR layout
+  float *Mred_f = nullptr;
+  bool K_valid = false, K_valid_f = false;  // Kstiff / Kstiff_f hold the current stiffness
+  double *Uhost_dev = nullptr; // device copy of U for the host-buffer solve
+  // Newton / Krylov workspace
+  double *J64 = nullptr;
+  float *J32 = nullptr;
+  double *wk = nullptr;        // vectors: F, dU, Utrial, Ftrial, diag, z, w, ...
+  double *V = nullptr;         // GMRES basis (m+1) x N
+  int V_m = 0;
+  double *red = nullptr;       // reduction partials
+  double *ctl = nullptr;       // GMRES scalar control block (device)
+  double *ctl_host = nullptr;  // pinned mirror
+  int nblk_red = 0;
+};
+
+// ---- host set-up (iga_host.cpp) ----
+iga_status iga_build_dirs(iga_s *h, const iga_desc *d);
+void iga_rowptr(const iga_s *h, std::vector<int64_t> &rowptr);
+
+// ---- kernels (iga_assembly.cu) ----
+DirArgs dir_args(const DirDev &d);
+cudaError_t launch_geometry(iga_s *h, const double *ctrl_dev, const double *logk_dev);
+cudaError_t launch_colidx(iga_s *h);
+cudaError_t launch_residual(iga_s *h, const double *U, double *F);
+cudaError_t launch_q00(iga_s *h, const double *U, double lambda_scale);
+// Jacobian: mode 0 = full, 1 = stiffness only (U-independent), 2 = reaction only
+cudaError_t launch_jacobian64(iga_s *h, const double *U, double *vals, int mode);
+cudaError_t launch_jacobian32(iga_s *h, const double *U, float *vals, int mode, int opmode);
+cudaError_t launch_combine64(iga_s *h, const double *K, const double *Mred, double *vals);
+cudaError_t launch_combine32(iga_s *h, const float *K, const float *Mred, float *vals);
+
+// ---- Krylov (iga_krylov.cu) ----
+cudaError_t launch_spmv64(iga_s *h, const double *vals, const double *x, double *y);
+cudaError_t launch_spmv32(iga_s *h, const float *vals, const double *x, double *y);
+cudaError_t launch_diag_inv(iga_s *h, const void *vals, int is_f32, double *dinv);
+cudaError_t launch_norm2(iga_s *h, const double *x, double *out_dev);
+cudaError_t launch_nan_check(iga_s *h, const double *x, double *out_dev);
+int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double *x, double rtol_abs,
+                int m, int maxit, int *its, cudaError_t *cerr);
+
+std::string iga_format(const char *fmt, ...);

@@ -1,0 +1,387 @@
+// Krylov kernels of libiga: CSR SpMV, Jacobi scaling, deterministic dot
+// products and norms, and restarted GMRES(m) with right Jacobi preconditioning
+// and classical Gram-Schmidt applied twice, all in FP64.  The scalar GMRES
+// bookkeeping (Givens rotations, residual estimate, triangular solve) runs in
+// one-thread kernels on the device; every kernel of an iteration returns at
+// once when the device "done" flag is set, so the host enqueues several
+// iterations between synchronisations.  Every reduction has a fixed shape and
+// order, so results do not depend on scheduling.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "iga_internal.h"
+
+namespace {
+
+constexpr int RED_THREADS = 256;
+constexpr int RED_BLOCKS = 304;  // 2 x 152 SMs
+
+// GMRES scalar block layout (doubles) for restart m
+struct GmLayout {
+  int m;
+  int H, cs, sn, g, y, flags;
+  int size;
+};
+__host__ __device__ inline GmLayout gm_layout(int m) {
+  GmLayout L;
+  L.m = m;
+  L.H = 0;                     // (m+1) x m, column j at H + j*(m+1)
+  L.cs = L.H + (m + 1) * m;
+  L.sn = L.cs + m;
+  L.g = L.sn + m;              // m+1
+  L.y = L.g + m + 1;           // m
+  L.flags = L.y + m;           // 0: done, 1: iterations in cycle, 2: residual estimate, 3: breakdown
+  L.size = L.flags + 8;
+  return L;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum with a fixed tree; result valid in thread 0
+__device__ double block_sum(double v, double *sh) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  __syncthreads();
+  return r;
+}
+
+template <typename V, int LPR>
+__global__ void __launch_bounds__(256) k_spmv(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                              const V *__restrict__ val, const double *__restrict__ x,
+                                              double *__restrict__ y, int64_t N, const double *__restrict__ done) {
+  if (done && done[0] != 0.0) return;
+  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t row = gid / LPR;
+  int lane = threadIdx.x % LPR;
+  if (row >= N) return;
+  int64_t a = rowptr[row], b = rowptr[row + 1];
+  double acc = 0.0;
+  for (int64_t k = a + lane; k < b; k += LPR) acc = fma((double)val[k], x[col[k]], acc);
+#pragma unroll
+  for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, LPR);
+  if (lane == 0) y[row] = acc;
+}
+
+template <typename V>
+__global__ void k_diag_inv(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col, const V *__restrict__ val,
+                           double *__restrict__ dinv, int64_t N) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  int64_t lo = rowptr[r], hi = rowptr[r + 1] - 1;
+  double d = 0.0;
+  while (lo <= hi) {  // columns ascend: binary search for the diagonal
+    int64_t mid = (lo + hi) >> 1;
+    int c = col[mid];
+    if (c == r) { d = (double)val[mid]; break; }
+    if (c < r) lo = mid + 1; else hi = mid - 1;
+  }
+  dinv[r] = (d != 0.0) ? 1.0 / d : 1.0;
+}
+
+// partial[blk] = sum over the block's fixed row range of x*y
+__global__ void __launch_bounds__(RED_THREADS) k_dot_partial(const double *__restrict__ x, const double *__restrict__ y,
+                                                             double *__restrict__ partial, int64_t N, const double *__restrict__ done) {
+  __shared__ double sh[32];
+  if (done && done[0] != 0.0) return;
+  int64_t per = (N + gridDim.x - 1) / gridDim.x;
+  int64_t a = blockIdx.x * per, b = min(N, a + per);
+  double acc = 0.0;
+  for (int64_t r = a + threadIdx.x; r < b; r += blockDim.x) acc = fma(x[r], y[r], acc);
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// multi-dot: partial[i][blk] = sum_r V[i][r] w[r], i = 0..j (grid.y = j+1)
+__global__ void __launch_bounds__(RED_THREADS) k_mdot_partial(const double *__restrict__ Vb, int64_t ld,
+                                                              const double *__restrict__ w, double *__restrict__ partial,
+                                                              int64_t N, const double *__restrict__ done) {
+  __shared__ double sh[32];
+  if (done[0] != 0.0) return;
+  int i = blockIdx.y;
+  const double *v = Vb + (size_t)i * ld;
+  int64_t per = (N + gridDim.x - 1) / gridDim.x;
+  int64_t a = blockIdx.x * per, b = min(N, a + per);
+  double acc = 0.0;
+  for (int64_t r = a + threadIdx.x; r < b; r += blockDim.x) acc = fma(v[r], w[r], acc);
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[(size_t)i * gridDim.x + blockIdx.x] = acc;
+}
+
+// out[i] (+)= sum_blk partial[i][blk] in index order (one block per i)
+__global__ void __launch_bounds__(RED_THREADS) k_reduce_rows(const double *__restrict__ partial, int nb, double *__restrict__ out,
+                                                             int accumulate, const double *__restrict__ done) {
+  __shared__ double sh[32];
+  if (done && done[0] != 0.0) return;
+  int i = blockIdx.x;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) acc += partial[(size_t)i * nb + k];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) out[i] = accumulate ? out[i] + acc : acc;
+}
+
+// w -= sum_{i<=j} h[i] V[i]
+__global__ void k_orth_update(const double *__restrict__ Vb, int64_t ld, const double *__restrict__ h, int jp1,
+                              double *__restrict__ w, int64_t N, const double *__restrict__ done) {
+  __shared__ double hs[1024];
+  if (done[0] != 0.0) return;
+  for (int i = threadIdx.x; i < jp1; i += blockDim.x) hs[i] = h[i];
+  __syncthreads();
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x) {
+    double acc = w[r];
+    for (int i = 0; i < jp1; i++) acc = fma(-hs[i], Vb[(size_t)i * ld + r], acc);
+    w[r] = acc;
+  }
+}
+
+// v_next = w / hnorm ; z = dinv .* v_next   (skipped on breakdown)
+__global__ void k_normalize(const double *w, const double *__restrict__ hn, double *vnext,
+                            const double *__restrict__ dinv, double *__restrict__ z, int64_t N, const double *__restrict__ done) {
+  if (done[0] != 0.0) return;
+  double s = hn[0];
+  double inv = (s > 0.0) ? 1.0 / s : 0.0;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x) {
+    double v = w[r] * inv;
+    vnext[r] = v;
+    z[r] = dinv[r] * v;
+  }
+}
+
+// h[i] += d[i] for i < n (one block)
+__global__ void k_add_vec(double *__restrict__ h, const double *__restrict__ d, int n, const double *__restrict__ done) {
+  if (done[0] != 0.0) return;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) h[i] += d[i];
+}
+
+// Givens step for column j of H (one thread)
+__global__ void k_givens(double *__restrict__ gm, int m, int j, double tol) {
+  GmLayout L = gm_layout(m);
+  double *fl = gm + L.flags;
+  if (fl[0] != 0.0) return;
+  double *Hj = gm + L.H + (size_t)j * (m + 1);
+  // H[j+1][j] arrives as a sum of squares; take the root
+  double hn = sqrt(Hj[j + 1]);
+  Hj[j + 1] = hn;
+  for (int i = 0; i < j; i++) {
+    double c = gm[L.cs + i], s = gm[L.sn + i];
+    double a = Hj[i], b = Hj[i + 1];
+    Hj[i] = c * a + s * b;
+    Hj[i + 1] = -s * a + c * b;
+  }
+  double a = Hj[j], b = Hj[j + 1];
+  double r = hypot(a, b);
+  double c = (r > 0.0) ? a / r : 1.0, s = (r > 0.0) ? b / r : 0.0;
+  gm[L.cs + j] = c;
+  gm[L.sn + j] = s;
+  Hj[j] = r;
+  Hj[j + 1] = 0.0;
+  double gj = gm[L.g + j];
+  gm[L.g + j] = c * gj;
+  gm[L.g + j + 1] = -s * gj;
+  double res = fabs(gm[L.g + j + 1]);
+  fl[1] = j + 1;
+  fl[2] = res;
+  bool breakdown = !(hn > 1e-300) || !isfinite(res);
+  if (breakdown) fl[3] = 1.0;
+  if (res <= tol || breakdown || j + 1 == m) fl[0] = 1.0;
+  // keep the norm for the normalisation kernel
+  fl[4] = hn;
+}
+
+// solve the k x k upper triangular system H y = g (one thread); k = fl[1]
+__global__ void k_trisolve(double *__restrict__ gm, int m) {
+  GmLayout L = gm_layout(m);
+  int k = (int)gm[L.flags + 1];
+  for (int i = k - 1; i >= 0; i--) {
+    double s = gm[L.g + i];
+    for (int c = i + 1; c < k; c++) s -= gm[L.H + (size_t)c * (m + 1) + i] * gm[L.y + c];
+    double d = gm[L.H + (size_t)i * (m + 1) + i];
+    gm[L.y + i] = (d != 0.0) ? s / d : 0.0;
+  }
+}
+
+// x += dinv .* (sum_i y_i V[i])
+__global__ void k_update_x(const double *__restrict__ Vb, int64_t ld, const double *__restrict__ gm, int m,
+                           const double *__restrict__ dinv, double *__restrict__ x, int64_t N) {
+  GmLayout L = gm_layout(m);
+  __shared__ double ys[1024];
+  int k = (int)gm[L.flags + 1];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = gm[L.y + i];
+  __syncthreads();
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < k; i++) acc = fma(ys[i], Vb[(size_t)i * ld + r], acc);
+    x[r] += dinv[r] * acc;
+  }
+}
+
+// r = b - Ax ; then the caller normalises
+__global__ void k_residual_vec(const double *__restrict__ b, const double *__restrict__ Ax, double *__restrict__ r, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) r[i] = b[i] - Ax[i];
+}
+
+// start a cycle: beta = sqrt(sumsq); V0 = r / beta; z = dinv V0; g = (beta, 0..); flags reset
+__global__ void k_cycle_init_scalars(double *__restrict__ gm, int m, const double *__restrict__ sumsq, double tol) {
+  GmLayout L = gm_layout(m);
+  double beta = sqrt(sumsq[0]);
+  for (int i = 0; i < L.size; i++) gm[i] = 0.0;
+  gm[L.g] = beta;
+  gm[L.flags + 2] = beta;
+  gm[L.flags + 4] = beta;
+  if (!(beta > tol) || !isfinite(beta)) {
+    gm[L.flags + 0] = 1.0;  // already converged (or NaN): nothing to do
+    if (!isfinite(beta)) gm[L.flags + 3] = 1.0;
+  }
+}
+
+__global__ void k_fill(double *__restrict__ x, double v, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) x[i] = v;
+}
+
+__global__ void k_nan_partial(const double *__restrict__ x, double *__restrict__ partial, int64_t N) {
+  __shared__ double sh[32];
+  int64_t per = (N + gridDim.x - 1) / gridDim.x;
+  int64_t a = blockIdx.x * per, b = min(N, a + per);
+  double bad = 0.0;
+  for (int64_t r = a + threadIdx.x; r < b; r += blockDim.x)
+    if (!isfinite(x[r])) bad = 1.0;
+  bad = block_sum(bad, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = bad;
+}
+
+}  // namespace
+
+static int grid_for(int64_t N, int threads, int cap) {
+  int64_t g = (N + threads - 1) / threads;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <typename V>
+static cudaError_t spmv_launch(iga_s *h, const V *vals, const double *x, double *y, const double *done) {
+  double avg = (double)h->nnz / (double)h->N;
+  int lpr = avg >= 96 ? 32 : (avg >= 40 ? 16 : (avg >= 16 ? 8 : 4));
+  int64_t threads = h->N * lpr;
+  unsigned grid = (unsigned)((threads + 255) / 256);
+  switch (lpr) {
+    case 32: k_spmv<V, 32><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, x, y, h->N, done); break;
+    case 16: k_spmv<V, 16><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, x, y, h->N, done); break;
+    case 8: k_spmv<V, 8><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, x, y, h->N, done); break;
+    default: k_spmv<V, 4><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, x, y, h->N, done); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spmv64(iga_s *h, const double *vals, const double *x, double *y) { return spmv_launch<double>(h, vals, x, y, nullptr); }
+cudaError_t launch_spmv32(iga_s *h, const float *vals, const double *x, double *y) { return spmv_launch<float>(h, vals, x, y, nullptr); }
+
+cudaError_t launch_diag_inv(iga_s *h, const void *vals, int is_f32, double *dinv) {
+  unsigned g = (unsigned)((h->N + 255) / 256);
+  if (is_f32) k_diag_inv<float><<<g, 256, 0, h->stream>>>(h->rowptr, h->colidx, (const float *)vals, dinv, h->N);
+  else k_diag_inv<double><<<g, 256, 0, h->stream>>>(h->rowptr, h->colidx, (const double *)vals, dinv, h->N);
+  return cudaGetLastError();
+}
+
+// out_dev[0] = sum x^2 (deterministic)
+static void sumsq(iga_s *h, const double *x, double *out_dev) {
+  k_dot_partial<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(x, x, h->red, h->N, nullptr);
+  k_reduce_rows<<<1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, out_dev, 0, nullptr);
+}
+
+cudaError_t launch_norm2(iga_s *h, const double *x, double *out_dev) {
+  sumsq(h, x, out_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nan_check(iga_s *h, const double *x, double *out_dev) {
+  k_nan_partial<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(x, h->red, h->N);
+  k_reduce_rows<<<1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, out_dev, 0, nullptr);
+  return cudaGetLastError();
+}
+
+// Restarted GMRES(m), right Jacobi preconditioning: solves A x = b from x = 0
+// until ||b - A x|| <= tol_abs or maxit iterations.  Returns 0 on convergence,
+// 1 when the cap was hit, 2 on breakdown/NaN, -1 on a CUDA error.
+int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double *x, double tol_abs, int m, int maxit,
+                int *its, cudaError_t *cerr) {
+  const int64_t N = h->N, ld = N;
+  GmLayout L = gm_layout(m);
+  double *gm = h->ctl;
+  double *fl_host = h->ctl_host;
+  double *dinv = h->wk + 4 * N, *z = h->wk + 5 * N, *w = h->wk + 6 * N, *tmp = h->wk + 7 * N;
+  double *scal = h->wk + 8 * N;        // device scalars
+  double *h2 = h->wk + 8 * N + 64;     // second Gram-Schmidt pass coefficients (m+1)
+  double *Vb = h->V;
+  int total = 0, rc = 1;
+  *cerr = cudaSuccess;
+  int eg = grid_for(N, 256, 4 * 152);
+  launch_diag_inv(h, vals, is_f32, dinv);
+  k_fill<<<eg, 256, 0, h->stream>>>(x, 0.0, N);
+  const int batch = 8;
+  while (total < maxit) {
+    // r = b - A x
+    if (total == 0) {
+      cudaMemcpyAsync(Vb, b, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+    } else {
+      if (is_f32) spmv_launch<float>(h, (const float *)vals, x, tmp, nullptr);
+      else spmv_launch<double>(h, (const double *)vals, x, tmp, nullptr);
+      k_residual_vec<<<eg, 256, 0, h->stream>>>(b, tmp, Vb, N);
+    }
+    sumsq(h, Vb, scal);
+    k_cycle_init_scalars<<<1, 1, 0, h->stream>>>(gm, m, scal, tol_abs);
+    k_normalize<<<eg, 256, 0, h->stream>>>(Vb, gm + L.flags + 4, Vb, dinv, z, N, gm + L.flags + 5);  // flags[5] stays 0
+    int j = 0;
+    bool cycle_done = false;
+    while (!cycle_done) {
+      int jend = j + batch < m ? j + batch : m;
+      for (; j < jend; j++) {
+        const double *done = gm + L.flags;
+        double *Hj = gm + L.H + (size_t)j * (m + 1);
+        if (is_f32) spmv_launch<float>(h, (const float *)vals, z, w, done);
+        else spmv_launch<double>(h, (const double *)vals, z, w, done);
+        // classical Gram-Schmidt, applied twice
+        dim3 gd(RED_BLOCKS, j + 1);
+        k_mdot_partial<<<gd, RED_THREADS, 0, h->stream>>>(Vb, ld, w, h->red, N, done);
+        k_reduce_rows<<<j + 1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, Hj, 0, done);
+        k_orth_update<<<eg, 256, 0, h->stream>>>(Vb, ld, Hj, j + 1, w, N, done);
+        k_mdot_partial<<<gd, RED_THREADS, 0, h->stream>>>(Vb, ld, w, h->red, N, done);
+        k_reduce_rows<<<j + 1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, h2, 0, done);
+        k_orth_update<<<eg, 256, 0, h->stream>>>(Vb, ld, h2, j + 1, w, N, done);
+        k_add_vec<<<1, 256, 0, h->stream>>>(Hj, h2, j + 1, done);
+        k_dot_partial<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(w, w, h->red, N, done);
+        k_reduce_rows<<<1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, Hj + j + 1, 0, done);
+        k_givens<<<1, 1, 0, h->stream>>>(gm, m, j, tol_abs);
+        // the next basis vector is formed unless this was the last column
+        k_normalize<<<eg, 256, 0, h->stream>>>(w, gm + L.flags + 4, Vb + (size_t)(j + 1) * ld, dinv, z, N, gm + L.flags);
+      }
+      cudaMemcpyAsync(fl_host, gm + L.flags, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+      cudaError_t ce = cudaStreamSynchronize(h->stream);
+      if (ce) { *cerr = ce; return -1; }
+      if (fl_host[0] != 0.0 || j >= m) cycle_done = true;
+    }
+    int k = (int)fl_host[1];
+    total += k;
+    if (k > 0) {
+      k_trisolve<<<1, 1, 0, h->stream>>>(gm, m);
+      k_update_x<<<eg, 256, 0, h->stream>>>(Vb, ld, gm, m, dinv, x, N);
+    }
+    if (fl_host[3] != 0.0) { rc = (fl_host[2] <= tol_abs) ? 0 : 2; break; }
+    if (fl_host[2] <= tol_abs) { rc = 0; break; }
+    if (k == 0) { rc = 0; break; }
+  }
+  cudaError_t ce = cudaGetLastError();
+  if (ce) { *cerr = ce; return -1; }
+  *its = total;
+  return rc;
+}

@@ -1,0 +1,234 @@
+"""Thin ctypes binding of libiga (include/iga.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Functions keep the C names; ``Discretization`` bundles a handle with
+its host-side arrays and takes torch CUDA tensors for device buffers.  There is
+no fallback: if libiga.so is missing, ``lib()`` raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libiga.so")
+
+IGA_OK, IGA_EINVAL, IGA_ENOMEM, IGA_ECUDA, IGA_ENOCONV, IGA_EDIVERGED, IGA_ETIMEOUT, IGA_ENAN = range(8)
+STATUS_NAMES = ["IGA_OK", "IGA_EINVAL", "IGA_ENOMEM", "IGA_ECUDA", "IGA_ENOCONV", "IGA_EDIVERGED", "IGA_ETIMEOUT", "IGA_ENAN"]
+IGA_FP64, IGA_JAC_TF32, IGA_JAC_BF16 = 0, 1, 2
+
+# every symbol include/iga.h declares
+EXPORTS = ["iga_create", "iga_set_boundary_value", "iga_set_lambda", "iga_get_pattern", "iga_form_residual",
+           "iga_form_jacobian", "iga_newton_defaults", "iga_solve_newton", "iga_solve_newton_host", "iga_destroy",
+           "iga_last_error"]
+
+
+class IgaDesc(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("degree", ctypes.c_int * 3),
+        ("nel", ctypes.c_int * 3),
+        ("continuity", ctypes.c_int * 3),
+        ("knots", ctypes.c_void_p * 3),
+        ("nknots", ctypes.c_int * 3),
+        ("quad", ctypes.c_int * 3),
+        ("ctrl", ctypes.c_void_p),
+        ("weights", ctypes.c_void_p),
+    ]
+
+
+class IgaBratu(ctypes.Structure):
+    _fields_ = [("lam", ctypes.c_double), ("log_kappa", ctypes.c_void_p)]
+
+
+class IgaNewtonOpts(ctypes.Structure):
+    _fields_ = [
+        ("atol", ctypes.c_double),
+        ("max_newton", ctypes.c_int),
+        ("gmres_restart", ctypes.c_int),
+        ("max_krylov", ctypes.c_int),
+        ("krylov_rtol", ctypes.c_double),
+        ("jac", ctypes.c_int),
+        ("reuse_stiffness", ctypes.c_int),
+    ]
+
+
+class IgaNewtonReport(ctypes.Structure):
+    _fields_ = [
+        ("newton_its", ctypes.c_int),
+        ("krylov_its", ctypes.c_int),
+        ("fnorm0", ctypes.c_double),
+        ("fnorm", ctypes.c_double),
+        ("fnorm_hist", ctypes.c_double * 64),
+        ("status", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libiga.so (build it first with paper_1305_4452_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libiga.so is not built (%s); run paper_1305_4452_gb300.build.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)
+        L.iga_create.argtypes = [ctypes.POINTER(IgaDesc), ctypes.POINTER(IgaBratu), vp, ctypes.POINTER(vp)]
+        L.iga_create.restype = ctypes.c_int
+        L.iga_set_boundary_value.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+        L.iga_set_lambda.argtypes = [vp, ctypes.c_double]
+        L.iga_get_pattern.argtypes = [vp, i64p, i64p, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+        L.iga_form_residual.argtypes = [vp, vp, vp]
+        L.iga_form_jacobian.argtypes = [vp, vp, vp, ctypes.c_int]
+        L.iga_newton_defaults.argtypes = [ctypes.POINTER(IgaNewtonOpts)]
+        L.iga_newton_defaults.restype = None
+        L.iga_solve_newton.argtypes = [vp, vp, ctypes.POINTER(IgaNewtonOpts), ctypes.POINTER(IgaNewtonReport)]
+        L.iga_solve_newton_host.argtypes = [vp, vp, ctypes.POINTER(IgaNewtonOpts), ctypes.POINTER(IgaNewtonReport)]
+        L.iga_destroy.argtypes = [vp]
+        L.iga_destroy.restype = None
+        L.iga_last_error.argtypes = [vp]
+        L.iga_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+class IgaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 8 else status, msg))
+        self.status = status
+
+
+def _check(rc, handle=None):
+    if rc != IGA_OK:
+        raise IgaError(rc, lib().iga_last_error(handle).decode())
+    return rc
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def newton_defaults():
+    o = IgaNewtonOpts()
+    lib().iga_newton_defaults(ctypes.byref(o))
+    return o
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(stream)
+
+
+class Discretization:
+    """An iga_t handle: a scalar Bratu problem on a tensor-product NURBS space.
+
+    knots: per-direction knot vectors (None: uniform from nel/continuity);
+    ctrl (N, dim) / weights (N,) / log_kappa (N,) host arrays or None.
+    """
+
+    def __init__(self, dim, degree, nel=None, continuity=None, knots=None, ctrl=None, weights=None, lam=1.0,
+                 log_kappa=None, dirichlet=None, stream=None):
+        d = IgaDesc()
+        d.dim = dim
+        self._keep = []
+        for ax in range(dim):
+            d.degree[ax] = degree if np.isscalar(degree) else degree[ax]
+            d.continuity[ax] = -1 if continuity is None else (continuity if np.isscalar(continuity) else continuity[ax])
+            if knots is not None and knots[ax] is not None:
+                k = _f64(knots[ax])
+                self._keep.append(k)
+                d.knots[ax] = k.ctypes.data
+                d.nknots[ax] = len(k)
+            else:
+                d.nel[ax] = nel if np.isscalar(nel) else nel[ax]
+        ctrl, weights, log_kappa = _f64(ctrl), _f64(weights), _f64(log_kappa)
+        self._keep += [a for a in (ctrl, weights, log_kappa) if a is not None]
+        d.ctrl = None if ctrl is None else ctrl.ctypes.data
+        d.weights = None if weights is None else weights.ctypes.data
+        b = IgaBratu(float(lam), None if log_kappa is None else log_kappa.ctypes.data)
+        h = ctypes.c_void_p()
+        self.stream = _stream_ptr(stream)
+        _check(lib().iga_create(ctypes.byref(d), ctypes.byref(b), ctypes.c_void_p(self.stream), ctypes.byref(h)))
+        self.h = h
+        self.dim = dim
+        for (ax, side), v in (dirichlet or {}).items():
+            _check(lib().iga_set_boundary_value(self.h, ax, side, float(v)), self.h)
+        n = ctypes.c_int64()
+        nnz = ctypes.c_int64()
+        rp = ctypes.c_void_p()
+        ci = ctypes.c_void_p()
+        _check(lib().iga_get_pattern(self.h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(rp), ctypes.byref(ci)), self.h)
+        self.N, self.nnz = n.value, nnz.value
+        self.rowptr_ptr, self.colidx_ptr = rp.value, ci.value
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().iga_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_lambda(self, lam):
+        _check(lib().iga_set_lambda(self.h, float(lam)), self.h)
+
+    def pattern(self):
+        """Copy the device CSR pattern into torch tensors (rowptr int64, colidx int32)."""
+        import torch
+        rp = torch.empty(self.N + 1, dtype=torch.int64, device="cuda")
+        ci = torch.empty(self.nnz, dtype=torch.int32, device="cuda")
+        rp.copy_(_wrap_device(self.rowptr_ptr, self.N + 1, torch.int64))
+        ci.copy_(_wrap_device(self.colidx_ptr, self.nnz, torch.int32))
+        return rp, ci
+
+    def form_residual(self, U, F=None):
+        import torch
+        if F is None:
+            F = torch.empty_like(U)
+        _check(lib().iga_form_residual(self.h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(F.data_ptr())), self.h)
+        return F
+
+    def form_jacobian(self, U, prec=IGA_FP64, vals=None):
+        import torch
+        if vals is None:
+            vals = torch.empty(self.nnz, dtype=torch.float64 if prec == IGA_FP64 else torch.float32, device=U.device)
+        _check(lib().iga_form_jacobian(self.h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(vals.data_ptr()), int(prec)), self.h)
+        return vals
+
+    def solve_newton(self, U, opts=None, check=True):
+        o = opts if opts is not None else newton_defaults()
+        r = IgaNewtonReport()
+        rc = lib().iga_solve_newton(self.h, ctypes.c_void_p(U.data_ptr()), ctypes.byref(o), ctypes.byref(r))
+        if check and rc not in (IGA_OK,):
+            raise IgaError(rc, lib().iga_last_error(self.h).decode())
+        return r
+
+    def solve_newton_host(self, U_host, opts=None, check=True):
+        """U_host: numpy float64 array (ideally in pinned memory), updated in place."""
+        o = opts if opts is not None else newton_defaults()
+        r = IgaNewtonReport()
+        rc = lib().iga_solve_newton_host(self.h, ctypes.c_void_p(U_host.ctypes.data if isinstance(U_host, np.ndarray) else U_host.data_ptr()),
+                                         ctypes.byref(o), ctypes.byref(r))
+        if check and rc != IGA_OK:
+            raise IgaError(rc, lib().iga_last_error(self.h).decode())
+        return r
+
+
+def _wrap_device(ptr, n, dtype):
+    """A torch view of library-owned device memory (no copy)."""
+    import torch
+
+    class _Arr:
+        pass
+
+    a = _Arr()
+    typestr = {torch.int64: "<i8", torch.int32: "<i4", torch.float64: "<f8", torch.float32: "<f4"}[dtype]
+    a.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 2}
+    return torch.as_tensor(a, device="cuda")

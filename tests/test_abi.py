@@ -1,0 +1,65 @@
+"""The C-ABI library builds, loads and exports every symbol include/iga.h declares;
+argument validation that needs no GPU (CPU only)."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1305_4452_gb300 import build, iga
+    build.build()
+    return iga
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "iga.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(iga_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_symbols()
+    assert names, "no declarations found"
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (iga_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    L = lib.lib()
+    for n in names:
+        assert hasattr(L, n)
+    assert sorted(lib.EXPORTS) == names
+
+
+def test_build_targets_sm103a_only():
+    from paper_1305_4452_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+@pytest.mark.parametrize("kwargs,needle", [
+    (dict(dim=2, degree=2, knots=[np.array([0, 0, 0, .5, .4, 1, 1, 1.]), None], nel=4), "non-decreasing"),
+    (dict(dim=2, degree=5, nel=4), "degrees"),
+    (dict(dim=1, degree=2, nel=4), "dim"),
+    (dict(dim=2, degree=2, knots=[np.array([0, 0, .5, 1, 1, 1.]), None], nel=4), "open"),
+    (dict(dim=2, degree=2, knots=[np.array([0, 0, 0, 1.]), None], nel=4), "too few"),
+    (dict(dim=2, degree=2, nel=4, continuity=2), "continuity"),
+    (dict(dim=2, degree=2, nel=2, weights=np.array([1.0] * 15 + [-1.0])), "weight"),
+    (dict(dim=2, degree=2, nel=2, ctrl=np.full((16, 2), np.nan)), "finite"),
+    (dict(dim=2, degree=2, nel=2, log_kappa=np.full(16, np.inf)), "finite"),
+    (dict(dim=2, degree=2, knots=[np.array([0, 0, 0, .5, .5, .5, 1, 1, 1.]), None], nel=4), "multiplicity"),
+])
+def test_invalid_descriptions_rejected_before_any_device_work(lib, kwargs, needle):
+    with pytest.raises(lib.IgaError) as ei:
+        lib.Discretization(stream=0, lam=1.0, **kwargs)
+    assert ei.value.status == lib.IGA_EINVAL
+    assert needle in str(ei.value)
+
+
+def test_newton_defaults(lib):
+    o = lib.newton_defaults()
+    assert o.atol == 1e-10 and o.max_newton == 50 and o.gmres_restart > 0 and o.jac == lib.IGA_FP64

@@ -1,0 +1,226 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+Bar (from the method's statement of the target): FP64 residual and Jacobian
+equal to the oracle within 1e-12 relative max-norm; CSR pattern bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1305_4452_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1305_4452_gb300 import build
+    build.build()
+    O.build()
+
+
+def iga():
+    from paper_1305_4452_gb300 import iga as I
+    return I
+
+
+def bc_all(dim, v=0.0):
+    return {(a, s): v for a in range(dim) for s in range(2)}
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def make_pair(dim, p, nel, lam=1.0, k=None, geom=None, kappa_seed=None, bc=True):
+    """GPU discretisation and oracle problem on the same inputs."""
+    I = iga()
+    nel = [nel] * dim if np.isscalar(nel) else list(nel)
+    ctrl = weights = knots = None
+    if geom == "annulus":
+        kn, ctrl, weights = W.quarter_annulus(tuple(nel) if dim == 3 else (nel[0], nel[1], 1), p)
+        if dim == 2:
+            n0, n1 = len(kn[0]) - p - 1, len(kn[1]) - p - 1
+            ctrl = ctrl.reshape(-1, n1, n0, 3)[0, :, :, :2].reshape(-1, 2)
+            weights = weights.reshape(-1, n1, n0)[0].reshape(-1)
+            kn = kn[:2]
+        knots = kn
+    else:
+        knots = [W.uniform_open_knots(nel[d], p, k) for d in range(dim)]
+    n = [len(kk) - p - 1 for kk in knots]
+    lk = None
+    if kappa_seed is not None:
+        lk = W.grf_log_kappa(n, p, nel, kappa_seed) if dim == 2 else W.uniform(kappa_seed, int(np.prod(n)), -0.5, 0.5)
+    dirichlet = bc_all(dim) if bc else None
+    disc = I.Discretization(dim, p, knots=knots, ctrl=ctrl, weights=weights, lam=lam, log_kappa=lk, dirichlet=dirichlet)
+    prob = O.Problem(knots, [p] * dim, ctrl=ctrl, weights=weights, lam=lam, log_kappa=lk, dirichlet=dirichlet)
+    return disc, prob, n
+
+
+SMALL = [
+    # (dim, p, nel, k, geom, kappa)
+    (2, 2, 16, None, None, None),      # the 16x16 quadratic C1 configuration
+    (2, 1, (7, 5), None, None, None),
+    (2, 3, (6, 9), 1, None, None),     # reduced continuity
+    (2, 4, (5, 4), None, None, None),
+    (2, 3, (7, 6), None, "annulus", None),
+    (2, 2, (9, 7), None, None, 3),     # kappa-weighted
+    (3, 2, (7, 5, 3), None, None, None),
+    (3, 3, (5, 6, 3), None, "annulus", None),
+    (3, 1, (4, 3, 5), None, None, None),
+    (3, 4, (3, 2, 3), 2, None, None),
+]
+
+
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: "d%dp%d_%s_%s_%s_%s" % (c[0], c[1], c[2], c[3], c[4], c[5]))
+def test_small_full_parity(case):
+    dim, p, nel, k, geom, kap = case
+    disc, prob, n = make_pair(dim, p, nel, lam=1.7, k=k, geom=geom, kappa_seed=kap)
+    U0 = W.interior_field(n, seed=11, lo=-0.3, hi=0.3)
+    U = torch.tensor(U0, device="cuda")
+    F = disc.form_residual(U).cpu().numpy()
+    J = disc.form_jacobian(U).cpu().numpy()
+    rp, ci = disc.pattern()
+    rpo, cio = prob.pattern()
+    assert np.array_equal(rp.cpu().numpy(), rpo)
+    assert np.array_equal(ci.cpu().numpy(), cio)
+    Fo = prob.residual(U0)
+    Jo = prob.jacobian(U0)
+    assert rel(F, Fo) <= TOL, rel(F, Fo)
+    assert rel(J, Jo) <= TOL, rel(J, Jo)
+    disc.close()
+
+
+def test_no_dirichlet_and_mixed_faces():
+    I = iga()
+    p, nel = 2, (6, 5)
+    knots = [W.uniform_open_knots(e, p) for e in nel]
+    n = [len(kk) - p - 1 for kk in knots]
+    for bc in (None, {(0, 0): 0.5, (1, 1): -0.25}):
+        disc = I.Discretization(2, p, knots=knots, lam=0.9, dirichlet=bc)
+        prob = O.Problem(knots, [p, p], lam=0.9, dirichlet=bc)
+        U0 = W.uniform(4, int(np.prod(n)), -0.4, 0.4)
+        U = torch.tensor(U0, device="cuda")
+        assert rel(disc.form_residual(U).cpu().numpy(), prob.residual(U0)) <= TOL
+        assert rel(disc.form_jacobian(U).cpu().numpy(), prob.jacobian(U0)) <= TOL
+        disc.close()
+
+
+def test_deterministic_bitwise():
+    disc, prob, n = make_pair(3, 3, (5, 4, 3), geom="annulus")
+    U = torch.tensor(W.interior_field(n, 5), device="cuda")
+    F1, F2 = disc.form_residual(U).clone(), disc.form_residual(U).clone()
+    J1, J2 = disc.form_jacobian(U).clone(), disc.form_jacobian(U).clone()
+    assert torch.equal(F1, F2) and torch.equal(J1, J2)
+    disc.close()
+
+
+def test_appendix_b_initial_norm_on_gpu():
+    I = iga()
+    disc = I.Discretization(2, 2, nel=128, lam=6.80, dirichlet=bc_all(2))
+    U = torch.zeros(disc.N, dtype=torch.float64, device="cuda")
+    F = disc.form_residual(U)
+    trace0 = 5.266384548611e-02  # Appendix B, iteration 0
+    assert abs(torch.linalg.norm(F).item() - trace0) <= 1e-12 * trace0
+    rep = disc.solve_newton(U)
+    assert rep.fnorm <= 1e-10 and rep.status == 0
+    # loose pin: the paper's run took 7 Newton steps
+    assert 5 <= rep.newton_its <= 9
+    disc.close()
+
+
+def test_newton_config1_and_oracle_residual_at_solution():
+    disc, prob, n = make_pair(2, 2, 16, lam=1.0)
+    U0 = W.interior_field(n, seed=1)
+    U = torch.tensor(U0, device="cuda")
+    rep = disc.solve_newton(U)
+    assert rep.status == 0 and rep.fnorm <= 1e-10
+    Fo = prob.residual(U.cpu().numpy())
+    assert np.linalg.norm(Fo) <= 1e-10 + 1e-12
+    disc.close()
+
+
+@pytest.mark.parametrize("jac_reuse", [0, 1])
+def test_newton_3d_annulus_small(jac_reuse):
+    I = iga()
+    disc, prob, n = make_pair(3, 3, (8, 8, 6), lam=2.0, geom="annulus")
+    U = torch.zeros(disc.N, dtype=torch.float64, device="cuda")
+    o = I.newton_defaults()
+    o.reuse_stiffness = jac_reuse
+    rep = disc.solve_newton(U, o)
+    assert rep.status == 0 and rep.fnorm <= 1e-10
+    assert np.linalg.norm(prob.residual(U.cpu().numpy())) <= 1.5e-10
+    disc.close()
+
+
+def test_beyond_fold_reports_failure():
+    I = iga()
+    disc = I.Discretization(2, 2, nel=16, lam=7.5, dirichlet=bc_all(2))
+    U = torch.zeros(disc.N, dtype=torch.float64, device="cuda")
+    o = I.newton_defaults()
+    o.max_newton = 25
+    rep = disc.solve_newton(U, o, check=False)
+    assert rep.status in (I.IGA_ENOCONV, I.IGA_EDIVERGED)
+    assert rep.newton_its <= 25
+    disc.close()
+
+
+def test_nan_input_reports_enan():
+    I = iga()
+    disc = I.Discretization(2, 2, nel=8, lam=1.0, dirichlet=bc_all(2))
+    U = torch.zeros(disc.N, dtype=torch.float64, device="cuda")
+    U[disc.N // 2] = float("nan")
+    rep = disc.solve_newton(U, check=False)
+    assert rep.status == I.IGA_ENAN
+    disc.close()
+
+
+def sample_rows(N, count, seed):
+    rows = np.unique(np.concatenate([[0, N - 1, N // 2], (W.uniform(seed, count) * N).astype(np.int64)]))
+    return rows
+
+
+@pytest.mark.slow
+def test_full_size_annulus_64_cubed_sampled():
+    """3D annulus, 64^3 cubic C2, lambda = 2: pattern bit-exact, sampled rows of F and J."""
+    disc, prob, n = make_pair(3, 3, 64, lam=2.0, geom="annulus")
+    assert disc.N == 300763 and disc.nnz == 95443993
+    U0 = W.interior_field(n, seed=2)
+    U = torch.tensor(U0, device="cuda")
+    F = disc.form_residual(U).cpu().numpy()
+    J = disc.form_jacobian(U)
+    rp, ci = disc.pattern()
+    rpo, cio = prob.pattern()
+    assert np.array_equal(rp.cpu().numpy(), rpo) and np.array_equal(ci.cpu().numpy(), cio)
+    rows = sample_rows(disc.N, 12, 77)
+    Fo = prob.residual_rows(U0, rows)
+    scale = np.abs(F).max()
+    assert np.abs(F[rows] - Fo).max() <= TOL * scale
+    Jo = prob.jacobian_rows(U0, rows)
+    rp_h = rpo
+    Jg = np.concatenate([J[rp_h[r]:rp_h[r + 1]].cpu().numpy() for r in rows])
+    jscale = torch.abs(J).max().item()
+    assert np.abs(Jg - Jo).max() <= TOL * jscale
+    disc.close()
+
+
+@pytest.mark.slow
+def test_full_size_cube_128_cubed_sampled():
+    """3D unit cube, 128^3 quadratic, lambda = 2 (FP64 Jacobian): sampled rows."""
+    disc, prob, n = make_pair(3, 2, 128, lam=2.0)
+    assert disc.N == 2197000 and disc.nnz == 267089984
+    U0 = W.interior_field(n, seed=3)
+    U = torch.tensor(U0, device="cuda")
+    F = disc.form_residual(U).cpu().numpy()
+    rows = sample_rows(disc.N, 12, 78)
+    assert np.abs(F[rows] - prob.residual_rows(U0, rows)).max() <= TOL * np.abs(F).max()
+    J = disc.form_jacobian(U)
+    rpo, _ = prob.pattern()
+    Jg = np.concatenate([J[rpo[r]:rpo[r + 1]].cpu().numpy() for r in rows])
+    assert np.abs(Jg - prob.jacobian_rows(U0, rows)).max() <= TOL * torch.abs(J).max().item()
+    disc.close()
