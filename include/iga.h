@@ -161,6 +161,26 @@ iga_status iga_solve_newton(iga_t iga, double *U, const iga_newton_opts *opts,
 iga_status iga_solve_newton_host(iga_t iga, double *U_host, const iga_newton_opts *opts,
                                  iga_newton_report *report);
 
+/* Per-kernel-class launch counts and device times (the tracing facility; the
+ * paper's -snes_monitor / -log_view analogue).  Classes, in order:
+ *   0 geometry factors, 1 residual element kernel, 2 residual gather, 3 Q00 /
+ *   u at Gauss points, 4 Jacobian stage 1, 5 Jacobian stage 2, 6 Jacobian final
+ *   stage, 7 SpMV, 8 Gram-Schmidt multi-dot/update, 9 GMRES scalar kernels,
+ *   10 vector kernels, 11 stiffness + reaction combine, 12 CSR pattern.
+ * iga_profile_enable(iga, mask): classes whose bit is set get a CUDA event pair
+ * recorded around each launch on the library's stream (mask 0: timing off;
+ * launches are always counted).  iga_profile_read synchronises the stream,
+ * returns the totals since the last read (ms[c], timed[c] = timed launches,
+ * launches[c] = all launches) and resets them. */
+#define IGA_NCLASS 13
+typedef struct {
+  double ms[16];
+  long long timed[16];
+  long long launches[16];
+} iga_profile;
+iga_status iga_profile_enable(iga_t iga, unsigned mask);
+iga_status iga_profile_read(iga_t iga, iga_profile *out);
+
 /* Release every library-owned device buffer.  NULL is accepted. */
 void iga_destroy(iga_t iga);
 

@@ -45,6 +45,11 @@ static void release(iga_s *h) {
   for (void *p : ps)
     if (p) cudaFree(p);
   if (h->ctl_host) cudaFreeHost(h->ctl_host);
+  for (ProfRec &r : h->prof.pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
 }
 
 static iga_status upload_dir(iga_s *h, int ax) {
@@ -348,7 +353,7 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
     if (k >= o.max_newton) { R.status = IGA_ENOCONV; break; }
     st = newton_jacobian(h, U, f32, o.reuse_stiffness != 0);
     if (st != IGA_OK) return st;
-    k_neg<<<eg, 256, 0, h->stream>>>(F, Ft, N);
+    IGA_LAUNCH(h, KC_VEC, (k_neg<<<eg, 256, 0, h->stream>>>(F, Ft, N)));
     double rtol = o.krylov_rtol < fn ? o.krylov_rtol : fn;
     double tol_abs = rtol * fn;
     if (tol_abs < 1e-14 * fn) tol_abs = 1e-14 * fn;
@@ -365,7 +370,7 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
     double alpha = 1.0, ft = 0.0;
     bool ok = false;
     for (int ls = 0; ls <= 10; ls++) {
-      k_axpby<<<eg, 256, 0, h->stream>>>(U, alpha, dU, Ut, N);
+      IGA_LAUNCH(h, KC_VEC, (k_axpby<<<eg, 256, 0, h->stream>>>(U, alpha, dU, Ut, N)));
       CK(launch_residual(h, Ut, Ft));
       st = norm_host(h, Ft, &ft);
       if (st != IGA_OK) return st;
@@ -400,4 +405,67 @@ extern "C" iga_status iga_solve_newton_host(iga_t h, double *U_host, const iga_n
   CK(cudaMemcpyAsync(U_host, h->Uhost_dev, h->N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return st;
+}
+
+// ---- tracing: launch counters and per-class event timing ----
+int prof_begin(iga_s *h, int cls) {
+  h->prof.launches[cls]++;
+  if (!(h->prof.mask & (1u << cls))) return -1;
+  ProfRec r;
+  r.cls = cls;
+  for (int k = 0; k < 2; k++) {
+    cudaEvent_t e;
+    if (!h->prof.pool.empty()) {
+      e = h->prof.pool.back();
+      h->prof.pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+      return -1;
+    }
+    (k == 0 ? r.a : r.b) = e;
+  }
+  cudaEventRecord(r.a, h->stream);
+  h->prof.pending.push_back(r);
+  return (int)h->prof.pending.size() - 1;
+}
+
+void prof_end(iga_s *h, int token) {
+  if (token < 0) return;
+  cudaEventRecord(h->prof.pending[token].b, h->stream);
+}
+
+static void prof_drain(iga_s *h) {
+  if (h->prof.pending.empty()) return;
+  cudaStreamSynchronize(h->stream);
+  for (ProfRec &r : h->prof.pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      h->prof.ms[r.cls] += ms;
+      h->prof.timed[r.cls]++;
+    }
+    h->prof.pool.push_back(r.a);
+    h->prof.pool.push_back(r.b);
+  }
+  h->prof.pending.clear();
+}
+
+extern "C" iga_status iga_profile_enable(iga_t h, unsigned mask) {
+  if (!h) return IGA_EINVAL;
+  prof_drain(h);
+  h->prof.mask = mask;
+  return IGA_OK;
+}
+
+extern "C" iga_status iga_profile_read(iga_t h, iga_profile *out) {
+  if (!h || !out) return IGA_EINVAL;
+  prof_drain(h);
+  memset(out, 0, sizeof *out);
+  for (int c = 0; c < KC_N; c++) {
+    out->ms[c] = h->prof.ms[c];
+    out->timed[c] = h->prof.timed[c];
+    out->launches[c] = h->prof.launches[c];
+    h->prof.ms[c] = 0.0;
+    h->prof.timed[c] = 0;
+    h->prof.launches[c] = 0;
+  }
+  return IGA_OK;
 }

@@ -787,7 +787,7 @@ cudaError_t launch_geometry(iga_s *h, const double *ctrl_dev, const double *logk
   int NQ = (h->dim == 3) ? h->q * h->q * h->q : h->q * h->q;
   int64_t tot = h->nelem * NQ;
   unsigned grid = (unsigned)((tot + 127) / 128);
-  DISPATCH_DP(h->dim, h->p, (k_geometry<D, PP><<<grid, 128, 0, h->stream>>>(a0, a1, a2, ctrl_dev, h->weights, logk_dev, h->gl, h->geom, h->nelem, err)));
+  IGA_LAUNCH(h, KC_GEOM, DISPATCH_DP(h->dim, h->p, (k_geometry<D, PP><<<grid, 128, 0, h->stream>>>(a0, a1, a2, ctrl_dev, h->weights, logk_dev, h->gl, h->geom, h->nelem, err))));
   int herr = 0;
   cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   ce = cudaStreamSynchronize(h->stream);
@@ -804,16 +804,16 @@ cudaError_t launch_residual(iga_s *h, const double *U, double *F) {
   DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
   constexpr int NE = 4;
   unsigned grid = (unsigned)((h->nelem + NE - 1) / NE);
-  DISPATCH_DP(h->dim, h->p, ({
+  IGA_LAUNCH(h, KC_RES_ELEM, DISPATCH_DP(h->dim, h->p, ({
     size_t sm = res_smem<D, PP>(NE);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_residual<D, PP, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_residual<D, PP, NE><<<grid, 128, sm, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, h->lambda, h->Fe, h->nelem);
-  }));
+  })));
   unsigned g2 = (unsigned)((h->N + 255) / 256);
   if (h->dim == 3)
-    k_gather_residual<3><<<g2, 256, 0, h->stream>>>(a0, a1, a2, h->Fe, U, h->bnd, F, h->N, h->p + 1);
+    IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<3><<<g2, 256, 0, h->stream>>>(a0, a1, a2, h->Fe, U, h->bnd, F, h->N, h->p + 1)));
   else
-    k_gather_residual<2><<<g2, 256, 0, h->stream>>>(a0, a1, a2, h->Fe, U, h->bnd, F, h->N, h->p + 1);
+    IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<2><<<g2, 256, 0, h->stream>>>(a0, a1, a2, h->Fe, U, h->bnd, F, h->N, h->p + 1)));
   return cudaGetLastError();
 }
 
@@ -821,11 +821,11 @@ cudaError_t launch_q00(iga_s *h, const double *U, double cs, double cr) {
   DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
   constexpr int NE = 4;
   unsigned grid = (unsigned)((h->nelem + NE - 1) / NE);
-  DISPATCH_DP(h->dim, h->p, ({
+  IGA_LAUNCH(h, KC_Q00, DISPATCH_DP(h->dim, h->p, ({
     size_t sm = res_smem<D, PP>(NE);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_q00<D, PP, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_q00<D, PP, NE><<<grid, 128, sm, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, h->lambda, cs, cr, h->Q00, h->nelem);
-  }));
+  })));
   return cudaGetLastError();
 }
 
@@ -840,21 +840,21 @@ static cudaError_t jacobian_stages(iga_s *h, V *vals, int mode, int fix) {
   {
     dim3 grid(a1.X, h->dim == 3 ? a2.X : 1);
     size_t sm = (size_t)plan.s1.nslot * a0.X * sizeof(double);
-    DISPATCH_DP(h->dim, h->p, ({
+    IGA_LAUNCH(h, KC_STAGE1, DISPATCH_DP(h->dim, h->p, ({
       if (sm > 48 * 1024) cudaFuncSetAttribute(k_stage1<T, D, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       k_stage1<T, D, PP><<<grid, 256, sm, h->stream>>>(a0, a1, a2, h->geom, h->Q00, h->gl, plan.s1, T1);
-    }));
+    })));
   }
   CsrArgs csr{h->rowptr, h->weights, h->bnd};
   const int chunk = 8;
   if (h->dim == 3) {
     dim3 g2((a0.np + 127) / 128, (a1.np + chunk - 1) / chunk, a2.X);
-    k_stage2<T><<<g2, 128, 0, h->stream>>>(a0, a1, a2, plan.s2, T1, T2, chunk);
+    IGA_LAUNCH(h, KC_STAGE2, (k_stage2<T><<<g2, 128, 0, h->stream>>>(a0, a1, a2, plan.s2, T1, T2, chunk)));
     dim3 g3((a0.np + 127) / 128, (a2.np + chunk - 1) / chunk, a1.np);
-    k_final<T, V, 3><<<g3, 128, 0, h->stream>>>(a0, a1, a2, plan.s3, T2, csr, vals, chunk, fix);
+    IGA_LAUNCH(h, KC_FINAL, (k_final<T, V, 3><<<g3, 128, 0, h->stream>>>(a0, a1, a2, plan.s3, T2, csr, vals, chunk, fix)));
   } else {
     dim3 g3((a0.np + 127) / 128, (a1.np + chunk - 1) / chunk, 1);
-    k_final<T, V, 2><<<g3, 128, 0, h->stream>>>(a0, a1, a2, plan.s2, T1, csr, vals, chunk, fix);
+    IGA_LAUNCH(h, KC_FINAL, (k_final<T, V, 2><<<g3, 128, 0, h->stream>>>(a0, a1, a2, plan.s2, T1, csr, vals, chunk, fix)));
   }
   return cudaGetLastError();
 }
@@ -877,19 +877,19 @@ cudaError_t launch_jacobian32(iga_s *h, const double *U, float *vals, int mode, 
 
 cudaError_t launch_combine64(iga_s *h, const double *K, const double *M, double *vals) {
   unsigned g = (unsigned)((h->nnz + 255) / 256);
-  k_combine<double><<<g, 256, 0, h->stream>>>(K, M, vals, h->nnz);
+  IGA_LAUNCH(h, KC_COMBINE, (k_combine<double><<<g, 256, 0, h->stream>>>(K, M, vals, h->nnz)));
   return cudaGetLastError();
 }
 
 cudaError_t launch_combine32(iga_s *h, const float *K, const float *M, float *vals) {
   unsigned g = (unsigned)((h->nnz + 255) / 256);
-  k_combine<float><<<g, 256, 0, h->stream>>>(K, M, vals, h->nnz);
+  IGA_LAUNCH(h, KC_COMBINE, (k_combine<float><<<g, 256, 0, h->stream>>>(K, M, vals, h->nnz)));
   return cudaGetLastError();
 }
 
 cudaError_t launch_colidx(iga_s *h) {
   DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
   unsigned g = (unsigned)((h->N + 255) / 256);
-  k_colidx<<<g, 256, 0, h->stream>>>(a0, a1, a2, h->dim, h->rowptr, h->colidx, h->N);
+  IGA_LAUNCH(h, KC_PATTERN, (k_colidx<<<g, 256, 0, h->stream>>>(a0, a1, a2, h->dim, h->rowptr, h->colidx, h->N)));
   return cudaGetLastError();
 }

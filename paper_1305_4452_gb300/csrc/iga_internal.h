@@ -88,7 +88,38 @@ struct BndArgs {
   double val[3][2];
 };
 
+// Kernel classes for launch counting and event timing (iga_profile_*).
+enum KClass {
+  KC_GEOM = 0, KC_RES_ELEM, KC_RES_GATHER, KC_Q00, KC_STAGE1, KC_STAGE2, KC_FINAL, KC_SPMV, KC_ORTH,
+  KC_GMRES_SCALAR, KC_VEC, KC_COMBINE, KC_PATTERN, KC_N
+};
+
+struct ProfRec {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+struct Prof {
+  unsigned mask = 0;             // classes timed with events
+  long long launches[KC_N] = {}; // every launch is counted
+  double ms[KC_N] = {};
+  long long timed[KC_N] = {};
+  std::vector<ProfRec> pending;
+  std::vector<cudaEvent_t> pool;
+};
+
+struct iga_s;
+int prof_begin(iga_s *h, int cls);
+void prof_end(iga_s *h, int token);
+#define IGA_LAUNCH(h, cls, ...)          \
+  do {                                   \
+    int tok_ = prof_begin((h), (cls));   \
+    __VA_ARGS__;                         \
+    prof_end((h), tok_);                 \
+  } while (0)
+
 struct iga_s {
+  Prof prof;
   int dim = 0, p = 0, q = 0;
   int64_t N = 0, nnz = 0, nelem = 0, nqp = 0;
   Dir dir[3];

@@ -275,10 +275,10 @@ static cudaError_t spmv_launch(iga_s *h, const V *vals, const double *x, double 
   int64_t threads = h->N * lpr;
   unsigned grid = (unsigned)((threads + 255) / 256);
   switch (lpr) {
-    case 32: k_spmv<V, 32><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, x, y, h->N, done); break;
-    case 16: k_spmv<V, 16><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, x, y, h->N, done); break;
-    case 8: k_spmv<V, 8><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, x, y, h->N, done); break;
-    default: k_spmv<V, 4><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, x, y, h->N, done); break;
+    case 32: IGA_LAUNCH(h, KC_SPMV, (k_spmv<V, 32><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, x, y, h->N, done))); break;
+    case 16: IGA_LAUNCH(h, KC_SPMV, (k_spmv<V, 16><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, x, y, h->N, done))); break;
+    case 8: IGA_LAUNCH(h, KC_SPMV, (k_spmv<V, 8><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, x, y, h->N, done))); break;
+    default: IGA_LAUNCH(h, KC_SPMV, (k_spmv<V, 4><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, x, y, h->N, done))); break;
   }
   return cudaGetLastError();
 }
@@ -288,15 +288,15 @@ cudaError_t launch_spmv32(iga_s *h, const float *vals, const double *x, double *
 
 cudaError_t launch_diag_inv(iga_s *h, const void *vals, int is_f32, double *dinv) {
   unsigned g = (unsigned)((h->N + 255) / 256);
-  if (is_f32) k_diag_inv<float><<<g, 256, 0, h->stream>>>(h->rowptr, h->colidx, (const float *)vals, dinv, h->N);
-  else k_diag_inv<double><<<g, 256, 0, h->stream>>>(h->rowptr, h->colidx, (const double *)vals, dinv, h->N);
+  if (is_f32) IGA_LAUNCH(h, KC_VEC, (k_diag_inv<float><<<g, 256, 0, h->stream>>>(h->rowptr, h->colidx, (const float *)vals, dinv, h->N)));
+  else IGA_LAUNCH(h, KC_VEC, (k_diag_inv<double><<<g, 256, 0, h->stream>>>(h->rowptr, h->colidx, (const double *)vals, dinv, h->N)));
   return cudaGetLastError();
 }
 
 // out_dev[0] = sum x^2 (deterministic)
 static void sumsq(iga_s *h, const double *x, double *out_dev) {
-  k_dot_partial<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(x, x, h->red, h->N, nullptr);
-  k_reduce_rows<<<1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, out_dev, 0, nullptr);
+  IGA_LAUNCH(h, KC_VEC, (k_dot_partial<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(x, x, h->red, h->N, nullptr)));
+  IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce_rows<<<1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, out_dev, 0, nullptr)));
 }
 
 cudaError_t launch_norm2(iga_s *h, const double *x, double *out_dev) {
@@ -305,8 +305,8 @@ cudaError_t launch_norm2(iga_s *h, const double *x, double *out_dev) {
 }
 
 cudaError_t launch_nan_check(iga_s *h, const double *x, double *out_dev) {
-  k_nan_partial<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(x, h->red, h->N);
-  k_reduce_rows<<<1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, out_dev, 0, nullptr);
+  IGA_LAUNCH(h, KC_VEC, (k_nan_partial<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(x, h->red, h->N)));
+  IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce_rows<<<1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, out_dev, 0, nullptr)));
   return cudaGetLastError();
 }
 
@@ -327,7 +327,7 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
   *cerr = cudaSuccess;
   int eg = grid_for(N, 256, 4 * 152);
   launch_diag_inv(h, vals, is_f32, dinv);
-  k_fill<<<eg, 256, 0, h->stream>>>(x, 0.0, N);
+  IGA_LAUNCH(h, KC_VEC, (k_fill<<<eg, 256, 0, h->stream>>>(x, 0.0, N)));
   const int batch = 8;
   while (total < maxit) {
     // r = b - A x
@@ -336,11 +336,11 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
     } else {
       if (is_f32) spmv_launch<float>(h, (const float *)vals, x, tmp, nullptr);
       else spmv_launch<double>(h, (const double *)vals, x, tmp, nullptr);
-      k_residual_vec<<<eg, 256, 0, h->stream>>>(b, tmp, Vb, N);
+      IGA_LAUNCH(h, KC_VEC, (k_residual_vec<<<eg, 256, 0, h->stream>>>(b, tmp, Vb, N)));
     }
     sumsq(h, Vb, scal);
-    k_cycle_init_scalars<<<1, 1, 0, h->stream>>>(gm, m, scal, tol_abs);
-    k_normalize<<<eg, 256, 0, h->stream>>>(Vb, gm + L.flags + 4, Vb, dinv, z, N, gm + L.flags + 5);  // flags[5] stays 0
+    IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_cycle_init_scalars<<<1, 1, 0, h->stream>>>(gm, m, scal, tol_abs)));
+    IGA_LAUNCH(h, KC_VEC, (k_normalize<<<eg, 256, 0, h->stream>>>(Vb, gm + L.flags + 4, Vb, dinv, z, N, gm + L.flags + 5)));  // flags[5] stays 0
     int j = 0;
     bool cycle_done = false;
     while (!cycle_done) {
@@ -352,18 +352,18 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
         else spmv_launch<double>(h, (const double *)vals, z, w, done);
         // classical Gram-Schmidt, applied twice
         dim3 gd(RED_BLOCKS, j + 1);
-        k_mdot_partial<<<gd, RED_THREADS, 0, h->stream>>>(Vb, ld, w, h->red, N, done);
-        k_reduce_rows<<<j + 1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, Hj, 0, done);
-        k_orth_update<<<eg, 256, 0, h->stream>>>(Vb, ld, Hj, j + 1, w, N, done);
-        k_mdot_partial<<<gd, RED_THREADS, 0, h->stream>>>(Vb, ld, w, h->red, N, done);
-        k_reduce_rows<<<j + 1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, h2, 0, done);
-        k_orth_update<<<eg, 256, 0, h->stream>>>(Vb, ld, h2, j + 1, w, N, done);
-        k_add_vec<<<1, 256, 0, h->stream>>>(Hj, h2, j + 1, done);
-        k_dot_partial<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(w, w, h->red, N, done);
-        k_reduce_rows<<<1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, Hj + j + 1, 0, done);
-        k_givens<<<1, 1, 0, h->stream>>>(gm, m, j, tol_abs);
+        IGA_LAUNCH(h, KC_ORTH, (k_mdot_partial<<<gd, RED_THREADS, 0, h->stream>>>(Vb, ld, w, h->red, N, done)));
+        IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce_rows<<<j + 1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, Hj, 0, done)));
+        IGA_LAUNCH(h, KC_ORTH, (k_orth_update<<<eg, 256, 0, h->stream>>>(Vb, ld, Hj, j + 1, w, N, done)));
+        IGA_LAUNCH(h, KC_ORTH, (k_mdot_partial<<<gd, RED_THREADS, 0, h->stream>>>(Vb, ld, w, h->red, N, done)));
+        IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce_rows<<<j + 1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, h2, 0, done)));
+        IGA_LAUNCH(h, KC_ORTH, (k_orth_update<<<eg, 256, 0, h->stream>>>(Vb, ld, h2, j + 1, w, N, done)));
+        IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_add_vec<<<1, 256, 0, h->stream>>>(Hj, h2, j + 1, done)));
+        IGA_LAUNCH(h, KC_VEC, (k_dot_partial<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(w, w, h->red, N, done)));
+        IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce_rows<<<1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, Hj + j + 1, 0, done)));
+        IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_givens<<<1, 1, 0, h->stream>>>(gm, m, j, tol_abs)));
         // the next basis vector is formed unless this was the last column
-        k_normalize<<<eg, 256, 0, h->stream>>>(w, gm + L.flags + 4, Vb + (size_t)(j + 1) * ld, dinv, z, N, gm + L.flags);
+        IGA_LAUNCH(h, KC_VEC, (k_normalize<<<eg, 256, 0, h->stream>>>(w, gm + L.flags + 4, Vb + (size_t)(j + 1) * ld, dinv, z, N, gm + L.flags)));
       }
       cudaMemcpyAsync(fl_host, gm + L.flags, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
       cudaError_t ce = cudaStreamSynchronize(h->stream);
@@ -373,8 +373,8 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
     int k = (int)fl_host[1];
     total += k;
     if (k > 0) {
-      k_trisolve<<<1, 1, 0, h->stream>>>(gm, m);
-      k_update_x<<<eg, 256, 0, h->stream>>>(Vb, ld, gm, m, dinv, x, N);
+      IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_trisolve<<<1, 1, 0, h->stream>>>(gm, m)));
+      IGA_LAUNCH(h, KC_VEC, (k_update_x<<<eg, 256, 0, h->stream>>>(Vb, ld, gm, m, dinv, x, N)));
     }
     if (fl_host[3] != 0.0) { rc = (fl_host[2] <= tol_abs) ? 0 : 2; break; }
     if (fl_host[2] <= tol_abs) { rc = 0; break; }

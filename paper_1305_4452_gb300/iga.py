@@ -20,7 +20,10 @@ IGA_FP64, IGA_JAC_TF32, IGA_JAC_BF16 = 0, 1, 2
 # every symbol include/iga.h declares
 EXPORTS = ["iga_create", "iga_set_boundary_value", "iga_set_lambda", "iga_get_pattern", "iga_form_residual",
            "iga_form_jacobian", "iga_newton_defaults", "iga_solve_newton", "iga_solve_newton_host", "iga_destroy",
-           "iga_last_error"]
+           "iga_last_error", "iga_profile_enable", "iga_profile_read"]
+
+KERNEL_CLASSES = ["geometry", "residual_element", "residual_gather", "q00", "jac_stage1", "jac_stage2", "jac_final",
+                  "spmv", "gs_orth", "gmres_scalar", "vector", "combine", "pattern"]
 
 
 class IgaDesc(ctypes.Structure):
@@ -64,6 +67,10 @@ class IgaNewtonReport(ctypes.Structure):
     ]
 
 
+class IgaProfile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 16), ("timed", ctypes.c_longlong * 16), ("launches", ctypes.c_longlong * 16)]
+
+
 _lib = None
 
 
@@ -90,6 +97,8 @@ def lib():
         L.iga_destroy.restype = None
         L.iga_last_error.argtypes = [vp]
         L.iga_last_error.restype = ctypes.c_char_p
+        L.iga_profile_enable.argtypes = [vp, ctypes.c_uint]
+        L.iga_profile_read.argtypes = [vp, ctypes.POINTER(IgaProfile)]
         _lib = L
     return _lib
 
@@ -175,6 +184,19 @@ class Discretization:
             self.close()
         except Exception:
             pass
+
+    def profile_enable(self, classes=()):
+        """Time the named kernel classes (see KERNEL_CLASSES) with CUDA events."""
+        mask = 0
+        for c in classes:
+            mask |= 1 << KERNEL_CLASSES.index(c)
+        _check(lib().iga_profile_enable(self.h, mask), self.h)
+
+    def profile_read(self):
+        """{class: (ms, timed launches, all launches)} since the last read."""
+        p = IgaProfile()
+        _check(lib().iga_profile_read(self.h, ctypes.byref(p)), self.h)
+        return {c: (p.ms[i], p.timed[i], p.launches[i]) for i, c in enumerate(KERNEL_CLASSES)}
 
     def set_lambda(self, lam):
         _check(lib().iga_set_lambda(self.h, float(lam)), self.h)
