@@ -32,7 +32,7 @@ static cudaError_t upload(T **dst, const std::vector<T> &src) {
 
 static void free_dir(DirDev &d) {
   void *ps[] = {d.first, d.tab, d.wq, d.l, d.r, d.pair_off, d.pair_i, d.pair_j, d.pair_x0,
-                d.pair_np, d.pair_po, d.pair_val, d.pair_val_f, d.node_e0, d.node_ne};
+                d.pair_np, d.pair_po, d.pair_T, d.pair_val, d.pair_val_f, d.node_e0, d.node_ne};
   for (void *p : ps)
     if (p) cudaFree(p);
   memset(&d, 0, sizeof d);
@@ -69,6 +69,7 @@ static iga_status upload_dir(iga_s *h, int ax) {
   CK(upload(&d.pair_x0, D.pair_x0));
   CK(upload(&d.pair_np, D.pair_np));
   CK(upload(&d.pair_po, D.pair_po));
+  CK(upload(&d.pair_T, D.pair_T));
   CK(upload(&d.pair_val, D.pair_val));
   std::vector<float> pf(D.pair_val.begin(), D.pair_val.end());
   CK(upload(&d.pair_val_f, pf));
@@ -148,7 +149,7 @@ static iga_status create_impl(iga_s *h, const iga_desc *d, const iga_bratu *b) {
   CK(cudaMalloc((void **)&h->Q00, (size_t)h->nelem * nq * sizeof(double)));
   // stage intermediates (sized for FP64)
   const Dir &D0 = h->dir[0], &D1 = h->dir[1], &D2 = h->dir[2];
-  int ng1 = (h->dim == 3) ? 9 : 4, ng2 = 4;
+  size_t ng1 = jacobian_t1_groups(h->dim), ng2 = jacobian_t2_groups(h->dim);
   h->T1_bytes = (size_t)ng1 * D0.npairs() * D1.X() * (h->dim == 3 ? D2.X() : 1) * sizeof(double);
   CK(cudaMalloc(&h->T1, h->T1_bytes));
   if (h->dim == 3) {
@@ -235,9 +236,9 @@ extern "C" iga_status iga_form_jacobian(iga_t h, const double *U, void *vals, ig
     return IGA_EINVAL;
   }
   if (prec == IGA_FP64) {
-    CK(launch_jacobian64(h, U, (double *)vals, 0));
+    CK(launch_jacobian64(h, U, (double *)vals, 0, nullptr));
   } else if (prec == IGA_JAC_TF32 || prec == IGA_JAC_BF16) {
-    CK(launch_jacobian32(h, U, (float *)vals, 0, (int)prec));
+    CK(launch_jacobian32(h, U, (float *)vals, 0, nullptr));
   } else {
     h->err = "unknown precision";
     return IGA_EINVAL;
@@ -297,22 +298,19 @@ static iga_status norm_host(iga_s *h, const double *x, double *out) {
 // Assemble the Newton Jacobian at U into h->J64 / h->J32.
 static iga_status newton_jacobian(iga_s *h, const double *U, bool f32, bool reuse) {
   if (!reuse) {
-    if (f32) CK(launch_jacobian32(h, U, h->J32, 0, 1));
-    else CK(launch_jacobian64(h, U, h->J64, 0));
+    if (f32) CK(launch_jacobian32(h, U, h->J32, 0, nullptr));
+    else CK(launch_jacobian64(h, U, h->J64, 0, nullptr));
     return IGA_OK;
   }
+  // J(U) = K + reaction(U): the stiffness K does not depend on U or lambda
   if (f32) {
     if (!h->Kstiff_f) CK(cudaMalloc((void **)&h->Kstiff_f, h->nnz * sizeof(float)));
-    if (!h->Mred_f) CK(cudaMalloc((void **)&h->Mred_f, h->nnz * sizeof(float)));
-    if (!h->K_valid_f) { CK(launch_jacobian32(h, nullptr, h->Kstiff_f, 1, 1)); h->K_valid_f = true; }
-    CK(launch_jacobian32(h, U, h->Mred_f, 2, 1));
-    CK(launch_combine32(h, h->Kstiff_f, h->Mred_f, h->J32));
+    if (!h->K_valid_f) { CK(launch_jacobian32(h, nullptr, h->Kstiff_f, 1, nullptr)); h->K_valid_f = true; }
+    CK(launch_jacobian32(h, U, h->J32, 2, h->Kstiff_f));
   } else {
     if (!h->Kstiff) CK(cudaMalloc((void **)&h->Kstiff, h->nnz * sizeof(double)));
-    if (!h->Mred) CK(cudaMalloc((void **)&h->Mred, h->nnz * sizeof(double)));
-    if (!h->K_valid) { CK(launch_jacobian64(h, nullptr, h->Kstiff, 1)); h->K_valid = true; }
-    CK(launch_jacobian64(h, U, h->Mred, 2));
-    CK(launch_combine64(h, h->Kstiff, h->Mred, h->J64));
+    if (!h->K_valid) { CK(launch_jacobian64(h, nullptr, h->Kstiff, 1, nullptr)); h->K_valid = true; }
+    CK(launch_jacobian64(h, U, h->J64, 2, h->Kstiff));
   }
   return IGA_OK;
 }
@@ -354,8 +352,11 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
     st = newton_jacobian(h, U, f32, o.reuse_stiffness != 0);
     if (st != IGA_OK) return st;
     IGA_LAUNCH(h, KC_VEC, (k_neg<<<eg, 256, 0, h->stream>>>(F, Ft, N)));
+    // forcing term min(rtol, ||F||) (quadratic Newton), but never below half the
+    // Newton tolerance: a linear residual under atol/2 already lets the step meet atol
     double rtol = o.krylov_rtol < fn ? o.krylov_rtol : fn;
     double tol_abs = rtol * fn;
+    if (tol_abs < 0.5 * o.atol) tol_abs = 0.5 * o.atol;
     if (tol_abs < 1e-14 * fn) tol_abs = 1e-14 * fn;
     int its = 0;
     cudaError_t ce = cudaSuccess;

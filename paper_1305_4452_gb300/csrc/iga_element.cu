@@ -1,4 +1,4 @@
-// Assembly kernels of libiga for sm_103a.
+// Element-level kernels of libiga for sm_103a: geometry factors, residual, Q00.
 //
 // Residual (Sec. 2.7 Algorithm 3 with Eq. residual): one fused kernel per
 // element tile -- gather U_e, sum-factorised interpolation of u~ and grad u~ to
@@ -7,15 +7,8 @@
 // gather kernel adds the element vectors of each control variable in a fixed
 // order (no atomics) and applies the Dirichlet rows.
 //
-// Jacobian (Eq. jacobian): the element integrals are written as one symmetric
-// 4x4 (3x3 in 2D) coefficient field Q_{mu nu} per Gauss point contracted with
-// tensor products of 1D basis functions and derivatives.  Because every
-// Jacobian entry J_AB is a sum over the Gauss points shared by the supports of
-// A and B, the contraction is done direction by direction over the whole mesh
-// ("global" sum factorisation): stage 1 contracts axis 0 into 1D function pairs
-// (i0, j0), stage 2 axis 1, stage 3 axis 2, which writes each CSR entry exactly
-// once.  Terms whose remaining directions share a derivative pattern are merged
-// after each stage (16 -> 9 -> 4 -> 1 in 3D).  Every sum runs in a fixed order.
+// The Gauss-point field Q00 for the Jacobian (u~ interpolated to the Gauss points)
+// is formed here too; the Jacobian stages live in iga_jacobian.cu.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -27,7 +20,7 @@ DirArgs dir_args(const DirDev &d) {
   a.p = d.p; a.q = d.q; a.nel = d.nel; a.n = d.n; a.np = d.np; a.X = d.X;
   a.first = d.first; a.tab = d.tab; a.wq = d.wq; a.l = d.l; a.r = d.r;
   a.pair_off = d.pair_off; a.pair_i = d.pair_i; a.pair_j = d.pair_j;
-  a.pair_x0 = d.pair_x0; a.pair_np = d.pair_np; a.pair_po = d.pair_po;
+  a.pair_x0 = d.pair_x0; a.pair_np = d.pair_np; a.pair_po = d.pair_po; a.pair_T = d.pair_T;
   a.pair_val = d.pair_val; a.pair_val_f = d.pair_val_f;
   a.node_e0 = d.node_e0; a.node_ne = d.node_ne;
   return a;
@@ -126,7 +119,7 @@ __global__ void __launch_bounds__(128) k_geometry(DirArgs d0, DirArgs d1, DirArg
   for (int al = 0; al < DIM; al++) {
     double sg = 0.0;
     for (int be = 0; be < DIM; be++) sg += S[al][be] * g[be];
-    rec[(gl.Sg + al) * NQ] = sg;
+    rec[(gl.Sg + al) * NQ] = -sg;  // stored negated: it enters the Jacobian as Q_0a = -(S g)_a
     gSg += g[al] * sg;
   }
   rec[gl.gSg * NQ] = gSg;
@@ -519,220 +512,6 @@ __global__ void __launch_bounds__(128) k_q00(DirArgs d0, DirArgs d1, DirArgs d2,
 #undef TB
 }
 
-// ---------------------------------------------------------------------------
-// Global sum-factorised Jacobian stages.
-// ---------------------------------------------------------------------------
-// A term of stage 1: Q field slot, sign, axis-0 pattern, output group.
-struct S1Term { int slot; int sign; int pat; int grp; };
-struct S1Terms { int n, ngrp, nslot; S1Term t[16]; int slot_field[10]; };  // slot_field: record field (-1 = Q00)
-struct SNTerm { int in; int pat; int out; };
-struct SNTerms { int n, nout; SNTerm t[9]; };
-
-// pattern code: (s,t) -> s + 2t ; s = derivative order of the test function, t of the trial
-static int patcode(int s, int t) { return s + 2 * t; }
-
-// Build the term lists of the three (3D) or two (2D) stages for a mode.
-// mode 0 = full Jacobian, 1 = stiffness only (Q00 = g^T S g), 2 = reaction only (Q00 only).
-struct StagePlan { S1Terms s1; SNTerms s2; SNTerms s3; };
-
-static StagePlan make_plan(int dim, const GeomLayout &gl, int mode) {
-  StagePlan P{};
-  int ns = dim * (dim + 1) / 2;
-  // slots: 0 = Q00, 1..ns = S, ns+1..ns+dim = Sg
-  P.s1.nslot = (mode == 2) ? 1 : 1 + ns + dim;
-  P.s1.slot_field[0] = -1;
-  for (int k = 0; k < ns; k++) P.s1.slot_field[1 + k] = gl.S + k;
-  for (int k = 0; k < dim; k++) P.s1.slot_field[1 + ns + k] = gl.Sg + k;
-  auto sidx = [&](int a, int b) {
-    if (a == b) return a;
-    if (a > b) { int t = a; a = b; b = t; }
-    if (dim == 2) return 2;
-    return (a == 0 && b == 1) ? 3 : ((a == 0 && b == 2) ? 4 : 5);
-  };
-  // keys of the groups after stage 1: (pattern axis1, pattern axis2)
-  int keys1[16], nk1 = 0;
-  auto key1_index = [&](int key) {
-    for (int i = 0; i < nk1; i++)
-      if (keys1[i] == key) return i;
-    keys1[nk1] = key;
-    return nk1++;
-  };
-  int nmu = dim + 1;
-  for (int mu = 0; mu < nmu; mu++)
-    for (int nu = 0; nu < nmu; nu++) {
-      if (mode == 2 && (mu != 0 || nu != 0)) continue;
-      int pat[3];
-      for (int ax = 0; ax < 3; ax++) pat[ax] = patcode(mu == ax + 1, nu == ax + 1);
-      S1Term T;
-      if (mu == 0 && nu == 0) { T.slot = 0; T.sign = 1; }
-      else if (mu == 0 || nu == 0) { T.slot = 1 + ns + (mu + nu - 1); T.sign = -1; }
-      else { T.slot = 1 + sidx(mu - 1, nu - 1); T.sign = 1; }
-      T.pat = pat[0];
-      int key = (dim == 3) ? pat[1] + 4 * pat[2] : pat[1];
-      T.grp = key1_index(key);
-      P.s1.t[P.s1.n++] = T;
-    }
-  P.s1.ngrp = nk1;
-  if (dim == 2) {
-    // final stage over axis 1: each group contracted with its axis-1 pattern
-    P.s2.nout = 1;
-    for (int i = 0; i < nk1; i++) P.s2.t[P.s2.n++] = SNTerm{i, keys1[i], 0};
-  } else {
-    int keys2[4], nk2 = 0;
-    for (int i = 0; i < nk1; i++) {
-      int pat1 = keys1[i] % 4, pat2 = keys1[i] / 4;
-      int o = -1;
-      for (int k = 0; k < nk2; k++)
-        if (keys2[k] == pat2) o = k;
-      if (o < 0) { keys2[nk2] = pat2; o = nk2++; }
-      P.s2.t[P.s2.n++] = SNTerm{i, pat1, o};
-    }
-    P.s2.nout = nk2;
-    P.s3.nout = 1;
-    for (int k = 0; k < nk2; k++) P.s3.t[P.s3.n++] = SNTerm{k, keys2[k], 0};
-  }
-  return P;
-}
-
-// Stage 1: contract axis 0 of the Q fields along one Gauss line (x1, x2).
-// out[grp][x2][x1][pi0] (3D) or out[grp][x1][pi0] (2D).
-template <typename T, int DIM, int P>
-__global__ void __launch_bounds__(256) k_stage1(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ geom,
-                                                const double *__restrict__ Q00, GeomLayout gl, S1Terms terms,
-                                                T *__restrict__ out) {
-  constexpr int Q = P + 1, NQ = ipow<DIM>(Q);
-  extern __shared__ double line[];  // [nslot][X0]
-  const int X0 = d0.X;
-  const int x1 = blockIdx.x, x2 = blockIdx.y;
-  const int e1 = x1 / Q, g1 = x1 % Q, e2 = x2 / Q, g2 = x2 % Q;
-  for (int idx = threadIdx.x; idx < terms.nslot * X0; idx += blockDim.x) {
-    int s = idx / X0, x0 = idx % X0;
-    int e0 = x0 / Q, g0 = x0 % Q;
-    int64_t e = e0 + (int64_t)d0.nel * (e1 + (int64_t)d1.nel * e2);
-    int qp = g0 + Q * (g1 + Q * g2);
-    int f = terms.slot_field[s];
-    line[idx] = (f < 0) ? Q00[(size_t)e * NQ + qp] : geom[((size_t)e * gl.nf + f) * NQ + qp];
-  }
-  __syncthreads();
-  const size_t plane = (size_t)d0.np * d1.X * (DIM == 3 ? d2.X : 1);
-  const size_t lineoff = ((size_t)x2 * d1.X + x1) * d0.np;
-  for (int pi = threadIdx.x; pi < d0.np; pi += blockDim.x) {
-    double acc[9];
-#pragma unroll
-    for (int g = 0; g < 9; g++) acc[g] = 0.0;
-    const int x0 = d0.pair_x0[pi], np = d0.pair_np[pi];
-    const double *pv = d0.pair_val + (size_t)d0.pair_po[pi] * 4;
-    for (int k = 0; k < np; k++) {
-      const double *pk = pv + 4 * k;
-#pragma unroll 1
-      for (int t = 0; t < terms.n; t++) {
-        const S1Term tt = terms.t[t];
-        double q = line[tt.slot * X0 + x0 + k];
-        double pr = pk[tt.pat];
-        if (tt.sign < 0) pr = -pr;
-        acc[tt.grp] = fma(pr, q, acc[tt.grp]);
-      }
-    }
-    for (int g = 0; g < terms.ngrp; g++) out[g * plane + lineoff + pi] = (T)acc[g];
-  }
-}
-
-// Stage 2 (3D): contract axis 1.  in[g1][x2][x1][pi0] -> out[g2][x2][pi1][pi0].
-template <typename T>
-__global__ void __launch_bounds__(128) k_stage2(DirArgs d0, DirArgs d1, DirArgs d2, SNTerms terms,
-                                                const T *__restrict__ in, T *__restrict__ out, int chunk) {
-  const int pi0 = blockIdx.x * blockDim.x + threadIdx.x;
-  const int x2 = blockIdx.z;
-  const int pa = blockIdx.y * chunk, pb = min(pa + chunk, d1.np);
-  if (pi0 >= d0.np) return;
-  const size_t inplane = (size_t)d0.np * d1.X * d2.X;
-  const size_t outplane = (size_t)d0.np * d1.np * d2.X;
-  for (int pi1 = pa; pi1 < pb; pi1++) {
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    const int xs = d1.pair_x0[pi1], np = d1.pair_np[pi1];
-    const double *pv = d1.pair_val + (size_t)d1.pair_po[pi1] * 4;
-    for (int k = 0; k < np; k++) {
-      const size_t o = ((size_t)x2 * d1.X + xs + k) * d0.np + pi0;
-#pragma unroll 1
-      for (int t = 0; t < terms.n; t++) {
-        const SNTerm tt = terms.t[t];
-        acc[tt.out] = fma(pv[4 * k + tt.pat], (double)in[tt.in * inplane + o], acc[tt.out]);
-      }
-    }
-    for (int g = 0; g < terms.nout; g++) out[g * outplane + ((size_t)x2 * d1.np + pi1) * d0.np + pi0] = (T)acc[g];
-  }
-}
-
-// Position of the entry (A, B) in the CSR values, and Dirichlet handling.
-struct CsrArgs {
-  const int64_t *rowptr;
-  const double *wts;  // rational weights (J_AB carries w_A w_B) or null
-  BndArgs bnd;
-};
-
-__device__ __forceinline__ bool on_dirichlet(const BndArgs &b, int dim, const int *i, const int *n) {
-  bool on = false;
-  for (int ax = 0; ax < dim; ax++) {
-    if (b.flag[ax][0] && i[ax] == 0) on = true;
-    if (b.flag[ax][1] && i[ax] == n[ax] - 1) on = true;
-  }
-  return on;
-}
-
-// Final stage.  3D: contract axis 2 of in[g2][x2][pi1][pi0]; 2D: contract axis 1
-// of in[g1][x1][pi0].  Writes every CSR entry once; Dirichlet rows/columns fixed.
-template <typename T, typename V, int DIM>
-__global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d2, SNTerms terms, const T *__restrict__ in,
-                                               CsrArgs csr, V *__restrict__ vals, int chunk, int fix) {
-  const int pi0 = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pi0 >= d0.np) return;
-  const DirArgs &dl = (DIM == 3) ? d2 : d1;   // the axis contracted here
-  const int pmid = (DIM == 3) ? blockIdx.z : 0;  // pi1 in 3D
-  const int pa = blockIdx.y * chunk, pb = min(pa + chunk, dl.np);
-  const size_t plane = (DIM == 3) ? (size_t)d0.np * d1.np * d2.X : (size_t)d0.np * d1.X;
-  const int i0 = d0.pair_i[pi0], j0 = d0.pair_j[pi0];
-  const int o0 = pi0 - d0.pair_off[i0], w0 = d0.r[i0] - d0.l[i0] + 1;
-  int i1 = 0, j1 = 0, o1 = 0, w1 = 1;
-  if (DIM == 3) {
-    i1 = d1.pair_i[pmid]; j1 = d1.pair_j[pmid];
-    o1 = pmid - d1.pair_off[i1]; w1 = d1.r[i1] - d1.l[i1] + 1;
-  }
-  for (int pl = pa; pl < pb; pl++) {
-    double acc = 0.0;
-    const int xs = dl.pair_x0[pl], np = dl.pair_np[pl];
-    const double *pv = dl.pair_val + (size_t)dl.pair_po[pl] * 4;
-    for (int k = 0; k < np; k++) {
-      size_t o = (DIM == 3) ? (((size_t)(xs + k) * d1.np + pmid) * d0.np + pi0) : ((size_t)(xs + k) * d0.np + pi0);
-#pragma unroll 1
-      for (int t = 0; t < terms.n; t++) acc = fma(pv[4 * k + terms.t[t].pat], (double)in[terms.t[t].in * plane + o], acc);
-    }
-    const int il = dl.pair_i[pl], jl = dl.pair_j[pl];
-    const int ol = pl - dl.pair_off[il];
-    int I[3], J[3], n[3] = {d0.n, d1.n, d2.n};
-    int64_t A, B, pos;
-    if (DIM == 3) {
-      I[0] = i0; I[1] = i1; I[2] = il; J[0] = j0; J[1] = j1; J[2] = jl;
-      A = i0 + (int64_t)d0.n * (i1 + (int64_t)d1.n * il);
-      B = j0 + (int64_t)d0.n * (j1 + (int64_t)d1.n * jl);
-      pos = csr.rowptr[A] + ((int64_t)ol * w1 + o1) * w0 + o0;
-    } else {
-      I[0] = i0; I[1] = il; J[0] = j0; J[1] = jl;
-      A = i0 + (int64_t)d0.n * il;
-      B = j0 + (int64_t)d0.n * jl;
-      pos = csr.rowptr[A] + (int64_t)ol * w0 + o0;
-    }
-    if (csr.wts) acc *= csr.wts[A] * csr.wts[B];
-    // fix 1: identity row and zero column (full or stiffness Jacobian);
-    // fix 2: zero row and column (the reaction part added to a fixed stiffness)
-    if (fix) {
-      bool ra = on_dirichlet(csr.bnd, DIM, I, n), cb = on_dirichlet(csr.bnd, DIM, J, n);
-      if (ra) acc = (fix == 1 && A == B) ? 1.0 : 0.0;
-      else if (cb) acc = 0.0;
-    }
-    vals[pos] = (V)acc;
-  }
-}
-
 // Column indices of the CSR pattern (Sec. 2.5): row A lists the lexicographic
 // product of the BasisStencil ranges, axis 0 fastest, so columns ascend.
 __global__ void k_colidx(DirArgs d0, DirArgs d1, DirArgs d2, int dim, const int64_t *__restrict__ rowptr,
@@ -746,14 +525,6 @@ __global__ void k_colidx(DirArgs d0, DirArgs d1, DirArgs d2, int dim, const int6
     for (int j1 = d1.l[i1]; j1 <= d1.r[i1]; j1++)
       for (int j0 = d0.l[i0]; j0 <= d0.r[i0]; j0++)
         colidx[k++] = (int32_t)(j0 + (int64_t)d0.n * (j1 + (int64_t)d1.n * j2));
-}
-
-// J = K + M: add the reaction-only values (on the same CSR layout) to the cached
-// stiffness; Dirichlet rows/columns were fixed in both with fix = 1 / 0.
-template <typename V>
-__global__ void k_combine(const V *__restrict__ K, const V *__restrict__ M, V *__restrict__ J, int64_t nnz) {
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k < nnz) J[k] = K[k] + M[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -829,63 +600,6 @@ cudaError_t launch_q00(iga_s *h, const double *U, double cs, double cr) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_q00(iga_s *h, const double *U, double lambda_scale) { return launch_q00(h, U, 1.0, lambda_scale); }
-
-template <typename T, typename V>
-static cudaError_t jacobian_stages(iga_s *h, V *vals, int mode, int fix) {
-  DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
-  StagePlan plan = make_plan(h->dim, h->gl, mode);
-  T *T1 = (T *)h->T1, *T2 = (T *)h->T2;
-  // stage 1
-  {
-    dim3 grid(a1.X, h->dim == 3 ? a2.X : 1);
-    size_t sm = (size_t)plan.s1.nslot * a0.X * sizeof(double);
-    IGA_LAUNCH(h, KC_STAGE1, DISPATCH_DP(h->dim, h->p, ({
-      if (sm > 48 * 1024) cudaFuncSetAttribute(k_stage1<T, D, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k_stage1<T, D, PP><<<grid, 256, sm, h->stream>>>(a0, a1, a2, h->geom, h->Q00, h->gl, plan.s1, T1);
-    })));
-  }
-  CsrArgs csr{h->rowptr, h->weights, h->bnd};
-  const int chunk = 8;
-  if (h->dim == 3) {
-    dim3 g2((a0.np + 127) / 128, (a1.np + chunk - 1) / chunk, a2.X);
-    IGA_LAUNCH(h, KC_STAGE2, (k_stage2<T><<<g2, 128, 0, h->stream>>>(a0, a1, a2, plan.s2, T1, T2, chunk)));
-    dim3 g3((a0.np + 127) / 128, (a2.np + chunk - 1) / chunk, a1.np);
-    IGA_LAUNCH(h, KC_FINAL, (k_final<T, V, 3><<<g3, 128, 0, h->stream>>>(a0, a1, a2, plan.s3, T2, csr, vals, chunk, fix)));
-  } else {
-    dim3 g3((a0.np + 127) / 128, (a1.np + chunk - 1) / chunk, 1);
-    IGA_LAUNCH(h, KC_FINAL, (k_final<T, V, 2><<<g3, 128, 0, h->stream>>>(a0, a1, a2, plan.s2, T1, csr, vals, chunk, fix)));
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_jacobian64(iga_s *h, const double *U, double *vals, int mode) {
-  // mode 0: full; 1: stiffness only (U ignored); 2: reaction only (no Dirichlet fix)
-  double cs = (mode == 2) ? 0.0 : 1.0, cr = (mode == 1) ? 0.0 : 1.0;
-  cudaError_t ce = launch_q00(h, U, cs, cr);
-  if (ce) return ce;
-  return jacobian_stages<double, double>(h, vals, mode, mode == 2 ? 2 : 1);
-}
-
-cudaError_t launch_jacobian32(iga_s *h, const double *U, float *vals, int mode, int opmode) {
-  (void)opmode;
-  double cs = (mode == 2) ? 0.0 : 1.0, cr = (mode == 1) ? 0.0 : 1.0;
-  cudaError_t ce = launch_q00(h, U, cs, cr);
-  if (ce) return ce;
-  return jacobian_stages<float, float>(h, vals, mode, mode == 2 ? 2 : 1);
-}
-
-cudaError_t launch_combine64(iga_s *h, const double *K, const double *M, double *vals) {
-  unsigned g = (unsigned)((h->nnz + 255) / 256);
-  IGA_LAUNCH(h, KC_COMBINE, (k_combine<double><<<g, 256, 0, h->stream>>>(K, M, vals, h->nnz)));
-  return cudaGetLastError();
-}
-
-cudaError_t launch_combine32(iga_s *h, const float *K, const float *M, float *vals) {
-  unsigned g = (unsigned)((h->nnz + 255) / 256);
-  IGA_LAUNCH(h, KC_COMBINE, (k_combine<float><<<g, 256, 0, h->stream>>>(K, M, vals, h->nnz)));
-  return cudaGetLastError();
-}
 
 cudaError_t launch_colidx(iga_s *h) {
   DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);

@@ -228,7 +228,7 @@ static iga_status build_dir(iga_s *h, const iga_desc *d, int ax, Dir &D) {
       D.pair_j.push_back(j);
       D.pair_x0.push_back(e0 * q);
       D.pair_np.push_back((e1 - e0) * q);
-      D.pair_po.push_back((int)(D.pair_val.size() / 4));
+      D.pair_po.push_back((int)(D.pair_val.size() / IGA_PVS));
       for (int e = e0; e < e1; e++)
         for (int g = 0; g < q; g++) {
           const double *ti = &D.tab[(((size_t)e * q + g) * n1 + (i - D.first[e])) * 2];
@@ -237,10 +237,21 @@ static iga_status build_dir(iga_s *h, const iga_desc *d, int ax, Dir &D) {
           D.pair_val.push_back(ti[1] * tj[0]);
           D.pair_val.push_back(ti[0] * tj[1]);
           D.pair_val.push_back(ti[1] * tj[1]);
+          D.pair_val.push_back(ti[1] * tj[0] + ti[0] * tj[1]);
         }
     }
   }
   D.pair_off[D.n] = (int)D.pair_j.size();
+  // index of the transposed pair (j, i); the stencil relation is symmetric
+  D.pair_T.resize(D.pair_j.size());
+  for (size_t k = 0; k < D.pair_j.size(); k++) {
+    int i = D.pair_i[k], j = D.pair_j[k];
+    if (i < D.l[j] || i > D.r[j]) {
+      h->err = iga_format("axis %d: stencil of %d does not contain %d", ax, j, i);
+      return IGA_EINVAL;
+    }
+    D.pair_T[k] = D.pair_off[j] + (i - D.l[j]);
+  }
   return IGA_OK;
 }
 

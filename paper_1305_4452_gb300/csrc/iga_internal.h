@@ -11,6 +11,7 @@
 #define IGA_MAXP 4                 // largest supported degree
 #define IGA_MAXN (IGA_MAXP + 1)    // largest number of nonzero 1D functions per element
 #define IGA_MAXQ (IGA_MAXP + 1)    // largest Gauss rule (q = p + 1)
+#define IGA_PVS 5                  // values per Gauss point in the 1D pair tables
 
 // Number of per-quadrature-point geometry fields (see GeomField) for each dimension.
 #define IGA_NGF2 11
@@ -23,13 +24,13 @@
 //   g[a]            grad_xi W / W
 //   S[ab]           kappa * jw * C / W^2   (symmetric; 2D: 00,11,01; 3D: 00,11,22,01,02,12)
 //   jwW             jw / W
-//   Sg[a]           (S g)_a
+//   nSg[a]          -(S g)_a
 //   gSg             g^T S g
 //   jwW2            jw / W^2
 // These turn the rational-basis integrands into polynomial-basis contractions:
 //   F_A = w_A sum_q [ grad M_A . v + M_A s ],  v = S (grad ũ - ũ g),  s = -g.v - jwW lambda e^u
 //   J_AB = w_A w_B sum_q sum_{mu,nu} Q_{mu nu} D_mu M_A D_nu M_B, with
-//   Q_00 = gSg - jwW2 lambda e^u, Q_0a = -Sg_a, Q_ab = S_ab
+//   Q_00 = gSg - jwW2 lambda e^u, Q_0a = nSg_a, Q_ab = S_ab
 // where ũ = sum (w_A U_A) M_A and u = ũ / W.
 struct GeomLayout {
   int nf;      // number of fields
@@ -51,7 +52,8 @@ struct Dir {
   std::vector<int> pair_x0;    // [P] first Gauss point (global index) of the overlap
   std::vector<int> pair_np;    // [P] number of Gauss points in the overlap
   std::vector<int> pair_po;    // [P] offset into pair_val (in points)
-  std::vector<double> pair_val;// [sum np][4]: B_i B_j, B'_i B_j, B_i B'_j, B'_i B'_j
+  std::vector<double> pair_val;// [sum np][5]: B_i B_j, B'_i B_j, B_i B'_j, B'_i B'_j, B'_i B_j + B_i B'_j
+  std::vector<int> pair_T;     // [P] index of the transposed pair (j, i)
   std::vector<int> node_e0;    // [n] first element containing the function
   std::vector<int> node_ne;    // [n] number of elements containing it
   int npairs() const { return (int)pair_j.size(); }
@@ -65,7 +67,7 @@ struct DirDev {
   double *tab;
   double *wq;
   int *l, *r;
-  int *pair_off, *pair_i, *pair_j, *pair_x0, *pair_np, *pair_po;
+  int *pair_off, *pair_i, *pair_j, *pair_x0, *pair_np, *pair_po, *pair_T;
   double *pair_val;
   float *pair_val_f;  // FP32 copy for the mixed-precision stages
   int *node_e0, *node_ne;
@@ -77,7 +79,7 @@ struct DirArgs {  // passed by value to kernels
   const double *tab;
   const double *wq;
   const int *l, *r;
-  const int *pair_off, *pair_i, *pair_j, *pair_x0, *pair_np, *pair_po;
+  const int *pair_off, *pair_i, *pair_j, *pair_x0, *pair_np, *pair_po, *pair_T;
   const double *pair_val;
   const float *pair_val_f;
   const int *node_e0, *node_ne;
@@ -163,17 +165,20 @@ struct iga_s {
 iga_status iga_build_dirs(iga_s *h, const iga_desc *d);
 void iga_rowptr(const iga_s *h, std::vector<int64_t> &rowptr);
 
-// ---- kernels (iga_assembly.cu) ----
+// ---- element kernels (iga_element.cu) ----
 DirArgs dir_args(const DirDev &d);
 cudaError_t launch_geometry(iga_s *h, const double *ctrl_dev, const double *logk_dev);
 cudaError_t launch_colidx(iga_s *h);
 cudaError_t launch_residual(iga_s *h, const double *U, double *F);
-cudaError_t launch_q00(iga_s *h, const double *U, double lambda_scale);
-// Jacobian: mode 0 = full, 1 = stiffness only (U-independent), 2 = reaction only
-cudaError_t launch_jacobian64(iga_s *h, const double *U, double *vals, int mode);
-cudaError_t launch_jacobian32(iga_s *h, const double *U, float *vals, int mode, int opmode);
-cudaError_t launch_combine64(iga_s *h, const double *K, const double *Mred, double *vals);
-cudaError_t launch_combine32(iga_s *h, const float *K, const float *Mred, float *vals);
+// Q00 = cs * g^T S g - cr * jw/W^2 * lambda * exp(u) at every Gauss point (U may be null when cr == 0)
+cudaError_t launch_q00(iga_s *h, const double *U, double cs, double cr);
+
+// ---- Jacobian stages (iga_jacobian.cu) ----
+// mode 0: full Jacobian; 1: stiffness only (U-independent); 2: vals = base + reaction(U)
+cudaError_t launch_jacobian64(iga_s *h, const double *U, double *vals, int mode, const double *base);
+cudaError_t launch_jacobian32(iga_s *h, const double *U, float *vals, int mode, const float *base);
+size_t jacobian_t1_groups(int dim);
+size_t jacobian_t2_groups(int dim);
 
 // ---- Krylov (iga_krylov.cu) ----
 cudaError_t launch_spmv64(iga_s *h, const double *vals, const double *x, double *y);

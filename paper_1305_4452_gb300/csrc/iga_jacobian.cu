@@ -1,0 +1,316 @@
+// Jacobian assembly of libiga by global sum factorisation (Eq. jacobian).
+//
+// With the cached geometry factors the Jacobian entry is
+//     J_AB = w_A w_B sum_q sum_{mu,nu} Q_{mu nu}(q) D_mu M_A(q) D_nu M_B(q),
+// mu, nu in {value, d/dxi_0, d/dxi_1, d/dxi_2}, Q symmetric.  M_A is a tensor
+// product of 1D B-splines, so the sum over the Gauss points of the whole mesh is
+// done one direction at a time: stage 1 contracts axis 0 into 1D function pairs
+// (i0, j0) -- the BasisStencil pairs of Sec. 2.5 -- stage 2 contracts axis 1, and
+// the final stage contracts the last axis and writes each CSR entry exactly once
+// (deterministic, no atomics).  After a stage, terms that share their derivative
+// pattern in the remaining directions are added, and Q's symmetry makes some
+// partial sums the pair-transposes of others, so the stiffness needs 10, 7 and 4
+// one-dimensional contractions per output in 3D (6 and 4 in 2D) instead of
+// 16, 9 and 4.  The reaction term alone (Q00 only) is one chain of single
+// contractions and can be added onto a previously assembled stiffness.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "iga_internal.h"
+
+namespace {
+
+template <int DIM> __host__ __device__ constexpr int ipow(int b) { return DIM == 2 ? b * b : b * b * b; }
+
+enum { PLAN_STIFF = 0, PLAN_MASS = 1 };
+
+struct CsrArgs {
+  const int64_t *rowptr;
+  const double *wts;  // rational weights (J_AB carries w_A w_B) or null
+  BndArgs bnd;
+};
+
+template <typename T> __device__ __forceinline__ const T *ptab(const DirArgs &d);
+template <> __device__ __forceinline__ const double *ptab<double>(const DirArgs &d) { return d.pair_val; }
+template <> __device__ __forceinline__ const float *ptab<float>(const DirArgs &d) { return d.pair_val_f; }
+
+template <int PLAN, int DIM> struct Shape {
+  static constexpr int NS = (PLAN == PLAN_MASS) ? 1 : (DIM == 3 ? 10 : 6);  // Q slots
+  static constexpr int NG1 = (PLAN == PLAN_MASS) ? 1 : (DIM == 3 ? 6 : 3);  // stored stage-1 groups
+  static constexpr int NG2 = (PLAN == PLAN_MASS) ? 1 : 3;                   // stored stage-2 groups (3D)
+};
+
+// Stage 1: one CTA per Gauss line (x1, x2); contract axis 0.
+// Q slots, 3D: 0 Q00, 1 S00, 2 S11, 3 S22, 4 S01, 5 S02, 6 S12, 7..9 nSg0..2
+//          2D: 0 Q00, 1 S00, 2 S11, 3 S01, 4 nSg0, 5 nSg1
+// Stored groups, keyed by the (axis-1, axis-2) derivative patterns:
+//   3D: G0 (00,00)  G1 (10,00)  G2 (11,00)  G3 (00,10)  G4 (10,01)  G5 (00,11)
+//       [(01,00), (00,01), (01,10) are the pair-transposes of G1, G3, G4]
+//   2D: G0 (00)  G1 (10)  G2 (11)   [(01) is the transpose of G1]
+template <typename T, int DIM, int P, int PLAN>
+__global__ void __launch_bounds__(256) k_stage1(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ geom,
+                                                const double *__restrict__ Q00, GeomLayout gl, T *__restrict__ out) {
+  constexpr int Q = P + 1, NQ = ipow<DIM>(Q);
+  using SH = Shape<PLAN, DIM>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *line = reinterpret_cast<T *>(smem_raw);  // [NS][X0]
+  const int X0 = d0.X;
+  const int x1 = blockIdx.x, x2 = blockIdx.y;
+  const int e1 = x1 / Q, g1 = x1 % Q, e2 = x2 / Q, g2 = x2 % Q;
+  for (int idx = threadIdx.x; idx < SH::NS * X0; idx += blockDim.x) {
+    int s = idx / X0, x0 = idx % X0;
+    int e0 = x0 / Q, g0 = x0 % Q;
+    int64_t e = e0 + (int64_t)d0.nel * (e1 + (int64_t)d1.nel * e2);
+    int qp = g0 + Q * (g1 + Q * g2);
+    int f;
+    if (s == 0) f = -1;
+    else if (DIM == 3) f = (s <= 6) ? gl.S + (s - 1) : gl.Sg + (s - 7);
+    else f = (s <= 3) ? gl.S + (s - 1) : gl.Sg + (s - 4);
+    line[idx] = (T)((f < 0) ? Q00[(size_t)e * NQ + qp] : geom[((size_t)e * gl.nf + f) * NQ + qp]);
+  }
+  __syncthreads();
+  const size_t plane = (size_t)d0.np * d1.X * (DIM == 3 ? d2.X : 1);
+  const size_t lineoff = ((size_t)x2 * d1.X + x1) * d0.np;
+  const T *tab = ptab<T>(d0);
+  for (int pi = threadIdx.x; pi < d0.np; pi += blockDim.x) {
+    const int xs = d0.pair_x0[pi], np = d0.pair_np[pi];
+    const T *pv = tab + (size_t)d0.pair_po[pi] * IGA_PVS;
+    const T *L = line + xs;
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
+    for (int k = 0; k < np; k++) {
+      const T p00 = pv[IGA_PVS * k + 0];
+      if (PLAN == PLAN_MASS) {
+        a0 = fma(p00, L[k], a0);
+      } else {
+        const T p01 = pv[IGA_PVS * k + 2], p11 = pv[IGA_PVS * k + 3], psym = pv[IGA_PVS * k + 4];
+        if (DIM == 3) {
+          a0 = fma(p00, L[k], a0);
+          a0 = fma(psym, L[7 * X0 + k], a0);
+          a0 = fma(p11, L[1 * X0 + k], a0);
+          a1 = fma(p00, L[8 * X0 + k], a1);
+          a1 = fma(p01, L[4 * X0 + k], a1);
+          a2 = fma(p00, L[2 * X0 + k], a2);
+          a3 = fma(p00, L[9 * X0 + k], a3);
+          a3 = fma(p01, L[5 * X0 + k], a3);
+          a4 = fma(p00, L[6 * X0 + k], a4);
+          a5 = fma(p00, L[3 * X0 + k], a5);
+        } else {
+          a0 = fma(p00, L[k], a0);
+          a0 = fma(psym, L[4 * X0 + k], a0);
+          a0 = fma(p11, L[1 * X0 + k], a0);
+          a1 = fma(p00, L[5 * X0 + k], a1);
+          a1 = fma(p01, L[3 * X0 + k], a1);
+          a2 = fma(p00, L[2 * X0 + k], a2);
+        }
+      }
+    }
+    T *o = out + lineoff + pi;
+    o[0] = a0;
+    if (PLAN == PLAN_STIFF) {
+      o[plane] = a1;
+      o[2 * plane] = a2;
+      if (DIM == 3) {
+        o[3 * plane] = a3;
+        o[4 * plane] = a4;
+        o[5 * plane] = a5;
+      }
+    }
+  }
+}
+
+// Stage 2 (3D): contract axis 1.  in[g1][x2][x1][pi0] -> out[g2][x2][pi1][pi0] with
+//   H0 (axis-2 pattern 00) = P^00 G0 + P^10 G1 + P^01 G1^T + P^11 G2
+//   H1 (axis-2 pattern 10) = P^00 G3 + P^01 G4^T
+//   H2 (axis-2 pattern 11) = P^00 G5          [pattern 01 is the transpose of H1]
+template <typename T, int PLAN>
+__global__ void __launch_bounds__(128) k_stage2(DirArgs d0, DirArgs d1, DirArgs d2, const T *__restrict__ in,
+                                                T *__restrict__ out, int chunk) {
+  const int pi0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int x2 = blockIdx.z;
+  const int pa = blockIdx.y * chunk, pb = min(pa + chunk, d1.np);
+  if (pi0 >= d0.np) return;
+  const int pi0T = d0.pair_T[pi0];
+  const size_t inplane = (size_t)d0.np * d1.X * d2.X;
+  const size_t outplane = (size_t)d0.np * d1.np * d2.X;
+  const T *tab = ptab<T>(d1);
+  for (int pi1 = pa; pi1 < pb; pi1++) {
+    const int xs = d1.pair_x0[pi1], np = d1.pair_np[pi1];
+    const T *pv = tab + (size_t)d1.pair_po[pi1] * IGA_PVS;
+    T h0 = 0, h1 = 0, h2 = 0;
+    for (int k = 0; k < np; k++) {
+      const size_t row = ((size_t)x2 * d1.X + xs + k) * d0.np;
+      const T p00 = pv[IGA_PVS * k + 0];
+      if (PLAN == PLAN_MASS) {
+        h0 = fma(p00, in[row + pi0], h0);
+      } else {
+        const T p10 = pv[IGA_PVS * k + 1], p01 = pv[IGA_PVS * k + 2], p11 = pv[IGA_PVS * k + 3];
+        h0 = fma(p00, in[row + pi0], h0);
+        h0 = fma(p10, in[inplane + row + pi0], h0);
+        h0 = fma(p01, in[inplane + row + pi0T], h0);
+        h0 = fma(p11, in[2 * inplane + row + pi0], h0);
+        h1 = fma(p00, in[3 * inplane + row + pi0], h1);
+        h1 = fma(p01, in[4 * inplane + row + pi0T], h1);
+        h2 = fma(p00, in[5 * inplane + row + pi0], h2);
+      }
+    }
+    T *o = out + ((size_t)x2 * d1.np + pi1) * d0.np + pi0;
+    o[0] = h0;
+    if (PLAN == PLAN_STIFF) {
+      o[outplane] = h1;
+      o[2 * outplane] = h2;
+    }
+  }
+}
+
+__device__ __forceinline__ bool on_dirichlet(const BndArgs &b, int dim, const int *i, const int *n) {
+  bool on = false;
+  for (int ax = 0; ax < dim; ax++) {
+    if (b.flag[ax][0] && i[ax] == 0) on = true;
+    if (b.flag[ax][1] && i[ax] == n[ax] - 1) on = true;
+  }
+  return on;
+}
+
+// Final stage: contract the last axis and write the CSR entries.
+//   3D: in = T2[g2][x2][pi1][pi0];  J = P^00 H0 + P^10 H1 + P^01 H1^T + P^11 H2
+//   2D: in = T1[g1][x1][pi0];       J = P^00 G0 + P^10 G1 + P^01 G1^T + P^11 G2
+// fix = 1: Dirichlet rows become identity rows and Dirichlet columns zero;
+// fix = 2: vals = base + contribution, with no contribution in Dirichlet rows or
+//          columns (the base -- a stiffness assembled with fix = 1 -- holds them).
+template <typename T, typename V, int DIM, int PLAN>
+__global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d2, const T *__restrict__ in, CsrArgs csr,
+                                               V *__restrict__ vals, const V *__restrict__ base, int chunk, int fix) {
+  const int pi0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pi0 >= d0.np) return;
+  const DirArgs &dl = (DIM == 3) ? d2 : d1;
+  const int pmid = (DIM == 3) ? blockIdx.z : 0;
+  const int pa = blockIdx.y * chunk, pb = min(pa + chunk, dl.np);
+  const size_t plane = (DIM == 3) ? (size_t)d0.np * d1.np * d2.X : (size_t)d0.np * d1.X;
+  const int pi0T = d0.pair_T[pi0];
+  const int i0 = d0.pair_i[pi0], j0 = d0.pair_j[pi0];
+  const int o0 = pi0 - d0.pair_off[i0], w0 = d0.r[i0] - d0.l[i0] + 1;
+  int i1 = 0, j1 = 0, o1 = 0, w1 = 1, pmidT = 0;
+  if (DIM == 3) {
+    i1 = d1.pair_i[pmid]; j1 = d1.pair_j[pmid];
+    o1 = pmid - d1.pair_off[i1]; w1 = d1.r[i1] - d1.l[i1] + 1;
+    pmidT = d1.pair_T[pmid];
+  }
+  const T *tab = ptab<T>(dl);
+  for (int pl = pa; pl < pb; pl++) {
+    const int xs = dl.pair_x0[pl], np = dl.pair_np[pl];
+    const T *pv = tab + (size_t)dl.pair_po[pl] * IGA_PVS;
+    T acc = 0;
+    for (int k = 0; k < np; k++) {
+      const size_t xo = (size_t)(xs + k);
+      const T p00 = pv[IGA_PVS * k + 0];
+      size_t r, rT;
+      if (DIM == 3) {
+        r = (xo * d1.np + pmid) * d0.np + pi0;
+        rT = (xo * d1.np + pmidT) * d0.np + pi0T;
+      } else {
+        r = xo * d0.np + pi0;
+        rT = xo * d0.np + pi0T;
+      }
+      if (PLAN == PLAN_MASS) {
+        acc = fma(p00, in[r], acc);
+      } else {
+        const T p10 = pv[IGA_PVS * k + 1], p01 = pv[IGA_PVS * k + 2], p11 = pv[IGA_PVS * k + 3];
+        acc = fma(p00, in[r], acc);
+        acc = fma(p10, in[plane + r], acc);
+        acc = fma(p01, in[plane + rT], acc);
+        acc = fma(p11, in[2 * plane + r], acc);
+      }
+    }
+    const int il = dl.pair_i[pl], jl = dl.pair_j[pl];
+    const int ol = pl - dl.pair_off[il];
+    int I[3], J[3], n[3] = {d0.n, d1.n, d2.n};
+    int64_t A, B, pos;
+    if (DIM == 3) {
+      I[0] = i0; I[1] = i1; I[2] = il; J[0] = j0; J[1] = j1; J[2] = jl;
+      A = i0 + (int64_t)d0.n * (i1 + (int64_t)d1.n * il);
+      B = j0 + (int64_t)d0.n * (j1 + (int64_t)d1.n * jl);
+      pos = csr.rowptr[A] + ((int64_t)ol * w1 + o1) * w0 + o0;
+    } else {
+      I[0] = i0; I[1] = il; J[0] = j0; J[1] = jl;
+      A = i0 + (int64_t)d0.n * il;
+      B = j0 + (int64_t)d0.n * jl;
+      pos = csr.rowptr[A] + (int64_t)ol * w0 + o0;
+    }
+    double v = (double)acc;
+    if (csr.wts) v *= csr.wts[A] * csr.wts[B];
+    if (fix) {
+      bool ra = on_dirichlet(csr.bnd, DIM, I, n), cb = on_dirichlet(csr.bnd, DIM, J, n);
+      if (ra || cb) v = (fix == 1 && A == B) ? 1.0 : 0.0;
+    }
+    vals[pos] = base ? (V)((double)base[pos] + v) : (V)v;
+  }
+}
+
+#define DISPATCH_P(P_, CALL)                        \
+  do {                                              \
+    switch (P_) {                                   \
+      case 1: { constexpr int PP = 1; CALL; } break; \
+      case 2: { constexpr int PP = 2; CALL; } break; \
+      case 3: { constexpr int PP = 3; CALL; } break; \
+      case 4: { constexpr int PP = 4; CALL; } break; \
+    }                                               \
+  } while (0)
+
+template <typename T, int DIM, int PLAN>
+cudaError_t run_stage1(iga_s *h, T *T1) {
+  DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
+  dim3 grid(a1.X, DIM == 3 ? a2.X : 1);
+  size_t sm = (size_t)Shape<PLAN, DIM>::NS * a0.X * sizeof(T);
+  IGA_LAUNCH(h, KC_STAGE1, DISPATCH_P(h->p, ({
+    auto kern = k_stage1<T, DIM, PP, PLAN>;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    kern<<<grid, 256, sm, h->stream>>>(a0, a1, a2, h->geom, h->Q00, h->gl, T1);
+  })));
+  return cudaGetLastError();
+}
+
+template <typename T, typename V, int DIM, int PLAN>
+cudaError_t run_stages(iga_s *h, V *vals, const V *base, int fix) {
+  DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
+  T *T1 = (T *)h->T1, *T2 = (T *)h->T2;
+  cudaError_t ce = run_stage1<T, DIM, PLAN>(h, T1);
+  if (ce) return ce;
+  CsrArgs csr{h->rowptr, h->weights, h->bnd};
+  const int chunk = 8;
+  if (DIM == 3) {
+    dim3 g2((a0.np + 127) / 128, (a1.np + chunk - 1) / chunk, a2.X);
+    IGA_LAUNCH(h, KC_STAGE2, (k_stage2<T, PLAN><<<g2, 128, 0, h->stream>>>(a0, a1, a2, T1, T2, chunk)));
+    dim3 g3((a0.np + 127) / 128, (a2.np + chunk - 1) / chunk, a1.np);
+    IGA_LAUNCH(h, KC_FINAL, (k_final<T, V, 3, PLAN><<<g3, 128, 0, h->stream>>>(a0, a1, a2, T2, csr, vals, base, chunk, fix)));
+  } else {
+    dim3 g3((a0.np + 127) / 128, (a1.np + chunk - 1) / chunk, 1);
+    IGA_LAUNCH(h, KC_FINAL, (k_final<T, V, 2, PLAN><<<g3, 128, 0, h->stream>>>(a0, a1, a2, T1, csr, vals, base, chunk, fix)));
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, typename V>
+cudaError_t jacobian(iga_s *h, const double *U, V *vals, int mode, const V *base) {
+  // mode 0: full; 1: stiffness only (U-independent); 2: base + reaction
+  double cs = (mode == 2) ? 0.0 : 1.0, cr = (mode == 1) ? 0.0 : 1.0;
+  cudaError_t ce = launch_q00(h, U, cs, cr);
+  if (ce) return ce;
+  if (mode == 2) {
+    if (!base) return cudaErrorInvalidValue;
+    return h->dim == 3 ? run_stages<T, V, 3, PLAN_MASS>(h, vals, base, 2) : run_stages<T, V, 2, PLAN_MASS>(h, vals, base, 2);
+  }
+  return h->dim == 3 ? run_stages<T, V, 3, PLAN_STIFF>(h, vals, nullptr, 1) : run_stages<T, V, 2, PLAN_STIFF>(h, vals, nullptr, 1);
+}
+
+}  // namespace
+
+size_t jacobian_t1_groups(int dim) { return dim == 3 ? 6 : 3; }
+size_t jacobian_t2_groups(int dim) { return dim == 3 ? 3 : 0; }
+
+cudaError_t launch_jacobian64(iga_s *h, const double *U, double *vals, int mode, const double *base) {
+  return jacobian<double, double>(h, U, vals, mode, base);
+}
+
+cudaError_t launch_jacobian32(iga_s *h, const double *U, float *vals, int mode, const float *base) {
+  return jacobian<float, float>(h, U, vals, mode, base);
+}

@@ -270,15 +270,16 @@ static int grid_for(int64_t N, int threads, int cap) {
 
 template <typename V>
 static cudaError_t spmv_launch(iga_s *h, const V *vals, const double *x, double *y, const double *done) {
+  // Few lanes per row: the cross-lane reduction costs log2(LPR) FP64 adds on every
+  // lane of the group, which on GB300's narrow FP64 pipe is not free; 4 lanes keep
+  // the loads sector-efficient (4 x 8 B contiguous per row and step).
   double avg = (double)h->nnz / (double)h->N;
-  int lpr = avg >= 96 ? 32 : (avg >= 40 ? 16 : (avg >= 16 ? 8 : 4));
+  int lpr = avg >= 8 ? 4 : 2;
   int64_t threads = h->N * lpr;
   unsigned grid = (unsigned)((threads + 255) / 256);
   switch (lpr) {
-    case 32: IGA_LAUNCH(h, KC_SPMV, (k_spmv<V, 32><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, x, y, h->N, done))); break;
-    case 16: IGA_LAUNCH(h, KC_SPMV, (k_spmv<V, 16><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, x, y, h->N, done))); break;
-    case 8: IGA_LAUNCH(h, KC_SPMV, (k_spmv<V, 8><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, x, y, h->N, done))); break;
-    default: IGA_LAUNCH(h, KC_SPMV, (k_spmv<V, 4><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, x, y, h->N, done))); break;
+    case 4: IGA_LAUNCH(h, KC_SPMV, (k_spmv<V, 4><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, x, y, h->N, done))); break;
+    default: IGA_LAUNCH(h, KC_SPMV, (k_spmv<V, 2><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, x, y, h->N, done))); break;
   }
   return cudaGetLastError();
 }
