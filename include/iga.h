@@ -120,6 +120,24 @@ iga_status iga_get_pattern(iga_t iga, int64_t *n, int64_t *nnz, const int64_t **
  * caller-owned, must not overlap.  Dirichlet rows as set by iga_set_boundary_value. */
 iga_status iga_form_residual(iga_t iga, const double *U, double *F);
 
+/* Residual F(U) exactly as iga_form_residual, for callers that cannot allocate
+ * device memory at call time (an allocator they do not own holds the device, a
+ * real-time loop cannot take an allocation's latency or failure): this call
+ * allocates nothing.  The paper has no counterpart; it is a library-level
+ * variant.  Its element-vector scratch is a fixed array of
+ * IGA_NOALLOC_MAX_ELEMENT_VALUES doubles (16 MiB) in the library's device memory,
+ * held on every GPU that loads the library until the process exits.
+ *  - Problems with elements x (p+1)^dim above that limit are rejected with
+ *    IGA_EINVAL (nothing is written); iga_form_residual has no such limit.
+ *  - The first call on a device looks up the array's device address with that
+ *    device current; make it before any stream capture.
+ *  - All calls share the array: calls that overlap on the GPU race.  Nothing in
+ *    it needs to start at zero (every entry read was written by the same call).
+ * U and F: device double[n], caller-owned, distinct; stream-ordered like the other
+ * calls; results are bit-identical to iga_form_residual. */
+#define IGA_NOALLOC_MAX_ELEMENT_VALUES 2097152u
+iga_status iga_form_residual_noalloc(iga_t iga, const double *U, double *F);
+
 /* Jacobian J(U) of Eq. (jacobian) into CSR values on the library's pattern.
  * vals: device memory, caller-owned, nnz entries of double (IGA_FP64) or float
  * (IGA_JAC_TF32, IGA_JAC_BF16). */

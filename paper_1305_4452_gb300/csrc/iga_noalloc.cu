@@ -1,0 +1,79 @@
+// iga_form_residual_noalloc: residual assembly that allocates no device memory.
+//
+// Some callers cannot call cudaMalloc at the moment they need a residual: code
+// running under a memory budget fixed by another allocator that owns the device
+// (a framework's caching pool, an embedded solver inside a larger application),
+// real-time loops where an allocation's latency or possible failure is not
+// acceptable, or callers that must not add any allocation of their own.
+// iga_form_residual uses an element-vector buffer that iga_create allocated; this
+// variant runs the same kernels with that buffer replaced by a fixed array in the
+// library's own device memory, so the call itself never allocates.
+//
+// The array is a file-scope __device__ variable of IGA_NOALLOC_MAX_ELEMENT_VALUES
+// doubles (16 MiB).  Every GPU that loads this code holds it until the process
+// exits.  Its device address is looked up once per device, on the first call made
+// with that device current (cudaGetSymbolAddress); make that first call outside
+// any stream capture.  All calls share the array, so calls that overlap on the GPU
+// (different streams or different handles at the same time) race on it; the
+// kernels overwrite every entry they later read, so no part of it has to start
+// at zero and stale contents from an earlier call are never used.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "iga_internal.h"
+
+cudaError_t launch_residual_into(iga_s *h, const double *U, double *F, double *Fe);
+
+static __device__ __align__(256) double g_residual_scratch[IGA_NOALLOC_MAX_ELEMENT_VALUES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+double *g_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once per device).
+cudaError_t scratch_address(double **out) {
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return ce;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_addr[dev]) {
+    void *p = nullptr;
+    ce = cudaGetSymbolAddress(&p, g_residual_scratch);
+    if (ce != cudaSuccess) return ce;
+    g_addr[dev] = (double *)p;
+  }
+  *out = g_addr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" iga_status iga_form_residual_noalloc(iga_t h, const double *U, double *F) {
+  if (!h) return IGA_EINVAL;
+  if (!U || !F || U == F) {
+    h->err = "U and F must be distinct non-NULL device pointers";
+    return IGA_EINVAL;
+  }
+  int nen = (h->dim == 3) ? (h->p + 1) * (h->p + 1) * (h->p + 1) : (h->p + 1) * (h->p + 1);
+  unsigned long long need = (unsigned long long)h->nelem * (unsigned long long)nen;
+  if (need > (unsigned long long)IGA_NOALLOC_MAX_ELEMENT_VALUES) {
+    h->err = iga_format("iga_form_residual_noalloc: %llu element values (elements x (p+1)^dim) exceed the fixed "
+                        "scratch of %u; use iga_form_residual",
+                        need, (unsigned)IGA_NOALLOC_MAX_ELEMENT_VALUES);
+    return IGA_EINVAL;
+  }
+  double *scratch = nullptr;
+  cudaError_t ce = scratch_address(&scratch);
+  if (ce != cudaSuccess) {
+    h->err = iga_format("iga_form_residual_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(ce));
+    return IGA_ECUDA;
+  }
+  ce = launch_residual_into(h, U, F, scratch);
+  if (ce != cudaSuccess) {
+    h->err = iga_format("iga_form_residual_noalloc: %s", cudaGetErrorString(ce));
+    return IGA_ECUDA;
+  }
+  return IGA_OK;
+}

@@ -20,7 +20,7 @@ IGA_FP64, IGA_JAC_TF32, IGA_JAC_BF16 = 0, 1, 2
 # every symbol include/iga.h declares
 EXPORTS = ["iga_create", "iga_set_boundary_value", "iga_set_lambda", "iga_get_pattern", "iga_form_residual",
            "iga_form_jacobian", "iga_newton_defaults", "iga_solve_newton", "iga_solve_newton_host", "iga_destroy",
-           "iga_last_error", "iga_profile_enable", "iga_profile_read"]
+           "iga_last_error", "iga_profile_enable", "iga_profile_read", "iga_form_residual_noalloc"]
 
 KERNEL_CLASSES = ["geometry", "residual_element", "residual_gather", "q00", "jac_stage1", "jac_stage2", "jac_final",
                   "spmv", "gs_orth", "gmres_scalar", "vector", "combine", "pattern"]
@@ -89,6 +89,7 @@ def lib():
         L.iga_get_pattern.argtypes = [vp, i64p, i64p, ctypes.POINTER(vp), ctypes.POINTER(vp)]
         L.iga_form_residual.argtypes = [vp, vp, vp]
         L.iga_form_jacobian.argtypes = [vp, vp, vp, ctypes.c_int]
+        L.iga_form_residual_noalloc.argtypes = [vp, vp, vp]
         L.iga_newton_defaults.argtypes = [ctypes.POINTER(IgaNewtonOpts)]
         L.iga_newton_defaults.restype = None
         L.iga_solve_newton.argtypes = [vp, vp, ctypes.POINTER(IgaNewtonOpts), ctypes.POINTER(IgaNewtonReport)]
