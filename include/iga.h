@@ -56,7 +56,8 @@ typedef enum {
 typedef enum {
   IGA_FP64 = 0,     /* FP64 element arithmetic, FP64 values (double *) */
   IGA_JAC_TF32 = 1, /* element contraction with TF32 operands, FP32 accumulate; float * values */
-  IGA_JAC_BF16 = 2  /* element contraction with BF16 operands, FP32 accumulate; float * values */
+  IGA_JAC_BF16 = 2, /* element contraction with BF16 operands, FP32 accumulate; float * values */
+  IGA_JAC_FP32 = 3  /* global sum factorisation in FP32 on the CUDA cores; float * values */
 } iga_precision;
 
 /* Discretisation (the IGASetDim / IGASetFromOptions data of Sec. 3.2).
@@ -184,13 +185,14 @@ iga_status iga_solve_newton_host(iga_t iga, double *U_host, const iga_newton_opt
  *   0 geometry factors, 1 residual element kernel, 2 residual gather, 3 Q00 /
  *   u at Gauss points, 4 Jacobian stage 1, 5 Jacobian stage 2, 6 Jacobian final
  *   stage, 7 SpMV, 8 Gram-Schmidt multi-dot/update, 9 GMRES scalar kernels,
- *   10 vector kernels, 11 stiffness + reaction combine, 12 CSR pattern.
+ *   10 vector kernels, 11 stiffness + reaction combine, 12 CSR pattern,
+ *   13 tensor-core element matrices, 14 element-matrix gather.
  * iga_profile_enable(iga, mask): classes whose bit is set get a CUDA event pair
  * recorded around each launch on the library's stream (mask 0: timing off;
  * launches are always counted).  iga_profile_read synchronises the stream,
  * returns the totals since the last read (ms[c], timed[c] = timed launches,
  * launches[c] = all launches) and resets them. */
-#define IGA_NCLASS 13
+#define IGA_NCLASS 15
 typedef struct {
   double ms[16];
   long long timed[16];

@@ -41,7 +41,8 @@ static void free_dir(DirDev &d) {
 static void release(iga_s *h) {
   for (int ax = 0; ax < 3; ax++) free_dir(h->ddev[ax]);
   void *ps[] = {h->rowptr, h->colidx, h->weights, h->geom, h->Fe, h->Q00, h->T1, h->T2, h->Kstiff, h->Kstiff_f,
-                h->Mred, h->Mred_f, h->J64, h->J32, h->wk, h->V, h->red, h->ctl, h->Uhost_dev};
+                h->Mred, h->Mred_f, h->J64, h->J32, h->wk, h->V, h->red, h->ctl, h->Uhost_dev,
+                h->geom32, h->tab32[0], h->tab32[1], h->tab32[2], h->Ebuf, h->z32};
   for (void *p : ps)
     if (p) cudaFree(p);
   if (h->ctl_host) cudaFreeHost(h->ctl_host);
@@ -237,8 +238,14 @@ extern "C" iga_status iga_form_jacobian(iga_t h, const double *U, void *vals, ig
   }
   if (prec == IGA_FP64) {
     CK(launch_jacobian64(h, U, (double *)vals, 0, nullptr));
-  } else if (prec == IGA_JAC_TF32 || prec == IGA_JAC_BF16) {
+  } else if (prec == IGA_JAC_FP32) {
     CK(launch_jacobian32(h, U, (float *)vals, 0, nullptr));
+  } else if (prec == IGA_JAC_TF32 || prec == IGA_JAC_BF16) {
+    if (!mixed_supported(h->dim, h->p)) {
+      h->err = iga_format("mixed-precision Jacobian supports p <= %d in %dD", h->dim == 3 ? 3 : 4, h->dim);
+      return IGA_EINVAL;
+    }
+    CK(launch_jacobian_mixed(h, U, (float *)vals, (int)prec));
   } else {
     h->err = "unknown precision";
     return IGA_EINVAL;
@@ -283,6 +290,7 @@ static iga_status ensure_workspace(iga_s *h, int m, bool f32) {
   }
   if (!f32 && !h->J64) CK(cudaMalloc((void **)&h->J64, h->nnz * sizeof(double)));
   if (f32 && !h->J32) CK(cudaMalloc((void **)&h->J32, h->nnz * sizeof(float)));
+  if (f32 && !h->z32) CK(cudaMalloc((void **)&h->z32, N * sizeof(float)));
   return IGA_OK;
 }
 
@@ -296,7 +304,11 @@ static iga_status norm_host(iga_s *h, const double *x, double *out) {
 }
 
 // Assemble the Newton Jacobian at U into h->J64 / h->J32.
-static iga_status newton_jacobian(iga_s *h, const double *U, bool f32, bool reuse) {
+static iga_status newton_jacobian(iga_s *h, const double *U, bool f32, bool reuse, int prec) {
+  if (f32 && prec != IGA_JAC_FP32) {  // tensor-core element matrices, assembled in full each step
+    CK(launch_jacobian_mixed(h, U, h->J32, prec));
+    return IGA_OK;
+  }
   if (!reuse) {
     if (f32) CK(launch_jacobian32(h, U, h->J32, 0, nullptr));
     else CK(launch_jacobian64(h, U, h->J64, 0, nullptr));
@@ -320,8 +332,12 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
   iga_newton_opts o;
   iga_newton_defaults(&o);
   if (opts_in) o = *opts_in;
+  if ((o.jac == IGA_JAC_TF32 || o.jac == IGA_JAC_BF16) && !mixed_supported(h->dim, h->p)) {
+    h->err = "mixed-precision Jacobian not supported for this degree";
+    return IGA_EINVAL;
+  }
   if (!U || o.gmres_restart < 1 || o.gmres_restart > 1000 || o.max_newton < 0 || !(o.atol >= 0.0) ||
-      (o.jac != IGA_FP64 && o.jac != IGA_JAC_TF32 && o.jac != IGA_JAC_BF16)) {
+      (o.jac != IGA_FP64 && o.jac != IGA_JAC_TF32 && o.jac != IGA_JAC_BF16 && o.jac != IGA_JAC_FP32)) {
     h->err = "bad Newton options or NULL U";
     return IGA_EINVAL;
   }
@@ -349,12 +365,15 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
     if (!isfinite(fn)) { R.status = IGA_ENAN; break; }
     if (fn <= o.atol) { R.status = IGA_OK; break; }
     if (k >= o.max_newton) { R.status = IGA_ENOCONV; break; }
-    st = newton_jacobian(h, U, f32, o.reuse_stiffness != 0);
+    st = newton_jacobian(h, U, f32, o.reuse_stiffness != 0, (int)o.jac);
     if (st != IGA_OK) return st;
     IGA_LAUNCH(h, KC_VEC, (k_neg<<<eg, 256, 0, h->stream>>>(F, Ft, N)));
     // forcing term min(rtol, ||F||) (quadratic Newton), but never below half the
     // Newton tolerance: a linear residual under atol/2 already lets the step meet atol
     double rtol = o.krylov_rtol < fn ? o.krylov_rtol : fn;
+    // with a reduced-precision Jacobian (and FP32 operator products) a linear solve
+    // tighter than the Jacobian's own error buys nothing
+    if (f32 && rtol < 1e-4) rtol = 1e-4;
     double tol_abs = rtol * fn;
     if (tol_abs < 0.5 * o.atol) tol_abs = 0.5 * o.atol;
     if (tol_abs < 1e-14 * fn) tol_abs = 1e-14 * fn;

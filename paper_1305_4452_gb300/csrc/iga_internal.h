@@ -93,7 +93,7 @@ struct BndArgs {
 // Kernel classes for launch counting and event timing (iga_profile_*).
 enum KClass {
   KC_GEOM = 0, KC_RES_ELEM, KC_RES_GATHER, KC_Q00, KC_STAGE1, KC_STAGE2, KC_FINAL, KC_SPMV, KC_ORTH,
-  KC_GMRES_SCALAR, KC_VEC, KC_COMBINE, KC_PATTERN, KC_N
+  KC_GMRES_SCALAR, KC_VEC, KC_COMBINE, KC_PATTERN, KC_ELEM_TC, KC_ELEM_GATHER, KC_N
 };
 
 struct ProfRec {
@@ -149,6 +149,11 @@ struct iga_s {
   float *Mred_f = nullptr;
   bool K_valid = false, K_valid_f = false;  // Kstiff / Kstiff_f hold the current stiffness
   double *Uhost_dev = nullptr; // device copy of U for the host-buffer solve
+  // mixed-precision Jacobian (tensor cores)
+  float *geom32 = nullptr;     // [nelem][slots][nq] FP32 geometry factors
+  float *tab32[3] = {nullptr, nullptr, nullptr};  // FP32 basis tables
+  float *Ebuf = nullptr;       // [nelem][nen][nen] element matrices
+  float *z32 = nullptr;        // FP32 copy of the Krylov vector for the FP32 SpMV
   // Newton / Krylov workspace
   double *J64 = nullptr;
   float *J32 = nullptr;
@@ -178,6 +183,9 @@ cudaError_t launch_q00(iga_s *h, const double *U, double cs, double cr);
 cudaError_t launch_jacobian64(iga_s *h, const double *U, double *vals, int mode, const double *base);
 cudaError_t launch_jacobian32(iga_s *h, const double *U, float *vals, int mode, const float *base);
 size_t jacobian_t1_groups(int dim);
+// ---- mixed-precision Jacobian (iga_mixed.cu) ----
+bool mixed_supported(int dim, int p);
+cudaError_t launch_jacobian_mixed(iga_s *h, const double *U, float *vals, int prec);
 size_t jacobian_t2_groups(int dim);
 
 // ---- Krylov (iga_krylov.cu) ----

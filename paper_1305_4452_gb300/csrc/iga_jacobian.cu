@@ -35,9 +35,8 @@ template <> __device__ __forceinline__ const double *ptab<double>(const DirArgs 
 template <> __device__ __forceinline__ const float *ptab<float>(const DirArgs &d) { return d.pair_val_f; }
 
 template <int PLAN, int DIM> struct Shape {
-  static constexpr int NS = (PLAN == PLAN_MASS) ? 1 : (DIM == 3 ? 10 : 6);  // Q slots
-  static constexpr int NG1 = (PLAN == PLAN_MASS) ? 1 : (DIM == 3 ? 6 : 3);  // stored stage-1 groups
-  static constexpr int NG2 = (PLAN == PLAN_MASS) ? 1 : 3;                   // stored stage-2 groups (3D)
+  // Q slots read by stage 1; stored groups: stage 1 6 (3D) / 3 (2D), stage 2 3 (1 for PLAN_MASS)
+  static constexpr int NS = (PLAN == PLAN_MASS) ? 1 : (DIM == 3 ? 10 : 6);
 };
 
 // Stage 1: one CTA per Gauss line (x1, x2); contract axis 0.

@@ -73,6 +73,30 @@ __global__ void __launch_bounds__(256) k_spmv(const int64_t *__restrict__ rowptr
   if (lane == 0) y[row] = acc;
 }
 
+// y = J x with FP32 values and an FP32 copy of x, accumulated in FP32 (the
+// reduced-precision Jacobian only steers Newton; vectors stay FP64 outside).
+template <int LPR>
+__global__ void __launch_bounds__(256) k_spmv_f32(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                                  const float *__restrict__ val, const float *__restrict__ x,
+                                                  double *__restrict__ y, int64_t N, const double *__restrict__ done) {
+  if (done && done[0] != 0.0) return;
+  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t row = gid / LPR;
+  int lane = threadIdx.x % LPR;
+  if (row >= N) return;
+  int64_t a = rowptr[row], b = rowptr[row + 1];
+  float acc = 0.f;
+  for (int64_t k = a + lane; k < b; k += LPR) acc = fmaf(val[k], x[col[k]], acc);
+#pragma unroll
+  for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, LPR);
+  if (lane == 0) y[row] = (double)acc;
+}
+
+__global__ void k_cvt_f32(const double *__restrict__ x, float *__restrict__ y, int64_t N, const double *__restrict__ done) {
+  if (done && done[0] != 0.0) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) y[i] = (float)x[i];
+}
+
 template <typename V>
 __global__ void k_diag_inv(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col, const V *__restrict__ val,
                            double *__restrict__ dinv, int64_t N) {
@@ -268,6 +292,16 @@ static int grid_for(int64_t N, int threads, int cap) {
   return (int)g;
 }
 
+// FP32-value operator product used by the mixed-precision Newton: x -> FP32 copy, FP32 SpMV
+static cudaError_t spmv_f32_launch(iga_s *h, const float *vals, const double *x, double *y, const double *done) {
+  int eg = (int)((h->N + 255) / 256);
+  if (eg > 608) eg = 608;
+  IGA_LAUNCH(h, KC_VEC, (k_cvt_f32<<<eg, 256, 0, h->stream>>>(x, h->z32, h->N, done)));
+  unsigned grid = (unsigned)((h->N * 8 + 255) / 256);
+  IGA_LAUNCH(h, KC_SPMV, (k_spmv_f32<8><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, h->z32, y, h->N, done)));
+  return cudaGetLastError();
+}
+
 template <typename V>
 static cudaError_t spmv_launch(iga_s *h, const V *vals, const double *x, double *y, const double *done) {
   // Few lanes per row: the cross-lane reduction costs log2(LPR) FP64 adds on every
@@ -335,7 +369,7 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
     if (total == 0) {
       cudaMemcpyAsync(Vb, b, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
     } else {
-      if (is_f32) spmv_launch<float>(h, (const float *)vals, x, tmp, nullptr);
+      if (is_f32) spmv_f32_launch(h, (const float *)vals, x, tmp, nullptr);
       else spmv_launch<double>(h, (const double *)vals, x, tmp, nullptr);
       IGA_LAUNCH(h, KC_VEC, (k_residual_vec<<<eg, 256, 0, h->stream>>>(b, tmp, Vb, N)));
     }
@@ -349,7 +383,7 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
       for (; j < jend; j++) {
         const double *done = gm + L.flags;
         double *Hj = gm + L.H + (size_t)j * (m + 1);
-        if (is_f32) spmv_launch<float>(h, (const float *)vals, z, w, done);
+        if (is_f32) spmv_f32_launch(h, (const float *)vals, z, w, done);
         else spmv_launch<double>(h, (const double *)vals, z, w, done);
         // classical Gram-Schmidt, applied twice
         dim3 gd(RED_BLOCKS, j + 1);

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_PKG, "lib", "libiga.so")
 
 IGA_OK, IGA_EINVAL, IGA_ENOMEM, IGA_ECUDA, IGA_ENOCONV, IGA_EDIVERGED, IGA_ETIMEOUT, IGA_ENAN = range(8)
 STATUS_NAMES = ["IGA_OK", "IGA_EINVAL", "IGA_ENOMEM", "IGA_ECUDA", "IGA_ENOCONV", "IGA_EDIVERGED", "IGA_ETIMEOUT", "IGA_ENAN"]
-IGA_FP64, IGA_JAC_TF32, IGA_JAC_BF16 = 0, 1, 2
+IGA_FP64, IGA_JAC_TF32, IGA_JAC_BF16, IGA_JAC_FP32 = 0, 1, 2, 3
 
 # every symbol include/iga.h declares
 EXPORTS = ["iga_create", "iga_set_boundary_value", "iga_set_lambda", "iga_get_pattern", "iga_form_residual",
@@ -23,7 +23,7 @@ EXPORTS = ["iga_create", "iga_set_boundary_value", "iga_set_lambda", "iga_get_pa
            "iga_last_error", "iga_profile_enable", "iga_profile_read", "iga_form_residual_noalloc"]
 
 KERNEL_CLASSES = ["geometry", "residual_element", "residual_gather", "q00", "jac_stage1", "jac_stage2", "jac_final",
-                  "spmv", "gs_orth", "gmres_scalar", "vector", "combine", "pattern"]
+                  "spmv", "gs_orth", "gmres_scalar", "vector", "combine", "pattern", "elem_tc", "elem_gather"]
 
 
 class IgaDesc(ctypes.Structure):

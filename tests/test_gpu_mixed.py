@@ -1,0 +1,135 @@
+"""Mixed-precision Jacobian (tensor-core element matrices, BF16/TF32 operands, FP32
+accumulation) against the FP64 oracle, and Newton steered by it.
+
+There is no exact value to pin a rounded Jacobian to ("parity unpinned"); the
+tests bound its relative Frobenius error by the operand precision (unit roundoff
+2^-9 for BF16, 2^-11 for TF32, amplified by the cancellation between the
+stiffness and reaction terms) and check what stays exact: the pattern, the
+Dirichlet identity rows and zero columns, determinism, and that Newton driven by
+it still reaches ||F||_2 <= 1e-10 on the FP64 residual.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1305_4452_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# relative Frobenius error bounds: ~10x the unit roundoff of the operand type
+FRO_TOL = {"bf16": 2e-2, "tf32": 5e-3}
+
+
+@pytest.fixture(scope="module")
+def I():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1305_4452_gb300 import build, iga
+    build.build()
+    O.build()
+    return iga
+
+
+def bc_all(dim):
+    return {(a, s): 0.0 for a in range(dim) for s in range(2)}
+
+
+def pair(I, dim, p, nel, lam, geom=None, kappa=False):
+    nel = [nel] * dim if np.isscalar(nel) else list(nel)
+    ctrl = weights = lk = None
+    if geom == "annulus":
+        knots, ctrl, weights = W.quarter_annulus(tuple(nel), p)
+    else:
+        knots = [W.uniform_open_knots(nel[d], p) for d in range(dim)]
+    n = [len(k) - p - 1 for k in knots]
+    if kappa:
+        lk = W.grf_log_kappa(n, p, nel, 7)
+    disc = I.Discretization(dim, p, knots=knots, ctrl=ctrl, weights=weights, lam=lam, log_kappa=lk, dirichlet=bc_all(dim))
+    prob = O.Problem(knots, [p] * dim, ctrl=ctrl, weights=weights, lam=lam, log_kappa=lk, dirichlet=bc_all(dim))
+    return disc, prob, n
+
+
+CASES = [(2, 2, 16, None, False), (2, 3, (9, 7), None, False), (2, 2, (12, 10), None, True),
+         (3, 2, (6, 5, 4), None, False), (3, 3, (5, 4, 4), "annulus", False), (3, 1, (5, 4, 3), None, False)]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "d%dp%d_%s_%s_%s" % c)
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_mixed_jacobian_error_and_exact_structure(I, case, prec):
+    dim, p, nel, geom, kappa = case
+    disc, prob, n = pair(I, dim, p, nel, 1.5, geom, kappa)
+    U0 = W.interior_field(n, seed=3, lo=-0.3, hi=0.3)
+    U = torch.tensor(U0, device="cuda")
+    code = I.IGA_JAC_BF16 if prec == "bf16" else I.IGA_JAC_TF32
+    Jm = disc.form_jacobian(U, prec=code)
+    Jm2 = disc.form_jacobian(U, prec=code)
+    assert torch.equal(Jm, Jm2)  # deterministic
+    Jm = Jm.double().cpu().numpy()
+    Jo = prob.jacobian(U0)
+    err = np.linalg.norm(Jm - Jo) / np.linalg.norm(Jo)
+    assert err < FRO_TOL[prec], err
+    # Dirichlet rows/columns are exact
+    rowptr, colidx = prob.pattern()
+    mask = prob.dirichlet_mask()
+    rows = np.repeat(np.arange(prob.N), np.diff(rowptr))
+    fixed = mask[rows] | mask[colidx]
+    assert np.array_equal(Jm[fixed], Jo[fixed])
+    disc.close()
+
+
+def test_tf32_more_accurate_than_bf16(I):
+    disc, prob, n = pair(I, 3, 2, (6, 5, 4), 2.0)
+    U0 = W.interior_field(n, seed=4)
+    U = torch.tensor(U0, device="cuda")
+    Jo = prob.jacobian(U0)
+    e = {}
+    for name, code in (("bf16", I.IGA_JAC_BF16), ("tf32", I.IGA_JAC_TF32)):
+        Jm = disc.form_jacobian(U, prec=code).double().cpu().numpy()
+        e[name] = np.linalg.norm(Jm - Jo) / np.linalg.norm(Jo)
+    assert e["tf32"] < e["bf16"]
+    disc.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_newton_with_mixed_jacobian_reaches_fp64_tolerance(I, prec):
+    for dim, p, nel, geom, lam in ((2, 2, 16, None, 1.0), (3, 3, (8, 8, 6), "annulus", 2.0), (2, 3, 32, None, 6.0)):
+        disc, prob, n = pair(I, dim, p, nel, lam, geom)
+        U = torch.zeros(disc.N, dtype=torch.float64, device="cuda")
+        o = I.newton_defaults()
+        o.jac = I.IGA_JAC_BF16 if prec == "bf16" else I.IGA_JAC_TF32
+        rep = disc.solve_newton(U, o)
+        assert rep.status == 0 and rep.fnorm <= 1e-10
+        assert np.linalg.norm(prob.residual(U.cpu().numpy())) <= 1.5e-10
+        disc.close()
+
+
+def test_mixed_rejects_unsupported_degree(I):
+    disc = I.Discretization(3, 4, nel=2, lam=1.0)
+    U = torch.zeros(disc.N, dtype=torch.float64, device="cuda")
+    with pytest.raises(I.IgaError) as ei:
+        disc.form_jacobian(U, prec=I.IGA_JAC_BF16)
+    assert ei.value.status == I.IGA_EINVAL
+    disc.close()
+
+
+@pytest.mark.parametrize("case", CASES[:5], ids=lambda c: "d%dp%d_%s_%s_%s" % c)
+def test_fp32_sum_factorised_jacobian(I, case):
+    # FP32 storage and arithmetic on the CUDA cores: error at the FP32 unit roundoff scale
+    dim, p, nel, geom, kappa = case
+    disc, prob, n = pair(I, dim, p, nel, 1.5, geom, kappa)
+    U0 = W.interior_field(n, seed=3, lo=-0.3, hi=0.3)
+    Jm = disc.form_jacobian(torch.tensor(U0, device="cuda"), prec=I.IGA_JAC_FP32).double().cpu().numpy()
+    Jo = prob.jacobian(U0)
+    assert np.linalg.norm(Jm - Jo) / np.linalg.norm(Jo) < 1e-5
+    disc.close()
+
+
+def test_newton_with_fp32_jacobian(I):
+    disc, prob, n = pair(I, 3, 3, (8, 8, 6), 2.0, "annulus")
+    U = torch.zeros(disc.N, dtype=torch.float64, device="cuda")
+    o = I.newton_defaults()
+    o.jac = I.IGA_JAC_FP32
+    rep = disc.solve_newton(U, o)
+    assert rep.status == 0 and rep.fnorm <= 1e-10
+    disc.close()
