@@ -154,7 +154,12 @@ typedef struct {
   iga_precision jac;   /* Jacobian precision used to steer Newton (default IGA_FP64) */
   int reuse_stiffness; /* 1: assemble the U-independent part of J once per solve and add
                           the reaction term each step (default 1); 0: full assembly each step */
+  int ksp;             /* Krylov method: IGA_KSP_GMRES (default) or IGA_KSP_CG (Jacobi-
+                          preconditioned conjugate gradients, the -ksp_type cg run of App. B;
+                          valid because the Jacobian with symmetric Dirichlet rows is symmetric) */
 } iga_newton_opts;
+#define IGA_KSP_GMRES 0
+#define IGA_KSP_CG 1
 
 typedef struct {
   int newton_its;         /* Newton steps taken */
@@ -179,6 +184,43 @@ iga_status iga_solve_newton(iga_t iga, double *U, const iga_newton_opts *opts,
  * copies the solution back. */
 iga_status iga_solve_newton_host(iga_t iga, double *U_host, const iga_newton_opts *opts,
                                  iga_newton_report *report);
+
+/* ---- Batched solves: many independent 2D problems in one persistent launch ----
+ * Each instance i is a 2D Bratu problem described by descs[i] (dim 2, identity
+ * map: ctrl = weights = NULL, equal degree 1..3 and equal knot vectors in both
+ * directions; knots or nel/continuity as for iga_create) and params[i] (lambda,
+ * optional host log-kappa of the instance's N_i control variables), with
+ * homogeneous Dirichlet values on all four sides.  Instances with identical
+ * descriptions share their tables and CSR pattern.  The paper solves one problem
+ * per SNESSolve; the batch is this library's extension for many small problems.
+ * iga_batch_create allocates every device buffer (cudaMalloc) and the work
+ * arenas; its stream argument is unused (the batch runs on an internal stream). */
+typedef struct iga_batch_s *iga_batch_t;
+typedef struct {
+  int solved;       /* instances that reached ||F|| <= atol */
+  int *newton_its;  /* host arrays of length count, or NULL */
+  int *krylov_its;
+  double *fnorm;
+  int *status;      /* iga_status per instance */
+} iga_batch_report;
+iga_status iga_batch_create(int count, const iga_desc *descs, const iga_bratu *params, void *stream,
+                            iga_batch_t *out);
+/* offsets[count+1]: instance i owns U[offsets[i] .. offsets[i+1]) of the
+ * concatenated solution array (natural order within an instance). */
+iga_status iga_batch_offsets(iga_batch_t batch, int64_t *offsets);
+/* Launch shape of the persistent kernel: CTAs per SM (256 threads each); the
+ * autotuner in paper_1305_4452_gb300/autotune.py chooses it. */
+iga_status iga_batch_set_launch(iga_batch_t batch, int ctas_per_sm);
+/* Solve every instance from the initial values in U (device, concatenated,
+ * in/out) with Newton + GMRES(m, at most 64) + Jacobi, FP64 residual and norms,
+ * FP32 sum-factorised Jacobian.  One graph launch (captured on the first call
+ * and replayed): argument copy, work-counter reset, the persistent kernel (each
+ * CTA takes the next instance, largest first, until none is left) and the
+ * report copy.  Synchronises the device.  Returns IGA_OK when every instance
+ * converged, IGA_ENOCONV otherwise (see report->status). */
+iga_status iga_batch_solve(iga_batch_t batch, double *U, const iga_newton_opts *opts, iga_batch_report *report);
+void iga_batch_destroy(iga_batch_t batch);
+const char *iga_batch_last_error(iga_batch_t batch);
 
 /* Per-kernel-class launch counts and device times (the tracing facility; the
  * paper's -snes_monitor / -log_view analogue).  Classes, in order:

@@ -262,6 +262,7 @@ extern "C" void iga_newton_defaults(iga_newton_opts *o) {
   o->krylov_rtol = 1e-2;
   o->jac = IGA_FP64;
   o->reuse_stiffness = 1;
+  o->ksp = IGA_KSP_GMRES;
 }
 
 // ---- small vector kernels of the Newton driver ----
@@ -379,8 +380,9 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
     if (tol_abs < 1e-14 * fn) tol_abs = 1e-14 * fn;
     int its = 0;
     cudaError_t ce = cudaSuccess;
-    int grc = gmres_solve(h, f32 ? (const void *)h->J32 : (const void *)h->J64, f32, Ft, dU, tol_abs,
-                          o.gmres_restart, o.max_krylov, &its, &ce);
+    const void *Jv = f32 ? (const void *)h->J32 : (const void *)h->J64;
+    int grc = (o.ksp == IGA_KSP_CG) ? cg_solve(h, Jv, f32, Ft, dU, tol_abs, o.max_krylov, &its, &ce)
+                                    : gmres_solve(h, Jv, f32, Ft, dU, tol_abs, o.gmres_restart, o.max_krylov, &its, &ce);
     if (grc < 0) {
       h->err = iga_format("GMRES: %s", cudaGetErrorString(ce));
       return IGA_ECUDA;

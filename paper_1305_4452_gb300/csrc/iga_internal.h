@@ -194,6 +194,8 @@ cudaError_t launch_spmv32(iga_s *h, const float *vals, const double *x, double *
 cudaError_t launch_diag_inv(iga_s *h, const void *vals, int is_f32, double *dinv);
 cudaError_t launch_norm2(iga_s *h, const double *x, double *out_dev);
 cudaError_t launch_nan_check(iga_s *h, const double *x, double *out_dev);
+int cg_solve(iga_s *h, const void *vals, int is_f32, const double *b, double *x, double tol_abs, int maxit, int *its,
+             cudaError_t *cerr);
 int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double *x, double rtol_abs,
                 int m, int maxit, int *its, cudaError_t *cerr);
 

@@ -420,3 +420,149 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
   *its = total;
   return rc;
 }
+
+// ---------------------------------------------------------------------------
+// Jacobi-preconditioned conjugate gradients (the -ksp_type cg solve of App. B).
+// Scalars live on the device (layout below); every kernel after convergence
+// returns at once, so the host synchronises only every few iterations.
+// ---------------------------------------------------------------------------
+namespace {
+enum { CG_DONE = 0, CG_ITS, CG_RZ, CG_RR, CG_PQ, CG_ALPHA, CG_BETA, CG_RZ2, CG_RR2, CG_BRK, CG_NS };
+
+__global__ void __launch_bounds__(RED_THREADS) k_cg_init(const double *__restrict__ b, const double *__restrict__ dinv,
+                                                         double *__restrict__ x, double *__restrict__ r, double *__restrict__ p,
+                                                         double *__restrict__ partial, int64_t N) {
+  __shared__ double sh[32];
+  int64_t per = (N + gridDim.x - 1) / gridDim.x;
+  int64_t a = blockIdx.x * per, e = min(N, a + per);
+  double rz = 0.0, rr = 0.0;
+  for (int64_t i = a + threadIdx.x; i < e; i += blockDim.x) {
+    double bi = b[i], pi = dinv[i] * bi;
+    x[i] = 0.0;
+    r[i] = bi;
+    p[i] = pi;
+    rz = fma(bi, pi, rz);
+    rr = fma(bi, bi, rr);
+  }
+  rz = block_sum(rz, sh);
+  rr = block_sum(rr, sh);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = rz;
+    partial[2 * blockIdx.x + 1] = rr;
+  }
+}
+
+// out[0], out[1] = column sums of partial[nb][2] in index order (one block)
+__global__ void __launch_bounds__(RED_THREADS) k_reduce2(const double *__restrict__ partial, int nb, double *__restrict__ out0,
+                                                         double *__restrict__ out1, const double *__restrict__ done) {
+  __shared__ double sh[32];
+  if (done && done[0] != 0.0) return;
+  double a = 0.0, c = 0.0;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+    a += partial[2 * k];
+    c += partial[2 * k + 1];
+  }
+  a = block_sum(a, sh);
+  c = block_sum(c, sh);
+  if (threadIdx.x == 0) {
+    *out0 = a;
+    *out1 = c;
+  }
+}
+
+__global__ void k_cg_check0(double *s, double tol) {
+  for (int k = 0; k < CG_NS; k++)
+    if (k != CG_RZ && k != CG_RR) s[k] = 0.0;
+  if (!isfinite(s[CG_RR])) { s[CG_DONE] = 1.0; s[CG_BRK] = 1.0; }
+  else if (!(sqrt(s[CG_RR]) > tol)) s[CG_DONE] = 1.0;
+}
+
+__global__ void k_cg_alpha(double *s) {
+  if (s[CG_DONE] != 0.0) return;
+  double pq = s[CG_PQ];
+  if (!(pq > 0.0) || !isfinite(pq)) { s[CG_DONE] = 1.0; s[CG_BRK] = 1.0; return; }
+  s[CG_ALPHA] = s[CG_RZ] / pq;
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_cg_xr(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+                                                       const double *__restrict__ q, const double *__restrict__ dinv,
+                                                       const double *__restrict__ s, double *__restrict__ partial, int64_t N) {
+  __shared__ double sh[32];
+  if (s[CG_DONE] != 0.0) return;
+  const double alpha = s[CG_ALPHA];
+  int64_t per = (N + gridDim.x - 1) / gridDim.x;
+  int64_t a = blockIdx.x * per, e = min(N, a + per);
+  double rr = 0.0, rz = 0.0;
+  for (int64_t i = a + threadIdx.x; i < e; i += blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    double ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    rr = fma(ri, ri, rr);
+    rz = fma(ri, dinv[i] * ri, rz);
+  }
+  rz = block_sum(rz, sh);
+  rr = block_sum(rr, sh);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = rz;
+    partial[2 * blockIdx.x + 1] = rr;
+  }
+}
+
+__global__ void k_cg_beta(double *s, double tol) {
+  if (s[CG_DONE] != 0.0) return;
+  s[CG_ITS] += 1.0;
+  double rr = s[CG_RR2];
+  if (!isfinite(rr)) { s[CG_DONE] = 1.0; s[CG_BRK] = 1.0; return; }
+  s[CG_RR] = rr;
+  if (sqrt(rr) <= tol) { s[CG_DONE] = 1.0; return; }
+  s[CG_BETA] = s[CG_RZ2] / s[CG_RZ];
+  s[CG_RZ] = s[CG_RZ2];
+}
+
+__global__ void k_cg_p(double *__restrict__ p, const double *__restrict__ r, const double *__restrict__ dinv,
+                       const double *__restrict__ s, int64_t N) {
+  if (s[CG_DONE] != 0.0) return;
+  const double beta = s[CG_BETA];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], dinv[i] * r[i]);
+}
+}  // namespace
+
+// Returns 0 on convergence, 1 when the cap was hit, 2 on breakdown/NaN, -1 on a CUDA error.
+int cg_solve(iga_s *h, const void *vals, int is_f32, const double *b, double *x, double tol_abs, int maxit, int *its,
+             cudaError_t *cerr) {
+  const int64_t N = h->N;
+  double *s = h->ctl;
+  double *dinv = h->wk + 4 * N, *r = h->wk + 5 * N, *p = h->wk + 6 * N, *q = h->wk + 7 * N;
+  int eg = grid_for(N, 256, 4 * 152);
+  *cerr = cudaSuccess;
+  launch_diag_inv(h, vals, is_f32, dinv);
+  IGA_LAUNCH(h, KC_VEC, (k_cg_init<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(b, dinv, x, r, p, h->red, N)));
+  IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce2<<<1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, s + CG_RZ, s + CG_RR, nullptr)));
+  IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_cg_check0<<<1, 1, 0, h->stream>>>(s, tol_abs)));
+  const double *done = s + CG_DONE;
+  const int batch = 16;
+  int enq = 0;
+  while (enq < maxit) {
+    for (int k = 0; k < batch && enq < maxit; k++, enq++) {
+      if (is_f32) spmv_f32_launch(h, (const float *)vals, p, q, done);
+      else spmv_launch<double>(h, (const double *)vals, p, q, done);
+      IGA_LAUNCH(h, KC_VEC, (k_dot_partial<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(p, q, h->red, N, done)));
+      IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce_rows<<<1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, s + CG_PQ, 0, done)));
+      IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_cg_alpha<<<1, 1, 0, h->stream>>>(s)));
+      IGA_LAUNCH(h, KC_VEC, (k_cg_xr<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(x, r, p, q, dinv, s, h->red, N)));
+      IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce2<<<1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, s + CG_RZ2, s + CG_RR2, done)));
+      IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_cg_beta<<<1, 1, 0, h->stream>>>(s, tol_abs)));
+      IGA_LAUNCH(h, KC_VEC, (k_cg_p<<<eg, 256, 0, h->stream>>>(p, r, dinv, s, N)));
+    }
+    cudaMemcpyAsync(h->ctl_host, s, CG_NS * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    cudaError_t ce = cudaStreamSynchronize(h->stream);
+    if (ce) { *cerr = ce; return -1; }
+    if (h->ctl_host[CG_DONE] != 0.0) break;
+  }
+  cudaError_t ce = cudaGetLastError();
+  if (ce) { *cerr = ce; return -1; }
+  *its = (int)h->ctl_host[CG_ITS];
+  if (h->ctl_host[CG_BRK] != 0.0) return 2;
+  return h->ctl_host[CG_DONE] != 0.0 ? 0 : 1;
+}

@@ -20,7 +20,9 @@ IGA_FP64, IGA_JAC_TF32, IGA_JAC_BF16, IGA_JAC_FP32 = 0, 1, 2, 3
 # every symbol include/iga.h declares
 EXPORTS = ["iga_create", "iga_set_boundary_value", "iga_set_lambda", "iga_get_pattern", "iga_form_residual",
            "iga_form_jacobian", "iga_newton_defaults", "iga_solve_newton", "iga_solve_newton_host", "iga_destroy",
-           "iga_last_error", "iga_profile_enable", "iga_profile_read", "iga_form_residual_noalloc"]
+           "iga_last_error", "iga_profile_enable", "iga_profile_read", "iga_form_residual_noalloc",
+           "iga_batch_create", "iga_batch_offsets", "iga_batch_set_launch", "iga_batch_solve", "iga_batch_destroy",
+           "iga_batch_last_error"]
 
 KERNEL_CLASSES = ["geometry", "residual_element", "residual_gather", "q00", "jac_stage1", "jac_stage2", "jac_final",
                   "spmv", "gs_orth", "gmres_scalar", "vector", "combine", "pattern", "elem_tc", "elem_gather"]
@@ -53,7 +55,11 @@ class IgaNewtonOpts(ctypes.Structure):
         ("krylov_rtol", ctypes.c_double),
         ("jac", ctypes.c_int),
         ("reuse_stiffness", ctypes.c_int),
+        ("ksp", ctypes.c_int),
     ]
+
+
+IGA_KSP_GMRES, IGA_KSP_CG = 0, 1
 
 
 class IgaNewtonReport(ctypes.Structure):
@@ -255,3 +261,102 @@ def _wrap_device(ptr, n, dtype):
     typestr = {torch.int64: "<i8", torch.int32: "<i4", torch.float64: "<f8", torch.float32: "<f4"}[dtype]
     a.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 2}
     return torch.as_tensor(a, device="cuda")
+
+
+# ------------------------------------------------------------------ batched ---
+class IgaBatchReport(ctypes.Structure):
+    _fields_ = [("solved", ctypes.c_int), ("newton_its", ctypes.c_void_p), ("krylov_its", ctypes.c_void_p),
+                ("fnorm", ctypes.c_void_p), ("status", ctypes.c_void_p)]
+
+
+def _batch_lib():
+    L = lib()
+    if not getattr(L, "_batch_ready", False):
+        vp = ctypes.c_void_p
+        L.iga_batch_create.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.POINTER(vp)]
+        L.iga_batch_offsets.argtypes = [vp, vp]
+        L.iga_batch_set_launch.argtypes = [vp, ctypes.c_int]
+        L.iga_batch_solve.argtypes = [vp, vp, ctypes.POINTER(IgaNewtonOpts), ctypes.POINTER(IgaBatchReport)]
+        L.iga_batch_destroy.argtypes = [vp]
+        L.iga_batch_destroy.restype = None
+        L.iga_batch_last_error.argtypes = [vp]
+        L.iga_batch_last_error.restype = ctypes.c_char_p
+        L._batch_ready = True
+    return L
+
+
+class Batch:
+    """iga_batch_t: many independent 2D problems solved in one persistent launch.
+
+    instances: list of dicts {"nel": int or (n0, n1), "p": int, "lam": float,
+    optional "knots": [U0, U1], "log_kappa": array}.
+    """
+
+    def __init__(self, instances):
+        L = _batch_lib()
+        n = len(instances)
+        descs = (IgaDesc * n)()
+        params = (IgaBratu * n)()
+        self._keep = []
+        for i, ins in enumerate(instances):
+            d = descs[i]
+            d.dim = 2
+            nel = ins.get("nel")
+            for ax in range(2):
+                d.degree[ax] = int(ins["p"])
+                d.continuity[ax] = -1
+                if ins.get("knots") is not None:
+                    k = _f64(ins["knots"][ax])
+                    self._keep.append(k)
+                    d.knots[ax] = k.ctypes.data
+                    d.nknots[ax] = len(k)
+                else:
+                    d.nel[ax] = int(nel if np.isscalar(nel) else nel[ax])
+            lk = ins.get("log_kappa")
+            if lk is not None:
+                lk = _f64(lk)
+                self._keep.append(lk)
+            params[i].lam = float(ins["lam"])
+            params[i].log_kappa = None if lk is None else lk.ctypes.data
+        h = ctypes.c_void_p()
+        rc = L.iga_batch_create(n, ctypes.addressof(descs), ctypes.addressof(params), None, ctypes.byref(h))
+        if rc != IGA_OK:
+            raise IgaError(rc, L.iga_batch_last_error(None).decode())
+        self.h = h
+        self.count = n
+        off = np.zeros(n + 1, dtype=np.int64)
+        L.iga_batch_offsets(self.h, off.ctypes.data)
+        self.offsets = off
+        self.total = int(off[-1])
+
+    def set_launch(self, ctas_per_sm):
+        L = _batch_lib()
+        rc = L.iga_batch_set_launch(self.h, int(ctas_per_sm))
+        if rc != IGA_OK:
+            raise IgaError(rc, L.iga_batch_last_error(self.h).decode())
+
+    def solve(self, U, opts=None, check=True):
+        """U: torch CUDA float64 tensor of length self.total (in/out).  Returns a dict
+        of per-instance arrays (newton_its, krylov_its, fnorm, status) and 'solved'."""
+        L = _batch_lib()
+        o = opts if opts is not None else newton_defaults()
+        nit = np.zeros(self.count, dtype=np.int32)
+        kit = np.zeros(self.count, dtype=np.int32)
+        fn = np.zeros(self.count)
+        st = np.zeros(self.count, dtype=np.int32)
+        r = IgaBatchReport(0, nit.ctypes.data, kit.ctypes.data, fn.ctypes.data, st.ctypes.data)
+        rc = L.iga_batch_solve(self.h, ctypes.c_void_p(U.data_ptr()), ctypes.byref(o), ctypes.byref(r))
+        if check and rc != IGA_OK:
+            raise IgaError(rc, L.iga_batch_last_error(self.h).decode())
+        return {"solved": r.solved, "newton_its": nit, "krylov_its": kit, "fnorm": fn, "status": st, "rc": rc}
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _batch_lib().iga_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

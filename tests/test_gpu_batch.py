@@ -1,0 +1,119 @@
+"""Batched solver (one persistent, graph-captured launch for many 2D instances)
+against the oracle and the single-problem solver."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1305_4452_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def I():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1305_4452_gb300 import build, iga
+    build.build()
+    O.build()
+    return iga
+
+
+BC = {(a, s): 0.0 for a in range(2) for s in range(2)}
+
+
+def instances(count, seed, nmin=6, nmax=24, kappa_every=0):
+    out = W.batch_instances(count, seed=seed, nmin=nmin, nmax=nmax, lam=(0.5, 6.0))
+    for i, ins in enumerate(out):
+        if kappa_every and i % kappa_every == 0:
+            n = ins["nel"] + ins["p"]
+            ins["log_kappa"] = W.grf_log_kappa([n, n], ins["p"], [ins["nel"]] * 2, 100 + i)
+            # a low-kappa field lowers the fold: keep lambda where these draws have a solution
+            ins["lam"] = 0.5 + (ins["lam"] - 0.5) * (2.5 / 5.5)
+    return out
+
+
+def oracle_problem(ins):
+    U = O.open_uniform_knots(ins["nel"], ins["p"])
+    return O.Problem([U, U], [ins["p"]] * 2, lam=ins["lam"], log_kappa=ins.get("log_kappa"), dirichlet=BC)
+
+
+@pytest.mark.parametrize("ctas", [1, 2])
+def test_batch_solves_every_instance_to_tolerance(I, ctas):
+    ins = instances(24, seed=3, kappa_every=4)
+    b = I.Batch(ins)
+    b.set_launch(ctas)
+    U = torch.zeros(b.total, dtype=torch.float64, device="cuda")
+    rep = b.solve(U)
+    assert rep["solved"] == len(ins)
+    assert np.all(rep["fnorm"] <= 1e-10)
+    Uh = U.cpu().numpy()
+    for i, x in enumerate(ins):
+        Ui = Uh[b.offsets[i]:b.offsets[i + 1]]
+        F = oracle_problem(x).residual(Ui)
+        assert np.linalg.norm(F) <= 1.5e-10, (i, np.linalg.norm(F))
+    b.close()
+
+
+def test_batch_matches_single_problem_solver(I):
+    ins = instances(8, seed=5)
+    b = I.Batch(ins)
+    U = torch.zeros(b.total, dtype=torch.float64, device="cuda")
+    b.solve(U)
+    for i, x in enumerate(ins):
+        d = I.Discretization(2, x["p"], nel=x["nel"], lam=x["lam"], dirichlet=BC)
+        Us = torch.zeros(d.N, dtype=torch.float64, device="cuda")
+        d.solve_newton(Us)
+        Ub = U[b.offsets[i]:b.offsets[i + 1]]
+        # both at ||F|| <= 1e-10 on the same (lower) branch
+        assert torch.abs(Ub - Us).max().item() <= 1e-7 * max(1.0, torch.abs(Us).max().item())
+        d.close()
+    b.close()
+
+
+def test_batch_is_deterministic_and_replays(I):
+    ins = instances(10, seed=7)
+    b = I.Batch(ins)
+    U1 = torch.zeros(b.total, dtype=torch.float64, device="cuda")
+    U2 = torch.zeros_like(U1)
+    r1 = b.solve(U1)
+    r2 = b.solve(U2)  # second call replays the captured graph
+    assert torch.equal(U1, U2)
+    assert np.array_equal(r1["krylov_its"], r2["krylov_its"])
+    b.close()
+
+
+def test_batch_reports_failing_instances_and_finishes_the_rest(I):
+    ins = instances(6, seed=9)
+    ins[2]["lam"] = 7.5  # above lambda_max: no solution
+    b = I.Batch(ins)
+    U = torch.zeros(b.total, dtype=torch.float64, device="cuda")
+    o = I.newton_defaults()
+    o.max_newton = 20
+    rep = b.solve(U, o, check=False)
+    assert rep["rc"] == I.IGA_ENOCONV and rep["solved"] == 5
+    assert rep["status"][2] in (I.IGA_ENOCONV, I.IGA_EDIVERGED)
+    assert all(rep["status"][i] == 0 for i in range(6) if i != 2)
+    assert rep["newton_its"][2] <= 20
+    b.close()
+
+
+def test_batch_rejects_3d_and_mapped_instances(I):
+    from paper_1305_4452_gb300.iga import IgaError
+    with pytest.raises(IgaError):
+        I.Batch([{"nel": 4, "p": 4, "lam": 1.0}])
+
+
+def test_batch_cg_matches_gmres(I):
+    ins = instances(12, seed=11, kappa_every=3)
+    b = I.Batch(ins)
+    Ug = torch.zeros(b.total, dtype=torch.float64, device="cuda")
+    Uc = torch.zeros_like(Ug)
+    b.solve(Ug)
+    o = I.newton_defaults()
+    o.ksp = I.IGA_KSP_CG
+    rep = b.solve(Uc, o)
+    assert rep["solved"] == len(ins)
+    assert torch.abs(Ug - Uc).max().item() <= 1e-7
+    b.close()

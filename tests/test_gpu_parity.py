@@ -224,3 +224,20 @@ def test_full_size_cube_128_cubed_sampled():
     Jg = np.concatenate([J[rpo[r]:rpo[r + 1]].cpu().numpy() for r in rows])
     assert np.abs(Jg - prob.jacobian_rows(U0, rows)).max() <= TOL * torch.abs(J).max().item()
     disc.close()
+
+
+@pytest.mark.parametrize("jac", ["fp64", "fp32"])
+def test_newton_cg_matches_gmres_solution(jac):
+    I = iga()
+    disc, prob, n = make_pair(3, 3, (8, 8, 6), lam=2.0, geom="annulus")
+    o = I.newton_defaults()
+    o.jac = I.IGA_FP64 if jac == "fp64" else I.IGA_JAC_FP32
+    Ug = torch.zeros(disc.N, dtype=torch.float64, device="cuda")
+    disc.solve_newton(Ug, o)
+    o.ksp = I.IGA_KSP_CG
+    Uc = torch.zeros_like(Ug)
+    rep = disc.solve_newton(Uc, o)
+    assert rep.status == 0 and rep.fnorm <= 1e-10
+    assert torch.abs(Ug - Uc).max().item() <= 1e-8
+    assert np.linalg.norm(prob.residual(Uc.cpu().numpy())) <= 1.5e-10
+    disc.close()
