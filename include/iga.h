@@ -222,6 +222,32 @@ iga_status iga_batch_solve(iga_batch_t batch, double *U, const iga_newton_opts *
 void iga_batch_destroy(iga_batch_t batch);
 const char *iga_batch_last_error(iga_batch_t batch);
 
+/* ---- Learned initial guess: a convolutional neural operator (not in the paper) ----
+ * An L-layer network of 3x3 convolutions (dilation dilations[l], zero padding) on
+ * an height x width grid, in_channels inputs per grid point, `hidden` channels
+ * between layers, SiLU activations and one linear output channel multiplied by a
+ * mask.  Forward, input- and weight-gradient convolutions run as BF16 x BF16 ->
+ * FP32 tensor-core GEMMs; master weights, gradients, Adam moments and the loss are
+ * FP32.  Parameters: a flat FP32 vector, per layer W[cout][3][3][cin] then
+ * b[cout].  Inputs are NHWC FP32 device arrays; batch size <= max_batch.
+ * iga_nn_create allocates all device memory; weights are He-uniform from `seed`. */
+typedef struct iga_nn_s *iga_nn_t;
+iga_status iga_nn_create(int height, int width, int in_channels, int hidden, int layers, const int *dilations,
+                         int max_batch, uint64_t seed, void *stream, iga_nn_t *out);
+iga_status iga_nn_num_params(iga_nn_t nn, int64_t *count);
+iga_status iga_nn_get_params(iga_nn_t nn, float *host);        /* host float[count] */
+iga_status iga_nn_set_params(iga_nn_t nn, const float *host);  /* also resets Adam */
+/* y[B][H][W] = mask * net(x); x: device float[B][H][W][in_channels]; mask: device float[H][W] or NULL */
+iga_status iga_nn_forward(iga_nn_t nn, const float *x, int B, const float *mask, float *y);
+/* forward + backward of the masked mean-squared error against tgt[B][H][W]; *loss
+ * (host) gets the loss; grads_out (device float[count]) gets the gradient if non-NULL */
+iga_status iga_nn_loss_grad(iga_nn_t nn, const float *x, const float *tgt, const float *mask, int B, float *loss,
+                            float *grads_out);
+/* one Adam update with the gradient of the last iga_nn_loss_grad */
+iga_status iga_nn_adam_step(iga_nn_t nn, float lr, float beta1, float beta2, float eps);
+void iga_nn_destroy(iga_nn_t nn);
+const char *iga_nn_last_error(iga_nn_t nn);
+
 /* Per-kernel-class launch counts and device times (the tracing facility; the
  * paper's -snes_monitor / -log_view analogue).  Classes, in order:
  *   0 geometry factors, 1 residual element kernel, 2 residual gather, 3 Q00 /

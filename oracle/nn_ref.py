@@ -1,0 +1,86 @@
+"""CPU FP64 reference of the convolutional neural operator (TEST INFRASTRUCTURE).
+
+Plain numpy: zero-padded dilated 3x3 convolutions written as nine shifted
+channel contractions, SiLU, a masked mean-squared error, and the backward pass
+written out by hand (chain rule per layer).  Parameters use the flat layout of
+the CUDA network: per layer W[cout][3][3][cin] then b[cout].  Never imported by
+the product path.
+"""
+import numpy as np
+
+
+def layer_shapes(in_channels, hidden, dilations):
+    out, off = [], 0
+    L = len(dilations)
+    for l, d in enumerate(dilations):
+        cin = in_channels if l == 0 else hidden
+        cout = 1 if l == L - 1 else hidden
+        woff = off
+        off += cout * 9 * cin
+        out.append((cin, cout, d, woff, off))
+        off += cout
+    return out, off
+
+
+def _shift(xp, d, ky, kx, H, W):
+    return xp[:, d * ky:d * ky + H, d * kx:d * kx + W, :]
+
+
+def conv(x, Wt, d):
+    """out[b,y,x,o] = sum_{ky,kx,c} Wt[o,ky,kx,c] x[b, y+d(ky-1), x+d(kx-1), c], zero outside."""
+    B, H, W, C = x.shape
+    xp = np.pad(x, ((0, 0), (d, d), (d, d), (0, 0)))
+    out = np.zeros((B, H, W, Wt.shape[0]))
+    for ky in range(3):
+        for kx in range(3):
+            out += np.einsum("bhwc,oc->bhwo", _shift(xp, d, ky, kx, H, W), Wt[:, ky, kx, :])
+    return out
+
+
+def silu(z):
+    return z / (1.0 + np.exp(-z))
+
+
+def dsilu(z):
+    s = 1.0 / (1.0 + np.exp(-z))
+    return s * (1.0 + z * (1.0 - s))
+
+
+def forward(params, shapes, x, mask):
+    acts, zs = [x], []
+    for l, (cin, cout, d, woff, boff) in enumerate(shapes):
+        Wt = params[woff:boff].reshape(cout, 3, 3, cin)
+        z = conv(acts[-1], Wt, d) + params[boff:boff + cout]
+        zs.append(z)
+        if l + 1 < len(shapes):
+            acts.append(silu(z))
+    y = mask[None] * zs[-1][..., 0]
+    return y, acts, zs
+
+
+def loss_and_grad(params, shapes, x, tgt, mask):
+    """Masked mean-squared error and its gradient with respect to params."""
+    y, acts, zs = forward(params, shapes, x, mask)
+    m = mask[None] * np.ones_like(tgt)
+    count = max(m.sum(), 1.0)
+    loss = float((m * (y - tgt) ** 2).sum() / count)
+    grad = np.zeros_like(params)
+    dz = (2.0 * m * (y - tgt) / count)[..., None]  # dL/dz of the last layer (mask is 0/1)
+    for l in range(len(shapes) - 1, -1, -1):
+        cin, cout, d, woff, boff = shapes[l]
+        if l < len(shapes) - 1:
+            dz = da * dsilu(zs[l])
+        xin = acts[l]
+        B, H, W, C = xin.shape
+        xp = np.pad(xin, ((0, 0), (d, d), (d, d), (0, 0)))
+        Wt = params[woff:boff].reshape(cout, 3, 3, cin)
+        gW = np.zeros((cout, 3, 3, cin))
+        dxp = np.zeros_like(xp)
+        for ky in range(3):
+            for kx in range(3):
+                gW[:, ky, kx, :] = np.einsum("bhwo,bhwc->oc", dz, _shift(xp, d, ky, kx, H, W))
+                dxp[:, d * ky:d * ky + H, d * kx:d * kx + W, :] += np.einsum("bhwo,oc->bhwc", dz, Wt[:, ky, kx, :])
+        grad[woff:boff] = gW.reshape(-1)
+        grad[boff:boff + cout] = dz.sum(axis=(0, 1, 2))
+        da = dxp[:, d:d + H, d:d + W, :]
+    return loss, grad

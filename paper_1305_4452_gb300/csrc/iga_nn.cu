@@ -1,0 +1,540 @@
+// Convolutional neural operator for Newton initial guesses (hand-written training
+// and inference kernels).  Not in the paper: it maps (lambda, log-kappa field) on
+// the control grid to an initial U for the kappa-weighted Bratu problem.
+//
+// Network: L layers of 3x3 convolutions with per-layer dilation and "same" zero
+// padding on an H x W grid (NHWC activations), SiLU between layers, a linear last
+// layer with one output channel, multiplied by a mask (zero on Dirichlet rows).
+// Every convolution -- forward, input gradient and weight gradient -- is an
+// explicit im2col (or its transpose) plus one dense GEMM on the tensor cores
+// (mma.sync m16n8k16, BF16 operands, FP32 accumulation).  Master weights, Adam
+// moments, gradients and the loss are FP32; activations are stored in BF16 for
+// the GEMMs and FP32 where the backward pass needs them.  Every reduction
+// (split-K weight gradients, bias gradients, loss) has a fixed order.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "iga_internal.h"
+
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+constexpr int GBM = 128, GBN = 64, GBK = 32, GLD = GBK + 8;
+
+// C[M][N] (+)= sum_k A(m,k) B(k,n).  A: row-major [M][K] (A_COL = false) or [K][M];
+// B: [N][K] (B_KN = false) or [K][N].  blockIdx.z selects a K chunk whose result
+// goes to C + z * split_stride (split-K); bias (if any) is added by chunk 0.
+template <bool A_COL, bool B_KN>
+__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const bf16 *__restrict__ A, int64_t lda,
+                                              const bf16 *__restrict__ B, int64_t ldb, float *__restrict__ C, int64_t ldc,
+                                              int64_t split_stride, int kchunk, const float *__restrict__ bias) {
+  __shared__ __align__(16) bf16 As[GBM][GLD];
+  __shared__ __align__(16) bf16 Bs[GBN][GLD];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m0 = blockIdx.x * GBM, n0 = blockIdx.y * GBN;
+  const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+  const int wm = (warp & 3) * 32, wn = (warp >> 2) * 32;
+  const int g = lane >> 2, t = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
+  const bf16 zero = __float2bfloat16(0.f);
+  for (int k0 = kbeg; k0 < kend; k0 += GBK) {
+    for (int idx = tid; idx < GBM * GBK; idx += 256) {
+      int r, kk;
+      if (!A_COL) { r = idx / GBK; kk = idx % GBK; } else { kk = idx / GBM; r = idx % GBM; }
+      const int gm = m0 + r, gk = k0 + kk;
+      bf16 v = zero;
+      if (gm < M && gk < kend) v = A_COL ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
+      As[r][kk] = v;
+    }
+    for (int idx = tid; idx < GBN * GBK; idx += 256) {
+      int r, kk;
+      if (!B_KN) { r = idx / GBK; kk = idx % GBK; } else { kk = idx / GBN; r = idx % GBN; }
+      const int gn = n0 + r, gk = k0 + kk;
+      bf16 v = zero;
+      if (gn < N && gk < kend) v = B_KN ? B[(int64_t)gk * ldb + gn] : B[(int64_t)gn * ldb + gk];
+      Bs[r][kk] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < GBK; ks += 16) {
+      uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; i++) {
+        const bf16 *r0 = &As[wm + i * 16 + g][ks + 2 * t];
+        const bf16 *r1 = &As[wm + i * 16 + g + 8][ks + 2 * t];
+        af[i][0] = *reinterpret_cast<const uint32_t *>(r0);
+        af[i][1] = *reinterpret_cast<const uint32_t *>(r1);
+        af[i][2] = *reinterpret_cast<const uint32_t *>(r0 + 8);
+        af[i][3] = *reinterpret_cast<const uint32_t *>(r1 + 8);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const bf16 *c0 = &Bs[wn + j * 8 + g][ks + 2 * t];
+        bfr[j][0] = *reinterpret_cast<const uint32_t *>(c0);
+        bfr[j][1] = *reinterpret_cast<const uint32_t *>(c0 + 8);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+              : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+              : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bfr[j][0]), "r"(bfr[j][1]));
+    }
+    __syncthreads();
+  }
+  float *Cz = C + (int64_t)blockIdx.z * split_stride;
+#pragma unroll
+  for (int i = 0; i < 2; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int row = m0 + wm + i * 16 + g, col = n0 + wn + j * 8 + 2 * t;
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int rr = row + 8 * h;
+        if (rr >= M) continue;
+#pragma unroll
+        for (int cc = 0; cc < 2; cc++) {
+          const int cn = col + cc;
+          if (cn >= N) continue;
+          float v = acc[i][j][2 * h + cc];
+          if (bias && blockIdx.z == 0) v += bias[cn];
+          Cz[(int64_t)rr * ldc + cn] = v;
+        }
+      }
+    }
+}
+
+// out[i] = sum_z part[z][i] in z order
+__global__ void k_sum_splits(const float *__restrict__ part, int nsplit, int64_t n, float *__restrict__ out, int accumulate) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s = 0.f;
+  for (int z = 0; z < nsplit; z++) s += part[(int64_t)z * n + i];
+  out[i] = accumulate ? out[i] + s : s;
+}
+
+// col[p][tap*C + c] = x[p + offset(tap)][c] (0 outside the grid); p = (b, y, x)
+__global__ void k_im2col(const bf16 *__restrict__ x, int B, int H, int W, int C, int dil, bf16 *__restrict__ col) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t total = (int64_t)B * H * W * 9 * C;
+  if (t >= total) return;
+  int c = (int)(t % C);
+  int tap = (int)((t / C) % 9);
+  int64_t p = t / (9 * C);
+  int xx = (int)(p % W), yy = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
+  int sy = yy + dil * (tap / 3 - 1), sx = xx + dil * (tap % 3 - 1);
+  bf16 v = __float2bfloat16(0.f);
+  if (sy >= 0 && sy < H && sx >= 0 && sx < W) v = x[(((int64_t)b * H + sy) * W + sx) * C + c];
+  col[t] = v;
+}
+
+// dx[p][c] = sum_tap dcol[p - offset(tap)][tap*C + c]   (taps in order; the transpose of im2col)
+__global__ void k_col2im(const float *__restrict__ dcol, int B, int H, int W, int C, int dil, float *__restrict__ dx) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t total = (int64_t)B * H * W * C;
+  if (t >= total) return;
+  int c = (int)(t % C);
+  int64_t p = t / C;
+  int xx = (int)(p % W), yy = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
+  float s = 0.f;
+  for (int tap = 0; tap < 9; tap++) {
+    int sy = yy - dil * (tap / 3 - 1), sx = xx - dil * (tap % 3 - 1);
+    if (sy >= 0 && sy < H && sx >= 0 && sx < W) s += dcol[(((int64_t)b * H + sy) * W + sx) * 9 * C + tap * C + c];
+  }
+  dx[t] = s;
+}
+
+__device__ __forceinline__ float sigm(float z) { return 1.f / (1.f + expf(-z)); }
+
+// a = SiLU(z) in BF16
+__global__ void k_silu_fwd(const float *__restrict__ z, bf16 *__restrict__ a, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) a[i] = __float2bfloat16(z[i] * sigm(z[i]));
+}
+
+// dz = da * SiLU'(z); FP32 and BF16 copies
+__global__ void k_silu_bwd(const float *__restrict__ da, const float *__restrict__ z, float *__restrict__ dz,
+                           bf16 *__restrict__ dzb, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s = sigm(z[i]);
+  float v = da[i] * s * (1.f + z[i] * (1.f - s));
+  dz[i] = v;
+  dzb[i] = __float2bfloat16(v);
+}
+
+__global__ void k_f32_to_bf16(const float *__restrict__ x, bf16 *__restrict__ y, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = __float2bfloat16(x[i]);
+}
+
+// y[b][p] = mask[p] * z[b][p]  (last layer, one channel)
+__global__ void k_output(const float *__restrict__ z, const float *__restrict__ mask, int64_t HW, int64_t n, float *__restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (mask ? mask[i % HW] : 1.f) * z[i];
+}
+
+// masked MSE: per-block partial sums of mask*(y-t)^2 and of mask; dz = 2 mask (y - t) / count later
+__global__ void __launch_bounds__(256) k_loss_partial(const float *__restrict__ y, const float *__restrict__ tgt,
+                                                      const float *__restrict__ mask, int64_t HW, int64_t n,
+                                                      float *__restrict__ part) {
+  __shared__ float sh[2][8];
+  int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  int64_t a = blockIdx.x * per, e = min(n, a + per);
+  float s = 0.f, m = 0.f;
+  for (int64_t i = a + threadIdx.x; i < e; i += blockDim.x) {
+    float mk = mask ? mask[i % HW] : 1.f;
+    float d = y[i] - tgt[i];
+    s += mk * d * d;
+    m += mk;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_down_sync(0xffffffffu, s, o);
+    m += __shfl_down_sync(0xffffffffu, m, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = s;
+    sh[1][threadIdx.x >> 5] = m;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float ts = 0.f, tm = 0.f;
+    for (int w = 0; w < 8; w++) { ts += sh[0][w]; tm += sh[1][w]; }
+    part[2 * blockIdx.x] = ts;
+    part[2 * blockIdx.x + 1] = tm;
+  }
+}
+
+__global__ void k_loss_final(const float *__restrict__ part, int nb, float *__restrict__ out) {
+  float s = 0.f, m = 0.f;
+  for (int k = 0; k < nb; k++) { s += part[2 * k]; m += part[2 * k + 1]; }
+  out[0] = s / fmaxf(m, 1.f);
+  out[1] = m;
+}
+
+__global__ void k_loss_grad(const float *__restrict__ y, const float *__restrict__ tgt, const float *__restrict__ mask,
+                            int64_t HW, int64_t n, const float *__restrict__ lossv, float *__restrict__ dz) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float mk = mask ? mask[i % HW] : 1.f;
+  dz[i] = 2.f * mk * mk * (y[i] - tgt[i]) / fmaxf(lossv[1], 1.f);
+}
+
+// db[c] = sum_p dz[p][c]: per-chunk partials then an ordered sum
+__global__ void k_colsum_partial(const float *__restrict__ dz, int64_t P, int C, int64_t chunk, float *__restrict__ part) {
+  int c = threadIdx.x;
+  if (c >= C) return;
+  int64_t a = blockIdx.x * chunk, e = min(P, a + chunk);
+  float s = 0.f;
+  for (int64_t p = a; p < e; p++) s += dz[p * C + c];
+  part[(int64_t)blockIdx.x * C + c] = s;
+}
+
+__global__ void k_adam(float *__restrict__ w, const float *__restrict__ gr, float *__restrict__ m, float *__restrict__ v,
+                       bf16 *__restrict__ wb, int64_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float gi = gr[i];
+  float mi = b1 * m[i] + (1.f - b1) * gi;
+  float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  w[i] = wi;
+  wb[i] = __float2bfloat16(wi);
+}
+
+// splitmix64-based uniform init in [-a, a]
+__global__ void k_init_uniform(float *__restrict__ w, int64_t n, uint64_t seed, float a) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  w[i] = (float)((2.0 * u - 1.0) * a);
+}
+
+inline unsigned g1(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+}  // namespace
+
+struct NNLayer {
+  int cin, cout, dil;
+  int64_t woff, boff;  // offsets in the flat parameter vector
+};
+
+struct iga_nn_s {
+  int H = 0, W = 0, cin = 0, hidden = 0, L = 0, maxB = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<NNLayer> layers;
+  int64_t nparams = 0;
+  float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // FP32 master, grad, Adam
+  bf16 *wb = nullptr;                                             // BF16 copy for the GEMMs
+  bf16 *wbt = nullptr;                                            // per-layer [9*Cin][Cout] ... (unused)
+  std::vector<bf16 *> X;      // inputs of each layer, BF16 [P][Cin]
+  std::vector<float *> Z;     // pre-activations FP32 [P][Cout]
+  bf16 *col = nullptr;        // im2col [P][9 Cmax]
+  float *dcol = nullptr;      // [P][9 Cmax]
+  float *dA = nullptr, *dZ = nullptr;  // [P][Cmax]
+  bf16 *dZb = nullptr;
+  float *part = nullptr;      // split-K / column-sum / loss partials
+  float *y = nullptr, *lossv = nullptr, *lossh = nullptr;
+  int64_t part_n = 0;
+  int adam_t = 0;
+  std::string err;
+  Prof prof;
+};
+
+static void nn_release(iga_nn_s *n) {
+  void *ps[] = {n->w, n->g, n->m, n->v, n->wb, n->col, n->dcol, n->dA, n->dZ, n->dZb, n->part, n->y, n->lossv};
+  for (void *p : ps)
+    if (p) cudaFree(p);
+  for (auto p : n->X) if (p) cudaFree(p);
+  for (auto p : n->Z) if (p) cudaFree(p);
+  if (n->lossh) cudaFreeHost(n->lossh);
+}
+
+#define NCK(call)                                                              \
+  do {                                                                         \
+    cudaError_t ce_ = (call);                                                  \
+    if (ce_ != cudaSuccess) {                                                  \
+      n->err = iga_format("%s: %s", #call, cudaGetErrorString(ce_));           \
+      return ce_ == cudaErrorMemoryAllocation ? IGA_ENOMEM : IGA_ECUDA;        \
+    }                                                                          \
+  } while (0)
+
+static thread_local std::string g_nn_err;
+
+template <bool AC, bool BK>
+static void gemm(iga_nn_s *n, int M, int N, int K, const bf16 *A, int64_t lda, const bf16 *B, int64_t ldb, float *C,
+                 int64_t ldc, const float *bias, int splits = 1) {
+  int kchunk = (K + splits - 1) / splits;
+  kchunk = (kchunk + GBK - 1) / GBK * GBK;
+  splits = (K + kchunk - 1) / kchunk;
+  dim3 grid((M + GBM - 1) / GBM, (N + GBN - 1) / GBN, splits);
+  k_gemm<AC, BK><<<grid, 256, 0, n->stream>>>(M, N, K, A, lda, B, ldb, C, ldc, (int64_t)M * ldc, kchunk, bias);
+}
+
+extern "C" iga_status iga_nn_create(int height, int width, int in_channels, int hidden, int layers, const int *dilations,
+                                    int max_batch, uint64_t seed, void *stream, iga_nn_t *out) {
+  if (!out) return IGA_EINVAL;
+  *out = nullptr;
+  if (height < 1 || width < 1 || in_channels < 1 || in_channels > 64 || hidden < 8 || hidden > 256 || hidden % 8 ||
+      layers < 2 || layers > 16 || max_batch < 1 || !dilations) {
+    g_nn_err = "bad network shape";
+    return IGA_EINVAL;
+  }
+  iga_nn_s *n = new iga_nn_s();
+  n->H = height; n->W = width; n->cin = in_channels; n->hidden = hidden; n->L = layers; n->maxB = max_batch;
+  n->stream = (cudaStream_t)stream;
+  int64_t off = 0;
+  int cmax = std::max(in_channels, hidden);
+  for (int l = 0; l < layers; l++) {
+    NNLayer ly;
+    ly.cin = (l == 0) ? in_channels : hidden;
+    ly.cout = (l == layers - 1) ? 1 : hidden;
+    ly.dil = dilations[l];
+    if (ly.dil < 1 || ly.dil > height) {
+      g_nn_err = "dilations must be in [1, height]";
+      delete n;
+      return IGA_EINVAL;
+    }
+    ly.woff = off;
+    off += (int64_t)ly.cout * 9 * ly.cin;
+    ly.boff = off;
+    off += ly.cout;
+    n->layers.push_back(ly);
+  }
+  n->nparams = off;
+  auto fail = [&](iga_status st) {
+    g_nn_err = n->err;
+    nn_release(n);
+    delete n;
+    return st;
+  };
+#define NCK2(call)                                                        \
+  do {                                                                    \
+    cudaError_t ce_ = (call);                                             \
+    if (ce_ != cudaSuccess) {                                             \
+      n->err = iga_format("%s: %s", #call, cudaGetErrorString(ce_));      \
+      return fail(ce_ == cudaErrorMemoryAllocation ? IGA_ENOMEM : IGA_ECUDA); \
+    }                                                                     \
+  } while (0)
+  const int64_t P = (int64_t)max_batch * height * width;
+  NCK2(cudaMalloc((void **)&n->w, off * sizeof(float)));
+  NCK2(cudaMalloc((void **)&n->g, off * sizeof(float)));
+  NCK2(cudaMalloc((void **)&n->m, off * sizeof(float)));
+  NCK2(cudaMalloc((void **)&n->v, off * sizeof(float)));
+  NCK2(cudaMalloc((void **)&n->wb, off * sizeof(bf16)));
+  NCK2(cudaMemsetAsync(n->m, 0, off * sizeof(float), n->stream));
+  NCK2(cudaMemsetAsync(n->v, 0, off * sizeof(float), n->stream));
+  for (int l = 0; l < layers; l++) {
+    bf16 *x = nullptr;
+    float *z = nullptr;
+    NCK2(cudaMalloc((void **)&x, P * n->layers[l].cin * sizeof(bf16)));
+    n->X.push_back(x);
+    NCK2(cudaMalloc((void **)&z, P * n->layers[l].cout * sizeof(float)));
+    n->Z.push_back(z);
+  }
+  NCK2(cudaMalloc((void **)&n->col, P * 9 * cmax * sizeof(bf16)));
+  NCK2(cudaMalloc((void **)&n->dcol, P * 9 * cmax * sizeof(float)));
+  NCK2(cudaMalloc((void **)&n->dA, P * cmax * sizeof(float)));
+  NCK2(cudaMalloc((void **)&n->dZ, P * cmax * sizeof(float)));
+  NCK2(cudaMalloc((void **)&n->dZb, P * cmax * sizeof(bf16)));
+  n->part_n = std::max<int64_t>((int64_t)64 * 9 * cmax * cmax, 4096 * (int64_t)cmax);
+  NCK2(cudaMalloc((void **)&n->part, n->part_n * sizeof(float)));
+  NCK2(cudaMalloc((void **)&n->y, P * sizeof(float)));
+  NCK2(cudaMalloc((void **)&n->lossv, 4 * sizeof(float)));
+  NCK2(cudaMallocHost((void **)&n->lossh, 4 * sizeof(float)));
+  // He-uniform weights (fan-in 9 Cin), zero biases
+  for (auto &ly : n->layers) {
+    float a = sqrtf(6.f / (9.f * ly.cin));
+    if (&ly == &n->layers.back()) a *= 0.1f;
+    k_init_uniform<<<g1((int64_t)ly.cout * 9 * ly.cin), 256, 0, n->stream>>>(n->w + ly.woff, (int64_t)ly.cout * 9 * ly.cin,
+                                                                              seed + (uint64_t)ly.woff, a);
+    NCK2(cudaMemsetAsync(n->w + ly.boff, 0, ly.cout * sizeof(float), n->stream));
+  }
+  k_f32_to_bf16<<<g1(off), 256, 0, n->stream>>>(n->w, n->wb, off);
+  NCK2(cudaStreamSynchronize(n->stream));
+#undef NCK2
+  *out = n;
+  return IGA_OK;
+}
+
+extern "C" void iga_nn_destroy(iga_nn_t n) {
+  if (!n) return;
+  cudaStreamSynchronize(n->stream);
+  nn_release(n);
+  delete n;
+}
+
+extern "C" const char *iga_nn_last_error(iga_nn_t n) { return n ? n->err.c_str() : g_nn_err.c_str(); }
+
+extern "C" iga_status iga_nn_num_params(iga_nn_t n, int64_t *count) {
+  if (!n || !count) return IGA_EINVAL;
+  *count = n->nparams;
+  return IGA_OK;
+}
+
+extern "C" iga_status iga_nn_get_params(iga_nn_t n, float *host) {
+  if (!n || !host) return IGA_EINVAL;
+  NCK(cudaMemcpyAsync(host, n->w, n->nparams * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
+  NCK(cudaStreamSynchronize(n->stream));
+  return IGA_OK;
+}
+
+extern "C" iga_status iga_nn_set_params(iga_nn_t n, const float *host) {
+  if (!n || !host) return IGA_EINVAL;
+  NCK(cudaMemcpyAsync(n->w, host, n->nparams * sizeof(float), cudaMemcpyHostToDevice, n->stream));
+  k_f32_to_bf16<<<g1(n->nparams), 256, 0, n->stream>>>(n->w, n->wb, n->nparams);
+  NCK(cudaMemsetAsync(n->m, 0, n->nparams * sizeof(float), n->stream));
+  NCK(cudaMemsetAsync(n->v, 0, n->nparams * sizeof(float), n->stream));
+  n->adam_t = 0;
+  NCK(cudaStreamSynchronize(n->stream));
+  return IGA_OK;
+}
+
+// forward pass for B samples: x device FP32 [B][H][W][cin]; result in n->y [B][H][W]
+static iga_status nn_forward(iga_nn_s *n, const float *x, int B, const float *mask) {
+  const int64_t HW = (int64_t)n->H * n->W, P = (int64_t)B * HW;
+  k_f32_to_bf16<<<g1(P * n->cin), 256, 0, n->stream>>>(x, n->X[0], P * n->cin);
+  for (int l = 0; l < n->L; l++) {
+    const NNLayer &ly = n->layers[l];
+    const int K = 9 * ly.cin;
+    k_im2col<<<g1(P * K), 256, 0, n->stream>>>(n->X[l], B, n->H, n->W, ly.cin, ly.dil, n->col);
+    // Z[P][cout] = col[P][K] * W^T  (W stored [cout][K]) + b
+    gemm<false, false>(n, (int)P, ly.cout, K, n->col, K, n->wb + ly.woff, K, n->Z[l], ly.cout, n->w + ly.boff);
+    if (l + 1 < n->L) k_silu_fwd<<<g1(P * ly.cout), 256, 0, n->stream>>>(n->Z[l], n->X[l + 1], P * ly.cout);
+  }
+  k_output<<<g1(P), 256, 0, n->stream>>>(n->Z[n->L - 1], mask, HW, P, n->y);
+  NCK(cudaGetLastError());
+  return IGA_OK;
+}
+
+extern "C" iga_status iga_nn_forward(iga_nn_t n, const float *x, int B, const float *mask, float *y) {
+  if (!n || !x || !y || B < 1 || B > n->maxB) {
+    if (n) n->err = "bad forward arguments";
+    return IGA_EINVAL;
+  }
+  iga_status st = nn_forward(n, x, B, mask);
+  if (st != IGA_OK) return st;
+  NCK(cudaMemcpyAsync(y, n->y, (size_t)B * n->H * n->W * sizeof(float), cudaMemcpyDeviceToDevice, n->stream));
+  return IGA_OK;
+}
+
+// forward + backward: masked mean-squared error against tgt [B][H][W]; gradients
+// of the loss w.r.t. all parameters into the internal FP32 gradient (and into
+// grads_out if non-NULL); the loss into *loss (host).
+extern "C" iga_status iga_nn_loss_grad(iga_nn_t n, const float *x, const float *tgt, const float *mask, int B, float *loss,
+                                       float *grads_out) {
+  if (!n || !x || !tgt || B < 1 || B > n->maxB) {
+    if (n) n->err = "bad loss_grad arguments";
+    return IGA_EINVAL;
+  }
+  iga_status st = nn_forward(n, x, B, mask);
+  if (st != IGA_OK) return st;
+  const int64_t HW = (int64_t)n->H * n->W, P = (int64_t)B * HW;
+  const int nbl = 256;
+  k_loss_partial<<<nbl, 256, 0, n->stream>>>(n->y, tgt, mask, HW, P, n->part);
+  k_loss_final<<<1, 1, 0, n->stream>>>(n->part, nbl, n->lossv);
+  // dL/dZ_last = 2 mask (y - t) / count  (y = mask * z)
+  k_loss_grad<<<g1(P), 256, 0, n->stream>>>(n->y, tgt, mask, HW, P, n->lossv, n->dZ);
+  for (int l = n->L - 1; l >= 0; l--) {
+    const NNLayer &ly = n->layers[l];
+    const int K = 9 * ly.cin;
+    if (l < n->L - 1) {
+      // dZ = dA * SiLU'(Z)
+      k_silu_bwd<<<g1(P * ly.cout), 256, 0, n->stream>>>(n->dA, n->Z[l], n->dZ, n->dZb, P * ly.cout);
+    } else {
+      k_f32_to_bf16<<<g1(P * ly.cout), 256, 0, n->stream>>>(n->dZ, n->dZb, P * ly.cout);
+    }
+    // bias gradient: column sums of dZ
+    const int64_t chunk = 4096;
+    const int nch = (int)((P + chunk - 1) / chunk);
+    k_colsum_partial<<<nch, 256, 0, n->stream>>>(n->dZ, P, ly.cout, chunk, n->part);
+    k_sum_splits<<<g1(ly.cout), 256, 0, n->stream>>>(n->part, nch, ly.cout, n->g + ly.boff, 0);
+    // weight gradient: dW[cout][K] = dZ^T (cout x P) * col (P x K), split over P
+    k_im2col<<<g1(P * K), 256, 0, n->stream>>>(n->X[l], B, n->H, n->W, ly.cin, ly.dil, n->col);
+    int splits = (int)std::min<int64_t>(64, std::max<int64_t>(1, P / 2048));
+    while ((int64_t)splits * ly.cout * K > n->part_n) splits--;
+    gemm<true, true>(n, ly.cout, K, (int)P, n->dZb, ly.cout, n->col, K, n->part, K, nullptr, splits);
+    int kchunk = ((int)((P + splits - 1) / splits) + GBK - 1) / GBK * GBK;
+    int used = (int)((P + kchunk - 1) / kchunk);
+    k_sum_splits<<<g1((int64_t)ly.cout * K), 256, 0, n->stream>>>(n->part, used, (int64_t)ly.cout * K, n->g + ly.woff, 0);
+    if (l > 0) {
+      // dcol[P][K] = dZ[P][cout] * W[cout][K]; dA_prev = col2im(dcol)
+      gemm<false, true>(n, (int)P, K, ly.cout, n->dZb, ly.cout, n->wb + ly.woff, K, n->dcol, K, nullptr);
+      k_col2im<<<g1(P * ly.cin), 256, 0, n->stream>>>(n->dcol, B, n->H, n->W, ly.cin, ly.dil, n->dA);
+    }
+  }
+  NCK(cudaGetLastError());
+  NCK(cudaMemcpyAsync(n->lossh, n->lossv, 2 * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
+  if (grads_out) NCK(cudaMemcpyAsync(grads_out, n->g, n->nparams * sizeof(float), cudaMemcpyDeviceToDevice, n->stream));
+  NCK(cudaStreamSynchronize(n->stream));
+  if (loss) *loss = n->lossh[0];
+  return IGA_OK;
+}
+
+extern "C" iga_status iga_nn_adam_step(iga_nn_t n, float lr, float beta1, float beta2, float eps) {
+  if (!n || !(lr > 0.f)) return IGA_EINVAL;
+  n->adam_t++;
+  float c1 = 1.f - powf(beta1, (float)n->adam_t), c2 = 1.f - powf(beta2, (float)n->adam_t);
+  k_adam<<<g1(n->nparams), 256, 0, n->stream>>>(n->w, n->g, n->m, n->v, n->wb, n->nparams, lr, beta1, beta2, eps, c1, c2);
+  NCK(cudaGetLastError());
+  return IGA_OK;
+}
