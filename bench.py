@@ -331,7 +331,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nel", type=int, default=64, help="elements per direction (64 is the benchmark workload)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sampling time (0: skip)")
+    ap.add_argument("--workload", default="annulus64",
+                    choices=["annulus64", "bratu16", "cube_mixed", "batch512", "learned64"],
+                    help="annulus64 is the benchmark line; the others print their configuration's line")
     args = ap.parse_args()
+    if args.workload != "annulus64" and args.impl == "ours":
+        import torch
+        import bench_workloads as BW
+        from paper_1305_4452_gb300 import build, iga, workloads as W
+        build.build()
+        torch.cuda.set_device(0)
+        print(BW.WORKLOADS[args.workload](torch, iga, W, ClockSampler(0)))
+        return 0
     global NEL
     NEL = args.nel
     if args.warmup < 3:

@@ -1,0 +1,223 @@
+"""Benchmark lines for the configurations other than the headline one.
+
+    python bench.py --workload {bratu16, cube_mixed, batch512, learned64}
+
+Each prints one JSON line with the keys of the headline line (metric, value,
+unit, config, clocks, e2e-style extras) for one configuration:
+
+  bratu16     2D Bratu, lambda = 1, 16x16 quadratic C1: one residual + Jacobian
+              assembly at seeded interior values U ~ U[-0.1, 0.1], then a full
+              Newton solve (the smallest case: launch-latency bound).
+  cube_mixed  3D unit cube, lambda = 2, 128^3 quadratic and 48^3 quartic:
+              Jacobian assembly in FP64, FP32 (sum factorisation) and, for
+              p <= 3, BF16/TF32 tensor-core element matrices; relative Frobenius
+              error against the FP64 Jacobian; Newton solves with each.
+  batch512    512 independent 2D instances (n ~ U{16..128}, p ~ U{2,3},
+              lambda ~ U[0.5, 6]) in one persistent, graph-captured launch.
+  learned64   kappa-Bratu on 64^2 quadratic (66 x 66 control grid): training
+              data from the batched solver, the convolutional guess trained on
+              the GPU, evaluation on held-out fields against the zero start and
+              against one-at-a-time FP64 Newton.
+"""
+import json
+import time
+
+import numpy as np
+
+METRIC = "assembled Jacobian nnz/s & Newton solves/s to ||F||≤1e-10, FP64 vs mixed/NN"
+
+
+def _ev(torch, fn, reps):
+    fn()
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return best
+
+
+def _line(metric_value, unit, workload, extra, clocks, hib=True, dtype="f64"):
+    d = {"metric": METRIC, "value": metric_value, "unit": unit, "n_gpus": 1, "higher_is_better": hib,
+         "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": {"workload": workload}}
+    d.update(extra)
+    d["clocks"] = clocks
+    return json.dumps(d)
+
+
+def bratu16(torch, iga, W, clock):
+    bc = {(a, s): 0.0 for a in range(2) for s in range(2)}
+    d = iga.Discretization(2, 2, nel=16, lam=1.0, dirichlet=bc)
+    U = torch.tensor(W.interior_field([18, 18], 1), device="cuda")
+    F = torch.empty_like(U)
+    J = torch.empty(d.nnz, dtype=torch.float64, device="cuda")
+    clock.start()
+    tr = _ev(torch, lambda: d.form_residual(U, F), 50)
+    tj = _ev(torch, lambda: d.form_jacobian(U, vals=J), 50)
+    o = iga.newton_defaults()
+    times, rep = [], None
+    for _ in range(20):
+        Us = U.clone()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        rep = d.solve_newton(Us, o)
+        times.append(time.perf_counter() - t)
+    ck = clock.stop()
+    t = min(times)
+    return _line(1.0 / t, "solves/s", "bratu2d_16x16_p2_lambda1_fp64", {
+        "residual_us": tr * 1e3, "jacobian_us": tj * 1e3, "jacobian_nnz_per_s": d.nnz / (tj * 1e-3),
+        "newton": {"its": rep.newton_its, "krylov_its": rep.krylov_its, "fnorm": rep.fnorm},
+        "ms_per_solve": t * 1e3, "dofs": d.N, "nnz": d.nnz}, ck)
+
+
+def cube_mixed(torch, iga, W, clock):
+    out = {}
+    clock.start()
+    for name, p, nel in (("cube128_p2", 2, 128), ("cube48_p4", 4, 48)):
+        bc = {(a, s): 0.0 for a in range(3) for s in range(2)}
+        d = iga.Discretization(3, p, nel=nel, lam=2.0, dirichlet=bc)
+        U = torch.tensor(W.interior_field([nel + p] * 3, 3), device="cuda")
+        J = torch.empty(d.nnz, dtype=torch.float64, device="cuda")
+        J32 = torch.empty(d.nnz, dtype=torch.float32, device="cuda")
+        res = {"dofs": d.N, "nnz": d.nnz}
+        t = _ev(torch, lambda: d.form_jacobian(U, vals=J), 3)
+        res["fp64"] = {"ms": t, "nnz_per_s": d.nnz / (t * 1e-3)}
+        modes = [("fp32_sumfact", iga.IGA_JAC_FP32)]
+        if p <= 3:
+            modes += [("bf16_tensor", iga.IGA_JAC_BF16), ("tf32_tensor", iga.IGA_JAC_TF32)]
+        d.form_jacobian(U, vals=J)
+        nJ = torch.linalg.norm(J).item()
+        for mname, code in modes:
+            t = _ev(torch, lambda: d.form_jacobian(U, prec=code, vals=J32), 3)
+            err = (torch.linalg.norm(J32.double() - J) / nJ).item()
+            res[mname] = {"ms": t, "nnz_per_s": d.nnz / (t * 1e-3), "rel_frobenius_error_vs_fp64": err}
+        del J32
+        solves = {}
+        for label, jac, ksp in (("fp64_gmres", iga.IGA_FP64, iga.IGA_KSP_GMRES), ("fp32_gmres", iga.IGA_JAC_FP32, iga.IGA_KSP_GMRES),
+                                ("fp32_cg", iga.IGA_JAC_FP32, iga.IGA_KSP_CG)) + ((("bf16_gmres", iga.IGA_JAC_BF16, iga.IGA_KSP_GMRES),) if p <= 3 else ()):
+            o = iga.newton_defaults()
+            o.jac, o.ksp = jac, ksp
+            best, rep = 1e30, None
+            for _ in range(2):
+                Us = torch.zeros(d.N, dtype=torch.float64, device="cuda")
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rep = d.solve_newton(Us, o)
+                best = min(best, time.perf_counter() - t0)
+            solves[label] = {"ms": best * 1e3, "newton_its": rep.newton_its, "krylov_its": rep.krylov_its, "fnorm": rep.fnorm}
+        res["newton"] = solves
+        out[name] = res
+        d.close()
+        del J
+        torch.cuda.empty_cache()
+    ck = clock.stop()
+    v = out["cube128_p2"]["fp32_sumfact"]["nnz_per_s"]
+    return _line(v, "nnz/s", "cube_128cubed_p2_and_48cubed_p4_lambda2_mixed_jacobian", {"cases": out}, ck, dtype="f32")
+
+
+def batch512(torch, iga, W, clock):
+    ins = W.batch_instances(512, seed=0)
+    t0 = time.perf_counter()
+    b = iga.Batch(ins)
+    setup = time.perf_counter() - t0
+    U = torch.zeros(b.total, dtype=torch.float64, device="cuda")
+    from paper_1305_4452_gb300 import autotune
+    o = iga.newton_defaults()
+    o.ksp = iga.IGA_KSP_CG
+    tuned = autotune.tune(b, ins, U, o, retime=True)
+    res = {"autotune": tuned}
+    clock.start()
+    for label, ksp in (("cg", iga.IGA_KSP_CG), ("gmres30", iga.IGA_KSP_GMRES)):
+        o = iga.newton_defaults()
+        o.ksp = ksp
+        o.gmres_restart = 30
+        best, r = 1e30, None
+        for _ in range(3):
+            U.zero_()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            r = b.solve(U, o)
+            best = min(best, time.perf_counter() - t)
+        res[label] = {"ms": best * 1e3, "solves_per_s": 512 / best, "solved": int(r["solved"]),
+                      "newton_its_total": int(r["newton_its"].sum()), "krylov_its_total": int(r["krylov_its"].sum()),
+                      "max_fnorm": float(r["fnorm"].max())}
+    ck = clock.stop()
+    b.close()
+    return _line(res["cg"]["solves_per_s"], "solves/s", "batch512_2d_n16to128_p2or3_lambda0.5to6_fp64res_fp32jac",
+                 {"results": res, "setup_s": setup, "total_dofs": int(b.total)}, ck)
+
+
+def learned64(torch, iga, W, clock, n_train=20000, n_test=2000, steps=6000):
+    from paper_1305_4452_gb300 import nn
+    nel = 64
+    t0 = time.perf_counter()
+    train = nn.kappa_instances(range(0, n_train), nel=nel)
+    test = nn.kappa_instances(range(1_000_000, 1_000_000 + n_test), nel=nel)
+    Utr, rtr, gen_s = nn.solve_batch(train)
+    keep = rtr["status"] == 0
+    train = [x for x, k in zip(train, keep) if k]
+    Utr = Utr[keep]
+    x, mask = nn.features(train)
+    tgt = torch.tensor(Utr.reshape(len(train), nel + 2, nel + 2), dtype=torch.float32, device="cuda")
+    net = nn.Net(nel + 2, nel + 2, hidden=64, max_batch=64, seed=0)
+    net.set_h1_weight(64.0)  # discrete H1 term: penalise the oscillatory error Newton's residual sees
+    rng = np.random.default_rng(0)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    losses = []
+    for step in range(steps):
+        idx = torch.as_tensor(rng.choice(len(train), 64, replace=False), device="cuda")
+        lr = 2e-3 * (0.5 * (1 + np.cos(np.pi * step / steps))) + 1e-5
+        losses.append(net.loss_grad(x[idx], tgt[idx], mask))
+        net.adam_step(lr)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    clock.start()
+    # held-out: batched mixed Newton from zero and from the network's guess (inference timed)
+    U0, r0, s0 = nn.solve_batch(test)
+    xt, _ = nn.features(test)
+    torch.cuda.synchronize()
+    ti = time.perf_counter()
+    guess = torch.cat([net.forward(xt[a:a + 64], mask) for a in range(0, len(test), 64)])
+    torch.cuda.synchronize()
+    infer_s = time.perf_counter() - ti
+    U1, r1, s1 = nn.solve_batch(test, U0=guess.double().cpu().numpy().reshape(len(test), -1))
+    ok = (r0["status"] == 0) & (r1["status"] == 0)
+    # one-at-a-time plain FP64 Newton (GMRES + Jacobi, zero start) on a sample of the test fields
+    bc = {(a, s): 0.0 for a in range(2) for s in range(2)}
+    nsamp = 64
+    tp = 0.0
+    its_plain = []
+    for ins in test[:nsamp]:
+        d = iga.Discretization(2, 2, nel=nel, lam=ins["lam"], log_kappa=ins["log_kappa"], dirichlet=bc)
+        Us = torch.zeros(d.N, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        rep = d.solve_newton(Us, iga.newton_defaults(), check=False)
+        tp += time.perf_counter() - t
+        its_plain.append(rep.newton_its)
+        d.close()
+    ck = clock.stop()
+    rel_err = float(np.median(np.linalg.norm(U1[ok] - guess.double().cpu().numpy().reshape(len(test), -1)[ok], axis=1)
+                              / np.maximum(np.linalg.norm(U1[ok], axis=1), 1e-30)))
+    res = {
+        "train_solves": int(keep.sum()), "train_skipped_no_convergence": int((~keep).sum()), "data_gen_s": gen_s,
+        "train_steps": steps, "train_s": train_s, "loss_first": losses[0], "loss_last": float(np.mean(losses[-50:])),
+        "params": net.nparams, "test": n_test, "test_both_converged": int(ok.sum()),
+        "guess_median_rel_error": rel_err,
+        "zero_start": {"solves_per_s": n_test / s0, "newton_its_mean": float(r0["newton_its"][ok].mean()),
+                       "krylov_its_mean": float(r0["krylov_its"][ok].mean())},
+        "nn_start": {"solves_per_s": n_test / (s1 + infer_s), "inference_s": infer_s,
+                     "newton_its_mean": float(r1["newton_its"][ok].mean()), "krylov_its_mean": float(r1["krylov_its"][ok].mean())},
+        "plain_fp64_single": {"solves_per_s": nsamp / tp, "newton_its_mean": float(np.mean(its_plain)), "sample": nsamp},
+        "total_s": time.perf_counter() - t0,
+    }
+    net.close()
+    return _line(res["nn_start"]["solves_per_s"], "solves/s", "kappa_bratu_64x64_p2_learned_initial_guess", {"results": res}, ck)
+
+
+WORKLOADS = {"bratu16": bratu16, "cube_mixed": cube_mixed, "batch512": batch512, "learned64": learned64}

@@ -243,6 +243,10 @@ iga_status iga_nn_forward(iga_nn_t nn, const float *x, int B, const float *mask,
  * (host) gets the loss; grads_out (device float[count]) gets the gradient if non-NULL */
 iga_status iga_nn_loss_grad(iga_nn_t nn, const float *x, const float *tgt, const float *mask, int B, float *loss,
                             float *grads_out);
+/* Loss = [sum mask (y-t)^2 + beta * sum over grid edges ((y-t)_i - (y-t)_j)^2] / sum mask:
+ * beta >= 0 weights a discrete H1 seminorm of the error (default 0).  The Newton
+ * residual of a guess is dominated by its oscillatory error, which this term targets. */
+iga_status iga_nn_set_h1_weight(iga_nn_t nn, float beta);
 /* one Adam update with the gradient of the last iga_nn_loss_grad */
 iga_status iga_nn_adam_step(iga_nn_t nn, float lr, float beta1, float beta2, float eps);
 void iga_nn_destroy(iga_nn_t nn);

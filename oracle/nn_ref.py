@@ -58,14 +58,25 @@ def forward(params, shapes, x, mask):
     return y, acts, zs
 
 
-def loss_and_grad(params, shapes, x, tgt, mask):
-    """Masked mean-squared error and its gradient with respect to params."""
+def loss_and_grad(params, shapes, x, tgt, mask, beta=0.0):
+    """Loss [sum mask e^2 + beta * sum over grid edges (e_i - e_j)^2] / sum mask with
+    e = y - tgt, and its gradient with respect to params."""
     y, acts, zs = forward(params, shapes, x, mask)
     m = mask[None] * np.ones_like(tgt)
     count = max(m.sum(), 1.0)
-    loss = float((m * (y - tgt) ** 2).sum() / count)
+    e = y - tgt
+    dx, dy = np.diff(e, axis=2), np.diff(e, axis=1)
+    loss = float(((m * e ** 2).sum() + beta * ((dx ** 2).sum() + (dy ** 2).sum())) / count)
     grad = np.zeros_like(params)
-    dz = (2.0 * m * (y - tgt) / count)[..., None]  # dL/dz of the last layer (mask is 0/1)
+    gy = 2.0 * m * e
+    if beta:
+        lap = np.zeros_like(e)
+        lap[:, :, :-1] -= dx
+        lap[:, :, 1:] += dx
+        lap[:, :-1, :] -= dy
+        lap[:, 1:, :] += dy
+        gy = gy + 2.0 * beta * lap
+    dz = (mask[None] * gy / count)[..., None]  # dL/dz of the last layer, y = mask * z
     for l in range(len(shapes) - 1, -1, -1):
         cin, cout, d, woff, boff = shapes[l]
         if l < len(shapes) - 1:

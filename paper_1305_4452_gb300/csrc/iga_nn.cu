@@ -48,22 +48,53 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const bf16 *_
 #pragma unroll
     for (int j = 0; j < 4; j++) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
   const bf16 zero = __float2bfloat16(0.f);
+  // 8-element (16-byte) chunks along the contiguous dimension of each operand;
+  // a chunk that is fully in range and 16-byte aligned is loaded with one vector
+  // load, otherwise element by element with zero fill
+  const bool avec = (lda % 8) == 0 && ((uintptr_t)A % 16) == 0;
+  const bool bvec = (ldb % 8) == 0 && ((uintptr_t)B % 16) == 0;
   for (int k0 = kbeg; k0 < kend; k0 += GBK) {
-    for (int idx = tid; idx < GBM * GBK; idx += 256) {
-      int r, kk;
-      if (!A_COL) { r = idx / GBK; kk = idx % GBK; } else { kk = idx / GBM; r = idx % GBM; }
+    for (int c = tid; c < GBM * GBK / 8; c += 256) {
+      int r, kk;  // chunk origin in the tile
+      if (!A_COL) { r = c / (GBK / 8); kk = (c % (GBK / 8)) * 8; } else { kk = c / (GBM / 8); r = (c % (GBM / 8)) * 8; }
       const int gm = m0 + r, gk = k0 + kk;
-      bf16 v = zero;
-      if (gm < M && gk < kend) v = A_COL ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
-      As[r][kk] = v;
+      if (!A_COL) {
+        if (avec && gm < M && gk + 8 <= kend) {
+          const uint4 v = *reinterpret_cast<const uint4 *>(A + (int64_t)gm * lda + gk);
+          *reinterpret_cast<uint4 *>(&As[r][kk]) = v;
+        } else {
+          for (int u = 0; u < 8; u++) As[r][kk + u] = (gm < M && gk + u < kend) ? A[(int64_t)gm * lda + gk + u] : zero;
+        }
+      } else {
+        if (avec && gk < kend && gm + 8 <= M) {
+          const uint4 v = *reinterpret_cast<const uint4 *>(A + (int64_t)gk * lda + gm);
+          const bf16 *e = reinterpret_cast<const bf16 *>(&v);
+          for (int u = 0; u < 8; u++) As[r + u][kk] = e[u];
+        } else {
+          for (int u = 0; u < 8; u++) As[r + u][kk] = (gk < kend && gm + u < M) ? A[(int64_t)gk * lda + gm + u] : zero;
+        }
+      }
     }
-    for (int idx = tid; idx < GBN * GBK; idx += 256) {
+    for (int c = tid; c < GBN * GBK / 8; c += 256) {
       int r, kk;
-      if (!B_KN) { r = idx / GBK; kk = idx % GBK; } else { kk = idx / GBN; r = idx % GBN; }
+      if (!B_KN) { r = c / (GBK / 8); kk = (c % (GBK / 8)) * 8; } else { kk = c / (GBN / 8); r = (c % (GBN / 8)) * 8; }
       const int gn = n0 + r, gk = k0 + kk;
-      bf16 v = zero;
-      if (gn < N && gk < kend) v = B_KN ? B[(int64_t)gk * ldb + gn] : B[(int64_t)gn * ldb + gk];
-      Bs[r][kk] = v;
+      if (!B_KN) {
+        if (bvec && gn < N && gk + 8 <= kend) {
+          const uint4 v = *reinterpret_cast<const uint4 *>(B + (int64_t)gn * ldb + gk);
+          *reinterpret_cast<uint4 *>(&Bs[r][kk]) = v;
+        } else {
+          for (int u = 0; u < 8; u++) Bs[r][kk + u] = (gn < N && gk + u < kend) ? B[(int64_t)gn * ldb + gk + u] : zero;
+        }
+      } else {
+        if (bvec && gk < kend && gn + 8 <= N) {
+          const uint4 v = *reinterpret_cast<const uint4 *>(B + (int64_t)gk * ldb + gn);
+          const bf16 *e = reinterpret_cast<const bf16 *>(&v);
+          for (int u = 0; u < 8; u++) Bs[r + u][kk] = e[u];
+        } else {
+          for (int u = 0; u < 8; u++) Bs[r + u][kk] = (gk < kend && gn + u < N) ? B[(int64_t)gk * ldb + gn + u] : zero;
+        }
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -187,10 +218,13 @@ __global__ void k_output(const float *__restrict__ z, const float *__restrict__ 
   if (i < n) y[i] = (mask ? mask[i % HW] : 1.f) * z[i];
 }
 
-// masked MSE: per-block partial sums of mask*(y-t)^2 and of mask; dz = 2 mask (y - t) / count later
+// Loss = [ sum mask (y-t)^2 + beta * sum over grid edges (difference of (y-t))^2 ] / sum mask:
+// the mean-squared error plus a discrete H1 seminorm of the error (beta >= 0), which
+// weighs the oscillatory error components that dominate the initial Newton residual.
+// Per-block partial sums of the numerator and of the mask count.
 __global__ void __launch_bounds__(256) k_loss_partial(const float *__restrict__ y, const float *__restrict__ tgt,
-                                                      const float *__restrict__ mask, int64_t HW, int64_t n,
-                                                      float *__restrict__ part) {
+                                                      const float *__restrict__ mask, int64_t HW, int64_t n, int Wd,
+                                                      int Hh, float beta, float *__restrict__ part) {
   __shared__ float sh[2][8];
   int64_t per = (n + gridDim.x - 1) / gridDim.x;
   int64_t a = blockIdx.x * per, e = min(n, a + per);
@@ -200,6 +234,12 @@ __global__ void __launch_bounds__(256) k_loss_partial(const float *__restrict__ 
     float d = y[i] - tgt[i];
     s += mk * d * d;
     m += mk;
+    if (beta != 0.f) {
+      const int64_t pix = i % HW;
+      const int xx = (int)(pix % Wd), yy = (int)(pix / Wd);
+      if (xx + 1 < Wd) { float dd = (y[i + 1] - tgt[i + 1]) - d; s += beta * dd * dd; }
+      if (yy + 1 < Hh) { float dd = (y[i + Wd] - tgt[i + Wd]) - d; s += beta * dd * dd; }
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     s += __shfl_down_sync(0xffffffffu, s, o);
@@ -225,12 +265,26 @@ __global__ void k_loss_final(const float *__restrict__ part, int nb, float *__re
   out[1] = m;
 }
 
+// dL/dz with y = mask * z: mask * [2 mask e + 2 beta (sum over neighbours (e - e_nb))] / count
 __global__ void k_loss_grad(const float *__restrict__ y, const float *__restrict__ tgt, const float *__restrict__ mask,
-                            int64_t HW, int64_t n, const float *__restrict__ lossv, float *__restrict__ dz) {
+                            int64_t HW, int64_t n, int Wd, int Hh, float beta, const float *__restrict__ lossv,
+                            float *__restrict__ dz) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   float mk = mask ? mask[i % HW] : 1.f;
-  dz[i] = 2.f * mk * mk * (y[i] - tgt[i]) / fmaxf(lossv[1], 1.f);
+  float e = y[i] - tgt[i];
+  float g = 2.f * mk * e;
+  if (beta != 0.f) {
+    const int64_t pix = i % HW;
+    const int xx = (int)(pix % Wd), yy = (int)(pix / Wd);
+    float lap = 0.f;
+    if (xx + 1 < Wd) lap += e - (y[i + 1] - tgt[i + 1]);
+    if (xx > 0) lap += e - (y[i - 1] - tgt[i - 1]);
+    if (yy + 1 < Hh) lap += e - (y[i + Wd] - tgt[i + Wd]);
+    if (yy > 0) lap += e - (y[i - Wd] - tgt[i - Wd]);
+    g += 2.f * beta * lap;
+  }
+  dz[i] = mk * g / fmaxf(lossv[1], 1.f);
 }
 
 // db[c] = sum_p dz[p][c]: per-chunk partials then an ordered sum
@@ -296,8 +350,8 @@ struct iga_nn_s {
   float *y = nullptr, *lossv = nullptr, *lossh = nullptr;
   int64_t part_n = 0;
   int adam_t = 0;
+  float h1 = 0.f;  // weight of the discrete H1 term of the loss
   std::string err;
-  Prof prof;
 };
 
 static void nn_release(iga_nn_s *n) {
@@ -490,10 +544,9 @@ extern "C" iga_status iga_nn_loss_grad(iga_nn_t n, const float *x, const float *
   if (st != IGA_OK) return st;
   const int64_t HW = (int64_t)n->H * n->W, P = (int64_t)B * HW;
   const int nbl = 256;
-  k_loss_partial<<<nbl, 256, 0, n->stream>>>(n->y, tgt, mask, HW, P, n->part);
+  k_loss_partial<<<nbl, 256, 0, n->stream>>>(n->y, tgt, mask, HW, P, n->W, n->H, n->h1, n->part);
   k_loss_final<<<1, 1, 0, n->stream>>>(n->part, nbl, n->lossv);
-  // dL/dZ_last = 2 mask (y - t) / count  (y = mask * z)
-  k_loss_grad<<<g1(P), 256, 0, n->stream>>>(n->y, tgt, mask, HW, P, n->lossv, n->dZ);
+  k_loss_grad<<<g1(P), 256, 0, n->stream>>>(n->y, tgt, mask, HW, P, n->W, n->H, n->h1, n->lossv, n->dZ);
   for (int l = n->L - 1; l >= 0; l--) {
     const NNLayer &ly = n->layers[l];
     const int K = 9 * ly.cin;
@@ -527,6 +580,12 @@ extern "C" iga_status iga_nn_loss_grad(iga_nn_t n, const float *x, const float *
   if (grads_out) NCK(cudaMemcpyAsync(grads_out, n->g, n->nparams * sizeof(float), cudaMemcpyDeviceToDevice, n->stream));
   NCK(cudaStreamSynchronize(n->stream));
   if (loss) *loss = n->lossh[0];
+  return IGA_OK;
+}
+
+extern "C" iga_status iga_nn_set_h1_weight(iga_nn_t n, float beta) {
+  if (!n || !(beta >= 0.f) || !isfinite(beta)) return IGA_EINVAL;
+  n->h1 = beta;
   return IGA_OK;
 }
 

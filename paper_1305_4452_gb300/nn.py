@@ -31,6 +31,7 @@ def _lib():
         L.iga_nn_forward.argtypes = [vp, vp, ctypes.c_int, vp, vp]
         L.iga_nn_loss_grad.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), vp]
         L.iga_nn_adam_step.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]
+        L.iga_nn_set_h1_weight.argtypes = [vp, ctypes.c_float]
         L.iga_nn_destroy.argtypes = [vp]
         L.iga_nn_destroy.restype = None
         L.iga_nn_last_error.argtypes = [vp]
@@ -97,6 +98,9 @@ class Net:
                                      None if mask is None else ctypes.c_void_p(mask.data_ptr()), x.shape[0], ctypes.byref(loss),
                                      None if grads is None else ctypes.c_void_p(grads.data_ptr())), self.h)
         return loss.value
+
+    def set_h1_weight(self, beta):
+        _chk(_lib().iga_nn_set_h1_weight(self.h, float(beta)), self.h)
 
     def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         _chk(_lib().iga_nn_adam_step(self.h, lr, beta1, beta2, eps), self.h)

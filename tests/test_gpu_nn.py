@@ -22,10 +22,11 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
 
 
-@pytest.mark.parametrize("shape", [(10, 10, 16, (1, 2, 4, 1), 3), (13, 11, 24, (1, 3, 1), 2)])
+@pytest.mark.parametrize("shape", [(10, 10, 16, (1, 2, 4, 1), 3, 0.0), (13, 11, 24, (1, 3, 1), 2, 4.0)])
 def test_forward_loss_and_gradients_match_cpu_reference(M, shape):
-    H, Wd, hidden, dil, B = shape
+    H, Wd, hidden, dil, B, beta = shape
     net = M.Net(H, Wd, hidden=hidden, dilations=dil, max_batch=4, seed=3)
+    net.set_h1_weight(beta)
     shapes, n = R.layer_shapes(4, hidden, dil)
     assert n == net.nparams
     rng = np.random.default_rng(7)
@@ -42,7 +43,7 @@ def test_forward_loss_and_gradients_match_cpu_reference(M, shape):
     grads = torch.zeros(net.nparams, dtype=torch.float32, device="cuda")
     loss = net.loss_grad(xd, td, md, grads)
     yr, _, _ = R.forward(params, shapes, x.astype(np.float64), mask.astype(np.float64))
-    lr, gr = R.loss_and_grad(params, shapes, x.astype(np.float64), tgt.astype(np.float64), mask.astype(np.float64))
+    lr, gr = R.loss_and_grad(params, shapes, x.astype(np.float64), tgt.astype(np.float64), mask.astype(np.float64), beta)
     # BF16 operands (8-bit significands) with FP32 accumulation
     assert rel(y, yr) < 2e-2
     assert abs(loss - lr) < 2e-2 * lr

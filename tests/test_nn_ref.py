@@ -35,9 +35,13 @@ def test_conv_matches_direct_sum():
                 assert abs(out[0, yy, xx, o] - s) < 1e-12
 
 
-def test_backward_matches_finite_differences():
+import pytest
+
+
+@pytest.mark.parametrize("beta", [0.0, 3.0])
+def test_backward_matches_finite_differences(beta):
     shapes, params, x, tgt, mask = small_problem()
-    loss, grad = R.loss_and_grad(params, shapes, x, tgt, mask)
+    loss, grad = R.loss_and_grad(params, shapes, x, tgt, mask, beta)
     rng = np.random.default_rng(2)
     idx = rng.choice(len(params), 40, replace=False)
     idx = np.concatenate([idx, [shapes[l][4] for l in range(len(shapes))]])  # a bias of every layer
@@ -45,7 +49,7 @@ def test_backward_matches_finite_differences():
     for i in idx:
         e = np.zeros_like(params)
         e[i] = h
-        lp, _ = R.loss_and_grad(params + e, shapes, x, tgt, mask)
-        lm, _ = R.loss_and_grad(params - e, shapes, x, tgt, mask)
+        lp, _ = R.loss_and_grad(params + e, shapes, x, tgt, mask, beta)
+        lm, _ = R.loss_and_grad(params - e, shapes, x, tgt, mask, beta)
         fd = (lp - lm) / (2 * h)
         assert abs(fd - grad[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, grad[i])
