@@ -300,10 +300,18 @@ def roofline_entry(disc, cls, avg_ms, hbm_gbs, hbm_src):
     X = NEL * (P + 1)
     P1 = sum(min(i, P) + min(NEL + P - 1 - i, P) + 1 for i in range(NEL + P))  # 1D pairs
     if cls == "spmv":
-        bytes_ = nnz * 12 + (N + 1) * 8 + 2 * N * 8
-        return {"kernel": "k_spmv (CSR, FP64)", "bound": "hbm", "achieved": bytes_ / (avg_ms * 1e-3) / 1e9,
-                "peak": hbm_gbs, "unit": "GB/s", "frac": bytes_ / (avg_ms * 1e-3) / 1e9 / hbm_gbs,
-                "traffic": None, "peak_source": hbm_src, "algorithmic_bytes_per_launch": bytes_}
+        # values (columns follow from the stencil), rowptr, x read, y written; one FP64 FMA per
+        # stored value.  At 8 B per FMA this product is bound by GB300's FP64 pipe, not by HBM.
+        bytes_ = nnz * 8 + (N + 1) * 8 + 2 * N * 8
+        flops = 2.0 * nnz
+        t = avg_ms * 1e-3
+        hbm_frac = bytes_ / t / 1e9 / hbm_gbs
+        fp_frac = flops / t / 1e12 / FP64_PEAK_TFLOPS
+        return {"kernel": "k_spmv_stencil (FP64 values, stencil columns)", "bound": "alu", "achieved": flops / t / 1e12,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": fp_frac, "traffic": None,
+                "peak_source": "derived: 152 SM x 2 DFMA/clk x 2.07 GHz",
+                "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": bytes_,
+                "hbm": {"achieved_gbs": bytes_ / t / 1e9, "peak_gbs": hbm_gbs, "frac": hbm_frac, "peak_source": hbm_src}}
     if cls == "jac_stage1":
         flops = 2.0 * 16 * npair * X * X  # 16 terms x sum of pair points per line x lines (stiffness launch)
     elif cls == "jac_stage2":

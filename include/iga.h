@@ -97,7 +97,9 @@ typedef struct {
  * pattern (Algorithm 2), and the per-quadrature-point geometry factors on the
  * device.  `stream` is a cudaStream_t (NULL: default stream); all library-owned
  * device memory is allocated here with cudaMalloc and freed by iga_destroy.
- * Synchronises the stream before returning.  On failure *out is NULL. */
+ * Synchronises the stream before returning.  On failure *out is NULL.
+ * IGA_EINVAL also for more than 2^28 control variables (int32 column and
+ * thread indices). */
 iga_status iga_create(const iga_desc *desc, const iga_bratu *bratu, void *stream, iga_t *out);
 
 /* IGASetBoundaryValue(iga, axis, side, 0, value) of Sec. 3.2: Dirichlet value on
@@ -144,6 +146,14 @@ iga_status iga_form_residual_noalloc(iga_t iga, const double *U, double *F);
  * (IGA_JAC_TF32, IGA_JAC_BF16). */
 iga_status iga_form_jacobian(iga_t iga, const double *U, void *vals, iga_precision prec);
 
+/* y = J x for CSR values on the library's pattern (the operator product of the
+ * Krylov solvers of Sec. 5; PETSc's MatMult).  vals as written by
+ * iga_form_jacobian: double for IGA_FP64, float for the other precisions (their
+ * values are widened; x, y and the sums are FP64).  x and y: device double[n],
+ * caller-owned, distinct.  Columns are not read: they follow from the stencil
+ * structure of the pattern.  Stream-ordered, deterministic. */
+iga_status iga_apply_jacobian(iga_t iga, const void *vals, iga_precision prec, const double *x, double *y);
+
 /* Newton-Krylov options (SNESSolve of Sec. 3.2; -snes_atol, -ksp_* analogues). */
 typedef struct {
   double atol;         /* stop when ||F||_2 <= atol (default 1e-10) */
@@ -152,8 +162,10 @@ typedef struct {
   int max_krylov;      /* Krylov iteration cap per Newton step (default 4000) */
   double krylov_rtol;  /* forcing term cap; the solve uses min(krylov_rtol, ||F_k||) (default 1e-2) */
   iga_precision jac;   /* Jacobian precision used to steer Newton (default IGA_FP64) */
-  int reuse_stiffness; /* 1: assemble the U-independent part of J once per solve and add
-                          the reaction term each step (default 1); 0: full assembly each step */
+  int reuse_stiffness; /* 1: assemble the U-independent part K of J once per solve and add
+                          the reaction term each step (default 1); with an FP64 Jacobian the
+                          residuals after the first are then K U plus the reaction term
+                          (equal to Eq. (residual) up to rounding); 0: full assembly each step */
   int ksp;             /* Krylov method: IGA_KSP_GMRES (default) or IGA_KSP_CG (Jacobi-
                           preconditioned conjugate gradients, the -ksp_type cg run of App. B;
                           valid because the Jacobian with symmetric Dirichlet rows is symmetric) */

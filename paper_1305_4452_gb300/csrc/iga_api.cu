@@ -253,6 +253,23 @@ extern "C" iga_status iga_form_jacobian(iga_t h, const double *U, void *vals, ig
   return IGA_OK;
 }
 
+extern "C" iga_status iga_apply_jacobian(iga_t h, const void *vals, iga_precision prec, const double *x, double *y) {
+  if (!h) return IGA_EINVAL;
+  if (!vals || !x || !y || x == y) {
+    h->err = "vals, x and y must be non-NULL device pointers, x != y";
+    return IGA_EINVAL;
+  }
+  if (prec == IGA_FP64) {
+    CK(launch_spmv64(h, (const double *)vals, x, y));
+  } else if (prec == IGA_JAC_FP32 || prec == IGA_JAC_TF32 || prec == IGA_JAC_BF16) {
+    CK(launch_spmv32(h, (const float *)vals, x, y));
+  } else {
+    h->err = "unknown precision";
+    return IGA_EINVAL;
+  }
+  return IGA_OK;
+}
+
 extern "C" void iga_newton_defaults(iga_newton_opts *o) {
   if (!o) return;
   o->atol = 1e-10;
@@ -285,7 +302,8 @@ static iga_status ensure_workspace(iga_s *h, int m, bool f32) {
     if (h->ctl) cudaFree(h->ctl);
     h->V = nullptr; h->red = nullptr; h->ctl = nullptr;
     CK(cudaMalloc((void **)&h->V, (size_t)(m + 1) * N * sizeof(double)));
-    CK(cudaMalloc((void **)&h->red, (size_t)(m + 2) * 304 * sizeof(double)));
+    const int nb = gs_partition(N).nb > 304 ? gs_partition(N).nb : 304;
+    CK(cudaMalloc((void **)&h->red, (size_t)(m + 2) * nb * sizeof(double)));
     CK(cudaMalloc((void **)&h->ctl, (size_t)((m + 1) * m + 4 * m + 16) * sizeof(double)));
     h->V_m = m;
   }
@@ -346,6 +364,7 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
   memset(&R, 0, sizeof R);
   R.status = IGA_ENOCONV;
   const bool f32 = o.jac != IGA_FP64;
+  const bool split = !f32 && o.reuse_stiffness != 0;
   iga_status st = ensure_workspace(h, o.gmres_restart, f32);
   if (st != IGA_OK) return st;
   const int64_t N = h->N;
@@ -393,7 +412,9 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
     bool ok = false;
     for (int ls = 0; ls <= 10; ls++) {
       IGA_LAUNCH(h, KC_VEC, (k_axpby<<<eg, 256, 0, h->stream>>>(U, alpha, dU, Ut, N)));
-      CK(launch_residual(h, Ut, Ft));
+      // with the stiffness assembled (FP64), F = K U + reaction(U)
+      if (split) CK(launch_residual_split(h, Ut, Ft, h->Kstiff, h->wk + 7 * N));
+      else CK(launch_residual(h, Ut, Ft));
       st = norm_host(h, Ft, &ft);
       if (st != IGA_OK) return st;
       if (isfinite(ft) && ft < fn) { ok = true; break; }

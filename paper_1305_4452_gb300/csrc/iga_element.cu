@@ -384,15 +384,17 @@ __global__ void __launch_bounds__(128) k_residual(DirArgs d0, DirArgs d1, DirArg
 }
 
 // Gather F_A = sum of the element vectors of the elements containing A
-// (Algorithm 3: F_e -> F), fixed order e2, e1, e0 ascending; Dirichlet rows.
+// (Algorithm 3: F_e -> F), fixed order e2, e1, e0 ascending, added to add[A]
+// when given; Dirichlet rows.
 template <int DIM>
 __global__ void k_gather_residual(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ Fe,
-                                  const double *__restrict__ U, BndArgs bnd, double *__restrict__ F, int64_t N, int N1) {
+                                  const double *__restrict__ U, BndArgs bnd, double *__restrict__ F, int64_t N, int N1,
+                                  const double *__restrict__ add) {
   int64_t A = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (A >= N) return;
   int i0 = (int)(A % d0.n), i1 = (int)((A / d0.n) % d1.n), i2 = (DIM == 3) ? (int)(A / ((int64_t)d0.n * d1.n)) : 0;
   int NEN = (DIM == 3) ? N1 * N1 * N1 : N1 * N1;
-  double acc = 0.0;
+  double acc = add ? add[A] : 0.0;
   int lo2 = (DIM == 3) ? d2.node_e0[i2] : 0, hi2 = (DIM == 3) ? lo2 + d2.node_ne[i2] : 1;
   for (int e2 = lo2; e2 < hi2; e2++) {
     int a2 = (DIM == 3) ? i2 - d2.first[e2] : 0;
@@ -421,7 +423,14 @@ __global__ void k_gather_residual(DirArgs d0, DirArgs d1, DirArgs d2, const doub
 // Q_00 at the Gauss points: sum-factorised value-only interpolation of u~,
 // then Q00 = cs * g^T S g - cr * jw/W^2 * lambda * exp(u~/W).
 // ---------------------------------------------------------------------------
-template <int DIM, int P, int NE>
+//
+// With RES the same interpolation yields the reaction part of the residual
+// instead: s = -jw/W * lambda * exp(u) at the Gauss points, projected back on
+// the element's functions (value tables only) into Fe[e][A] (times w_A).  The
+// Newton solver adds it to K U, K the assembled U-independent stiffness: since
+// Eq. (residual) is K U plus this term under the same quadrature, F(U) then
+// needs one operator product and a quarter of the sum-factorised contractions.
+template <int DIM, int P, int NE, bool RES>
 __global__ void __launch_bounds__(128) k_q00(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ U,
                                              const double *__restrict__ wts, const double *__restrict__ geom, GeomLayout gl,
                                              double lambda, double cs, double cr, double *__restrict__ Q00, int64_t nelem) {
@@ -504,10 +513,85 @@ __global__ void __launch_bounds__(128) k_q00(DirArgs d0, DirArgs d1, DirArgs d2,
       for (int a1 = 0; a1 < N1; a1++) ut = fma(TB(base, 1, g1, a1), Y[a1 * Q + g0], ut);
     }
     const double *rec = geom + (size_t)e * gl.nf * NQ + qp;
+    if (RES) {
+      (base + SM::TAB + NEN)[qp] = -rec[gl.jwW * NQ] * lambda * exp(ut * rec[gl.invW * NQ]);
+      continue;
+    }
     double v = 0.0;
     if (cs != 0.0) v = cs * rec[gl.gSg * NQ];
     if (cr != 0.0) v -= cr * rec[gl.jwW2 * NQ] * lambda * exp(ut * rec[gl.invW * NQ]);
     Q00[(size_t)e * NQ + qp] = v;
+  }
+  if (!RES) return;
+  __syncthreads();
+  // project s on the element's functions: contract axis 2 (3D), then 1, then 0
+  if (DIM == 3) {
+    for (int idx = tid; idx < NE * N1 * Q * Q; idx += nt) {
+      int le = idx / (N1 * Q * Q), r = idx % (N1 * Q * Q);
+      int a2 = r / (Q * Q), g1 = (r / Q) % Q, g0 = r % Q;
+      double *base = smem + (size_t)le * SM::PER;
+      const double *X = base + SM::TAB + NEN;
+      double acc = 0.0;
+#pragma unroll
+      for (int g2 = 0; g2 < Q; g2++) acc = fma(TB(base, 2, g2, a2), X[(g2 * Q + g1) * Q + g0], acc);
+      (base + SM::TAB + NEN + SM::BUF)[r] = acc;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < NE * N1 * N1 * Q; idx += nt) {
+      int le = idx / (N1 * N1 * Q), r = idx % (N1 * N1 * Q);
+      int a2 = r / (N1 * Q), a1 = (r / Q) % N1, g0 = r % Q;
+      double *base = smem + (size_t)le * SM::PER;
+      const double *Y = base + SM::TAB + NEN + SM::BUF;
+      double acc = 0.0;
+#pragma unroll
+      for (int g1 = 0; g1 < Q; g1++) acc = fma(TB(base, 1, g1, a1), Y[(a2 * Q + g1) * Q + g0], acc);
+      (base + SM::TAB + NEN)[r] = acc;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < NE * NEN; idx += nt) {
+      int le = idx / NEN, a = idx % NEN;
+      int64_t e = ebase + le;
+      if (e >= nelem) continue;
+      int a0 = a % N1, a1 = (a / N1) % N1, a2 = a / (N1 * N1);
+      double *base = smem + (size_t)le * SM::PER;
+      const double *Z = base + SM::TAB + NEN;
+      double acc = 0.0;
+#pragma unroll
+      for (int g0 = 0; g0 < Q; g0++) acc = fma(TB(base, 0, g0, a0), Z[(a2 * N1 + a1) * Q + g0], acc);
+      if (wts) {
+        int e0 = (int)(e % d0.nel), e1 = (int)((e / d0.nel) % d1.nel), e2 = (int)(e / ((int64_t)d0.nel * d1.nel));
+        acc *= wts[(d0.first[e0] + a0) + (int64_t)d0.n * ((d1.first[e1] + a1) + (int64_t)d1.n * (d2.first[e2] + a2))];
+      }
+      Q00[(size_t)e * NEN + a] = acc;
+    }
+  } else {
+    for (int idx = tid; idx < NE * N1 * Q; idx += nt) {
+      int le = idx / (N1 * Q), r = idx % (N1 * Q);
+      int a1 = r / Q, g0 = r % Q;
+      double *base = smem + (size_t)le * SM::PER;
+      const double *X = base + SM::TAB + NEN;
+      double acc = 0.0;
+#pragma unroll
+      for (int g1 = 0; g1 < Q; g1++) acc = fma(TB(base, 1, g1, a1), X[g1 * Q + g0], acc);
+      (base + SM::TAB + NEN + SM::BUF)[r] = acc;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < NE * NEN; idx += nt) {
+      int le = idx / NEN, a = idx % NEN;
+      int64_t e = ebase + le;
+      if (e >= nelem) continue;
+      int a0 = a % N1, a1 = a / N1;
+      double *base = smem + (size_t)le * SM::PER;
+      const double *Y = base + SM::TAB + NEN + SM::BUF;
+      double acc = 0.0;
+#pragma unroll
+      for (int g0 = 0; g0 < Q; g0++) acc = fma(TB(base, 0, g0, a0), Y[a1 * Q + g0], acc);
+      if (wts) {
+        int e0 = (int)(e % d0.nel), e1 = (int)(e / d0.nel);
+        acc *= wts[(d0.first[e0] + a0) + (int64_t)d0.n * (d1.first[e1] + a1)];
+      }
+      Q00[(size_t)e * NEN + a] = acc;
+    }
   }
 #undef TB
 }
@@ -582,9 +666,9 @@ cudaError_t launch_residual(iga_s *h, const double *U, double *F) {
   })));
   unsigned g2 = (unsigned)((h->N + 255) / 256);
   if (h->dim == 3)
-    IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<3><<<g2, 256, 0, h->stream>>>(a0, a1, a2, h->Fe, U, h->bnd, F, h->N, h->p + 1)));
+    IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<3><<<g2, 256, 0, h->stream>>>(a0, a1, a2, h->Fe, U, h->bnd, F, h->N, h->p + 1, nullptr)));
   else
-    IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<2><<<g2, 256, 0, h->stream>>>(a0, a1, a2, h->Fe, U, h->bnd, F, h->N, h->p + 1)));
+    IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<2><<<g2, 256, 0, h->stream>>>(a0, a1, a2, h->Fe, U, h->bnd, F, h->N, h->p + 1, nullptr)));
   return cudaGetLastError();
 }
 
@@ -601,9 +685,9 @@ cudaError_t launch_residual_into(iga_s *h, const double *U, double *F, double *F
   })));
   unsigned g2 = (unsigned)((h->N + 255) / 256);
   if (h->dim == 3)
-    IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<3><<<g2, 256, 0, h->stream>>>(a0, a1, a2, Fe, U, h->bnd, F, h->N, h->p + 1)));
+    IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<3><<<g2, 256, 0, h->stream>>>(a0, a1, a2, Fe, U, h->bnd, F, h->N, h->p + 1, nullptr)));
   else
-    IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<2><<<g2, 256, 0, h->stream>>>(a0, a1, a2, Fe, U, h->bnd, F, h->N, h->p + 1)));
+    IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<2><<<g2, 256, 0, h->stream>>>(a0, a1, a2, Fe, U, h->bnd, F, h->N, h->p + 1, nullptr)));
   return cudaGetLastError();
 }
 
@@ -613,9 +697,28 @@ cudaError_t launch_q00(iga_s *h, const double *U, double cs, double cr) {
   unsigned grid = (unsigned)((h->nelem + NE - 1) / NE);
   IGA_LAUNCH(h, KC_Q00, DISPATCH_DP(h->dim, h->p, ({
     size_t sm = res_smem<D, PP>(NE);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_q00<D, PP, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_q00<D, PP, NE><<<grid, 128, sm, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, h->lambda, cs, cr, h->Q00, h->nelem);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_q00<D, PP, NE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_q00<D, PP, NE, false><<<grid, 128, sm, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, h->lambda, cs, cr, h->Q00, h->nelem);
   })));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_split(iga_s *h, const double *U, double *F, const double *K, double *KU) {
+  DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
+  cudaError_t ce = launch_spmv64(h, K, U, KU);
+  if (ce) return ce;
+  constexpr int NE = 4;
+  unsigned grid = (unsigned)((h->nelem + NE - 1) / NE);
+  IGA_LAUNCH(h, KC_RES_ELEM, DISPATCH_DP(h->dim, h->p, ({
+    size_t sm = res_smem<D, PP>(NE);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_q00<D, PP, NE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_q00<D, PP, NE, true><<<grid, 128, sm, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, h->lambda, 0.0, 1.0, h->Fe, h->nelem);
+  })));
+  unsigned g2 = (unsigned)((h->N + 255) / 256);
+  if (h->dim == 3)
+    IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<3><<<g2, 256, 0, h->stream>>>(a0, a1, a2, h->Fe, U, h->bnd, F, h->N, h->p + 1, KU)));
+  else
+    IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<2><<<g2, 256, 0, h->stream>>>(a0, a1, a2, h->Fe, U, h->bnd, F, h->N, h->p + 1, KU)));
   return cudaGetLastError();
 }
 

@@ -290,8 +290,8 @@ iga_status iga_build_dirs(iga_s *h, const iga_desc *d) {
     h->N *= h->dir[ax].n;
     h->nelem *= h->dir[ax].nel;
   }
-  if (h->N > (int64_t)INT32_MAX) {
-    h->err = "too many control variables for int32 column indices";
+  if (h->N > (int64_t)(INT32_MAX / 8)) {  // int32 columns and thread indices (8 lanes per row)
+    h->err = "more than 2^28 control variables";
     return IGA_EINVAL;
   }
   int nq = 1;

@@ -177,9 +177,13 @@ cudaError_t launch_colidx(iga_s *h);
 cudaError_t launch_residual(iga_s *h, const double *U, double *F);
 // Q00 = cs * g^T S g - cr * jw/W^2 * lambda * exp(u) at every Gauss point (U may be null when cr == 0)
 cudaError_t launch_q00(iga_s *h, const double *U, double cs, double cr);
+// F(U) = K U + reaction(U) with Dirichlet rows, K the assembled stiffness without
+// the Dirichlet fix (Jacobian mode 1); KU: scratch of N doubles
+cudaError_t launch_residual_split(iga_s *h, const double *U, double *F, const double *K, double *KU);
 
 // ---- Jacobian stages (iga_jacobian.cu) ----
-// mode 0: full Jacobian; 1: stiffness only (U-independent); 2: vals = base + reaction(U)
+// mode 0: full Jacobian; 1: stiffness only (U-independent), without the Dirichlet
+// fix; 2: vals = base + reaction(U) with the Dirichlet fix (base from mode 1)
 cudaError_t launch_jacobian64(iga_s *h, const double *U, double *vals, int mode, const double *base);
 cudaError_t launch_jacobian32(iga_s *h, const double *U, float *vals, int mode, const float *base);
 size_t jacobian_t1_groups(int dim);
@@ -189,6 +193,11 @@ cudaError_t launch_jacobian_mixed(iga_s *h, const double *U, float *vals, int pr
 size_t jacobian_t2_groups(int dim);
 
 // ---- Krylov (iga_krylov.cu) ----
+// Row partition of the Gram-Schmidt passes: nb blocks of per rows (the last may be shorter)
+struct GsPartition {
+  int nb, per;
+};
+GsPartition gs_partition(int64_t N);
 cudaError_t launch_spmv64(iga_s *h, const double *vals, const double *x, double *y);
 cudaError_t launch_spmv32(iga_s *h, const float *vals, const double *x, double *y);
 cudaError_t launch_diag_inv(iga_s *h, const void *vals, int is_f32, double *dinv);

@@ -173,9 +173,8 @@ __device__ __forceinline__ bool on_dirichlet(const BndArgs &b, int dim, const in
 // Final stage: contract the last axis and write the CSR entries.
 //   3D: in = T2[g2][x2][pi1][pi0];  J = P^00 H0 + P^10 H1 + P^01 H1^T + P^11 H2
 //   2D: in = T1[g1][x1][pi0];       J = P^00 G0 + P^10 G1 + P^01 G1^T + P^11 G2
-// fix = 1: Dirichlet rows become identity rows and Dirichlet columns zero;
-// fix = 2: vals = base + contribution, with no contribution in Dirichlet rows or
-//          columns (the base -- a stiffness assembled with fix = 1 -- holds them).
+// vals = base + contribution (base optional).  fix = 1: entries in Dirichlet rows
+// or columns become those of an identity row and a zeroed column instead.
 template <typename T, typename V, int DIM, int PLAN>
 __global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d2, const T *__restrict__ in, CsrArgs csr,
                                                V *__restrict__ vals, const V *__restrict__ base, int chunk, int fix) {
@@ -237,11 +236,10 @@ __global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d
     }
     double v = (double)acc;
     if (csr.wts) v *= csr.wts[A] * csr.wts[B];
-    if (fix) {
-      bool ra = on_dirichlet(csr.bnd, DIM, I, n), cb = on_dirichlet(csr.bnd, DIM, J, n);
-      if (ra || cb) v = (fix == 1 && A == B) ? 1.0 : 0.0;
-    }
-    vals[pos] = base ? (V)((double)base[pos] + v) : (V)v;
+    if (fix && (on_dirichlet(csr.bnd, DIM, I, n) || on_dirichlet(csr.bnd, DIM, J, n)))
+      vals[pos] = (V)(A == B ? 1.0 : 0.0);  // identity row, zeroed column
+    else
+      vals[pos] = base ? (V)((double)base[pos] + v) : (V)v;
   }
 }
 
@@ -290,15 +288,17 @@ cudaError_t run_stages(iga_s *h, V *vals, const V *base, int fix) {
 
 template <typename T, typename V>
 cudaError_t jacobian(iga_s *h, const double *U, V *vals, int mode, const V *base) {
-  // mode 0: full; 1: stiffness only (U-independent); 2: base + reaction
+  // mode 0: full, Dirichlet-fixed; 1: stiffness only (U-independent), unfixed;
+  // 2: base (a mode-1 stiffness) + reaction, Dirichlet-fixed
   double cs = (mode == 2) ? 0.0 : 1.0, cr = (mode == 1) ? 0.0 : 1.0;
   cudaError_t ce = launch_q00(h, U, cs, cr);
   if (ce) return ce;
   if (mode == 2) {
     if (!base) return cudaErrorInvalidValue;
-    return h->dim == 3 ? run_stages<T, V, 3, PLAN_MASS>(h, vals, base, 2) : run_stages<T, V, 2, PLAN_MASS>(h, vals, base, 2);
+    return h->dim == 3 ? run_stages<T, V, 3, PLAN_MASS>(h, vals, base, 1) : run_stages<T, V, 2, PLAN_MASS>(h, vals, base, 1);
   }
-  return h->dim == 3 ? run_stages<T, V, 3, PLAN_STIFF>(h, vals, nullptr, 1) : run_stages<T, V, 2, PLAN_STIFF>(h, vals, nullptr, 1);
+  const int fix = (mode == 1) ? 0 : 1;
+  return h->dim == 3 ? run_stages<T, V, 3, PLAN_STIFF>(h, vals, nullptr, fix) : run_stages<T, V, 2, PLAN_STIFF>(h, vals, nullptr, fix);
 }
 
 }  // namespace

@@ -56,40 +56,82 @@ __device__ double block_sum(double v, double *sh) {
   return r;
 }
 
-template <typename V, int LPR>
-__global__ void __launch_bounds__(256) k_spmv(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                                              const V *__restrict__ val, const double *__restrict__ x,
-                                              double *__restrict__ y, int64_t N, const double *__restrict__ done) {
-  if (done && done[0] != 0.0) return;
-  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t row = gid / LPR;
-  int lane = threadIdx.x % LPR;
-  if (row >= N) return;
-  int64_t a = rowptr[row], b = rowptr[row + 1];
-  double acc = 0.0;
-  for (int64_t k = a + lane; k < b; k += LPR) acc = fma((double)val[k], x[col[k]], acc);
-#pragma unroll
-  for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, LPR);
-  if (lane == 0) y[row] = acc;
+// The CSR pattern is the stencil product of Sec. 4: the columns of row
+// A = (i0, i1, i2) are the lexicographic product of the 1D BasisStencil ranges
+// [l_d(i_d), r_d(i_d)], ascending.  The column of every stored value therefore
+// follows from its position in the row, and the operator product streams the
+// values and gathers x without reading column indices (8 instead of 12 bytes
+// per FP64 nonzero, 4 instead of 8 per FP32 one).
+struct StencilRows {
+  int n0, n01;                 // functions along axis 0, along axes 0 and 1
+  const int *l0, *r0, *l1, *r1, *l2, *r2;
+};
+
+struct RowShape {
+  int lo0, w0, lo1, w1, lo2, w2;
+};
+
+template <int DIM>
+__device__ __forceinline__ RowShape row_shape(const StencilRows &S, int row) {
+  int i0, i1, i2 = 0;
+  if (DIM == 3) {
+    i2 = row / S.n01;
+    int t = row - i2 * S.n01;
+    i1 = t / S.n0;
+    i0 = t - i1 * S.n0;
+  } else {
+    i1 = row / S.n0;
+    i0 = row - i1 * S.n0;
+  }
+  RowShape R;
+  R.lo0 = S.l0[i0];
+  R.w0 = S.r0[i0] - R.lo0 + 1;
+  R.lo1 = S.l1[i1];
+  R.w1 = S.r1[i1] - R.lo1 + 1;
+  R.lo2 = 0;
+  R.w2 = 1;
+  if (DIM == 3) {
+    R.lo2 = S.l2[i2];
+    R.w2 = S.r2[i2] - R.lo2 + 1;
+  }
+  return R;
 }
 
-// y = J x with FP32 values and an FP32 copy of x, accumulated in FP32 (the
-// reduced-precision Jacobian only steers Newton; vectors stay FP64 outside).
-template <int LPR>
-__global__ void __launch_bounds__(256) k_spmv_f32(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                                                  const float *__restrict__ val, const float *__restrict__ x,
-                                                  double *__restrict__ y, int64_t N, const double *__restrict__ done) {
+// y = A x over the stencil CSR, LPR lanes per row.  Lane t of a row takes the
+// row's entries t, t+LPR, ...; the column is advanced incrementally (a run of w0
+// consecutive columns per (i1, i2) offset).  Every lane reaches the shuffles.
+template <int DIM, int LPR, typename V, typename X, typename ACC>
+__global__ void __launch_bounds__(256) k_spmv_stencil(StencilRows S, const int64_t *__restrict__ rowptr,
+                                                      const V *__restrict__ val, const X *__restrict__ x,
+                                                      double *__restrict__ y, int N, const double *__restrict__ done) {
   if (done && done[0] != 0.0) return;
-  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t row = gid / LPR;
-  int lane = threadIdx.x % LPR;
-  if (row >= N) return;
-  int64_t a = rowptr[row], b = rowptr[row + 1];
-  float acc = 0.f;
-  for (int64_t k = a + lane; k < b; k += LPR) acc = fmaf(val[k], x[col[k]], acc);
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = gid / LPR, lane = gid % LPR;
+  ACC acc = 0;
+  if (row < N) {
+    const RowShape R = row_shape<DIM>(S, row);
+    const int cnt = R.w0 * R.w1 * R.w2;
+    const V *v = val + rowptr[row];
+    int ii = lane, jj = 0, kk = 0;
+    while (ii >= R.w0) { ii -= R.w0; jj++; }
+    while (jj >= R.w1) { jj -= R.w1; kk++; }
+    int col = (R.lo0 + ii) + (R.lo1 + jj) * S.n0 + (R.lo2 + kk) * S.n01;
+    const int djj = S.n0 - R.w0, dkk = S.n01 - R.w1 * S.n0;
+#pragma unroll 4
+    for (int e = lane; e < cnt; e += LPR) {
+      acc = fma((ACC)v[e], (ACC)x[col], acc);
+      ii += LPR;
+      col += LPR;
+      while (ii >= R.w0) {
+        ii -= R.w0;
+        col += djj;
+        if (++jj == R.w1) { jj = 0; col += dkk; }
+      }
+    }
+  }
 #pragma unroll
   for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, LPR);
-  if (lane == 0) y[row] = (double)acc;
+  if (row < N && lane == 0) y[row] = (double)acc;
 }
 
 __global__ void k_cvt_f32(const double *__restrict__ x, float *__restrict__ y, int64_t N, const double *__restrict__ done) {
@@ -97,20 +139,19 @@ __global__ void k_cvt_f32(const double *__restrict__ x, float *__restrict__ y, i
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) y[i] = (float)x[i];
 }
 
-template <typename V>
-__global__ void k_diag_inv(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col, const V *__restrict__ val,
-                           double *__restrict__ dinv, int64_t N) {
-  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (r >= N) return;
-  int64_t lo = rowptr[r], hi = rowptr[r + 1] - 1;
-  double d = 0.0;
-  while (lo <= hi) {  // columns ascend: binary search for the diagonal
-    int64_t mid = (lo + hi) >> 1;
-    int c = col[mid];
-    if (c == r) { d = (double)val[mid]; break; }
-    if (c < r) lo = mid + 1; else hi = mid - 1;
-  }
-  dinv[r] = (d != 0.0) ? 1.0 / d : 1.0;
+// dinv = 1 / diag(A); the diagonal's position in row A follows from the stencil
+template <int DIM, typename V>
+__global__ void k_diag_stencil(StencilRows S, const int64_t *__restrict__ rowptr, const V *__restrict__ val,
+                               double *__restrict__ dinv, int N) {
+  int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= N) return;
+  const RowShape R = row_shape<DIM>(S, row);
+  int i2 = (DIM == 3) ? row / S.n01 : 0;
+  int t = row - i2 * S.n01;
+  int i1 = t / S.n0, i0 = t - i1 * S.n0;
+  int pos = (i0 - R.lo0) + R.w0 * ((i1 - R.lo1) + R.w1 * (DIM == 3 ? i2 - R.lo2 : 0));
+  double d = (double)val[rowptr[row] + pos];
+  dinv[row] = (d != 0.0) ? 1.0 / d : 1.0;
 }
 
 // partial[blk] = sum over the block's fixed row range of x*y
@@ -126,22 +167,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot_partial(const double *__res
   if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
-// multi-dot: partial[i][blk] = sum_r V[i][r] w[r], i = 0..j (grid.y = j+1)
-__global__ void __launch_bounds__(RED_THREADS) k_mdot_partial(const double *__restrict__ Vb, int64_t ld,
-                                                              const double *__restrict__ w, double *__restrict__ partial,
-                                                              int64_t N, const double *__restrict__ done) {
-  __shared__ double sh[32];
-  if (done[0] != 0.0) return;
-  int i = blockIdx.y;
-  const double *v = Vb + (size_t)i * ld;
-  int64_t per = (N + gridDim.x - 1) / gridDim.x;
-  int64_t a = blockIdx.x * per, b = min(N, a + per);
-  double acc = 0.0;
-  for (int64_t r = a + threadIdx.x; r < b; r += blockDim.x) acc = fma(v[r], w[r], acc);
-  acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) partial[(size_t)i * gridDim.x + blockIdx.x] = acc;
-}
-
 // out[i] (+)= sum_blk partial[i][blk] in index order (one block per i)
 __global__ void __launch_bounds__(RED_THREADS) k_reduce_rows(const double *__restrict__ partial, int nb, double *__restrict__ out,
                                                              int accumulate, const double *__restrict__ done) {
@@ -154,17 +179,71 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_rows(const double *__res
   if (threadIdx.x == 0) out[i] = accumulate ? out[i] + acc : acc;
 }
 
-// w -= sum_{i<=j} h[i] V[i]
-__global__ void k_orth_update(const double *__restrict__ Vb, int64_t ld, const double *__restrict__ h, int jp1,
-                              double *__restrict__ w, int64_t N, const double *__restrict__ done) {
-  __shared__ double hs[1024];
+// Classical Gram-Schmidt passes over a block-contiguous row partition: block b
+// owns rows [b*per, min(N, (b+1)*per)).  With UPDATE the block first applies
+// w -= sum_i h[i] V[i] on its rows; then (DOTS) every warp takes basis vectors
+// i = warp, warp+8, ... and writes partial[i][b] = sum over the block's rows of
+// V[i][r] w[r], with w read from shared memory, or (NORM) the block writes
+// partial[b] = sum of w[r]^2.  One pass reads the active basis once; the fixed
+// partition and fixed shuffle/smem trees keep every sum independent of timing.
+template <bool UPDATE, bool NORM>
+__global__ void __launch_bounds__(RED_THREADS) k_gs_pass(const double *__restrict__ Vb, int64_t ld, int jp1,
+                                                         const double *__restrict__ h, double *__restrict__ w,
+                                                         double *__restrict__ partial, int64_t N, int per,
+                                                         const double *__restrict__ done) {
+  extern __shared__ double gs_sm[];
+  double *ws = gs_sm;          // [per]
+  double *hs = gs_sm + per;    // [jp1]
+  __shared__ double sh[32];
   if (done[0] != 0.0) return;
-  for (int i = threadIdx.x; i < jp1; i += blockDim.x) hs[i] = h[i];
+  const int64_t a = (int64_t)blockIdx.x * per;
+  const int cnt = (int)max((int64_t)0, min((int64_t)per, N - a));
+  if (UPDATE) {
+    for (int i = threadIdx.x; i < jp1; i += blockDim.x) hs[i] = h[i];
+    __syncthreads();
+  }
+  double sq = 0.0;
+  for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+    double v = w[a + r];
+    if (UPDATE) {
+      const double *col = Vb + a + r;
+#pragma unroll 4
+      for (int i = 0; i < jp1; i++) v = fma(-hs[i], col[(size_t)i * ld], v);
+      w[a + r] = v;
+    }
+    if (NORM) sq = fma(v, v, sq);
+    else ws[r] = v;
+  }
+  if (NORM) {
+    sq = block_sum(sq, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = sq;
+    return;
+  }
   __syncthreads();
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x) {
-    double acc = w[r];
-    for (int i = 0; i < jp1; i++) acc = fma(-hs[i], Vb[(size_t)i * ld + r], acc);
-    w[r] = acc;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < jp1; i += nw) {
+    const double *v = Vb + (size_t)i * ld + a;
+    double acc = 0.0;
+#pragma unroll 4
+    for (int r = lane; r < cnt; r += 32) acc = fma(v[r], ws[r], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) partial[(size_t)i * gridDim.x + blockIdx.x] = acc;
+  }
+}
+
+// out[i] = sum_blk partial[i][blk] in index order, and add[i] += out[i] when add
+// is given (the second Gram-Schmidt pass's correction to column j of H)
+__global__ void __launch_bounds__(RED_THREADS) k_reduce_rows_add(const double *__restrict__ partial, int nb, double *__restrict__ out,
+                                                                 double *__restrict__ add, const double *__restrict__ done) {
+  __shared__ double sh[32];
+  if (done[0] != 0.0) return;
+  int i = blockIdx.x;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) acc += partial[(size_t)i * nb + k];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    out[i] = acc;
+    if (add) add[i] += acc;
   }
 }
 
@@ -181,14 +260,8 @@ __global__ void k_normalize(const double *w, const double *__restrict__ hn, doub
   }
 }
 
-// h[i] += d[i] for i < n (one block)
-__global__ void k_add_vec(double *__restrict__ h, const double *__restrict__ d, int n, const double *__restrict__ done) {
-  if (done[0] != 0.0) return;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) h[i] += d[i];
-}
-
 // Givens step for column j of H (one thread)
-__global__ void k_givens(double *__restrict__ gm, int m, int j, double tol) {
+__device__ void givens_step(double *__restrict__ gm, int m, int j, double tol) {
   GmLayout L = gm_layout(m);
   double *fl = gm + L.flags;
   if (fl[0] != 0.0) return;
@@ -220,6 +293,24 @@ __global__ void k_givens(double *__restrict__ gm, int m, int j, double tol) {
   if (res <= tol || breakdown || j + 1 == m) fl[0] = 1.0;
   // keep the norm for the normalisation kernel
   fl[4] = hn;
+}
+
+__global__ void k_givens(double *__restrict__ gm, int m, int j, double tol) { givens_step(gm, m, j, tol); }
+
+// H[j+1][j] (as a sum of squares) = sum of the norm partials in index order,
+// then the Givens step for column j (one block)
+__global__ void __launch_bounds__(RED_THREADS) k_reduce_givens(const double *__restrict__ partial, int nb, double *__restrict__ gm,
+                                                               int m, int j, double tol) {
+  __shared__ double sh[32];
+  GmLayout L = gm_layout(m);
+  if (gm[L.flags] != 0.0) return;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) acc += partial[k];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    gm[L.H + (size_t)j * (m + 1) + j + 1] = acc;
+    givens_step(gm, m, j, tol);
+  }
 }
 
 // solve the k x k upper triangular system H y = g (one thread); k = fl[1]
@@ -292,13 +383,30 @@ static int grid_for(int64_t N, int threads, int cap) {
   return (int)g;
 }
 
-// FP32-value operator product used by the mixed-precision Newton: x -> FP32 copy, FP32 SpMV
+static StencilRows stencil_rows(const iga_s *h) {
+  StencilRows S;
+  S.n0 = h->dir[0].n;
+  S.n01 = h->dir[0].n * h->dir[1].n;
+  S.l0 = h->ddev[0].l; S.r0 = h->ddev[0].r;
+  S.l1 = h->ddev[1].l; S.r1 = h->ddev[1].r;
+  S.l2 = h->dim == 3 ? h->ddev[2].l : nullptr;
+  S.r2 = h->dim == 3 ? h->ddev[2].r : nullptr;
+  return S;
+}
+
+// FP32-value operator product used by the mixed-precision Newton: x -> FP32 copy,
+// FP32 SpMV (8 lanes x 4 B = one 32 B sector per row and step)
 static cudaError_t spmv_f32_launch(iga_s *h, const float *vals, const double *x, double *y, const double *done) {
   int eg = (int)((h->N + 255) / 256);
   if (eg > 608) eg = 608;
   IGA_LAUNCH(h, KC_VEC, (k_cvt_f32<<<eg, 256, 0, h->stream>>>(x, h->z32, h->N, done)));
-  unsigned grid = (unsigned)((h->N * 8 + 255) / 256);
-  IGA_LAUNCH(h, KC_SPMV, (k_spmv_f32<8><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, h->z32, y, h->N, done)));
+  const StencilRows S = stencil_rows(h);
+  const int N = (int)h->N;
+  unsigned grid = (unsigned)(((int64_t)N * 8 + 255) / 256);
+  if (h->dim == 3)
+    IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<3, 8, float, float, float><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, h->z32, y, N, done)));
+  else
+    IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<2, 8, float, float, float><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, h->z32, y, N, done)));
   return cudaGetLastError();
 }
 
@@ -307,14 +415,13 @@ static cudaError_t spmv_launch(iga_s *h, const V *vals, const double *x, double 
   // Few lanes per row: the cross-lane reduction costs log2(LPR) FP64 adds on every
   // lane of the group, which on GB300's narrow FP64 pipe is not free; 4 lanes keep
   // the loads sector-efficient (4 x 8 B contiguous per row and step).
-  double avg = (double)h->nnz / (double)h->N;
-  int lpr = avg >= 8 ? 4 : 2;
-  int64_t threads = h->N * lpr;
-  unsigned grid = (unsigned)((threads + 255) / 256);
-  switch (lpr) {
-    case 4: IGA_LAUNCH(h, KC_SPMV, (k_spmv<V, 4><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, x, y, h->N, done))); break;
-    default: IGA_LAUNCH(h, KC_SPMV, (k_spmv<V, 2><<<grid, 256, 0, h->stream>>>(h->rowptr, h->colidx, vals, x, y, h->N, done))); break;
-  }
+  const StencilRows S = stencil_rows(h);
+  const int N = (int)h->N;
+  unsigned grid = (unsigned)(((int64_t)N * 4 + 255) / 256);
+  if (h->dim == 3)
+    IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<3, 4, V, double, double><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, x, y, N, done)));
+  else
+    IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<2, 4, V, double, double><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, x, y, N, done)));
   return cudaGetLastError();
 }
 
@@ -322,10 +429,29 @@ cudaError_t launch_spmv64(iga_s *h, const double *vals, const double *x, double 
 cudaError_t launch_spmv32(iga_s *h, const float *vals, const double *x, double *y) { return spmv_launch<float>(h, vals, x, y, nullptr); }
 
 cudaError_t launch_diag_inv(iga_s *h, const void *vals, int is_f32, double *dinv) {
-  unsigned g = (unsigned)((h->N + 255) / 256);
-  if (is_f32) IGA_LAUNCH(h, KC_VEC, (k_diag_inv<float><<<g, 256, 0, h->stream>>>(h->rowptr, h->colidx, (const float *)vals, dinv, h->N)));
-  else IGA_LAUNCH(h, KC_VEC, (k_diag_inv<double><<<g, 256, 0, h->stream>>>(h->rowptr, h->colidx, (const double *)vals, dinv, h->N)));
+  const StencilRows S = stencil_rows(h);
+  const int N = (int)h->N;
+  unsigned g = (unsigned)((N + 255) / 256);
+  if (h->dim == 3) {
+    if (is_f32) IGA_LAUNCH(h, KC_VEC, (k_diag_stencil<3, float><<<g, 256, 0, h->stream>>>(S, h->rowptr, (const float *)vals, dinv, N)));
+    else IGA_LAUNCH(h, KC_VEC, (k_diag_stencil<3, double><<<g, 256, 0, h->stream>>>(S, h->rowptr, (const double *)vals, dinv, N)));
+  } else {
+    if (is_f32) IGA_LAUNCH(h, KC_VEC, (k_diag_stencil<2, float><<<g, 256, 0, h->stream>>>(S, h->rowptr, (const float *)vals, dinv, N)));
+    else IGA_LAUNCH(h, KC_VEC, (k_diag_stencil<2, double><<<g, 256, 0, h->stream>>>(S, h->rowptr, (const double *)vals, dinv, N)));
+  }
   return cudaGetLastError();
+}
+
+GsPartition gs_partition(int64_t N) {
+  // at least 4 blocks per SM; at most 2048 rows (16 KB of shared memory) per block
+  GsPartition g;
+  int64_t nb = (N + 2047) / 2048;
+  if (nb < 4 * 152) nb = 4 * 152;
+  g.per = (int)((N + nb - 1) / nb);
+  if (g.per < 1) g.per = 1;
+  g.nb = (int)((N + g.per - 1) / g.per);
+  if (g.nb < 1) g.nb = 1;
+  return g;
 }
 
 // out_dev[0] = sum x^2 (deterministic)
@@ -361,6 +487,7 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
   int total = 0, rc = 1;
   *cerr = cudaSuccess;
   int eg = grid_for(N, 256, 4 * 152);
+  const GsPartition gs = gs_partition(N);
   launch_diag_inv(h, vals, is_f32, dinv);
   IGA_LAUNCH(h, KC_VEC, (k_fill<<<eg, 256, 0, h->stream>>>(x, 0.0, N)));
   const int batch = 8;
@@ -385,18 +512,15 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
         double *Hj = gm + L.H + (size_t)j * (m + 1);
         if (is_f32) spmv_f32_launch(h, (const float *)vals, z, w, done);
         else spmv_launch<double>(h, (const double *)vals, z, w, done);
-        // classical Gram-Schmidt, applied twice
-        dim3 gd(RED_BLOCKS, j + 1);
-        IGA_LAUNCH(h, KC_ORTH, (k_mdot_partial<<<gd, RED_THREADS, 0, h->stream>>>(Vb, ld, w, h->red, N, done)));
-        IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce_rows<<<j + 1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, Hj, 0, done)));
-        IGA_LAUNCH(h, KC_ORTH, (k_orth_update<<<eg, 256, 0, h->stream>>>(Vb, ld, Hj, j + 1, w, N, done)));
-        IGA_LAUNCH(h, KC_ORTH, (k_mdot_partial<<<gd, RED_THREADS, 0, h->stream>>>(Vb, ld, w, h->red, N, done)));
-        IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce_rows<<<j + 1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, h2, 0, done)));
-        IGA_LAUNCH(h, KC_ORTH, (k_orth_update<<<eg, 256, 0, h->stream>>>(Vb, ld, h2, j + 1, w, N, done)));
-        IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_add_vec<<<1, 256, 0, h->stream>>>(Hj, h2, j + 1, done)));
-        IGA_LAUNCH(h, KC_VEC, (k_dot_partial<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(w, w, h->red, N, done)));
-        IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce_rows<<<1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, Hj + j + 1, 0, done)));
-        IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_givens<<<1, 1, 0, h->stream>>>(gm, m, j, tol_abs)));
+        // classical Gram-Schmidt, applied twice: dots; update + dots; update + norm
+        const int jp1 = j + 1;
+        const size_t smem = (size_t)(gs.per + jp1) * sizeof(double);
+        IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<false, false><<<gs.nb, RED_THREADS, smem, h->stream>>>(Vb, ld, jp1, nullptr, w, h->red, N, gs.per, done)));
+        IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce_rows_add<<<jp1, RED_THREADS, 0, h->stream>>>(h->red, gs.nb, Hj, nullptr, done)));
+        IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<true, false><<<gs.nb, RED_THREADS, smem, h->stream>>>(Vb, ld, jp1, Hj, w, h->red, N, gs.per, done)));
+        IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce_rows_add<<<jp1, RED_THREADS, 0, h->stream>>>(h->red, gs.nb, h2, Hj, done)));
+        IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<true, true><<<gs.nb, RED_THREADS, smem, h->stream>>>(Vb, ld, jp1, h2, w, h->red, N, gs.per, done)));
+        IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce_givens<<<1, RED_THREADS, 0, h->stream>>>(h->red, gs.nb, gm, m, j, tol_abs)));
         // the next basis vector is formed unless this was the last column
         IGA_LAUNCH(h, KC_VEC, (k_normalize<<<eg, 256, 0, h->stream>>>(w, gm + L.flags + 4, Vb + (size_t)(j + 1) * ld, dinv, z, N, gm + L.flags)));
       }

@@ -24,7 +24,7 @@ EXPORTS = ["iga_create", "iga_set_boundary_value", "iga_set_lambda", "iga_get_pa
            "iga_batch_create", "iga_batch_offsets", "iga_batch_set_launch", "iga_batch_solve", "iga_batch_destroy",
            "iga_batch_last_error", "iga_nn_create", "iga_nn_num_params", "iga_nn_get_params", "iga_nn_set_params",
            "iga_nn_forward", "iga_nn_loss_grad", "iga_nn_adam_step", "iga_nn_destroy", "iga_nn_last_error",
-           "iga_nn_set_h1_weight"]
+           "iga_nn_set_h1_weight", "iga_apply_jacobian"]
 
 KERNEL_CLASSES = ["geometry", "residual_element", "residual_gather", "q00", "jac_stage1", "jac_stage2", "jac_final",
                   "spmv", "gs_orth", "gmres_scalar", "vector", "combine", "pattern", "elem_tc", "elem_gather"]
@@ -97,6 +97,7 @@ def lib():
         L.iga_get_pattern.argtypes = [vp, i64p, i64p, ctypes.POINTER(vp), ctypes.POINTER(vp)]
         L.iga_form_residual.argtypes = [vp, vp, vp]
         L.iga_form_jacobian.argtypes = [vp, vp, vp, ctypes.c_int]
+        L.iga_apply_jacobian.argtypes = [vp, vp, ctypes.c_int, vp, vp]
         L.iga_form_residual_noalloc.argtypes = [vp, vp, vp]
         L.iga_newton_defaults.argtypes = [ctypes.POINTER(IgaNewtonOpts)]
         L.iga_newton_defaults.restype = None
@@ -232,6 +233,17 @@ class Discretization:
             vals = torch.empty(self.nnz, dtype=torch.float64 if prec == IGA_FP64 else torch.float32, device=U.device)
         _check(lib().iga_form_jacobian(self.h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(vals.data_ptr()), int(prec)), self.h)
         return vals
+
+    def apply_jacobian(self, vals, x, y=None, prec=None):
+        """y = J x for CSR values `vals` on the library's pattern (FP64 or FP32 values)."""
+        import torch
+        if prec is None:
+            prec = IGA_FP64 if vals.dtype == torch.float64 else IGA_JAC_FP32
+        if y is None:
+            y = torch.empty_like(x)
+        _check(lib().iga_apply_jacobian(self.h, ctypes.c_void_p(vals.data_ptr()), int(prec), ctypes.c_void_p(x.data_ptr()),
+                                        ctypes.c_void_p(y.data_ptr())), self.h)
+        return y
 
     def solve_newton(self, U, opts=None, check=True):
         o = opts if opts is not None else newton_defaults()
