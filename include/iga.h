@@ -238,11 +238,16 @@ const char *iga_batch_last_error(iga_batch_t batch);
  * An L-layer network of 3x3 convolutions (dilation dilations[l], zero padding) on
  * an height x width grid, in_channels inputs per grid point, `hidden` channels
  * between layers, SiLU activations and one linear output channel multiplied by a
- * mask.  Forward, input- and weight-gradient convolutions run as BF16 x BF16 ->
- * FP32 tensor-core GEMMs; master weights, gradients, Adam moments and the loss are
- * FP32.  Parameters: a flat FP32 vector, per layer W[cout][3][3][cin] then
- * b[cout].  Inputs are NHWC FP32 device arrays; batch size <= max_batch.
- * iga_nn_create allocates all device memory; weights are He-uniform from `seed`. */
+ * mask.  Forward and input-gradient convolutions run as implicit GEMMs on the
+ * tcgen05 tensor cores, weight gradients as im2col + mma.sync GEMMs, all BF16 x
+ * BF16 -> FP32; master weights, gradients, Adam moments and the loss are FP32.
+ * Parameters: a flat FP32 vector, per layer W[cout][3][3][cin] then b[cout].
+ * Inputs are NHWC FP32 device arrays; batch size <= max_batch.  Shapes:
+ * in_channels 1..16, hidden 16, 32 or 64, 2..16 layers, max_batch*height*width
+ * <= 2^28; anything else is IGA_EINVAL before any device work.  iga_nn_create
+ * allocates all device memory; weights are He-uniform from `seed`.
+ * iga_nn_forward and iga_nn_loss_grad synchronise the stream; IGA_ETIMEOUT if a
+ * tensor-core pipeline wait gave up (the call's outputs are then invalid). */
 typedef struct iga_nn_s *iga_nn_t;
 iga_status iga_nn_create(int height, int width, int in_channels, int hidden, int layers, const int *dilations,
                          int max_batch, uint64_t seed, void *stream, iga_nn_t *out);

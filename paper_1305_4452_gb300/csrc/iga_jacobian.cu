@@ -175,6 +175,9 @@ __device__ __forceinline__ bool on_dirichlet(const BndArgs &b, int dim, const in
 //   2D: in = T1[g1][x1][pi0];       J = P^00 G0 + P^10 G1 + P^01 G1^T + P^11 G2
 // vals = base + contribution (base optional).  fix = 1: entries in Dirichlet rows
 // or columns become those of an identity row and a zeroed column instead.
+// J is symmetric (Q is), so only the entries whose pair triple (pl, pmid, pi0)
+// is not above its transpose (plT, pmidT, pi0T) in lexicographic order are
+// contracted; each value is written at (A, B) and at (B, A).
 template <typename T, typename V, int DIM, int PLAN>
 __global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d2, const T *__restrict__ in, CsrArgs csr,
                                                V *__restrict__ vals, const V *__restrict__ base, int chunk, int fix) {
@@ -187,14 +190,18 @@ __global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d
   const int pi0T = d0.pair_T[pi0];
   const int i0 = d0.pair_i[pi0], j0 = d0.pair_j[pi0];
   const int o0 = pi0 - d0.pair_off[i0], w0 = d0.r[i0] - d0.l[i0] + 1;
-  int i1 = 0, j1 = 0, o1 = 0, w1 = 1, pmidT = 0;
+  const int o0T = pi0T - d0.pair_off[j0], w0T = d0.r[j0] - d0.l[j0] + 1;
+  int i1 = 0, j1 = 0, o1 = 0, w1 = 1, pmidT = 0, o1T = 0, w1T = 1;
   if (DIM == 3) {
     i1 = d1.pair_i[pmid]; j1 = d1.pair_j[pmid];
     o1 = pmid - d1.pair_off[i1]; w1 = d1.r[i1] - d1.l[i1] + 1;
     pmidT = d1.pair_T[pmid];
+    o1T = pmidT - d1.pair_off[j1]; w1T = d1.r[j1] - d1.l[j1] + 1;
   }
   const T *tab = ptab<T>(dl);
   for (int pl = pa; pl < pb; pl++) {
+    const int plT = dl.pair_T[pl];
+    if (pl > plT || (pl == plT && (pmid > pmidT || (pmid == pmidT && pi0 > pi0T)))) continue;
     const int xs = dl.pair_x0[pl], np = dl.pair_np[pl];
     const T *pv = tab + (size_t)dl.pair_po[pl] * IGA_PVS;
     T acc = 0;
@@ -220,26 +227,32 @@ __global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d
       }
     }
     const int il = dl.pair_i[pl], jl = dl.pair_j[pl];
-    const int ol = pl - dl.pair_off[il];
+    const int ol = pl - dl.pair_off[il], olT = plT - dl.pair_off[jl];
     int I[3], J[3], n[3] = {d0.n, d1.n, d2.n};
-    int64_t A, B, pos;
+    int64_t A, B, pos, posT;
     if (DIM == 3) {
       I[0] = i0; I[1] = i1; I[2] = il; J[0] = j0; J[1] = j1; J[2] = jl;
       A = i0 + (int64_t)d0.n * (i1 + (int64_t)d1.n * il);
       B = j0 + (int64_t)d0.n * (j1 + (int64_t)d1.n * jl);
       pos = csr.rowptr[A] + ((int64_t)ol * w1 + o1) * w0 + o0;
+      posT = csr.rowptr[B] + ((int64_t)olT * w1T + o1T) * w0T + o0T;
     } else {
       I[0] = i0; I[1] = il; J[0] = j0; J[1] = jl;
       A = i0 + (int64_t)d0.n * il;
       B = j0 + (int64_t)d0.n * jl;
       pos = csr.rowptr[A] + (int64_t)ol * w0 + o0;
+      posT = csr.rowptr[B] + (int64_t)olT * w0T + o0T;
     }
     double v = (double)acc;
     if (csr.wts) v *= csr.wts[A] * csr.wts[B];
-    if (fix && (on_dirichlet(csr.bnd, DIM, I, n) || on_dirichlet(csr.bnd, DIM, J, n)))
-      vals[pos] = (V)(A == B ? 1.0 : 0.0);  // identity row, zeroed column
-    else
+    if (fix && (on_dirichlet(csr.bnd, DIM, I, n) || on_dirichlet(csr.bnd, DIM, J, n))) {
+      const V e = (V)(A == B ? 1.0 : 0.0);  // identity row, zeroed column
+      vals[pos] = e;
+      vals[posT] = e;
+    } else {
       vals[pos] = base ? (V)((double)base[pos] + v) : (V)v;
+      if (posT != pos) vals[posT] = base ? (V)((double)base[posT] + v) : (V)v;
+    }
   }
 }
 

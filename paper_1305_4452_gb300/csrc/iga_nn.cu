@@ -5,22 +5,26 @@
 // Network: L layers of 3x3 convolutions with per-layer dilation and "same" zero
 // padding on an H x W grid (NHWC activations), SiLU between layers, a linear last
 // layer with one output channel, multiplied by a mask (zero on Dirichlet rows).
-// Every convolution -- forward, input gradient and weight gradient -- is an
-// explicit im2col (or its transpose) plus one dense GEMM on the tensor cores
-// (mma.sync m16n8k16, BF16 operands, FP32 accumulation).  Master weights, Adam
-// moments, gradients and the loss are FP32; activations are stored in BF16 for
-// the GEMMs and FP32 where the backward pass needs them.  Every reduction
-// (split-K weight gradients, bias gradients, loss) has a fixed order.
+// The forward convolutions and the input-gradient (transposed) convolutions run
+// as implicit GEMMs on the tcgen05 tensor cores with fused bias + SiLU and SiLU'
+// epilogues (iga_conv_tc.cu); the weight gradients are an explicit im2col plus a
+// split-K GEMM on mma.sync (m16n8k16).  Operands are BF16 with FP32 accumulation.
+// Master weights, Adam moments, gradients and the loss are FP32; activations are
+// stored in BF16 for the GEMMs and FP32 where the backward pass needs them.  Every
+// reduction (split-K weight gradients, bias gradients, loss) has a fixed order.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "iga_internal.h"
+#include "iga_conv_tc.h"
 
 typedef __nv_bfloat16 bf16;
 
@@ -172,44 +176,49 @@ __global__ void k_im2col(const bf16 *__restrict__ x, int B, int H, int W, int C,
   col[t] = v;
 }
 
-// dx[p][c] = sum_tap dcol[p - offset(tap)][tap*C + c]   (taps in order; the transpose of im2col)
-__global__ void k_col2im(const float *__restrict__ dcol, int B, int H, int W, int C, int dil, float *__restrict__ dx) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t total = (int64_t)B * H * W * C;
-  if (t >= total) return;
-  int c = (int)(t % C);
-  int64_t p = t / C;
-  int xx = (int)(p % W), yy = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
-  float s = 0.f;
-  for (int tap = 0; tap < 9; tap++) {
-    int sy = yy - dil * (tap / 3 - 1), sx = xx - dil * (tap % 3 - 1);
-    if (sy >= 0 && sy < H && sx >= 0 && sx < W) s += dcol[(((int64_t)b * H + sy) * W + sx) * 9 * C + tap * C + c];
-  }
-  dx[t] = s;
-}
-
-__device__ __forceinline__ float sigm(float z) { return 1.f / (1.f + expf(-z)); }
-
-// a = SiLU(z) in BF16
-__global__ void k_silu_fwd(const float *__restrict__ z, bf16 *__restrict__ a, int64_t n) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) a[i] = __float2bfloat16(z[i] * sigm(z[i]));
-}
-
-// dz = da * SiLU'(z); FP32 and BF16 copies
-__global__ void k_silu_bwd(const float *__restrict__ da, const float *__restrict__ z, float *__restrict__ dz,
-                           bf16 *__restrict__ dzb, int64_t n) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  float s = sigm(z[i]);
-  float v = da[i] * s * (1.f + z[i] * (1.f - s));
-  dz[i] = v;
-  dzb[i] = __float2bfloat16(v);
-}
-
 __global__ void k_f32_to_bf16(const float *__restrict__ x, bf16 *__restrict__ y, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) y[i] = __float2bfloat16(x[i]);
+}
+
+// features x[p][c] (FP32, c < C) -> xp[p][16] BF16 zero-padded for the tensor-core
+// convolution, and (training) x16[p][c] unpadded for the weight-gradient im2col
+__global__ void k_pad_input(const float *__restrict__ x, int C, int64_t P, bf16 *__restrict__ xp, bf16 *__restrict__ x16) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= P * 16) return;
+  const int64_t p = t / 16;
+  const int c = (int)(t % 16);
+  const float v = c < C ? x[p * C + c] : 0.f;
+  xp[t] = __float2bfloat16(v);
+  if (x16 && c < C) x16[p * C + c] = __float2bfloat16(v);
+}
+
+// per layer, from the FP32 master W[co][tap][ci]: wk[n][tap][c] = W[n][tap][c] padded to
+// (NP outputs, CP inputs), and wt[ci][tap][co] = W[co][tap][ci] padded to CP2 = NP
+// inputs (the transposed convolution's operand)
+__global__ void k_prep_w(const float *__restrict__ w, int cin, int cout, int CP, int NP, bf16 *__restrict__ wk,
+                         bf16 *__restrict__ wt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < NP * 9 * CP) {
+    const int n = t / (9 * CP), r = t % (9 * CP), tap = r / CP, c = r % CP;
+    wk[t] = __float2bfloat16((n < cout && c < cin) ? w[(n * 9 + tap) * cin + c] : 0.f);
+  }
+  if (wt && t < cin * 9 * NP) {
+    const int ci = t / (9 * NP), r = t % (9 * NP), tap = r / NP, co = r % NP;
+    wt[t] = __float2bfloat16(co < cout ? w[(co * 9 + tap) * cin + ci] : 0.f);
+  }
+}
+
+// last layer's output gradient dz[p] (one channel) -> BF16 [p][1] for the weight
+// gradient and [p][16] zero-padded for the transposed convolution
+__global__ void k_pad_grad(const float *__restrict__ dz, int64_t P, bf16 *__restrict__ d1, bf16 *__restrict__ d16) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= P * 16) return;
+  const int64_t p = t / 16;
+  const int c = (int)(t % 16);
+  const bf16 v = __float2bfloat16(dz[p]);
+  d16[t] = c == 0 ? v : __float2bfloat16(0.f);
+  if (c == 0) d1[p] = v;
 }
 
 // y[b][p] = mask[p] * z[b][p]  (last layer, one channel)
@@ -298,7 +307,7 @@ __global__ void k_colsum_partial(const float *__restrict__ dz, int64_t P, int C,
 }
 
 __global__ void k_adam(float *__restrict__ w, const float *__restrict__ gr, float *__restrict__ m, float *__restrict__ v,
-                       bf16 *__restrict__ wb, int64_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
+                       int64_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   float gi = gr[i];
@@ -308,7 +317,6 @@ __global__ void k_adam(float *__restrict__ w, const float *__restrict__ gr, floa
   v[i] = vi;
   float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
   w[i] = wi;
-  wb[i] = __float2bfloat16(wi);
 }
 
 // splitmix64-based uniform init in [-a, a]
@@ -330,6 +338,9 @@ inline unsigned g1(int64_t n) { return (unsigned)((n + 255) / 256); }
 struct NNLayer {
   int cin, cout, dil;
   int64_t woff, boff;  // offsets in the flat parameter vector
+  int cp, np;          // tensor-core operand widths: inputs and outputs padded to >= 16
+  bf16 *wk = nullptr;  // [np][9][cp] forward operand
+  bf16 *wt = nullptr;  // [cin][9][np] transposed-convolution operand (layers > 0)
 };
 
 struct iga_nn_s {
@@ -338,14 +349,16 @@ struct iga_nn_s {
   std::vector<NNLayer> layers;
   int64_t nparams = 0;
   float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // FP32 master, grad, Adam
-  bf16 *wb = nullptr;                                             // BF16 copy for the GEMMs
-  bf16 *wbt = nullptr;                                            // per-layer [9*Cin][Cout] ... (unused)
+  bf16 *wops = nullptr;       // BF16 tensor-core operands of all layers (NNLayer::wk, wt)
   std::vector<bf16 *> X;      // inputs of each layer, BF16 [P][Cin]
+  bf16 *X0p = nullptr;        // network input padded to 16 channels
   std::vector<float *> Z;     // pre-activations FP32 [P][Cout]
-  bf16 *col = nullptr;        // im2col [P][9 Cmax]
-  float *dcol = nullptr;      // [P][9 Cmax]
-  float *dA = nullptr, *dZ = nullptr;  // [P][Cmax]
-  bf16 *dZb = nullptr;
+  bf16 *col = nullptr;        // im2col [P][9 Cmax] (weight gradients)
+  float *dZ = nullptr, *dZ2 = nullptr;  // output gradients FP32 [P][Cmax] (ping-pong)
+  bf16 *dZb = nullptr, *dZb2 = nullptr; // their BF16 copies
+  bf16 *dZb16 = nullptr;      // last layer's gradient padded to 16 channels
+  int *tc_err = nullptr;      // tensor-core wait timeout flag (device)
+  int *tc_err_h = nullptr;    // pinned mirror
   float *part = nullptr;      // split-K / column-sum / loss partials
   float *y = nullptr, *lossv = nullptr, *lossh = nullptr;
   int64_t part_n = 0;
@@ -355,12 +368,14 @@ struct iga_nn_s {
 };
 
 static void nn_release(iga_nn_s *n) {
-  void *ps[] = {n->w, n->g, n->m, n->v, n->wb, n->col, n->dcol, n->dA, n->dZ, n->dZb, n->part, n->y, n->lossv};
+  void *ps[] = {n->w, n->g, n->m, n->v, n->wops, n->X0p, n->col, n->dZ, n->dZ2, n->dZb, n->dZb2, n->dZb16,
+                n->part, n->y, n->lossv, n->tc_err};
   for (void *p : ps)
     if (p) cudaFree(p);
   for (auto p : n->X) if (p) cudaFree(p);
   for (auto p : n->Z) if (p) cudaFree(p);
   if (n->lossh) cudaFreeHost(n->lossh);
+  if (n->tc_err_h) cudaFreeHost(n->tc_err_h);
 }
 
 #define NCK(call)                                                              \
@@ -388,9 +403,9 @@ extern "C" iga_status iga_nn_create(int height, int width, int in_channels, int 
                                     int max_batch, uint64_t seed, void *stream, iga_nn_t *out) {
   if (!out) return IGA_EINVAL;
   *out = nullptr;
-  if (height < 1 || width < 1 || in_channels < 1 || in_channels > 64 || hidden < 8 || hidden > 256 || hidden % 8 ||
-      layers < 2 || layers > 16 || max_batch < 1 || !dilations) {
-    g_nn_err = "bad network shape";
+  if (height < 1 || width < 1 || in_channels < 1 || in_channels > 16 || (hidden != 16 && hidden != 32 && hidden != 64) ||
+      layers < 2 || layers > 16 || max_batch < 1 || !dilations || (int64_t)max_batch * height * width > (1 << 28)) {
+    g_nn_err = "bad network shape (in_channels 1..16, hidden 16, 32 or 64, 2..16 layers, at most 2^28 pixels)";
     return IGA_EINVAL;
   }
   iga_nn_s *n = new iga_nn_s();
@@ -412,6 +427,8 @@ extern "C" iga_status iga_nn_create(int height, int width, int in_channels, int 
     off += (int64_t)ly.cout * 9 * ly.cin;
     ly.boff = off;
     off += ly.cout;
+    ly.cp = (l == 0) ? 16 : hidden;
+    ly.np = (l == layers - 1) ? 16 : hidden;
     n->layers.push_back(ly);
   }
   n->nparams = off;
@@ -434,7 +451,23 @@ extern "C" iga_status iga_nn_create(int height, int width, int in_channels, int 
   NCK2(cudaMalloc((void **)&n->g, off * sizeof(float)));
   NCK2(cudaMalloc((void **)&n->m, off * sizeof(float)));
   NCK2(cudaMalloc((void **)&n->v, off * sizeof(float)));
-  NCK2(cudaMalloc((void **)&n->wb, off * sizeof(bf16)));
+  int64_t wops = 0;
+  for (auto &ly : n->layers) wops += (int64_t)9 * (ly.np * ly.cp + ly.cin * ly.np);
+  NCK2(cudaMalloc((void **)&n->wops, wops * sizeof(bf16)));
+  {
+    bf16 *q = n->wops;
+    for (int l = 0; l < layers; l++) {
+      NNLayer &ly = n->layers[l];
+      ly.wk = q;
+      q += (int64_t)9 * ly.np * ly.cp;
+      ly.wt = l > 0 ? q : nullptr;
+      q += (int64_t)9 * ly.cin * ly.np;
+    }
+  }
+  NCK2(cudaMalloc((void **)&n->X0p, P * 16 * sizeof(bf16)));
+  NCK2(cudaMalloc((void **)&n->tc_err, sizeof(int)));
+  NCK2(cudaMemsetAsync(n->tc_err, 0, sizeof(int), n->stream));
+  NCK2(cudaMallocHost((void **)&n->tc_err_h, sizeof(int)));
   NCK2(cudaMemsetAsync(n->m, 0, off * sizeof(float), n->stream));
   NCK2(cudaMemsetAsync(n->v, 0, off * sizeof(float), n->stream));
   for (int l = 0; l < layers; l++) {
@@ -446,10 +479,11 @@ extern "C" iga_status iga_nn_create(int height, int width, int in_channels, int 
     n->Z.push_back(z);
   }
   NCK2(cudaMalloc((void **)&n->col, P * 9 * cmax * sizeof(bf16)));
-  NCK2(cudaMalloc((void **)&n->dcol, P * 9 * cmax * sizeof(float)));
-  NCK2(cudaMalloc((void **)&n->dA, P * cmax * sizeof(float)));
   NCK2(cudaMalloc((void **)&n->dZ, P * cmax * sizeof(float)));
+  NCK2(cudaMalloc((void **)&n->dZ2, P * cmax * sizeof(float)));
   NCK2(cudaMalloc((void **)&n->dZb, P * cmax * sizeof(bf16)));
+  NCK2(cudaMalloc((void **)&n->dZb2, P * cmax * sizeof(bf16)));
+  NCK2(cudaMalloc((void **)&n->dZb16, P * 16 * sizeof(bf16)));
   n->part_n = std::max<int64_t>((int64_t)64 * 9 * cmax * cmax, 4096 * (int64_t)cmax);
   NCK2(cudaMalloc((void **)&n->part, n->part_n * sizeof(float)));
   NCK2(cudaMalloc((void **)&n->y, P * sizeof(float)));
@@ -463,7 +497,6 @@ extern "C" iga_status iga_nn_create(int height, int width, int in_channels, int 
                                                                               seed + (uint64_t)ly.woff, a);
     NCK2(cudaMemsetAsync(n->w + ly.boff, 0, ly.cout * sizeof(float), n->stream));
   }
-  k_f32_to_bf16<<<g1(off), 256, 0, n->stream>>>(n->w, n->wb, off);
   NCK2(cudaStreamSynchronize(n->stream));
 #undef NCK2
   *out = n;
@@ -495,7 +528,6 @@ extern "C" iga_status iga_nn_get_params(iga_nn_t n, float *host) {
 extern "C" iga_status iga_nn_set_params(iga_nn_t n, const float *host) {
   if (!n || !host) return IGA_EINVAL;
   NCK(cudaMemcpyAsync(n->w, host, n->nparams * sizeof(float), cudaMemcpyHostToDevice, n->stream));
-  k_f32_to_bf16<<<g1(n->nparams), 256, 0, n->stream>>>(n->w, n->wb, n->nparams);
   NCK(cudaMemsetAsync(n->m, 0, n->nparams * sizeof(float), n->stream));
   NCK(cudaMemsetAsync(n->v, 0, n->nparams * sizeof(float), n->stream));
   n->adam_t = 0;
@@ -503,17 +535,61 @@ extern "C" iga_status iga_nn_set_params(iga_nn_t n, const float *host) {
   return IGA_OK;
 }
 
-// forward pass for B samples: x device FP32 [B][H][W][cin]; result in n->y [B][H][W]
-static iga_status nn_forward(iga_nn_s *n, const float *x, int B, const float *mask) {
+#define TCK(call)                                                              \
+  do {                                                                         \
+    cudaError_t ce_ = (call);                                                  \
+    if (ce_ != cudaSuccess) {                                                  \
+      n->err = iga_format("tensor-core convolution: %s", cudaGetErrorString(ce_)); \
+      return IGA_ECUDA;                                                        \
+    }                                                                          \
+  } while (0)
+
+// the flag raised by a tensor-core wait that timed out (synchronises the stream)
+static iga_status nn_check_tc(iga_nn_s *n) {
+  NCK(cudaMemcpyAsync(n->tc_err_h, n->tc_err, sizeof(int), cudaMemcpyDeviceToHost, n->stream));
+  NCK(cudaStreamSynchronize(n->stream));
+  if (*n->tc_err_h) {
+    n->err = "tensor-core convolution: an mbarrier wait timed out";
+    cudaMemsetAsync(n->tc_err, 0, sizeof(int), n->stream);
+    return IGA_ETIMEOUT;
+  }
+  return IGA_OK;
+}
+
+static ConvArgs conv_args(iga_nn_s *n, int B) {
+  ConvArgs a{};
+  a.P = B * n->H * n->W;
+  a.H = n->H;
+  a.W = n->W;
+  a.err = n->tc_err;
+  return a;
+}
+
+// forward pass for B samples: x device FP32 [B][H][W][cin]; result in n->y [B][H][W].
+// train: keep the pre-activations (FP32) and the unpadded BF16 input for the backward pass.
+static iga_status nn_forward(iga_nn_s *n, const float *x, int B, const float *mask, bool train) {
   const int64_t HW = (int64_t)n->H * n->W, P = (int64_t)B * HW;
-  k_f32_to_bf16<<<g1(P * n->cin), 256, 0, n->stream>>>(x, n->X[0], P * n->cin);
+  for (auto &ly : n->layers) {
+    int cnt = std::max(ly.np * 9 * ly.cp, ly.cin * 9 * ly.np);
+    k_prep_w<<<g1(cnt), 256, 0, n->stream>>>(n->w + ly.woff, ly.cin, ly.cout, ly.cp, ly.np, ly.wk, ly.wt);
+  }
+  k_pad_input<<<g1(P * 16), 256, 0, n->stream>>>(x, n->cin, P, n->X0p, train ? n->X[0] : nullptr);
   for (int l = 0; l < n->L; l++) {
     const NNLayer &ly = n->layers[l];
-    const int K = 9 * ly.cin;
-    k_im2col<<<g1(P * K), 256, 0, n->stream>>>(n->X[l], B, n->H, n->W, ly.cin, ly.dil, n->col);
-    // Z[P][cout] = col[P][K] * W^T  (W stored [cout][K]) + b
-    gemm<false, false>(n, (int)P, ly.cout, K, n->col, K, n->wb + ly.woff, K, n->Z[l], ly.cout, n->w + ly.boff);
-    if (l + 1 < n->L) k_silu_fwd<<<g1(P * ly.cout), 256, 0, n->stream>>>(n->Z[l], n->X[l + 1], P * ly.cout);
+    ConvArgs a = conv_args(n, B);
+    a.in = (l == 0) ? n->X0p : n->X[l];
+    a.wk = ly.wk;
+    a.bias = n->w + ly.boff;
+    a.dil = ly.dil;
+    a.sign = 1;
+    if (l + 1 < n->L) {
+      a.z = train ? n->Z[l] : nullptr;
+      a.act = n->X[l + 1];
+      TCK(launch_conv_tc(ly.cp, ly.np, CONV_EPI_FWD_SILU, a, n->stream));
+    } else {
+      a.z = n->Z[l];
+      TCK(launch_conv_tc(ly.cp, ly.np, CONV_EPI_LAST, a, n->stream));
+    }
   }
   k_output<<<g1(P), 256, 0, n->stream>>>(n->Z[n->L - 1], mask, HW, P, n->y);
   NCK(cudaGetLastError());
@@ -525,10 +601,10 @@ extern "C" iga_status iga_nn_forward(iga_nn_t n, const float *x, int B, const fl
     if (n) n->err = "bad forward arguments";
     return IGA_EINVAL;
   }
-  iga_status st = nn_forward(n, x, B, mask);
+  iga_status st = nn_forward(n, x, B, mask, false);
   if (st != IGA_OK) return st;
   NCK(cudaMemcpyAsync(y, n->y, (size_t)B * n->H * n->W * sizeof(float), cudaMemcpyDeviceToDevice, n->stream));
-  return IGA_OK;
+  return nn_check_tc(n);
 }
 
 // forward + backward: masked mean-squared error against tgt [B][H][W]; gradients
@@ -540,45 +616,54 @@ extern "C" iga_status iga_nn_loss_grad(iga_nn_t n, const float *x, const float *
     if (n) n->err = "bad loss_grad arguments";
     return IGA_EINVAL;
   }
-  iga_status st = nn_forward(n, x, B, mask);
+  iga_status st = nn_forward(n, x, B, mask, true);
   if (st != IGA_OK) return st;
   const int64_t HW = (int64_t)n->H * n->W, P = (int64_t)B * HW;
   const int nbl = 256;
   k_loss_partial<<<nbl, 256, 0, n->stream>>>(n->y, tgt, mask, HW, P, n->W, n->H, n->h1, n->part);
   k_loss_final<<<1, 1, 0, n->stream>>>(n->part, nbl, n->lossv);
   k_loss_grad<<<g1(P), 256, 0, n->stream>>>(n->y, tgt, mask, HW, P, n->W, n->H, n->h1, n->lossv, n->dZ);
+  // the output layer's gradient in the layouts its weight gradient and its
+  // transposed convolution read
+  k_pad_grad<<<g1(P * 16), 256, 0, n->stream>>>(n->dZ, P, n->dZb, n->dZb16);
+  float *dz = n->dZ, *dz_next = n->dZ2;
+  bf16 *dzb = n->dZb, *dzb_next = n->dZb2;
   for (int l = n->L - 1; l >= 0; l--) {
     const NNLayer &ly = n->layers[l];
     const int K = 9 * ly.cin;
-    if (l < n->L - 1) {
-      // dZ = dA * SiLU'(Z)
-      k_silu_bwd<<<g1(P * ly.cout), 256, 0, n->stream>>>(n->dA, n->Z[l], n->dZ, n->dZb, P * ly.cout);
-    } else {
-      k_f32_to_bf16<<<g1(P * ly.cout), 256, 0, n->stream>>>(n->dZ, n->dZb, P * ly.cout);
-    }
     // bias gradient: column sums of dZ
     const int64_t chunk = 4096;
     const int nch = (int)((P + chunk - 1) / chunk);
-    k_colsum_partial<<<nch, 256, 0, n->stream>>>(n->dZ, P, ly.cout, chunk, n->part);
+    k_colsum_partial<<<nch, 256, 0, n->stream>>>(dz, P, ly.cout, chunk, n->part);
     k_sum_splits<<<g1(ly.cout), 256, 0, n->stream>>>(n->part, nch, ly.cout, n->g + ly.boff, 0);
     // weight gradient: dW[cout][K] = dZ^T (cout x P) * col (P x K), split over P
     k_im2col<<<g1(P * K), 256, 0, n->stream>>>(n->X[l], B, n->H, n->W, ly.cin, ly.dil, n->col);
     int splits = (int)std::min<int64_t>(64, std::max<int64_t>(1, P / 2048));
     while ((int64_t)splits * ly.cout * K > n->part_n) splits--;
-    gemm<true, true>(n, ly.cout, K, (int)P, n->dZb, ly.cout, n->col, K, n->part, K, nullptr, splits);
+    gemm<true, true>(n, ly.cout, K, (int)P, dzb, ly.cout, n->col, K, n->part, K, nullptr, splits);
     int kchunk = ((int)((P + splits - 1) / splits) + GBK - 1) / GBK * GBK;
     int used = (int)((P + kchunk - 1) / kchunk);
     k_sum_splits<<<g1((int64_t)ly.cout * K), 256, 0, n->stream>>>(n->part, used, (int64_t)ly.cout * K, n->g + ly.woff, 0);
     if (l > 0) {
-      // dcol[P][K] = dZ[P][cout] * W[cout][K]; dA_prev = col2im(dcol)
-      gemm<false, true>(n, (int)P, K, ly.cout, n->dZb, ly.cout, n->wb + ly.woff, K, n->dcol, K, nullptr);
-      k_col2im<<<g1(P * ly.cin), 256, 0, n->stream>>>(n->dcol, B, n->H, n->W, ly.cin, ly.dil, n->dA);
+      // dZ of the layer below = (transposed convolution of dZ) * SiLU'(Z below), on the tensor cores
+      ConvArgs a = conv_args(n, B);
+      a.in = (l == n->L - 1) ? n->dZb16 : dzb;
+      a.wk = ly.wt;
+      a.zprev = n->Z[l - 1];
+      a.z = dz_next;
+      a.act = dzb_next;
+      a.dil = ly.dil;
+      a.sign = -1;
+      TCK(launch_conv_tc(ly.np, ly.cin, CONV_EPI_BWD_SILU, a, n->stream));
+      std::swap(dz, dz_next);
+      std::swap(dzb, dzb_next);
     }
   }
   NCK(cudaGetLastError());
   NCK(cudaMemcpyAsync(n->lossh, n->lossv, 2 * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
   if (grads_out) NCK(cudaMemcpyAsync(grads_out, n->g, n->nparams * sizeof(float), cudaMemcpyDeviceToDevice, n->stream));
-  NCK(cudaStreamSynchronize(n->stream));
+  st = nn_check_tc(n);
+  if (st != IGA_OK) return st;
   if (loss) *loss = n->lossh[0];
   return IGA_OK;
 }
@@ -593,7 +678,7 @@ extern "C" iga_status iga_nn_adam_step(iga_nn_t n, float lr, float beta1, float 
   if (!n || !(lr > 0.f)) return IGA_EINVAL;
   n->adam_t++;
   float c1 = 1.f - powf(beta1, (float)n->adam_t), c2 = 1.f - powf(beta2, (float)n->adam_t);
-  k_adam<<<g1(n->nparams), 256, 0, n->stream>>>(n->w, n->g, n->m, n->v, n->wb, n->nparams, lr, beta1, beta2, eps, c1, c2);
+  k_adam<<<g1(n->nparams), 256, 0, n->stream>>>(n->w, n->g, n->m, n->v, n->nparams, lr, beta1, beta2, eps, c1, c2);
   NCK(cudaGetLastError());
   return IGA_OK;
 }

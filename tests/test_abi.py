@@ -63,3 +63,15 @@ def test_invalid_descriptions_rejected_before_any_device_work(lib, kwargs, needl
 def test_newton_defaults(lib):
     o = lib.newton_defaults()
     assert o.atol == 1e-10 and o.max_newton == 50 and o.gmres_restart > 0 and o.jac == lib.IGA_FP64
+
+
+@pytest.mark.parametrize("cin,hidden", [(4, 24), (17, 64), (4, 128), (0, 32)])
+def test_nn_shapes_outside_the_compiled_convolutions_rejected(lib, cin, hidden):
+    import ctypes
+    from paper_1305_4452_gb300 import nn
+    L = nn._lib()
+    dil = (ctypes.c_int * 3)(1, 2, 1)
+    h = ctypes.c_void_p()
+    rc = L.iga_nn_create(8, 8, cin, hidden, 3, dil, 4, 0, None, ctypes.byref(h))
+    assert rc == lib.IGA_EINVAL and not h.value
+    assert b"hidden" in L.iga_nn_last_error(None)

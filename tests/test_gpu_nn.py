@@ -22,7 +22,8 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
 
 
-@pytest.mark.parametrize("shape", [(10, 10, 16, (1, 2, 4, 1), 3, 0.0), (13, 11, 24, (1, 3, 1), 2, 4.0)])
+@pytest.mark.parametrize("shape", [(10, 10, 16, (1, 2, 4, 1), 3, 0.0), (13, 11, 32, (1, 3, 1), 2, 4.0),
+                                   (9, 12, 64, (2, 1), 4, 1.0)])
 def test_forward_loss_and_gradients_match_cpu_reference(M, shape):
     H, Wd, hidden, dil, B, beta = shape
     net = M.Net(H, Wd, hidden=hidden, dilations=dil, max_batch=4, seed=3)
