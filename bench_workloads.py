@@ -1,6 +1,6 @@
 """Benchmark lines for the configurations other than the headline one.
 
-    python bench.py --workload {bratu16, cube_mixed, batch512, learned64}
+    python bench.py --workload {bratu16, cube_mixed, batch512, learned64, nn64}
 
 Each prints one JSON line with the keys of the headline line (metric, value,
 unit, config, clocks, e2e-style extras) for one configuration:
@@ -14,6 +14,8 @@ unit, config, clocks, e2e-style extras) for one configuration:
               error against the FP64 Jacobian; Newton solves with each.
   batch512    512 independent 2D instances (n ~ U{16..128}, p ~ U{2,3},
               lambda ~ U[0.5, 6]) in one persistent, graph-captured launch.
+  nn64        the learned-guess network alone: forward and training step on a batch
+              of 64 synthetic 66 x 66 inputs, against the BF16 tensor peak.
   learned64   kappa-Bratu on 64^2 quadratic (66 x 66 control grid): training
               data from the batched solver, the convolutional guess trained on
               the GPU, evaluation on held-out fields against the zero start and
@@ -220,4 +222,43 @@ def learned64(torch, iga, W, clock, n_train=20000, n_test=2000, steps=6000):
     return _line(res["nn_start"]["solves_per_s"], "solves/s", "kappa_bratu_64x64_p2_learned_initial_guess", {"results": res}, ck)
 
 
-WORKLOADS = {"bratu16": bratu16, "cube_mixed": cube_mixed, "batch512": batch512, "learned64": learned64}
+def nn64(torch, iga, W, clock, batch=64, reps=10):
+    """The learned-guess network alone (random weights, synthetic inputs of the
+    66 x 66 control grid): inference and training-step throughput against the
+    measured dense BF16 tensor peak."""
+    import json as _json
+    import os as _os
+    from paper_1305_4452_gb300 import nn
+    H = Wd = 66
+    net = nn.Net(H, Wd, hidden=64, max_batch=batch, seed=0)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(batch, H, Wd, 4, device="cuda", generator=g)
+    tgt = 0.1 * torch.randn(batch, H, Wd, device="cuda", generator=g)
+    mask = torch.ones(H, Wd, device="cuda")
+    shapes, _ = nn.layer_shapes(4, 64, nn.DILATIONS)
+    P = batch * H * Wd
+    fwd_flops = sum(2.0 * P * 9 * cin * cout for cin, cout, _, _, _ in shapes)
+    tc_flops = sum(2.0 * P * 9 * (16 if i == 0 else cin) * (16 if i == len(shapes) - 1 else cout)
+                   for i, (cin, cout, _, _, _) in enumerate(shapes))
+    clock.start()
+    t_fwd = _ev(torch, lambda: net.forward(x, mask), reps)
+    t_step = _ev(torch, lambda: (net.loss_grad(x, tgt, mask), net.adam_step(1e-4)), reps)
+    ck = clock.stop()
+    try:
+        with open(_os.path.join(_os.path.dirname(_os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            peak, src = float(_json.load(f)["bf16_tflops"]), "measured burst"
+    except Exception:
+        peak, src = 1900.0, "fallback"
+    ach = fwd_flops / (t_fwd * 1e-3) / 1e12
+    net.close()
+    return _line(batch / (t_fwd * 1e-3), "fields/s", "neural_operator_66x66_6layers_64ch_batch%d_bf16" % batch, {
+        "forward_ms": t_fwd, "train_step_ms": t_step, "forward_flops": fwd_flops,
+        "forward_flops_on_tensor_cores": tc_flops,
+        "roofline": {"kernel": "k_conv_tc (forward, 6 launches)", "bound": "tensor", "achieved": ach, "peak": peak,
+                     "unit": "TFLOP/s", "frac": ach / peak, "peak_source": src,
+                     "note": "achieved = unpadded network FLOPs / forward time; the padded first and last layers run "
+                             "%.1f%% more tensor-core FLOPs" % (100 * (tc_flops / fwd_flops - 1))},
+        "train_step_tflops": 3 * fwd_flops / (t_step * 1e-3) / 1e12}, ck, dtype="bf16")
+
+
+WORKLOADS = {"bratu16": bratu16, "cube_mixed": cube_mixed, "batch512": batch512, "learned64": learned64, "nn64": nn64}

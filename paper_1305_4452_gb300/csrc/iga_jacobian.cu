@@ -121,6 +121,8 @@ __global__ void __launch_bounds__(256) k_stage1(DirArgs d0, DirArgs d1, DirArgs 
 //   H0 (axis-2 pattern 00) = P^00 G0 + P^10 G1 + P^01 G1^T + P^11 G2
 //   H1 (axis-2 pattern 10) = P^00 G3 + P^01 G4^T
 //   H2 (axis-2 pattern 11) = P^00 G5          [pattern 01 is the transpose of H1]
+// H0 and H2 are unchanged when both pairs are transposed, so they are formed only
+// for pi1 <= pi1T; the final stage reads them at (pi1T, pi0T) otherwise.
 template <typename T, int PLAN>
 __global__ void __launch_bounds__(128) k_stage2(DirArgs d0, DirArgs d1, DirArgs d2, const T *__restrict__ in,
                                                 T *__restrict__ out, int chunk) {
@@ -133,6 +135,8 @@ __global__ void __launch_bounds__(128) k_stage2(DirArgs d0, DirArgs d1, DirArgs 
   const size_t outplane = (size_t)d0.np * d1.np * d2.X;
   const T *tab = ptab<T>(d1);
   for (int pi1 = pa; pi1 < pb; pi1++) {
+    const bool sym = pi1 <= d1.pair_T[pi1];  // uniform across the block
+    if (PLAN == PLAN_MASS && !sym) continue;
     const int xs = d1.pair_x0[pi1], np = d1.pair_np[pi1];
     const T *pv = tab + (size_t)d1.pair_po[pi1] * IGA_PVS;
     T h0 = 0, h1 = 0, h2 = 0;
@@ -142,21 +146,24 @@ __global__ void __launch_bounds__(128) k_stage2(DirArgs d0, DirArgs d1, DirArgs 
       if (PLAN == PLAN_MASS) {
         h0 = fma(p00, in[row + pi0], h0);
       } else {
-        const T p10 = pv[IGA_PVS * k + 1], p01 = pv[IGA_PVS * k + 2], p11 = pv[IGA_PVS * k + 3];
-        h0 = fma(p00, in[row + pi0], h0);
-        h0 = fma(p10, in[inplane + row + pi0], h0);
-        h0 = fma(p01, in[inplane + row + pi0T], h0);
-        h0 = fma(p11, in[2 * inplane + row + pi0], h0);
+        const T p01 = pv[IGA_PVS * k + 2];
+        if (sym) {
+          const T p10 = pv[IGA_PVS * k + 1], p11 = pv[IGA_PVS * k + 3];
+          h0 = fma(p00, in[row + pi0], h0);
+          h0 = fma(p10, in[inplane + row + pi0], h0);
+          h0 = fma(p01, in[inplane + row + pi0T], h0);
+          h0 = fma(p11, in[2 * inplane + row + pi0], h0);
+          h2 = fma(p00, in[5 * inplane + row + pi0], h2);
+        }
         h1 = fma(p00, in[3 * inplane + row + pi0], h1);
         h1 = fma(p01, in[4 * inplane + row + pi0T], h1);
-        h2 = fma(p00, in[5 * inplane + row + pi0], h2);
       }
     }
     T *o = out + ((size_t)x2 * d1.np + pi1) * d0.np + pi0;
-    o[0] = h0;
+    if (sym) o[0] = h0;
     if (PLAN == PLAN_STIFF) {
       o[outplane] = h1;
-      o[2 * outplane] = h2;
+      if (sym) o[2 * outplane] = h2;
     }
   }
 }
@@ -199,6 +206,7 @@ __global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d
     o1T = pmidT - d1.pair_off[j1]; w1T = d1.r[j1] - d1.l[j1] + 1;
   }
   const T *tab = ptab<T>(dl);
+  const bool mid_sym = pmid <= pmidT;  // 3D: where stage 2 stored H0 and H2
   for (int pl = pa; pl < pb; pl++) {
     const int plT = dl.pair_T[pl];
     if (pl > plT || (pl == plT && (pmid > pmidT || (pmid == pmidT && pi0 > pi0T)))) continue;
@@ -216,14 +224,15 @@ __global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d
         r = xo * d0.np + pi0;
         rT = xo * d0.np + pi0T;
       }
+      const size_t rs = (DIM == 2 || mid_sym) ? r : rT;
       if (PLAN == PLAN_MASS) {
-        acc = fma(p00, in[r], acc);
+        acc = fma(p00, in[rs], acc);
       } else {
         const T p10 = pv[IGA_PVS * k + 1], p01 = pv[IGA_PVS * k + 2], p11 = pv[IGA_PVS * k + 3];
-        acc = fma(p00, in[r], acc);
+        acc = fma(p00, in[rs], acc);
         acc = fma(p10, in[plane + r], acc);
         acc = fma(p01, in[plane + rT], acc);
-        acc = fma(p11, in[2 * plane + r], acc);
+        acc = fma(p11, in[2 * plane + rs], acc);
       }
     }
     const int il = dl.pair_i[pl], jl = dl.pair_j[pl];
