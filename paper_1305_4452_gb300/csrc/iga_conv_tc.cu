@@ -10,21 +10,28 @@
 // with Wk[ci][tap][co] = W[co][tap][ci] is its input gradient (the transposed
 // convolution).  The GEMM is M = 128 pixels per tile, N = NOUT, K = 9 * CIN.
 //
-// One CTA of 128 threads per tile stream (persistent over tiles):
-//   - the weights of the layer sit in shared memory for the whole kernel;
-//   - every thread gathers its own pixel row of the shifted input for each tap
-//     with 16-byte cp.async copies (zero-filled outside the grid) into a
-//     4-stage ring of A tiles, three taps ahead of the tensor core;
-//   - one thread issues the MMAs of a tap (CIN/16 instructions of K = 16) and
-//     commits them to the stage's mbarrier, which frees the stage for reuse;
-//   - after the ninth tap the accumulator (128 lanes x NOUT columns of TMEM) is
-//     read back with tcgen05.ld, thread t owning pixel row t, and the epilogue
-//     (bias + SiLU, or the SiLU derivative of the layer below) is fused.
+// One persistent CTA per SM, warp-specialised (288 threads):
+//   - warps 4-7 (producers): thread j gathers pixel row j of the shifted, dilated
+//     input for each (tile, tap) with 16-byte cp.async copies (zero-filled outside
+//     the grid) into an 8-stage ring; once its copies of a stage have landed it
+//     fences them into the async proxy and arrives on the stage's "full" barrier;
+//     it refills a stage after the stage's "empty" barrier reports the MMAs that
+//     read it complete;
+//   - warp 8 (MMA): allocates tensor memory; one thread waits for "full", issues
+//     the tap's CIN/16 tcgen05.mma instructions (K = 16, FP32 accumulator in
+//     TMEM) and commits them to "empty"; after the ninth tap it commits the
+//     accumulator to "acc full";
+//   - warps 0-3 (epilogue): thread t reads accumulator row t (pixel t of the tile)
+//     with tcgen05.ld, applies the fused epilogue (bias + SiLU, or the SiLU
+//     derivative of the layer below), stores, and arrives on "acc empty".
+//   Two accumulators in TMEM (2 x NOUT columns) let the epilogue of one tile
+//   overlap the MMAs of the next; the layer's weights stay in shared memory.
 // Operand tiles use the canonical K-major layout without swizzling: 8-row x
 // 16-byte core matrices, 128 bytes apart along M/N (SBO) and one column of
-// core matrices per 8 K values (LBO).  Every mbarrier wait is bounded; on
-// timeout the kernel raises an error flag, drains its copies, frees its tensor
-// memory and returns.
+// core matrices per 8 K values (LBO).  Every mbarrier wait is bounded in time
+// (globaltimer); on timeout the kernel raises an error flag, every role stops,
+// the MMA thread waits (bounded) for its last commit, and the tensor memory is
+// freed before the kernel returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -45,17 +52,34 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (int i = 0; i < (1 << 24); i++) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (ok) return true;
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(ok)
+               : "r"(mbar), "r"(parity)
+               : "memory");
+  return ok != 0;
+}
+
+// wait for the phase with the given parity to complete; false after ~2 s, or
+// at once when another role has given up (*abort set)
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int *abort) {
+  if (mbar_try(mbar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  for (uint32_t i = 1;; i++) {
+    if (mbar_try(mbar, parity)) return true;
+    if ((i & 63) == 0 && ((abort && *abort) || gtimer() - t0 > 2000000000ull)) return false;
   }
-  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mbar) : "memory");
 }
 
 __device__ __forceinline__ void cp16(uint32_t dst, const void *src, bool valid) {
@@ -87,8 +111,9 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
   return *reinterpret_cast<uint32_t *>(&h);
 }
 
-constexpr int CONV_THREADS = 128;
-constexpr int CONV_STAGES = 4;
+constexpr int CONV_THREADS = 288;  // 4 epilogue warps, 4 producer warps, 1 MMA warp
+constexpr int CONV_STAGES = 8;
+constexpr int CONV_LAG = 2;        // copy groups a producer keeps in flight beyond the one it signals
 
 template <int CIN, int NOUT>
 struct ConvSmem {
@@ -98,48 +123,124 @@ struct ConvSmem {
   static constexpr uint32_t A_BYTES = 128 * CIN * 2;
   static constexpr uint32_t W_BYTES = NOUT * 9 * CIN * 2;
   static constexpr uint32_t BAR = W_BYTES + CONV_STAGES * A_BYTES;
-  static constexpr uint32_t TOTAL = BAR + 8 * (CONV_STAGES + 1) + 16;
-  static constexpr uint32_t TMEM_COLS = NOUT <= 32 ? 32 : (NOUT <= 64 ? 64 : 128);
+  // barriers: full[S], empty[S], acc_full[2], acc_empty[2]; then the TMEM slot and the abort flag
+  static constexpr uint32_t TOTAL = BAR + 8 * (2 * CONV_STAGES + 4) + 16;
+  static constexpr uint32_t TMEM_COLS = 2 * NOUT < 32 ? 32 : 2 * NOUT;  // two accumulators
 };
+
+template <int CIN, int NOUT, int EPI>
+__device__ __forceinline__ void conv_epilogue(const ConvArgs &a, uint32_t taddr, int p) {
+  if constexpr (EPI == CONV_EPI_LAST) {
+    float v[16];
+    tmem_ld16(taddr, v);
+    if (p < a.P) a.z[p] = v[0] + (a.bias ? a.bias[0] : 0.f);
+  } else {
+#pragma unroll
+  for (int c0 = 0; c0 < NOUT; c0 += 16) {
+    float v[16];
+    tmem_ld16(taddr + c0, v);
+    if (p >= a.P) continue;
+    float d[16];
+    if constexpr (EPI == CONV_EPI_FWD_SILU) {
+#pragma unroll
+      for (int j = 0; j < 16; j++) d[j] = v[j] + (a.bias ? a.bias[c0 + j] : 0.f);
+      if (a.z) {
+        float4 *z4 = reinterpret_cast<float4 *>(a.z + (size_t)p * NOUT + c0);
+#pragma unroll
+        for (int q = 0; q < 4; q++) z4[q] = make_float4(d[4 * q], d[4 * q + 1], d[4 * q + 2], d[4 * q + 3]);
+      }
+#pragma unroll
+      for (int j = 0; j < 16; j++) d[j] = d[j] * sigm(d[j]);
+    } else {  // CONV_EPI_BWD_SILU: d = v * SiLU'(z of the layer below)
+      const float4 *zp = reinterpret_cast<const float4 *>(a.zprev + (size_t)p * NOUT + c0);
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const float4 z = zp[q];
+        const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const float sg = sigm(zz[u]);
+          d[4 * q + u] = v[4 * q + u] * sg * (1.f + zz[u] * (1.f - sg));
+        }
+      }
+      float4 *z4 = reinterpret_cast<float4 *>(a.z + (size_t)p * NOUT + c0);
+#pragma unroll
+      for (int q = 0; q < 4; q++) z4[q] = make_float4(d[4 * q], d[4 * q + 1], d[4 * q + 2], d[4 * q + 3]);
+    }
+    uint4 o[2];
+    uint32_t *ow = reinterpret_cast<uint32_t *>(o);
+#pragma unroll
+    for (int j = 0; j < 8; j++) ow[j] = pack2(d[2 * j], d[2 * j + 1]);
+    uint4 *dst = reinterpret_cast<uint4 *>(a.act + (size_t)p * NOUT + c0);
+    dst[0] = o[0];
+    dst[1] = o[1];
+  }
+  }
+}
 
 template <int CIN, int NOUT, int EPI>
 __global__ void __launch_bounds__(CONV_THREADS, 1) k_conv_tc(ConvArgs a) {
   using SM = ConvSmem<CIN, NOUT>;
-  constexpr int KCH = CIN / 8, KSTEPS = CIN / 16, S = CONV_STAGES, DIST = S - 1;
+  constexpr int KCH = CIN / 8, KSTEPS = CIN / 16, S = CONV_STAGES, LAG = CONV_LAG;
   static_assert(CIN % 16 == 0 && NOUT % 16 == 0 && NOUT <= 128, "tile shape");
   extern __shared__ __align__(128) uint8_t sm[];
   uint8_t *Ws = sm;
   uint8_t *As = sm + SM::W_BYTES;
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + SM::BAR);  // [S] stages, [S] accumulator
-  uint32_t *slot = reinterpret_cast<uint32_t *>(mbar + S + 1);
-  int *abort_s = reinterpret_cast<int *>(slot + 1);
+  uint64_t *full = reinterpret_cast<uint64_t *>(sm + SM::BAR);
+  uint64_t *empty = full + S;
+  uint64_t *accf = empty + S;
+  uint64_t *acce = accf + 2;
+  uint32_t *slot = reinterpret_cast<uint32_t *>(acce + 2);
+  volatile int *abort_s = reinterpret_cast<volatile int *>(slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int HW = a.H * a.W;
   const int ntiles = (a.P + 127) / 128;
   const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const int total_it = my_tiles * 9;
 
-  // the layer's weights, resident for the whole kernel (joins the first copy group)
+  // the layer's weights, resident for the whole kernel
   for (int c = tid; c < NOUT * 9 * KCH; c += CONV_THREADS) {
     const int n = c % NOUT, kc = c / NOUT;
     cp16(su32(Ws + (n / 8) * SM::SBO + kc * SM::LBO_W + (n % 8) * 16), a.wk + (size_t)n * 9 * CIN + kc * 8, true);
   }
-  if (warp == 0) {
+  cp_commit();
+  if (warp == 8) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)), "r"(SM::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int i = 0; i <= S; i++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(mbar + i)) : "memory");
+    for (int i = 0; i < S; i++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(su32(full + i)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(empty + i)) : "memory");
+    }
+    for (int i = 0; i < 2; i++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(accf + i)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(su32(acce + i)) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *abort_s = 0;
   }
+  cp_wait<0>();
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
 
-  // gather of iteration it = (local tile, tap): thread t copies pixel row t
-  auto load_it = [&](int it) {
-    if (it < total_it) {
+  if (warp >= 4 && warp < 8) {
+    // ---------------- producers ----------------
+    const int j = tid - 128;  // pixel row within the tile
+    const int HW = a.H * a.W;
+    int it = 0;
+    for (; it < total_it; it++) {
+      const int s = it % S;
+      if (it >= S && !mbar_wait(su32(empty + s), ((it / S) - 1) & 1, abort_s)) {
+        atomicExch(a.err, 1);
+        *abort_s = 1;
+        break;
+      }
       const int tl = it / 9, tap = it - tl * 9;
-      const int p = ((int)blockIdx.x + tl * (int)gridDim.x) * 128 + tid;
+      const int p = ((int)blockIdx.x + tl * (int)gridDim.x) * 128 + j;
       const int dy = (tap / 3 - 1) * a.dil * a.sign, dx = (tap % 3 - 1) * a.dil * a.sign;
       bool valid = false;
       const bf16 *src = a.in;
@@ -151,122 +252,80 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) k_conv_tc(ConvArgs a) {
           src = a.in + ((size_t)b * HW + (size_t)sy * a.W + sx) * CIN;
         }
       }
-      const uint32_t dst = su32(As + (it % S) * SM::A_BYTES + (tid / 8) * SM::SBO + (tid % 8) * 16);
+      const uint32_t dst = su32(As + s * SM::A_BYTES + (j / 8) * SM::SBO + (j % 8) * 16);
 #pragma unroll
       for (int kc = 0; kc < KCH; kc++) cp16(dst + kc * SM::LBO_A, src + kc * 8, valid);
-    }
-    cp_commit();
-  };
-  for (int i = 0; i < DIST; i++) load_it(i);
-
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *slot;
-  // instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, N, M = 128
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NOUT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-
-  int issued = -1;  // last iteration whose MMAs were issued (uniform)
-  bool failed = false;
-  for (int it = 0; it < total_it; it++) {
-    const int s = it % S, tl = it / 9, tap = it - tl * 9;
-    cp_wait<DIST - 1>();
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc_fence_before();
-    __syncthreads();
-    if (*abort_s) { failed = true; break; }
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t a0 = su32(As + s * SM::A_BYTES), w0 = su32(Ws);
-#pragma unroll
-      for (int j = 0; j < KSTEPS; j++) {
-        const uint64_t ad = sdesc(a0 + 2 * j * SM::LBO_A, SM::LBO_A, SM::SBO);
-        const uint64_t bd = sdesc(w0 + 2 * (tap * KSTEPS + j) * SM::LBO_W, SM::LBO_W, SM::SBO);
-        const uint32_t acc = (tap > 0 || j > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-            : "memory");
+      cp_commit();
+      if (it >= LAG) {
+        cp_wait<LAG>();  // the copies of iteration it - LAG have landed
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(su32(full + (it - LAG) % S));
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(mbar + s)) : "memory");
-      if (tap == 8)
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(mbar + S)) : "memory");
     }
-    issued = it;
-    // the stage of iteration it-1 receives iteration it+DIST once its MMAs are done
-    if (it >= 1 && !mbar_wait(su32(mbar + (it - 1) % S), ((it - 1) / S) & 1)) {
-      atomicExch(a.err, 1);
-      *abort_s = 1;
+    cp_wait<0>();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    for (int k = (it > LAG ? it - LAG : 0); k < it; k++) mbar_arrive(su32(full + k % S));
+  } else if (warp == 8) {
+    // ---------------- MMA issuer ----------------
+    if ((tid & 31) == 0) {
+      const uint32_t idesc =
+          (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NOUT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+      const uint32_t w0 = su32(Ws);
+      int last = -1;  // last iteration whose MMAs were committed
+      for (int it = 0; it < total_it; it++) {
+        const int s = it % S, tl = it / 9, tap = it - tl * 9, buf = tl & 1;
+        if (tap == 0 && tl >= 2 && !mbar_wait(su32(acce + buf), ((tl / 2) - 1) & 1, abort_s)) {
+          atomicExch(a.err, 1);
+          *abort_s = 1;
+          break;
+        }
+        if (!mbar_wait(su32(full + s), (it / S) & 1, abort_s)) {
+          atomicExch(a.err, 1);
+          *abort_s = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a0 = su32(As + s * SM::A_BYTES), d = tmem + (uint32_t)(buf * NOUT);
+#pragma unroll
+        for (int k = 0; k < KSTEPS; k++) {
+          const uint64_t ad = sdesc(a0 + 2 * k * SM::LBO_A, SM::LBO_A, SM::SBO);
+          const uint64_t bd = sdesc(w0 + 2 * (tap * KSTEPS + k) * SM::LBO_W, SM::LBO_W, SM::SBO);
+          const uint32_t acc = (tap > 0 || k > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(empty + s))
+                     : "memory");
+        if (tap == 8)
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(accf + buf))
+                       : "memory");
+        last = it;
+      }
+      // after a failure, let the MMAs already issued finish before the memory is freed
+      if (*abort_s && last >= 0) mbar_wait(su32(empty + last % S), (last / S) & 1, nullptr);
     }
-    load_it(it + DIST);
-    if (tap == 8) {
-      if (!mbar_wait(su32(mbar + S), tl & 1)) {
+    __syncwarp();
+  } else {
+    // ---------------- epilogue (warps 0-3: TMEM lanes 0-127) ----------------
+    for (int tl = 0; tl < my_tiles; tl++) {
+      const int buf = tl & 1;
+      if (!mbar_wait(su32(accf + buf), (tl / 2) & 1, abort_s)) {
         atomicExch(a.err, 1);
         *abort_s = 1;
-        continue;
+        break;
       }
       tc_fence_after();
       const int p = ((int)blockIdx.x + tl * (int)gridDim.x) * 128 + tid;
-      const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-      if (EPI == CONV_EPI_LAST) {
-        float v[16];
-        tmem_ld16(trow, v);
-        if (p < a.P) a.z[p] = v[0] + (a.bias ? a.bias[0] : 0.f);
-      } else {
-#pragma unroll
-        for (int c0 = 0; c0 < NOUT; c0 += 16) {
-          float v[16];
-          tmem_ld16(trow + c0, v);
-          if (p >= a.P) continue;
-          if (EPI == CONV_EPI_FWD_SILU) {
-#pragma unroll
-            for (int j = 0; j < 16; j++) v[j] += a.bias ? a.bias[c0 + j] : 0.f;
-            if (a.z) {
-              float4 *z4 = reinterpret_cast<float4 *>(a.z + (size_t)p * NOUT + c0);
-#pragma unroll
-              for (int q = 0; q < 4; q++) z4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-            }
-            uint4 o[2];
-            uint32_t *ow = reinterpret_cast<uint32_t *>(o);
-#pragma unroll
-            for (int j = 0; j < 8; j++) ow[j] = pack2(v[2 * j] * sigm(v[2 * j]), v[2 * j + 1] * sigm(v[2 * j + 1]));
-            uint4 *dst = reinterpret_cast<uint4 *>(a.act + (size_t)p * NOUT + c0);
-            dst[0] = o[0];
-            dst[1] = o[1];
-          } else {  // CONV_EPI_BWD_SILU: d = v * SiLU'(z_below)
-            const float4 *zp = reinterpret_cast<const float4 *>(a.zprev + (size_t)p * NOUT + c0);
-            float d[16];
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-              const float4 z = zp[q];
-              const float zz[4] = {z.x, z.y, z.z, z.w};
-#pragma unroll
-              for (int u = 0; u < 4; u++) {
-                const float sg = sigm(zz[u]);
-                d[4 * q + u] = v[4 * q + u] * sg * (1.f + zz[u] * (1.f - sg));
-              }
-            }
-            float4 *z4 = reinterpret_cast<float4 *>(a.z + (size_t)p * NOUT + c0);
-#pragma unroll
-            for (int q = 0; q < 4; q++) z4[q] = make_float4(d[4 * q], d[4 * q + 1], d[4 * q + 2], d[4 * q + 3]);
-            uint4 o[2];
-            uint32_t *ow = reinterpret_cast<uint32_t *>(o);
-#pragma unroll
-            for (int j = 0; j < 8; j++) ow[j] = pack2(d[2 * j], d[2 * j + 1]);
-            uint4 *dst = reinterpret_cast<uint4 *>(a.act + (size_t)p * NOUT + c0);
-            dst[0] = o[0];
-            dst[1] = o[1];
-          }
-        }
-      }
+      conv_epilogue<CIN, NOUT, EPI>(a, tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * NOUT), p);
+      tc_fence_before();
+      mbar_arrive(su32(acce + buf));
     }
   }
-  // drain: outstanding copies, then (after a failure) the MMAs already issued
-  cp_wait<0>();
-  if (failed && issued >= 0) mbar_wait(su32(mbar + issued % S), (issued / S) & 1);
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 8) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(SM::TMEM_COLS) : "memory");
   }
