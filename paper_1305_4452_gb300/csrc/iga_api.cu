@@ -302,8 +302,9 @@ static iga_status ensure_workspace(iga_s *h, int m, bool f32) {
     if (h->ctl) cudaFree(h->ctl);
     h->V = nullptr; h->red = nullptr; h->ctl = nullptr;
     CK(cudaMalloc((void **)&h->V, (size_t)(m + 1) * N * sizeof(double)));
+    // Gram-Schmidt partials of two passes in flight: 2 (m + 1) x nb (and >= the 304 of the norms)
     const int nb = gs_partition(N).nb > 304 ? gs_partition(N).nb : 304;
-    CK(cudaMalloc((void **)&h->red, (size_t)(m + 2) * nb * sizeof(double)));
+    CK(cudaMalloc((void **)&h->red, (size_t)(2 * m + 4) * nb * sizeof(double)));
     CK(cudaMalloc((void **)&h->ctl, (size_t)((m + 1) * m + 4 * m + 16) * sizeof(double)));
     h->V_m = m;
   }

@@ -16,6 +16,7 @@ namespace {
 
 constexpr int RED_THREADS = 256;
 constexpr int RED_BLOCKS = 304;  // 2 x 152 SMs
+constexpr int GS_THREADS = 512;  // Gram-Schmidt passes: one block of 16 warps per SM
 
 // GMRES scalar block layout (doubles) for restart m
 struct GmLayout {
@@ -179,18 +180,37 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_rows(const double *__res
   if (threadIdx.x == 0) out[i] = accumulate ? out[i] + acc : acc;
 }
 
-// Classical Gram-Schmidt passes over a block-contiguous row partition: block b
-// owns rows [b*per, min(N, (b+1)*per)).  With UPDATE the block first applies
-// w -= sum_i h[i] V[i] on its rows; then (DOTS) every warp takes basis vectors
-// i = warp, warp+8, ... and writes partial[i][b] = sum over the block's rows of
-// V[i][r] w[r], with w read from shared memory, or (NORM) the block writes
-// partial[b] = sum of w[r]^2.  One pass reads the active basis once; the fixed
-// partition and fixed shuffle/smem trees keep every sum independent of timing.
-template <bool UPDATE, bool NORM>
-__global__ void __launch_bounds__(RED_THREADS) k_gs_pass(const double *__restrict__ Vb, int64_t ld, int jp1,
-                                                         const double *__restrict__ h, double *__restrict__ w,
-                                                         double *__restrict__ partial, int64_t N, int per,
-                                                         const double *__restrict__ done) {
+// Classical Gram-Schmidt applied twice, as three passes over a block-contiguous
+// row partition (block b owns rows [b*per, min(N, (b+1)*per))), each reading the
+// active basis once:
+//   pass 1:  partial1[i][b] = sum over the block's rows of V[i][r] w[r]
+//   pass 2:  h1 = sum_b partial1 (every block forms the same sums, in the same
+//            order); H[:, j] = h1 (block 0); w -= V h1; partial2[i][b] = V[i] . w
+//   pass 3:  h2 = sum_b partial2; H[:, j] += h2 (block 0); w -= V h2;
+//            partial3[b] = sum of w[r]^2
+// followed by k_gs_finish (norm, Givens step, next basis vector).  Dots use one
+// warp per basis vector over the block's rows with w in shared memory; the
+// block-local sums of the partials make the separate reduction launches
+// unnecessary.  Every sum has a fixed shape and order.
+
+// out_sh[i] = sum_{b < nb} partial[i * nb + b], i < n: one warp per i, lanes
+// stride b in order, then a fixed shuffle tree (the same result in every block)
+__device__ void block_sum_cols(const double *__restrict__ partial, int nb, int n, double *out_sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < n; i += nw) {
+    double acc = 0.0;
+    for (int b = lane; b < nb; b += 32) acc += partial[(size_t)i * nb + b];
+    acc = warp_sum(acc);
+    if (lane == 0) out_sh[i] = acc;
+  }
+  __syncthreads();
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(GS_THREADS) k_gs_pass(const double *__restrict__ Vb, int64_t ld, int jp1,
+                                                        const double *__restrict__ prev, double *__restrict__ Hj,
+                                                        double *__restrict__ w, double *__restrict__ partial, int64_t N,
+                                                        int per, const double *__restrict__ done) {
   extern __shared__ double gs_sm[];
   double *ws = gs_sm;          // [per]
   double *hs = gs_sm + per;    // [jp1]
@@ -198,23 +218,24 @@ __global__ void __launch_bounds__(RED_THREADS) k_gs_pass(const double *__restric
   if (done[0] != 0.0) return;
   const int64_t a = (int64_t)blockIdx.x * per;
   const int cnt = (int)max((int64_t)0, min((int64_t)per, N - a));
-  if (UPDATE) {
-    for (int i = threadIdx.x; i < jp1; i += blockDim.x) hs[i] = h[i];
-    __syncthreads();
+  if (PASS >= 2) {
+    block_sum_cols(prev, gridDim.x, jp1, hs);
+    if (blockIdx.x == 0)
+      for (int i = threadIdx.x; i < jp1; i += blockDim.x) Hj[i] = (PASS == 2) ? hs[i] : Hj[i] + hs[i];
   }
   double sq = 0.0;
   for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
     double v = w[a + r];
-    if (UPDATE) {
+    if (PASS >= 2) {
       const double *col = Vb + a + r;
 #pragma unroll 4
       for (int i = 0; i < jp1; i++) v = fma(-hs[i], col[(size_t)i * ld], v);
       w[a + r] = v;
     }
-    if (NORM) sq = fma(v, v, sq);
+    if (PASS == 3) sq = fma(v, v, sq);
     else ws[r] = v;
   }
-  if (NORM) {
+  if (PASS == 3) {
     sq = block_sum(sq, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = sq;
     return;
@@ -228,22 +249,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_gs_pass(const double *__restric
     for (int r = lane; r < cnt; r += 32) acc = fma(v[r], ws[r], acc);
     acc = warp_sum(acc);
     if (lane == 0) partial[(size_t)i * gridDim.x + blockIdx.x] = acc;
-  }
-}
-
-// out[i] = sum_blk partial[i][blk] in index order, and add[i] += out[i] when add
-// is given (the second Gram-Schmidt pass's correction to column j of H)
-__global__ void __launch_bounds__(RED_THREADS) k_reduce_rows_add(const double *__restrict__ partial, int nb, double *__restrict__ out,
-                                                                 double *__restrict__ add, const double *__restrict__ done) {
-  __shared__ double sh[32];
-  if (done[0] != 0.0) return;
-  int i = blockIdx.x;
-  double acc = 0.0;
-  for (int k = threadIdx.x; k < nb; k += blockDim.x) acc += partial[(size_t)i * nb + k];
-  acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) {
-    out[i] = acc;
-    if (add) add[i] += acc;
   }
 }
 
@@ -295,20 +300,36 @@ __device__ void givens_step(double *__restrict__ gm, int m, int j, double tol) {
   fl[4] = hn;
 }
 
-__global__ void k_givens(double *__restrict__ gm, int m, int j, double tol) { givens_step(gm, m, j, tol); }
-
-// H[j+1][j] (as a sum of squares) = sum of the norm partials in index order,
-// then the Givens step for column j (one block)
-__global__ void __launch_bounds__(RED_THREADS) k_reduce_givens(const double *__restrict__ partial, int nb, double *__restrict__ gm,
-                                                               int m, int j, double tol) {
-  __shared__ double sh[32];
+// End of a GMRES iteration: ||w||^2 = sum of the pass-3 partials (every block,
+// same order); v_{j+1} = w / ||w||, z = dinv .* v_{j+1}; block 0 also stores
+// H[j+1][j] and runs the Givens step, which sets the done flag for the kernels
+// that follow (blocks of this kernel may still form v_{j+1}; it is then unused).
+__global__ void __launch_bounds__(GS_THREADS) k_gs_finish(const double *__restrict__ partial, int nb, const double *w,
+                                                          double *vnext, const double *__restrict__ dinv,
+                                                          double *__restrict__ z, int64_t N, int per,
+                                                          double *__restrict__ gm, int m, int j, double tol) {
+  __shared__ double hn2;
   GmLayout L = gm_layout(m);
   if (gm[L.flags] != 0.0) return;
-  double acc = 0.0;
-  for (int k = threadIdx.x; k < nb; k += blockDim.x) acc += partial[k];
-  acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) {
-    gm[L.H + (size_t)j * (m + 1) + j + 1] = acc;
+  if (threadIdx.x < 32) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 32) acc += partial[b];
+    acc = warp_sum(acc);
+    if (threadIdx.x == 0) hn2 = acc;
+  }
+  __syncthreads();
+  const double s2 = hn2;
+  const double hn = sqrt(s2);
+  const double inv = (hn > 0.0) ? 1.0 / hn : 0.0;
+  const int64_t a = (int64_t)blockIdx.x * per;
+  const int cnt = (int)max((int64_t)0, min((int64_t)per, N - a));
+  for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+    const double v = w[a + r] * inv;
+    vnext[a + r] = v;
+    z[a + r] = dinv[a + r] * v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    gm[L.H + (size_t)j * (m + 1) + j + 1] = s2;
     givens_step(gm, m, j, tol);
   }
 }
@@ -443,10 +464,12 @@ cudaError_t launch_diag_inv(iga_s *h, const void *vals, int is_f32, double *dinv
 }
 
 GsPartition gs_partition(int64_t N) {
-  // at least 4 blocks per SM; at most 2048 rows (16 KB of shared memory) per block
+  // one block per SM (the passes re-sum the previous pass's per-block partials in
+  // every block, so few blocks keep that cheap); more when a block would exceed
+  // 16384 rows (128 KB of shared memory for w)
   GsPartition g;
-  int64_t nb = (N + 2047) / 2048;
-  if (nb < 4 * 152) nb = 4 * 152;
+  int64_t nb = (N + 16383) / 16384;
+  if (nb < 152) nb = 152;
   g.per = (int)((N + nb - 1) / nb);
   if (g.per < 1) g.per = 1;
   g.nb = (int)((N + g.per - 1) / g.per);
@@ -482,12 +505,19 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
   double *fl_host = h->ctl_host;
   double *dinv = h->wk + 4 * N, *z = h->wk + 5 * N, *w = h->wk + 6 * N, *tmp = h->wk + 7 * N;
   double *scal = h->wk + 8 * N;        // device scalars
-  double *h2 = h->wk + 8 * N + 64;     // second Gram-Schmidt pass coefficients (m+1)
   double *Vb = h->V;
   int total = 0, rc = 1;
   *cerr = cudaSuccess;
   int eg = grid_for(N, 256, 4 * 152);
   const GsPartition gs = gs_partition(N);
+  {
+    const int smax = (int)((gs.per + m + 1) * sizeof(double));
+    if (smax > 48 * 1024) {
+      cudaFuncSetAttribute(k_gs_pass<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+      cudaFuncSetAttribute(k_gs_pass<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+      cudaFuncSetAttribute(k_gs_pass<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    }
+  }
   launch_diag_inv(h, vals, is_f32, dinv);
   IGA_LAUNCH(h, KC_VEC, (k_fill<<<eg, 256, 0, h->stream>>>(x, 0.0, N)));
   const int batch = 8;
@@ -512,17 +542,15 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
         double *Hj = gm + L.H + (size_t)j * (m + 1);
         if (is_f32) spmv_f32_launch(h, (const float *)vals, z, w, done);
         else spmv_launch<double>(h, (const double *)vals, z, w, done);
-        // classical Gram-Schmidt, applied twice: dots; update + dots; update + norm
+        // classical Gram-Schmidt, applied twice (three passes), then norm + Givens + next vector
         const int jp1 = j + 1;
         const size_t smem = (size_t)(gs.per + jp1) * sizeof(double);
-        IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<false, false><<<gs.nb, RED_THREADS, smem, h->stream>>>(Vb, ld, jp1, nullptr, w, h->red, N, gs.per, done)));
-        IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce_rows_add<<<jp1, RED_THREADS, 0, h->stream>>>(h->red, gs.nb, Hj, nullptr, done)));
-        IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<true, false><<<gs.nb, RED_THREADS, smem, h->stream>>>(Vb, ld, jp1, Hj, w, h->red, N, gs.per, done)));
-        IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce_rows_add<<<jp1, RED_THREADS, 0, h->stream>>>(h->red, gs.nb, h2, Hj, done)));
-        IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<true, true><<<gs.nb, RED_THREADS, smem, h->stream>>>(Vb, ld, jp1, h2, w, h->red, N, gs.per, done)));
-        IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce_givens<<<1, RED_THREADS, 0, h->stream>>>(h->red, gs.nb, gm, m, j, tol_abs)));
-        // the next basis vector is formed unless this was the last column
-        IGA_LAUNCH(h, KC_VEC, (k_normalize<<<eg, 256, 0, h->stream>>>(w, gm + L.flags + 4, Vb + (size_t)(j + 1) * ld, dinv, z, N, gm + L.flags)));
+        double *P1 = h->red, *P2 = h->red + (size_t)(m + 1) * gs.nb, *P3 = h->red;
+        IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<1><<<gs.nb, GS_THREADS, smem, h->stream>>>(Vb, ld, jp1, nullptr, Hj, w, P1, N, gs.per, done)));
+        IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<2><<<gs.nb, GS_THREADS, smem, h->stream>>>(Vb, ld, jp1, P1, Hj, w, P2, N, gs.per, done)));
+        IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<3><<<gs.nb, GS_THREADS, smem, h->stream>>>(Vb, ld, jp1, P2, Hj, w, P3, N, gs.per, done)));
+        IGA_LAUNCH(h, KC_VEC, (k_gs_finish<<<gs.nb, GS_THREADS, 0, h->stream>>>(P3, gs.nb, w, Vb + (size_t)(j + 1) * ld, dinv, z, N,
+                                                                               gs.per, gm, m, j, tol_abs)));
       }
       cudaMemcpyAsync(fl_host, gm + L.flags, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
       cudaError_t ce = cudaStreamSynchronize(h->stream);
