@@ -24,3 +24,18 @@ struct ConvArgs {
 // one-channel output padded to 16): FWD (16,H) and (H,H), LAST (H,16), BWD (H,H) and
 // (16,H).  Any other (cin, nout, epi) returns cudaErrorInvalidValue.
 cudaError_t launch_conv_tc(int cin, int nout, int epi, const ConvArgs &a, cudaStream_t stream);
+
+struct WgradArgs {
+  const __nv_bfloat16 *x;   // [P][CINP] layer input (channels beyond cin are zero)
+  const __nv_bfloat16 *dz;  // [P][ldz] output gradient, channels < cout used
+  int ldz, cout, cin;       // dz row length; real output / input channels
+  float *part;              // [nparts][NOUTP][9][CINP] per-CTA partial sums (scratch)
+  float *dw;                // [cout][9][cin] result (the parameter layout)
+  int nparts;               // CTAs (pixel ranges), <= 1024
+  int P, H, W, dil;
+  int *err;
+};
+
+// dW[co][tap][ci] = sum_p dZ[p][co] X[p + dil * off(tap)][ci] on the tensor cores, with
+// the input padded to CINP and the gradient channels to NOUTP (16, 32 or 64).
+cudaError_t launch_conv_wgrad_tc(int cinp, int noutp, const WgradArgs &a, cudaStream_t stream);

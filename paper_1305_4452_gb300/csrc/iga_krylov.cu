@@ -193,15 +193,23 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_rows(const double *__res
 // block-local sums of the partials make the separate reduction launches
 // unnecessary.  Every sum has a fixed shape and order.
 
-// out_sh[i] = sum_{b < nb} partial[i * nb + b], i < n: one warp per i, lanes
-// stride b in order, then a fixed shuffle tree (the same result in every block)
+// out_sh[i] = sum_{b < nb} partial[i * nb + b], i < n: eight lanes per i, lane t
+// summing b = t, t+8, ... in order, then a fixed 3-level shuffle tree (the same
+// result in every block); all loads of a thread are independent
 __device__ void block_sum_cols(const double *__restrict__ partial, int nb, int n, double *out_sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = warp; i < n; i += nw) {
+  const int g = threadIdx.x >> 3, t = threadIdx.x & 7, ng = blockDim.x >> 3;
+  for (int i0 = 0; i0 < n; i0 += ng) {
+    const int i = i0 + g;
     double acc = 0.0;
-    for (int b = lane; b < nb; b += 32) acc += partial[(size_t)i * nb + b];
-    acc = warp_sum(acc);
-    if (lane == 0) out_sh[i] = acc;
+    if (i < n) {
+      const double *pi = partial + (size_t)i * nb;
+#pragma unroll 4
+      for (int b = t; b < nb; b += 8) acc += pi[b];
+    }
+    acc += __shfl_down_sync(0xffffffffu, acc, 4, 8);
+    acc += __shfl_down_sync(0xffffffffu, acc, 2, 8);
+    acc += __shfl_down_sync(0xffffffffu, acc, 1, 8);
+    if (t == 0 && i < n) out_sh[i] = acc;
   }
   __syncthreads();
 }

@@ -5,10 +5,10 @@
 // Network: L layers of 3x3 convolutions with per-layer dilation and "same" zero
 // padding on an H x W grid (NHWC activations), SiLU between layers, a linear last
 // layer with one output channel, multiplied by a mask (zero on Dirichlet rows).
-// The forward convolutions and the input-gradient (transposed) convolutions run
-// as implicit GEMMs on the tcgen05 tensor cores with fused bias + SiLU and SiLU'
-// epilogues (iga_conv_tc.cu); the weight gradients are an explicit im2col plus a
-// split-K GEMM on mma.sync (m16n8k16).  Operands are BF16 with FP32 accumulation.
+// The forward convolutions, the input-gradient (transposed) convolutions and the
+// weight gradients run as implicit GEMMs on the tcgen05 tensor cores, with fused
+// bias + SiLU and SiLU' epilogues (iga_conv_tc.cu).  Operands are BF16 with FP32
+// accumulation.
 // Master weights, Adam moments, gradients and the loss are FP32; activations are
 // stored in BF16 for the GEMMs and FP32 where the backward pass needs them.  Every
 // reduction (split-K weight gradients, bias gradients, loss) has a fixed order.
@@ -30,128 +30,6 @@ typedef __nv_bfloat16 bf16;
 
 namespace {
 
-constexpr int GBM = 128, GBN = 64, GBK = 32, GLD = GBK + 8;
-
-// C[M][N] (+)= sum_k A(m,k) B(k,n).  A: row-major [M][K] (A_COL = false) or [K][M];
-// B: [N][K] (B_KN = false) or [K][N].  blockIdx.z selects a K chunk whose result
-// goes to C + z * split_stride (split-K); bias (if any) is added by chunk 0.
-template <bool A_COL, bool B_KN>
-__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const bf16 *__restrict__ A, int64_t lda,
-                                              const bf16 *__restrict__ B, int64_t ldb, float *__restrict__ C, int64_t ldc,
-                                              int64_t split_stride, int kchunk, const float *__restrict__ bias) {
-  __shared__ __align__(16) bf16 As[GBM][GLD];
-  __shared__ __align__(16) bf16 Bs[GBN][GLD];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int m0 = blockIdx.x * GBM, n0 = blockIdx.y * GBN;
-  const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
-  const int wm = (warp & 3) * 32, wn = (warp >> 2) * 32;
-  const int g = lane >> 2, t = lane & 3;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; i++)
-#pragma unroll
-    for (int j = 0; j < 4; j++) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
-  const bf16 zero = __float2bfloat16(0.f);
-  // 8-element (16-byte) chunks along the contiguous dimension of each operand;
-  // a chunk that is fully in range and 16-byte aligned is loaded with one vector
-  // load, otherwise element by element with zero fill
-  const bool avec = (lda % 8) == 0 && ((uintptr_t)A % 16) == 0;
-  const bool bvec = (ldb % 8) == 0 && ((uintptr_t)B % 16) == 0;
-  for (int k0 = kbeg; k0 < kend; k0 += GBK) {
-    for (int c = tid; c < GBM * GBK / 8; c += 256) {
-      int r, kk;  // chunk origin in the tile
-      if (!A_COL) { r = c / (GBK / 8); kk = (c % (GBK / 8)) * 8; } else { kk = c / (GBM / 8); r = (c % (GBM / 8)) * 8; }
-      const int gm = m0 + r, gk = k0 + kk;
-      if (!A_COL) {
-        if (avec && gm < M && gk + 8 <= kend) {
-          const uint4 v = *reinterpret_cast<const uint4 *>(A + (int64_t)gm * lda + gk);
-          *reinterpret_cast<uint4 *>(&As[r][kk]) = v;
-        } else {
-          for (int u = 0; u < 8; u++) As[r][kk + u] = (gm < M && gk + u < kend) ? A[(int64_t)gm * lda + gk + u] : zero;
-        }
-      } else {
-        if (avec && gk < kend && gm + 8 <= M) {
-          const uint4 v = *reinterpret_cast<const uint4 *>(A + (int64_t)gk * lda + gm);
-          const bf16 *e = reinterpret_cast<const bf16 *>(&v);
-          for (int u = 0; u < 8; u++) As[r + u][kk] = e[u];
-        } else {
-          for (int u = 0; u < 8; u++) As[r + u][kk] = (gk < kend && gm + u < M) ? A[(int64_t)gk * lda + gm + u] : zero;
-        }
-      }
-    }
-    for (int c = tid; c < GBN * GBK / 8; c += 256) {
-      int r, kk;
-      if (!B_KN) { r = c / (GBK / 8); kk = (c % (GBK / 8)) * 8; } else { kk = c / (GBN / 8); r = (c % (GBN / 8)) * 8; }
-      const int gn = n0 + r, gk = k0 + kk;
-      if (!B_KN) {
-        if (bvec && gn < N && gk + 8 <= kend) {
-          const uint4 v = *reinterpret_cast<const uint4 *>(B + (int64_t)gn * ldb + gk);
-          *reinterpret_cast<uint4 *>(&Bs[r][kk]) = v;
-        } else {
-          for (int u = 0; u < 8; u++) Bs[r][kk + u] = (gn < N && gk + u < kend) ? B[(int64_t)gn * ldb + gk + u] : zero;
-        }
-      } else {
-        if (bvec && gk < kend && gn + 8 <= N) {
-          const uint4 v = *reinterpret_cast<const uint4 *>(B + (int64_t)gk * ldb + gn);
-          const bf16 *e = reinterpret_cast<const bf16 *>(&v);
-          for (int u = 0; u < 8; u++) Bs[r + u][kk] = e[u];
-        } else {
-          for (int u = 0; u < 8; u++) Bs[r + u][kk] = (gk < kend && gn + u < N) ? B[(int64_t)gk * ldb + gn + u] : zero;
-        }
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ks = 0; ks < GBK; ks += 16) {
-      uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; i++) {
-        const bf16 *r0 = &As[wm + i * 16 + g][ks + 2 * t];
-        const bf16 *r1 = &As[wm + i * 16 + g + 8][ks + 2 * t];
-        af[i][0] = *reinterpret_cast<const uint32_t *>(r0);
-        af[i][1] = *reinterpret_cast<const uint32_t *>(r1);
-        af[i][2] = *reinterpret_cast<const uint32_t *>(r0 + 8);
-        af[i][3] = *reinterpret_cast<const uint32_t *>(r1 + 8);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; j++) {
-        const bf16 *c0 = &Bs[wn + j * 8 + g][ks + 2 * t];
-        bfr[j][0] = *reinterpret_cast<const uint32_t *>(c0);
-        bfr[j][1] = *reinterpret_cast<const uint32_t *>(c0 + 8);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-          asm volatile(
-              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-              : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-              : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bfr[j][0]), "r"(bfr[j][1]));
-    }
-    __syncthreads();
-  }
-  float *Cz = C + (int64_t)blockIdx.z * split_stride;
-#pragma unroll
-  for (int i = 0; i < 2; i++)
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-      const int row = m0 + wm + i * 16 + g, col = n0 + wn + j * 8 + 2 * t;
-#pragma unroll
-      for (int h = 0; h < 2; h++) {
-        const int rr = row + 8 * h;
-        if (rr >= M) continue;
-#pragma unroll
-        for (int cc = 0; cc < 2; cc++) {
-          const int cn = col + cc;
-          if (cn >= N) continue;
-          float v = acc[i][j][2 * h + cc];
-          if (bias && blockIdx.z == 0) v += bias[cn];
-          Cz[(int64_t)rr * ldc + cn] = v;
-        }
-      }
-    }
-}
-
 // out[i] = sum_z part[z][i] in z order
 __global__ void k_sum_splits(const float *__restrict__ part, int nsplit, int64_t n, float *__restrict__ out, int accumulate) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -159,26 +37,6 @@ __global__ void k_sum_splits(const float *__restrict__ part, int nsplit, int64_t
   float s = 0.f;
   for (int z = 0; z < nsplit; z++) s += part[(int64_t)z * n + i];
   out[i] = accumulate ? out[i] + s : s;
-}
-
-// col[p][tap*C + c] = x[p + offset(tap)][c] (0 outside the grid); p = (b, y, x)
-__global__ void k_im2col(const bf16 *__restrict__ x, int B, int H, int W, int C, int dil, bf16 *__restrict__ col) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t total = (int64_t)B * H * W * 9 * C;
-  if (t >= total) return;
-  int c = (int)(t % C);
-  int tap = (int)((t / C) % 9);
-  int64_t p = t / (9 * C);
-  int xx = (int)(p % W), yy = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
-  int sy = yy + dil * (tap / 3 - 1), sx = xx + dil * (tap % 3 - 1);
-  bf16 v = __float2bfloat16(0.f);
-  if (sy >= 0 && sy < H && sx >= 0 && sx < W) v = x[(((int64_t)b * H + sy) * W + sx) * C + c];
-  col[t] = v;
-}
-
-__global__ void k_f32_to_bf16(const float *__restrict__ x, bf16 *__restrict__ y, int64_t n) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) y[i] = __float2bfloat16(x[i]);
 }
 
 // features x[p][c] (FP32, c < C) -> xp[p][16] BF16 zero-padded for the tensor-core
@@ -353,7 +211,8 @@ struct iga_nn_s {
   std::vector<bf16 *> X;      // inputs of each layer, BF16 [P][Cin]
   bf16 *X0p = nullptr;        // network input padded to 16 channels
   std::vector<float *> Z;     // pre-activations FP32 [P][Cout]
-  bf16 *col = nullptr;        // im2col [P][9 Cmax] (weight gradients)
+  float *wpart = nullptr;     // per-CTA partial weight gradients [nparts][64][9][64]
+  int nparts = 0;
   float *dZ = nullptr, *dZ2 = nullptr;  // output gradients FP32 [P][Cmax] (ping-pong)
   bf16 *dZb = nullptr, *dZb2 = nullptr; // their BF16 copies
   bf16 *dZb16 = nullptr;      // last layer's gradient padded to 16 channels
@@ -368,7 +227,7 @@ struct iga_nn_s {
 };
 
 static void nn_release(iga_nn_s *n) {
-  void *ps[] = {n->w, n->g, n->m, n->v, n->wops, n->X0p, n->col, n->dZ, n->dZ2, n->dZb, n->dZb2, n->dZb16,
+  void *ps[] = {n->w, n->g, n->m, n->v, n->wops, n->X0p, n->wpart, n->dZ, n->dZ2, n->dZb, n->dZb2, n->dZb16,
                 n->part, n->y, n->lossv, n->tc_err};
   for (void *p : ps)
     if (p) cudaFree(p);
@@ -388,16 +247,6 @@ static void nn_release(iga_nn_s *n) {
   } while (0)
 
 static thread_local std::string g_nn_err;
-
-template <bool AC, bool BK>
-static void gemm(iga_nn_s *n, int M, int N, int K, const bf16 *A, int64_t lda, const bf16 *B, int64_t ldb, float *C,
-                 int64_t ldc, const float *bias, int splits = 1) {
-  int kchunk = (K + splits - 1) / splits;
-  kchunk = (kchunk + GBK - 1) / GBK * GBK;
-  splits = (K + kchunk - 1) / kchunk;
-  dim3 grid((M + GBM - 1) / GBM, (N + GBN - 1) / GBN, splits);
-  k_gemm<AC, BK><<<grid, 256, 0, n->stream>>>(M, N, K, A, lda, B, ldb, C, ldc, (int64_t)M * ldc, kchunk, bias);
-}
 
 extern "C" iga_status iga_nn_create(int height, int width, int in_channels, int hidden, int layers, const int *dilations,
                                     int max_batch, uint64_t seed, void *stream, iga_nn_t *out) {
@@ -473,18 +322,24 @@ extern "C" iga_status iga_nn_create(int height, int width, int in_channels, int 
   for (int l = 0; l < layers; l++) {
     bf16 *x = nullptr;
     float *z = nullptr;
-    NCK2(cudaMalloc((void **)&x, P * n->layers[l].cin * sizeof(bf16)));
+    if (l > 0) NCK2(cudaMalloc((void **)&x, P * n->layers[l].cin * sizeof(bf16)));  // layer 0 reads X0p
     n->X.push_back(x);
     NCK2(cudaMalloc((void **)&z, P * n->layers[l].cout * sizeof(float)));
     n->Z.push_back(z);
   }
-  NCK2(cudaMalloc((void **)&n->col, P * 9 * cmax * sizeof(bf16)));
+  {
+    int dev = 0, sms = 0;
+    NCK2(cudaGetDevice(&dev));
+    NCK2(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    n->nparts = std::min(1024, std::max(1, sms));
+  }
+  NCK2(cudaMalloc((void **)&n->wpart, (size_t)n->nparts * 64 * 9 * 64 * sizeof(float)));
   NCK2(cudaMalloc((void **)&n->dZ, P * cmax * sizeof(float)));
   NCK2(cudaMalloc((void **)&n->dZ2, P * cmax * sizeof(float)));
   NCK2(cudaMalloc((void **)&n->dZb, P * cmax * sizeof(bf16)));
   NCK2(cudaMalloc((void **)&n->dZb2, P * cmax * sizeof(bf16)));
   NCK2(cudaMalloc((void **)&n->dZb16, P * 16 * sizeof(bf16)));
-  n->part_n = std::max<int64_t>((int64_t)64 * 9 * cmax * cmax, 4096 * (int64_t)cmax);
+  n->part_n = std::max<int64_t>(2 * 256, (P + 4095) / 4096 * (int64_t)cmax);  // loss and bias-gradient partials
   NCK2(cudaMalloc((void **)&n->part, n->part_n * sizeof(float)));
   NCK2(cudaMalloc((void **)&n->y, P * sizeof(float)));
   NCK2(cudaMalloc((void **)&n->lossv, 4 * sizeof(float)));
@@ -573,7 +428,7 @@ static iga_status nn_forward(iga_nn_s *n, const float *x, int B, const float *ma
     int cnt = std::max(ly.np * 9 * ly.cp, ly.cin * 9 * ly.np);
     k_prep_w<<<g1(cnt), 256, 0, n->stream>>>(n->w + ly.woff, ly.cin, ly.cout, ly.cp, ly.np, ly.wk, ly.wt);
   }
-  k_pad_input<<<g1(P * 16), 256, 0, n->stream>>>(x, n->cin, P, n->X0p, train ? n->X[0] : nullptr);
+  k_pad_input<<<g1(P * 16), 256, 0, n->stream>>>(x, n->cin, P, n->X0p, nullptr);
   for (int l = 0; l < n->L; l++) {
     const NNLayer &ly = n->layers[l];
     ConvArgs a = conv_args(n, B);
@@ -630,20 +485,30 @@ extern "C" iga_status iga_nn_loss_grad(iga_nn_t n, const float *x, const float *
   bf16 *dzb = n->dZb, *dzb_next = n->dZb2;
   for (int l = n->L - 1; l >= 0; l--) {
     const NNLayer &ly = n->layers[l];
-    const int K = 9 * ly.cin;
     // bias gradient: column sums of dZ
     const int64_t chunk = 4096;
     const int nch = (int)((P + chunk - 1) / chunk);
     k_colsum_partial<<<nch, 256, 0, n->stream>>>(dz, P, ly.cout, chunk, n->part);
     k_sum_splits<<<g1(ly.cout), 256, 0, n->stream>>>(n->part, nch, ly.cout, n->g + ly.boff, 0);
-    // weight gradient: dW[cout][K] = dZ^T (cout x P) * col (P x K), split over P
-    k_im2col<<<g1(P * K), 256, 0, n->stream>>>(n->X[l], B, n->H, n->W, ly.cin, ly.dil, n->col);
-    int splits = (int)std::min<int64_t>(64, std::max<int64_t>(1, P / 2048));
-    while ((int64_t)splits * ly.cout * K > n->part_n) splits--;
-    gemm<true, true>(n, ly.cout, K, (int)P, dzb, ly.cout, n->col, K, n->part, K, nullptr, splits);
-    int kchunk = ((int)((P + splits - 1) / splits) + GBK - 1) / GBK * GBK;
-    int used = (int)((P + kchunk - 1) / kchunk);
-    k_sum_splits<<<g1((int64_t)ly.cout * K), 256, 0, n->stream>>>(n->part, used, (int64_t)ly.cout * K, n->g + ly.woff, 0);
+    // weight gradient on the tensor cores: dW[co][tap][ci] = sum_p dZ[p][co] X[p + off(tap)][ci],
+    // one partial per pixel range, summed in a fixed order
+    {
+      WgradArgs w{};
+      w.x = (l == 0) ? n->X0p : n->X[l];
+      w.dz = (l == n->L - 1) ? n->dZb16 : dzb;
+      w.ldz = ly.np;
+      w.cout = ly.cout;
+      w.cin = ly.cin;
+      w.part = n->wpart;
+      w.dw = n->g + ly.woff;
+      w.nparts = n->nparts;
+      w.P = (int)P;
+      w.H = n->H;
+      w.W = n->W;
+      w.dil = ly.dil;
+      w.err = n->tc_err;
+      TCK(launch_conv_wgrad_tc(ly.cp, ly.np, w, n->stream));
+    }
     if (l > 0) {
       // dZ of the layer below = (transposed convolution of dZ) * SiLU'(Z below), on the tensor cores
       ConvArgs a = conv_args(n, B);
