@@ -375,6 +375,7 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
   // stiffness part is rebuilt once per solve (reuse across Newton steps only)
   h->K_valid = false;
   h->K_valid_f = false;
+  h->q00_valid = false;
   CK(launch_residual(h, U, F));
   double fn;
   st = norm_host(h, F, &fn);
@@ -414,11 +415,16 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
     for (int ls = 0; ls <= 10; ls++) {
       IGA_LAUNCH(h, KC_VEC, (k_axpby<<<eg, 256, 0, h->stream>>>(U, alpha, dU, Ut, N)));
       // with the stiffness assembled (FP64), F = K U + reaction(U)
+      h->q00_valid = false;
       if (split) CK(launch_residual_split(h, Ut, Ft, h->Kstiff, h->wk + 7 * N));
       else CK(launch_residual(h, Ut, Ft));
       st = norm_host(h, Ft, &ft);
       if (st != IGA_OK) return st;
-      if (isfinite(ft) && ft < fn) { ok = true; break; }
+      if (isfinite(ft) && ft < fn) {
+        ok = true;
+        h->q00_valid = split;  // the split residual left Q00 at the accepted point
+        break;
+      }
       alpha *= 0.5;
     }
     k++;

@@ -425,7 +425,8 @@ __global__ void k_gather_residual(DirArgs d0, DirArgs d1, DirArgs d2, const doub
 // ---------------------------------------------------------------------------
 //
 // With RES the same interpolation yields the reaction part of the residual
-// instead: s = -jw/W * lambda * exp(u) at the Gauss points, projected back on
+// instead (and the reaction part of Q00 at the same U, for the Jacobian that
+// follows an accepted line-search point): s = -jw/W * lambda * exp(u) at the Gauss points, projected back on
 // the element's functions (value tables only) into Fe[e][A] (times w_A).  The
 // Newton solver adds it to K U, K the assembled U-independent stiffness: since
 // Eq. (residual) is K U plus this term under the same quadrature, F(U) then
@@ -433,7 +434,8 @@ __global__ void k_gather_residual(DirArgs d0, DirArgs d1, DirArgs d2, const doub
 template <int DIM, int P, int NE, bool RES>
 __global__ void __launch_bounds__(128) k_q00(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ U,
                                              const double *__restrict__ wts, const double *__restrict__ geom, GeomLayout gl,
-                                             double lambda, double cs, double cr, double *__restrict__ Q00, int64_t nelem) {
+                                             double lambda, double cs, double cr, double *__restrict__ Q00, int64_t nelem,
+                                             double *__restrict__ q00_out) {
   using SM = ResSmem<DIM, P>;
   constexpr int N1 = SM::N1, Q = SM::Q, NEN = SM::NEN, NQ = SM::NQ;
   extern __shared__ double smem[];
@@ -514,7 +516,10 @@ __global__ void __launch_bounds__(128) k_q00(DirArgs d0, DirArgs d1, DirArgs d2,
     }
     const double *rec = geom + (size_t)e * gl.nf * NQ + qp;
     if (RES) {
-      (base + SM::TAB + NEN)[qp] = -rec[gl.jwW * NQ] * lambda * exp(ut * rec[gl.invW * NQ]);
+      const double lex = lambda * exp(ut * rec[gl.invW * NQ]);
+      (base + SM::TAB + NEN)[qp] = -rec[gl.jwW * NQ] * lex;
+      // the reaction part of Q00 at the same point, for the next Jacobian
+      if (q00_out) q00_out[(size_t)e * NQ + qp] = -rec[gl.jwW2 * NQ] * lex;
       continue;
     }
     double v = 0.0;
@@ -693,12 +698,12 @@ cudaError_t launch_residual_into(iga_s *h, const double *U, double *F, double *F
 
 cudaError_t launch_q00(iga_s *h, const double *U, double cs, double cr) {
   DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
-  constexpr int NE = 4;
+  constexpr int NE = 8;  // value-only interpolation: more elements per CTA
   unsigned grid = (unsigned)((h->nelem + NE - 1) / NE);
   IGA_LAUNCH(h, KC_Q00, DISPATCH_DP(h->dim, h->p, ({
     size_t sm = res_smem<D, PP>(NE);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_q00<D, PP, NE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_q00<D, PP, NE, false><<<grid, 128, sm, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, h->lambda, cs, cr, h->Q00, h->nelem);
+    k_q00<D, PP, NE, false><<<grid, 128, sm, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, h->lambda, cs, cr, h->Q00, h->nelem, nullptr);
   })));
   return cudaGetLastError();
 }
@@ -712,7 +717,7 @@ cudaError_t launch_residual_split(iga_s *h, const double *U, double *F, const do
   IGA_LAUNCH(h, KC_RES_ELEM, DISPATCH_DP(h->dim, h->p, ({
     size_t sm = res_smem<D, PP>(NE);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_q00<D, PP, NE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_q00<D, PP, NE, true><<<grid, 128, sm, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, h->lambda, 0.0, 1.0, h->Fe, h->nelem);
+    k_q00<D, PP, NE, true><<<grid, 128, sm, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, h->lambda, 0.0, 1.0, h->Fe, h->nelem, h->Q00);
   })));
   unsigned g2 = (unsigned)((h->N + 255) / 256);
   if (h->dim == 3)

@@ -148,6 +148,7 @@ struct iga_s {
   double *Mred = nullptr;      // reaction-only contraction on the CSR layout
   float *Mred_f = nullptr;
   bool K_valid = false, K_valid_f = false;  // Kstiff / Kstiff_f hold the current stiffness
+  bool q00_valid = false;      // Q00 holds the reaction part of Q00 at the current Newton iterate
   double *Uhost_dev = nullptr; // device copy of U for the host-buffer solve
   // mixed-precision Jacobian (tensor cores)
   float *geom32 = nullptr;     // [nelem][slots][nq] FP32 geometry factors
@@ -178,7 +179,8 @@ cudaError_t launch_residual(iga_s *h, const double *U, double *F);
 // Q00 = cs * g^T S g - cr * jw/W^2 * lambda * exp(u) at every Gauss point (U may be null when cr == 0)
 cudaError_t launch_q00(iga_s *h, const double *U, double cs, double cr);
 // F(U) = K U + reaction(U) with Dirichlet rows, K the assembled stiffness without
-// the Dirichlet fix (Jacobian mode 1); KU: scratch of N doubles
+// the Dirichlet fix (Jacobian mode 1); KU: scratch of N doubles.  Also leaves the
+// reaction part of Q00 at U in h->Q00 (see iga_s::q00_valid).
 cudaError_t launch_residual_split(iga_s *h, const double *U, double *F, const double *K, double *KU);
 
 // ---- Jacobian stages (iga_jacobian.cu) ----

@@ -46,9 +46,47 @@ template <int PLAN, int DIM> struct Shape {
 //   3D: G0 (00,00)  G1 (10,00)  G2 (11,00)  G3 (00,10)  G4 (10,01)  G5 (00,11)
 //       [(01,00), (00,01), (01,10) are the pair-transposes of G1, G3, G4]
 //   2D: G0 (00)  G1 (10)  G2 (11)   [(01) is the transpose of G1]
+// The reaction-only plan has one contraction per output, so a CTA takes
+// STAGE1_MASS_LINES consecutive axis-1 lines to give its threads enough work.
+constexpr int STAGE1_MASS_LINES = 8;
+
 template <typename T, int DIM, int P, int PLAN>
 __global__ void __launch_bounds__(256) k_stage1(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ geom,
                                                 const double *__restrict__ Q00, GeomLayout gl, T *__restrict__ out) {
+  if (PLAN == PLAN_MASS) {
+    // lines x1 = blockIdx.x * LINES + l; each line's Q00 in shared memory
+    constexpr int Q = P + 1, NQ = ipow<DIM>(Q), LINES = STAGE1_MASS_LINES;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *lines = reinterpret_cast<T *>(smem_raw);  // [LINES][X0]
+    const int X0 = d0.X, x2 = blockIdx.y;
+    const int e2 = x2 / Q, g2 = x2 % Q;
+    const int x1a = blockIdx.x * LINES, nl = min(LINES, d1.X - x1a);
+    for (int idx = threadIdx.x; idx < nl * X0; idx += blockDim.x) {
+      const int l = idx / X0, x0 = idx % X0, x1 = x1a + l;
+      const int e0 = x0 / Q, g0 = x0 % Q, e1 = x1 / Q, g1 = x1 % Q;
+      const int64_t e = e0 + (int64_t)d0.nel * (e1 + (int64_t)d1.nel * e2);
+      lines[idx] = (T)Q00[(size_t)e * NQ + g0 + Q * (g1 + Q * g2)];
+    }
+    __syncthreads();
+    // one pair per thread, all lines at once: each table value serves LINES FMAs
+    const T *tab = ptab<T>(d0);
+    for (int pi = threadIdx.x; pi < d0.np; pi += blockDim.x) {
+      const int xs = d0.pair_x0[pi], np = d0.pair_np[pi];
+      const T *pv = tab + (size_t)d0.pair_po[pi] * IGA_PVS;
+      T acc[LINES];
+#pragma unroll
+      for (int l = 0; l < LINES; l++) acc[l] = 0;
+      for (int k = 0; k < np; k++) {
+        const T p00 = pv[IGA_PVS * k];
+#pragma unroll
+        for (int l = 0; l < LINES; l++) acc[l] = fma(p00, lines[l * X0 + xs + k], acc[l]);
+      }
+#pragma unroll
+      for (int l = 0; l < LINES; l++)
+        if (l < nl) out[((size_t)x2 * d1.X + x1a + l) * d0.np + pi] = acc[l];
+    }
+    return;
+  }
   constexpr int Q = P + 1, NQ = ipow<DIM>(Q);
   using SH = Shape<PLAN, DIM>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -278,8 +316,9 @@ __global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d
 template <typename T, int DIM, int PLAN>
 cudaError_t run_stage1(iga_s *h, T *T1) {
   DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
-  dim3 grid(a1.X, DIM == 3 ? a2.X : 1);
-  size_t sm = (size_t)Shape<PLAN, DIM>::NS * a0.X * sizeof(T);
+  const int lines = (PLAN == PLAN_MASS) ? STAGE1_MASS_LINES : 1;
+  dim3 grid((a1.X + lines - 1) / lines, DIM == 3 ? a2.X : 1);
+  size_t sm = (size_t)(PLAN == PLAN_MASS ? lines : Shape<PLAN, DIM>::NS) * a0.X * sizeof(T);
   IGA_LAUNCH(h, KC_STAGE1, DISPATCH_P(h->p, ({
     auto kern = k_stage1<T, DIM, PP, PLAN>;
     if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -313,8 +352,12 @@ cudaError_t jacobian(iga_s *h, const double *U, V *vals, int mode, const V *base
   // mode 0: full, Dirichlet-fixed; 1: stiffness only (U-independent), unfixed;
   // 2: base (a mode-1 stiffness) + reaction, Dirichlet-fixed
   double cs = (mode == 2) ? 0.0 : 1.0, cr = (mode == 1) ? 0.0 : 1.0;
-  cudaError_t ce = launch_q00(h, U, cs, cr);
-  if (ce) return ce;
+  // mode 2 after an accepted split-residual evaluation at this U: Q00 is already there
+  if (!(mode == 2 && h->q00_valid)) {
+    cudaError_t ce = launch_q00(h, U, cs, cr);
+    if (ce) return ce;
+  }
+  h->q00_valid = false;
   if (mode == 2) {
     if (!base) return cudaErrorInvalidValue;
     return h->dim == 3 ? run_stages<T, V, 3, PLAN_MASS>(h, vals, base, 1) : run_stages<T, V, 2, PLAN_MASS>(h, vals, base, 1);

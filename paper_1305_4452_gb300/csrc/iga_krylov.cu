@@ -16,7 +16,7 @@ namespace {
 
 constexpr int RED_THREADS = 256;
 constexpr int RED_BLOCKS = 304;  // 2 x 152 SMs
-constexpr int GS_THREADS = 512;  // Gram-Schmidt passes: one block of 16 warps per SM
+constexpr int GS_THREADS = 1024;  // Gram-Schmidt passes: one block of 32 warps per SM
 
 // GMRES scalar block layout (doubles) for restart m
 struct GmLayout {
@@ -220,8 +220,9 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_pass(const double *__restrict
                                                         double *__restrict__ w, double *__restrict__ partial, int64_t N,
                                                         int per, const double *__restrict__ done) {
   extern __shared__ double gs_sm[];
-  double *ws = gs_sm;          // [per]
-  double *hs = gs_sm + per;    // [jp1]
+  double *ws = gs_sm;                   // [per]
+  double *hs = gs_sm + per;             // [jp1]
+  double *dp = gs_sm + per + jp1;       // [GS_THREADS / 32] dot partials of the (column, chunk) items
   __shared__ double sh[32];
   if (done[0] != 0.0) return;
   const int64_t a = (int64_t)blockIdx.x * per;
@@ -232,16 +233,30 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_pass(const double *__restrict
       for (int i = threadIdx.x; i < jp1; i += blockDim.x) Hj[i] = (PASS == 2) ? hs[i] : Hj[i] + hs[i];
   }
   double sq = 0.0;
-  for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
-    double v = w[a + r];
+  // two rows per thread and step: two independent FMA chains, their loads interleaved
+  const int T = blockDim.x;
+  for (int r = threadIdx.x; r < cnt; r += 2 * T) {
+    const int r2 = r + T;
+    const bool two = r2 < cnt;
+    double v = w[a + r], v2 = two ? w[a + r2] : 0.0;
     if (PASS >= 2) {
-      const double *col = Vb + a + r;
+      const double *c1 = Vb + a + r, *c2 = Vb + a + (two ? r2 : r);
 #pragma unroll 4
-      for (int i = 0; i < jp1; i++) v = fma(-hs[i], col[(size_t)i * ld], v);
+      for (int i = 0; i < jp1; i++) {
+        const double hi = hs[i];
+        v = fma(-hi, c1[(size_t)i * ld], v);
+        v2 = fma(-hi, c2[(size_t)i * ld], v2);
+      }
       w[a + r] = v;
+      if (two) w[a + r2] = v2;
     }
-    if (PASS == 3) sq = fma(v, v, sq);
-    else ws[r] = v;
+    if (PASS == 3) {
+      sq = fma(v, v, sq);
+      if (two) sq = fma(v2, v2, sq);
+    } else {
+      ws[r] = v;
+      if (two) ws[r2] = v2;
+    }
   }
   if (PASS == 3) {
     sq = block_sum(sq, sh);
@@ -249,14 +264,35 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_pass(const double *__restrict
     return;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = warp; i < jp1; i += nw) {
-    const double *v = Vb + (size_t)i * ld + a;
-    double acc = 0.0;
+  // dots: items (column i, row chunk c), R chunks per column so that the warps are
+  // busy even for few columns; chunk sums in shared memory, then per column in order
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
+  const int R = jp1 >= nw ? 1 : nw / jp1;
+  const int items = jp1 * R, clen = (cnt + R - 1) / R;
+  for (int base = 0; base < items; base += nw) {
+    const int it = base + warp;
+    if (it < items) {
+      const int i = it / R, c = it - i * R;
+      const int r0 = c * clen, r1 = min(cnt, r0 + clen);
+      const double *v = Vb + (size_t)i * ld + a;
+      double acc = 0.0;
 #pragma unroll 4
-    for (int r = lane; r < cnt; r += 32) acc = fma(v[r], ws[r], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) partial[(size_t)i * gridDim.x + blockIdx.x] = acc;
+      for (int r = r0 + lane; r < r1; r += 32) acc = fma(v[r], ws[r], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) dp[warp] = acc;
+    }
+    __syncthreads();
+    // columns completed in this round: items [base, base + nw)
+    if (threadIdx.x < nw) {
+      const int it0 = base + threadIdx.x;
+      if (it0 < items && (it0 % R) == 0) {
+        const int i = it0 / R;
+        double acc = 0.0;
+        for (int c = 0; c < R; c++) acc += dp[threadIdx.x + c];
+        partial[(size_t)i * gridDim.x + blockIdx.x] = acc;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -519,7 +555,7 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
   int eg = grid_for(N, 256, 4 * 152);
   const GsPartition gs = gs_partition(N);
   {
-    const int smax = (int)((gs.per + m + 1) * sizeof(double));
+    const int smax = (int)((gs.per + m + 1 + GS_THREADS / 32) * sizeof(double));
     if (smax > 48 * 1024) {
       cudaFuncSetAttribute(k_gs_pass<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
       cudaFuncSetAttribute(k_gs_pass<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
@@ -552,7 +588,7 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
         else spmv_launch<double>(h, (const double *)vals, z, w, done);
         // classical Gram-Schmidt, applied twice (three passes), then norm + Givens + next vector
         const int jp1 = j + 1;
-        const size_t smem = (size_t)(gs.per + jp1) * sizeof(double);
+        const size_t smem = (size_t)(gs.per + jp1 + GS_THREADS / 32) * sizeof(double);
         double *P1 = h->red, *P2 = h->red + (size_t)(m + 1) * gs.nb, *P3 = h->red;
         IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<1><<<gs.nb, GS_THREADS, smem, h->stream>>>(Vb, ld, jp1, nullptr, Hj, w, P1, N, gs.per, done)));
         IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<2><<<gs.nb, GS_THREADS, smem, h->stream>>>(Vb, ld, jp1, P1, Hj, w, P2, N, gs.per, done)));
