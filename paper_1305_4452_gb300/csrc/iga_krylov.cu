@@ -310,37 +310,40 @@ __global__ void k_normalize(const double *w, const double *__restrict__ hn, doub
 }
 
 // Givens step for column j of H (one thread)
-__device__ void givens_step(double *__restrict__ gm, int m, int j, double tol) {
+// Givens step for column j of H, on a copy of the column and of the previous
+// rotations in shared memory (Hs[0..j+1], cs_s[0..j), sn_s[0..j)); one thread.
+// H[j+1][j] arrives in Hs[j+1] as a sum of squares.  Writes the rotated column,
+// the new rotation, g and the flags back to gm.
+__device__ void givens_step_sm(double *Hs, const double *cs_s, const double *sn_s, double *__restrict__ gm, int m, int j,
+                               double tol) {
   GmLayout L = gm_layout(m);
   double *fl = gm + L.flags;
-  if (fl[0] != 0.0) return;
   double *Hj = gm + L.H + (size_t)j * (m + 1);
-  // H[j+1][j] arrives as a sum of squares; take the root
-  double hn = sqrt(Hj[j + 1]);
-  Hj[j + 1] = hn;
+  const double hn = sqrt(Hs[j + 1]);
+  Hs[j + 1] = hn;
   for (int i = 0; i < j; i++) {
-    double c = gm[L.cs + i], s = gm[L.sn + i];
-    double a = Hj[i], b = Hj[i + 1];
-    Hj[i] = c * a + s * b;
-    Hj[i + 1] = -s * a + c * b;
+    const double c = cs_s[i], s = sn_s[i];
+    const double a = Hs[i], b = Hs[i + 1];
+    Hs[i] = c * a + s * b;
+    Hs[i + 1] = -s * a + c * b;
   }
-  double a = Hj[j], b = Hj[j + 1];
-  double r = hypot(a, b);
-  double c = (r > 0.0) ? a / r : 1.0, s = (r > 0.0) ? b / r : 0.0;
+  const double a = Hs[j], b = Hs[j + 1];
+  const double r = hypot(a, b);
+  const double c = (r > 0.0) ? a / r : 1.0, s = (r > 0.0) ? b / r : 0.0;
   gm[L.cs + j] = c;
   gm[L.sn + j] = s;
-  Hj[j] = r;
-  Hj[j + 1] = 0.0;
-  double gj = gm[L.g + j];
+  Hs[j] = r;
+  Hs[j + 1] = 0.0;
+  for (int i = 0; i <= j + 1; i++) Hj[i] = Hs[i];
+  const double gj = gm[L.g + j];
   gm[L.g + j] = c * gj;
   gm[L.g + j + 1] = -s * gj;
-  double res = fabs(gm[L.g + j + 1]);
+  const double res = fabs(s * gj);
   fl[1] = j + 1;
   fl[2] = res;
-  bool breakdown = !(hn > 1e-300) || !isfinite(res);
+  const bool breakdown = !(hn > 1e-300) || !isfinite(res);
   if (breakdown) fl[3] = 1.0;
   if (res <= tol || breakdown || j + 1 == m) fl[0] = 1.0;
-  // keep the norm for the normalisation kernel
   fl[4] = hn;
 }
 
@@ -372,9 +375,19 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_finish(const double *__restri
     vnext[a + r] = v;
     z[a + r] = dinv[a + r] * v;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    gm[L.H + (size_t)j * (m + 1) + j + 1] = s2;
-    givens_step(gm, m, j, tol);
+  if (blockIdx.x == 0) {
+    // the column and the previous rotations, loaded in parallel, then one thread rotates
+    extern __shared__ double fin_sm[];
+    double *Hs = fin_sm, *cs_s = Hs + (m + 2), *sn_s = cs_s + m;
+    const double *Hj = gm + L.H + (size_t)j * (m + 1);
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) Hs[i] = Hj[i];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+      cs_s[i] = gm[L.cs + i];
+      sn_s[i] = gm[L.sn + i];
+    }
+    if (threadIdx.x == 0) Hs[j + 1] = s2;
+    __syncthreads();
+    if (threadIdx.x == 0) givens_step_sm(Hs, cs_s, sn_s, gm, m, j, tol);
   }
 }
 
@@ -593,8 +606,8 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
         IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<1><<<gs.nb, GS_THREADS, smem, h->stream>>>(Vb, ld, jp1, nullptr, Hj, w, P1, N, gs.per, done)));
         IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<2><<<gs.nb, GS_THREADS, smem, h->stream>>>(Vb, ld, jp1, P1, Hj, w, P2, N, gs.per, done)));
         IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<3><<<gs.nb, GS_THREADS, smem, h->stream>>>(Vb, ld, jp1, P2, Hj, w, P3, N, gs.per, done)));
-        IGA_LAUNCH(h, KC_VEC, (k_gs_finish<<<gs.nb, GS_THREADS, 0, h->stream>>>(P3, gs.nb, w, Vb + (size_t)(j + 1) * ld, dinv, z, N,
-                                                                               gs.per, gm, m, j, tol_abs)));
+        IGA_LAUNCH(h, KC_VEC, (k_gs_finish<<<gs.nb, GS_THREADS, (size_t)(3 * m + 2) * sizeof(double), h->stream>>>(
+                                  P3, gs.nb, w, Vb + (size_t)(j + 1) * ld, dinv, z, N, gs.per, gm, m, j, tol_abs)));
       }
       cudaMemcpyAsync(fl_host, gm + L.flags, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
       cudaError_t ce = cudaStreamSynchronize(h->stream);
