@@ -153,7 +153,7 @@ def batch512(torch, iga, W, clock):
                  {"results": res, "setup_s": setup, "total_dofs": int(b.total)}, ck)
 
 
-def learned64(torch, iga, W, clock, n_train=20000, n_test=2000, steps=6000):
+def learned64(torch, iga, W, clock, n_train=20000, n_test=2000, steps=16000):
     from paper_1305_4452_gb300 import nn
     nel = 64
     t0 = time.perf_counter()
