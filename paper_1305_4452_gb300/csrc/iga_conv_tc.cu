@@ -34,9 +34,12 @@
 // (globaltimer); on timeout the kernel raises an error flag, every role stops,
 // the MMA thread waits (bounded) for its last commit, and the tensor memory is
 // freed before the kernel returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <mutex>
 
 #include "iga_internal.h"
 #include "iga_conv_tc.h"
@@ -52,6 +55,14 @@ __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvt
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// K-major operand in 128-byte swizzled atoms (8 rows x 128 B, 1024 B apart): the
+// layout a TMA load with CU_TENSOR_MAP_SWIZZLE_128B writes.  K steps of 16 BF16
+// advance the start address by 32 B inside the atom.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+         (2ull << 61);
 }
 
 __device__ __forceinline__ uint64_t gtimer() {
@@ -287,7 +298,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) k_conv_tc(ConvArgs a) {
     if ((tid & 31) == 0) {
       const uint32_t idesc =
           (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NOUT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-      const uint32_t w0 = su32(Ws);
+      const uint64_t adesc0 = sdesc(su32(As), SM::LBO_A, SM::SBO), bdesc0 = sdesc(su32(Ws), SM::LBO_W, SM::SBO);
       int last = -1;  // last iteration whose MMAs were committed
       for (int it = 0; it < total_it; it++) {
         const int s = it % S, tl = it / 9, tap = it - tl * 9, buf = tl & 1;
@@ -302,15 +313,17 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) k_conv_tc(ConvArgs a) {
           break;
         }
         tc_fence_after();
-        const uint32_t a0 = su32(As + s * SM::A_BYTES), d = tmem + (uint32_t)(buf * NOUT);
+        // descriptors by addition to the start-address field (bytes / 16)
+        const uint64_t ad0 = adesc0 + (uint64_t)((s * SM::A_BYTES) >> 4);
+        const uint64_t bd0 = bdesc0 + (uint64_t)((tap * KSTEPS * 2 * SM::LBO_W) >> 4);
+        const uint32_t d = tmem + (uint32_t)(buf * NOUT);
 #pragma unroll
         for (int k = 0; k < KSTEPS; k++) {
-          const uint64_t ad = sdesc(a0 + 2 * k * SM::LBO_A, SM::LBO_A, SM::SBO);
-          const uint64_t bd = sdesc(w0 + 2 * (tap * KSTEPS + k) * SM::LBO_W, SM::LBO_W, SM::SBO);
           const uint32_t acc = (tap > 0 || k > 0) ? 1u : 0u;
           asm volatile(
               "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              "l"(ad0 + (uint64_t)((k * 2 * SM::LBO_A) >> 4)), "l"(bd0 + (uint64_t)((k * 2 * SM::LBO_W) >> 4)), "r"(idesc),
+              "r"(acc)
               : "memory");
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(empty + s))
@@ -490,6 +503,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1) k_conv_wgrad_tc(WgradArgs a) {
       // FP32 accumulator, BF16 A and B, both MN-major, N = NOUT, M = 128
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
                              ((uint32_t)(NOUT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+      const uint64_t adesc0 = sdesc(su32(sm), SM::CK_A, 128), bdesc0 = sdesc(su32(sm + SM::A_BYTES), SM::CK_B, 128);
       int last = -1;
       for (int it = 0; it < nsteps; it++) {
         const int s = it % S;
@@ -499,13 +513,13 @@ __global__ void __launch_bounds__(WG_THREADS, 1) k_conv_wgrad_tc(WgradArgs a) {
           break;
         }
         tc_fence_after();
-        const uint32_t st = su32(sm + s * SM::STAGE);
+        const uint64_t soff = (uint64_t)((s * SM::STAGE) >> 4);
 #pragma unroll
         for (int mt = 0; mt < MT; mt++)
 #pragma unroll
           for (int kk = 0; kk < WG_BK / 16; kk++) {
-            const uint64_t ad = sdesc(st + mt * SM::A_TILE + 2 * kk * SM::CK_A, SM::CK_A, 128);
-            const uint64_t bd = sdesc(st + SM::A_BYTES + 2 * kk * SM::CK_B, SM::CK_B, 128);
+            const uint64_t ad = adesc0 + soff + (uint64_t)((mt * SM::A_TILE + 2 * kk * SM::CK_A) >> 4);
+            const uint64_t bd = bdesc0 + soff + (uint64_t)((2 * kk * SM::CK_B) >> 4);
             const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
@@ -582,6 +596,227 @@ cudaError_t launch_wgrad(const WgradArgs &a, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// 64-channel inputs: the shifted input of a tap is a TMA box.
+// Tiles are 16 x 8 pixel boxes of one image (M = 128 rows, row m = pixel
+// (y0 + m / 16, x0 + m % 16)); a tap's A tile is the box at (x0 + dx, y0 + dy),
+// loaded by cp.async.bulk.tensor from a 4D tensor map {C, W, H, B} with 128-byte
+// swizzle, the parts outside the grid filled with zeros by the copy engine (the
+// "same" padding, negative coordinates included).  One thread issues the loads
+// (arrive.expect_tx on the stage's "full" barrier), one thread the MMAs, and
+// 8 epilogue warps drain the two TMEM accumulators as in k_conv_tc; boxes that
+// overhang the grid compute rows that the epilogue does not store.
+// ---------------------------------------------------------------------------
+constexpr int TMA_THREADS = 32 * (CONV_EPI_WARPS + 2);  // + producer warp + MMA warp
+constexpr int TMA_STAGES = 8;
+constexpr int TMA_BX = 16, TMA_BY = 8;
+
+template <int NOUT>
+struct TmaSmem {
+  static constexpr uint32_t A_BYTES = 128 * 64 * 2;       // one box: 128 pixels x 128 B
+  static constexpr uint32_t W_BYTES = NOUT * 9 * 64 * 2;
+  static constexpr uint32_t LBO_W = 128 * (NOUT / 8);
+  static constexpr uint32_t A0 = 0;                        // stages first (1024-aligned)
+  static constexpr uint32_t W0 = TMA_STAGES * A_BYTES;
+  static constexpr uint32_t BAR = W0 + W_BYTES;
+  static constexpr uint32_t BIAS = BAR + 8 * (2 * TMA_STAGES + 4) + 16;
+  static constexpr uint32_t TOTAL = BIAS + 4 * NOUT + 1024;  // + alignment slack
+  static constexpr uint32_t TMEM_COLS = 2 * NOUT < 32 ? 32 : 2 * NOUT;
+};
+
+template <int NOUT, int EPI>
+__global__ void __launch_bounds__(TMA_THREADS, 1) k_conv_tma(const __grid_constant__ CUtensorMap tmap, ConvArgs a) {
+  using SM = TmaSmem<NOUT>;
+  constexpr int S = TMA_STAGES, KSTEPS = 4;
+  extern __shared__ uint8_t smraw[];
+  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+  uint8_t *As = sm + SM::A0;
+  uint8_t *Ws = sm + SM::W0;
+  uint64_t *full = reinterpret_cast<uint64_t *>(sm + SM::BAR);
+  uint64_t *empty = full + S;
+  uint64_t *accf = empty + S;
+  uint64_t *acce = accf + 2;
+  uint32_t *slot = reinterpret_cast<uint32_t *>(acce + 2);
+  volatile int *abort_s = reinterpret_cast<volatile int *>(slot + 1);
+  float *bias_s = reinterpret_cast<float *>(sm + SM::BIAS);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int PRODUCER = CONV_EPI_WARPS, MMA = CONV_EPI_WARPS + 1;
+  const int TXN = (a.W + TMA_BX - 1) / TMA_BX, TYN = (a.H + TMA_BY - 1) / TMA_BY;
+  const int nimg = a.P / (a.H * a.W);
+  const int ntiles = nimg * TXN * TYN;
+  const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int total_it = my_tiles * 9;
+
+  for (int c = tid; c < NOUT * 9 * 8; c += TMA_THREADS) {
+    const int n = c % NOUT, kc = c / NOUT;
+    cp16(su32(Ws + (n / 8) * 128 + kc * SM::LBO_W + (n % 8) * 16), a.wk + (size_t)n * 9 * 64 + kc * 8, true);
+  }
+  cp_commit();
+  for (int c = tid; c < NOUT; c += TMA_THREADS) bias_s[c] = a.bias ? a.bias[c] : 0.f;
+  if (warp == MMA) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)), "r"(SM::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < S; i++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(full + i)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(empty + i)) : "memory");
+    }
+    for (int i = 0; i < 2; i++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(accf + i)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(acce + i)), "n"(32 * CONV_EPI_WARPS) : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *abort_s = 0;
+  }
+  cp_wait<0>();
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+
+  if (warp == PRODUCER) {
+    if ((tid & 31) == 0) {
+      for (int it = 0; it < total_it; it++) {
+        const int s = it % S;
+        if (it >= S && !mbar_wait(su32(empty + s), ((it / S) - 1) & 1, abort_s)) {
+          atomicExch(a.err, 1);
+          *abort_s = 1;
+          break;
+        }
+        const int tl = it / 9, tap = it - tl * 9;
+        const int t = (int)blockIdx.x + tl * (int)gridDim.x;
+        const int tx = t % TXN, ty = (t / TXN) % TYN, b = t / (TXN * TYN);
+        const int x = tx * TMA_BX + (tap % 3 - 1) * a.dil * a.sign, y = ty * TMA_BY + (tap / 3 - 1) * a.dil * a.sign;
+        asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(su32(full + s)),
+                     "r"(SM::A_BYTES)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
+                su32(As + s * SM::A_BYTES)),
+            "l"(&tmap), "r"(0), "r"(x), "r"(y), "r"(b), "r"(su32(full + s))
+            : "memory");
+      }
+    }
+    __syncwarp();
+  } else if (warp == MMA) {
+    if ((tid & 31) == 0) {
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NOUT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+      const uint64_t adesc0 = sdesc_sw128(su32(As)), bdesc0 = sdesc(su32(Ws), SM::LBO_W, 128);
+      int last = -1;
+      for (int it = 0; it < total_it; it++) {
+        const int s = it % S, tl = it / 9, tap = it - tl * 9, buf = tl & 1;
+        if (tap == 0 && tl >= 2 && !mbar_wait(su32(acce + buf), ((tl / 2) - 1) & 1, abort_s)) {
+          atomicExch(a.err, 1);
+          *abort_s = 1;
+          break;
+        }
+        if (!mbar_wait(su32(full + s), (it / S) & 1, abort_s)) {
+          atomicExch(a.err, 1);
+          *abort_s = 1;
+          break;
+        }
+        tc_fence_after();
+        // descriptors by addition: +32 B along K inside the swizzle atom is +2 in the
+        // start-address field; the weights advance by 2 * LBO_W per K step
+        const uint64_t ad0 = adesc0 + (uint64_t)((s * SM::A_BYTES) >> 4);
+        const uint64_t bd0 = bdesc0 + (uint64_t)((tap * KSTEPS * 2 * SM::LBO_W) >> 4);
+        const uint32_t d = tmem + (uint32_t)(buf * NOUT);
+#pragma unroll
+        for (int k = 0; k < KSTEPS; k++) {
+          const uint32_t acc = (tap > 0 || k > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+              "l"(ad0 + 2 * k), "l"(bd0 + (uint64_t)((k * 2 * SM::LBO_W) >> 4)), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(empty + s))
+                     : "memory");
+        if (tap == 8)
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(accf + buf))
+                       : "memory");
+        last = it;
+      }
+      if (*abort_s && last >= 0) mbar_wait(su32(empty + last % S), (last / S) & 1, nullptr);
+    }
+    __syncwarp();
+  } else {
+    constexpr int CW = NOUT / 2 < 16 ? 16 : NOUT / 2;
+    const int quarter = warp & 3, cb = (warp >> 2) * CW;
+    const int m = quarter * 32 + (tid & 31);
+    for (int tl = 0; tl < my_tiles; tl++) {
+      const int buf = tl & 1;
+      if (!mbar_wait(su32(accf + buf), (tl / 2) & 1, abort_s)) {
+        atomicExch(a.err, 1);
+        *abort_s = 1;
+        break;
+      }
+      tc_fence_after();
+      const int t = (int)blockIdx.x + tl * (int)gridDim.x;
+      const int tx = t % TXN, ty = (t / TXN) % TYN, b = t / (TXN * TYN);
+      const int x = tx * TMA_BX + m % TMA_BX, y = ty * TMA_BY + m / TMA_BX;
+      const int p = (x < a.W && y < a.H) ? (b * a.H + y) * a.W + x : a.P;  // a.P: not stored
+      if (cb < NOUT)
+        conv_epilogue<64, NOUT, EPI, CW>(a, tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * NOUT), p, cb, bias_s);
+      tc_fence_before();
+      mbar_arrive(su32(acce + buf));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == MMA) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(SM::TMEM_COLS) : "memory");
+  }
+}
+
+typedef CUresult (*TensorMapEncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                         const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                         CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+TensorMapEncodeTiled tensor_map_encoder() {
+  static TensorMapEncodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void *p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<TensorMapEncodeTiled>(p);
+  });
+  return fn;
+}
+
+template <int NOUT, int EPI>
+cudaError_t launch_tma(const ConvArgs &a, cudaStream_t stream) {
+  using SM = TmaSmem<NOUT>;
+  TensorMapEncodeTiled enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const int HW = a.H * a.W;
+  if (a.P % HW) return cudaErrorInvalidValue;
+  CUtensorMap tm;
+  const cuuint64_t dims[4] = {64, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)(a.P / HW)};
+  const cuuint64_t strides[3] = {64 * 2, (cuuint64_t)a.W * 64 * 2, (cuuint64_t)HW * 64 * 2};
+  const cuuint32_t box[4] = {64, TMA_BX, TMA_BY, 1}, es[4] = {1, 1, 1, 1};
+  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(a.in), dims, strides, box, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  auto kern = k_conv_tma<NOUT, EPI>;
+  cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::TOTAL);
+  if (ce) return ce;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int ntiles = (a.P / HW) * ((a.W + TMA_BX - 1) / TMA_BX) * ((a.H + TMA_BY - 1) / TMA_BY);
+  const int grid = ntiles < sms ? ntiles : sms;
+  if (grid < 1) return cudaSuccess;
+  kern<<<grid, TMA_THREADS, SM::TOTAL, stream>>>(tm, a);
+  return cudaGetLastError();
+}
+
 template <int CIN, int NOUT, int EPI>
 cudaError_t launch_one(const ConvArgs &a, cudaStream_t stream) {
   using SM = ConvSmem<CIN, NOUT>;
@@ -615,15 +850,16 @@ cudaError_t launch_conv_tc(int cin, int nout, int epi, const ConvArgs &a, cudaSt
   CONV_CASE(16, 32, CONV_EPI_FWD_SILU)
   CONV_CASE(32, 32, CONV_EPI_FWD_SILU)
   CONV_CASE(16, 64, CONV_EPI_FWD_SILU)
-  CONV_CASE(64, 64, CONV_EPI_FWD_SILU)
+  // 64-channel inputs: TMA-fed kernel
+  if (cin == 64 && nout == 64 && epi == CONV_EPI_FWD_SILU) return launch_tma<64, CONV_EPI_FWD_SILU>(a, stream);
+  if (cin == 64 && nout == 16 && epi == CONV_EPI_LAST) return launch_tma<16, CONV_EPI_LAST>(a, stream);
+  if (cin == 64 && nout == 64 && epi == CONV_EPI_BWD_SILU) return launch_tma<64, CONV_EPI_BWD_SILU>(a, stream);
   CONV_CASE(16, 16, CONV_EPI_LAST)
   CONV_CASE(32, 16, CONV_EPI_LAST)
-  CONV_CASE(64, 16, CONV_EPI_LAST)
   CONV_CASE(16, 16, CONV_EPI_BWD_SILU)
   CONV_CASE(16, 32, CONV_EPI_BWD_SILU)
   CONV_CASE(32, 32, CONV_EPI_BWD_SILU)
   CONV_CASE(16, 64, CONV_EPI_BWD_SILU)
-  CONV_CASE(64, 64, CONV_EPI_BWD_SILU)
 #undef CONV_CASE
   return cudaErrorInvalidValue;
 }
