@@ -260,6 +260,20 @@ def run_ours(args):
 
     t_res = timeit(lambda: disc.form_residual(Ur, F), 10)
     t_jac = timeit(lambda: disc.form_jacobian(Ur, vals=J), 3)
+    # matrix-free Newton-Krylov on the same problem (exact products, no assembled Jacobian):
+    # one product, and one whole solve, outside the timed region
+    xr = torch.ones_like(U0)
+    t_jv = timeit(lambda: disc.apply_jacobian_mf(Ur, xr, F), 5)
+    o_mf = iga.newton_defaults()
+    o_mf.jac = iga.IGA_JAC_NONE
+    Umf = torch.zeros_like(U0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r_mf = disc.solve_newton(Umf, o_mf)
+    torch.cuda.synchronize()
+    mf = {"solve_ms": 1e3 * (time.perf_counter() - t0), "newton_its": r_mf.newton_its, "krylov_its": r_mf.krylov_its,
+          "fnorm": r_mf.fnorm, "jv_ms": t_jv, "spmv_ms_for_comparison": prof["spmv"][0] / max(prof["spmv"][1], 1),
+          "csr_bytes_avoided": disc.nnz * 8}
 
     # roofline of the dominant kernel class in the timed region
     hbm, hbm_src = peaks()
@@ -278,6 +292,7 @@ def run_ours(args):
             "kernel_share": {c: round(v[0] / max(ms, 1e-9), 4) for c, v in prof.items() if v[1] > 0},
             "assembly_fp64": {"jacobian_ms": t_jac, "jacobian_nnz_per_s": disc.nnz / (t_jac / 1e3),
                               "residual_ms": t_res, "residual_dofs_per_s": N / (t_res / 1e3)},
+            "matrix_free_newton": mf,
             "setup_ms": setup_ms}
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
         import oracle as O

@@ -57,7 +57,12 @@ typedef enum {
   IGA_FP64 = 0,     /* FP64 element arithmetic, FP64 values (double *) */
   IGA_JAC_TF32 = 1, /* element contraction with TF32 operands, FP32 accumulate; float * values */
   IGA_JAC_BF16 = 2, /* element contraction with BF16 operands, FP32 accumulate; float * values */
-  IGA_JAC_FP32 = 3  /* global sum factorisation in FP32 on the CUDA cores; float * values */
+  IGA_JAC_FP32 = 3, /* global sum factorisation in FP32 on the CUDA cores; float * values */
+  IGA_JAC_NONE = 4  /* Newton only: matrix-free Newton-Krylov, no assembled Jacobian; the Krylov
+                       solver applies J(U) exactly on the fly (sum-factorised element passes,
+                       iga_apply_jacobian_mf) with Jacobi preconditioning from
+                       iga_form_jacobian_diagonal (the -snes_mf run of Sec. 2.10, with exact
+                       products instead of finite differences) */
 } iga_precision;
 
 /* Discretisation (the IGASetDim / IGASetFromOptions data of Sec. 3.2).
@@ -154,6 +159,18 @@ iga_status iga_form_jacobian(iga_t iga, const double *U, void *vals, iga_precisi
  * structure of the pattern.  Stream-ordered, deterministic. */
 iga_status iga_apply_jacobian(iga_t iga, const void *vals, iga_precision prec, const double *x, double *y);
 
+/* y = J(U) x without assembling J: the linearisation of Eq. (residual) at U applied
+ * to x by the same sum-factorised element passes as the residual (columns of
+ * Dirichlet variables zero, identity Dirichlet rows), gathered per row in a fixed
+ * order.  Equal to iga_form_jacobian(U) followed by iga_apply_jacobian up to
+ * rounding.  U, x, y: device double[n], caller-owned, x != y.  Stream-ordered. */
+iga_status iga_apply_jacobian_mf(iga_t iga, const double *U, const double *x, double *y);
+
+/* d = diag(J(U)) (1 on Dirichlet rows) without assembling J: per element and local
+ * function, the quadratic form of Eq. (jacobian) over the Gauss points, gathered
+ * per row.  d: device double[n], caller-owned.  Stream-ordered. */
+iga_status iga_form_jacobian_diagonal(iga_t iga, const double *U, double *d);
+
 /* Newton-Krylov options (SNESSolve of Sec. 3.2; -snes_atol, -ksp_* analogues). */
 typedef struct {
   double atol;         /* stop when ||F||_2 <= atol (default 1e-10) */
@@ -161,7 +178,8 @@ typedef struct {
   int gmres_restart;   /* GMRES(m) restart length (default 60) */
   int max_krylov;      /* Krylov iteration cap per Newton step (default 4000) */
   double krylov_rtol;  /* forcing term cap; the solve uses min(krylov_rtol, ||F_k||) (default 1e-2) */
-  iga_precision jac;   /* Jacobian precision used to steer Newton (default IGA_FP64) */
+  iga_precision jac;   /* Jacobian precision used to steer Newton (default IGA_FP64);
+                          IGA_JAC_NONE: matrix-free (no assembled Jacobian) */
   int reuse_stiffness; /* 1: assemble the U-independent part K of J once per solve and add
                           the reaction term each step (default 1); with an FP64 Jacobian the
                           residuals after the first are then K U plus the reaction term

@@ -270,6 +270,30 @@ extern "C" iga_status iga_apply_jacobian(iga_t h, const void *vals, iga_precisio
   return IGA_OK;
 }
 
+extern "C" iga_status iga_apply_jacobian_mf(iga_t h, const double *U, const double *x, double *y) {
+  if (!h) return IGA_EINVAL;
+  if (!U || !x || !y || x == y) {
+    h->err = "U, x and y must be non-NULL device pointers, x != y";
+    return IGA_EINVAL;
+  }
+  CK(launch_q00(h, U, 0.0, 1.0));
+  h->q00_valid = false;
+  CK(launch_jv(h, x, y, nullptr));
+  return IGA_OK;
+}
+
+extern "C" iga_status iga_form_jacobian_diagonal(iga_t h, const double *U, double *d) {
+  if (!h) return IGA_EINVAL;
+  if (!U || !d) {
+    h->err = "U and d must be non-NULL device pointers";
+    return IGA_EINVAL;
+  }
+  CK(launch_q00(h, U, 0.0, 1.0));
+  h->q00_valid = false;
+  CK(launch_jacobian_diagonal(h, d));
+  return IGA_OK;
+}
+
 extern "C" void iga_newton_defaults(iga_newton_opts *o) {
   if (!o) return;
   o->atol = 1e-10;
@@ -292,7 +316,7 @@ __global__ static void k_neg(const double *__restrict__ x, double *__restrict__ 
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) y[i] = -x[i];
 }
 
-static iga_status ensure_workspace(iga_s *h, int m, bool f32) {
+static iga_status ensure_workspace(iga_s *h, int m, bool f32, bool mf = false) {
   const int64_t N = h->N;
   if (!h->wk) CK(cudaMalloc((void **)&h->wk, (size_t)(8 * N + 64 + 2 * 1025) * sizeof(double)));
   if (!h->ctl_host) CK(cudaMallocHost((void **)&h->ctl_host, 16 * sizeof(double)));
@@ -308,7 +332,7 @@ static iga_status ensure_workspace(iga_s *h, int m, bool f32) {
     CK(cudaMalloc((void **)&h->ctl, (size_t)((m + 1) * m + 4 * m + 16) * sizeof(double)));
     h->V_m = m;
   }
-  if (!f32 && !h->J64) CK(cudaMalloc((void **)&h->J64, h->nnz * sizeof(double)));
+  if (!f32 && !mf && !h->J64) CK(cudaMalloc((void **)&h->J64, h->nnz * sizeof(double)));
   if (f32 && !h->J32) CK(cudaMalloc((void **)&h->J32, h->nnz * sizeof(float)));
   if (f32 && !h->z32) CK(cudaMalloc((void **)&h->z32, N * sizeof(float)));
   return IGA_OK;
@@ -357,16 +381,18 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
     return IGA_EINVAL;
   }
   if (!U || o.gmres_restart < 1 || o.gmres_restart > 1000 || o.max_newton < 0 || !(o.atol >= 0.0) ||
-      (o.jac != IGA_FP64 && o.jac != IGA_JAC_TF32 && o.jac != IGA_JAC_BF16 && o.jac != IGA_JAC_FP32)) {
+      (o.jac != IGA_FP64 && o.jac != IGA_JAC_TF32 && o.jac != IGA_JAC_BF16 && o.jac != IGA_JAC_FP32 &&
+       o.jac != IGA_JAC_NONE)) {
     h->err = "bad Newton options or NULL U";
     return IGA_EINVAL;
   }
   iga_newton_report R;
   memset(&R, 0, sizeof R);
   R.status = IGA_ENOCONV;
-  const bool f32 = o.jac != IGA_FP64;
-  const bool split = !f32 && o.reuse_stiffness != 0;
-  iga_status st = ensure_workspace(h, o.gmres_restart, f32);
+  const bool mf = o.jac == IGA_JAC_NONE;  // matrix-free
+  const bool f32 = !mf && o.jac != IGA_FP64;
+  const bool split = !f32 && !mf && o.reuse_stiffness != 0;
+  iga_status st = ensure_workspace(h, o.gmres_restart, f32, mf);
   if (st != IGA_OK) return st;
   const int64_t N = h->N;
   double *F = h->wk, *dU = h->wk + N, *Ut = h->wk + 2 * N, *Ft = h->wk + 3 * N;
@@ -387,8 +413,13 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
     if (!isfinite(fn)) { R.status = IGA_ENAN; break; }
     if (fn <= o.atol) { R.status = IGA_OK; break; }
     if (k >= o.max_newton) { R.status = IGA_ENOCONV; break; }
-    st = newton_jacobian(h, U, f32, o.reuse_stiffness != 0, (int)o.jac);
-    if (st != IGA_OK) return st;
+    if (mf) {
+      CK(launch_q00(h, U, 0.0, 1.0));  // the reaction coefficient the matrix-free products use
+      h->q00_valid = false;
+    } else {
+      st = newton_jacobian(h, U, f32, o.reuse_stiffness != 0, (int)o.jac);
+      if (st != IGA_OK) return st;
+    }
     IGA_LAUNCH(h, KC_VEC, (k_neg<<<eg, 256, 0, h->stream>>>(F, Ft, N)));
     // forcing term min(rtol, ||F||) (quadratic Newton), but never below half the
     // Newton tolerance: a linear residual under atol/2 already lets the step meet atol
@@ -401,9 +432,10 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
     if (tol_abs < 1e-14 * fn) tol_abs = 1e-14 * fn;
     int its = 0;
     cudaError_t ce = cudaSuccess;
-    const void *Jv = f32 ? (const void *)h->J32 : (const void *)h->J64;
-    int grc = (o.ksp == IGA_KSP_CG) ? cg_solve(h, Jv, f32, Ft, dU, tol_abs, o.max_krylov, &its, &ce)
-                                    : gmres_solve(h, Jv, f32, Ft, dU, tol_abs, o.gmres_restart, o.max_krylov, &its, &ce);
+    const void *Jv = mf ? nullptr : (f32 ? (const void *)h->J32 : (const void *)h->J64);
+    const int kind = mf ? 2 : (f32 ? 1 : 0);
+    int grc = (o.ksp == IGA_KSP_CG) ? cg_solve(h, Jv, kind, Ft, dU, tol_abs, o.max_krylov, &its, &ce)
+                                    : gmres_solve(h, Jv, kind, Ft, dU, tol_abs, o.gmres_restart, o.max_krylov, &its, &ce);
     if (grc < 0) {
       h->err = iga_format("GMRES: %s", cudaGetErrorString(ce));
       return IGA_ECUDA;

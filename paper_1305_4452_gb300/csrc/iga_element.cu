@@ -139,13 +139,21 @@ struct ResSmem {
   static constexpr int PER = TAB + NEN + 2 * BUF;
 };
 
-template <int DIM, int P, int NE>
+// LIN: the Jacobian applied to a direction instead (matrix-free Newton-Krylov):
+// U holds the direction x, its Dirichlet entries read as zero (the columns the
+// Dirichlet fix removes), and the reaction term becomes q00[e][qp] * ũ_x, q00 the
+// reaction part of Q00 at the Newton iterate (-jw/W^2 lambda e^u): the derivative
+// of -jw/W lambda e^u in direction x, with u = ũ / W.
+template <int DIM, int P, int NE, bool LIN = false>
 __global__ void __launch_bounds__(128) k_residual(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ U,
                                                   const double *__restrict__ wts, const double *__restrict__ geom,
-                                                  GeomLayout gl, double lambda, double *__restrict__ Fe, int64_t nelem) {
+                                                  GeomLayout gl, double lambda, double *__restrict__ Fe, int64_t nelem,
+                                                  const double *__restrict__ q00 = nullptr, BndArgs bnd = BndArgs{},
+                                                  const double *__restrict__ done = nullptr) {
   using SM = ResSmem<DIM, P>;
   constexpr int N1 = SM::N1, Q = SM::Q, NEN = SM::NEN, NQ = SM::NQ;
   extern __shared__ double smem[];
+  if (LIN && done && done[0] != 0.0) return;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int64_t ebase = (int64_t)blockIdx.x * NE;
   // ---- load tables and gather w_A U_A (Algorithm 3: U_e <- U) ----
@@ -163,8 +171,15 @@ __global__ void __launch_bounds__(128) k_residual(DirArgs d0, DirArgs d1, DirArg
     } else {
       int a = k - SM::TAB;
       int a0 = a % N1, a1 = (a / N1) % N1, a2 = (DIM == 3) ? a / (N1 * N1) : 0;
-      int64_t G = (d0.first[e0] + a0) + (int64_t)d0.n * ((d1.first[e1] + a1) + (int64_t)d1.n * ((DIM == 3 ? d2.first[e2] : 0) + a2));
-      base[k] = U[G] * (wts ? wts[G] : 1.0);
+      const int j0 = d0.first[e0] + a0, j1 = d1.first[e1] + a1, j2 = (DIM == 3 ? d2.first[e2] : 0) + a2;
+      int64_t G = j0 + (int64_t)d0.n * (j1 + (int64_t)d1.n * j2);
+      double x = U[G];
+      if (LIN) {
+        const int jj[3] = {j0, j1, j2}, nn[3] = {d0.n, d1.n, d2.n};
+        for (int ax = 0; ax < DIM; ax++)
+          if ((bnd.flag[ax][0] && jj[ax] == 0) || (bnd.flag[ax][1] && jj[ax] == nn[ax] - 1)) x = 0.0;
+      }
+      base[k] = x * (wts ? wts[G] : 1.0);
     }
   }
   __syncthreads();
@@ -268,8 +283,13 @@ __global__ void __launch_bounds__(128) k_residual(DirArgs d0, DirArgs d1, DirArg
       v[1] = s01 * r[0] + s11 * r[1] + s12 * r[2];
       v[2] = s02 * r[0] + s12 * r[1] + s22 * r[2];
     }
-    double u = ut * rec[gl.invW * NQ];
-    double s = -rec[gl.jwW * NQ] * lambda * exp(u);
+    double s;
+    if (LIN) {
+      s = q00[(size_t)e * NQ + qp] * ut;
+    } else {
+      double u = ut * rec[gl.invW * NQ];
+      s = -rec[gl.jwW * NQ] * lambda * exp(u);
+    }
     for (int a = 0; a < DIM; a++) s -= rec[(gl.g + a) * NQ] * v[a];
     X[qp] = s;
     for (int a = 0; a < DIM; a++) X[(1 + a) * NQ + qp] = v[a];
@@ -389,7 +409,8 @@ __global__ void __launch_bounds__(128) k_residual(DirArgs d0, DirArgs d1, DirArg
 template <int DIM>
 __global__ void k_gather_residual(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ Fe,
                                   const double *__restrict__ U, BndArgs bnd, double *__restrict__ F, int64_t N, int N1,
-                                  const double *__restrict__ add) {
+                                  const double *__restrict__ add, int lin = 0, const double *__restrict__ done = nullptr) {
+  if (done && done[0] != 0.0) return;
   int64_t A = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (A >= N) return;
   int i0 = (int)(A % d0.n), i1 = (int)((A / d0.n) % d1.n), i2 = (DIM == 3) ? (int)(A / ((int64_t)d0.n * d1.n)) : 0;
@@ -416,7 +437,8 @@ __global__ void k_gather_residual(DirArgs d0, DirArgs d1, DirArgs d2, const doub
     if (bnd.flag[ax][0] && idx[ax] == 0) { on = true; g = bnd.val[ax][0]; }
     if (bnd.flag[ax][1] && idx[ax] == nn[ax] - 1) { on = true; g = bnd.val[ax][1]; }
   }
-  F[A] = on ? U[A] - g : acc;
+  // lin 1: Jacobian times a direction (identity rows); 2: Jacobian diagonal (1)
+  F[A] = on ? (lin == 2 ? 1.0 : (lin ? U[A] : U[A] - g)) : acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -727,6 +749,108 @@ cudaError_t launch_residual_split(iga_s *h, const double *U, double *F, const do
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Diagonal of the Jacobian (the Jacobi preconditioner of the matrix-free solve):
+//   J_AA = w_A^2 sum_q [Q00 M^2 + 2 sum_a Q0a M dM_a + sum_ab S_ab dM_a dM_b](x_q),
+// Q00 = g^T S g + q00 (q00: the reaction part at the Newton iterate), Q0a = (-S g)_a.
+// One CTA per element; its geometry record and 1D tables in shared memory, one
+// thread per local function A.  Element contributions go to Fe and are gathered
+// per row in a fixed order (Dirichlet rows: 1).
+// ---------------------------------------------------------------------------
+template <int DIM, int P>
+__global__ void __launch_bounds__(128) k_diag_elem(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ wts,
+                                                   const double *__restrict__ geom, GeomLayout gl,
+                                                   const double *__restrict__ q00, double *__restrict__ Fe, int64_t nelem) {
+  constexpr int N1 = P + 1, Q = P + 1;
+  constexpr int NEN = DIM == 3 ? N1 * N1 * N1 : N1 * N1, NQ = DIM == 3 ? Q * Q * Q : Q * Q;
+  constexpr int NS = DIM * (DIM + 1) / 2;
+  __shared__ double tab[3][Q][N1][2];
+  __shared__ double qf[1 + DIM + NS][NQ];  // Q00, Q0a, S_ab (00,11,22,01,02,12 / 00,11,01)
+  const int64_t e = blockIdx.x;
+  if (e >= nelem) return;
+  const int e0 = (int)(e % d0.nel), e1 = (int)((e / d0.nel) % d1.nel), e2 = DIM == 3 ? (int)(e / ((int64_t)d0.nel * d1.nel)) : 0;
+  for (int k = threadIdx.x; k < DIM * Q * N1 * 2; k += blockDim.x) {
+    const int ax = k / (Q * N1 * 2), r = k % (Q * N1 * 2);
+    const DirArgs &d = ax == 0 ? d0 : (ax == 1 ? d1 : d2);
+    const int ee = ax == 0 ? e0 : (ax == 1 ? e1 : e2);
+    (&tab[ax][0][0][0])[r] = d.tab[(size_t)ee * Q * N1 * 2 + r];
+  }
+  const double *rec = geom + (size_t)e * gl.nf * NQ;
+  for (int k = threadIdx.x; k < NQ; k += blockDim.x) {
+    qf[0][k] = rec[gl.gSg * NQ + k] + q00[(size_t)e * NQ + k];
+    for (int a = 0; a < DIM; a++) qf[1 + a][k] = rec[(gl.Sg + a) * NQ + k];
+    for (int b = 0; b < NS; b++) qf[1 + DIM + b][k] = rec[(gl.S + b) * NQ + k];
+  }
+  __syncthreads();
+  for (int A = threadIdx.x; A < NEN; A += blockDim.x) {
+    const int a0 = A % N1, a1 = (A / N1) % N1, a2 = DIM == 3 ? A / (N1 * N1) : 0;
+    double acc = 0.0;
+    for (int qp = 0; qp < NQ; qp++) {
+      const int g0 = qp % Q, g1 = (qp / Q) % Q, g2 = DIM == 3 ? qp / (Q * Q) : 0;
+      const double b0 = tab[0][g0][a0][0], db0 = tab[0][g0][a0][1];
+      const double b1 = tab[1][g1][a1][0], db1 = tab[1][g1][a1][1];
+      double m, d[3];
+      if (DIM == 3) {
+        const double b2 = tab[2][g2][a2][0], db2 = tab[2][g2][a2][1];
+        m = b0 * b1 * b2;
+        d[0] = db0 * b1 * b2;
+        d[1] = b0 * db1 * b2;
+        d[2] = b0 * b1 * db2;
+        const double t = qf[0][qp] * m * m + 2.0 * m * (qf[1][qp] * d[0] + qf[2][qp] * d[1] + qf[3][qp] * d[2]) +
+                         qf[4][qp] * d[0] * d[0] + qf[5][qp] * d[1] * d[1] + qf[6][qp] * d[2] * d[2] +
+                         2.0 * (qf[7][qp] * d[0] * d[1] + qf[8][qp] * d[0] * d[2] + qf[9][qp] * d[1] * d[2]);
+        acc += t;
+      } else {
+        m = b0 * b1;
+        d[0] = db0 * b1;
+        d[1] = b0 * db1;
+        const double t = qf[0][qp] * m * m + 2.0 * m * (qf[1][qp] * d[0] + qf[2][qp] * d[1]) + qf[3][qp] * d[0] * d[0] +
+                         qf[4][qp] * d[1] * d[1] + 2.0 * qf[5][qp] * d[0] * d[1];
+        acc += t;
+      }
+    }
+    if (wts) {
+      const int64_t G = (d0.first[e0] + a0) + (int64_t)d0.n * ((d1.first[e1] + a1) + (int64_t)d1.n * ((DIM == 3 ? d2.first[e2] : 0) + a2));
+      acc *= wts[G] * wts[G];
+    }
+    Fe[(size_t)e * NEN + A] = acc;
+  }
+}
+
+// y = J(U) x without an assembled matrix; h->Q00 must hold the reaction part of Q00 at U
+// (launch_q00(h, U, 0, 1)).  done: device flag that skips the work once set (may be null).
+cudaError_t launch_jv(iga_s *h, const double *x, double *y, const double *done) {
+  DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
+  constexpr int NE = 4;
+  unsigned grid = (unsigned)((h->nelem + NE - 1) / NE);
+  IGA_LAUNCH(h, KC_RES_ELEM, DISPATCH_DP(h->dim, h->p, ({
+    size_t sm = res_smem<D, PP>(NE);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_residual<D, PP, NE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_residual<D, PP, NE, true><<<grid, 128, sm, h->stream>>>(a0, a1, a2, x, h->weights, h->geom, h->gl, h->lambda, h->Fe,
+                                                             h->nelem, h->Q00, h->bnd, done);
+  })));
+  unsigned g2 = (unsigned)((h->N + 255) / 256);
+  if (h->dim == 3)
+    IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<3><<<g2, 256, 0, h->stream>>>(a0, a1, a2, h->Fe, x, h->bnd, y, h->N, h->p + 1, nullptr, 1, done)));
+  else
+    IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<2><<<g2, 256, 0, h->stream>>>(a0, a1, a2, h->Fe, x, h->bnd, y, h->N, h->p + 1, nullptr, 1, done)));
+  return cudaGetLastError();
+}
+
+// diag(J(U)) (Dirichlet rows 1); h->Q00 as for launch_jv
+cudaError_t launch_jacobian_diagonal(iga_s *h, double *diag) {
+  DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
+  IGA_LAUNCH(h, KC_RES_ELEM, DISPATCH_DP(h->dim, h->p, ({
+    k_diag_elem<D, PP><<<(unsigned)h->nelem, 128, 0, h->stream>>>(a0, a1, a2, h->weights, h->geom, h->gl, h->Q00, h->Fe, h->nelem);
+  })));
+  unsigned g2 = (unsigned)((h->N + 255) / 256);
+  if (h->dim == 3)
+    IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<3><<<g2, 256, 0, h->stream>>>(a0, a1, a2, h->Fe, nullptr, h->bnd, diag, h->N, h->p + 1, nullptr, 2, nullptr)));
+  else
+    IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<2><<<g2, 256, 0, h->stream>>>(a0, a1, a2, h->Fe, nullptr, h->bnd, diag, h->N, h->p + 1, nullptr, 2, nullptr)));
+  return cudaGetLastError();
+}
 
 cudaError_t launch_colidx(iga_s *h) {
   DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);

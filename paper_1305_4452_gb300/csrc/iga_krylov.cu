@@ -554,6 +554,28 @@ cudaError_t launch_nan_check(iga_s *h, const double *x, double *out_dev) {
 // Restarted GMRES(m), right Jacobi preconditioning: solves A x = b from x = 0
 // until ||b - A x|| <= tol_abs or maxit iterations.  Returns 0 on convergence,
 // 1 when the cap was hit, 2 on breakdown/NaN, -1 on a CUDA error.
+// Operator of the Krylov solvers: FP64 values (kind 0), FP32 values (1) or the
+// matrix-free product J(U) x (2; vals unused, h->Q00 holds the reaction part at U)
+static void apply_op(iga_s *h, const void *vals, int kind, const double *x, double *y, const double *done) {
+  if (kind == 2) launch_jv(h, x, y, done);
+  else if (kind == 1) spmv_f32_launch(h, (const float *)vals, x, y, done);
+  else spmv_launch<double>(h, (const double *)vals, x, y, done);
+}
+
+__global__ void k_invert_diag(double *__restrict__ d, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = (d[i] != 0.0) ? 1.0 / d[i] : 1.0;
+}
+
+static void jacobi_scaling(iga_s *h, const void *vals, int kind, double *dinv) {
+  if (kind == 2) {
+    launch_jacobian_diagonal(h, dinv);
+    IGA_LAUNCH(h, KC_VEC, (k_invert_diag<<<grid_for(h->N, 256, 4 * 152), 256, 0, h->stream>>>(dinv, h->N)));
+  } else {
+    launch_diag_inv(h, vals, kind, dinv);
+  }
+}
+
 int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double *x, double tol_abs, int m, int maxit,
                 int *its, cudaError_t *cerr) {
   const int64_t N = h->N, ld = N;
@@ -575,7 +597,7 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
       cudaFuncSetAttribute(k_gs_pass<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
     }
   }
-  launch_diag_inv(h, vals, is_f32, dinv);
+  jacobi_scaling(h, vals, is_f32, dinv);
   IGA_LAUNCH(h, KC_VEC, (k_fill<<<eg, 256, 0, h->stream>>>(x, 0.0, N)));
   const int batch = 8;
   while (total < maxit) {
@@ -583,8 +605,7 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
     if (total == 0) {
       cudaMemcpyAsync(Vb, b, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
     } else {
-      if (is_f32) spmv_f32_launch(h, (const float *)vals, x, tmp, nullptr);
-      else spmv_launch<double>(h, (const double *)vals, x, tmp, nullptr);
+      apply_op(h, vals, is_f32, x, tmp, nullptr);
       IGA_LAUNCH(h, KC_VEC, (k_residual_vec<<<eg, 256, 0, h->stream>>>(b, tmp, Vb, N)));
     }
     sumsq(h, Vb, scal);
@@ -597,8 +618,7 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
       for (; j < jend; j++) {
         const double *done = gm + L.flags;
         double *Hj = gm + L.H + (size_t)j * (m + 1);
-        if (is_f32) spmv_f32_launch(h, (const float *)vals, z, w, done);
-        else spmv_launch<double>(h, (const double *)vals, z, w, done);
+        apply_op(h, vals, is_f32, z, w, done);
         // classical Gram-Schmidt, applied twice (three passes), then norm + Givens + next vector
         const int jp1 = j + 1;
         const size_t smem = (size_t)(gs.per + jp1 + GS_THREADS / 32) * sizeof(double);
@@ -745,7 +765,7 @@ int cg_solve(iga_s *h, const void *vals, int is_f32, const double *b, double *x,
   double *dinv = h->wk + 4 * N, *r = h->wk + 5 * N, *p = h->wk + 6 * N, *q = h->wk + 7 * N;
   int eg = grid_for(N, 256, 4 * 152);
   *cerr = cudaSuccess;
-  launch_diag_inv(h, vals, is_f32, dinv);
+  jacobi_scaling(h, vals, is_f32, dinv);
   IGA_LAUNCH(h, KC_VEC, (k_cg_init<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(b, dinv, x, r, p, h->red, N)));
   IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce2<<<1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, s + CG_RZ, s + CG_RR, nullptr)));
   IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_cg_check0<<<1, 1, 0, h->stream>>>(s, tol_abs)));
@@ -754,8 +774,7 @@ int cg_solve(iga_s *h, const void *vals, int is_f32, const double *b, double *x,
   int enq = 0;
   while (enq < maxit) {
     for (int k = 0; k < batch && enq < maxit; k++, enq++) {
-      if (is_f32) spmv_f32_launch(h, (const float *)vals, p, q, done);
-      else spmv_launch<double>(h, (const double *)vals, p, q, done);
+      apply_op(h, vals, is_f32, p, q, done);
       IGA_LAUNCH(h, KC_VEC, (k_dot_partial<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(p, q, h->red, N, done)));
       IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce_rows<<<1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, s + CG_PQ, 0, done)));
       IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_cg_alpha<<<1, 1, 0, h->stream>>>(s)));

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_PKG, "lib", "libiga.so")
 
 IGA_OK, IGA_EINVAL, IGA_ENOMEM, IGA_ECUDA, IGA_ENOCONV, IGA_EDIVERGED, IGA_ETIMEOUT, IGA_ENAN = range(8)
 STATUS_NAMES = ["IGA_OK", "IGA_EINVAL", "IGA_ENOMEM", "IGA_ECUDA", "IGA_ENOCONV", "IGA_EDIVERGED", "IGA_ETIMEOUT", "IGA_ENAN"]
-IGA_FP64, IGA_JAC_TF32, IGA_JAC_BF16, IGA_JAC_FP32 = 0, 1, 2, 3
+IGA_FP64, IGA_JAC_TF32, IGA_JAC_BF16, IGA_JAC_FP32, IGA_JAC_NONE = 0, 1, 2, 3, 4
 
 # every symbol include/iga.h declares
 EXPORTS = ["iga_create", "iga_set_boundary_value", "iga_set_lambda", "iga_get_pattern", "iga_form_residual",
@@ -24,7 +24,7 @@ EXPORTS = ["iga_create", "iga_set_boundary_value", "iga_set_lambda", "iga_get_pa
            "iga_batch_create", "iga_batch_offsets", "iga_batch_set_launch", "iga_batch_solve", "iga_batch_destroy",
            "iga_batch_last_error", "iga_nn_create", "iga_nn_num_params", "iga_nn_get_params", "iga_nn_set_params",
            "iga_nn_forward", "iga_nn_loss_grad", "iga_nn_adam_step", "iga_nn_destroy", "iga_nn_last_error",
-           "iga_nn_set_h1_weight", "iga_apply_jacobian"]
+           "iga_nn_set_h1_weight", "iga_apply_jacobian", "iga_apply_jacobian_mf", "iga_form_jacobian_diagonal"]
 
 KERNEL_CLASSES = ["geometry", "residual_element", "residual_gather", "q00", "jac_stage1", "jac_stage2", "jac_final",
                   "spmv", "gs_orth", "gmres_scalar", "vector", "combine", "pattern", "elem_tc", "elem_gather"]
@@ -98,6 +98,8 @@ def lib():
         L.iga_form_residual.argtypes = [vp, vp, vp]
         L.iga_form_jacobian.argtypes = [vp, vp, vp, ctypes.c_int]
         L.iga_apply_jacobian.argtypes = [vp, vp, ctypes.c_int, vp, vp]
+        L.iga_apply_jacobian_mf.argtypes = [vp, vp, vp, vp]
+        L.iga_form_jacobian_diagonal.argtypes = [vp, vp, vp]
         L.iga_form_residual_noalloc.argtypes = [vp, vp, vp]
         L.iga_newton_defaults.argtypes = [ctypes.POINTER(IgaNewtonOpts)]
         L.iga_newton_defaults.restype = None
@@ -244,6 +246,23 @@ class Discretization:
         _check(lib().iga_apply_jacobian(self.h, ctypes.c_void_p(vals.data_ptr()), int(prec), ctypes.c_void_p(x.data_ptr()),
                                         ctypes.c_void_p(y.data_ptr())), self.h)
         return y
+
+    def apply_jacobian_mf(self, U, x, y=None):
+        """y = J(U) x without assembling J (matrix-free)."""
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        _check(lib().iga_apply_jacobian_mf(self.h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                           ctypes.c_void_p(y.data_ptr())), self.h)
+        return y
+
+    def jacobian_diagonal(self, U, d=None):
+        """diag(J(U)) without assembling J (1 on Dirichlet rows)."""
+        import torch
+        if d is None:
+            d = torch.empty_like(U)
+        _check(lib().iga_form_jacobian_diagonal(self.h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(d.data_ptr())), self.h)
+        return d
 
     def solve_newton(self, U, opts=None, check=True):
         o = opts if opts is not None else newton_defaults()
