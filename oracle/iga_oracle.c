@@ -23,6 +23,9 @@
  *   - Element-by-element Gauss-Legendre assembly of the residual, Sec. 2.7
  *     Algorithm 3, with the Bratu integrand of Sec. 3.1 Eq. (residual); the
  *     Jacobian of Eq. (jacobian), assembled "in a similar fashion" (Sec. 2.7).
+ *   - The Jacobian by local numerical differentiation, Sec. 2.10 Eq. (fdjac):
+ *     forward differences of the quadrature-point integrand in each element value,
+ *     step sqrt(eps) sqrt(1 + ||U_e||_2) (or_jacobian_fd).
  *   - The CSR adjacency pattern from BasisStencil, Sec. 2.5 Algorithm 2, in
  *     lexicographic tensor-product order.
  *   - Dirichlet rows set with IGASetBoundaryValue (Sec. 3.2): F_A = U_A - g and an
@@ -33,6 +36,7 @@
  *
  * Every function returns 0 on success and a negative code on malformed input.
  */
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -395,9 +399,37 @@ static void mesh_free(or_mesh *M) {
 
 /* Element integrals of one element: Fe[a] and (optionally) Ke[a*nen+b].
  * Sec. 2.7 Algorithm 3 steps: gather U_e, loop over quadrature points, ShapeFuns,
- * Integrand of Eq. (residual) / Eq. (jacobian), accumulate J_q w_q F_q. */
+ * Integrand of Eq. (residual) / Eq. (jacobian), accumulate J_q w_q F_q.
+ * fd != 0: Ke by the local numerical differentiation of Sec. 2.10, Eq. (fdjac):
+ * at every quadrature point, column b of dF_q/dU_e is (F_q(U_e + delta e_b) - F_q(U_e))
+ * / delta with delta = sqrt(eps) * sqrt(1 + ||U_e||_2), F_q recomputed from the
+ * perturbed element values. */
+static int element_integrals_mode(const or_mesh *Msh, const int *e, const double *Uc, int64_t *gidx,
+                                  double *Fe, double *Ke, int fd);
 static int element_integrals(const or_mesh *Msh, const int *e, const double *Uc, int64_t *gidx,
                              double *Fe, double *Ke) {
+  return element_integrals_mode(Msh, e, Uc, gidx, Fe, Ke, 0);
+}
+
+/* F_q[a] (a < nen) at one quadrature point from element values Ue (the integrand of
+ * Eq. (residual) times J_q w_q, without the U-independent source term) */
+static void point_integrand(int dim, int nen, const double *N, const double *dN, const double *Ue, double kappa,
+                            double lambda, double jw, double *Fq) {
+  double u = 0.0, gu[3] = {0, 0, 0};
+  for (int a = 0; a < nen; a++) {
+    u += Ue[a] * N[a];
+    for (int i = 0; i < dim; i++) gu[i] += Ue[a] * dN[a * dim + i];
+  }
+  double re = lambda * exp(u);
+  for (int a = 0; a < nen; a++) {
+    double gg = 0.0;
+    for (int i = 0; i < dim; i++) gg += dN[a * dim + i] * gu[i];
+    Fq[a] = jw * (kappa * gg - re * N[a]);
+  }
+}
+
+static int element_integrals_mode(const or_mesh *Msh, const int *e, const double *Uc, int64_t *gidx,
+                                  double *Fe, double *Ke, int fd) {
   const or_problem *P = Msh->P;
   int dim = P->dim;
   int s[3] = {0, 0, 0}, q[3] = {1, 1, 1};
@@ -441,13 +473,29 @@ static int element_integrals(const or_mesh *Msh, const int *e, const double *Uc,
           for (int i = 0; i < dim; i++) gg += dN[a * dim + i] * gu[i];
           /* Eq. (residual): (grad N_A, kappa grad u) - (N_A, lambda e^u) [- (N_A, f)] */
           Fe[a] += jw * (kappa * gg - re * N[a] - f * N[a]);
-          if (Ke)
+          if (Ke && !fd)
             for (int b = 0; b < nen; b++) {
               double gab = 0.0;
               for (int i = 0; i < dim; i++) gab += dN[a * dim + i] * dN[b * dim + i];
               /* Eq. (jacobian): (grad N_A, kappa grad N_B) - (N_A, lambda e^u N_B) */
               Ke[a * nen + b] += jw * (kappa * gab - re * N[a] * N[b]);
             }
+        }
+        if (Ke && fd) {
+          /* Eq. (fdjac), column by column */
+          double Ue[OR_MAXEN], Up[OR_MAXEN], F0[OR_MAXEN], F1[OR_MAXEN], nrm = 0.0;
+          for (int a = 0; a < nen; a++) {
+            Ue[a] = Uc[gidx[a]];
+            nrm += Ue[a] * Ue[a];
+          }
+          const double delta = sqrt(DBL_EPSILON) * sqrt(1.0 + sqrt(nrm));
+          point_integrand(dim, nen, N, dN, Ue, kappa, P->lambda, jw, F0);
+          for (int b = 0; b < nen; b++) {
+            for (int a = 0; a < nen; a++) Up[a] = Ue[a];
+            Up[b] += delta;
+            point_integrand(dim, nen, N, dN, Up, kappa, P->lambda, jw, F1);
+            for (int a = 0; a < nen; a++) Ke[a * nen + b] += (F1[a] - F0[a]) / delta;
+          }
         }
       }
   return nen;
@@ -538,6 +586,37 @@ int or_jacobian(const or_problem *P, const double *Uc, const int64_t *rowptr,
       for (int e0 = 0; e0 < Msh.ne[0]; e0++) {
         int e[3] = {e0, e1, e2};
         int nen = element_integrals(&Msh, e, Uc, gidx, Fe, Ke);
+        if (nen < 0) { free(Ke); mesh_free(&Msh); return nen; }
+        for (int a = 0; a < nen; a++)
+          for (int b = 0; b < nen; b++) {
+            int64_t k = find_col(rowptr, colidx, gidx[a], gidx[b]);
+            if (k < 0) { free(Ke); mesh_free(&Msh); return -20; }
+            vals[k] += Ke[a * nen + b];
+          }
+      }
+  for (int64_t A = 0; A < N; A++) dirichlet_fix_row(P, A, rowptr, colidx, vals + rowptr[A]);
+  free(Ke);
+  mesh_free(&Msh);
+  return 0;
+}
+
+/* Jacobian by local numerical differentiation (Sec. 2.10, Eq. fdjac) into CSR values
+ * on the given pattern, Dirichlet rows and columns as in or_jacobian. */
+int or_jacobian_fd(const or_problem *P, const double *Uc, const int64_t *rowptr,
+                   const int32_t *colidx, double *vals) {
+  or_mesh Msh;
+  int rc = mesh_init(P, &Msh);
+  if (rc) return rc;
+  int64_t N = num_dofs(P);
+  for (int64_t k = 0; k < rowptr[N]; k++) vals[k] = 0.0;
+  static int64_t gidx[OR_MAXEN];
+  static double Fe[OR_MAXEN];
+  double *Ke = (double *)malloc(sizeof(double) * OR_MAXEN * OR_MAXEN);
+  for (int e2 = 0; e2 < Msh.ne[2]; e2++)
+    for (int e1 = 0; e1 < Msh.ne[1]; e1++)
+      for (int e0 = 0; e0 < Msh.ne[0]; e0++) {
+        int e[3] = {e0, e1, e2};
+        int nen = element_integrals_mode(&Msh, e, Uc, gidx, Fe, Ke, 1);
         if (nen < 0) { free(Ke); mesh_free(&Msh); return nen; }
         for (int a = 0; a < nen; a++)
           for (int b = 0; b < nen; b++) {

@@ -75,6 +75,7 @@ def lib():
         L.or_pattern_dense_from_elements.argtypes = [P, vp]
         L.or_residual.argtypes = [P, vp, vp]
         L.or_jacobian.argtypes = [P, vp, vp, vp, vp]
+        L.or_jacobian_fd.argtypes = [P, vp, vp, vp, vp]
         L.or_residual_rows.argtypes = [P, vp, i64, vp, vp]
         L.or_jacobian_rows.argtypes = [P, vp, i64, vp, vp, vp, vp]
         L.or_dense_bruteforce.argtypes = [P, vp, vp, vp, ctypes.c_int]
@@ -214,6 +215,17 @@ class Problem:
         rc = lib().or_jacobian(ctypes.byref(c), _ptr(U), _ptr(rowptr), _ptr(colidx), _ptr(vals))
         if rc:
             raise RuntimeError("or_jacobian failed: %d" % rc)
+        return vals
+
+    def jacobian_fd(self, U):
+        """Sec. 2.10 local numerical differentiation, Eq. (fdjac), on the pattern."""
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        rowptr, colidx = self.pattern()
+        vals = np.zeros(len(colidx))
+        c = self._c()
+        rc = lib().or_jacobian_fd(ctypes.byref(c), _ptr(U), _ptr(rowptr), _ptr(colidx), _ptr(vals))
+        if rc:
+            raise RuntimeError("or_jacobian_fd failed: %d" % rc)
         return vals
 
     def jacobian_csr(self, U):

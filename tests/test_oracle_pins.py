@@ -384,3 +384,44 @@ def test_lambda_beyond_fold_does_not_converge():
     P = O.Problem([U, U], [2, 2], lam=7.5, dirichlet=dirichlet_all(2))
     _, hist = O.newton(P, np.zeros(P.N), max_it=30)
     assert not (hist[-1] <= 1e-10)
+
+
+@pytest.mark.parametrize("case", [(2, 2, 8, 1.0, None), (2, 3, 6, 2.5, "kappa"), (3, 2, 3, 1.5, None), (3, 3, 3, 2.0, "annulus")])
+def test_fd_jacobian_matches_the_analytic_jacobian(case):
+    """Sec. 2.10 Eq. (fdjac): first-order differences with step sqrt(eps) sqrt(1 + ||U_e||)
+    differ from the analytic Eq. (jacobian) by O(delta) + O(eps / delta) ~ 1e-8 relative;
+    a dropped term, a wrong step or a transposed column fails by orders of magnitude."""
+    dim, p, nel, lam, kind = case
+    lk = None
+    if kind == "annulus":
+        kn, ctrl, w = W.quarter_annulus((nel, nel, nel), p)
+    else:
+        kn, ctrl, w = [O.open_uniform_knots(nel, p)] * dim, None, None
+    n = [len(k) - p - 1 for k in kn]
+    N = int(np.prod(n))
+    if kind == "kappa":
+        lk = W.uniform(3, N, -0.5, 0.5)
+    bc = {(a, s): 0.0 for a in range(dim) for s in range(2)}
+    prob = O.Problem(kn, [p] * dim, ctrl=ctrl, weights=w, lam=lam, log_kappa=lk, dirichlet=bc)
+    U = W.uniform(11, N, -0.5, 0.5)
+    J = prob.jacobian(U)
+    Jfd = prob.jacobian_fd(U)
+    err = np.abs(Jfd - J).max() / np.abs(J).max()
+    assert err < 1e-6, err
+    assert err > 1e-12  # it is an approximation, not the analytic formula again
+    # the Dirichlet rows and columns are fixed the same way
+    rowptr, colidx = prob.pattern()
+    diag_rows = np.flatnonzero(prob.dirichlet_mask())[:5]
+    for A in diag_rows:
+        row = Jfd[rowptr[A]:rowptr[A + 1]]
+        assert np.array_equal(row, (colidx[rowptr[A]:rowptr[A + 1]] == A).astype(float))
+
+
+def test_fd_jacobian_of_a_linear_problem_is_the_stiffness():
+    """lambda = 0: the residual is linear in U, so the difference quotient equals the
+    stiffness up to the rounding of the differences (eps / delta ~ 1e-8)."""
+    kn = [O.open_uniform_knots(6, 2)] * 2
+    prob = O.Problem(kn, [2, 2], lam=0.0)
+    U = W.uniform(2, prob.N, -1.0, 1.0)
+    J = prob.jacobian(U)
+    assert np.abs(prob.jacobian_fd(U) - J).max() <= 1e-6 * np.abs(J).max()
