@@ -1,6 +1,6 @@
 """Benchmark lines for the configurations other than the headline one.
 
-    python bench.py --workload {bratu16, cube_mixed, batch512, learned64, nn64}
+    python bench.py --workload {bratu16, cube_mixed, batch512, learned64, nn64, fdjac}
 
 Each prints one JSON line with the keys of the headline line (metric, value,
 unit, config, clocks, e2e-style extras) for one configuration:
@@ -14,6 +14,8 @@ unit, config, clocks, e2e-style extras) for one configuration:
               error against the FP64 Jacobian; Newton solves with each.
   batch512    512 independent 2D instances (n ~ U{16..128}, p ~ U{2,3},
               lambda ~ U[0.5, 6]) in one persistent, graph-captured launch.
+  fdjac       Appendix C / Table 3: explicit versus local numerical differentiation
+              Jacobians of 3D Bratu on the unit cube (32^3-128^3, p = 1-3).
   nn64        the learned-guess network alone: forward and training step on a batch
               of 64 synthetic 66 x 66 inputs, against the BF16 tensor peak.
   learned64   kappa-Bratu on 64^2 quadratic (66 x 66 control grid): training
@@ -261,4 +263,36 @@ def nn64(torch, iga, W, clock, batch=64, reps=10):
         "train_step_tflops": 3 * fwd_flops / (t_step * 1e-3) / 1e12}, ck, dtype="bf16")
 
 
-WORKLOADS = {"bratu16": bratu16, "cube_mixed": cube_mixed, "batch512": batch512, "learned64": learned64, "nn64": nn64}
+def fdjac(torch, iga, W, clock):
+    """Sec. 2.10 / Appendix C (Table 3): the 3D Bratu Jacobian on the unit cube computed
+    explicitly (global sum factorisation, FP64) and by local numerical differentiation
+    (Eq. fdjac: per Gauss point and element value, FP64), best of 3 each, for the
+    table's cases that run on one GPU; the paper's CPU times are context."""
+    # (nel, p, k, paper explicit s, paper local ND s, paper cores)
+    cases = [(32, 2, 0, 0.31, 1.21, 8), (32, 2, 1, 0.33, 1.24, 8), (32, 3, 2, 3.71, 15.27, 8),
+             (64, 2, 0, 1.31, 5.15, 16), (64, 2, 1, 1.35, 5.26, 16), (64, 3, 2, 15.41, 64.93, 16),
+             (128, 1, 0, 0.52, 1.72, 16), (128, 2, 1, 10.74, 41.46, 16)]
+    out = []
+    clock.start()
+    for nel, p, k, pe, pn, cores in cases:
+        bc = {(a, s): 0.0 for a in range(3) for s in range(2)}
+        d = iga.Discretization(3, p, nel=nel, continuity=k, lam=2.0, dirichlet=bc)
+        U = torch.tensor(W.uniform(4, d.N, -0.1, 0.1), device="cuda")
+        J = torch.empty(d.nnz, dtype=torch.float64, device="cuda")
+        t_exp = _ev(torch, lambda: d.form_jacobian(U, vals=J), 3)
+        Jx = J.clone()
+        t_fd = _ev(torch, lambda: d.form_jacobian(U, prec=iga.IGA_JAC_FD, vals=J), 3)
+        err = (torch.linalg.norm(J - Jx) / torch.linalg.norm(Jx)).item()
+        out.append({"nel": nel, "p": p, "k": k, "nnz": d.nnz, "explicit_ms": t_exp, "local_nd_ms": t_fd,
+                    "ratio": t_fd / t_exp, "rel_frobenius_fd_vs_explicit": err,
+                    "paper_cpu_s": {"explicit": pe, "local_nd": pn, "ratio": pn / pe, "cores": cores}})
+        d.close()
+        del J, Jx
+        torch.cuda.empty_cache()
+    ck = clock.stop()
+    big = out[5]
+    return _line(big["nnz"] / (big["local_nd_ms"] * 1e-3), "nnz/s", "bratu3d_cube_table3_cases_local_numerical_differentiation",
+                 {"cases": out}, ck)
+
+
+WORKLOADS = {"bratu16": bratu16, "cube_mixed": cube_mixed, "batch512": batch512, "learned64": learned64, "nn64": nn64, "fdjac": fdjac}

@@ -58,6 +58,9 @@ typedef enum {
   IGA_JAC_TF32 = 1, /* element contraction with TF32 operands, FP32 accumulate; float * values */
   IGA_JAC_BF16 = 2, /* element contraction with BF16 operands, FP32 accumulate; float * values */
   IGA_JAC_FP32 = 3, /* global sum factorisation in FP32 on the CUDA cores; float * values */
+  IGA_JAC_FD = 5,   /* local numerical differentiation, Sec. 2.10 Eq. (fdjac): forward differences
+                       of the quadrature-point integrand in each element value, step
+                       sqrt(eps) sqrt(1 + ||U_e||_2); FP64 (double *) values; 3D p <= 3, 2D p <= 4 */
   IGA_JAC_NONE = 4  /* Newton only: matrix-free Newton-Krylov, no assembled Jacobian; the Krylov
                        solver applies J(U) exactly on the fly (sum-factorised element passes,
                        iga_apply_jacobian_mf) with Jacobi preconditioning from
@@ -147,8 +150,9 @@ iga_status iga_form_residual(iga_t iga, const double *U, double *F);
 iga_status iga_form_residual_noalloc(iga_t iga, const double *U, double *F);
 
 /* Jacobian J(U) of Eq. (jacobian) into CSR values on the library's pattern.
- * vals: device memory, caller-owned, nnz entries of double (IGA_FP64) or float
- * (IGA_JAC_TF32, IGA_JAC_BF16). */
+ * vals: device memory, caller-owned, nnz entries of double (IGA_FP64, IGA_JAC_FD) or
+ * float (IGA_JAC_TF32, IGA_JAC_BF16, IGA_JAC_FP32).  IGA_JAC_NONE is not a format:
+ * IGA_EINVAL. */
 iga_status iga_form_jacobian(iga_t iga, const double *U, void *vals, iga_precision prec);
 
 /* y = J x for CSR values on the library's pattern (the operator product of the

@@ -40,7 +40,7 @@ static void free_dir(DirDev &d) {
 
 static void release(iga_s *h) {
   for (int ax = 0; ax < 3; ax++) free_dir(h->ddev[ax]);
-  void *ps[] = {h->rowptr, h->colidx, h->weights, h->geom, h->Fe, h->Q00, h->T1, h->T2, h->Kstiff, h->Kstiff_f,
+  void *ps[] = {h->rowptr, h->colidx, h->weights, h->geom, h->Fe, h->Q00, h->T1, h->T2, h->Kstiff, h->Kstiff_f, h->Ebuf64,
                 h->Mred, h->Mred_f, h->J64, h->J32, h->wk, h->V, h->red, h->ctl, h->Uhost_dev,
                 h->geom32, h->tab32[0], h->tab32[1], h->tab32[2], h->Ebuf, h->z32};
   for (void *p : ps)
@@ -240,12 +240,13 @@ extern "C" iga_status iga_form_jacobian(iga_t h, const double *U, void *vals, ig
     CK(launch_jacobian64(h, U, (double *)vals, 0, nullptr));
   } else if (prec == IGA_JAC_FP32) {
     CK(launch_jacobian32(h, U, (float *)vals, 0, nullptr));
-  } else if (prec == IGA_JAC_TF32 || prec == IGA_JAC_BF16) {
+  } else if (prec == IGA_JAC_TF32 || prec == IGA_JAC_BF16 || prec == IGA_JAC_FD) {
     if (!mixed_supported(h->dim, h->p)) {
-      h->err = iga_format("mixed-precision Jacobian supports p <= %d in %dD", h->dim == 3 ? 3 : 4, h->dim);
+      h->err = iga_format("element-matrix Jacobians support p <= %d in %dD", h->dim == 3 ? 3 : 4, h->dim);
       return IGA_EINVAL;
     }
-    CK(launch_jacobian_mixed(h, U, (float *)vals, (int)prec));
+    if (prec == IGA_JAC_FD) CK(launch_jacobian_fd(h, U, (double *)vals));
+    else CK(launch_jacobian_mixed(h, U, (float *)vals, (int)prec));
   } else {
     h->err = "unknown precision";
     return IGA_EINVAL;
@@ -259,7 +260,7 @@ extern "C" iga_status iga_apply_jacobian(iga_t h, const void *vals, iga_precisio
     h->err = "vals, x and y must be non-NULL device pointers, x != y";
     return IGA_EINVAL;
   }
-  if (prec == IGA_FP64) {
+  if (prec == IGA_FP64 || prec == IGA_JAC_FD) {
     CK(launch_spmv64(h, (const double *)vals, x, y));
   } else if (prec == IGA_JAC_FP32 || prec == IGA_JAC_TF32 || prec == IGA_JAC_BF16) {
     CK(launch_spmv32(h, (const float *)vals, x, y));
@@ -349,6 +350,10 @@ static iga_status norm_host(iga_s *h, const double *x, double *out) {
 
 // Assemble the Newton Jacobian at U into h->J64 / h->J32.
 static iga_status newton_jacobian(iga_s *h, const double *U, bool f32, bool reuse, int prec) {
+  if (prec == IGA_JAC_FD) {  // local numerical differentiation, assembled in full each step
+    CK(launch_jacobian_fd(h, U, h->J64));
+    return IGA_OK;
+  }
   if (f32 && prec != IGA_JAC_FP32) {  // tensor-core element matrices, assembled in full each step
     CK(launch_jacobian_mixed(h, U, h->J32, prec));
     return IGA_OK;
@@ -376,13 +381,13 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
   iga_newton_opts o;
   iga_newton_defaults(&o);
   if (opts_in) o = *opts_in;
-  if ((o.jac == IGA_JAC_TF32 || o.jac == IGA_JAC_BF16) && !mixed_supported(h->dim, h->p)) {
-    h->err = "mixed-precision Jacobian not supported for this degree";
+  if ((o.jac == IGA_JAC_TF32 || o.jac == IGA_JAC_BF16 || o.jac == IGA_JAC_FD) && !mixed_supported(h->dim, h->p)) {
+    h->err = "element-matrix Jacobian not supported for this degree";
     return IGA_EINVAL;
   }
   if (!U || o.gmres_restart < 1 || o.gmres_restart > 1000 || o.max_newton < 0 || !(o.atol >= 0.0) ||
       (o.jac != IGA_FP64 && o.jac != IGA_JAC_TF32 && o.jac != IGA_JAC_BF16 && o.jac != IGA_JAC_FP32 &&
-       o.jac != IGA_JAC_NONE)) {
+       o.jac != IGA_JAC_NONE && o.jac != IGA_JAC_FD)) {
     h->err = "bad Newton options or NULL U";
     return IGA_EINVAL;
   }
@@ -390,8 +395,9 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
   memset(&R, 0, sizeof R);
   R.status = IGA_ENOCONV;
   const bool mf = o.jac == IGA_JAC_NONE;  // matrix-free
-  const bool f32 = !mf && o.jac != IGA_FP64;
-  const bool split = !f32 && !mf && o.reuse_stiffness != 0;
+  const bool fd = o.jac == IGA_JAC_FD;    // FP64 values by numerical differentiation
+  const bool f32 = !mf && !fd && o.jac != IGA_FP64;
+  const bool split = !f32 && !mf && !fd && o.reuse_stiffness != 0;
   iga_status st = ensure_workspace(h, o.gmres_restart, f32, mf);
   if (st != IGA_OK) return st;
   const int64_t N = h->N;

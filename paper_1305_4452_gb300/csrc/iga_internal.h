@@ -154,6 +154,7 @@ struct iga_s {
   float *geom32 = nullptr;     // [nelem][slots][nq] FP32 geometry factors
   float *tab32[3] = {nullptr, nullptr, nullptr};  // FP32 basis tables
   float *Ebuf = nullptr;       // [nelem][nen][nen] element matrices
+  double *Ebuf64 = nullptr;    // [nelem][nen][nen] FP64 element matrices (local numerical differentiation)
   float *z32 = nullptr;        // FP32 copy of the Krylov vector for the FP32 SpMV
   // Newton / Krylov workspace
   double *J64 = nullptr;
@@ -196,6 +197,8 @@ size_t jacobian_t1_groups(int dim);
 // ---- mixed-precision Jacobian (iga_mixed.cu) ----
 bool mixed_supported(int dim, int p);
 cudaError_t launch_jacobian_mixed(iga_s *h, const double *U, float *vals, int prec);
+// Jacobian by local numerical differentiation (Sec. 2.10 Eq. fdjac), FP64 values
+cudaError_t launch_jacobian_fd(iga_s *h, const double *U, double *vals);
 size_t jacobian_t2_groups(int dim);
 
 // ---- Krylov (iga_krylov.cu) ----

@@ -15,6 +15,7 @@
 // and writes FP32 values.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <float.h>
 #include <stdint.h>
 
 #include "iga_internal.h"
@@ -302,22 +303,22 @@ __device__ __forceinline__ bool on_dirichlet(const BndArgs &b, int dim, const in
 // value into the row accumulator in shared memory at the position of its column;
 // within one element the columns are distinct, so every entry is summed in element
 // order.  The finished row (weights, Dirichlet) is written contiguously.
-template <int DIM, int P>
-__global__ void __launch_bounds__(256) k_gather_elem(DirArgs d0, DirArgs d1, DirArgs d2, const float *__restrict__ Ebuf,
+template <int DIM, int P, typename T = float>
+__global__ void __launch_bounds__(256) k_gather_elem(DirArgs d0, DirArgs d1, DirArgs d2, const T *__restrict__ Ebuf,
                                                      const int64_t *__restrict__ rowptr, const double *__restrict__ wts,
-                                                     BndArgs bnd, float *__restrict__ vals, int64_t N) {
+                                                     BndArgs bnd, T *__restrict__ vals, int64_t N) {
   constexpr int N1 = P + 1, NEN = ipow<DIM>(N1), RMAX = ipow<DIM>(2 * P + 1);
-  __shared__ float rowacc[8][RMAX];
+  __shared__ T rowacc[8][RMAX];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t A = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (A >= N) return;
-  float *acc = rowacc[warp];
+  T *acc = rowacc[warp];
   int I[3] = {(int)(A % d0.n), (int)((A / d0.n) % d1.n), (DIM == 3) ? (int)(A / ((int64_t)d0.n * d1.n)) : 0};
   int n[3] = {d0.n, d1.n, d2.n};
   int l[3] = {d0.l[I[0]], d1.l[I[1]], DIM == 3 ? d2.l[I[2]] : 0};
   int w[3] = {d0.r[I[0]] - l[0] + 1, d1.r[I[1]] - l[1] + 1, DIM == 3 ? d2.r[I[2]] - l[2] + 1 : 1};
   const int len = w[0] * w[1] * w[2];
-  for (int k = lane; k < len; k += 32) acc[k] = 0.f;
+  for (int k = lane; k < len; k += 32) acc[k] = (T)0;
   __syncwarp();
   const int lo2 = (DIM == 3) ? d2.node_e0[I[2]] : 0, hi2 = (DIM == 3) ? lo2 + d2.node_ne[I[2]] : 1;
   const int lo1 = d1.node_e0[I[1]], hi1 = lo1 + d1.node_ne[I[1]];
@@ -330,7 +331,7 @@ __global__ void __launch_bounds__(256) k_gather_elem(DirArgs d0, DirArgs d1, Dir
         const int f0 = d0.first[e0];
         const int64_t e = e0 + (int64_t)d0.nel * (e1 + (int64_t)d1.nel * e2);
         const int a = (I[0] - f0) + N1 * ((I[1] - f1) + N1 * (I[2] - f2));
-        const float *Er = Ebuf + (size_t)e * NEN * NEN + (size_t)a * NEN;
+        const T *Er = Ebuf + (size_t)e * NEN * NEN + (size_t)a * NEN;
         for (int b = lane; b < NEN; b += 32) {
           int b0 = b % N1, b1 = (b / N1) % N1, b2 = (DIM == 3) ? b / (N1 * N1) : 0;
           int pos = ((f2 + b2 - l[2]) * w[1] + (f1 + b1 - l[1])) * w[0] + (f0 + b0 - l[0]);
@@ -341,15 +342,168 @@ __global__ void __launch_bounds__(256) k_gather_elem(DirArgs d0, DirArgs d1, Dir
     }
   }
   const bool rowfix = on_dirichlet(bnd, DIM, I, n);
-  const float wA = wts ? (float)wts[A] : 1.f;
+  const T wA = wts ? (T)wts[A] : (T)1;
   const int64_t r0 = rowptr[A];
   for (int k = lane; k < len; k += 32) {
     int J[3] = {l[0] + k % w[0], l[1] + (k / w[0]) % w[1], l[2] + k / (w[0] * w[1])};
     int64_t B = J[0] + (int64_t)d0.n * (J[1] + (int64_t)d1.n * J[2]);
-    float v = acc[k];
-    if (wts) v *= wA * (float)wts[B];
-    if (rowfix || on_dirichlet(bnd, DIM, J, n)) v = (A == B) ? 1.f : 0.f;
+    T v = acc[k];
+    if (wts) v *= wA * (T)wts[B];
+    if (rowfix || on_dirichlet(bnd, DIM, J, n)) v = (A == B) ? (T)1 : (T)0;
     vals[r0 + k] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Local numerical differentiation (Sec. 2.10, Eq. fdjac): per element, per Gauss
+// point q and element value k, the integrand F_q(U_e + delta e_k) - F_q(U_e) over
+// delta, delta = sqrt(eps) sqrt(1 + ||U_e||_2), summed over q into the element
+// matrix E[a][k] (weights included), then gathered per row like the tensor-core
+// element matrices.  The integrand is the factored form of the residual
+// (F_q,a = w_a (grad M_a . v + M_a s), v = S (grad u~ - u~ g), s = -g . v -
+// jw/W lambda e^(u~/W)) re-evaluated at the perturbed u~' = u~ + delta w_k M_k.
+// One CTA of 128 threads per element: unperturbed values per point, then chunks
+// of FD_QC points: the perturbed (v' - v, s' - s) per (point, k) in shared
+// memory, and each thread accumulates its (a, k) pairs over the points in order.
+// ---------------------------------------------------------------------------
+constexpr int FD_QC = 8;
+template <int DIM, int P>
+struct FdShape {
+  static constexpr int NEN = ipow<DIM>(P + 1);
+  static constexpr int THREADS = NEN >= 64 ? 256 : 128;  // (a, k) pairs per thread stay <= 16
+};
+
+template <int DIM, int P>
+__global__ void __launch_bounds__(FdShape<DIM, P>::THREADS) k_elem_fd(DirArgs d0, DirArgs d1, DirArgs d2,
+                                                                      const double *__restrict__ U, const double *__restrict__ wts,
+                                                                      const double *__restrict__ geom, GeomLayout gl,
+                                                                      double lambda, double *__restrict__ E, int64_t nelem) {
+  constexpr int N1 = P + 1, Q = P + 1, NEN = ipow<DIM>(N1), NQ = ipow<DIM>(Q);
+  constexpr int T = FdShape<DIM, P>::THREADS;
+  constexpr int PAIRS = NEN * NEN, PPT = (PAIRS + T - 1) / T;
+  __shared__ double tab[3][Q][N1][2];
+  __shared__ double wa[NEN], ua[NEN];
+  __shared__ double ut[NQ], gut[NQ][3], vq[NQ][3], sq[NQ];
+  __shared__ double dv[FD_QC][NEN][3], ds[FD_QC][NEN];
+  __shared__ double delta_s;
+  const int64_t e = blockIdx.x;
+  if (e >= nelem) return;
+  const int tid = threadIdx.x;
+  const int e0 = (int)(e % d0.nel), e1 = (int)((e / d0.nel) % d1.nel), e2 = DIM == 3 ? (int)(e / ((int64_t)d0.nel * d1.nel)) : 0;
+  for (int k = tid; k < DIM * Q * N1 * 2; k += blockDim.x) {
+    const int ax = k / (Q * N1 * 2), r = k % (Q * N1 * 2);
+    const DirArgs &d = ax == 0 ? d0 : (ax == 1 ? d1 : d2);
+    const int ee = ax == 0 ? e0 : (ax == 1 ? e1 : e2);
+    (&tab[ax][0][0][0])[r] = d.tab[(size_t)ee * Q * N1 * 2 + r];
+  }
+  for (int a = tid; a < NEN; a += blockDim.x) {
+    const int a0 = a % N1, a1 = (a / N1) % N1, a2 = DIM == 3 ? a / (N1 * N1) : 0;
+    const int64_t G = (d0.first[e0] + a0) + (int64_t)d0.n * ((d1.first[e1] + a1) + (int64_t)d1.n * ((DIM == 3 ? d2.first[e2] : 0) + a2));
+    ua[a] = U[G];
+    wa[a] = wts ? wts[G] : 1.0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double nrm = 0.0;
+    for (int a = 0; a < NEN; a++) nrm += ua[a] * ua[a];
+    delta_s = sqrt(DBL_EPSILON) * sqrt(1.0 + sqrt(nrm));
+  }
+  // M_a and grad M_a at point q from the tables
+  auto basis = [&](int a, int q, double &m, double *dm) {
+    const int a0 = a % N1, a1 = (a / N1) % N1, a2 = DIM == 3 ? a / (N1 * N1) : 0;
+    const int g0 = q % Q, g1 = (q / Q) % Q, g2 = DIM == 3 ? q / (Q * Q) : 0;
+    const double b0 = tab[0][g0][a0][0], db0 = tab[0][g0][a0][1], b1 = tab[1][g1][a1][0], db1 = tab[1][g1][a1][1];
+    if (DIM == 3) {
+      const double b2 = tab[2][g2][a2][0], db2 = tab[2][g2][a2][1];
+      m = b0 * b1 * b2;
+      dm[0] = db0 * b1 * b2;
+      dm[1] = b0 * db1 * b2;
+      dm[2] = b0 * b1 * db2;
+    } else {
+      m = b0 * b1;
+      dm[0] = db0 * b1;
+      dm[1] = b0 * db1;
+    }
+  };
+  // v = S (grad u~ - u~ g), s = -g . v - jw/W lambda e^(u~ / W) at point q for given u~, grad u~
+  auto integrand = [&](int q, double u, const double *gu, double *v, double &sv) {
+    const double *rec = geom + (size_t)e * gl.nf * NQ + q;
+    double r[3];
+    for (int a = 0; a < DIM; a++) r[a] = gu[a] - u * rec[(gl.g + a) * NQ];
+    if (DIM == 2) {
+      const double s00 = rec[gl.S * NQ], s11 = rec[(gl.S + 1) * NQ], s01 = rec[(gl.S + 2) * NQ];
+      v[0] = s00 * r[0] + s01 * r[1];
+      v[1] = s01 * r[0] + s11 * r[1];
+    } else {
+      const double s00 = rec[gl.S * NQ], s11 = rec[(gl.S + 1) * NQ], s22 = rec[(gl.S + 2) * NQ];
+      const double s01 = rec[(gl.S + 3) * NQ], s02 = rec[(gl.S + 4) * NQ], s12 = rec[(gl.S + 5) * NQ];
+      v[0] = s00 * r[0] + s01 * r[1] + s02 * r[2];
+      v[1] = s01 * r[0] + s11 * r[1] + s12 * r[2];
+      v[2] = s02 * r[0] + s12 * r[1] + s22 * r[2];
+    }
+    sv = -rec[gl.jwW * NQ] * lambda * exp(u * rec[gl.invW * NQ]);
+    for (int a = 0; a < DIM; a++) sv -= rec[(gl.g + a) * NQ] * v[a];
+  };
+  for (int q = tid; q < NQ; q += blockDim.x) {
+    double u = 0.0, gu[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < NEN; a++) {
+      double m, dm[3];
+      basis(a, q, m, dm);
+      const double c = wa[a] * ua[a];
+      u = fma(c, m, u);
+      for (int i = 0; i < DIM; i++) gu[i] = fma(c, dm[i], gu[i]);
+    }
+    double v[3], sv;
+    integrand(q, u, gu, v, sv);
+    ut[q] = u;
+    sq[q] = sv;
+    for (int i = 0; i < DIM; i++) {
+      gut[q][i] = gu[i];
+      vq[q][i] = v[i];
+    }
+  }
+  __syncthreads();
+  const double delta = delta_s;
+  double acc[PPT];
+#pragma unroll
+  for (int j = 0; j < PPT; j++) acc[j] = 0.0;
+  for (int q0 = 0; q0 < NQ; q0 += FD_QC) {
+    const int nq = min(FD_QC, NQ - q0);
+    for (int idx = tid; idx < nq * NEN; idx += blockDim.x) {
+      const int qq = idx / NEN, k = idx % NEN, q = q0 + qq;
+      double m, dm[3];
+      basis(k, q, m, dm);
+      const double c = delta * wa[k];
+      double gu[3], v[3], sv;
+      for (int i = 0; i < DIM; i++) gu[i] = gut[q][i] + c * dm[i];
+      integrand(q, ut[q] + c * m, gu, v, sv);
+      for (int i = 0; i < DIM; i++) dv[qq][k][i] = v[i] - vq[q][i];
+      ds[qq][k] = sv - sq[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < PPT; j++) {
+      const int pr = tid + T * j;
+      if (pr < PAIRS) {
+        const int a = pr / NEN, k = pr % NEN;
+        for (int qq = 0; qq < nq; qq++) {
+          double m, dm[3];
+          basis(a, q0 + qq, m, dm);
+          double t = m * ds[qq][k];
+          for (int i = 0; i < DIM; i++) t = fma(dm[i], dv[qq][k][i], t);
+          acc[j] += t;
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < PPT; j++) {
+    const int pr = tid + T * j;
+    if (pr < PAIRS) {
+      const int a = pr / NEN, k = pr % NEN;
+      E[(size_t)e * PAIRS + (size_t)a * NEN + k] = wa[a] * acc[j] / delta;
+    }
   }
 }
 
@@ -414,6 +568,24 @@ static cudaError_t mixed_prepare(iga_s *h) {
     ce = cudaMalloc((void **)&h->Ebuf, (size_t)h->nelem * nen * nen * sizeof(float));
     if (ce) return ce;
   }
+  return cudaGetLastError();
+}
+
+// Jacobian by local numerical differentiation (FP64 values), same degrees as the
+// tensor-core path; the element matrices go to a library-owned FP64 buffer.
+cudaError_t launch_jacobian_fd(iga_s *h, const double *U, double *vals) {
+  if (!mixed_supported(h->dim, h->p)) return cudaErrorNotSupported;
+  const int nen = (h->dim == 3) ? (h->p + 1) * (h->p + 1) * (h->p + 1) : (h->p + 1) * (h->p + 1);
+  if (!h->Ebuf64) {
+    cudaError_t ce = cudaMalloc((void **)&h->Ebuf64, (size_t)h->nelem * nen * nen * sizeof(double));
+    if (ce) return ce;
+  }
+  DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
+  IGA_LAUNCH(h, KC_ELEM_TC, DISPATCH_TC(h->dim, h->p, (k_elem_fd<D, PP><<<(unsigned)h->nelem, FdShape<D, PP>::THREADS, 0, h->stream>>>(
+                                                          a0, a1, a2, U, h->weights, h->geom, h->gl, h->lambda, h->Ebuf64, h->nelem))));
+  unsigned grid = (unsigned)((h->N * 32 + 255) / 256);
+  IGA_LAUNCH(h, KC_ELEM_GATHER, DISPATCH_TC(h->dim, h->p, (k_gather_elem<D, PP, double><<<grid, 256, 0, h->stream>>>(
+                                                              a0, a1, a2, h->Ebuf64, h->rowptr, nullptr, h->bnd, vals, h->N))));
   return cudaGetLastError();
 }
 

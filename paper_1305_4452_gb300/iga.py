@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_PKG, "lib", "libiga.so")
 
 IGA_OK, IGA_EINVAL, IGA_ENOMEM, IGA_ECUDA, IGA_ENOCONV, IGA_EDIVERGED, IGA_ETIMEOUT, IGA_ENAN = range(8)
 STATUS_NAMES = ["IGA_OK", "IGA_EINVAL", "IGA_ENOMEM", "IGA_ECUDA", "IGA_ENOCONV", "IGA_EDIVERGED", "IGA_ETIMEOUT", "IGA_ENAN"]
-IGA_FP64, IGA_JAC_TF32, IGA_JAC_BF16, IGA_JAC_FP32, IGA_JAC_NONE = 0, 1, 2, 3, 4
+IGA_FP64, IGA_JAC_TF32, IGA_JAC_BF16, IGA_JAC_FP32, IGA_JAC_NONE, IGA_JAC_FD = 0, 1, 2, 3, 4, 5
 
 # every symbol include/iga.h declares
 EXPORTS = ["iga_create", "iga_set_boundary_value", "iga_set_lambda", "iga_get_pattern", "iga_form_residual",
@@ -232,7 +232,8 @@ class Discretization:
     def form_jacobian(self, U, prec=IGA_FP64, vals=None):
         import torch
         if vals is None:
-            vals = torch.empty(self.nnz, dtype=torch.float64 if prec == IGA_FP64 else torch.float32, device=U.device)
+            vals = torch.empty(self.nnz, dtype=torch.float64 if prec in (IGA_FP64, IGA_JAC_FD) else torch.float32,
+                               device=U.device)
         _check(lib().iga_form_jacobian(self.h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(vals.data_ptr()), int(prec)), self.h)
         return vals
 
