@@ -160,6 +160,24 @@ def config_dict(disc):
     return d
 
 
+# ------------------------------------------------------ replica timing -----
+def max_over_ranks(value, world, device):
+    """The job's time is its slowest rank's: MAX all-reduce of a per-rank time (the
+    process group must exist when world > 1; gloo on the CPU, NCCL on GPUs)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_throughput(world, steps, seconds):
+    """Whole-job solves per second: every rank solves `steps` independent problems."""
+    return world * steps / seconds
+
+
 # ------------------------------------------------------------- our arm -----
 def run_ours(args):
     import numpy as np
@@ -214,11 +232,8 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     prof = disc.profile_read()
     disc.profile_enable([])
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
-    value = world * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, world, "cuda")
+    value = job_throughput(world, args.steps, ms / 1e3)
     launches = sum(v[2] for v in prof.values())
 
     # end to end through the host-buffer entry point (H2D of U0, D2H of the solution)
@@ -236,11 +251,9 @@ def run_ours(args):
         disc.solve_newton_host(Uh_np, opts)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t
-    if world > 1:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = tt.item()
-    e2e = {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8}
+    e2e_s = max_over_ranks(e2e_s, world, "cuda")
+    e2e = {"value": job_throughput(world, args.steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": N * 8,
+           "d2h_bytes_per_step": N * 8}
 
     # secondary throughputs of the FP64 assembly calls (same discretisation)
     Ur = torch.tensor(W.interior_field([NEL + P] * 3, 2), device="cuda")
