@@ -58,13 +58,13 @@ typedef enum {
   IGA_JAC_TF32 = 1, /* element contraction with TF32 operands, FP32 accumulate; float * values */
   IGA_JAC_BF16 = 2, /* element contraction with BF16 operands, FP32 accumulate; float * values */
   IGA_JAC_FP32 = 3, /* global sum factorisation in FP32 on the CUDA cores; float * values */
-  IGA_JAC_FD = 5,   /* local numerical differentiation, Sec. 2.10 Eq. (fdjac): forward differences
+  IGA_JAC_FD = 5,   /* local numerical differentiation, Sec. 2.8 Eq. (fdjac): forward differences
                        of the quadrature-point integrand in each element value, step
                        sqrt(eps) sqrt(1 + ||U_e||_2); FP64 (double *) values; 3D p <= 3, 2D p <= 4 */
   IGA_JAC_NONE = 4  /* Newton only: matrix-free Newton-Krylov, no assembled Jacobian; the Krylov
                        solver applies J(U) exactly on the fly (sum-factorised element passes,
                        iga_apply_jacobian_mf) with Jacobi preconditioning from
-                       iga_form_jacobian_diagonal (the -snes_mf run of Sec. 2.10, with exact
+                       iga_form_jacobian_diagonal (the -snes_mf run of Sec. 2.8, with exact
                        products instead of finite differences) */
 } iga_precision;
 

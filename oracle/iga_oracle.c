@@ -23,9 +23,11 @@
  *   - Element-by-element Gauss-Legendre assembly of the residual, Sec. 2.7
  *     Algorithm 3, with the Bratu integrand of Sec. 3.1 Eq. (residual); the
  *     Jacobian of Eq. (jacobian), assembled "in a similar fashion" (Sec. 2.7).
- *   - The Jacobian by local numerical differentiation, Sec. 2.10 Eq. (fdjac):
+ *   - The Jacobian by local numerical differentiation, Sec. 2.8 Eq. (fdjac):
  *     forward differences of the quadrature-point integrand in each element value,
  *     step sqrt(eps) sqrt(1 + ||U_e||_2) (or_jacobian_fd).
+ *   - The mass matrix (N_A, N_B) of the time-dependent residual of Sec. 4.2
+ *     (the u-dot term of R(w; u-dot, u)), by the same quadrature (or_mass).
  *   - The CSR adjacency pattern from BasisStencil, Sec. 2.5 Algorithm 2, in
  *     lexicographic tensor-product order.
  *   - Dirichlet rows set with IGASetBoundaryValue (Sec. 3.2): F_A = U_A - g and an
@@ -400,7 +402,7 @@ static void mesh_free(or_mesh *M) {
 /* Element integrals of one element: Fe[a] and (optionally) Ke[a*nen+b].
  * Sec. 2.7 Algorithm 3 steps: gather U_e, loop over quadrature points, ShapeFuns,
  * Integrand of Eq. (residual) / Eq. (jacobian), accumulate J_q w_q F_q.
- * fd != 0: Ke by the local numerical differentiation of Sec. 2.10, Eq. (fdjac):
+ * fd != 0: Ke by the local numerical differentiation of Sec. 2.8, Eq. (fdjac):
  * at every quadrature point, column b of dF_q/dU_e is (F_q(U_e + delta e_b) - F_q(U_e))
  * / delta with delta = sqrt(eps) * sqrt(1 + ||U_e||_2), F_q recomputed from the
  * perturbed element values. */
@@ -600,7 +602,7 @@ int or_jacobian(const or_problem *P, const double *Uc, const int64_t *rowptr,
   return 0;
 }
 
-/* Jacobian by local numerical differentiation (Sec. 2.10, Eq. fdjac) into CSR values
+/* Jacobian by local numerical differentiation (Sec. 2.8, Eq. fdjac) into CSR values
  * on the given pattern, Dirichlet rows and columns as in or_jacobian. */
 int or_jacobian_fd(const or_problem *P, const double *Uc, const int64_t *rowptr,
                    const int32_t *colidx, double *vals) {
@@ -627,6 +629,53 @@ int or_jacobian_fd(const or_problem *P, const double *Uc, const int64_t *rowptr,
       }
   for (int64_t A = 0; A < N; A++) dirichlet_fix_row(P, A, rowptr, colidx, vals + rowptr[A]);
   free(Ke);
+  mesh_free(&Msh);
+  return 0;
+}
+
+/* Mass matrix M_AB = sum_e sum_q J_q w_q N_A N_B (Sec. 4.2: the derivative of the
+ * residual's u-dot term (N_A, u-dot^h) in U-dot_B) into CSR values on the given
+ * pattern, with no Dirichlet fix; same element loop and quadrature as or_jacobian. */
+int or_mass(const or_problem *P, const int64_t *rowptr, const int32_t *colidx, double *vals) {
+  or_mesh Msh;
+  int rc = mesh_init(P, &Msh);
+  if (rc) return rc;
+  const int dim = P->dim;
+  int64_t N = num_dofs(P);
+  for (int64_t k = 0; k < rowptr[N]; k++) vals[k] = 0.0;
+  static int64_t gidx[OR_MAXEN];
+  static double Nq[OR_MAXEN], dN[OR_MAXEN * 3];
+  int nen = 1;
+  for (int d = 0; d < dim; d++) nen *= P->p[d] + 1;
+  for (int e2 = 0; e2 < Msh.ne[2]; e2++)
+    for (int e1 = 0; e1 < Msh.ne[1]; e1++)
+      for (int e0 = 0; e0 < Msh.ne[0]; e0++) {
+        int e[3] = {e0, e1, e2}, s[3] = {0, 0, 0}, q[3] = {1, 1, 1};
+        for (int d = 0; d < dim; d++) {
+          s[d] = Msh.sp[d][e[d]];
+          q[d] = P->q[d];
+        }
+        for (int g2 = 0; g2 < q[2]; g2++)
+          for (int g1 = 0; g1 < q[1]; g1++)
+            for (int g0 = 0; g0 < q[0]; g0++) {
+              int g[3] = {g0, g1, g2};
+              double xi[3] = {0, 0, 0}, wq = 1.0;
+              for (int d = 0; d < dim; d++) {
+                double lo = P->U[d][s[d]], hi = P->U[d][s[d] + 1];
+                xi[d] = 0.5 * (lo + hi) + 0.5 * (hi - lo) * Msh.gx[d][g[d]];
+                wq *= Msh.gw[d][g[d]] * 0.5 * (hi - lo);
+              }
+              double x[3], detJ;
+              rc = or_shape(P, s, xi, gidx, Nq, dN, x, &detJ);
+              if (rc < 0) { mesh_free(&Msh); return rc; }
+              for (int a = 0; a < nen; a++)
+                for (int b = 0; b < nen; b++) {
+                  int64_t k = find_col(rowptr, colidx, gidx[a], gidx[b]);
+                  if (k < 0) { mesh_free(&Msh); return -20; }
+                  vals[k] += detJ * wq * Nq[a] * Nq[b];
+                }
+            }
+      }
   mesh_free(&Msh);
   return 0;
 }

@@ -13,6 +13,11 @@ passage of the PetIGA paper, cited where it is defined in ``iga_oracle.c``:
 * ``pattern``                 -- Algorithm 2 (Sec. 2.5).
 * ``newton``                  -- Newton's method on R(U) = 0 (Sec. 3.1), each
   linear system solved exactly by a sparse LU (a library primitive).
+* ``mass``/``residual_ts``/``jacobian_ts`` -- the semi-discrete time-dependent
+  residual R(U-dot, U) of Sec. 4.2 for the transient Bratu problem, and its
+  derivative dR/dU + shift dR/dU-dot.
+* ``alpha_params``/``alpha_step`` -- one step of the generalized-alpha method for
+  first-order systems, Sec. 4.2 Eq. (ga), parameters from rho_infinity.
 """
 import ctypes
 import os
@@ -76,6 +81,7 @@ def lib():
         L.or_residual.argtypes = [P, vp, vp]
         L.or_jacobian.argtypes = [P, vp, vp, vp, vp]
         L.or_jacobian_fd.argtypes = [P, vp, vp, vp, vp]
+        L.or_mass.argtypes = [P, vp, vp, vp]
         L.or_residual_rows.argtypes = [P, vp, i64, vp, vp]
         L.or_jacobian_rows.argtypes = [P, vp, i64, vp, vp, vp, vp]
         L.or_dense_bruteforce.argtypes = [P, vp, vp, vp, ctypes.c_int]
@@ -218,7 +224,7 @@ class Problem:
         return vals
 
     def jacobian_fd(self, U):
-        """Sec. 2.10 local numerical differentiation, Eq. (fdjac), on the pattern."""
+        """Sec. 2.8 local numerical differentiation, Eq. (fdjac), on the pattern."""
         U = np.ascontiguousarray(U, dtype=np.float64)
         rowptr, colidx = self.pattern()
         vals = np.zeros(len(colidx))
@@ -227,6 +233,42 @@ class Problem:
         if rc:
             raise RuntimeError("or_jacobian_fd failed: %d" % rc)
         return vals
+
+    def mass(self):
+        """Mass matrix (N_A, N_B) on the pattern, no Dirichlet fix (Sec. 4.2)."""
+        rowptr, colidx = self.pattern()
+        vals = np.zeros(len(colidx))
+        c = self._c()
+        rc = lib().or_mass(ctypes.byref(c), _ptr(rowptr), _ptr(colidx), _ptr(vals))
+        if rc:
+            raise RuntimeError("or_mass failed: %d" % rc)
+        return vals
+
+    def mass_csr(self):
+        import scipy.sparse as sp
+        rowptr, colidx = self.pattern()
+        return sp.csr_matrix((self.mass(), colidx, rowptr), shape=(self.N, self.N))
+
+    def residual_ts(self, V, U):
+        """Sec. 4.2: R_A(U-dot, U) = (N_A, u-dot^h) + [Eq. (residual)]_A on the rows
+        without Dirichlet data; Dirichlet rows U_A - g as in ``residual``."""
+        F = self.residual(U)
+        MV = self.mass_csr() @ np.asarray(V, dtype=np.float64)
+        free = ~self.dirichlet_mask()
+        F[free] += MV[free]
+        return F
+
+    def jacobian_ts(self, shift, U):
+        """dR/dU + shift dR/dU-dot on the pattern: Eq. (jacobian) plus shift times the
+        mass matrix, with the Dirichlet fix of ``jacobian`` (identity rows, zero columns)."""
+        J = self.jacobian(U)
+        M = self.mass()
+        rowptr, colidx = self.pattern()
+        bnd = self.dirichlet_mask()
+        rows = np.repeat(np.arange(self.N), np.diff(rowptr))
+        keep = ~bnd[rows] & ~bnd[colidx]
+        J[keep] += shift * M[keep]
+        return J
 
     def jacobian_csr(self, U):
         import scipy.sparse as sp
@@ -306,3 +348,48 @@ def newton(prob, U0, atol=1e-10, max_it=50):
         J = prob.jacobian_csr(U)
         U = U + spla.spsolve(J.tocsc(), -F)
     return U, hist
+
+
+def alpha_params(rho_inf):
+    """Sec. 4.2: alpha_m, alpha_f and gamma of the generalized-alpha method from the
+    spectral radius rho_infinity of the amplification matrix as dt -> infinity."""
+    am = 0.5 * (3.0 - rho_inf) / (1.0 + rho_inf)
+    af = 1.0 / (1.0 + rho_inf)
+    return am, af, 0.5 + am - af
+
+
+def alpha_step(prob, U_n, V_n, dt, rho_inf, atol=1e-12, max_it=50):
+    """One step of Eq. (ga) (Sec. 4.2) for the transient residual ``residual_ts``:
+    given U_n and U-dot_n, find U-dot_{n+1} (and U_{n+1}) with
+        R(U-dot_{n+alpha_m}, U_{n+alpha_f}) = 0,
+        U-dot_{n+alpha_m} = U-dot_n + alpha_m (U-dot_{n+1} - U-dot_n),
+        U_{n+alpha_f}     = U_n + alpha_f (U_{n+1} - U_n),
+        U_{n+1}           = U_n + dt (gamma U-dot_{n+1} + (1 - gamma) U-dot_n).
+    Newton on the unknown U-dot_{n+1}, starting from the value that makes U_{n+1} = U_n
+    (U-dot_{n+1} = (gamma - 1) / gamma U-dot_n); its Jacobian is
+    alpha_m dR/dU-dot + alpha_f gamma dt dR/dU at the stage values, each linear
+    system solved by sparse LU.  Returns (U_{n+1}, U-dot_{n+1}, history of ||R||)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    am, af, gam = alpha_params(rho_inf)
+    U_n = np.asarray(U_n, dtype=np.float64)
+    V_n = np.asarray(V_n, dtype=np.float64)
+    rowptr, colidx = prob.pattern()
+    V1 = (gam - 1.0) / gam * V_n
+    hist = []
+    for _ in range(max_it + 1):
+        U1 = U_n + dt * (gam * V1 + (1.0 - gam) * V_n)
+        Vm = V_n + am * (V1 - V_n)
+        Uf = U_n + af * (U1 - U_n)
+        R = prob.residual_ts(Vm, Uf)
+        nr = float(np.linalg.norm(R))
+        hist.append(nr)
+        if nr <= atol or not np.isfinite(nr):
+            break
+        # dR/dU-dot_{n+1} = alpha_m dR/dU-dot + alpha_f gamma dt dR/dU; the Dirichlet rows
+        # U_A - g depend on U-dot_{n+1} through U_{n+alpha_f} only
+        vals = af * gam * dt * prob.jacobian_ts(am / (af * gam * dt), Uf)
+        J = sp.csr_matrix((vals, colidx, rowptr), shape=(prob.N, prob.N))
+        V1 = V1 + spla.spsolve(J.tocsc(), -R)
+    U1 = U_n + dt * (gam * V1 + (1.0 - gam) * V_n)
+    return U1, V1, hist

@@ -197,7 +197,7 @@ size_t jacobian_t1_groups(int dim);
 // ---- mixed-precision Jacobian (iga_mixed.cu) ----
 bool mixed_supported(int dim, int p);
 cudaError_t launch_jacobian_mixed(iga_s *h, const double *U, float *vals, int prec);
-// Jacobian by local numerical differentiation (Sec. 2.10 Eq. fdjac), FP64 values
+// Jacobian by local numerical differentiation (Sec. 2.8 Eq. fdjac), FP64 values
 cudaError_t launch_jacobian_fd(iga_s *h, const double *U, double *vals);
 size_t jacobian_t2_groups(int dim);
 

@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(256) k_gather_elem(DirArgs d0, DirArgs d1, Dir
 }
 
 // ---------------------------------------------------------------------------
-// Local numerical differentiation (Sec. 2.10, Eq. fdjac): per element, per Gauss
+// Local numerical differentiation (Sec. 2.8, Eq. fdjac): per element, per Gauss
 // point q and element value k, the integrand F_q(U_e + delta e_k) - F_q(U_e) over
 // delta, delta = sqrt(eps) sqrt(1 + ||U_e||_2), summed over q into the element
 // matrix E[a][k] (weights included), then gathered per row like the tensor-core

@@ -357,7 +357,7 @@ FD_CASES = [(2, 2, (9, 7), None, None, None), (2, 4, (5, 4), None, None, None), 
 
 @pytest.mark.parametrize("case", FD_CASES, ids=lambda c: "d%dp%d_%s_%s_%s" % (c[0], c[1], c[3], c[4], c[5]))
 def test_local_fd_jacobian_matches_the_oracle(case):
-    """Sec. 2.10 Eq. (fdjac) on the GPU against the oracle's implementation of the same
+    """Sec. 2.8 Eq. (fdjac) on the GPU against the oracle's implementation of the same
     formula: both are FP64 difference quotients with step ~1.5e-8 sqrt(1 + ||U_e||), so
     their rounding differs by ~eps |F_q| / delta ~ 1e-8 |J|; the bar is 1e-7 relative in
     the max norm.  Against the analytic Jacobian the FD error is O(delta) (< 1e-6)."""

@@ -388,7 +388,7 @@ def test_lambda_beyond_fold_does_not_converge():
 
 @pytest.mark.parametrize("case", [(2, 2, 8, 1.0, None), (2, 3, 6, 2.5, "kappa"), (3, 2, 3, 1.5, None), (3, 3, 3, 2.0, "annulus")])
 def test_fd_jacobian_matches_the_analytic_jacobian(case):
-    """Sec. 2.10 Eq. (fdjac): first-order differences with step sqrt(eps) sqrt(1 + ||U_e||)
+    """Sec. 2.8 Eq. (fdjac): first-order differences with step sqrt(eps) sqrt(1 + ||U_e||)
     differ from the analytic Eq. (jacobian) by O(delta) + O(eps / delta) ~ 1e-8 relative;
     a dropped term, a wrong step or a transposed column fails by orders of magnitude."""
     dim, p, nel, lam, kind = case
@@ -425,3 +425,119 @@ def test_fd_jacobian_of_a_linear_problem_is_the_stiffness():
     U = W.uniform(2, prob.N, -1.0, 1.0)
     J = prob.jacobian(U)
     assert np.abs(prob.jacobian_fd(U) - J).max() <= 1e-6 * np.abs(J).max()
+
+
+# ------------------------------------------- Sec. 4.2 time-dependent problems
+
+def test_mass_matrix_linear_kronecker_and_volume():
+    """(N_A, N_B) for p = 1 on a uniform mesh is the Kronecker product of the
+    textbook 1D linear-element mass matrix h/6 tridiag(1, 4, 1) (h/3 at the two
+    ends); on the NURBS annulus its entries sum to the volume 3 pi / 4."""
+    nel = 5
+    h = 1.0 / nel
+    kn = O.open_uniform_knots(nel, 1)
+    P = O.Problem([kn, kn], [1, 1], lam=0.0)
+    M = P.mass_csr().toarray()
+    M1 = np.diag(np.full(nel + 1, 4.0 * h / 6.0)) + np.diag(np.full(nel, h / 6.0), 1) + np.diag(np.full(nel, h / 6.0), -1)
+    M1[0, 0] = M1[-1, -1] = h / 3.0
+    assert np.abs(M - np.kron(M1, M1)).max() < 1e-16
+    kn3, ctrl, w = W.quarter_annulus(3, 3)
+    A = O.Problem(kn3, [3] * 3, quad=[8] * 3, ctrl=ctrl, weights=w, lam=0.0)
+    assert abs(A.mass().sum() - 3.0 * math.pi / 4.0) < 1e-13
+
+
+def test_alpha_parameters():
+    """rho_inf = 1 gives the implicit midpoint rule (alpha_m = alpha_f = gamma = 1/2);
+    every rho_inf gives gamma = 1/2 + alpha_m - alpha_f (second order)."""
+    assert O.alpha_params(1.0) == (0.5, 0.5, 0.5)
+    am, af, g = O.alpha_params(0.0)
+    assert (am, af, g) == (1.5, 1.0, 1.0)
+
+
+def _heat_mode(nel=6, p=2):
+    """lambda = 0 (the heat equation M U-dot + K U = 0): lowest generalised
+    eigenpair K phi = omega M phi on the free variables (a library eigensolver)."""
+    import scipy.linalg as sla
+    kn = O.open_uniform_knots(nel, p)
+    P = O.Problem([kn, kn], [p, p], lam=0.0, dirichlet=dirichlet_all(2))
+    free = ~P.dirichlet_mask()
+    K = P.jacobian_csr(np.zeros(P.N)).toarray()[np.ix_(free, free)]
+    M = P.mass_csr().toarray()[np.ix_(free, free)]
+    om, vec = sla.eigh(K, M)
+    phi = np.zeros(P.N)
+    phi[free] = vec[:, 0]  # M-normalised
+    Mf = np.zeros((P.N, P.N))
+    Mf[np.ix_(free, free)] = M
+    return P, phi, float(om[0]), Mf
+
+
+def test_alpha_midpoint_amplification():
+    """With rho_inf = 1 the method is the implicit midpoint rule, whose amplification
+    of a mode y' = -omega y is (1 - omega dt / 2) / (1 + omega dt / 2) whatever the
+    starting rate."""
+    P, phi, om, Mf = _heat_mode()
+    for dt in (0.01, 0.1, 1.0):
+        U1, V1, hist = O.alpha_step(P, phi, 0.3 * phi, dt, 1.0)
+        y1 = phi @ Mf @ U1
+        assert abs(y1 - (1 - om * dt / 2) / (1 + om * dt / 2)) < 1e-11, dt
+
+
+@pytest.mark.parametrize("rho", [0.0, 0.5])
+def test_alpha_spectral_radius_at_infinite_step(rho):
+    """Sec. 4.2: rho_inf is the spectral radius of the amplification matrix as
+    dt -> infinity.  The step maps (y_n, ydot_n) of one mode linearly; its 2 x 2 matrix
+    is read off two steps and its eigenvalues measured at omega dt ~ 2e9."""
+    P, phi, om, Mf = _heat_mode()
+    dt = 1e8
+    G = np.zeros((2, 2))
+    for j, (u0, v0) in enumerate([(phi, 0 * phi), (0 * phi, phi)]):
+        U1, V1, _ = O.alpha_step(P, u0, v0, dt, rho)
+        G[:, j] = [phi @ Mf @ U1, phi @ Mf @ V1]
+    r = np.abs(np.linalg.eigvals(G)).max()
+    assert abs(r - rho) < 1e-4, r
+
+
+def test_alpha_second_order():
+    """Second-order accuracy (Sec. 4.2): with the consistent start ydot_0 = -omega y_0
+    the error of a mode at T against exp(-omega T) falls 4x per halving of dt."""
+    P, phi, om, Mf = _heat_mode()
+    T = 0.1
+    errs = []
+    for nsteps in (4, 8, 16, 32):
+        dt = T / nsteps
+        U, V = phi.copy(), -om * phi
+        for _ in range(nsteps):
+            U, V, _ = O.alpha_step(P, U, V, dt, 0.5)
+        errs.append(abs(phi @ Mf @ U - math.exp(-om * T)))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(3)]
+    assert all(abs(o - 2.0) < 0.15 for o in orders[1:]), orders
+
+
+def test_alpha_step_keeps_a_steady_state():
+    """A steady Bratu solution (Sec. 3.1) with zero rate is a fixed point of the step."""
+    kn = O.open_uniform_knots(8, 2)
+    P = O.Problem([kn, kn], [2, 2], lam=1.0, dirichlet=dirichlet_all(2))
+    Us, hist = O.newton(P, np.zeros(P.N), atol=1e-13)
+    assert hist[-1] <= 1e-13
+    U1, V1, h = O.alpha_step(P, Us, np.zeros(P.N), 0.1, 0.5)
+    assert np.abs(U1 - Us).max() < 1e-13 and np.abs(V1).max() < 1e-12
+
+
+def test_transient_jacobian_is_derivative_of_transient_residual():
+    """dR/dU + a dR/dU-dot against central differences of R(V + a x, U + x) on a
+    NURBS annulus with random U and V (Dirichlet rows and columns removed)."""
+    kn, ctrl, w = W.quarter_annulus(2, 2)
+    P = O.Problem(kn, [2] * 3, ctrl=ctrl, weights=w, lam=1.5, dirichlet=dirichlet_all(3))
+    rng = np.random.default_rng(3)
+    free = ~P.dirichlet_mask()
+    U = np.where(free, rng.uniform(-0.3, 0.3, P.N), 0.0)
+    V = rng.uniform(-1, 1, P.N)
+    a = 7.0
+    rowptr, colidx = P.pattern()
+    J = sp.csr_matrix((P.jacobian_ts(a, U), colidx, rowptr), shape=(P.N, P.N)).toarray()
+    eps = 1e-6
+    for B in np.flatnonzero(free)[::7]:
+        e = np.zeros(P.N)
+        e[B] = eps
+        col = (P.residual_ts(V + a * e, U + e) - P.residual_ts(V - a * e, U - e)) / (2 * eps)
+        assert np.abs(col[free] - J[free, B]).max() < 1e-7 * max(1.0, np.abs(J).max()), B
