@@ -1,6 +1,6 @@
 """Benchmark lines for the configurations other than the headline one.
 
-    python bench.py --workload {bratu16, cube_mixed, batch512, learned64, nn64, fdjac}
+    python bench.py --workload {bratu16, cube_mixed, batch512, learned64, nn64, fdjac, genalpha}
 
 Each prints one JSON line with the keys of the headline line (metric, value,
 unit, config, clocks, e2e-style extras) for one configuration:
@@ -18,6 +18,9 @@ unit, config, clocks, e2e-style extras) for one configuration:
               Jacobians of 3D Bratu on the unit cube (32^3-128^3, p = 1-3).
   nn64        the learned-guess network alone: forward and training step on a batch
               of 64 synthetic 66 x 66 inputs, against the BF16 tensor peak.
+  genalpha    Sec. 4.2: generalized-alpha time steps (rho_inf = 0.5, dt = 0.01) of the
+              transient Bratu problem u_t = div grad u + 2 e^u on the 64^3 cubic NURBS
+              quarter annulus from u = 0, each step a Newton-Krylov solve to 1e-10.
   learned64   kappa-Bratu on 64^2 quadratic (66 x 66 control grid): training
               data from the batched solver, the convolutional guess trained on
               the GPU, evaluation on held-out fields against the zero start and
@@ -295,4 +298,33 @@ def fdjac(torch, iga, W, clock):
                  {"cases": out}, ck)
 
 
-WORKLOADS = {"bratu16": bratu16, "cube_mixed": cube_mixed, "batch512": batch512, "learned64": learned64, "nn64": nn64, "fdjac": fdjac}
+def genalpha(torch, iga, W, clock, nel=64, steps=10, dt=0.01, rho=0.5):
+    kn, ctrl, w = W.quarter_annulus(nel, 3)
+    bc = {(a, s): 0.0 for a in range(3) for s in range(2)}
+    d = iga.Discretization(3, 3, knots=kn, ctrl=ctrl, weights=w, lam=2.0, dirichlet=bc)
+    out = {}
+    clock.start()
+    for label, jac, ksp in (("fp64_gmres", iga.IGA_FP64, iga.IGA_KSP_GMRES), ("fp32_cg", iga.IGA_JAC_FP32, iga.IGA_KSP_CG)):
+        o = iga.newton_defaults()
+        o.jac, o.ksp = jac, ksp
+        U = torch.zeros(d.N, dtype=torch.float64, device="cuda")
+        V = torch.zeros_like(U)
+        d.ts_alpha_step(U.clone(), V.clone(), dt, rho, o)  # warm-up (also assembles the stiffness once)
+        its, kits = [], []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            rep = d.ts_alpha_step(U, V, dt, rho, o)
+            its.append(rep.newton_its)
+            kits.append(rep.krylov_its)
+        t = time.perf_counter() - t0
+        out[label] = {"ms_per_step": 1e3 * t / steps, "steps_per_s": steps / t, "newton_its": its, "krylov_its": kits,
+                      "u_max_at_end": U.max().item(), "t_end": steps * dt}
+    ck = clock.stop()
+    d.close()
+    return _line(out["fp64_gmres"]["steps_per_s"], "time steps/s",
+                 "transient_bratu_annulus64_p3_lambda2_genalpha_rho0.5_dt0.01", {"cases": out, "dofs": d.N}, ck)
+
+
+WORKLOADS = {"bratu16": bratu16, "cube_mixed": cube_mixed, "batch512": batch512, "learned64": learned64, "nn64": nn64, "fdjac": fdjac,
+             "genalpha": genalpha}

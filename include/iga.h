@@ -219,6 +219,42 @@ iga_status iga_solve_newton(iga_t iga, double *U, const iga_newton_opts *opts,
 iga_status iga_solve_newton_host(iga_t iga, double *U_host, const iga_newton_opts *opts,
                                  iga_newton_report *report);
 
+/* ---- Time-dependent problems: generalized-alpha (Sec. 4.2, Eq. ga) ----
+ * The transient Bratu problem u_t - div(kappa grad u) - lambda e^u = 0 in the
+ * semi-discrete form of Sec. 4.2: with U-dot the rates of the control variables,
+ *   R_A(U-dot, U) = (N_A, u-dot^h) + [Eq. (residual)]_A   (rows without Dirichlet data),
+ *   R_A = U_A - g_A                                        (Dirichlet rows; no U-dot),
+ * u-dot^h = sum_B U-dot_B N_B, integrated by the same Gauss rule as Eq. (residual). */
+
+/* R(V, U) with V = U-dot.  V, U, F: device double[n], caller-owned; F distinct from V
+ * and U.  Stream-ordered, deterministic. */
+iga_status iga_form_residual_ts(iga_t iga, const double *V, const double *U, double *F);
+
+/* dR/dU + shift dR/dU-dot at U (the shifted Jacobian of an implicit time step): the
+ * Jacobian of Eq. (jacobian) plus shift times the mass matrix (N_A, N_B), with the
+ * Dirichlet fix of iga_form_jacobian.  vals: caller-owned device memory, nnz doubles
+ * (IGA_FP64) or floats (IGA_JAC_FP32); other precisions: IGA_EINVAL. */
+iga_status iga_form_jacobian_ts(iga_t iga, double shift, const double *U, void *vals, iga_precision prec);
+
+typedef struct {
+  double dt;       /* time step t_{n+1} - t_n, > 0 */
+  double rho_inf;  /* spectral radius at dt -> infinity, in [0, 1]; 1 = implicit midpoint rule */
+} iga_ts_opts;
+
+/* One generalized-alpha step (Sec. 4.2, Eq. ga) with
+ *   alpha_m = (3 - rho_inf) / (2 (1 + rho_inf)), alpha_f = 1 / (1 + rho_inf),
+ *   gamma = 1/2 + alpha_m - alpha_f.
+ * In: U = U_n, V = U-dot_n (device double[n], caller-owned, distinct; U_n should meet
+ * the Dirichlet data and V_n be zero there).  Newton-Krylov (opts as for
+ * iga_solve_newton; jac IGA_FP64, IGA_JAC_FP32 or IGA_JAC_NONE, others IGA_EINVAL) solves
+ * R(U-dot_{n+alpha_m}, U_{n+alpha_f}) = 0 for W = U_{n+alpha_f} starting from W = U_n;
+ * its Jacobian is the shifted one with shift alpha_m / (alpha_f gamma dt).  Out, when the
+ * report's status is IGA_OK: U = U_{n+1}, V = U-dot_{n+1}; otherwise U and V keep
+ * U_n and U-dot_n.  The U-independent stiffness is assembled on the first step and
+ * kept by the later ones.  Synchronises the stream; returns report->status. */
+iga_status iga_ts_alpha_step(iga_t iga, const iga_ts_opts *ts, double *U, double *V, const iga_newton_opts *opts,
+                             iga_newton_report *report);
+
 /* ---- Batched solves: many independent 2D problems in one persistent launch ----
  * Each instance i is a 2D Bratu problem described by descs[i] (dim 2, identity
  * map: ctrl = weights = NULL, equal degree 1..3 and equal knot vectors in both

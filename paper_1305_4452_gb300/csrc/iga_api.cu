@@ -40,7 +40,7 @@ static void free_dir(DirDev &d) {
 
 static void release(iga_s *h) {
   for (int ax = 0; ax < 3; ax++) free_dir(h->ddev[ax]);
-  void *ps[] = {h->rowptr, h->colidx, h->weights, h->geom, h->Fe, h->Q00, h->T1, h->T2, h->Kstiff, h->Kstiff_f, h->Ebuf64,
+  void *ps[] = {h->rowptr, h->colidx, h->weights, h->geom, h->Fe, h->Q00, h->T1, h->T2, h->Kstiff, h->Kstiff_f, h->Ebuf64, h->ts_buf,
                 h->Mred, h->Mred_f, h->J64, h->J32, h->wk, h->V, h->red, h->ctl, h->Uhost_dev,
                 h->geom32, h->tab32[0], h->tab32[1], h->tab32[2], h->Ebuf, h->z32};
   for (void *p : ps)
@@ -404,9 +404,12 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
   double *F = h->wk, *dU = h->wk + N, *Ut = h->wk + 2 * N, *Ft = h->wk + 3 * N;
   int eg = (int)((N + 255) / 256);
   if (eg > 608) eg = 608;
-  // stiffness part is rebuilt once per solve (reuse across Newton steps only)
-  h->K_valid = false;
-  h->K_valid_f = false;
+  // stiffness part is rebuilt once per solve (reuse across Newton steps only); the
+  // steps of a time integration keep it (K depends on the geometry alone)
+  if (!h->ts_on) {
+    h->K_valid = false;
+    h->K_valid_f = false;
+  }
   h->q00_valid = false;
   CK(launch_residual(h, U, F));
   double fn;
@@ -491,6 +494,106 @@ extern "C" iga_status iga_solve_newton_host(iga_t h, double *U_host, const iga_n
   iga_status st = iga_solve_newton(h, h->Uhost_dev, opts, rep);
   if (st == IGA_EINVAL || st == IGA_ECUDA || st == IGA_ENOMEM) return st;
   CK(cudaMemcpyAsync(U_host, h->Uhost_dev, h->N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return st;
+}
+
+// ---- time-dependent problems (Sec. 4.2) ----
+extern "C" iga_status iga_form_residual_ts(iga_t h, const double *V, const double *U, double *F) {
+  if (!h) return IGA_EINVAL;
+  if (!V || !U || !F || F == U || F == V) {
+    h->err = "V, U and F must be non-NULL device pointers, F distinct from U and V";
+    return IGA_EINVAL;
+  }
+  h->ts_on = true;
+  h->ts_a = 0.0;
+  h->ts_C = V;
+  cudaError_t ce = launch_residual(h, U, F);
+  h->ts_on = false;
+  h->ts_C = nullptr;
+  CK(ce);
+  return IGA_OK;
+}
+
+extern "C" iga_status iga_form_jacobian_ts(iga_t h, double shift, const double *U, void *vals, iga_precision prec) {
+  if (!h) return IGA_EINVAL;
+  if (!U || !vals || !isfinite(shift) || (prec != IGA_FP64 && prec != IGA_JAC_FP32)) {
+    h->err = "U and vals must be non-NULL device pointers, shift finite, precision IGA_FP64 or IGA_JAC_FP32";
+    return IGA_EINVAL;
+  }
+  h->ts_on = true;
+  h->ts_a = shift;
+  h->ts_C = nullptr;
+  cudaError_t ce = prec == IGA_FP64 ? launch_jacobian64(h, U, (double *)vals, 0, nullptr)
+                                    : launch_jacobian32(h, U, (float *)vals, 0, nullptr);
+  h->ts_on = false;
+  h->ts_a = 0.0;
+  CK(ce);
+  return IGA_OK;
+}
+
+// C = -a U_n + b U-dot_n and a copy of U_n (the Newton start W = U_n stays in U)
+__global__ static void k_alpha_begin(const double *__restrict__ U, const double *__restrict__ V, double a, double b,
+                                     double *__restrict__ C, double *__restrict__ Un, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double u = U[i];
+    C[i] = -a * u + b * V[i];
+    Un[i] = u;
+  }
+}
+// From the stage value W = U_{n+alpha_f} in U: U_{n+1} = U_n + (W - U_n) / alpha_f and
+// U-dot_{n+1} = (U_{n+1} - U_n) / (gamma dt) - (1 - gamma) / gamma U-dot_n
+__global__ static void k_alpha_end(double *__restrict__ U, double *__restrict__ V, const double *__restrict__ Un,
+                                   double inv_af, double inv_gdt, double c_v, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double un = Un[i];
+    const double du = (U[i] - un) * inv_af;
+    U[i] = un + du;
+    V[i] = du * inv_gdt - c_v * V[i];
+  }
+}
+
+extern "C" iga_status iga_ts_alpha_step(iga_t h, const iga_ts_opts *ts, double *U, double *V, const iga_newton_opts *opts,
+                                        iga_newton_report *rep) {
+  if (!h) return IGA_EINVAL;
+  if (!ts || !U || !V || U == V || !(ts->dt > 0.0) || !isfinite(ts->dt) || !(ts->rho_inf >= 0.0) || !(ts->rho_inf <= 1.0)) {
+    h->err = "need distinct device U and V, dt > 0 and 0 <= rho_inf <= 1";
+    return IGA_EINVAL;
+  }
+  iga_newton_opts o;
+  iga_newton_defaults(&o);
+  if (opts) o = *opts;
+  if (o.jac != IGA_FP64 && o.jac != IGA_JAC_FP32 && o.jac != IGA_JAC_NONE) {
+    h->err = "time steps support the IGA_FP64, IGA_JAC_FP32 and IGA_JAC_NONE Jacobians";
+    return IGA_EINVAL;
+  }
+  // Sec. 4.2: parameters from rho_inf; with W = U_{n+alpha_f} the unknown,
+  // U-dot_{n+alpha_m} = a (W - U_n) + b U-dot_n, a = alpha_m / (alpha_f gamma dt), b = 1 - alpha_m / gamma
+  const double rho = ts->rho_inf, dt = ts->dt;
+  const double am = 0.5 * (3.0 - rho) / (1.0 + rho), af = 1.0 / (1.0 + rho), gam = 0.5 + am - af;
+  const double a = am / (af * gam * dt), b = 1.0 - am / gam;
+  const int64_t N = h->N;
+  if (!h->ts_buf) CK(cudaMalloc((void **)&h->ts_buf, 2 * N * sizeof(double)));
+  double *C = h->ts_buf, *Un = h->ts_buf + N;
+  int eg = (int)((N + 255) / 256);
+  if (eg > 608) eg = 608;
+  IGA_LAUNCH(h, KC_VEC, (k_alpha_begin<<<eg, 256, 0, h->stream>>>(U, V, a, b, C, Un, N)));
+  CK(cudaGetLastError());
+  h->ts_on = true;
+  h->ts_a = a;
+  h->ts_C = C;
+  iga_status st = iga_solve_newton(h, U, &o, rep);
+  h->ts_on = false;
+  h->ts_a = 0.0;
+  h->ts_C = nullptr;
+  if (st == IGA_OK) {
+    IGA_LAUNCH(h, KC_VEC, (k_alpha_end<<<eg, 256, 0, h->stream>>>(U, V, Un, 1.0 / af, 1.0 / (gam * dt), (1.0 - gam) / gam, N)));
+  } else {  // leave U_n and U-dot_n as they were
+    const std::string msg = h->err;
+    CK(cudaMemcpyAsync(U, Un, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    h->err = msg;
+  }
+  CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
   return st;
 }

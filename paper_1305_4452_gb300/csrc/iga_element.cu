@@ -446,18 +446,25 @@ __global__ void k_gather_residual(DirArgs d0, DirArgs d1, DirArgs d2, const doub
 // then Q00 = cs * g^T S g - cr * jw/W^2 * lambda * exp(u~/W).
 // ---------------------------------------------------------------------------
 //
-// With RES the same interpolation yields the reaction part of the residual
+// With MODE 1 the same interpolation yields the reaction part of the residual
 // instead (and the reaction part of Q00 at the same U, for the Jacobian that
 // follows an accepted line-search point): s = -jw/W * lambda * exp(u) at the Gauss points, projected back on
 // the element's functions (value tables only) into Fe[e][A] (times w_A).  The
 // Newton solver adds it to K U, K the assembled U-independent stiffness: since
 // Eq. (residual) is K U plus this term under the same quadrature, F(U) then
 // needs one operator product and a quarter of the sum-factorised contractions.
-template <int DIM, int P, int NE, bool RES>
+//
+// With MODE 2 it adds the rate term of the time-dependent residual (Sec. 4.2),
+// (N_A, v^h) with v^h = sum (shift U_B + C_B) N_B, to Fe: the interpolated value is
+// ṽ = sum w_B (shift U_B + C_B) M_B, s = jw/W^2 ṽ.  In MODES 0 and 1 shift is the
+// coefficient of dR/dU-dot in the Jacobian: Q00 gains cr * shift * jw/W^2.
+template <int DIM, int P, int NE, int MODE>
 __global__ void __launch_bounds__(128) k_q00(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ U,
                                              const double *__restrict__ wts, const double *__restrict__ geom, GeomLayout gl,
                                              double lambda, double cs, double cr, double *__restrict__ Q00, int64_t nelem,
-                                             double *__restrict__ q00_out) {
+                                             double *__restrict__ q00_out, double shift = 0.0,
+                                             const double *__restrict__ C = nullptr) {
+  constexpr bool RES = MODE != 0;
   using SM = ResSmem<DIM, P>;
   constexpr int N1 = SM::N1, Q = SM::Q, NEN = SM::NEN, NQ = SM::NQ;
   extern __shared__ double smem[];
@@ -478,7 +485,9 @@ __global__ void __launch_bounds__(128) k_q00(DirArgs d0, DirArgs d1, DirArgs d2,
       int a = k - SM::TAB;
       int a0 = a % N1, a1 = (a / N1) % N1, a2 = (DIM == 3) ? a / (N1 * N1) : 0;
       int64_t G = (d0.first[e0] + a0) + (int64_t)d0.n * ((d1.first[e1] + a1) + (int64_t)d1.n * ((DIM == 3 ? d2.first[e2] : 0) + a2));
-      base[k] = U ? U[G] * (wts ? wts[G] : 1.0) : 0.0;
+      double x = U ? U[G] : 0.0;
+      if (MODE == 2) x = shift * x + (C ? C[G] : 0.0);
+      base[k] = x * (wts ? wts[G] : 1.0);
     }
   }
   __syncthreads();
@@ -537,16 +546,27 @@ __global__ void __launch_bounds__(128) k_q00(DirArgs d0, DirArgs d1, DirArgs d2,
       for (int a1 = 0; a1 < N1; a1++) ut = fma(TB(base, 1, g1, a1), Y[a1 * Q + g0], ut);
     }
     const double *rec = geom + (size_t)e * gl.nf * NQ + qp;
+    if (MODE == 2) {
+      (base + SM::TAB + NEN)[qp] = rec[gl.jwW2 * NQ] * ut;
+      continue;
+    }
     if (RES) {
       const double lex = lambda * exp(ut * rec[gl.invW * NQ]);
       (base + SM::TAB + NEN)[qp] = -rec[gl.jwW * NQ] * lex;
       // the reaction part of Q00 at the same point, for the next Jacobian
-      if (q00_out) q00_out[(size_t)e * NQ + qp] = -rec[gl.jwW2 * NQ] * lex;
+      if (q00_out) {
+        double v = -rec[gl.jwW2 * NQ] * lex;
+        if (shift != 0.0) v += shift * rec[gl.jwW2 * NQ];
+        q00_out[(size_t)e * NQ + qp] = v;
+      }
       continue;
     }
     double v = 0.0;
     if (cs != 0.0) v = cs * rec[gl.gSg * NQ];
-    if (cr != 0.0) v -= cr * rec[gl.jwW2 * NQ] * lambda * exp(ut * rec[gl.invW * NQ]);
+    if (cr != 0.0) {
+      v -= cr * rec[gl.jwW2 * NQ] * lambda * exp(ut * rec[gl.invW * NQ]);
+      if (shift != 0.0) v += cr * shift * rec[gl.jwW2 * NQ];
+    }
     Q00[(size_t)e * NQ + qp] = v;
   }
   if (!RES) return;
@@ -589,7 +609,8 @@ __global__ void __launch_bounds__(128) k_q00(DirArgs d0, DirArgs d1, DirArgs d2,
         int e0 = (int)(e % d0.nel), e1 = (int)((e / d0.nel) % d1.nel), e2 = (int)(e / ((int64_t)d0.nel * d1.nel));
         acc *= wts[(d0.first[e0] + a0) + (int64_t)d0.n * ((d1.first[e1] + a1) + (int64_t)d1.n * (d2.first[e2] + a2))];
       }
-      Q00[(size_t)e * NEN + a] = acc;
+      if (MODE == 2) Q00[(size_t)e * NEN + a] += acc;
+      else Q00[(size_t)e * NEN + a] = acc;
     }
   } else {
     for (int idx = tid; idx < NE * N1 * Q; idx += nt) {
@@ -617,7 +638,8 @@ __global__ void __launch_bounds__(128) k_q00(DirArgs d0, DirArgs d1, DirArgs d2,
         int e0 = (int)(e % d0.nel), e1 = (int)(e / d0.nel);
         acc *= wts[(d0.first[e0] + a0) + (int64_t)d0.n * (d1.first[e1] + a1)];
       }
-      Q00[(size_t)e * NEN + a] = acc;
+      if (MODE == 2) Q00[(size_t)e * NEN + a] += acc;
+      else Q00[(size_t)e * NEN + a] = acc;
     }
   }
 #undef TB
@@ -682,6 +704,22 @@ cudaError_t launch_geometry(iga_s *h, const double *ctrl_dev, const double *logk
 template <int DIM, int P>
 static size_t res_smem(int NE) { return (size_t)NE * ResSmem<DIM, P>::PER * sizeof(double); }
 
+// Adds the rate term (N_A, v^h) of the time-dependent residual (Sec. 4.2) to the
+// element vectors Fe, v = ts_a U + ts_C per control variable; nothing unless h->ts_on.
+static cudaError_t launch_rate_term(iga_s *h, const double *U, double *Fe) {
+  if (!h->ts_on) return cudaSuccess;
+  DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
+  constexpr int NE = 4;
+  unsigned grid = (unsigned)((h->nelem + NE - 1) / NE);
+  IGA_LAUNCH(h, KC_RES_ELEM, DISPATCH_DP(h->dim, h->p, ({
+    size_t sm = res_smem<D, PP>(NE);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_q00<D, PP, NE, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_q00<D, PP, NE, 2><<<grid, 128, sm, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, 0.0, 0.0, 0.0, Fe,
+                                                      h->nelem, nullptr, h->ts_a, h->ts_C);
+  })));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_residual(iga_s *h, const double *U, double *F) {
   DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
   constexpr int NE = 4;
@@ -691,6 +729,8 @@ cudaError_t launch_residual(iga_s *h, const double *U, double *F) {
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_residual<D, PP, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_residual<D, PP, NE><<<grid, 128, sm, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, h->lambda, h->Fe, h->nelem);
   })));
+  cudaError_t ce = launch_rate_term(h, U, h->Fe);
+  if (ce) return ce;
   unsigned g2 = (unsigned)((h->N + 255) / 256);
   if (h->dim == 3)
     IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<3><<<g2, 256, 0, h->stream>>>(a0, a1, a2, h->Fe, U, h->bnd, F, h->N, h->p + 1, nullptr)));
@@ -710,6 +750,8 @@ cudaError_t launch_residual_into(iga_s *h, const double *U, double *F, double *F
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_residual<D, PP, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_residual<D, PP, NE><<<grid, 128, sm, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, h->lambda, Fe, h->nelem);
   })));
+  cudaError_t ce = launch_rate_term(h, U, Fe);
+  if (ce) return ce;
   unsigned g2 = (unsigned)((h->N + 255) / 256);
   if (h->dim == 3)
     IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<3><<<g2, 256, 0, h->stream>>>(a0, a1, a2, Fe, U, h->bnd, F, h->N, h->p + 1, nullptr)));
@@ -724,8 +766,9 @@ cudaError_t launch_q00(iga_s *h, const double *U, double cs, double cr) {
   unsigned grid = (unsigned)((h->nelem + NE - 1) / NE);
   IGA_LAUNCH(h, KC_Q00, DISPATCH_DP(h->dim, h->p, ({
     size_t sm = res_smem<D, PP>(NE);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_q00<D, PP, NE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_q00<D, PP, NE, false><<<grid, 128, sm, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, h->lambda, cs, cr, h->Q00, h->nelem, nullptr);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_q00<D, PP, NE, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_q00<D, PP, NE, 0><<<grid, 128, sm, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, h->lambda, cs, cr, h->Q00, h->nelem,
+                                                      nullptr, h->ts_on ? h->ts_a : 0.0);
   })));
   return cudaGetLastError();
 }
@@ -738,9 +781,12 @@ cudaError_t launch_residual_split(iga_s *h, const double *U, double *F, const do
   unsigned grid = (unsigned)((h->nelem + NE - 1) / NE);
   IGA_LAUNCH(h, KC_RES_ELEM, DISPATCH_DP(h->dim, h->p, ({
     size_t sm = res_smem<D, PP>(NE);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_q00<D, PP, NE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_q00<D, PP, NE, true><<<grid, 128, sm, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, h->lambda, 0.0, 1.0, h->Fe, h->nelem, h->Q00);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_q00<D, PP, NE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_q00<D, PP, NE, 1><<<grid, 128, sm, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, h->lambda, 0.0, 1.0, h->Fe, h->nelem,
+                                                      h->Q00, h->ts_on ? h->ts_a : 0.0);
   })));
+  ce = launch_rate_term(h, U, h->Fe);
+  if (ce) return ce;
   unsigned g2 = (unsigned)((h->N + 255) / 256);
   if (h->dim == 3)
     IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<3><<<g2, 256, 0, h->stream>>>(a0, a1, a2, h->Fe, U, h->bnd, F, h->N, h->p + 1, KU)));

@@ -149,6 +149,12 @@ struct iga_s {
   float *Mred_f = nullptr;
   bool K_valid = false, K_valid_f = false;  // Kstiff / Kstiff_f hold the current stiffness
   bool q00_valid = false;      // Q00 holds the reaction part of Q00 at the current Newton iterate
+  // time-dependent residual (Sec. 4.2): while ts_on, every residual adds (N_A, v^h) with
+  // v = ts_a U + ts_C per control variable, and every Jacobian adds ts_a times the mass matrix
+  bool ts_on = false;
+  double ts_a = 0.0;
+  const double *ts_C = nullptr;
+  double *ts_buf = nullptr;    // generalized-alpha workspace: C and U_n (2 N doubles)
   double *Uhost_dev = nullptr; // device copy of U for the host-buffer solve
   // mixed-precision Jacobian (tensor cores)
   float *geom32 = nullptr;     // [nelem][slots][nq] FP32 geometry factors

@@ -24,7 +24,8 @@ EXPORTS = ["iga_create", "iga_set_boundary_value", "iga_set_lambda", "iga_get_pa
            "iga_batch_create", "iga_batch_offsets", "iga_batch_set_launch", "iga_batch_solve", "iga_batch_destroy",
            "iga_batch_last_error", "iga_nn_create", "iga_nn_num_params", "iga_nn_get_params", "iga_nn_set_params",
            "iga_nn_forward", "iga_nn_loss_grad", "iga_nn_adam_step", "iga_nn_destroy", "iga_nn_last_error",
-           "iga_nn_set_h1_weight", "iga_apply_jacobian", "iga_apply_jacobian_mf", "iga_form_jacobian_diagonal"]
+           "iga_nn_set_h1_weight", "iga_apply_jacobian", "iga_apply_jacobian_mf", "iga_form_jacobian_diagonal",
+           "iga_form_residual_ts", "iga_form_jacobian_ts", "iga_ts_alpha_step"]
 
 KERNEL_CLASSES = ["geometry", "residual_element", "residual_gather", "q00", "jac_stage1", "jac_stage2", "jac_final",
                   "spmv", "gs_orth", "gmres_scalar", "vector", "combine", "pattern", "elem_tc", "elem_gather"]
@@ -75,6 +76,10 @@ class IgaNewtonReport(ctypes.Structure):
     ]
 
 
+class IgaTsOpts(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("rho_inf", ctypes.c_double)]
+
+
 class IgaProfile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 16), ("timed", ctypes.c_longlong * 16), ("launches", ctypes.c_longlong * 16)]
 
@@ -105,6 +110,10 @@ def lib():
         L.iga_newton_defaults.restype = None
         L.iga_solve_newton.argtypes = [vp, vp, ctypes.POINTER(IgaNewtonOpts), ctypes.POINTER(IgaNewtonReport)]
         L.iga_solve_newton_host.argtypes = [vp, vp, ctypes.POINTER(IgaNewtonOpts), ctypes.POINTER(IgaNewtonReport)]
+        L.iga_form_residual_ts.argtypes = [vp, vp, vp, vp]
+        L.iga_form_jacobian_ts.argtypes = [vp, ctypes.c_double, vp, vp, ctypes.c_int]
+        L.iga_ts_alpha_step.argtypes = [vp, ctypes.POINTER(IgaTsOpts), vp, vp, ctypes.POINTER(IgaNewtonOpts),
+                                        ctypes.POINTER(IgaNewtonReport)]
         L.iga_destroy.argtypes = [vp]
         L.iga_destroy.restype = None
         L.iga_last_error.argtypes = [vp]
@@ -270,6 +279,36 @@ class Discretization:
         r = IgaNewtonReport()
         rc = lib().iga_solve_newton(self.h, ctypes.c_void_p(U.data_ptr()), ctypes.byref(o), ctypes.byref(r))
         if check and rc not in (IGA_OK,):
+            raise IgaError(rc, lib().iga_last_error(self.h).decode())
+        return r
+
+    def form_residual_ts(self, V, U, F=None):
+        """R(V, U) of the time-dependent problem, V the rates U-dot (Sec. 4.2)."""
+        import torch
+        if F is None:
+            F = torch.empty_like(U)
+        _check(lib().iga_form_residual_ts(self.h, ctypes.c_void_p(V.data_ptr()), ctypes.c_void_p(U.data_ptr()),
+                                          ctypes.c_void_p(F.data_ptr())), self.h)
+        return F
+
+    def form_jacobian_ts(self, shift, U, prec=IGA_FP64, vals=None):
+        """dR/dU + shift dR/dU-dot at U (FP64 or FP32 values on the pattern)."""
+        import torch
+        if vals is None:
+            vals = torch.empty(self.nnz, dtype=torch.float64 if prec == IGA_FP64 else torch.float32, device=U.device)
+        _check(lib().iga_form_jacobian_ts(self.h, float(shift), ctypes.c_void_p(U.data_ptr()),
+                                          ctypes.c_void_p(vals.data_ptr()), int(prec)), self.h)
+        return vals
+
+    def ts_alpha_step(self, U, V, dt, rho_inf=0.5, opts=None, check=True):
+        """One generalized-alpha step (Sec. 4.2): U = U_n, V = U-dot_n in, U_{n+1} and
+        U-dot_{n+1} out (in place)."""
+        o = opts if opts is not None else newton_defaults()
+        t = IgaTsOpts(float(dt), float(rho_inf))
+        r = IgaNewtonReport()
+        rc = lib().iga_ts_alpha_step(self.h, ctypes.byref(t), ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(V.data_ptr()),
+                                     ctypes.byref(o), ctypes.byref(r))
+        if check and rc != IGA_OK:
             raise IgaError(rc, lib().iga_last_error(self.h).decode())
         return r
 

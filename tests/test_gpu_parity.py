@@ -386,3 +386,114 @@ def test_newton_with_fd_jacobian_reaches_the_oracle_solution():
     assert rep.status == 0 and rep.fnorm <= 1e-10
     assert np.linalg.norm(prob.residual(U.cpu().numpy())) <= 1e-10 * (1 + 1e-12)
     disc.close()
+
+
+# ------------------------------------------- Sec. 4.2 time-dependent problems
+
+TS_CASES = [(2, 2, (9, 7), None, None, None), (2, 3, (7, 6), None, "annulus", None), (2, 2, (9, 7), None, None, 3),
+            (3, 3, (4, 5, 3), None, "annulus", None), (3, 2, (5, 4, 3), None, None, None), (2, 4, (5, 4), None, None, None)]
+
+
+@pytest.mark.parametrize("case", TS_CASES, ids=lambda c: "d%dp%d_%s_%s_%s" % (c[0], c[1], c[3], c[4], c[5]))
+def test_transient_residual_and_shifted_jacobian_match_the_oracle(case):
+    dim, p, nel, k, geom, kap = case
+    disc, prob, n = make_pair(dim, p, nel, lam=1.3, k=k, geom=geom, kappa_seed=kap)
+    U0 = W.interior_field(n, seed=21, lo=-0.3, hi=0.3)
+    V0 = W.uniform(22, disc.N, -1.0, 1.0)
+    U = torch.tensor(U0, device="cuda")
+    V = torch.tensor(V0, device="cuda")
+    F = disc.form_residual_ts(V, U).cpu().numpy()
+    Fo = prob.residual_ts(V0, U0)
+    assert rel(F, Fo) <= TOL, rel(F, Fo)
+    for shift in (0.0, 37.5):
+        J = disc.form_jacobian_ts(shift, U).cpu().numpy()
+        Jo = prob.jacobian_ts(shift, U0)
+        assert rel(J, Jo) <= TOL, (shift, rel(J, Jo))
+    J32 = disc.form_jacobian_ts(37.5, U, prec=iga().IGA_JAC_FP32).cpu().numpy().astype(np.float64)
+    assert rel(J32, prob.jacobian_ts(37.5, U0)) <= 1e-5
+    # the steady residual is unchanged by the transient calls (state restored)
+    assert rel(disc.form_residual(U).cpu().numpy(), prob.residual(U0)) <= TOL
+    disc.close()
+
+
+def _stage_residual(prob, Un, Vn, U1, V1, dt, rho):
+    am, af, g = O.alpha_params(rho)
+    return prob.residual_ts(Vn + am * (V1 - Vn), Un + af * (U1 - Un))
+
+
+@pytest.mark.parametrize("jac", ["fp64", "fp32_cg", "mf"])
+def test_alpha_steps_match_the_oracle(jac):
+    """Three generalized-alpha steps of the transient Bratu problem (Sec. 4.2) from a
+    random start: U_{n+1}, U-dot_{n+1} against the oracle's steps (which iterate on
+    U-dot_{n+1}, not on the stage value), and the oracle's stage residual at the GPU's
+    result."""
+    I = iga()
+    disc, prob, n = make_pair(2, 2, (12, 10), lam=1.5)
+    U0 = W.interior_field(n, seed=31, lo=-0.2, hi=0.2)
+    V0 = np.zeros(disc.N)
+    U = torch.tensor(U0, device="cuda")
+    V = torch.tensor(V0, device="cuda")
+    o = I.newton_defaults()
+    o.atol = 1e-12
+    if jac == "fp32_cg":
+        o.jac, o.ksp = I.IGA_JAC_FP32, I.IGA_KSP_CG
+    elif jac == "mf":
+        o.jac = I.IGA_JAC_NONE
+    Uo, Vo = U0.copy(), V0.copy()
+    dt, rho = 0.02, 0.5
+    for step in range(3):
+        Un, Vn = Uo, Vo
+        rep = disc.ts_alpha_step(U, V, dt, rho, o)
+        assert rep.status == 0 and rep.fnorm <= 1e-12
+        Uo, Vo, hist = O.alpha_step(prob, Un, Vn, dt, rho, atol=1e-13)
+        Ug, Vg = U.cpu().numpy(), V.cpu().numpy()
+        assert np.abs(Ug - Uo).max() <= 1e-10 * np.abs(Uo).max(), (step, np.abs(Ug - Uo).max())
+        assert np.abs(Vg - Vo).max() <= 1e-8 * np.abs(Vo).max(), (step, np.abs(Vg - Vo).max())
+        assert np.linalg.norm(_stage_residual(prob, Un, Vn, Ug, Vg, dt, rho)) <= 2e-12
+        Uo, Vo = Ug, Vg  # continue both from the GPU's state
+    disc.close()
+
+
+def test_alpha_step_3d_annulus_and_midpoint():
+    I = iga()
+    disc, prob, n = make_pair(3, 3, (4, 5, 3), lam=2.0, geom="annulus")
+    U0 = W.interior_field(n, seed=41, lo=-0.1, hi=0.1)
+    V0 = np.zeros(disc.N)
+    for rho in (1.0, 0.0):
+        U = torch.tensor(U0, device="cuda")
+        V = torch.tensor(V0, device="cuda")
+        o = I.newton_defaults()
+        o.atol = 1e-12
+        rep = disc.ts_alpha_step(U, V, 0.05, rho, o)
+        assert rep.status == 0
+        Uo, Vo, _ = O.alpha_step(prob, U0, V0, 0.05, rho, atol=1e-13)
+        Ug, Vg = U.cpu().numpy(), V.cpu().numpy()
+        # what is unique: the stage equations hold at the GPU's result; the iterates of the
+        # two solvers (each stopped at ||R|| <= 1e-12) differ by ||J^-1|| ||R||, ||J^-1|| ~ 30 here
+        assert np.linalg.norm(_stage_residual(prob, U0, V0, Ug, Vg, 0.05, rho)) <= 2e-12
+        assert np.abs(Ug - Uo).max() <= 1e-9 * np.abs(Uo).max()
+        assert np.abs(Vg - Vo).max() <= 1e-7 * np.abs(Vo).max()
+    disc.close()
+
+
+def test_alpha_step_rejects_bad_input_and_keeps_state():
+    I = iga()
+    disc, prob, n = make_pair(2, 2, (6, 5), lam=1.0)
+    U = torch.tensor(W.interior_field(n, seed=5, lo=-0.1, hi=0.1), device="cuda")
+    V = torch.zeros_like(U)
+    U_before = U.clone()
+    for dt, rho in ((0.0, 0.5), (0.1, 1.5), (0.1, -0.1), (float("nan"), 0.5)):
+        with pytest.raises(I.IgaError) as ei:
+            disc.ts_alpha_step(U, V, dt, rho)
+        assert ei.value.status == I.IGA_EINVAL
+    o = I.newton_defaults()
+    o.jac = I.IGA_JAC_BF16
+    with pytest.raises(I.IgaError):
+        disc.ts_alpha_step(U, V, 0.1, 0.5, o)
+    # a Newton failure (one iteration allowed, tight tolerance) leaves U_n and U-dot_n
+    o = I.newton_defaults()
+    o.max_newton, o.atol = 1, 1e-30
+    rep = disc.ts_alpha_step(U, V, 0.1, 0.5, o, check=False)
+    assert rep.status != 0
+    assert torch.equal(U, U_before) and torch.count_nonzero(V).item() == 0
+    disc.close()
