@@ -28,6 +28,10 @@
  *     step sqrt(eps) sqrt(1 + ||U_e||_2) (or_jacobian_fd).
  *   - The mass matrix (N_A, N_B) of the time-dependent residual of Sec. 4.2
  *     (the u-dot term of R(w; u-dot, u)), by the same quadrature (or_mass).
+ *   - Periodic spaces, Sec. 2.4: the caller passes the knot vector unclamped by
+ *     Eqs. (unclamp-left)-(unclamp-right) and wrap[d] = k+1, the number of redundant
+ *     functions; every function index i is wrapped by Eq. (map-wrap),
+ *     i -> mod(i, n-k), in the assembly, the pattern and the brute-force check.
  *   - The CSR adjacency pattern from BasisStencil, Sec. 2.5 Algorithm 2, in
  *     lexicographic tensor-product order.
  *   - Dirichlet rows set with IGASetBoundaryValue (Sec. 3.2): F_A = U_A - g and an
@@ -61,6 +65,8 @@ typedef struct {
   int bnd[3][2];           /* Dirichlet flag per (axis, side) */
   double bval[3][2];       /* Dirichlet value per (axis, side) */
   int source;              /* 1: add the manufactured source of u* = prod sin(pi x) */
+  int wrap[3];             /* periodic direction: k+1 (unclamped knots, C^k across the
+                              boundary); 0: not periodic */
 } or_problem;
 
 /* ---------------- Sec. 2.1: B-spline basis, Cox-de Boor ---------------- */
@@ -122,8 +128,16 @@ int or_gauss_legendre(int q, double *x, double *w) {
   return 0;
 }
 
-/* Number of basis functions in direction d: m - p - 1 (Sec. 2.1). */
-static int nfun(const or_problem *P, int d) { return P->m[d] - P->p[d] - 1; }
+/* Number of basis functions in direction d: m - p - 1 (Sec. 2.1), less the k+1
+ * functions a periodic direction eliminates (Sec. 2.4). */
+static int nfun(const or_problem *P, int d) { return P->m[d] - P->p[d] - 1 - P->wrap[d]; }
+
+/* Eq. (map-wrap): mod(a, b) = a - b floor(a / b), for any integer a. */
+static int map_wrap(int a, int b) {
+  int q = a / b;
+  if (a % b != 0 && a < 0) q -= 1;
+  return a - b * q;
+}
 
 int or_num_funcs(const or_problem *P, int d) { return nfun(P, d); }
 
@@ -166,6 +180,8 @@ static int check(const or_problem *P) {
     if (P->q[d] < 1 || P->q[d] > 16) return -4;
     for (int k = 0; k + 1 < P->m[d]; k++)
       if (P->U[d][k] > P->U[d][k + 1]) return -5; /* knots must not decrease */
+    if (P->wrap[d] < 0 || P->wrap[d] > P->p[d] || nfun(P, d) < 1) return -7;
+    if (P->wrap[d] && (P->bnd[d][0] || P->bnd[d][1])) return -8; /* no Dirichlet face on a periodic axis */
   }
   int nen = 1;
   for (int d = 0; d < P->dim; d++) nen *= P->p[d] + 1;
@@ -176,22 +192,43 @@ static int check(const or_problem *P) {
 /* CSR pattern by BasisStencil (Algorithm 2) per direction and the lexicographic
  * tensor product of the ranges (Sec. 2.5).  Rows and columns are in the natural
  * order of Eq. (5).  With colidx == NULL only rowptr is filled; returns nnz. */
+/* The 1D column list of function i in direction d: BasisStencil's range, each
+ * index wrapped by Eq. (map-wrap) in a periodic direction (Sec. 2.5), sorted and
+ * without repeats.  Returns its length. */
+static int column_list(const or_problem *P, int d, int i, int *cols) {
+  int l, r, c = 0, n = nfun(P, d);
+  or_stencil(i, P->p[d], P->U[d], &l, &r);
+  for (int j = l; j <= r; j++) {
+    int w = P->wrap[d] ? map_wrap(j, n) : j, seen = 0;
+    for (int t = 0; t < c; t++) seen |= cols[t] == w;
+    if (!seen) cols[c++] = w;
+  }
+  for (int a = 1; a < c; a++)  /* insertion sort */
+    for (int b = a; b > 0 && cols[b - 1] > cols[b]; b--) {
+      int t = cols[b];
+      cols[b] = cols[b - 1];
+      cols[b - 1] = t;
+    }
+  return c;
+}
+
 int64_t or_pattern(const or_problem *P, int64_t *rowptr, int32_t *colidx) {
   if (check(P)) return -1;
   int n[3] = {1, 1, 1};
   for (int d = 0; d < P->dim; d++) n[d] = nfun(P, d);
   int64_t N = num_dofs(P), nnz = 0;
+  int cl[3][4 * OR_MAXP + 4], len[3] = {1, 1, 1};
   for (int64_t A = 0; A < N; A++) {
     int idx[3] = {0, 0, 0};
     int64_t t = A;
     for (int d = 0; d < P->dim; d++) { idx[d] = (int)(t % n[d]); t /= n[d]; }
-    int l[3] = {0, 0, 0}, r[3] = {0, 0, 0};
-    for (int d = 0; d < P->dim; d++) or_stencil(idx[d], P->p[d], P->U[d], &l[d], &r[d]);
+    cl[1][0] = cl[2][0] = 0;
+    for (int d = 0; d < P->dim; d++) len[d] = column_list(P, d, idx[d], cl[d]);
     if (rowptr) rowptr[A] = nnz;
-    for (int k = l[2]; k <= r[2]; k++)
-      for (int j = l[1]; j <= r[1]; j++)
-        for (int i = l[0]; i <= r[0]; i++) {
-          if (colidx) colidx[nnz] = (int32_t)(i + (int64_t)n[0] * (j + (int64_t)n[1] * k));
+    for (int k = 0; k < len[2]; k++)
+      for (int j = 0; j < len[1]; j++)
+        for (int i = 0; i < len[0]; i++) {
+          if (colidx) colidx[nnz] = (int32_t)(cl[0][i] + (int64_t)n[0] * (cl[1][j] + (int64_t)n[1] * cl[2][k]));
           nnz++;
         }
   }
@@ -224,11 +261,13 @@ int or_pattern_dense_from_elements(const or_problem *P, unsigned char *mark) {
         for (int c2 = 0; c2 <= pp[2]; c2++)
           for (int c1 = 0; c1 <= pp[1]; c1++)
             for (int c0 = 0; c0 <= pp[0]; c0++) {
-              int64_t A = (s0[0] + c0) + (int64_t)n[0] * ((s0[1] + c1) + (int64_t)n[1] * (s0[2] + c2));
+              int64_t A = map_wrap(s0[0] + c0, n[0]) +
+                          (int64_t)n[0] * (map_wrap(s0[1] + c1, n[1]) + (int64_t)n[1] * map_wrap(s0[2] + c2, n[2]));
               for (int b2 = 0; b2 <= pp[2]; b2++)
                 for (int b1 = 0; b1 <= pp[1]; b1++)
                   for (int b0 = 0; b0 <= pp[0]; b0++) {
-                    int64_t B = (s0[0] + b0) + (int64_t)n[0] * ((s0[1] + b1) + (int64_t)n[1] * (s0[2] + b2));
+                    int64_t B = map_wrap(s0[0] + b0, n[0]) +
+                                (int64_t)n[0] * (map_wrap(s0[1] + b1, n[1]) + (int64_t)n[1] * map_wrap(s0[2] + b2, n[2]));
                     mark[A * N + B] = 1;
                   }
             }
@@ -272,7 +311,7 @@ int or_shape(const or_problem *P, const int *s, const double *xi, int64_t *gidx,
         int c[3] = {c0, c1, c2};
         int64_t G = 0, stride = 1;
         for (int d = 0; d < dim; d++) {
-          G += (int64_t)(s[d] - pp[d] + c[d]) * stride;
+          G += (int64_t)map_wrap(s[d] - pp[d] + c[d], n[d]) * stride; /* Eq. (map-wrap) */
           stride *= n[d];
         }
         gidx[a] = G;
@@ -680,7 +719,8 @@ int or_mass(const or_problem *P, const int64_t *rowptr, const int32_t *colidx, d
   return 0;
 }
 
-/* Elements whose support contains natural node A: span s with s-p <= i <= s. */
+/* Elements whose support contains natural node A: span s with s-p <= i <= s
+ * (non-periodic directions only). */
 static int elements_of_node(const or_mesh *Msh, int64_t A, int lo[3], int hi[3]) {
   const or_problem *P = Msh->P;
   int64_t t = A;
@@ -706,6 +746,7 @@ static int elements_of_node(const or_mesh *Msh, int64_t A, int lo[3], int hi[3])
 /* Residual entries of selected rows only (same definition as or_residual). */
 int or_residual_rows(const or_problem *P, const double *Uc, int64_t nr, const int64_t *rows,
                      double *out) {
+  if (P->wrap[0] || P->wrap[1] || P->wrap[2]) return -30;
   or_mesh Msh;
   int rc = mesh_init(P, &Msh);
   if (rc) return rc;
@@ -737,6 +778,7 @@ int or_residual_rows(const or_problem *P, const double *Uc, int64_t nr, const in
  * row laid out as its pattern row rowptr[A]..rowptr[A+1]). */
 int or_jacobian_rows(const or_problem *P, const double *Uc, int64_t nr, const int64_t *rows,
                      const int64_t *rowptr, const int32_t *colidx, double *out) {
+  if (P->wrap[0] || P->wrap[1] || P->wrap[2]) return -30;
   or_mesh Msh;
   int rc = mesh_init(P, &Msh);
   if (rc) return rc;
@@ -817,8 +859,14 @@ int or_dense_bruteforce(const or_problem *P, const double *Uc, double *F, double
               for (int d = 0; d < 3; d++)
                 for (int i = 0; i < n[d]; i++) {
                   if (d < dim) {
-                    b[d][i] = or_bspline(i, P->p[d], P->U[d], xi[d]);
-                    db[d][i] = or_bspline_der(i, P->p[d], P->U[d], xi[d]);
+                    /* a periodic function is the sum of the unclamped B-splines whose
+                       index wraps onto it (Eq. map-wrap) */
+                    b[d][i] = db[d][i] = 0.0;
+                    for (int iu = i; iu < P->m[d] - P->p[d] - 1; iu += n[d]) {
+                      b[d][i] += or_bspline(iu, P->p[d], P->U[d], xi[d]);
+                      db[d][i] += or_bspline_der(iu, P->p[d], P->U[d], xi[d]);
+                      if (!P->wrap[d]) break;
+                    }
                   } else {
                     b[d][i] = 1.0;
                     db[d][i] = 0.0;

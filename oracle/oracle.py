@@ -16,6 +16,8 @@ passage of the PetIGA paper, cited where it is defined in ``iga_oracle.c``:
 * ``mass``/``residual_ts``/``jacobian_ts`` -- the semi-discrete time-dependent
   residual R(U-dot, U) of Sec. 4.2 for the transient Bratu problem, and its
   derivative dR/dU + shift dR/dU-dot.
+* ``unclamp_knots``           -- Sec. 2.4 Eqs. (unclamp-left)-(unclamp-right): the
+  knot vector of a periodic direction with continuity C^k across the boundary.
 * ``alpha_params``/``alpha_step`` -- one step of the generalized-alpha method for
   first-order systems, Sec. 4.2 Eq. (ga), parameters from rho_infinity.
 """
@@ -57,6 +59,7 @@ class _Problem(ctypes.Structure):
         ("bnd", (ctypes.c_int * 2) * 3),
         ("bval", (ctypes.c_double * 2) * 3),
         ("source", ctypes.c_int),
+        ("wrap", ctypes.c_int * 3),
     ]
 
 
@@ -128,6 +131,22 @@ def bspline_der(i, p, U, xi):
     return lib().or_bspline_der(i, p, _ptr(U), float(xi))
 
 
+def unclamp_knots(U, p, k):
+    """Sec. 2.4: redefine the k+1 end knots at each side of an open knot vector
+    (m = n + p + 1 its last index) so the space is C^k across the boundary:
+        xi_{k-i}   = xi_p - xi_{n+1} + xi_{n-i},       0 <= i <= k,
+        xi_{m-k+i} = xi_{n+1} - xi_p + xi_{p+i+1},     0 <= i <= k."""
+    X = np.array(U, dtype=np.float64)
+    m = len(X) - 1
+    n = m - p - 1
+    assert 0 <= k <= p - 1
+    for i in range(k + 1):
+        X[k - i] = X[p] - X[n + 1] + X[n - i]
+    for i in range(k + 1):
+        X[m - k + i] = X[n + 1] - X[p] + X[p + i + 1]
+    return X
+
+
 def stencil(i, p, U):
     U = np.ascontiguousarray(U, dtype=np.float64)
     l = ctypes.c_int()
@@ -142,17 +161,23 @@ class Problem:
     knots: list of per-direction knot vectors; degrees: list of p; quad: list of
     Gauss points per direction (default p+1); ctrl: (N, dim) control points or
     None (identity map); weights: (N,) or None; lam: lambda; log_kappa: (N,) or
-    None; dirichlet: dict {(axis, side): value}.
+    None; dirichlet: dict {(axis, side): value}; periodic: dict {axis: k}, the
+    open knot vector of that axis unclamped for C^k periodicity (Sec. 2.4), its
+    n - k functions numbered by Eq. (map-wrap).  ctrl, weights and log_kappa hold
+    one entry per (wrapped) function.
     """
 
     def __init__(self, knots, degrees, quad=None, ctrl=None, weights=None, lam=1.0,
-                 log_kappa=None, dirichlet=None, source=False):
+                 log_kappa=None, dirichlet=None, source=False, periodic=None):
         dim = len(knots)
         self.dim = dim
-        self.knots = [np.ascontiguousarray(k, dtype=np.float64) for k in knots]
+        self.periodic = dict(periodic or {})
+        self.wrap = [self.periodic[d] + 1 if d in self.periodic else 0 for d in range(dim)]
+        self.knots = [np.ascontiguousarray(unclamp_knots(k, p, self.periodic[d]) if d in self.periodic else k,
+                                           dtype=np.float64) for d, (k, p) in enumerate(zip(knots, degrees))]
         self.degrees = list(degrees)
         self.quad = list(quad) if quad is not None else [p + 1 for p in degrees]
-        self.n = [len(k) - p - 1 for k, p in zip(self.knots, self.degrees)]
+        self.n = [len(k) - p - 1 - w for k, p, w in zip(self.knots, self.degrees, self.wrap)]
         self.N = int(np.prod(self.n))
         self.ctrl = None if ctrl is None else np.ascontiguousarray(ctrl, dtype=np.float64).reshape(self.N, dim)
         self.weights = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64).reshape(self.N)
@@ -178,6 +203,8 @@ class Problem:
             s.bnd[ax][side] = 1
             s.bval[ax][side] = float(v)
         s.source = 1 if self.source else 0
+        for d in range(self.dim):
+            s.wrap[d] = self.wrap[d]
         return s
 
     # -- Sec. 2.5 Algorithm 2 -------------------------------------------------

@@ -541,3 +541,101 @@ def test_transient_jacobian_is_derivative_of_transient_residual():
         e[B] = eps
         col = (P.residual_ts(V + a * e, U + e) - P.residual_ts(V - a * e, U - e)) / (2 * eps)
         assert np.abs(col[free] - J[free, B]).max() < 1e-7 * max(1.0, np.abs(J).max()), B
+
+
+# ---------------------------------------------------- Sec. 2.4 periodic spaces
+
+def test_unclamped_knots_match_the_papers_figure():
+    """Eqs. (unclamp-left)-(unclamp-right) against the three knot vectors printed for
+    the C^0, C^1 and C^2 periodic cubic spaces (tests/golden/unclamp_fig.txt)."""
+    U = [0, 0, 0, 0, 0.2, 0.4, 0.6, 0.8, 1, 1, 1, 1]
+    rows = np.loadtxt(os.path.join(HERE, "golden", "unclamp_fig.txt"))
+    for row in rows:
+        k = int(row[0])
+        assert np.abs(O.unclamp_knots(U, 3, k) - row[1:]).max() < 1e-15, k
+
+
+PERIODIC = [  # (p, nel, {axis: k}), 2D unless nel has three entries
+    (2, (6, 5), {0: 1}),
+    (3, (7, 6), {0: 2, 1: 0}),
+    (3, (8, 5), {1: 1}),
+    (2, (5, 4, 4), {0: 1, 2: 0}),
+    (1, (6, 5), {0: 0}),
+]
+
+
+@pytest.mark.parametrize("case", PERIODIC)
+def test_periodic_assembly_equals_global_bruteforce(case):
+    """Element assembly with wrapped indices (Eq. map-wrap) against the dense brute
+    force that evaluates every periodic function as the sum of the unclamped B-splines
+    wrapping onto it; the wrapped BasisStencil pattern against element connectivity."""
+    p, nel, per = case
+    dim = len(nel)
+    kn = [O.open_uniform_knots(nel[d], p) for d in range(dim)]
+    P = O.Problem(kn, [p] * dim, lam=1.3, periodic=per)
+    rng = np.random.default_rng(5)
+    U = rng.uniform(-0.3, 0.3, P.N)
+    F, J = P.dense_bruteforce(U, fix=False)
+    assert np.abs(F - P.residual(U)).max() < 1e-14
+    assert np.abs(J - P.jacobian_csr(U).toarray()).max() < 1e-13
+    rowptr, colidx = P.pattern()
+    mark = P.pattern_dense_from_elements()
+    dense = np.zeros_like(mark)
+    for A in range(P.N):
+        dense[A, colidx[rowptr[A]:rowptr[A + 1]]] = 1
+        assert np.all(np.diff(colidx[rowptr[A]:rowptr[A + 1]]) > 0)
+    assert np.array_equal(dense, mark)
+
+
+def test_fully_periodic_space_reproduces_constants_and_is_shift_invariant():
+    """With both directions periodic the constant is in the space on every row (K 1 = 0),
+    the mass totals the area, and on a uniform mesh M and K commute with the shift of
+    the function index by one along x (circulant structure)."""
+    p, nel = 3, 7
+    kn = O.open_uniform_knots(nel, p)
+    P = O.Problem([kn, kn], [p, p], lam=0.0, periodic={0: p - 1, 1: p - 1})
+    K = P.jacobian_csr(np.zeros(P.N)).toarray()
+    M = P.mass_csr().toarray()
+    assert np.abs(K @ np.ones(P.N)).max() < 1e-13
+    assert abs(M.sum() - 1.0) < 1e-14
+    n0, n1 = P.n
+    idx = np.arange(P.N)
+    shift = ((idx % n0 + 1) % n0) + n0 * (idx // n0)
+    assert np.abs(M[np.ix_(shift, shift)] - M).max() < 1e-15
+    assert np.abs(K[np.ix_(shift, shift)] - K).max() < 1e-12
+
+
+def test_periodic_laplacian_eigenvalue_converges_at_order_2p():
+    """The lowest nonzero eigenvalue of -u'' = mu u on the periodic unit square is
+    (2 pi)^2; the discrete generalised eigenvalue of (K, M) converges as h^(2p)."""
+    import scipy.linalg as sla
+    errs = []
+    for nel in (6, 12):
+        kn = O.open_uniform_knots(nel, 2)
+        P = O.Problem([kn, kn], [2, 2], lam=0.0, periodic={0: 1, 1: 1})
+        K = P.jacobian_csr(np.zeros(P.N)).toarray()
+        M = P.mass_csr().toarray()
+        mu = sla.eigh(K, M, eigvals_only=True)
+        assert abs(mu[0]) < 1e-9
+        errs.append(mu[1] - (2 * math.pi) ** 2)
+    assert errs[0] > 0 and errs[1] > 0
+    assert abs(math.log2(errs[0] / errs[1]) - 4.0) < 0.3, errs
+
+
+def test_periodic_direction_with_x_independent_data_matches_natural_boundaries():
+    """Bratu periodic in x with Dirichlet faces in y: by the translation symmetry the
+    solution does not depend on x; so does the solution with natural (no) conditions on
+    the x faces, and the two coefficient profiles along y coincide."""
+    p, nel = 2, (6, 10)
+    kx, ky = O.open_uniform_knots(nel[0], p), O.open_uniform_knots(nel[1], p)
+    bc = {(1, 0): 0.0, (1, 1): 0.0}
+    Pp = O.Problem([kx, ky], [p, p], lam=1.5, dirichlet=bc, periodic={0: p - 1})
+    Pn = O.Problem([kx, ky], [p, p], lam=1.5, dirichlet=bc)
+    Up, hp = O.newton(Pp, np.zeros(Pp.N), atol=1e-12)
+    Un, hn = O.newton(Pn, np.zeros(Pn.N), atol=1e-12)
+    assert hp[-1] <= 1e-12 and hn[-1] <= 1e-12
+    Up = Up.reshape(Pp.n[1], Pp.n[0])
+    Un = Un.reshape(Pn.n[1], Pn.n[0])
+    assert np.abs(Up - Up[:, :1]).max() < 1e-13
+    assert np.abs(Un - Un[:, :1]).max() < 1e-12
+    assert np.abs(Up[:, 0] - Un[:, 0]).max() < 1e-12
