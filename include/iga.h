@@ -80,7 +80,19 @@ typedef enum {
  *                 Sec. 5 and App. C); only p+1 is supported.
  *  ctrl           host array N*dim of physical control points (natural order,
  *                 coordinates contiguous), or NULL for the identity map x = xi.
- *  weights        host array N of rational weights, or NULL for all ones. */
+ *  weights        host array N of rational weights, or NULL for all ones.
+ *  periodic[d]    0: not periodic.  k+1 (1..p): direction d is periodic with C^k
+ *                 continuity across the boundary (Sec. 2.4): its open knot vector
+ *                 (explicit or uniform) is unclamped by Eqs. (unclamp-left) and
+ *                 (unclamp-right), the k+1 redundant functions are eliminated and
+ *                 every function index wraps as mod(i, n-k) (Eq. map-wrap), so the
+ *                 direction has n-k functions; needs n-k >= k+1.  N, ctrl, weights
+ *                 and log-kappa count the wrapped functions only.  A periodic axis
+ *                 takes no Dirichlet value; the pattern stays Algorithm 2's with
+ *                 wrapped columns, ascending in each row.  Periodic handles assemble
+ *                 the FP64 and FP32 Jacobians (IGA_FP64, IGA_JAC_FP32) and solve with
+ *                 them; the element-matrix, matrix-free and no-allocation entry
+ *                 points return IGA_EINVAL. */
 typedef struct {
   int dim;
   int degree[3];
@@ -91,6 +103,7 @@ typedef struct {
   int quad[3];
   const double *ctrl;
   const double *weights;
+  int periodic[3];
 } iga_desc;
 
 /* Problem parameters: lambda of Eq. (strong), and an optional host array of N
@@ -115,7 +128,7 @@ iga_status iga_create(const iga_desc *desc, const iga_bratu *bratu, void *stream
  * boundary control variables become F_A = U_A - value and identity rows of the
  * Jacobian, with the column zeroed in the other rows (symmetric form).  When
  * faces meet, the face set later in the order (axis 0 side 0, axis 0 side 1,
- * axis 1 side 0, ...) gives the value. */
+ * axis 1 side 0, ...) gives the value.  A periodic axis has no faces: IGA_EINVAL. */
 iga_status iga_set_boundary_value(iga_t iga, int axis, int side, double value);
 
 /* Change lambda after creation (used by the batched and learned-start drivers). */

@@ -38,7 +38,8 @@ static void free_dir(DirDev &d) {
   memset(&d, 0, sizeof d);
 }
 
-static void release(iga_s *h) {
+void iga_release(iga_s *h) {
+  periodic_release(h);
   for (int ax = 0; ax < 3; ax++) free_dir(h->ddev[ax]);
   void *ps[] = {h->rowptr, h->colidx, h->weights, h->geom, h->Fe, h->Q00, h->T1, h->T2, h->Kstiff, h->Kstiff_f, h->Ebuf64, h->ts_buf,
                 h->Mred, h->Mred_f, h->J64, h->J32, h->wk, h->V, h->red, h->ctl, h->Uhost_dev,
@@ -79,7 +80,7 @@ static iga_status upload_dir(iga_s *h, int ax) {
   return IGA_OK;
 }
 
-static iga_status create_impl(iga_s *h, const iga_desc *d, const iga_bratu *b) {
+iga_status iga_create_impl(iga_s *h, const iga_desc *d, const iga_bratu *b) {
   iga_status st = iga_build_dirs(h, d);
   if (st != IGA_OK) return st;
   h->lambda = b ? b->lambda : 0.0;
@@ -170,10 +171,11 @@ extern "C" iga_status iga_create(const iga_desc *d, const iga_bratu *b, void *st
   }
   iga_s *h = new iga_s();
   h->stream = (cudaStream_t)stream;
-  iga_status st = create_impl(h, d, b);
+  const bool periodic = d->periodic[0] || d->periodic[1] || (d->dim == 3 && d->periodic[2]);
+  iga_status st = periodic ? iga_periodic_setup(h, d, b) : iga_create_impl(h, d, b);
   if (st != IGA_OK) {
     g_create_err = h->err;
-    release(h);
+    iga_release(h);
     delete h;
     return st;
   }
@@ -184,7 +186,7 @@ extern "C" iga_status iga_create(const iga_desc *d, const iga_bratu *b, void *st
 extern "C" void iga_destroy(iga_t h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
-  release(h);
+  iga_release(h);
   delete h;
 }
 
@@ -197,6 +199,10 @@ extern "C" iga_status iga_set_boundary_value(iga_t h, int axis, int side, double
   if (!h) return IGA_EINVAL;
   if (axis < 0 || axis >= h->dim || side < 0 || side > 1 || !isfinite(value)) {
     h->err = iga_format("bad boundary (axis %d, side %d)", axis, side);
+    return IGA_EINVAL;
+  }
+  if (h->inner && h->per_host[axis].n != h->per_host[axis].nu) {
+    h->err = iga_format("axis %d is periodic: it has no Dirichlet faces", axis);
     return IGA_EINVAL;
   }
   h->bnd.flag[axis][side] = 1;
@@ -241,6 +247,10 @@ extern "C" iga_status iga_form_jacobian(iga_t h, const double *U, void *vals, ig
   } else if (prec == IGA_JAC_FP32) {
     CK(launch_jacobian32(h, U, (float *)vals, 0, nullptr));
   } else if (prec == IGA_JAC_TF32 || prec == IGA_JAC_BF16 || prec == IGA_JAC_FD) {
+    if (h->inner) {
+      h->err = "periodic handles assemble the IGA_FP64 and IGA_JAC_FP32 Jacobians only";
+      return IGA_EINVAL;
+    }
     if (!mixed_supported(h->dim, h->p)) {
       h->err = iga_format("element-matrix Jacobians support p <= %d in %dD", h->dim == 3 ? 3 : 4, h->dim);
       return IGA_EINVAL;
@@ -277,6 +287,10 @@ extern "C" iga_status iga_apply_jacobian_mf(iga_t h, const double *U, const doub
     h->err = "U, x and y must be non-NULL device pointers, x != y";
     return IGA_EINVAL;
   }
+  if (h->inner) {
+    h->err = "matrix-free products are not available on periodic handles";
+    return IGA_EINVAL;
+  }
   CK(launch_q00(h, U, 0.0, 1.0));
   h->q00_valid = false;
   CK(launch_jv(h, x, y, nullptr));
@@ -287,6 +301,10 @@ extern "C" iga_status iga_form_jacobian_diagonal(iga_t h, const double *U, doubl
   if (!h) return IGA_EINVAL;
   if (!U || !d) {
     h->err = "U and d must be non-NULL device pointers";
+    return IGA_EINVAL;
+  }
+  if (h->inner) {
+    h->err = "the element-wise diagonal is not available on periodic handles";
     return IGA_EINVAL;
   }
   CK(launch_q00(h, U, 0.0, 1.0));
@@ -350,6 +368,7 @@ static iga_status norm_host(iga_s *h, const double *x, double *out) {
 
 // Assemble the Newton Jacobian at U into h->J64 / h->J32.
 static iga_status newton_jacobian(iga_s *h, const double *U, bool f32, bool reuse, int prec) {
+  if (h->inner) reuse = false;  // periodic: full assembly on the unwrapped space, then the fold
   if (prec == IGA_JAC_FD) {  // local numerical differentiation, assembled in full each step
     CK(launch_jacobian_fd(h, U, h->J64));
     return IGA_OK;
@@ -385,6 +404,10 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
     h->err = "element-matrix Jacobian not supported for this degree";
     return IGA_EINVAL;
   }
+  if (h->inner && o.jac != IGA_FP64 && o.jac != IGA_JAC_FP32) {
+    h->err = "periodic handles solve with the IGA_FP64 or IGA_JAC_FP32 Jacobian";
+    return IGA_EINVAL;
+  }
   if (!U || o.gmres_restart < 1 || o.gmres_restart > 1000 || o.max_newton < 0 || !(o.atol >= 0.0) ||
       (o.jac != IGA_FP64 && o.jac != IGA_JAC_TF32 && o.jac != IGA_JAC_BF16 && o.jac != IGA_JAC_FP32 &&
        o.jac != IGA_JAC_NONE && o.jac != IGA_JAC_FD)) {
@@ -397,7 +420,7 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
   const bool mf = o.jac == IGA_JAC_NONE;  // matrix-free
   const bool fd = o.jac == IGA_JAC_FD;    // FP64 values by numerical differentiation
   const bool f32 = !mf && !fd && o.jac != IGA_FP64;
-  const bool split = !f32 && !mf && !fd && o.reuse_stiffness != 0;
+  const bool split = !f32 && !mf && !fd && o.reuse_stiffness != 0 && !h->inner;
   iga_status st = ensure_workspace(h, o.gmres_restart, f32, mf);
   if (st != IGA_OK) return st;
   const int64_t N = h->N;
@@ -563,8 +586,8 @@ extern "C" iga_status iga_ts_alpha_step(iga_t h, const iga_ts_opts *ts, double *
   iga_newton_opts o;
   iga_newton_defaults(&o);
   if (opts) o = *opts;
-  if (o.jac != IGA_FP64 && o.jac != IGA_JAC_FP32 && o.jac != IGA_JAC_NONE) {
-    h->err = "time steps support the IGA_FP64, IGA_JAC_FP32 and IGA_JAC_NONE Jacobians";
+  if (o.jac != IGA_FP64 && o.jac != IGA_JAC_FP32 && (o.jac != IGA_JAC_NONE || h->inner)) {
+    h->err = "time steps support the IGA_FP64, IGA_JAC_FP32 and (not periodic) IGA_JAC_NONE Jacobians";
     return IGA_EINVAL;
   }
   // Sec. 4.2: parameters from rho_inf; with W = U_{n+alpha_f} the unknown,
@@ -643,20 +666,27 @@ extern "C" iga_status iga_profile_enable(iga_t h, unsigned mask) {
   if (!h) return IGA_EINVAL;
   prof_drain(h);
   h->prof.mask = mask;
+  if (h->inner) {  // a periodic handle's element kernels run on its inner handle
+    prof_drain(h->inner);
+    h->inner->prof.mask = mask;
+  }
   return IGA_OK;
 }
 
 extern "C" iga_status iga_profile_read(iga_t h, iga_profile *out) {
   if (!h || !out) return IGA_EINVAL;
-  prof_drain(h);
   memset(out, 0, sizeof *out);
-  for (int c = 0; c < KC_N; c++) {
-    out->ms[c] = h->prof.ms[c];
-    out->timed[c] = h->prof.timed[c];
-    out->launches[c] = h->prof.launches[c];
-    h->prof.ms[c] = 0.0;
-    h->prof.timed[c] = 0;
-    h->prof.launches[c] = 0;
+  for (iga_s *x : {h, h->inner}) {
+    if (!x) continue;
+    prof_drain(x);
+    for (int c = 0; c < KC_N; c++) {
+      out->ms[c] += x->prof.ms[c];
+      out->timed[c] += x->prof.timed[c];
+      out->launches[c] += x->prof.launches[c];
+      x->prof.ms[c] = 0.0;
+      x->prof.timed[c] = 0;
+      x->prof.launches[c] = 0;
+    }
   }
   return IGA_OK;
 }

@@ -706,8 +706,9 @@ static iga_status batch_create_impl(iga_batch_s *b, int count, const iga_desc *d
   std::vector<int> mi(count);
   for (int i = 0; i < count; i++) {
     const iga_desc &d = descs[i];
-    if (d.dim != 2 || d.ctrl || d.weights || d.degree[0] != d.degree[1] || d.degree[0] < 1 || d.degree[0] > 3) {
-      b->err = iga_format("instance %d: batched instances are 2D, identity map, unit weights, p = 1..3", i);
+    if (d.dim != 2 || d.ctrl || d.weights || d.degree[0] != d.degree[1] || d.degree[0] < 1 || d.degree[0] > 3 ||
+        d.periodic[0] || d.periodic[1]) {
+      b->err = iga_format("instance %d: batched instances are 2D, identity map, unit weights, p = 1..3, not periodic", i);
       return IGA_EINVAL;
     }
     if (!isfinite(params[i].lambda)) {

@@ -721,6 +721,7 @@ static cudaError_t launch_rate_term(iga_s *h, const double *U, double *Fe) {
 }
 
 cudaError_t launch_residual(iga_s *h, const double *U, double *F) {
+  if (h->inner) return periodic_residual(h, U, F);
   DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
   constexpr int NE = 4;
   unsigned grid = (unsigned)((h->nelem + NE - 1) / NE);

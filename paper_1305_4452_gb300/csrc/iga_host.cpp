@@ -116,17 +116,17 @@ static void basis_stencil(const std::vector<double> &U, int p, int i, int *l, in
   *r = j - 1;
 }
 
-static iga_status build_dir(iga_s *h, const iga_desc *d, int ax, Dir &D) {
-  int p = d->degree[ax];
-  D.p = p;
-  D.q = p + 1;
+// The knot vector of direction ax: explicit, or uniform open on [0, 1] with nel
+// elements and interior knots repeated p-k times (continuity C^k).
+iga_status iga_open_knots(iga_s *h, const iga_desc *d, int ax, std::vector<double> &U) {
+  const int p = d->degree[ax];
   if (d->knots[ax]) {
     int m = d->nknots[ax];
     if (m < 2 * p + 2) {
       h->err = iga_format("axis %d: %d knots is too few for degree %d", ax, m, p);
       return IGA_EINVAL;
     }
-    D.knots.assign(d->knots[ax], d->knots[ax] + m);
+    U.assign(d->knots[ax], d->knots[ax] + m);
   } else {
     int nel = d->nel[ax], k = d->continuity[ax];
     if (k < 0) k = p - 1;
@@ -134,11 +134,41 @@ static iga_status build_dir(iga_s *h, const iga_desc *d, int ax, Dir &D) {
       h->err = iga_format("axis %d: bad nel=%d or continuity=%d", ax, nel, k);
       return IGA_EINVAL;
     }
-    D.knots.assign(p + 1, 0.0);
+    U.assign(p + 1, 0.0);
     for (int e = 1; e < nel; e++)
-      for (int r = 0; r < p - k; r++) D.knots.push_back((double)e / (double)nel);
-    for (int r = 0; r <= p; r++) D.knots.push_back(1.0);
+      for (int r = 0; r < p - k; r++) U.push_back((double)e / (double)nel);
+    for (int r = 0; r <= p; r++) U.push_back(1.0);
   }
+  return IGA_OK;
+}
+
+// Sec. 2.4, Eqs. (unclamp-left)-(unclamp-right): with m the last knot index and
+// n = m - p - 1, the k+1 knots at each end are redefined from the other end,
+//   U[k-i] = U[p] - U[n+1] + U[n-i],  U[m-k+i] = U[n+1] - U[p] + U[p+i+1],  0 <= i <= k.
+// The two sides read only knots neither side writes when n - k >= k + 1.
+iga_status iga_unclamp(iga_s *h, int ax, int p, int k, std::vector<double> &U) {
+  const int m = (int)U.size() - 1, n = m - p - 1;
+  if (k < 0 || k > p - 1 || n - k < k + 1) {
+    h->err = iga_format("axis %d: cannot unclamp for C^%d periodicity (degree %d, %d functions)", ax, k, p, n + 1);
+    return IGA_EINVAL;
+  }
+  for (int k2 = 1; k2 <= p; k2++)
+    if (U[k2] != U[0] || U[m - k2] != U[m]) {
+      h->err = iga_format("axis %d: a periodic direction starts from an open knot vector", ax);
+      return IGA_EINVAL;
+    }
+  const double lo = U[p], hi = U[n + 1];
+  for (int i = 0; i <= k; i++) U[k - i] = lo - hi + U[n - i];
+  for (int i = 0; i <= k; i++) U[m - k + i] = hi - lo + U[p + i + 1];
+  return IGA_OK;
+}
+
+static iga_status build_dir(iga_s *h, const iga_desc *d, int ax, Dir &D) {
+  int p = d->degree[ax];
+  D.p = p;
+  D.q = p + 1;
+  iga_status kst = iga_open_knots(h, d, ax, D.knots);
+  if (kst != IGA_OK) return kst;
   const std::vector<double> &U = D.knots;
   int m = (int)U.size();
   for (int k = 0; k + 1 < m; k++)
@@ -146,7 +176,7 @@ static iga_status build_dir(iga_s *h, const iga_desc *d, int ax, Dir &D) {
       h->err = iga_format("axis %d: knots must be finite and non-decreasing", ax);
       return IGA_EINVAL;
     }
-  for (int k = 1; k <= p; k++)
+  for (int k = 1; k <= p && !h->unclamped; k++)
     if (U[k] != U[0] || U[m - 1 - k] != U[m - 1]) {
       h->err = iga_format("axis %d: knot vector must be open (p+1 repeated end knots)", ax);
       return IGA_EINVAL;
@@ -215,7 +245,16 @@ static iga_status build_dir(iga_s *h, const iga_desc *d, int ax, Dir &D) {
   D.pair_po.clear();
   D.pair_val.clear();
   for (int i = 0; i < D.n; i++) {
-    basis_stencil(U, p, i, &D.l[i], &D.r[i]);
+    if (h->unclamped) {
+      // the unwrapped space of a periodic direction: supports reach past the domain,
+      // so the range is that of the functions sharing one of i's elements (equal to
+      // BasisStencil's on an open knot vector)
+      const int ea = D.node_e0[i], eb = D.node_e0[i] + D.node_ne[i] - 1;
+      D.l[i] = D.first[ea];
+      D.r[i] = D.first[eb] + p;
+    } else {
+      basis_stencil(U, p, i, &D.l[i], &D.r[i]);
+    }
     D.pair_off[i] = (int)D.pair_j.size();
     for (int j = D.l[i]; j <= D.r[i]; j++) {
       int e0 = std::max(D.node_e0[i], D.node_e0[j]);

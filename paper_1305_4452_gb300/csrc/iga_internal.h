@@ -90,6 +90,29 @@ struct BndArgs {
   double val[3][2];
 };
 
+// Periodic directions (Sec. 2.4).  A periodic handle assembles on the unclamped
+// space of its inner handle (every unwrapped function kept, no index wrap, no
+// Dirichlet rows) and maps between the two numberings: U is prolonged to the
+// unwrapped functions, residual rows and Jacobian entries of the unwrapped
+// functions whose indices wrap (Eq. map-wrap) onto the same function are summed.
+// Per direction, for the outer (wrapped) functions i in [0, n) and the inner
+// (unwrapped) functions i' in [0, nu):
+struct PerAxisHost {
+  int n = 1, nu = 1;
+  std::vector<int> wrap;              // [nu] outer index of i'
+  std::vector<int> img_off, img;      // images of i: img[img_off[i] .. img_off[i+1])
+  std::vector<int> col_off, col;      // sorted wrapped columns of row i: col[col_off[i] .. col_off[i+1])
+  std::vector<int> con_off, con_row, con_pos;  // per column slot: unwrapped (i', position in row i') pairs
+  std::vector<int> ulen;              // [nu] length of the unwrapped row i'
+};
+struct PerAxis {  // device copy, passed by value
+  int n, nu;
+  const int *wrap, *img_off, *img, *col_off, *col, *con_off, *con_row, *con_pos, *ulen;
+};
+struct PerArgs {
+  PerAxis ax[3];
+};
+
 // Kernel classes for launch counting and event timing (iga_profile_*).
 enum KClass {
   KC_GEOM = 0, KC_RES_ELEM, KC_RES_GATHER, KC_Q00, KC_STAGE1, KC_STAGE2, KC_FINAL, KC_SPMV, KC_ORTH,
@@ -155,6 +178,14 @@ struct iga_s {
   double ts_a = 0.0;
   const double *ts_C = nullptr;
   double *ts_buf = nullptr;    // generalized-alpha workspace: C and U_n (2 N doubles)
+  // periodic handles (Sec. 2.4): the unwrapped discretisation and the maps to it
+  bool unclamped = false;      // inner handle: knots need not be open; stencils from elements
+  iga_s *inner = nullptr;      // set on a periodic handle
+  PerAxisHost per_host[3];
+  PerArgs per{};
+  std::vector<void *> per_bufs;  // device copies of the per-axis tables
+  double *Uu = nullptr, *Fu = nullptr, *Cu = nullptr, *Ju = nullptr;  // unwrapped U, F, rate data, Jacobian
+  float *Ju32 = nullptr;
   double *Uhost_dev = nullptr; // device copy of U for the host-buffer solve
   // mixed-precision Jacobian (tensor cores)
   float *geom32 = nullptr;     // [nelem][slots][nq] FP32 geometry factors
@@ -176,6 +207,10 @@ struct iga_s {
 
 // ---- host set-up (iga_host.cpp) ----
 iga_status iga_build_dirs(iga_s *h, const iga_desc *d);
+// The open knot vector of direction ax as iga_create builds it (explicit or uniform)
+iga_status iga_open_knots(iga_s *h, const iga_desc *d, int ax, std::vector<double> &U);
+// Eqs. (unclamp-left)-(unclamp-right): unclamp an open knot vector for C^k periodicity
+iga_status iga_unclamp(iga_s *h, int ax, int p, int k, std::vector<double> &U);
 void iga_rowptr(const iga_s *h, std::vector<int64_t> &rowptr);
 
 // ---- element kernels (iga_element.cu) ----
@@ -194,9 +229,23 @@ cudaError_t launch_jacobian_diagonal(iga_s *h, double *diag);
 // reaction part of Q00 at U in h->Q00 (see iga_s::q00_valid).
 cudaError_t launch_residual_split(iga_s *h, const double *U, double *F, const double *K, double *KU);
 
+// ---- periodic handles (iga_periodic.cu) ----
+iga_status iga_periodic_setup(iga_s *h, const iga_desc *d, const iga_bratu *b);
+cudaError_t periodic_residual(iga_s *h, const double *U, double *F);
+cudaError_t periodic_jacobian64(iga_s *h, const double *U, double *vals);
+cudaError_t periodic_jacobian32(iga_s *h, const double *U, float *vals);
+// y = J x on the wrapped CSR pattern (FP64 or FP32 values, FP64 x, y and sums); done may be null
+cudaError_t periodic_spmv(iga_s *h, const void *vals, int is_f32, const double *x, double *y, const double *done);
+cudaError_t periodic_diag_inv(iga_s *h, const void *vals, int is_f32, double *dinv);
+void periodic_release(iga_s *h);
+// Creation and release of an ordinary (non-periodic or inner) handle (iga_api.cu)
+iga_status iga_create_impl(iga_s *h, const iga_desc *d, const iga_bratu *b);
+void iga_release(iga_s *h);
+
 // ---- Jacobian stages (iga_jacobian.cu) ----
 // mode 0: full Jacobian; 1: stiffness only (U-independent), without the Dirichlet
-// fix; 2: vals = base + reaction(U) with the Dirichlet fix (base from mode 1)
+// fix; 2: vals = base + reaction(U) with the Dirichlet fix (base from mode 1);
+// 3: full Jacobian without the Dirichlet fix
 cudaError_t launch_jacobian64(iga_s *h, const double *U, double *vals, int mode, const double *base);
 cudaError_t launch_jacobian32(iga_s *h, const double *U, float *vals, int mode, const float *base);
 size_t jacobian_t1_groups(int dim);

@@ -351,6 +351,7 @@ template <typename T, typename V>
 cudaError_t jacobian(iga_s *h, const double *U, V *vals, int mode, const V *base) {
   // mode 0: full, Dirichlet-fixed; 1: stiffness only (U-independent), unfixed;
   // 2: base (a mode-1 stiffness) + reaction, Dirichlet-fixed
+  // 3: full, without the Dirichlet fix (the unwrapped space of a periodic handle)
   double cs = (mode == 2) ? 0.0 : 1.0, cr = (mode == 1) ? 0.0 : 1.0;
   // mode 2 after an accepted split-residual evaluation at this U: Q00 is already there
   if (!(mode == 2 && h->q00_valid)) {
@@ -362,7 +363,7 @@ cudaError_t jacobian(iga_s *h, const double *U, V *vals, int mode, const V *base
     if (!base) return cudaErrorInvalidValue;
     return h->dim == 3 ? run_stages<T, V, 3, PLAN_MASS>(h, vals, base, 1) : run_stages<T, V, 2, PLAN_MASS>(h, vals, base, 1);
   }
-  const int fix = (mode == 1) ? 0 : 1;
+  const int fix = (mode == 1 || mode == 3) ? 0 : 1;
   return h->dim == 3 ? run_stages<T, V, 3, PLAN_STIFF>(h, vals, nullptr, fix) : run_stages<T, V, 2, PLAN_STIFF>(h, vals, nullptr, fix);
 }
 
@@ -372,9 +373,11 @@ size_t jacobian_t1_groups(int dim) { return dim == 3 ? 6 : 3; }
 size_t jacobian_t2_groups(int dim) { return dim == 3 ? 3 : 0; }
 
 cudaError_t launch_jacobian64(iga_s *h, const double *U, double *vals, int mode, const double *base) {
+  if (h->inner) return mode == 0 ? periodic_jacobian64(h, U, vals) : cudaErrorInvalidValue;
   return jacobian<double, double>(h, U, vals, mode, base);
 }
 
 cudaError_t launch_jacobian32(iga_s *h, const double *U, float *vals, int mode, const float *base) {
+  if (h->inner) return mode == 0 ? periodic_jacobian32(h, U, vals) : cudaErrorInvalidValue;
   return jacobian<float, float>(h, U, vals, mode, base);
 }

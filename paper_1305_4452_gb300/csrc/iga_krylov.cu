@@ -475,6 +475,7 @@ static StencilRows stencil_rows(const iga_s *h) {
 // FP32-value operator product used by the mixed-precision Newton: x -> FP32 copy,
 // FP32 SpMV (8 lanes x 4 B = one 32 B sector per row and step)
 static cudaError_t spmv_f32_launch(iga_s *h, const float *vals, const double *x, double *y, const double *done) {
+  if (h->inner) return periodic_spmv(h, vals, 1, x, y, done);
   int eg = (int)((h->N + 255) / 256);
   if (eg > 608) eg = 608;
   IGA_LAUNCH(h, KC_VEC, (k_cvt_f32<<<eg, 256, 0, h->stream>>>(x, h->z32, h->N, done)));
@@ -493,6 +494,7 @@ static cudaError_t spmv_launch(iga_s *h, const V *vals, const double *x, double 
   // Few lanes per row: the cross-lane reduction costs log2(LPR) FP64 adds on every
   // lane of the group, which on GB300's narrow FP64 pipe is not free; 4 lanes keep
   // the loads sector-efficient (4 x 8 B contiguous per row and step).
+  if (h->inner) return periodic_spmv(h, vals, sizeof(V) == 4, x, y, done);
   const StencilRows S = stencil_rows(h);
   const int N = (int)h->N;
   unsigned grid = (unsigned)(((int64_t)N * 4 + 255) / 256);
@@ -507,6 +509,7 @@ cudaError_t launch_spmv64(iga_s *h, const double *vals, const double *x, double 
 cudaError_t launch_spmv32(iga_s *h, const float *vals, const double *x, double *y) { return spmv_launch<float>(h, vals, x, y, nullptr); }
 
 cudaError_t launch_diag_inv(iga_s *h, const void *vals, int is_f32, double *dinv) {
+  if (h->inner) return periodic_diag_inv(h, vals, is_f32, dinv);
   const StencilRows S = stencil_rows(h);
   const int N = (int)h->N;
   unsigned g = (unsigned)((N + 255) / 256);

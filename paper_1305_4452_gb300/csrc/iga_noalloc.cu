@@ -56,6 +56,10 @@ extern "C" iga_status iga_form_residual_noalloc(iga_t h, const double *U, double
     h->err = "U and F must be distinct non-NULL device pointers";
     return IGA_EINVAL;
   }
+  if (h->inner) {
+    h->err = "periodic handles have no allocation-free residual";
+    return IGA_EINVAL;
+  }
   int nen = (h->dim == 3) ? (h->p + 1) * (h->p + 1) * (h->p + 1) : (h->p + 1) * (h->p + 1);
   unsigned long long need = (unsigned long long)h->nelem * (unsigned long long)nen;
   if (need > (unsigned long long)IGA_NOALLOC_MAX_ELEMENT_VALUES) {

@@ -42,6 +42,7 @@ class IgaDesc(ctypes.Structure):
         ("quad", ctypes.c_int * 3),
         ("ctrl", ctypes.c_void_p),
         ("weights", ctypes.c_void_p),
+        ("periodic", ctypes.c_int * 3),
     ]
 
 
@@ -157,14 +158,18 @@ class Discretization:
     """An iga_t handle: a scalar Bratu problem on a tensor-product NURBS space.
 
     knots: per-direction knot vectors (None: uniform from nel/continuity);
-    ctrl (N, dim) / weights (N,) / log_kappa (N,) host arrays or None.
+    ctrl (N, dim) / weights (N,) / log_kappa (N,) host arrays or None;
+    periodic: {axis: k}, C^k periodic directions (Sec. 2.4; open knots unclamped by
+    the library, N counting the wrapped functions).
     """
 
     def __init__(self, dim, degree, nel=None, continuity=None, knots=None, ctrl=None, weights=None, lam=1.0,
-                 log_kappa=None, dirichlet=None, stream=None):
+                 log_kappa=None, dirichlet=None, stream=None, periodic=None):
         d = IgaDesc()
         d.dim = dim
         self._keep = []
+        for ax, k in (periodic or {}).items():
+            d.periodic[ax] = int(k) + 1
         for ax in range(dim):
             d.degree[ax] = degree if np.isscalar(degree) else degree[ax]
             d.continuity[ax] = -1 if continuity is None else (continuity if np.isscalar(continuity) else continuity[ax])

@@ -497,3 +497,119 @@ def test_alpha_step_rejects_bad_input_and_keeps_state():
     assert rep.status != 0
     assert torch.equal(U, U_before) and torch.count_nonzero(V).item() == 0
     disc.close()
+
+
+# ---------------------------------------------------- Sec. 2.4 periodic spaces
+
+PER_CASES = [
+    # (dim, p, nel, interior k, periodic {axis: k}, rational weights, kappa seed)
+    (2, 2, (9, 7), None, {0: 1}, False, None),
+    (2, 3, (7, 8), None, {0: 2, 1: 0}, False, None),   # no Dirichlet face at all
+    (2, 2, (8, 9), None, {1: 1}, True, None),          # rational basis, identity map
+    (2, 2, (9, 7), None, {0: 1}, False, 3),            # kappa-weighted
+    (2, 3, (4, 5), None, {0: 2}, False, None),         # n - k = 4 < 2p + 1: columns wrap onto themselves
+    (2, 1, (6, 5), None, {0: 0}, False, None),
+    (2, 3, (6, 5), 1, {0: 1}, False, None),            # C^1 inside, C^1 across the boundary
+    (3, 2, (5, 4, 4), None, {0: 1, 2: 0}, False, None),
+    (3, 3, (6, 5, 4), None, {1: 2}, True, None),
+]
+
+
+def make_periodic_pair(dim, p, nel, k, per, rational, kappa_seed, lam=1.3):
+    I = iga()
+    knots = [W.uniform_open_knots(nel[d], p, k) for d in range(dim)]
+    bc = {(a, s): 0.0 for a in range(dim) if a not in per for s in range(2)}
+    prob = O.Problem(knots, [p] * dim, lam=lam, dirichlet=bc, periodic=per)
+    weights = W.uniform(7, prob.N, 0.8, 1.2) if rational else None
+    lk = W.uniform(kappa_seed, prob.N, -0.5, 0.5) if kappa_seed is not None else None
+    prob = O.Problem(knots, [p] * dim, lam=lam, dirichlet=bc, periodic=per, weights=weights, log_kappa=lk)
+    disc = I.Discretization(dim, p, knots=knots, lam=lam, dirichlet=bc, periodic=per, weights=weights, log_kappa=lk)
+    return disc, prob
+
+
+@pytest.mark.parametrize("case", PER_CASES, ids=lambda c: "d%dp%d_%s_k%s_%s_w%d_kap%s" % (
+    c[0], c[1], "x".join(map(str, c[2])), c[3], "".join("%d%d" % kv for kv in c[4].items()), c[5], c[6]))
+def test_periodic_pattern_residual_jacobian_match_the_oracle(case):
+    disc, prob = make_periodic_pair(*case)
+    assert disc.N == prob.N
+    rng = np.random.default_rng(13)
+    U0 = np.where(prob.dirichlet_mask(), 0.0, rng.uniform(-0.3, 0.3, prob.N))
+    U = torch.tensor(U0, device="cuda")
+    rp, ci = disc.pattern()
+    rpo, cio = prob.pattern()
+    assert np.array_equal(rp.cpu().numpy(), rpo) and np.array_equal(ci.cpu().numpy(), cio)
+    F = disc.form_residual(U).cpu().numpy()
+    assert rel(F, prob.residual(U0)) <= TOL, rel(F, prob.residual(U0))
+    J = disc.form_jacobian(U)
+    Jo = prob.jacobian(U0)
+    assert rel(J.cpu().numpy(), Jo) <= TOL, rel(J.cpu().numpy(), Jo)
+    J32 = disc.form_jacobian(U, prec=iga().IGA_JAC_FP32).cpu().numpy().astype(np.float64)
+    assert rel(J32, Jo) <= 1e-5
+    x0 = rng.uniform(-1, 1, prob.N)
+    y = disc.apply_jacobian(J, torch.tensor(x0, device="cuda")).cpu().numpy()
+    Jc = prob.jacobian_csr(U0)
+    yo = Jc @ x0
+    assert np.all(np.abs(y - yo) <= 1e-13 * (abs(Jc) @ np.abs(x0)))
+    V0 = rng.uniform(-1, 1, prob.N)
+    Fts = disc.form_residual_ts(torch.tensor(V0, device="cuda"), U).cpu().numpy()
+    assert rel(Fts, prob.residual_ts(V0, U0)) <= TOL
+    Jts = disc.form_jacobian_ts(21.0, U).cpu().numpy()
+    assert rel(Jts, prob.jacobian_ts(21.0, U0)) <= TOL
+    disc.close()
+
+
+@pytest.mark.parametrize("jac", ["fp64_gmres", "fp32_cg"])
+def test_periodic_newton_reaches_the_oracle_solution(jac):
+    I = iga()
+    disc, prob = make_periodic_pair(2, 2, (12, 10), None, {0: 1}, False, None, lam=1.5)
+    U = torch.zeros(disc.N, dtype=torch.float64, device="cuda")
+    o = I.newton_defaults()
+    if jac == "fp32_cg":
+        o.jac, o.ksp = I.IGA_JAC_FP32, I.IGA_KSP_CG
+    rep = disc.solve_newton(U, o)
+    assert rep.status == 0 and rep.fnorm <= 1e-10
+    Ug = U.cpu().numpy()
+    assert np.linalg.norm(prob.residual(Ug)) <= 1e-10 * (1 + 1e-12)
+    Uo, hist = O.newton(prob, np.zeros(prob.N), atol=1e-12)
+    assert np.abs(Ug - Uo).max() <= 1e-8
+    disc.close()
+
+
+def test_periodic_alpha_step_matches_the_oracle():
+    I = iga()
+    disc, prob = make_periodic_pair(3, 2, (5, 4, 6), None, {0: 1, 1: 1}, False, None, lam=1.0)
+    rng = np.random.default_rng(17)
+    U0 = np.where(prob.dirichlet_mask(), 0.0, rng.uniform(-0.2, 0.2, prob.N))
+    V0 = np.zeros(prob.N)
+    U = torch.tensor(U0, device="cuda")
+    V = torch.tensor(V0, device="cuda")
+    o = I.newton_defaults()
+    o.atol = 1e-12
+    rep = disc.ts_alpha_step(U, V, 0.03, 0.5, o)
+    assert rep.status == 0
+    Uo, Vo, _ = O.alpha_step(prob, U0, V0, 0.03, 0.5, atol=1e-13)
+    Ug, Vg = U.cpu().numpy(), V.cpu().numpy()
+    assert np.linalg.norm(_stage_residual(prob, U0, V0, Ug, Vg, 0.03, 0.5)) <= 2e-12
+    assert np.abs(Ug - Uo).max() <= 1e-9 * np.abs(Uo).max()
+    assert np.abs(Vg - Vo).max() <= 1e-7 * np.abs(Vo).max()
+    disc.close()
+
+
+def test_periodic_rejections():
+    I = iga()
+    disc, prob = make_periodic_pair(2, 2, (6, 5), None, {0: 1}, False, None)
+    with pytest.raises(I.IgaError):
+        I._check(I.lib().iga_set_boundary_value(disc.h, 0, 0, 0.0), disc.h)
+    U = torch.zeros(disc.N, dtype=torch.float64, device="cuda")
+    with pytest.raises(I.IgaError):
+        disc.form_jacobian(U, prec=I.IGA_JAC_BF16)
+    with pytest.raises(I.IgaError):
+        disc.apply_jacobian_mf(U, U.clone())
+    o = I.newton_defaults()
+    o.jac = I.IGA_JAC_NONE
+    with pytest.raises(I.IgaError):
+        disc.solve_newton(U, o)
+    disc.close()
+    for nel, per in (((6, 5), {0: 2}), ((1, 5), {0: 1})):  # k > p - 1; n - k < k + 1
+        with pytest.raises(I.IgaError):
+            I.Discretization(2, 2, nel=list(nel), periodic=per)
