@@ -1,6 +1,6 @@
 """Benchmark lines for the configurations other than the headline one.
 
-    python bench.py --workload {bratu16, cube_mixed, batch512, learned64, nn64, fdjac, genalpha}
+    python bench.py --workload {bratu16, cube_mixed, batch512, learned64, nn64, fdjac, genalpha, periodic64}
 
 Each prints one JSON line with the keys of the headline line (metric, value,
 unit, config, clocks, e2e-style extras) for one configuration:
@@ -21,6 +21,9 @@ unit, config, clocks, e2e-style extras) for one configuration:
   genalpha    Sec. 4.2: generalized-alpha time steps (rho_inf = 0.5, dt = 0.01) of the
               transient Bratu problem u_t = div grad u + 2 e^u on the 64^3 cubic NURBS
               quarter annulus from u = 0, each step a Newton-Krylov solve to 1e-10.
+  periodic64  Sec. 2.4: 3D Bratu, lambda = 2, on the unit cube 64^3 cubic, C^2 periodic in
+              x and y, Dirichlet faces in z: residual and Jacobian assembly (unwrapped
+              space plus the fold onto the wrapped functions) and Newton solves.
   learned64   kappa-Bratu on 64^2 quadratic (66 x 66 control grid): training
               data from the batched solver, the convolutional guess trained on
               the GPU, evaluation on held-out fields against the zero start and
@@ -326,5 +329,41 @@ def genalpha(torch, iga, W, clock, nel=64, steps=10, dt=0.01, rho=0.5):
                  "transient_bratu_annulus64_p3_lambda2_genalpha_rho0.5_dt0.01", {"cases": out, "dofs": d.N}, ck)
 
 
+def periodic64(torch, iga, W, clock, nel=64, p=3):
+    per = {0: p - 1, 1: p - 1}
+    bc = {(2, 0): 0.0, (2, 1): 0.0}
+    d = iga.Discretization(3, p, nel=nel, lam=2.0, dirichlet=bc, periodic=per)
+    n = [nel, nel, nel + p]
+    U = torch.tensor(W.interior_field(n, 3), device="cuda")
+    F = torch.empty_like(U)
+    J = torch.empty(d.nnz, dtype=torch.float64, device="cuda")
+    clock.start()
+    tr = _ev(torch, lambda: d.form_residual(U, F), 5)
+    tj = _ev(torch, lambda: d.form_jacobian(U, vals=J), 3)
+    d.profile_enable(iga.KERNEL_CLASSES)
+    d.form_jacobian(U, vals=J)
+    torch.cuda.synchronize()
+    prof = d.profile_read()
+    d.profile_enable(())
+    solves = {}
+    for label, jac, ksp in (("fp64_gmres", iga.IGA_FP64, iga.IGA_KSP_GMRES), ("fp32_cg", iga.IGA_JAC_FP32, iga.IGA_KSP_CG)):
+        o = iga.newton_defaults()
+        o.jac, o.ksp = jac, ksp
+        best, rep = 1e30, None
+        for _ in range(2):
+            Us = torch.zeros(d.N, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep = d.solve_newton(Us, o)
+            best = min(best, time.perf_counter() - t0)
+        solves[label] = {"ms": best * 1e3, "newton_its": rep.newton_its, "krylov_its": rep.krylov_its, "fnorm": rep.fnorm}
+    ck = clock.stop()
+    d.close()
+    return _line(1e3 / solves["fp64_gmres"]["ms"], "solves/s", "bratu3d_cube64_p3_periodic_xy_C2_lambda2_fp64", {
+        "dofs": d.N, "nnz": d.nnz, "residual_ms": tr, "jacobian_ms": tj, "jacobian_nnz_per_s": d.nnz / (tj * 1e-3),
+        "jacobian_fold_ms": prof["combine"][0], "jacobian_unwrapped_stages_ms": prof["jac_stage1"][0] + prof["jac_stage2"][0] + prof["jac_final"][0],
+        "newton": solves}, ck)
+
+
 WORKLOADS = {"bratu16": bratu16, "cube_mixed": cube_mixed, "batch512": batch512, "learned64": learned64, "nn64": nn64, "fdjac": fdjac,
-             "genalpha": genalpha}
+             "genalpha": genalpha, "periodic64": periodic64}
