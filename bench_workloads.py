@@ -96,9 +96,9 @@ def cube_mixed(torch, iga, W, clock):
         res = {"dofs": d.N, "nnz": d.nnz}
         t = _ev(torch, lambda: d.form_jacobian(U, vals=J), 3)
         res["fp64"] = {"ms": t, "nnz_per_s": d.nnz / (t * 1e-3)}
-        modes = [("fp32_sumfact", iga.IGA_JAC_FP32)]
+        modes = [("fp32_sumfact", iga.IGA_JAC_FP32), ("bf16_tensor", iga.IGA_JAC_BF16)]
         if p <= 3:
-            modes += [("bf16_tensor", iga.IGA_JAC_BF16), ("tf32_tensor", iga.IGA_JAC_TF32)]
+            modes += [("tf32_tensor", iga.IGA_JAC_TF32)]
         d.form_jacobian(U, vals=J)
         nJ = torch.linalg.norm(J).item()
         for mname, code in modes:
@@ -108,7 +108,7 @@ def cube_mixed(torch, iga, W, clock):
         del J32
         solves = {}
         for label, jac, ksp in (("fp64_gmres", iga.IGA_FP64, iga.IGA_KSP_GMRES), ("fp32_gmres", iga.IGA_JAC_FP32, iga.IGA_KSP_GMRES),
-                                ("fp32_cg", iga.IGA_JAC_FP32, iga.IGA_KSP_CG)) + ((("bf16_gmres", iga.IGA_JAC_BF16, iga.IGA_KSP_GMRES),) if p <= 3 else ()):
+                                ("fp32_cg", iga.IGA_JAC_FP32, iga.IGA_KSP_CG), ("bf16_gmres", iga.IGA_JAC_BF16, iga.IGA_KSP_GMRES)):
             o = iga.newton_defaults()
             o.jac, o.ksp = jac, ksp
             best, rep = 1e30, None

@@ -40,6 +40,7 @@ static void free_dir(DirDev &d) {
 
 void iga_release(iga_s *h) {
   periodic_release(h);
+  elem_gemm_release(h);
   for (int ax = 0; ax < 3; ax++) free_dir(h->ddev[ax]);
   void *ps[] = {h->rowptr, h->colidx, h->weights, h->geom, h->Fe, h->Q00, h->T1, h->T2, h->Kstiff, h->Kstiff_f, h->Ebuf64, h->ts_buf,
                 h->Mred, h->Mred_f, h->J64, h->J32, h->wk, h->V, h->red, h->ctl, h->Uhost_dev,
@@ -251,8 +252,8 @@ extern "C" iga_status iga_form_jacobian(iga_t h, const double *U, void *vals, ig
       h->err = "periodic handles assemble the IGA_FP64 and IGA_JAC_FP32 Jacobians only";
       return IGA_EINVAL;
     }
-    if (!mixed_supported(h->dim, h->p)) {
-      h->err = iga_format("element-matrix Jacobians support p <= %d in %dD", h->dim == 3 ? 3 : 4, h->dim);
+    if (prec == IGA_JAC_FD ? !mixed_supported(h->dim, h->p) : !tc_jacobian_supported(h, prec)) {
+      h->err = iga_format("no element-matrix Jacobian of this kind for p = %d in %dD on this mesh", h->p, h->dim);
       return IGA_EINVAL;
     }
     if (prec == IGA_JAC_FD) CK(launch_jacobian_fd(h, U, (double *)vals));
@@ -400,7 +401,8 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
   iga_newton_opts o;
   iga_newton_defaults(&o);
   if (opts_in) o = *opts_in;
-  if ((o.jac == IGA_JAC_TF32 || o.jac == IGA_JAC_BF16 || o.jac == IGA_JAC_FD) && !mixed_supported(h->dim, h->p)) {
+  if ((o.jac == IGA_JAC_FD && !mixed_supported(h->dim, h->p)) ||
+      ((o.jac == IGA_JAC_TF32 || o.jac == IGA_JAC_BF16) && !h->inner && !tc_jacobian_supported(h, (int)o.jac))) {
     h->err = "element-matrix Jacobian not supported for this degree";
     return IGA_EINVAL;
   }

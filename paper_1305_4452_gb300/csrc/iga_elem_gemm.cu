@@ -1,0 +1,581 @@
+// Element matrices of the reduced-precision Jacobian as one GEMM across elements
+// on the 5th-generation tensor cores (tcgen05.mma, BF16 or TF32 operands, FP32
+// accumulator in tensor memory).
+//
+// With Q_{mu nu}(e, q) the per-Gauss-point coefficients (geometry, kappa and the
+// reaction term at U, mu, nu = 0 for values and 1..DIM for derivatives) and
+// D_mu M_a(q) the tensor-product B-spline values and first derivatives,
+//     E_ab(e) = sum_q sum_{mu,nu} Q_{mu nu}(e, q) D_mu M_a(q) D_nu M_b(q)
+// (the element matrix of Eq. (jacobian), Sec. 2.7, before the weights w_a w_b).
+// D_mu M_a(q) depends on the element only through its three 1D tables, and the
+// elements of a uniform knot vector share them except for p elements at each end
+// per direction.  For elements of one such type, with k = (slot s = (mu <= nu), q)
+// and the symmetric pairs a <= b,
+//     E(e, ab) = sum_k Qv(e, k) T(k, ab),       Qv(e, (s, q)) = Q_{mu nu}(e, q),
+//     T((s, q), ab) = D_mu M_a D_nu M_b + [mu != nu] D_nu M_a D_mu M_b,
+// a dense (elements x K) x (K x pairs) product: M = 128 elements of one type per
+// tile, N = 128 pairs, K = slots x NQ (padded to 64).  Identity maps with unit
+// weights have g = 0 and a diagonal S, so only the DIM+1 slots mu = nu are nonzero.
+//
+// k_elem_gemm, one CTA per (128 elements, 128 pairs) tile, 128 threads:
+//   - every thread copies its element row of the Qv chunk (cp.async, 16 B) and
+//     computes its pair row of the T chunk from the tile type's 1D tables, into the
+//     canonical K-major layout without swizzling (8-row x 16-byte core matrices,
+//     128 B apart along M/N, 2 KB apart along K), two stages;
+//   - thread 0 issues the chunk's four tcgen05.mma (32 bytes of K each) and commits
+//     them to the stage's barrier, which frees the stage two chunks later;
+//   - after the last chunk warp w reads accumulator rows 32w .. 32w+31 with
+//     tcgen05.ld and writes them to the element-matrix buffer E[slot][pair].
+// Every barrier wait is bounded in time; the decision to stop is taken by thread 0
+// and shared through shared memory, so all threads leave the loop together.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "iga_internal.h"
+#include "iga_tc.h"
+
+namespace {
+
+constexpr int GT = 128;          // elements (M) and pairs (N) per tile
+constexpr int KB = 128;          // bytes of K per chunk and row
+constexpr int STAGE = GT * KB;   // bytes of one operand chunk
+constexpr uint32_t LBO = 16 * 128;  // next 16 bytes of K: 16 row groups of 128 B
+constexpr int EG_GROUP = 32;        // m-tiles per CTA (one T tile computed per CTA)
+
+enum { EG_BF16 = 0, EG_TF32 = 1 };
+
+// (mu, nu) of each slot: the DIM+1 diagonal slots first, then mu < nu
+struct Slots {
+  int n;
+  int mu[10], nu[10];
+};
+__host__ __device__ inline Slots make_slots(int dim, bool general) {
+  Slots s;
+  s.n = 0;
+  for (int m = 0; m <= dim; m++) { s.mu[s.n] = m; s.nu[s.n] = m; s.n++; }
+  if (general)
+    for (int m = 0; m <= dim; m++)
+      for (int v = m + 1; v <= dim; v++) { s.mu[s.n] = m; s.nu[s.n] = v; s.n++; }
+  return s;
+}
+
+struct GemmArgs {
+  const void *Qv;          // [slots_total][Kp] operand values (BF16, or TF32 in FP32 containers)
+  float *E;                // [slots_total][Np]
+  const float *tab[3];     // FP32 1D tables [nel][q][p+1][2]
+  const int *group;        // [ngroups][5]: first m-tile, m-tiles, element of the type per direction
+  const int *pair_ab;      // [nsym]: a | b << 16, a <= b
+  int dim, p, nq, nsym, Kp, Np, n_tiles, general;
+  int *err;
+};
+
+__device__ __forceinline__ uint32_t op_bits(float x, int op) {
+  if (op == EG_BF16) {
+    __nv_bfloat16 h = __float2bfloat16_rn(x);
+    return (uint32_t)*reinterpret_cast<uint16_t *>(&h);
+  }
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// Shared memory of k_elem_gemm: the T tile for the whole K (one STAGE per chunk),
+// two A stages, the 1D tables, the slot table, barriers and flags.
+__host__ __device__ constexpr size_t eg_smem(int nchunks) {
+  return (size_t)(nchunks + 2) * STAGE + 3 * 5 * 5 * 2 * sizeof(float) + 32 * sizeof(int) + 2 * sizeof(uint64_t) + 16;
+}
+
+template <int OP>
+__global__ void __launch_bounds__(128) k_elem_gemm(GemmArgs g) {
+  constexpr int ES = OP == EG_BF16 ? 2 : 4;  // operand bytes
+  constexpr int KC = KB / ES;                // K values per chunk
+  constexpr int PER = 16 / ES;               // values per 16 bytes
+  const int nchunks = g.Kp / KC;
+  extern __shared__ __align__(128) uint8_t sm[];
+  uint8_t *Ts = sm;                                    // [nchunks][STAGE]
+  uint8_t *As = sm + (size_t)nchunks * STAGE;          // [2][STAGE]
+  float *tab = reinterpret_cast<float *>(As + 2 * STAGE);  // [3][q][p+1][2]
+  int *smu = reinterpret_cast<int *>(tab + 3 * 5 * 5 * 2), *snu = smu + 16;
+  uint64_t *done = reinterpret_cast<uint64_t *>(smu + 32);
+  uint32_t *slot = reinterpret_cast<uint32_t *>(done + 2);
+  volatile int *abort_s = reinterpret_cast<volatile int *>(slot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int grp = blockIdx.x / g.n_tiles, n_tile = blockIdx.x % g.n_tiles;
+  const int m_first = g.group[grp * 5 + 0], m_count = g.group[grp * 5 + 1];
+  const int q = g.p + 1, n1 = g.p + 1;
+  const int tsz = q * n1 * 2;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)), "r"(GT) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(done)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(done + 1)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *abort_s = 0;
+    const Slots S = make_slots(g.dim, g.general != 0);
+    for (int k = 0; k < 16; k++) {
+      smu[k] = k < S.n ? S.mu[k] : 0;
+      snu[k] = k < S.n ? S.nu[k] : 0;
+    }
+    smu[15] = S.n;
+  }
+  for (int k = tid; k < 3 * tsz; k += blockDim.x) {
+    const int ax = k / tsz, r = k - ax * tsz;
+    tab[k] = ax < g.dim ? g.tab[ax][(size_t)g.group[grp * 5 + 2 + ax] * tsz + r] : (r % 2 == 0 ? 1.f : 0.f);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  const int nslot = smu[15];
+  const int KV = nslot * g.nq;
+
+  // ---- T tile of this pair range for the whole K, once per group ----
+  {
+    const int npair = n_tile * GT + tid;
+    int a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0;
+    const bool pvalid = npair < g.nsym;
+    if (pvalid) {
+      const int ab = g.pair_ab[npair];
+      const int ia = ab & 0xFFFF, ib = ab >> 16;
+      a0 = ia % n1;
+      a1 = (ia / n1) % n1;
+      a2 = g.dim == 3 ? ia / (n1 * n1) : 0;
+      b0 = ib % n1;
+      b1 = (ib / n1) % n1;
+      b2 = g.dim == 3 ? ib / (n1 * n1) : 0;
+    }
+#define TB(ax, gq, aa, s) tab[(((ax) * q + (gq)) * n1 + (aa)) * 2 + (s)]
+    const uint32_t rowoff = (uint32_t)((tid >> 3) * 128 + (tid & 7) * 16);
+    int k = 0, sl = 0, qp = 0;  // running K index, its slot and Gauss point
+    for (int c = 0; c < nchunks; c++) {
+      const uint32_t bdst = su32(Ts + (size_t)c * STAGE) + rowoff;
+      for (int kc = 0; kc < 8; kc++) {
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int j = 0; j < PER; j++, k++) {
+          float v = 0.f;
+          if (pvalid && k < KV) {
+            const int mu = smu[sl], nu = snu[sl];
+            const int g0 = qp % q, g1 = (qp / q) % q, g2 = g.dim == 3 ? qp / (q * q) : 0;
+            const float Dam = TB(0, g0, a0, mu == 1) * TB(1, g1, a1, mu == 2) * TB(2, g2, a2, mu == 3);
+            const float Dbn = TB(0, g0, b0, nu == 1) * TB(1, g1, b1, nu == 2) * TB(2, g2, b2, nu == 3);
+            v = Dam * Dbn;
+            if (mu != nu) {
+              const float Dan = TB(0, g0, a0, nu == 1) * TB(1, g1, a1, nu == 2) * TB(2, g2, a2, nu == 3);
+              const float Dbm = TB(0, g0, b0, mu == 1) * TB(1, g1, b1, mu == 2) * TB(2, g2, b2, mu == 3);
+              v += Dan * Dbm;
+            }
+          }
+          if (++qp == g.nq) {
+            qp = 0;
+            sl++;
+          }
+          const uint32_t bits = op_bits(v, OP);
+          if (ES == 2) w[j >> 1] |= bits << (16 * (j & 1));
+          else w[j] = bits;
+        }
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(bdst + kc * LBO), "r"(w[0]), "r"(w[1]), "r"(w[2]),
+                     "r"(w[3])
+                     : "memory");
+      }
+    }
+#undef TB
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+
+  const uint32_t idesc = (1u << 4) | ((OP == EG_BF16 ? 1u : 2u) << 7) | ((OP == EG_BF16 ? 1u : 2u) << 10) |
+                         ((uint32_t)(GT >> 3) << 17) | ((uint32_t)(GT >> 4) << 24);
+  const uint32_t rowoff = (uint32_t)((tid >> 3) * 128 + (tid & 7) * 16);
+  int it = 0;     // chunk counter over all m-tiles (stage it & 1)
+  int last = -1;  // thread 0: the last chunk whose MMAs were committed
+  for (int mi = 0; mi < m_count && !*abort_s; mi++) {
+    const int mt = m_first + mi;
+    const uint8_t *qrow = reinterpret_cast<const uint8_t *>(g.Qv) + ((size_t)mt * GT + tid) * g.Kp * ES;
+    for (int c = 0; c < nchunks; c++, it++) {
+      const int st = it & 1;
+      if (it >= 2) {
+        if (tid == 0 && !mbar_wait(su32(done + st), ((it - 2) >> 1) & 1, abort_s)) *abort_s = 1;
+        __syncthreads();
+        if (*abort_s) break;
+      }
+      const uint32_t adst = su32(As + st * STAGE) + rowoff;
+#pragma unroll
+      for (int kc = 0; kc < 8; kc++) cp16(adst + kc * LBO, qrow + (size_t)c * KB + kc * 16, true);
+      cp_commit();
+      cp_wait<0>();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const uint64_t ad = sdesc(su32(As + st * STAGE), LBO, 128), bd = sdesc(su32(Ts + (size_t)c * STAGE), LBO, 128);
+#pragma unroll
+        for (int kk = 0; kk < 4; kk++) {
+          const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+          const uint64_t a_k = ad + (uint64_t)((kk * 2 * LBO) >> 4), b_k = bd + (uint64_t)((kk * 2 * LBO) >> 4);
+          if constexpr (OP == EG_BF16)
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                "l"(a_k), "l"(b_k), "r"(idesc), "r"(acc)
+                : "memory");
+          else
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                "l"(a_k), "l"(b_k), "r"(idesc), "r"(acc)
+                : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(done + st))
+                     : "memory");
+        last = it;
+      }
+    }
+    if (*abort_s) break;
+    // this m-tile's accumulator is complete once its last commit has arrived
+    if (tid == 0 && !mbar_wait(su32(done + ((it - 1) & 1)), ((it - 1) >> 1) & 1, abort_s)) *abort_s = 1;
+    __syncthreads();
+    if (*abort_s) break;
+    tc_fence_after();
+    const int row = warp * 32 + lane;
+    float *dst = g.E + ((size_t)mt * GT + row) * g.Np + (size_t)n_tile * GT;
+    for (int c0 = 0; c0 < GT; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      float4 *d4 = reinterpret_cast<float4 *>(dst + c0);
+#pragma unroll
+      for (int u = 0; u < 4; u++) d4[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+    }
+    tc_fence_before();
+    __syncthreads();  // the accumulator is read before the next m-tile's MMAs overwrite it
+  }
+  // after a stop, wait (bounded) for the last committed MMAs before freeing the tensor memory
+  if (tid == 0 && *abort_s) {
+    if (last >= 0) (void)mbar_wait(su32(done + (last & 1)), (last >> 1) & 1, nullptr);
+    atomicExch(g.err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GT) : "memory");
+}
+
+// Qv[slot(e)][(s, q)] = Q_{mu nu}(e, q) in the operand type, from the FP64 Q00 at U
+// (launch_q00) and the geometry record: Q_00 = Q00, Q_0a = nSg_a, Q_ab = S_ab.
+template <int DIM, int OP>
+__global__ void k_qv(const double *__restrict__ geom, GeomLayout gl, const double *__restrict__ Q00,
+                     const int *__restrict__ slot_of_elem, void *__restrict__ Qv, int Kp, int nq, int general, int64_t nelem) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nelem * nq) return;
+  const int64_t e = t / nq;
+  const int qp = (int)(t - e * nq);
+  const double *rec = geom + (size_t)e * gl.nf * nq + qp;
+  const Slots S = make_slots(DIM, general != 0);
+  const size_t row = (size_t)slot_of_elem[e] * Kp;
+  for (int s = 0; s < S.n; s++) {
+    const int mu = S.mu[s], nu = S.nu[s];
+    double v;
+    if (mu == 0 && nu == 0) v = Q00[(size_t)e * nq + qp];
+    else if (mu == 0) v = rec[(gl.Sg + nu - 1) * nq];
+    else {
+      // S slots: 2D 00, 11, 01; 3D 00, 11, 22, 01, 02, 12
+      const int i = mu - 1, j = nu - 1;
+      const int si = (i == j) ? i : (DIM == 2 ? 2 : (i == 0 ? (j == 1 ? 3 : 4) : 5));
+      v = rec[(gl.S + si) * nq];
+    }
+    const uint32_t bits = op_bits((float)v, OP);
+    if (OP == EG_BF16) reinterpret_cast<uint16_t *>(Qv)[row + (size_t)s * nq + qp] = (uint16_t)bits;
+    else reinterpret_cast<uint32_t *>(Qv)[row + (size_t)s * nq + qp] = bits;
+  }
+}
+
+template <int DIM> __host__ __device__ constexpr int ipow3(int b) { return DIM == 2 ? b * b : b * b * b; }
+
+// One warp per CSR row A: the element-matrix rows of the elements containing A
+// (e2, e1, e0 ascending), read from the packed upper triangle, summed at the
+// columns' positions in shared memory; then w_A w_B and the Dirichlet rows/columns.
+template <int DIM, int P>
+__global__ void __launch_bounds__(256) k_gather_sym(DirArgs d0, DirArgs d1, DirArgs d2, const float *__restrict__ E,
+                                                    const int *__restrict__ slot_of_elem, int Np,
+                                                    const int64_t *__restrict__ rowptr, const double *__restrict__ wts,
+                                                    BndArgs bnd, float *__restrict__ vals, int64_t N) {
+  constexpr int N1 = P + 1, NEN = ipow3<DIM>(N1), RMAX = ipow3<DIM>(2 * P + 1);
+  __shared__ float rowacc[8][RMAX];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t A = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (A >= N) return;
+  float *acc = rowacc[warp];
+  int I[3] = {(int)(A % d0.n), (int)((A / d0.n) % d1.n), (DIM == 3) ? (int)(A / ((int64_t)d0.n * d1.n)) : 0};
+  int n[3] = {d0.n, d1.n, d2.n};
+  int l[3] = {d0.l[I[0]], d1.l[I[1]], DIM == 3 ? d2.l[I[2]] : 0};
+  int w[3] = {d0.r[I[0]] - l[0] + 1, d1.r[I[1]] - l[1] + 1, DIM == 3 ? d2.r[I[2]] - l[2] + 1 : 1};
+  const int len = w[0] * w[1] * w[2];
+  for (int k = lane; k < len; k += 32) acc[k] = 0.f;
+  __syncwarp();
+  const int lo2 = (DIM == 3) ? d2.node_e0[I[2]] : 0, hi2 = (DIM == 3) ? lo2 + d2.node_ne[I[2]] : 1;
+  const int lo1 = d1.node_e0[I[1]], hi1 = lo1 + d1.node_ne[I[1]];
+  const int lo0 = d0.node_e0[I[0]], hi0 = lo0 + d0.node_ne[I[0]];
+  for (int e2 = lo2; e2 < hi2; e2++) {
+    const int f2 = (DIM == 3) ? d2.first[e2] : 0;
+    for (int e1 = lo1; e1 < hi1; e1++) {
+      const int f1 = d1.first[e1];
+      for (int e0 = lo0; e0 < hi0; e0++) {
+        const int f0 = d0.first[e0];
+        const int64_t e = e0 + (int64_t)d0.nel * (e1 + (int64_t)d1.nel * e2);
+        const int a = (I[0] - f0) + N1 * ((I[1] - f1) + N1 * (I[2] - f2));
+        const float *Er = E + (size_t)slot_of_elem[e] * Np;
+        for (int bb = lane; bb < NEN; bb += 32) {
+          const int lo = a < bb ? a : bb, hi = a < bb ? bb : a;
+          const int pk = lo * NEN - lo * (lo - 1) / 2 + (hi - lo);
+          const int b0 = bb % N1, b1 = (bb / N1) % N1, b2 = (DIM == 3) ? bb / (N1 * N1) : 0;
+          const int pos = ((f2 + b2 - l[2]) * w[1] + (f1 + b1 - l[1])) * w[0] + (f0 + b0 - l[0]);
+          acc[pos] += Er[pk];
+        }
+        __syncwarp();
+      }
+    }
+  }
+  bool rowfix = false;
+  for (int ax = 0; ax < DIM; ax++) rowfix |= (bnd.flag[ax][0] && I[ax] == 0) || (bnd.flag[ax][1] && I[ax] == n[ax] - 1);
+  const float wA = wts ? (float)wts[A] : 1.f;
+  const int64_t r0 = rowptr[A];
+  for (int k = lane; k < len; k += 32) {
+    int J[3] = {l[0] + k % w[0], l[1] + (k / w[0]) % w[1], l[2] + k / (w[0] * w[1])};
+    const int64_t B = J[0] + (int64_t)d0.n * (J[1] + (int64_t)d1.n * J[2]);
+    float v = acc[k];
+    if (wts) v *= wA * (float)wts[B];
+    bool colfix = false;
+    for (int ax = 0; ax < DIM; ax++) colfix |= (bnd.flag[ax][0] && J[ax] == 0) || (bnd.flag[ax][1] && J[ax] == n[ax] - 1);
+    if (rowfix || colfix) v = (A == B) ? 1.f : 0.f;
+    vals[r0 + k] = v;
+  }
+}
+
+}  // namespace
+
+// Host-side plan: element types per direction (elements whose FP64 1D tables agree
+// to 1e-12 relative), elements sorted by type into 128-element tiles, the symmetric
+// pair list, and the operand and result buffers.
+struct ElemGemmPlan {
+  bool ok = false;
+  int general = 0, nq = 0, nsym = 0, Kp = 0, Np = 0, n_tiles = 0, m_tiles = 0, es = 2;
+  int ngroups = 0;
+  int *slot_of_elem = nullptr, *group = nullptr, *pair_ab = nullptr, *err = nullptr;
+  void *Qv[2] = {nullptr, nullptr};  // BF16, TF32 operand buffers
+  float *E = nullptr;
+};
+
+static std::vector<int> dir_types(const Dir &D, std::vector<int> &rep) {
+  const size_t tsz = (size_t)D.q * (D.p + 1) * 2;
+  std::vector<int> type(D.nel, -1);
+  rep.clear();
+  for (int e = 0; e < D.nel; e++) {
+    const double *te = &D.tab[(size_t)e * tsz];
+    for (size_t t = 0; t < rep.size() && type[e] < 0; t++) {
+      const double *tr = &D.tab[(size_t)rep[t] * tsz];
+      bool same = true;
+      for (size_t k = 0; k < tsz && same; k++) same = std::fabs(te[k] - tr[k]) <= 1e-12 * (1.0 + std::fabs(tr[k]));
+      if (same) type[e] = (int)t;
+    }
+    if (type[e] < 0) {
+      type[e] = (int)rep.size();
+      rep.push_back(e);
+    }
+  }
+  return type;
+}
+
+static void plan_free(ElemGemmPlan *P) {
+  void *ps[] = {P->slot_of_elem, P->group, P->pair_ab, P->err, P->Qv[0], P->Qv[1], P->E};
+  for (void *p : ps)
+    if (p) cudaFree(p);
+}
+
+void elem_gemm_release(iga_s *h) {
+  if (!h->egemm) return;
+  plan_free(h->egemm);
+  delete h->egemm;
+  h->egemm = nullptr;
+}
+
+static cudaError_t elem_gemm_prepare(iga_s *h) {
+  if (h->egemm) return h->egemm->ok ? cudaSuccess : cudaErrorNotSupported;
+  ElemGemmPlan *P = new ElemGemmPlan();
+  h->egemm = P;
+  const int dim = h->dim, p = h->p, n1 = p + 1;
+  const int nen = dim == 3 ? n1 * n1 * n1 : n1 * n1;
+  P->nq = dim == 3 ? h->q * h->q * h->q : h->q * h->q;
+  P->general = (h->has_geom || h->has_w) ? 1 : 0;
+  const Slots S = make_slots(dim, P->general != 0);
+  P->Kp = (S.n * P->nq + 63) / 64 * 64;
+  P->nsym = nen * (nen + 1) / 2;
+  P->n_tiles = (P->nsym + GT - 1) / GT;
+  P->Np = P->n_tiles * GT;
+  // types and tiles
+  std::vector<int> rep[3], ty[3];
+  for (int ax = 0; ax < 3; ax++) {
+    if (ax < dim) ty[ax] = dir_types(h->dir[ax], rep[ax]);
+    else { ty[ax].assign(1, 0); rep[ax].assign(1, 0); }
+  }
+  const int nt0 = (int)rep[0].size(), nt1 = (int)rep[1].size(), nt2 = (int)rep[2].size();
+  const int64_t ntypes = (int64_t)nt0 * nt1 * nt2;
+  std::vector<int64_t> count(ntypes, 0);
+  const int nel0 = h->dir[0].nel, nel1 = h->dir[1].nel;
+  auto type_of = [&](int64_t e) {
+    const int e0 = (int)(e % nel0), e1 = (int)((e / nel0) % nel1), e2 = (int)(e / ((int64_t)nel0 * nel1));
+    return (int64_t)ty[0][e0] + nt0 * ((int64_t)ty[1][e1] + (int64_t)nt1 * ty[2][dim == 3 ? e2 : 0]);
+  };
+  for (int64_t e = 0; e < h->nelem; e++) count[type_of(e)]++;
+  std::vector<int64_t> first_slot(ntypes, 0);
+  int64_t m_tiles = 0;
+  for (int64_t t = 0; t < ntypes; t++) {
+    first_slot[t] = m_tiles * GT;
+    m_tiles += (count[t] + GT - 1) / GT;
+  }
+  // tiles beyond four times the elements (knot vectors with few repeated spans): not worth it
+  if (m_tiles * GT > 4 * h->nelem + 64 * GT) return cudaErrorNotSupported;
+  P->m_tiles = (int)m_tiles;
+  std::vector<int> slot(h->nelem), groups;
+  std::vector<int64_t> next = first_slot;
+  for (int64_t e = 0; e < h->nelem; e++) {
+    const int64_t t = type_of(e);
+    slot[e] = (int)next[t]++;
+  }
+  // work groups: up to EG_GROUP consecutive m-tiles of one type share the T tile
+  for (int64_t t = 0; t < ntypes; t++) {
+    const int t0 = (int)(t % nt0), t1 = (int)((t / nt0) % nt1), t2 = (int)(t / ((int64_t)nt0 * nt1));
+    const int64_t m0 = first_slot[t] / GT, m1 = (first_slot[t] + count[t] + GT - 1) / GT;
+    for (int64_t m = m0; m < m1; m += EG_GROUP) {
+      groups.push_back((int)m);
+      groups.push_back((int)std::min<int64_t>(EG_GROUP, m1 - m));
+      groups.push_back(rep[0][t0]);
+      groups.push_back(rep[1][t1]);
+      groups.push_back(rep[2][t2]);
+    }
+  }
+  P->ngroups = (int)(groups.size() / 5);
+  std::vector<int> pairs;
+  for (int a = 0; a < nen; a++)
+    for (int b = a; b < nen; b++) pairs.push_back(a | (b << 16));
+  const size_t slots_total = (size_t)m_tiles * GT;
+  cudaError_t ce;
+  if ((ce = cudaMalloc((void **)&P->slot_of_elem, slot.size() * sizeof(int)))) return ce;
+  if ((ce = cudaMemcpy(P->slot_of_elem, slot.data(), slot.size() * sizeof(int), cudaMemcpyHostToDevice))) return ce;
+  if ((ce = cudaMalloc((void **)&P->group, groups.size() * sizeof(int)))) return ce;
+  if ((ce = cudaMemcpy(P->group, groups.data(), groups.size() * sizeof(int), cudaMemcpyHostToDevice))) return ce;
+  if ((ce = cudaMalloc((void **)&P->pair_ab, pairs.size() * sizeof(int)))) return ce;
+  if ((ce = cudaMemcpy(P->pair_ab, pairs.data(), pairs.size() * sizeof(int), cudaMemcpyHostToDevice))) return ce;
+  if ((ce = cudaMalloc((void **)&P->err, sizeof(int)))) return ce;
+  if ((ce = cudaMemset(P->err, 0, sizeof(int)))) return ce;
+  if ((ce = cudaMalloc((void **)&P->E, slots_total * P->Np * sizeof(float)))) return ce;
+  (void)slots_total;
+  P->ok = true;
+  return cudaSuccess;
+}
+
+static cudaError_t qv_buffer(iga_s *h, int op, void **out) {
+  ElemGemmPlan *P = h->egemm;
+  const size_t es = op == EG_BF16 ? 2 : 4;
+  if (!P->Qv[op]) {
+    const size_t bytes = (size_t)P->m_tiles * GT * P->Kp * es;
+    cudaError_t ce = cudaMalloc(&P->Qv[op], bytes);
+    if (ce) return ce;
+    ce = cudaMemsetAsync(P->Qv[op], 0, bytes, h->stream);  // padding rows and K columns stay zero
+    if (ce) return ce;
+  }
+  *out = P->Qv[op];
+  return cudaSuccess;
+}
+
+#define EG_DISPATCH(DIM_, P_, CALL)                         \
+  do {                                                      \
+    if ((DIM_) == 2) {                                      \
+      switch (P_) {                                         \
+        case 1: { constexpr int D = 2, PP = 1; CALL; } break; \
+        case 2: { constexpr int D = 2, PP = 2; CALL; } break; \
+        case 3: { constexpr int D = 2, PP = 3; CALL; } break; \
+        case 4: { constexpr int D = 2, PP = 4; CALL; } break; \
+      }                                                     \
+    } else {                                                \
+      switch (P_) {                                         \
+        case 1: { constexpr int D = 3, PP = 1; CALL; } break; \
+        case 2: { constexpr int D = 3, PP = 2; CALL; } break; \
+        case 3: { constexpr int D = 3, PP = 3; CALL; } break; \
+        case 4: { constexpr int D = 3, PP = 4; CALL; } break; \
+      }                                                     \
+    }                                                       \
+  } while (0)
+
+// The plan exists and the T tile of the whole K fits in shared memory for the operand type.
+bool elem_gemm_supported(iga_s *h, int prec) {
+  if (elem_gemm_prepare(h) != cudaSuccess) return false;
+  const int es = prec == IGA_JAC_BF16 ? 2 : 4;
+  return eg_smem(h->egemm->Kp * es / KB) <= 200 * 1024;
+}
+
+// vals (FP32, CSR) = the Jacobian with BF16 (prec IGA_JAC_BF16) or TF32 element
+// contractions: Q00 at U in FP64 (launch_q00), the operand rows, the GEMM, the gather.
+// h->tab32 must hold the FP32 tables.
+cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, int prec) {
+  if (!elem_gemm_supported(h, prec)) return cudaErrorNotSupported;
+  cudaError_t ce;
+  ElemGemmPlan *P = h->egemm;
+  const int op = prec == IGA_JAC_BF16 ? EG_BF16 : EG_TF32;
+  void *Qv = nullptr;
+  if ((ce = qv_buffer(h, op, &Qv))) return ce;
+  h->q00_valid = false;
+  if ((ce = launch_q00(h, U, 1.0, 1.0))) return ce;
+  const int64_t tot = h->nelem * P->nq;
+  const unsigned gq = (unsigned)((tot + 255) / 256);
+  if (h->dim == 3) {
+    if (op == EG_BF16) IGA_LAUNCH(h, KC_ELEM_TC, (k_qv<3, EG_BF16><<<gq, 256, 0, h->stream>>>(h->geom, h->gl, h->Q00, P->slot_of_elem, Qv, P->Kp, P->nq, P->general, h->nelem)));
+    else IGA_LAUNCH(h, KC_ELEM_TC, (k_qv<3, EG_TF32><<<gq, 256, 0, h->stream>>>(h->geom, h->gl, h->Q00, P->slot_of_elem, Qv, P->Kp, P->nq, P->general, h->nelem)));
+  } else {
+    if (op == EG_BF16) IGA_LAUNCH(h, KC_ELEM_TC, (k_qv<2, EG_BF16><<<gq, 256, 0, h->stream>>>(h->geom, h->gl, h->Q00, P->slot_of_elem, Qv, P->Kp, P->nq, P->general, h->nelem)));
+    else IGA_LAUNCH(h, KC_ELEM_TC, (k_qv<2, EG_TF32><<<gq, 256, 0, h->stream>>>(h->geom, h->gl, h->Q00, P->slot_of_elem, Qv, P->Kp, P->nq, P->general, h->nelem)));
+  }
+  GemmArgs g;
+  g.Qv = Qv;
+  g.E = P->E;
+  for (int ax = 0; ax < 3; ax++) g.tab[ax] = ax < h->dim ? h->tab32[ax] : nullptr;
+  g.group = P->group;
+  g.pair_ab = P->pair_ab;
+  g.dim = h->dim;
+  g.p = h->p;
+  g.nq = P->nq;
+  g.nsym = P->nsym;
+  g.Kp = P->Kp;
+  g.Np = P->Np;
+  g.n_tiles = P->n_tiles;
+  g.general = P->general;
+  g.err = P->err;
+  const size_t smem = eg_smem(P->Kp * (op == EG_BF16 ? 2 : 4) / KB);
+  const unsigned grid = (unsigned)((int64_t)P->ngroups * P->n_tiles);
+  if (op == EG_BF16) {
+    cudaFuncSetAttribute(k_elem_gemm<EG_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    IGA_LAUNCH(h, KC_ELEM_TC, (k_elem_gemm<EG_BF16><<<grid, 128, smem, h->stream>>>(g)));
+  } else {
+    cudaFuncSetAttribute(k_elem_gemm<EG_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    IGA_LAUNCH(h, KC_ELEM_TC, (k_elem_gemm<EG_TF32><<<grid, 128, smem, h->stream>>>(g)));
+  }
+  if ((ce = cudaGetLastError())) return ce;
+  DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
+  const unsigned gg = (unsigned)((h->N * 32 + 255) / 256);
+  IGA_LAUNCH(h, KC_ELEM_GATHER, EG_DISPATCH(h->dim, h->p, (k_gather_sym<D, PP><<<gg, 256, 0, h->stream>>>(
+                                                              a0, a1, a2, P->E, P->slot_of_elem, P->Np, h->rowptr, h->weights,
+                                                              h->bnd, vals, h->N))));
+  return cudaGetLastError();
+}
+
+// Error flag of the element GEMM (a barrier wait that timed out); reading it synchronises.
+bool elem_gemm_failed(iga_s *h) {
+  if (!h->egemm || !h->egemm->err) return false;
+  int v = 0;
+  cudaMemcpy(&v, h->egemm->err, sizeof(int), cudaMemcpyDeviceToHost);
+  return v != 0;
+}

@@ -134,6 +134,7 @@ struct Prof {
 };
 
 struct iga_s;
+struct ElemGemmPlan;
 int prof_begin(iga_s *h, int cls);
 void prof_end(iga_s *h, int token);
 #define IGA_LAUNCH(h, cls, ...)          \
@@ -193,6 +194,7 @@ struct iga_s {
   float *Ebuf = nullptr;       // [nelem][nen][nen] element matrices
   double *Ebuf64 = nullptr;    // [nelem][nen][nen] FP64 element matrices (local numerical differentiation)
   float *z32 = nullptr;        // FP32 copy of the Krylov vector for the FP32 SpMV
+  ElemGemmPlan *egemm = nullptr;  // element matrices as one GEMM across elements (iga_elem_gemm.cu)
   // Newton / Krylov workspace
   double *J64 = nullptr;
   float *J32 = nullptr;
@@ -252,6 +254,14 @@ size_t jacobian_t1_groups(int dim);
 // ---- mixed-precision Jacobian (iga_mixed.cu) ----
 bool mixed_supported(int dim, int p);
 cudaError_t launch_jacobian_mixed(iga_s *h, const double *U, float *vals, int prec);
+// Element matrices as one tcgen05 GEMM across elements of equal 1D tables (iga_elem_gemm.cu):
+// available when the knot vectors repeat their spans (uniform meshes); frees in elem_gemm_release
+bool elem_gemm_supported(iga_s *h, int prec);
+cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, int prec);
+bool elem_gemm_failed(iga_s *h);
+void elem_gemm_release(iga_s *h);
+// Degrees and dimensions with a tensor-core Jacobian on this handle
+bool tc_jacobian_supported(iga_s *h, int prec);
 // Jacobian by local numerical differentiation (Sec. 2.8 Eq. fdjac), FP64 values
 cudaError_t launch_jacobian_fd(iga_s *h, const double *U, double *vals);
 size_t jacobian_t2_groups(int dim);

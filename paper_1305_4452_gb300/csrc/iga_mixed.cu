@@ -563,12 +563,21 @@ static cudaError_t mixed_prepare(iga_s *h) {
       IGA_LAUNCH(h, KC_VEC, (k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->ddev[ax].tab, h->tab32[ax], (int64_t)n)));
     }
   }
+  return cudaGetLastError();
+}
+
+static cudaError_t ebuf_prepare(iga_s *h) {
   if (!h->Ebuf) {
     int nen = (h->dim == 3) ? (h->p + 1) * (h->p + 1) * (h->p + 1) : (h->p + 1) * (h->p + 1);
-    ce = cudaMalloc((void **)&h->Ebuf, (size_t)h->nelem * nen * nen * sizeof(float));
+    cudaError_t ce = cudaMalloc((void **)&h->Ebuf, (size_t)h->nelem * nen * nen * sizeof(float));
     if (ce) return ce;
   }
-  return cudaGetLastError();
+  return cudaSuccess;
+}
+
+bool tc_jacobian_supported(iga_s *h, int prec) {
+  if (h->inner) return false;
+  return elem_gemm_supported(h, prec) || mixed_supported(h->dim, h->p);
 }
 
 // Jacobian by local numerical differentiation (FP64 values), same degrees as the
@@ -591,9 +600,12 @@ cudaError_t launch_jacobian_fd(iga_s *h, const double *U, double *vals) {
 
 // Full mixed-precision Jacobian into FP32 CSR values (prec: IGA_JAC_TF32 / IGA_JAC_BF16).
 cudaError_t launch_jacobian_mixed(iga_s *h, const double *U, float *vals, int prec) {
-  if (!mixed_supported(h->dim, h->p)) return cudaErrorNotSupported;
   cudaError_t ce = mixed_prepare(h);
   if (ce) return ce;
+  // repeated 1D tables: the element matrices as one tensor-core GEMM across elements
+  if (elem_gemm_supported(h, prec)) return launch_jacobian_elem_gemm(h, U, vals, prec);
+  if (!mixed_supported(h->dim, h->p)) return cudaErrorNotSupported;
+  if ((ce = ebuf_prepare(h))) return ce;
   if (prec == IGA_JAC_BF16) {
     DISPATCH_TC(h->dim, h->p, ce = (run_tc<D, PP, OP_BF16>(h, U, 1.f, 1.f)));
   } else {

@@ -105,11 +105,42 @@ def test_newton_with_mixed_jacobian_reaches_fp64_tolerance(I, prec):
 
 
 def test_mixed_rejects_unsupported_degree(I):
+    # 3D p = 4: the TF32 element GEMM's operand tile does not fit in shared memory
     disc = I.Discretization(3, 4, nel=2, lam=1.0)
     U = torch.zeros(disc.N, dtype=torch.float64, device="cuda")
     with pytest.raises(I.IgaError) as ei:
-        disc.form_jacobian(U, prec=I.IGA_JAC_BF16)
+        disc.form_jacobian(U, prec=I.IGA_JAC_TF32)
     assert ei.value.status == I.IGA_EINVAL
+    disc.close()
+
+
+def test_bf16_element_gemm_quartic_3d(I):
+    """3D p = 4 (the 48^3 quartic configuration's degree) through the element GEMM."""
+    disc, prob, n = pair(I, 3, 4, (5, 3, 3), 1.5)
+    U0 = W.interior_field(n, seed=5, lo=-0.3, hi=0.3)
+    Jm = disc.form_jacobian(torch.tensor(U0, device="cuda"), prec=I.IGA_JAC_BF16).double().cpu().numpy()
+    Jo = prob.jacobian(U0)
+    assert np.linalg.norm(Jm - Jo) / np.linalg.norm(Jo) < FRO_TOL["bf16"]
+    disc.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_nonuniform_knots_use_the_per_element_contraction(I, prec):
+    """Knot vectors with no repeated span lengths: every element its own type, so the
+    per-element tensor-core contraction serves them; same error bound."""
+    rng = np.random.default_rng(9)
+    knots = []
+    for nel in (40, 36):
+        inner = np.sort(rng.uniform(0.0, 1.0, nel - 1))
+        knots.append(np.concatenate([[0.0] * 3, inner, [1.0] * 3]))
+    bc = bc_all(2)
+    disc = I.Discretization(2, 2, knots=knots, lam=1.5, dirichlet=bc)
+    prob = O.Problem(knots, [2, 2], lam=1.5, dirichlet=bc)
+    U0 = np.where(prob.dirichlet_mask(), 0.0, rng.uniform(-0.3, 0.3, prob.N))
+    code = I.IGA_JAC_BF16 if prec == "bf16" else I.IGA_JAC_TF32
+    Jm = disc.form_jacobian(torch.tensor(U0, device="cuda"), prec=code).double().cpu().numpy()
+    Jo = prob.jacobian(U0)
+    assert np.linalg.norm(Jm - Jo) / np.linalg.norm(Jo) < FRO_TOL[prec]
     disc.close()
 
 
