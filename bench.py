@@ -368,7 +368,7 @@ def main():
     ap.add_argument("--nel", type=int, default=64, help="elements per direction (64 is the benchmark workload)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sampling time (0: skip)")
     ap.add_argument("--workload", default="annulus64",
-                    choices=["annulus64", "bratu16", "cube_mixed", "batch512", "learned64", "nn64", "fdjac", "genalpha", "periodic64"],
+                    choices=["annulus64", "bratu16", "cube_mixed", "batch512", "learned64", "nn64", "fdjac", "genalpha", "periodic64", "mixed64"],
                     help="annulus64 is the benchmark line; the others print their configuration's line")
     args = ap.parse_args()
     if args.workload != "annulus64" and args.impl == "ours":

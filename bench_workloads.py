@@ -1,6 +1,6 @@
 """Benchmark lines for the configurations other than the headline one.
 
-    python bench.py --workload {bratu16, cube_mixed, batch512, learned64, nn64, fdjac, genalpha, periodic64}
+    python bench.py --workload {bratu16, cube_mixed, batch512, learned64, nn64, fdjac, genalpha, periodic64, mixed64}
 
 Each prints one JSON line with the keys of the headline line (metric, value,
 unit, config, clocks, e2e-style extras) for one configuration:
@@ -24,6 +24,10 @@ unit, config, clocks, e2e-style extras) for one configuration:
   periodic64  Sec. 2.4: 3D Bratu, lambda = 2, on the unit cube 64^3 cubic, C^2 periodic in
               x and y, Dirichlet faces in z: residual and Jacobian assembly (unwrapped
               space plus the fold onto the wrapped functions) and Newton solves.
+  mixed64     the reduced-precision Jacobians alone on the 64^3 quadratic cube (lambda = 2,
+              U ~ U[-0.1, 0.1]): BF16 and TF32 element matrices (tcgen05 GEMM across
+              elements) and the FP32 sum factorisation, per-kernel-class times, error
+              against the FP64 Jacobian; sized for a profiler capture.
   learned64   kappa-Bratu on 64^2 quadratic (66 x 66 control grid): training
               data from the batched solver, the convolutional guess trained on
               the GPU, evaluation on held-out fields against the zero start and
@@ -365,5 +369,31 @@ def periodic64(torch, iga, W, clock, nel=64, p=3):
         "newton": solves}, ck)
 
 
+def mixed64(torch, iga, W, clock, nel=64, p=2):
+    bc = {(a, s): 0.0 for a in range(3) for s in range(2)}
+    d = iga.Discretization(3, p, nel=nel, lam=2.0, dirichlet=bc)
+    U = torch.tensor(W.interior_field([nel + p] * 3, 3), device="cuda")
+    J = torch.empty(d.nnz, dtype=torch.float64, device="cuda")
+    J32 = torch.empty(d.nnz, dtype=torch.float32, device="cuda")
+    clock.start()
+    d.form_jacobian(U, vals=J)
+    nJ = torch.linalg.norm(J).item()
+    res = {"dofs": d.N, "nnz": d.nnz, "fp64_ms": _ev(torch, lambda: d.form_jacobian(U, vals=J), 3)}
+    for name, code in (("bf16_tensor", iga.IGA_JAC_BF16), ("tf32_tensor", iga.IGA_JAC_TF32), ("fp32_sumfact", iga.IGA_JAC_FP32)):
+        t = _ev(torch, lambda: d.form_jacobian(U, prec=code, vals=J32), 3)
+        d.profile_enable(iga.KERNEL_CLASSES)
+        d.form_jacobian(U, prec=code, vals=J32)
+        torch.cuda.synchronize()
+        prof = d.profile_read()
+        d.profile_enable(())
+        err = (torch.linalg.norm(J32.double() - J) / nJ).item()
+        res[name] = {"ms": t, "nnz_per_s": d.nnz / (t * 1e-3), "rel_frobenius_error_vs_fp64": err,
+                     "classes_ms": {k: round(v[0], 4) for k, v in prof.items() if v[0] > 0}}
+    ck = clock.stop()
+    d.close()
+    return _line(res["bf16_tensor"]["nnz_per_s"], "nnz/s", "cube_64cubed_p2_lambda2_reduced_precision_jacobian", {"cases": res}, ck,
+                 dtype="bf16")
+
+
 WORKLOADS = {"bratu16": bratu16, "cube_mixed": cube_mixed, "batch512": batch512, "learned64": learned64, "nn64": nn64, "fdjac": fdjac,
-             "genalpha": genalpha, "periodic64": periodic64}
+             "genalpha": genalpha, "periodic64": periodic64, "mixed64": mixed64}

@@ -10,11 +10,12 @@
 // D_mu M_a(q) depends on the element only through its three 1D tables, and the
 // elements of a uniform knot vector share them except for p elements at each end
 // per direction.  For elements of one such type, with k = (slot s = (mu <= nu), q)
-// and the symmetric pairs a <= b,
+// and the pairs (a, b),
 //     E(e, ab) = sum_k Qv(e, k) T(k, ab),       Qv(e, (s, q)) = Q_{mu nu}(e, q),
 //     T((s, q), ab) = D_mu M_a D_nu M_b + [mu != nu] D_nu M_a D_mu M_b,
 // a dense (elements x K) x (K x pairs) product: M = 128 elements of one type per
-// tile, N = 128 pairs, K = slots x NQ (padded to 64).  Identity maps with unit
+// tile, N = 128 pairs, K = slots x NQ (padded to 64).  E is symmetric (Q is), so only
+// the pairs a <= b are formed, packed row by row.  Identity maps with unit
 // weights have g = 0 and a diagonal S, so only the DIM+1 slots mu = nu are nonzero.
 //
 // k_elem_gemm, one CTA per (128 elements, 128 pairs) tile, 128 threads:
@@ -25,7 +26,7 @@
 //   - thread 0 issues the chunk's four tcgen05.mma (32 bytes of K each) and commits
 //     them to the stage's barrier, which frees the stage two chunks later;
 //   - after the last chunk warp w reads accumulator rows 32w .. 32w+31 with
-//     tcgen05.ld and writes them to the element-matrix buffer E[slot][pair].
+//     tcgen05.ld and writes them to the element-matrix buffer E[slot][packed (a, b)].
 // Every barrier wait is bounded in time; the decision to stop is taken by thread 0
 // and shared through shared memory, so all threads leave the loop together.
 #include <cuda_bf16.h>
@@ -38,6 +39,7 @@
 
 #include "iga_internal.h"
 #include "iga_tc.h"
+#include "iga_interp.h"
 
 namespace {
 
@@ -45,7 +47,7 @@ constexpr int GT = 128;          // elements (M) and pairs (N) per tile
 constexpr int KB = 128;          // bytes of K per chunk and row
 constexpr int STAGE = GT * KB;   // bytes of one operand chunk
 constexpr uint32_t LBO = 16 * 128;  // next 16 bytes of K: 16 row groups of 128 B
-constexpr int EG_GROUP = 32;        // m-tiles per CTA (one T tile computed per CTA)
+constexpr int EG_GROUP_MAX = 32;    // m-tiles per CTA at most (one T tile computed per CTA)
 
 enum { EG_BF16 = 0, EG_TF32 = 1 };
 
@@ -69,8 +71,8 @@ struct GemmArgs {
   float *E;                // [slots_total][Np]
   const float *tab[3];     // FP32 1D tables [nel][q][p+1][2]
   const int *group;        // [ngroups][5]: first m-tile, m-tiles, element of the type per direction
-  const int *pair_ab;      // [nsym]: a | b << 16, a <= b
-  int dim, p, nq, nsym, Kp, Np, n_tiles, general;
+  const int *pair_ab;      // [nsym]: a | b << 16, a <= b, row by row
+  int dim, p, nq, nsym, Kp, Np, n_tiles, m_tiles, general;
   int *err;
 };
 
@@ -265,30 +267,40 @@ __global__ void __launch_bounds__(128) k_elem_gemm(GemmArgs g) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GT) : "memory");
 }
 
-// Qv[slot(e)][(s, q)] = Q_{mu nu}(e, q) in the operand type, from the FP64 Q00 at U
-// (launch_q00) and the geometry record: Q_00 = Q00, Q_0a = nSg_a, Q_ab = S_ab.
-template <int DIM, int OP>
-__global__ void k_qv(const double *__restrict__ geom, GeomLayout gl, const double *__restrict__ Q00,
-                     const int *__restrict__ slot_of_elem, void *__restrict__ Qv, int Kp, int nq, int general, int64_t nelem) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= nelem * nq) return;
-  const int64_t e = t / nq;
-  const int qp = (int)(t - e * nq);
+// Qv[slot(e)][(s, q)] = Q_{mu nu}(e, q) in the operand type from the geometry record
+// and U: Q_00 = gSg - jw/W^2 lambda e^u (u~ interpolated and the exponential taken in
+// FP32), Q_0a = nSg_a, Q_ab = S_ab.  One thread per Gauss point, EB elements per block.
+template <int DIM, int P, int OP>
+__global__ void __launch_bounds__(128) k_qv(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ U,
+                                            const double *__restrict__ wts, const double *__restrict__ geom, GeomLayout gl,
+                                            float lambda, const int *__restrict__ slot_of_elem, void *__restrict__ Qv, int Kp,
+                                            int general, int64_t nelem) {
+  using IS = InterpF32<DIM, P>;
+  constexpr int nq = IS::NQ;
+  __shared__ float ue[IS::EB * IS::NEN], tb[IS::EB * DIM * IS::Q * IS::N1];
+  const int64_t e_first = (int64_t)blockIdx.x * IS::EB;
+  const float ut = interp_u_block<DIM, P>(d0, d1, d2, U, wts, e_first, nelem, ue, tb);
+  const int le = threadIdx.x / nq, qp = threadIdx.x - le * nq;
+  const int64_t e = e_first + le;
+  if (le >= IS::EB || e >= nelem) return;
   const double *rec = geom + (size_t)e * gl.nf * nq + qp;
+  const float q00 = (float)rec[gl.gSg * nq] - (float)rec[gl.jwW2 * nq] * lambda * __expf(ut * (float)rec[gl.invW * nq]);
   const Slots S = make_slots(DIM, general != 0);
   const size_t row = (size_t)slot_of_elem[e] * Kp;
-  for (int s = 0; s < S.n; s++) {
+#pragma unroll
+  for (int s = 0; s < (DIM == 3 ? 10 : 6); s++) {
+    if (s >= S.n) break;
     const int mu = S.mu[s], nu = S.nu[s];
-    double v;
-    if (mu == 0 && nu == 0) v = Q00[(size_t)e * nq + qp];
-    else if (mu == 0) v = rec[(gl.Sg + nu - 1) * nq];
+    float v;
+    if (mu == 0 && nu == 0) v = q00;
+    else if (mu == 0) v = (float)rec[(gl.Sg + nu - 1) * nq];
     else {
       // S slots: 2D 00, 11, 01; 3D 00, 11, 22, 01, 02, 12
       const int i = mu - 1, j = nu - 1;
       const int si = (i == j) ? i : (DIM == 2 ? 2 : (i == 0 ? (j == 1 ? 3 : 4) : 5));
-      v = rec[(gl.S + si) * nq];
+      v = (float)rec[(gl.S + si) * nq];
     }
-    const uint32_t bits = op_bits((float)v, OP);
+    const uint32_t bits = op_bits(v, OP);
     if (OP == EG_BF16) reinterpret_cast<uint16_t *>(Qv)[row + (size_t)s * nq + qp] = (uint16_t)bits;
     else reinterpret_cast<uint32_t *>(Qv)[row + (size_t)s * nq + qp] = bits;
   }
@@ -296,14 +308,16 @@ __global__ void k_qv(const double *__restrict__ geom, GeomLayout gl, const doubl
 
 template <int DIM> __host__ __device__ constexpr int ipow3(int b) { return DIM == 2 ? b * b : b * b * b; }
 
-// One warp per CSR row A: the element-matrix rows of the elements containing A
-// (e2, e1, e0 ascending), read from the packed upper triangle, summed at the
-// columns' positions in shared memory; then w_A w_B and the Dirichlet rows/columns.
+// One warp per CSR row A.  For every element containing A (e2, e1, e0 ascending) the
+// warp reads that element's row a(A) -- (min(a,b), max(a,b)) of the packed triangle --
+// and adds each value into the row accumulator in shared memory at its column's
+// position; within one element the columns are distinct, so every entry is summed in
+// element order.  The finished row (weights, Dirichlet rows/columns) is written
+// contiguously.
 template <int DIM, int P>
-__global__ void __launch_bounds__(256) k_gather_sym(DirArgs d0, DirArgs d1, DirArgs d2, const float *__restrict__ E,
-                                                    const int *__restrict__ slot_of_elem, int Np,
-                                                    const int64_t *__restrict__ rowptr, const double *__restrict__ wts,
-                                                    BndArgs bnd, float *__restrict__ vals, int64_t N) {
+__global__ void __launch_bounds__(256) k_gather_el(DirArgs d0, DirArgs d1, DirArgs d2, const float *__restrict__ E, int Np,
+                                                   const int *__restrict__ slot_of_elem, const int64_t *__restrict__ rowptr,
+                                                   const double *__restrict__ wts, BndArgs bnd, float *__restrict__ vals, int64_t N) {
   constexpr int N1 = P + 1, NEN = ipow3<DIM>(N1), RMAX = ipow3<DIM>(2 * P + 1);
   __shared__ float rowacc[8][RMAX];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -329,18 +343,18 @@ __global__ void __launch_bounds__(256) k_gather_sym(DirArgs d0, DirArgs d1, DirA
         const int64_t e = e0 + (int64_t)d0.nel * (e1 + (int64_t)d1.nel * e2);
         const int a = (I[0] - f0) + N1 * ((I[1] - f1) + N1 * (I[2] - f2));
         const float *Er = E + (size_t)slot_of_elem[e] * Np;
-        for (int bb = lane; bb < NEN; bb += 32) {
-          const int lo = a < bb ? a : bb, hi = a < bb ? bb : a;
-          const int pk = lo * NEN - lo * (lo - 1) / 2 + (hi - lo);
-          const int b0 = bb % N1, b1 = (bb / N1) % N1, b2 = (DIM == 3) ? bb / (N1 * N1) : 0;
+        for (int b = lane; b < NEN; b += 32) {
+          const int b0 = b % N1, b1 = (b / N1) % N1, b2 = (DIM == 3) ? b / (N1 * N1) : 0;
           const int pos = ((f2 + b2 - l[2]) * w[1] + (f1 + b1 - l[1])) * w[0] + (f0 + b0 - l[0]);
-          acc[pos] += Er[pk];
+          const int lo = a < b ? a : b, hi = a < b ? b : a;
+          acc[pos] += Er[lo * NEN - lo * (lo - 1) / 2 + (hi - lo)];
         }
         __syncwarp();
       }
     }
   }
   bool rowfix = false;
+#pragma unroll
   for (int ax = 0; ax < DIM; ax++) rowfix |= (bnd.flag[ax][0] && I[ax] == 0) || (bnd.flag[ax][1] && I[ax] == n[ax] - 1);
   const float wA = wts ? (float)wts[A] : 1.f;
   const int64_t r0 = rowptr[A];
@@ -350,6 +364,7 @@ __global__ void __launch_bounds__(256) k_gather_sym(DirArgs d0, DirArgs d1, DirA
     float v = acc[k];
     if (wts) v *= wA * (float)wts[B];
     bool colfix = false;
+#pragma unroll
     for (int ax = 0; ax < DIM; ax++) colfix |= (bnd.flag[ax][0] && J[ax] == 0) || (bnd.flag[ax][1] && J[ax] == n[ax] - 1);
     if (rowfix || colfix) v = (A == B) ? 1.f : 0.f;
     vals[r0 + k] = v;
@@ -413,7 +428,7 @@ static cudaError_t elem_gemm_prepare(iga_s *h) {
   P->general = (h->has_geom || h->has_w) ? 1 : 0;
   const Slots S = make_slots(dim, P->general != 0);
   P->Kp = (S.n * P->nq + 63) / 64 * 64;
-  P->nsym = nen * (nen + 1) / 2;
+  P->nsym = nen * (nen + 1) / 2;  // the upper triangle a <= b, row by row
   P->n_tiles = (P->nsym + GT - 1) / GT;
   P->Np = P->n_tiles * GT;
   // types and tiles
@@ -446,7 +461,11 @@ static cudaError_t elem_gemm_prepare(iga_s *h) {
     const int64_t t = type_of(e);
     slot[e] = (int)next[t]++;
   }
-  // work groups: up to EG_GROUP consecutive m-tiles of one type share the T tile
+  // work groups: up to G consecutive m-tiles of one type share the T tile; G as large
+  // as keeps about two waves of CTAs (three per SM) on the GPU
+  int nsm = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t EG_GROUP = std::max<int64_t>(1, std::min<int64_t>(EG_GROUP_MAX, m_tiles * P->n_tiles / (2 * 3 * (int64_t)nsm)));
   for (int64_t t = 0; t < ntypes; t++) {
     const int t0 = (int)(t % nt0), t1 = (int)((t / nt0) % nt1), t2 = (int)(t / ((int64_t)nt0 * nt1));
     const int64_t m0 = first_slot[t] / GT, m1 = (first_slot[t] + count[t] + GT - 1) / GT;
@@ -529,16 +548,17 @@ cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, in
   void *Qv = nullptr;
   if ((ce = qv_buffer(h, op, &Qv))) return ce;
   h->q00_valid = false;
-  if ((ce = launch_q00(h, U, 1.0, 1.0))) return ce;
-  const int64_t tot = h->nelem * P->nq;
-  const unsigned gq = (unsigned)((tot + 255) / 256);
-  if (h->dim == 3) {
-    if (op == EG_BF16) IGA_LAUNCH(h, KC_ELEM_TC, (k_qv<3, EG_BF16><<<gq, 256, 0, h->stream>>>(h->geom, h->gl, h->Q00, P->slot_of_elem, Qv, P->Kp, P->nq, P->general, h->nelem)));
-    else IGA_LAUNCH(h, KC_ELEM_TC, (k_qv<3, EG_TF32><<<gq, 256, 0, h->stream>>>(h->geom, h->gl, h->Q00, P->slot_of_elem, Qv, P->Kp, P->nq, P->general, h->nelem)));
-  } else {
-    if (op == EG_BF16) IGA_LAUNCH(h, KC_ELEM_TC, (k_qv<2, EG_BF16><<<gq, 256, 0, h->stream>>>(h->geom, h->gl, h->Q00, P->slot_of_elem, Qv, P->Kp, P->nq, P->general, h->nelem)));
-    else IGA_LAUNCH(h, KC_ELEM_TC, (k_qv<2, EG_TF32><<<gq, 256, 0, h->stream>>>(h->geom, h->gl, h->Q00, P->slot_of_elem, Qv, P->Kp, P->nq, P->general, h->nelem)));
-  }
+  DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
+  IGA_LAUNCH(h, KC_Q00, EG_DISPATCH(h->dim, h->p, ({
+    using IS = InterpF32<D, PP>;
+    const unsigned gq = (unsigned)((h->nelem + IS::EB - 1) / IS::EB);
+    if (op == EG_BF16)
+      k_qv<D, PP, EG_BF16><<<gq, IS::THREADS, 0, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, (float)h->lambda,
+                                                              P->slot_of_elem, Qv, P->Kp, P->general, h->nelem);
+    else
+      k_qv<D, PP, EG_TF32><<<gq, IS::THREADS, 0, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, (float)h->lambda,
+                                                              P->slot_of_elem, Qv, P->Kp, P->general, h->nelem);
+  })));
   GemmArgs g;
   g.Qv = Qv;
   g.E = P->E;
@@ -552,6 +572,7 @@ cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, in
   g.Kp = P->Kp;
   g.Np = P->Np;
   g.n_tiles = P->n_tiles;
+  g.m_tiles = P->m_tiles;
   g.general = P->general;
   g.err = P->err;
   const size_t smem = eg_smem(P->Kp * (op == EG_BF16 ? 2 : 4) / KB);
@@ -564,10 +585,9 @@ cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, in
     IGA_LAUNCH(h, KC_ELEM_TC, (k_elem_gemm<EG_TF32><<<grid, 128, smem, h->stream>>>(g)));
   }
   if ((ce = cudaGetLastError())) return ce;
-  DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
   const unsigned gg = (unsigned)((h->N * 32 + 255) / 256);
-  IGA_LAUNCH(h, KC_ELEM_GATHER, EG_DISPATCH(h->dim, h->p, (k_gather_sym<D, PP><<<gg, 256, 0, h->stream>>>(
-                                                              a0, a1, a2, P->E, P->slot_of_elem, P->Np, h->rowptr, h->weights,
+  IGA_LAUNCH(h, KC_ELEM_GATHER, EG_DISPATCH(h->dim, h->p, (k_gather_el<D, PP><<<gg, 256, 0, h->stream>>>(
+                                                              a0, a1, a2, P->E, P->Np, P->slot_of_elem, h->rowptr, h->weights,
                                                               h->bnd, vals, h->N))));
   return cudaGetLastError();
 }

@@ -14,6 +14,7 @@
 #include <stdint.h>
 
 #include "iga_internal.h"
+#include "iga_interp.h"
 
 DirArgs dir_args(const DirDev &d) {
   DirArgs a;
@@ -770,6 +771,41 @@ cudaError_t launch_q00(iga_s *h, const double *U, double cs, double cr) {
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_q00<D, PP, NE, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_q00<D, PP, NE, 0><<<grid, 128, sm, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, h->lambda, cs, cr, h->Q00, h->nelem,
                                                       nullptr, h->ts_on ? h->ts_a : 0.0);
+  })));
+  return cudaGetLastError();
+}
+
+// Q00 in FP32 arithmetic for the reduced-precision Jacobians (same definition as
+// k_q00 MODE 0), stored as double.
+template <int DIM, int P>
+__global__ void __launch_bounds__(128) k_q00_f32(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ U,
+                                                 const double *__restrict__ wts, const double *__restrict__ geom, GeomLayout gl,
+                                                 float lambda, float cs, float cr, float shift, double *__restrict__ Q00,
+                                                 int64_t nelem) {
+  using S = InterpF32<DIM, P>;
+  __shared__ float ue[S::EB * S::NEN], tb[S::EB * DIM * S::Q * S::N1];
+  const int64_t e_first = (int64_t)blockIdx.x * S::EB;
+  const float ut = interp_u_block<DIM, P>(d0, d1, d2, cr != 0.f ? U : nullptr, wts, e_first, nelem, ue, tb);
+  const int le = threadIdx.x / S::NQ, qp = threadIdx.x - le * S::NQ;
+  const int64_t e = e_first + le;
+  if (le >= S::EB || e >= nelem) return;
+  const double *rec = geom + (size_t)e * gl.nf * S::NQ + qp;
+  float v = cs != 0.f ? cs * (float)rec[gl.gSg * S::NQ] : 0.f;
+  if (cr != 0.f) {
+    const float jw2 = (float)rec[gl.jwW2 * S::NQ];
+    v -= cr * jw2 * lambda * __expf(ut * (float)rec[gl.invW * S::NQ]);
+    if (shift != 0.f) v += cr * shift * jw2;
+  }
+  Q00[(size_t)e * S::NQ + qp] = (double)v;
+}
+
+cudaError_t launch_q00_f32(iga_s *h, const double *U, double cs, double cr) {
+  DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
+  IGA_LAUNCH(h, KC_Q00, DISPATCH_DP(h->dim, h->p, ({
+    using S = InterpF32<D, PP>;
+    const unsigned grid = (unsigned)((h->nelem + S::EB - 1) / S::EB);
+    k_q00_f32<D, PP><<<grid, S::THREADS, 0, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, (float)h->lambda, (float)cs,
+                                                         (float)cr, h->ts_on ? (float)h->ts_a : 0.f, h->Q00, h->nelem);
   })));
   return cudaGetLastError();
 }

@@ -222,6 +222,8 @@ cudaError_t launch_colidx(iga_s *h);
 cudaError_t launch_residual(iga_s *h, const double *U, double *F);
 // Q00 = cs * g^T S g - cr * jw/W^2 * lambda * exp(u) at every Gauss point (U may be null when cr == 0)
 cudaError_t launch_q00(iga_s *h, const double *U, double cs, double cr);
+// the same Q00 computed in FP32 arithmetic (stored as double), for the FP32 Jacobian
+cudaError_t launch_q00_f32(iga_s *h, const double *U, double cs, double cr);
 // Matrix-free Jacobian: y = J(U) x and diag(J(U)), with h->Q00 holding the reaction
 // part of Q00 at U (launch_q00(h, U, 0, 1)); done may be null
 cudaError_t launch_jv(iga_s *h, const double *x, double *y, const double *done);

@@ -355,7 +355,8 @@ cudaError_t jacobian(iga_s *h, const double *U, V *vals, int mode, const V *base
   double cs = (mode == 2) ? 0.0 : 1.0, cr = (mode == 1) ? 0.0 : 1.0;
   // mode 2 after an accepted split-residual evaluation at this U: Q00 is already there
   if (!(mode == 2 && h->q00_valid)) {
-    cudaError_t ce = launch_q00(h, U, cs, cr);
+    // the FP32 Jacobian takes its reaction coefficient from FP32 arithmetic too
+    cudaError_t ce = sizeof(T) == 4 ? launch_q00_f32(h, U, cs, cr) : launch_q00(h, U, cs, cr);
     if (ce) return ce;
   }
   h->q00_valid = false;
