@@ -436,7 +436,19 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
     h->K_valid_f = false;
   }
   h->q00_valid = false;
-  CK(launch_residual(h, U, F));
+  if (split) {
+    // the stiffness first, so that every residual of the solve is K U + reaction(U); the
+    // reaction pass leaves Q00 at U for the first Jacobian
+    if (!h->Kstiff) CK(cudaMalloc((void **)&h->Kstiff, h->nnz * sizeof(double)));
+    if (!h->K_valid) {
+      CK(launch_jacobian64(h, nullptr, h->Kstiff, 1, nullptr));
+      h->K_valid = true;
+    }
+    CK(launch_residual_split(h, U, F, h->Kstiff, h->wk + 7 * N));
+    h->q00_valid = true;
+  } else {
+    CK(launch_residual(h, U, F));
+  }
   double fn;
   st = norm_host(h, F, &fn);
   if (st != IGA_OK) return st;
