@@ -17,6 +17,10 @@ assembly or solver arithmetic.
   homogeneous coordinates and refined by inserting the interior knots of a
   uniform open knot vector one at a time (Boehm's algorithm), the geometry
   preparation the paper does with igakit (Sec. 2.9).
+* ``ring``: a closed annular ring for a periodic angular direction: uniform B-spline
+  control points on circles (radius at the radial Greville abscissae, angles
+  2 pi j / n for the n wrapped angular functions), weights 1; optionally extruded in
+  z.  A smooth closed approximation of the circle, positively oriented.
 * ``grf_log_kappa``: a Gaussian random field with a separable squared-exponential
   covariance on the control grid's Greville abscissae, sampled by Cholesky.
 * ``batch_instances``: the draw of the heterogeneous batched workload.
@@ -143,6 +147,27 @@ def quarter_annulus(nel, degree=3, r_in=1.0, r_out=2.0, height=1.0):
     ctrl[..., 2] = z[:, None, None]
     weights = np.broadcast_to(wth[None, :, None], (n2, n1, n0)).copy()
     return [Ur, Uth, Uz], ctrl.reshape(-1, 3), weights.reshape(-1)
+
+
+def ring(nel_r, nel_t, p, r_in=1.0, r_out=2.0, nel_z=None, height=1.0):
+    """Open knot vectors (radial, angular[, axial]) and control points (N, dim) of a ring
+    whose angular direction (axis 1) is meant to be C^(p-1) periodic: nel_t wrapped
+    angular functions with control points at angles 2 pi j / nel_t (natural order,
+    axis 0 fastest)."""
+    kr = uniform_open_knots(nel_r, p)
+    kt = uniform_open_knots(nel_t, p)
+    r = r_in + (r_out - r_in) * greville(kr, p)
+    th = 2.0 * math.pi * np.arange(nel_t) / nel_t
+    if nel_z is None:
+        X = np.stack([np.outer(np.cos(th), r), np.outer(np.sin(th), r)], axis=-1)  # [j][i][2]
+        return [kr, kt], X.reshape(-1, 2)
+    kz = uniform_open_knots(nel_z, p)
+    z = height * greville(kz, p)
+    X = np.zeros((len(z), nel_t, len(r), 3))
+    X[..., 0] = np.cos(th)[None, :, None] * r[None, None, :]
+    X[..., 1] = np.sin(th)[None, :, None] * r[None, None, :]
+    X[..., 2] = z[:, None, None]
+    return [kr, kt, kz], X.reshape(-1, 3)
 
 
 def greville(U, p):
