@@ -52,6 +52,9 @@ def test_build_targets_sm103a_only():
     (dict(dim=2, degree=2, nel=2, ctrl=np.full((16, 2), np.nan)), "finite"),
     (dict(dim=2, degree=2, nel=2, log_kappa=np.full(16, np.inf)), "finite"),
     (dict(dim=2, degree=2, knots=[np.array([0, 0, 0, .5, .5, .5, 1, 1, 1.]), None], nel=4), "multiplicity"),
+    (dict(dim=2, degree=2, nel=4, periodic={0: 2}), "periodic"),           # C^k with k > p - 1
+    (dict(dim=2, degree=2, nel=[1, 4], periodic={0: 1}), "unclamp"),      # n - k < k + 1
+    (dict(dim=2, degree=2, knots=[np.array([0, 0, .2, .5, 1, 1, 1.]), None], nel=4, periodic={0: 1}), "open"),
 ])
 def test_invalid_descriptions_rejected_before_any_device_work(lib, kwargs, needle):
     with pytest.raises(lib.IgaError) as ei:
@@ -75,3 +78,36 @@ def test_nn_shapes_outside_the_compiled_convolutions_rejected(lib, cin, hidden):
     rc = L.iga_nn_create(8, 8, cin, hidden, 3, dil, 4, 0, None, ctypes.byref(h))
     assert rc == lib.IGA_EINVAL and not h.value
     assert b"hidden" in L.iga_nn_last_error(None)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the sizes and field offsets that a C
+    compiler gives the header's structures (gcc, host ABI)."""
+    import ctypes
+    from paper_1305_4452_gb300 import iga
+    structs = {
+        "iga_desc": (iga.IgaDesc, ["dim", "degree", "nel", "continuity", "knots", "nknots", "quad", "ctrl", "weights",
+                                   "periodic"]),
+        "iga_bratu": (iga.IgaBratu, [("lam", "lambda"), "log_kappa"]),
+        "iga_newton_opts": (iga.IgaNewtonOpts, ["atol", "max_newton", "gmres_restart", "max_krylov", "krylov_rtol", "jac",
+                                                "reuse_stiffness", "ksp"]),
+        "iga_newton_report": (iga.IgaNewtonReport, ["newton_its", "krylov_its", "fnorm0", "fnorm", "fnorm_hist", "status"]),
+        "iga_ts_opts": (iga.IgaTsOpts, ["dt", "rho_inf"]),
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "iga.h"', 'int main(void) {']
+    for cname, (_, fields) in structs.items():
+        lines.append('  printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f in fields:
+            cf = f[1] if isinstance(f, tuple) else f
+            lines.append('  printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, cf, cname, cf))
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines())
+    for cname, (cls, fields) in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(cls), cname
+        for f in fields:
+            pf, cf = f if isinstance(f, tuple) else (f, f)
+            assert int(got["%s.%s" % (cname, cf)]) == getattr(cls, pf).offset, (cname, cf)
