@@ -55,6 +55,46 @@ def _ev(torch, fn, reps):
     return best
 
 
+# ------------------------------------------------------------------ oracle legs ---
+# Each line carries "cpu_baseline": the oracle (plain C / numpy, one thread) timed on this
+# host on a bounded sample of the line's workload, scaled to the line's unit; it is a
+# reported baseline, not a target.
+
+def _oracle_loop(fn, min_seconds):
+    import oracle as O
+    O.build()
+    fn()  # first call outside the clock (pattern caches, page-in)
+    t0, n = time.perf_counter(), 0
+    while n == 0 or time.perf_counter() - t0 < min_seconds:
+        fn()
+        n += 1
+    return (time.perf_counter() - t0) / n, n
+
+
+def _baseline(value, unit, sample, reps, seconds):
+    return {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
+            "sample": "%s; %d repetitions in %.1f s" % (sample, reps, seconds)}
+
+
+def _oracle_assembly_block(W, dim, p, sub, periodic=None, geom=None, lam=2.0, min_seconds=3.0):
+    """Seconds per element of the oracle's residual and of its Jacobian on a sub^dim block
+    (uniform cube, or the annulus with geom='annulus'; periodic axes as given)."""
+    import oracle as O
+    if geom == "annulus":
+        kn, ctrl, w = W.quarter_annulus(sub, p)
+    else:
+        kn, ctrl, w = [O.open_uniform_knots(sub, p)] * dim, None, None
+    per = periodic or {}
+    bc = {(a, s): 0.0 for a in range(dim) if a not in per for s in range(2)}
+    prob = O.Problem(kn, [p] * dim, ctrl=ctrl, weights=w, lam=lam, dirichlet=bc, periodic=per)
+    U = np.where(prob.dirichlet_mask(), 0.0, W.uniform(2, prob.N, -0.1, 0.1))
+    prob.pattern()
+    tr, nr = _oracle_loop(lambda: prob.residual(U), min_seconds / 2)
+    tj, nj = _oracle_loop(lambda: prob.jacobian(U), min_seconds / 2)
+    ne = float(sub ** dim)
+    return tr / ne, tj / ne, nr + nj, (tr * nr + tj * nj)
+
+
 def _line(metric_value, unit, workload, extra, clocks, hib=True, dtype="f64"):
     d = {"metric": METRIC, "value": metric_value, "unit": unit, "n_gpus": 1, "higher_is_better": hib,
          "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": {"workload": workload}}
@@ -82,10 +122,17 @@ def bratu16(torch, iga, W, clock):
         times.append(time.perf_counter() - t)
     ck = clock.stop()
     t = min(times)
+    import oracle as O
+    kn = O.open_uniform_knots(16, 2)
+    prob = O.Problem([kn, kn], [2, 2], lam=1.0, dirichlet=bc)
+    U0 = W.interior_field([18, 18], 1)
+    to, no = _oracle_loop(lambda: O.newton(prob, U0, atol=1e-10), 3.0)
+    cb = _baseline(1.0 / to, "solves/s", "oracle Newton (sparse LU per step) on the same 16x16 problem from the same U", no,
+                   to * no)
     return _line(1.0 / t, "solves/s", "bratu2d_16x16_p2_lambda1_fp64", {
         "residual_us": tr * 1e3, "jacobian_us": tj * 1e3, "jacobian_nnz_per_s": d.nnz / (tj * 1e-3),
         "newton": {"its": rep.newton_its, "krylov_its": rep.krylov_its, "fnorm": rep.fnorm},
-        "ms_per_solve": t * 1e3, "dofs": d.N, "nnz": d.nnz}, ck)
+        "ms_per_solve": t * 1e3, "dofs": d.N, "nnz": d.nnz, "cpu_baseline": cb}, ck)
 
 
 def cube_mixed(torch, iga, W, clock):
@@ -130,7 +177,11 @@ def cube_mixed(torch, iga, W, clock):
         torch.cuda.empty_cache()
     ck = clock.stop()
     v = out["cube128_p2"]["fp32_sumfact"]["nnz_per_s"]
-    return _line(v, "nnz/s", "cube_128cubed_p2_and_48cubed_p4_lambda2_mixed_jacobian", {"cases": out}, ck, dtype="f32")
+    _, tj, nr, sec = _oracle_assembly_block(W, 3, 2, 8)
+    cb = _baseline(out["cube128_p2"]["nnz"] / (tj * 128 ** 3), "nnz/s",
+                   "oracle FP64 Jacobian of an 8^3-element block of the p=2 cube, per element x 128^3", nr, sec)
+    return _line(v, "nnz/s", "cube_128cubed_p2_and_48cubed_p4_lambda2_mixed_jacobian", {"cases": out, "cpu_baseline": cb}, ck,
+                 dtype="f32")
 
 
 def batch512(torch, iga, W, clock):
@@ -161,8 +212,21 @@ def batch512(torch, iga, W, clock):
                       "max_fnorm": float(r["fnorm"].max())}
     ck = clock.stop()
     b.close()
+    import oracle as O
+    done, t_or, k = 0, 0.0, 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < 6.0 and k < len(ins):  # the seeded instances in order
+        x = ins[k]
+        kn = O.open_uniform_knots(x["nel"], x["p"])
+        prob = O.Problem([kn, kn], [x["p"]] * 2, lam=x["lam"], dirichlet={(a, s): 0.0 for a in range(2) for s in range(2)})
+        t = time.perf_counter()
+        O.newton(prob, np.zeros(prob.N), atol=1e-10)
+        t_or += time.perf_counter() - t
+        done, k = done + 1, k + 1
+    cb = _baseline(done / t_or, "solves/s", "oracle Newton (sparse LU) on the first %d of the 512 seeded instances, "
+                   "one at a time" % done, done, t_or)
     return _line(res["cg"]["solves_per_s"], "solves/s", "batch512_2d_n16to128_p2or3_lambda0.5to6_fp64res_fp32jac",
-                 {"results": res, "setup_s": setup, "total_dofs": int(b.total)}, ck)
+                 {"results": res, "setup_s": setup, "total_dofs": int(b.total), "cpu_baseline": cb}, ck)
 
 
 def learned64(torch, iga, W, clock, n_train=20000, n_test=2000, steps=16000):
@@ -231,6 +295,19 @@ def learned64(torch, iga, W, clock, n_train=20000, n_test=2000, steps=16000):
         "total_s": time.perf_counter() - t0,
     }
     net.close()
+    import oracle as O
+    kn = O.open_uniform_knots(nel, 2)
+    t_or, done = 0.0, 0
+    for ins in test[:64]:
+        prob = O.Problem([kn, kn], [2, 2], lam=ins["lam"], log_kappa=ins["log_kappa"], dirichlet=bc)
+        t = time.perf_counter()
+        O.newton(prob, np.zeros(prob.N), atol=1e-10)
+        t_or += time.perf_counter() - t
+        done += 1
+        if t_or > 6.0:
+            break
+    res["cpu_baseline"] = _baseline(done / t_or, "solves/s", "oracle Newton (sparse LU) from the zero start on the first "
+                                    "%d held-out fields" % done, done, t_or)
     return _line(res["nn_start"]["solves_per_s"], "solves/s", "kappa_bratu_64x64_p2_learned_initial_guess", {"results": res}, ck)
 
 
@@ -262,6 +339,12 @@ def nn64(torch, iga, W, clock, batch=64, reps=10):
     except Exception:
         peak, src = 1900.0, "fallback"
     ach = fwd_flops / (t_fwd * 1e-3) / 1e12
+    from oracle import nn_ref as R
+    shapes_r, _ = R.layer_shapes(4, 64, nn.DILATIONS)
+    params = net.get_params().astype(np.float64)
+    xs, ms = x[:2].double().cpu().numpy(), mask.double().cpu().numpy()
+    to, no = _oracle_loop(lambda: R.forward(params, shapes_r, xs, ms), 3.0)
+    cb = _baseline(2 / to, "fields/s", "numpy reference forward (FP64) of the same network on 2 of the fields", no, to * no)
     net.close()
     return _line(batch / (t_fwd * 1e-3), "fields/s", "neural_operator_66x66_6layers_64ch_batch%d_bf16" % batch, {
         "forward_ms": t_fwd, "train_step_ms": t_step, "forward_flops": fwd_flops,
@@ -270,7 +353,7 @@ def nn64(torch, iga, W, clock, batch=64, reps=10):
                      "unit": "TFLOP/s", "frac": ach / peak, "peak_source": src,
                      "note": "achieved = unpadded network FLOPs / forward time; the padded first and last layers run "
                              "%.1f%% more tensor-core FLOPs" % (100 * (tc_flops / fwd_flops - 1))},
-        "train_step_tflops": 3 * fwd_flops / (t_step * 1e-3) / 1e12}, ck, dtype="bf16")
+        "train_step_tflops": 3 * fwd_flops / (t_step * 1e-3) / 1e12, "cpu_baseline": cb}, ck, dtype="bf16")
 
 
 def fdjac(torch, iga, W, clock):
@@ -301,8 +384,16 @@ def fdjac(torch, iga, W, clock):
         torch.cuda.empty_cache()
     ck = clock.stop()
     big = out[5]
+    import oracle as O
+    kn = O.open_uniform_knots(8, 3)
+    prob = O.Problem([kn] * 3, [3] * 3, lam=2.0, dirichlet={(a, s): 0.0 for a in range(3) for s in range(2)})
+    U = np.where(prob.dirichlet_mask(), 0.0, W.uniform(4, prob.N, -0.1, 0.1))
+    prob.pattern()
+    to, no = _oracle_loop(lambda: prob.jacobian_fd(U), 4.0)
+    cb = _baseline(big["nnz"] / (to / 8 ** 3 * 64 ** 3), "nnz/s", "oracle local-ND Jacobian of an 8^3-element block of the "
+                   "p=3 cube, per element x 64^3 (the 64^3 p=3 case)", no, to * no)
     return _line(big["nnz"] / (big["local_nd_ms"] * 1e-3), "nnz/s", "bratu3d_cube_table3_cases_local_numerical_differentiation",
-                 {"cases": out}, ck)
+                 {"cases": out, "cpu_baseline": cb}, ck)
 
 
 def genalpha(torch, iga, W, clock, nel=64, steps=10, dt=0.01, rho=0.5):
@@ -329,8 +420,14 @@ def genalpha(torch, iga, W, clock, nel=64, steps=10, dt=0.01, rho=0.5):
                       "u_max_at_end": U.max().item(), "t_end": steps * dt}
     ck = clock.stop()
     d.close()
+    tr, tj, nr, sec = _oracle_assembly_block(W, 3, 3, 8, geom="annulus")
+    its = float(np.mean(out["fp64_gmres"]["newton_its"]))
+    t_step = (its * (tr + tj) + tr) * nel ** 3
+    cb = _baseline(1.0 / t_step, "time steps/s", "oracle residual+Jacobian of an 8^3-element annulus block, per element "
+                   "x 64^3, times the GPU's mean Newton steps per time step (%.1f); linear solves not counted" % its, nr, sec)
     return _line(out["fp64_gmres"]["steps_per_s"], "time steps/s",
-                 "transient_bratu_annulus64_p3_lambda2_genalpha_rho0.5_dt0.01", {"cases": out, "dofs": d.N}, ck)
+                 "transient_bratu_annulus64_p3_lambda2_genalpha_rho0.5_dt0.01", {"cases": out, "dofs": d.N,
+                                                                                "cpu_baseline": cb}, ck)
 
 
 def periodic64(torch, iga, W, clock, nel=64, p=3):
@@ -363,7 +460,12 @@ def periodic64(torch, iga, W, clock, nel=64, p=3):
         solves[label] = {"ms": best * 1e3, "newton_its": rep.newton_its, "krylov_its": rep.krylov_its, "fnorm": rep.fnorm}
     ck = clock.stop()
     d.close()
+    tr, tj, nr, sec = _oracle_assembly_block(W, 3, p, 8, periodic=per)
+    its = solves["fp64_gmres"]["newton_its"]
+    cb = _baseline(1.0 / ((its * (tr + tj) + tr) * nel ** 3), "solves/s", "oracle residual+Jacobian of an 8^3-element block "
+                   "periodic in x and y, per element x 64^3, times %d Newton steps; linear solves not counted" % its, nr, sec)
     return _line(1e3 / solves["fp64_gmres"]["ms"], "solves/s", "bratu3d_cube64_p3_periodic_xy_C2_lambda2_fp64", {
+        "cpu_baseline": cb,
         "dofs": d.N, "nnz": d.nnz, "residual_ms": tr, "jacobian_ms": tj, "jacobian_nnz_per_s": d.nnz / (tj * 1e-3),
         "jacobian_fold_ms": prof["combine"][0], "jacobian_unwrapped_stages_ms": prof["jac_stage1"][0] + prof["jac_stage2"][0] + prof["jac_final"][0],
         "newton": solves}, ck)
@@ -391,6 +493,9 @@ def mixed64(torch, iga, W, clock, nel=64, p=2):
                      "classes_ms": {k: round(v[0], 4) for k, v in prof.items() if v[0] > 0}}
     ck = clock.stop()
     d.close()
+    _, tj, nr, sec = _oracle_assembly_block(W, 3, p, 8)
+    res["cpu_baseline"] = _baseline(res["nnz"] / (tj * nel ** 3), "nnz/s", "oracle FP64 Jacobian of an 8^3-element block of "
+                                    "the p=2 cube, per element x 64^3", nr, sec)
     return _line(res["bf16_tensor"]["nnz_per_s"], "nnz/s", "cube_64cubed_p2_lambda2_reduced_precision_jacobian", {"cases": res}, ck,
                  dtype="bf16")
 

@@ -227,6 +227,48 @@ def test_full_size_cube_128_cubed_sampled():
     disc.close()
 
 
+@pytest.mark.slow
+def test_full_size_cube_48_cubed_quartic_sampled():
+    """3D unit cube, 48^3 quartic C^3, lambda = 2: pattern counts, sampled rows of F and of
+    the FP64 Jacobian at 1e-12, and of the BF16 element-GEMM Jacobian at the BF16 bound."""
+    I = iga()
+    disc, prob, n = make_pair(3, 4, 48, lam=2.0)
+    assert disc.N == 140608 and disc.nnz == 89915392
+    U0 = W.interior_field(n, seed=4)
+    U = torch.tensor(U0, device="cuda")
+    F = disc.form_residual(U).cpu().numpy()
+    rows = sample_rows(disc.N, 6, 79)
+    assert np.abs(F[rows] - prob.residual_rows(U0, rows)).max() <= TOL * np.abs(F).max()
+    rpo, _ = prob.pattern()
+    Jo = prob.jacobian_rows(U0, rows)
+    J = disc.form_jacobian(U)
+    Jg = np.concatenate([J[rpo[r]:rpo[r + 1]].cpu().numpy() for r in rows])
+    jscale = torch.abs(J).max().item()
+    assert np.abs(Jg - Jo).max() <= TOL * jscale
+    del J
+    Jb = disc.form_jacobian(U, prec=I.IGA_JAC_BF16)
+    Jbg = np.concatenate([Jb[rpo[r]:rpo[r + 1]].double().cpu().numpy() for r in rows])
+    assert np.linalg.norm(Jbg - Jo) <= 2e-2 * np.linalg.norm(Jo)
+    disc.close()
+
+
+@pytest.mark.slow
+def test_full_size_cube_128_cubed_bf16_element_gemm_sampled():
+    """128^3 quadratic: sampled rows of the BF16 tensor-core Jacobian against the oracle's
+    FP64 rows, within the BF16 bound."""
+    I = iga()
+    disc, prob, n = make_pair(3, 2, 128, lam=2.0)
+    U0 = W.interior_field(n, seed=3)
+    U = torch.tensor(U0, device="cuda")
+    Jb = disc.form_jacobian(U, prec=I.IGA_JAC_BF16)
+    rows = sample_rows(disc.N, 12, 80)
+    rpo, _ = prob.pattern()
+    Jbg = np.concatenate([Jb[rpo[r]:rpo[r + 1]].double().cpu().numpy() for r in rows])
+    Jo = prob.jacobian_rows(U0, rows)
+    assert np.linalg.norm(Jbg - Jo) <= 2e-2 * np.linalg.norm(Jo)
+    disc.close()
+
+
 @pytest.mark.parametrize("jac", ["fp64", "fp32"])
 def test_newton_cg_matches_gmres_solution(jac):
     I = iga()
