@@ -27,6 +27,11 @@
 //     them to the stage's barrier, which frees the stage two chunks later;
 //   - after the last chunk warp w reads accumulator rows 32w .. 32w+31 with
 //     tcgen05.ld and writes them to the element-matrix buffer E[slot][packed (a, b)].
+// T is the same for every element of a type, so its rounding error would perturb the
+// assembled matrix systematically (row sums of the stiffness part no longer vanish,
+// which slows Newton on fine meshes); where shared memory allows, T is kept as a
+// rounded part plus its rounded remainder and each chunk runs the MMAs on both with
+// the same Qv operand (about 16 significant bits for BF16, 21 for TF32).
 // Every barrier wait is bounded in time; the decision to stop is taken by thread 0
 // and shared through shared memory, so all threads leave the loop together.
 #include <cuda_bf16.h>
@@ -73,6 +78,7 @@ struct GemmArgs {
   const int *group;        // [ngroups][5]: first m-tile, m-tiles, element of the type per direction
   const int *pair_ab;      // [nsym]: a | b << 16, a <= b, row by row
   int dim, p, nq, nsym, Kp, Np, n_tiles, m_tiles, general;
+  int split;  // 1: T = T_hi + T_lo, both in the operand type (two MMAs per chunk on the same Qv)
   int *err;
 };
 
@@ -86,10 +92,12 @@ __device__ __forceinline__ uint32_t op_bits(float x, int op) {
   return r;
 }
 
-// Shared memory of k_elem_gemm: the T tile for the whole K (one STAGE per chunk),
-// two A stages, the 1D tables, the slot table, barriers and flags.
-__host__ __device__ constexpr size_t eg_smem(int nchunks) {
-  return (size_t)(nchunks + 2) * STAGE + 3 * 5 * 5 * 2 * sizeof(float) + 32 * sizeof(int) + 2 * sizeof(uint64_t) + 16;
+// Shared memory of k_elem_gemm: the T tile for the whole K (one STAGE per chunk; twice
+// with the split into a rounded part and its rounded remainder), two A stages, the 1D
+// tables, the slot table, barriers and flags.
+__host__ __device__ constexpr size_t eg_smem(int nchunks, int split) {
+  return (size_t)(nchunks * (1 + split) + 2) * STAGE + 3 * 5 * 5 * 2 * sizeof(float) + 32 * sizeof(int) +
+         2 * sizeof(uint64_t) + 16;
 }
 
 template <int OP>
@@ -99,8 +107,9 @@ __global__ void __launch_bounds__(128) k_elem_gemm(GemmArgs g) {
   constexpr int PER = 16 / ES;               // values per 16 bytes
   const int nchunks = g.Kp / KC;
   extern __shared__ __align__(128) uint8_t sm[];
-  uint8_t *Ts = sm;                                    // [nchunks][STAGE]
-  uint8_t *As = sm + (size_t)nchunks * STAGE;          // [2][STAGE]
+  uint8_t *Ts = sm;                                    // [nchunks][STAGE]  T rounded
+  uint8_t *Tl = sm + (size_t)nchunks * STAGE;          // [nchunks][STAGE]  remainder (split)
+  uint8_t *As = sm + (size_t)nchunks * (1 + g.split) * STAGE;  // [2][STAGE]
   float *tab = reinterpret_cast<float *>(As + 2 * STAGE);  // [3][q][p+1][2]
   int *smu = reinterpret_cast<int *>(tab + 3 * 5 * 5 * 2), *snu = smu + 16;
   uint64_t *done = reinterpret_cast<uint64_t *>(smu + 32);
@@ -158,9 +167,9 @@ __global__ void __launch_bounds__(128) k_elem_gemm(GemmArgs g) {
     const uint32_t rowoff = (uint32_t)((tid >> 3) * 128 + (tid & 7) * 16);
     int k = 0, sl = 0, qp = 0;  // running K index, its slot and Gauss point
     for (int c = 0; c < nchunks; c++) {
-      const uint32_t bdst = su32(Ts + (size_t)c * STAGE) + rowoff;
+      const uint32_t bdst = su32(Ts + (size_t)c * STAGE) + rowoff, ldst = su32(Tl + (size_t)c * STAGE) + rowoff;
       for (int kc = 0; kc < 8; kc++) {
-        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        uint32_t w[4] = {0u, 0u, 0u, 0u}, wl[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
         for (int j = 0; j < PER; j++, k++) {
           float v = 0.f;
@@ -181,12 +190,25 @@ __global__ void __launch_bounds__(128) k_elem_gemm(GemmArgs g) {
             sl++;
           }
           const uint32_t bits = op_bits(v, OP);
-          if (ES == 2) w[j >> 1] |= bits << (16 * (j & 1));
-          else w[j] = bits;
+          // the rounding error of T is the same in every element of the type: without the
+          // split it is a systematic perturbation of the assembled matrix
+          const float hv = ES == 2 ? __uint_as_float(bits << 16) : __uint_as_float(bits);
+          const uint32_t lbits = g.split ? op_bits(v - hv, OP) : 0u;
+          if (ES == 2) {
+            w[j >> 1] |= bits << (16 * (j & 1));
+            wl[j >> 1] |= lbits << (16 * (j & 1));
+          } else {
+            w[j] = bits;
+            wl[j] = lbits;
+          }
         }
         asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(bdst + kc * LBO), "r"(w[0]), "r"(w[1]), "r"(w[2]),
                      "r"(w[3])
                      : "memory");
+        if (g.split)
+          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ldst + kc * LBO), "r"(wl[0]), "r"(wl[1]), "r"(wl[2]),
+                       "r"(wl[3])
+                       : "memory");
       }
     }
 #undef TB
@@ -218,21 +240,24 @@ __global__ void __launch_bounds__(128) k_elem_gemm(GemmArgs g) {
       __syncthreads();
       if (tid == 0) {
         tc_fence_after();
-        const uint64_t ad = sdesc(su32(As + st * STAGE), LBO, 128), bd = sdesc(su32(Ts + (size_t)c * STAGE), LBO, 128);
+        const uint64_t ad = sdesc(su32(As + st * STAGE), LBO, 128);
+        for (int part = 0; part <= g.split; part++) {
+          const uint64_t bd = sdesc(su32((part ? Tl : Ts) + (size_t)c * STAGE), LBO, 128);
 #pragma unroll
-        for (int kk = 0; kk < 4; kk++) {
-          const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
-          const uint64_t a_k = ad + (uint64_t)((kk * 2 * LBO) >> 4), b_k = bd + (uint64_t)((kk * 2 * LBO) >> 4);
-          if constexpr (OP == EG_BF16)
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                "l"(a_k), "l"(b_k), "r"(idesc), "r"(acc)
-                : "memory");
-          else
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                "l"(a_k), "l"(b_k), "r"(idesc), "r"(acc)
-                : "memory");
+          for (int kk = 0; kk < 4; kk++) {
+            const uint32_t acc = (c > 0 || kk > 0 || part > 0) ? 1u : 0u;
+            const uint64_t a_k = ad + (uint64_t)((kk * 2 * LBO) >> 4), b_k = bd + (uint64_t)((kk * 2 * LBO) >> 4);
+            if constexpr (OP == EG_BF16)
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                  "l"(a_k), "l"(b_k), "r"(idesc), "r"(acc)
+                  : "memory");
+            else
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                  "l"(a_k), "l"(b_k), "r"(idesc), "r"(acc)
+                  : "memory");
+          }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(done + st))
                      : "memory");
@@ -534,7 +559,7 @@ static cudaError_t qv_buffer(iga_s *h, int op, void **out) {
 bool elem_gemm_supported(iga_s *h, int prec) {
   if (elem_gemm_prepare(h) != cudaSuccess) return false;
   const int es = prec == IGA_JAC_BF16 ? 2 : 4;
-  return eg_smem(h->egemm->Kp * es / KB) <= 200 * 1024;
+  return eg_smem(h->egemm->Kp * es / KB, 0) <= 200 * 1024;
 }
 
 // vals (FP32, CSR) = the Jacobian with BF16 (prec IGA_JAC_BF16) or TF32 element
@@ -575,7 +600,9 @@ cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, in
   g.m_tiles = P->m_tiles;
   g.general = P->general;
   g.err = P->err;
-  const size_t smem = eg_smem(P->Kp * (op == EG_BF16 ? 2 : 4) / KB);
+  const int nch = P->Kp * (op == EG_BF16 ? 2 : 4) / KB;
+  g.split = eg_smem(nch, 1) <= 200 * 1024 ? 1 : 0;
+  const size_t smem = eg_smem(nch, g.split);
   const unsigned grid = (unsigned)((int64_t)P->ngroups * P->n_tiles);
   if (op == EG_BF16) {
     cudaFuncSetAttribute(k_elem_gemm<EG_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

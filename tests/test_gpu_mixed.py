@@ -164,3 +164,23 @@ def test_newton_with_fp32_jacobian(I):
     rep = disc.solve_newton(U, o)
     assert rep.status == 0 and rep.fnorm <= 1e-10
     disc.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_element_gemm_newton_steps_on_a_fine_mesh(I, prec):
+    """On a fine uniform mesh a systematic rounding of the shared basis products would
+    slow Newton down; with the split constant operand Newton takes the FP64 step count
+    (+1) from the zero start."""
+    bc = bc_all(3)
+    steps = {}
+    for name, code in (("fp64", I.IGA_FP64), (prec, I.IGA_JAC_BF16 if prec == "bf16" else I.IGA_JAC_TF32)):
+        disc = I.Discretization(3, 2, nel=64, lam=2.0, dirichlet=bc)
+        U = torch.zeros(disc.N, dtype=torch.float64, device="cuda")
+        o = I.newton_defaults()
+        o.jac = code
+        rep = disc.solve_newton(U, o)
+        assert rep.status == 0
+        steps[name] = rep.newton_its
+        disc.close()
+    assert steps[prec] <= steps["fp64"] + 1, steps
