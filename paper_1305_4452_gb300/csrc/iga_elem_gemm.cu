@@ -73,11 +73,16 @@ __host__ __device__ inline Slots make_slots(int dim, bool general) {
 
 struct GemmArgs {
   const void *Qv;          // [slots_total][Kp] operand values (BF16, or TF32 in FP32 containers)
-  float *E;                // [slots_total][Np]
+  float *E;                // [nsym][N]: E_ab(e), a <= b, in slab pk(a, b) at column A(e, a)
+  const int *elem_of_slot; // [slots_total] element of each slot, -1 for padding
+  const int *first[3];     // first function of each element per direction
+  const int *pair_off;     // [nsym][2]: offsets of a and of b from the element's first function, natural order
+  int nel0, nel1;
+  int64_t N, N0, N1;        // functions in all, along x, along y
   const float *tab[3];     // FP32 1D tables [nel][q][p+1][2]
   const int *group;        // [ngroups][5]: first m-tile, m-tiles, element of the type per direction
   const int *pair_ab;      // [nsym]: a | b << 16, a <= b, row by row
-  int dim, p, nq, nsym, Kp, Np, n_tiles, m_tiles, general;
+  int dim, p, nq, nsym, nen, Kp, Np, n_tiles, m_tiles, general;
   int split;  // 1: T = T_hi + T_lo, both in the operand type (two MMAs per chunk on the same Qv)
   int *err;
 };
@@ -96,7 +101,7 @@ __device__ __forceinline__ uint32_t op_bits(float x, int op) {
 // with the split into a rounded part and its rounded remainder), two A stages, the 1D
 // tables, the slot table, barriers and flags.
 __host__ __device__ constexpr size_t eg_smem(int nchunks, int split) {
-  return (size_t)(nchunks * (1 + split) + 2) * STAGE + 3 * 5 * 5 * 2 * sizeof(float) + 32 * sizeof(int) +
+  return (size_t)(nchunks * (1 + split) + 2) * STAGE + 3 * 5 * 5 * 2 * sizeof(float) + (32 + 3 * GT) * sizeof(int) +
          2 * sizeof(uint64_t) + 16;
 }
 
@@ -112,7 +117,8 @@ __global__ void __launch_bounds__(128) k_elem_gemm(GemmArgs g) {
   uint8_t *As = sm + (size_t)nchunks * (1 + g.split) * STAGE;  // [2][STAGE]
   float *tab = reinterpret_cast<float *>(As + 2 * STAGE);  // [3][q][p+1][2]
   int *smu = reinterpret_cast<int *>(tab + 3 * 5 * 5 * 2), *snu = smu + 16;
-  uint64_t *done = reinterpret_cast<uint64_t *>(smu + 32);
+  int *spair = smu + 32;  // [GT][3]: this pair tile's (a | b << 16, offset of a, offset of b)
+  uint64_t *done = reinterpret_cast<uint64_t *>(spair + 3 * GT);
   uint32_t *slot = reinterpret_cast<uint32_t *>(done + 2);
   volatile int *abort_s = reinterpret_cast<volatile int *>(slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -140,6 +146,12 @@ __global__ void __launch_bounds__(128) k_elem_gemm(GemmArgs g) {
   for (int k = tid; k < 3 * tsz; k += blockDim.x) {
     const int ax = k / tsz, r = k - ax * tsz;
     tab[k] = ax < g.dim ? g.tab[ax][(size_t)g.group[grp * 5 + 2 + ax] * tsz + r] : (r % 2 == 0 ? 1.f : 0.f);
+  }
+  for (int c = tid; c < GT; c += blockDim.x) {
+    const int n = n_tile * GT + c;
+    spair[3 * c] = n < g.nsym ? g.pair_ab[n] : -1;
+    spair[3 * c + 1] = n < g.nsym ? g.pair_off[2 * n] : 0;
+    spair[3 * c + 2] = n < g.nsym ? g.pair_off[2 * n + 1] : 0;
   }
   tc_fence_before();
   __syncthreads();
@@ -270,14 +282,24 @@ __global__ void __launch_bounds__(128) k_elem_gemm(GemmArgs g) {
     __syncthreads();
     if (*abort_s) break;
     tc_fence_after();
+    // E_ab (a <= b) goes to slab pk(a, b) at column A(e, a): for consecutive elements
+    // along x the lanes write consecutive floats
     const int row = warp * 32 + lane;
-    float *dst = g.E + ((size_t)mt * GT + row) * g.Np + (size_t)n_tile * GT;
+    const int e = g.elem_of_slot[(size_t)mt * GT + row];
+    int64_t abase = 0;
+    if (e >= 0) {
+      const int e0 = e % g.nel0, e1 = (e / g.nel0) % g.nel1, e2 = g.dim == 3 ? e / (g.nel0 * g.nel1) : 0;
+      abase = g.first[0][e0] + g.N0 * ((int64_t)g.first[1][e1] + (int64_t)g.N1 * (g.dim == 3 ? g.first[2][e2] : 0));
+    }
     for (int c0 = 0; c0 < GT; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      float4 *d4 = reinterpret_cast<float4 *>(dst + c0);
+      if (e < 0) continue;
 #pragma unroll
-      for (int u = 0; u < 4; u++) d4[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+      for (int u = 0; u < 16; u++) {
+        if (spair[3 * (c0 + u)] < 0) break;
+        g.E[(size_t)(n_tile * GT + c0 + u) * g.N + abase + spair[3 * (c0 + u) + 1]] = v[u];
+      }
     }
     tc_fence_before();
     __syncthreads();  // the accumulator is read before the next m-tile's MMAs overwrite it
@@ -333,64 +355,82 @@ __global__ void __launch_bounds__(128) k_qv(DirArgs d0, DirArgs d1, DirArgs d2, 
 
 template <int DIM> __host__ __device__ constexpr int ipow3(int b) { return DIM == 2 ? b * b : b * b * b; }
 
-// One warp per CSR row A.  For every element containing A (e2, e1, e0 ascending) the
-// warp reads that element's row a(A) -- (min(a,b), max(a,b)) of the packed triangle --
-// and adds each value into the row accumulator in shared memory at its column's
-// position; within one element the columns are distinct, so every entry is summed in
-// element order.  The finished row (weights, Dirichlet rows/columns) is written
-// contiguously.
-template <int DIM, int P>
-__global__ void __launch_bounds__(256) k_gather_el(DirArgs d0, DirArgs d1, DirArgs d2, const float *__restrict__ E, int Np,
-                                                   const int *__restrict__ slot_of_elem, const int64_t *__restrict__ rowptr,
-                                                   const double *__restrict__ wts, BndArgs bnd, float *__restrict__ vals, int64_t N) {
+// One thread per CSR row A (consecutive rows across a warp).  For every element e
+// containing A (e2, e1, e0 ascending), with a the local index of A in e, the row reads
+// E_ab for all b -- slab pk(a, b) at column A for b >= a, slab pk(b, a) at column A(e, b)
+// = A + off(b) - off(a) for b < a; both coalesced across the warp's rows -- and adds it
+// at the column of e's function b, in a per-thread accumulator in shared memory; then
+// w_A w_B and the Dirichlet rows and columns.
+template <int DIM, int P, int TPB>
+__global__ void __launch_bounds__(TPB) k_gather_rows(DirArgs d0, DirArgs d1, DirArgs d2, const float *__restrict__ E,
+                                                     const int64_t *__restrict__ rowptr, const double *__restrict__ wts,
+                                                     BndArgs bnd, float *__restrict__ vals, int64_t N) {
   constexpr int N1 = P + 1, NEN = ipow3<DIM>(N1), RMAX = ipow3<DIM>(2 * P + 1);
-  __shared__ float rowacc[8][RMAX];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t A = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  extern __shared__ float acc_all[];  // [RMAX][TPB]
+  const int t = threadIdx.x;
+  const int64_t A = (int64_t)blockIdx.x * TPB + t;
   if (A >= N) return;
-  float *acc = rowacc[warp];
-  int I[3] = {(int)(A % d0.n), (int)((A / d0.n) % d1.n), (DIM == 3) ? (int)(A / ((int64_t)d0.n * d1.n)) : 0};
-  int n[3] = {d0.n, d1.n, d2.n};
-  int l[3] = {d0.l[I[0]], d1.l[I[1]], DIM == 3 ? d2.l[I[2]] : 0};
-  int w[3] = {d0.r[I[0]] - l[0] + 1, d1.r[I[1]] - l[1] + 1, DIM == 3 ? d2.r[I[2]] - l[2] + 1 : 1};
-  const int len = w[0] * w[1] * w[2];
-  for (int k = lane; k < len; k += 32) acc[k] = 0.f;
-  __syncwarp();
-  const int lo2 = (DIM == 3) ? d2.node_e0[I[2]] : 0, hi2 = (DIM == 3) ? lo2 + d2.node_ne[I[2]] : 1;
-  const int lo1 = d1.node_e0[I[1]], hi1 = lo1 + d1.node_ne[I[1]];
-  const int lo0 = d0.node_e0[I[0]], hi0 = lo0 + d0.node_ne[I[0]];
+  float *acc = acc_all + t;
+  const int I0 = (int)(A % d0.n), I1 = (int)((A / d0.n) % d1.n), I2 = (DIM == 3) ? (int)(A / ((int64_t)d0.n * d1.n)) : 0;
+  const int l0 = d0.l[I0], l1 = d1.l[I1], l2 = DIM == 3 ? d2.l[I2] : 0;
+  const int w0 = d0.r[I0] - l0 + 1, w1 = d1.r[I1] - l1 + 1, w2 = DIM == 3 ? d2.r[I2] - l2 + 1 : 1;
+  const int len = w0 * w1 * w2;
+  for (int k = 0; k < len; k++) acc[k * TPB] = 0.f;
+  const int lo2 = (DIM == 3) ? d2.node_e0[I2] : 0, hi2 = (DIM == 3) ? lo2 + d2.node_ne[I2] : 1;
+  const int lo1 = d1.node_e0[I1], hi1 = lo1 + d1.node_ne[I1];
+  const int lo0 = d0.node_e0[I0], hi0 = lo0 + d0.node_ne[I0];
   for (int e2 = lo2; e2 < hi2; e2++) {
     const int f2 = (DIM == 3) ? d2.first[e2] : 0;
     for (int e1 = lo1; e1 < hi1; e1++) {
       const int f1 = d1.first[e1];
       for (int e0 = lo0; e0 < hi0; e0++) {
         const int f0 = d0.first[e0];
-        const int64_t e = e0 + (int64_t)d0.nel * (e1 + (int64_t)d1.nel * e2);
-        const int a = (I[0] - f0) + N1 * ((I[1] - f1) + N1 * (I[2] - f2));
-        const float *Er = E + (size_t)slot_of_elem[e] * Np;
-        for (int b = lane; b < NEN; b += 32) {
-          const int b0 = b % N1, b1 = (b / N1) % N1, b2 = (DIM == 3) ? b / (N1 * N1) : 0;
-          const int pos = ((f2 + b2 - l[2]) * w[1] + (f1 + b1 - l[1])) * w[0] + (f0 + b0 - l[0]);
-          const int lo = a < b ? a : b, hi = a < b ? b : a;
-          acc[pos] += Er[lo * NEN - lo * (lo - 1) / 2 + (hi - lo)];
+        const int a = (I0 - f0) + N1 * ((I1 - f1) + N1 * (I2 - f2));
+        const int a0 = I0 - f0, a1 = I1 - f1, a2 = I2 - f2;
+        const int64_t offa = a0 + (int64_t)d0.n * (a1 + (int64_t)d1.n * a2);
+        const int base = ((f2 - l2) * w1 + (f1 - l1)) * w0 + (f0 - l0);
+        // the element's NEN values are loaded before any is added: independent loads in flight
+        constexpr int CH = NEN <= 64 ? NEN : 25;
+        for (int b0c = 0; b0c < NEN; b0c += CH) {
+          float ev[CH];
+#pragma unroll
+          for (int u = 0; u < CH; u++) {
+            const int b = b0c + u;
+            float x = 0.f;
+            if (b < NEN) {
+              const int lo = a < b ? a : b, hi = a < b ? b : a;
+              const int pk = lo * NEN - lo * (lo - 1) / 2 + (hi - lo);
+              const int b0 = b % N1, b1 = (b / N1) % N1, b2 = (DIM == 3) ? b / (N1 * N1) : 0;
+              const int64_t col = b >= a ? A : A + (b0 + (int64_t)d0.n * (b1 + (int64_t)d1.n * b2)) - offa;
+              x = __ldg(E + (size_t)pk * N + col);
+            }
+            ev[u] = x;
+          }
+#pragma unroll
+          for (int u = 0; u < CH; u++) {
+            const int b = b0c + u;
+            if (b >= NEN) break;
+            const int b0 = b % N1, b1 = (b / N1) % N1, b2 = (DIM == 3) ? b / (N1 * N1) : 0;
+            const int pos = base + (b2 * w1 + b1) * w0 + b0;
+            acc[pos * TPB] += ev[u];
+          }
         }
-        __syncwarp();
       }
     }
   }
-  bool rowfix = false;
-#pragma unroll
-  for (int ax = 0; ax < DIM; ax++) rowfix |= (bnd.flag[ax][0] && I[ax] == 0) || (bnd.flag[ax][1] && I[ax] == n[ax] - 1);
+  bool rowfix = (bnd.flag[0][0] && I0 == 0) || (bnd.flag[0][1] && I0 == d0.n - 1) || (bnd.flag[1][0] && I1 == 0) ||
+                (bnd.flag[1][1] && I1 == d1.n - 1);
+  if (DIM == 3) rowfix |= (bnd.flag[2][0] && I2 == 0) || (bnd.flag[2][1] && I2 == d2.n - 1);
   const float wA = wts ? (float)wts[A] : 1.f;
   const int64_t r0 = rowptr[A];
-  for (int k = lane; k < len; k += 32) {
-    int J[3] = {l[0] + k % w[0], l[1] + (k / w[0]) % w[1], l[2] + k / (w[0] * w[1])};
-    const int64_t B = J[0] + (int64_t)d0.n * (J[1] + (int64_t)d1.n * J[2]);
-    float v = acc[k];
+  for (int k = 0; k < len; k++) {
+    const int J0 = l0 + k % w0, J1 = l1 + (k / w0) % w1, J2 = l2 + k / (w0 * w1);
+    const int64_t B = J0 + (int64_t)d0.n * (J1 + (int64_t)d1.n * J2);
+    bool colfix = (bnd.flag[0][0] && J0 == 0) || (bnd.flag[0][1] && J0 == d0.n - 1) || (bnd.flag[1][0] && J1 == 0) ||
+                  (bnd.flag[1][1] && J1 == d1.n - 1);
+    if (DIM == 3) colfix |= (bnd.flag[2][0] && J2 == 0) || (bnd.flag[2][1] && J2 == d2.n - 1);
+    float v = acc[k * TPB];
     if (wts) v *= wA * (float)wts[B];
-    bool colfix = false;
-#pragma unroll
-    for (int ax = 0; ax < DIM; ax++) colfix |= (bnd.flag[ax][0] && J[ax] == 0) || (bnd.flag[ax][1] && J[ax] == n[ax] - 1);
     if (rowfix || colfix) v = (A == B) ? 1.f : 0.f;
     vals[r0 + k] = v;
   }
@@ -405,7 +445,8 @@ struct ElemGemmPlan {
   bool ok = false;
   int general = 0, nq = 0, nsym = 0, Kp = 0, Np = 0, n_tiles = 0, m_tiles = 0, es = 2;
   int ngroups = 0;
-  int *slot_of_elem = nullptr, *group = nullptr, *pair_ab = nullptr, *err = nullptr;
+  int *slot_of_elem = nullptr, *elem_of_slot = nullptr, *group = nullptr, *pair_ab = nullptr, *pair_off = nullptr,
+      *err = nullptr;
   void *Qv[2] = {nullptr, nullptr};  // BF16, TF32 operand buffers
   float *E = nullptr;
 };
@@ -431,7 +472,7 @@ static std::vector<int> dir_types(const Dir &D, std::vector<int> &rep) {
 }
 
 static void plan_free(ElemGemmPlan *P) {
-  void *ps[] = {P->slot_of_elem, P->group, P->pair_ab, P->err, P->Qv[0], P->Qv[1], P->E};
+  void *ps[] = {P->slot_of_elem, P->elem_of_slot, P->group, P->pair_ab, P->pair_off, P->err, P->Qv[0], P->Qv[1], P->E};
   for (void *p : ps)
     if (p) cudaFree(p);
 }
@@ -503,9 +544,20 @@ static cudaError_t elem_gemm_prepare(iga_s *h) {
     }
   }
   P->ngroups = (int)(groups.size() / 5);
-  std::vector<int> pairs;
+  std::vector<int> pairs, poff;
+  const int64_t n0f = h->dir[0].n, n1f = h->dir[1].n;
+  auto off = [&](int a) {
+    const int a0 = a % n1, a1 = (a / n1) % n1, a2 = dim == 3 ? a / (n1 * n1) : 0;
+    return (int)(a0 + n0f * (a1 + n1f * a2));
+  };
   for (int a = 0; a < nen; a++)
-    for (int b = a; b < nen; b++) pairs.push_back(a | (b << 16));
+    for (int b = a; b < nen; b++) {
+      pairs.push_back(a | (b << 16));
+      poff.push_back(off(a));
+      poff.push_back(off(b));
+    }
+  std::vector<int> eos((size_t)m_tiles * GT, -1);
+  for (int64_t e = 0; e < h->nelem; e++) eos[slot[e]] = (int)e;
   const size_t slots_total = (size_t)m_tiles * GT;
   cudaError_t ce;
   if ((ce = cudaMalloc((void **)&P->slot_of_elem, slot.size() * sizeof(int)))) return ce;
@@ -514,9 +566,13 @@ static cudaError_t elem_gemm_prepare(iga_s *h) {
   if ((ce = cudaMemcpy(P->group, groups.data(), groups.size() * sizeof(int), cudaMemcpyHostToDevice))) return ce;
   if ((ce = cudaMalloc((void **)&P->pair_ab, pairs.size() * sizeof(int)))) return ce;
   if ((ce = cudaMemcpy(P->pair_ab, pairs.data(), pairs.size() * sizeof(int), cudaMemcpyHostToDevice))) return ce;
+  if ((ce = cudaMalloc((void **)&P->pair_off, poff.size() * sizeof(int)))) return ce;
+  if ((ce = cudaMemcpy(P->pair_off, poff.data(), poff.size() * sizeof(int), cudaMemcpyHostToDevice))) return ce;
+  if ((ce = cudaMalloc((void **)&P->elem_of_slot, eos.size() * sizeof(int)))) return ce;
+  if ((ce = cudaMemcpy(P->elem_of_slot, eos.data(), eos.size() * sizeof(int), cudaMemcpyHostToDevice))) return ce;
   if ((ce = cudaMalloc((void **)&P->err, sizeof(int)))) return ce;
   if ((ce = cudaMemset(P->err, 0, sizeof(int)))) return ce;
-  if ((ce = cudaMalloc((void **)&P->E, slots_total * P->Np * sizeof(float)))) return ce;
+  if ((ce = cudaMalloc((void **)&P->E, (size_t)P->nsym * h->N * sizeof(float)))) return ce;
   (void)slots_total;
   P->ok = true;
   return cudaSuccess;
@@ -587,6 +643,15 @@ cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, in
   GemmArgs g;
   g.Qv = Qv;
   g.E = P->E;
+  g.elem_of_slot = P->elem_of_slot;
+  for (int ax = 0; ax < 3; ax++) g.first[ax] = ax < h->dim ? h->ddev[ax].first : nullptr;
+  g.pair_off = P->pair_off;
+  g.nel0 = h->dir[0].nel;
+  g.nel1 = h->dir[1].nel;
+  g.N = h->N;
+  g.N0 = h->dir[0].n;
+  g.N1 = h->dir[1].n;
+  g.nen = h->dim == 3 ? (h->p + 1) * (h->p + 1) * (h->p + 1) : (h->p + 1) * (h->p + 1);
   for (int ax = 0; ax < 3; ax++) g.tab[ax] = ax < h->dim ? h->tab32[ax] : nullptr;
   g.group = P->group;
   g.pair_ab = P->pair_ab;
@@ -612,10 +677,14 @@ cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, in
     IGA_LAUNCH(h, KC_ELEM_TC, (k_elem_gemm<EG_TF32><<<grid, 128, smem, h->stream>>>(g)));
   }
   if ((ce = cudaGetLastError())) return ce;
-  const unsigned gg = (unsigned)((h->N * 32 + 255) / 256);
-  IGA_LAUNCH(h, KC_ELEM_GATHER, EG_DISPATCH(h->dim, h->p, (k_gather_el<D, PP><<<gg, 256, 0, h->stream>>>(
-                                                              a0, a1, a2, P->E, P->Np, P->slot_of_elem, h->rowptr, h->weights,
-                                                              h->bnd, vals, h->N))));
+  IGA_LAUNCH(h, KC_ELEM_GATHER, EG_DISPATCH(h->dim, h->p, ({
+    constexpr int RMAX = ipow3<D>(2 * PP + 1);
+    constexpr int TPB = RMAX * 4 * 256 <= 96 * 1024 ? 256 : (RMAX * 4 * 128 <= 96 * 1024 ? 128 : (RMAX * 4 * 64 <= 96 * 1024 ? 64 : 32));
+    const size_t sm = (size_t)RMAX * TPB * sizeof(float);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_gather_rows<D, PP, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const unsigned gg = (unsigned)((h->N + TPB - 1) / TPB);
+    k_gather_rows<D, PP, TPB><<<gg, TPB, sm, h->stream>>>(a0, a1, a2, P->E, h->rowptr, h->weights, h->bnd, vals, h->N);
+  })));
   return cudaGetLastError();
 }
 
