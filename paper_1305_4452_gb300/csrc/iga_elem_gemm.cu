@@ -18,14 +18,16 @@
 // the pairs a <= b are formed, packed row by row.  Identity maps with unit
 // weights have g = 0 and a diagonal S, so only the DIM+1 slots mu = nu are nonzero.
 //
-// k_elem_gemm, one CTA per (128 elements, 128 pairs) tile, 128 threads:
-//   - every thread copies its element row of the Qv chunk (cp.async, 16 B) and
-//     computes its pair row of the T chunk from the tile type's 1D tables, into the
+// k_elem_gemm, one CTA per (128 elements, 128 pairs) tile and group of element tiles,
+// 256 threads:
+//   - two threads per row copy an element row of the Qv chunk (cp.async, 16 B) and
+//     compute a pair row of the T chunk from the tile type's 1D tables, into the
 //     canonical K-major layout without swizzling (8-row x 16-byte core matrices,
 //     128 B apart along M/N, 2 KB apart along K), two stages;
 //   - thread 0 issues the chunk's four tcgen05.mma (32 bytes of K each) and commits
 //     them to the stage's barrier, which frees the stage two chunks later;
-//   - after the last chunk warp w reads accumulator rows 32w .. 32w+31 with
+//   - after the last chunk warp w reads accumulator rows 32 (w % 4) .. + 31 (half the
+//     columns each) with
 //     tcgen05.ld and writes them to the element-matrix buffer E[slot][packed (a, b)].
 // T is the same for every element of a type, so its rounding error would perturb the
 // assembled matrix systematically (row sums of the stiffness part no longer vanish,
@@ -106,7 +108,7 @@ __host__ __device__ constexpr size_t eg_smem(int nchunks, int split) {
 }
 
 template <int OP>
-__global__ void __launch_bounds__(128) k_elem_gemm(GemmArgs g) {
+__global__ void __launch_bounds__(256) k_elem_gemm(GemmArgs g) {
   constexpr int ES = OP == EG_BF16 ? 2 : 4;  // operand bytes
   constexpr int KC = KB / ES;                // K values per chunk
   constexpr int PER = 16 / ES;               // values per 16 bytes
@@ -122,6 +124,7 @@ __global__ void __launch_bounds__(128) k_elem_gemm(GemmArgs g) {
   uint32_t *slot = reinterpret_cast<uint32_t *>(done + 2);
   volatile int *abort_s = reinterpret_cast<volatile int *>(slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r128 = tid & 127, half = tid >> 7;  // operand row of this thread, and which half of its 8 16-byte chunks
   const int grp = blockIdx.x / g.n_tiles, n_tile = blockIdx.x % g.n_tiles;
   const int m_first = g.group[grp * 5 + 0], m_count = g.group[grp * 5 + 1];
   const int q = g.p + 1, n1 = g.p + 1;
@@ -162,7 +165,7 @@ __global__ void __launch_bounds__(128) k_elem_gemm(GemmArgs g) {
 
   // ---- T tile of this pair range for the whole K, once per group ----
   {
-    const int npair = n_tile * GT + tid;
+    const int npair = n_tile * GT + r128;
     int a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0;
     const bool pvalid = npair < g.nsym;
     if (pvalid) {
@@ -176,11 +179,11 @@ __global__ void __launch_bounds__(128) k_elem_gemm(GemmArgs g) {
       b2 = g.dim == 3 ? ib / (n1 * n1) : 0;
     }
 #define TB(ax, gq, aa, s) tab[(((ax) * q + (gq)) * n1 + (aa)) * 2 + (s)]
-    const uint32_t rowoff = (uint32_t)((tid >> 3) * 128 + (tid & 7) * 16);
-    int k = 0, sl = 0, qp = 0;  // running K index, its slot and Gauss point
+    const uint32_t rowoff = (uint32_t)((r128 >> 3) * 128 + (r128 & 7) * 16);
     for (int c = 0; c < nchunks; c++) {
       const uint32_t bdst = su32(Ts + (size_t)c * STAGE) + rowoff, ldst = su32(Tl + (size_t)c * STAGE) + rowoff;
-      for (int kc = 0; kc < 8; kc++) {
+      for (int kc = half * 4; kc < half * 4 + 4; kc++) {
+        int k = c * KC + kc * PER, sl = k / g.nq, qp = k - sl * g.nq;  // K index, its slot and Gauss point
         uint32_t w[4] = {0u, 0u, 0u, 0u}, wl[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
         for (int j = 0; j < PER; j++, k++) {
@@ -230,12 +233,12 @@ __global__ void __launch_bounds__(128) k_elem_gemm(GemmArgs g) {
 
   const uint32_t idesc = (1u << 4) | ((OP == EG_BF16 ? 1u : 2u) << 7) | ((OP == EG_BF16 ? 1u : 2u) << 10) |
                          ((uint32_t)(GT >> 3) << 17) | ((uint32_t)(GT >> 4) << 24);
-  const uint32_t rowoff = (uint32_t)((tid >> 3) * 128 + (tid & 7) * 16);
+  const uint32_t rowoff = (uint32_t)((r128 >> 3) * 128 + (r128 & 7) * 16);
   int it = 0;     // chunk counter over all m-tiles (stage it & 1)
   int last = -1;  // thread 0: the last chunk whose MMAs were committed
   for (int mi = 0; mi < m_count && !*abort_s; mi++) {
     const int mt = m_first + mi;
-    const uint8_t *qrow = reinterpret_cast<const uint8_t *>(g.Qv) + ((size_t)mt * GT + tid) * g.Kp * ES;
+    const uint8_t *qrow = reinterpret_cast<const uint8_t *>(g.Qv) + ((size_t)mt * GT + r128) * g.Kp * ES;
     for (int c = 0; c < nchunks; c++, it++) {
       const int st = it & 1;
       if (it >= 2) {
@@ -245,7 +248,7 @@ __global__ void __launch_bounds__(128) k_elem_gemm(GemmArgs g) {
       }
       const uint32_t adst = su32(As + st * STAGE) + rowoff;
 #pragma unroll
-      for (int kc = 0; kc < 8; kc++) cp16(adst + kc * LBO, qrow + (size_t)c * KB + kc * 16, true);
+      for (int kc = half * 4; kc < half * 4 + 4; kc++) cp16(adst + kc * LBO, qrow + (size_t)c * KB + kc * 16, true);
       cp_commit();
       cp_wait<0>();
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -284,16 +287,18 @@ __global__ void __launch_bounds__(128) k_elem_gemm(GemmArgs g) {
     tc_fence_after();
     // E_ab (a <= b) goes to slab pk(a, b) at column A(e, a): for consecutive elements
     // along x the lanes write consecutive floats
-    const int row = warp * 32 + lane;
+    // warp w reads tensor-memory lanes 32 (w % 4) .. + 31, columns 64 (w / 4) .. + 63
+    const int quarter = warp & 3, ch = warp >> 2;
+    const int row = quarter * 32 + lane;
     const int e = g.elem_of_slot[(size_t)mt * GT + row];
     int64_t abase = 0;
     if (e >= 0) {
       const int e0 = e % g.nel0, e1 = (e / g.nel0) % g.nel1, e2 = g.dim == 3 ? e / (g.nel0 * g.nel1) : 0;
       abase = g.first[0][e0] + g.N0 * ((int64_t)g.first[1][e1] + (int64_t)g.N1 * (g.dim == 3 ? g.first[2][e2] : 0));
     }
-    for (int c0 = 0; c0 < GT; c0 += 16) {
+    for (int c0 = ch * (GT / 2); c0 < (ch + 1) * (GT / 2); c0 += 16) {
       float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
       if (e < 0) continue;
 #pragma unroll
       for (int u = 0; u < 16; u++) {
@@ -363,11 +368,20 @@ template <int DIM> __host__ __device__ constexpr int ipow3(int b) { return DIM =
 // w_A w_B and the Dirichlet rows and columns.
 template <int DIM, int P, int TPB>
 __global__ void __launch_bounds__(TPB) k_gather_rows(DirArgs d0, DirArgs d1, DirArgs d2, const float *__restrict__ E,
-                                                     const int64_t *__restrict__ rowptr, const double *__restrict__ wts,
-                                                     BndArgs bnd, float *__restrict__ vals, int64_t N) {
+                                                     const int2 *__restrict__ gtab_g, const int64_t *__restrict__ rowptr,
+                                                     const double *__restrict__ wts, BndArgs bnd, float *__restrict__ vals,
+                                                     int64_t N) {
   constexpr int N1 = P + 1, NEN = ipow3<DIM>(N1), RMAX = ipow3<DIM>(2 * P + 1);
-  extern __shared__ float acc_all[];  // [RMAX][TPB]
+  constexpr bool TAB_SMEM = NEN * NEN * 8 <= 8 * 1024;  // p = 2: small enough not to cost occupancy
+  extern __shared__ float acc_all[];  // [RMAX][TPB], then the (pk, column shift) table for p <= 3
   const int t = threadIdx.x;
+  const int2 *gtab = gtab_g;
+  if (TAB_SMEM) {
+    int2 *st = reinterpret_cast<int2 *>(acc_all + RMAX * TPB);
+    for (int k = t; k < NEN * NEN; k += TPB) st[k] = gtab_g[k];
+    __syncthreads();
+    gtab = st;
+  }
   const int64_t A = (int64_t)blockIdx.x * TPB + t;
   if (A >= N) return;
   float *acc = acc_all + t;
@@ -386,9 +400,8 @@ __global__ void __launch_bounds__(TPB) k_gather_rows(DirArgs d0, DirArgs d1, Dir
       for (int e0 = lo0; e0 < hi0; e0++) {
         const int f0 = d0.first[e0];
         const int a = (I0 - f0) + N1 * ((I1 - f1) + N1 * (I2 - f2));
-        const int a0 = I0 - f0, a1 = I1 - f1, a2 = I2 - f2;
-        const int64_t offa = a0 + (int64_t)d0.n * (a1 + (int64_t)d1.n * a2);
         const int base = ((f2 - l2) * w1 + (f1 - l1)) * w0 + (f0 - l0);
+        const int2 *ga = gtab + a * NEN;
         // the element's NEN values are loaded before any is added: independent loads in flight
         constexpr int CH = NEN <= 64 ? NEN : 25;
         for (int b0c = 0; b0c < NEN; b0c += CH) {
@@ -398,11 +411,8 @@ __global__ void __launch_bounds__(TPB) k_gather_rows(DirArgs d0, DirArgs d1, Dir
             const int b = b0c + u;
             float x = 0.f;
             if (b < NEN) {
-              const int lo = a < b ? a : b, hi = a < b ? b : a;
-              const int pk = lo * NEN - lo * (lo - 1) / 2 + (hi - lo);
-              const int b0 = b % N1, b1 = (b / N1) % N1, b2 = (DIM == 3) ? b / (N1 * N1) : 0;
-              const int64_t col = b >= a ? A : A + (b0 + (int64_t)d0.n * (b1 + (int64_t)d1.n * b2)) - offa;
-              x = __ldg(E + (size_t)pk * N + col);
+              const int2 pc = ga[b];  // packed slab of (min(a,b), max(a,b)); column shift off(b) - off(a) for b < a
+              x = __ldg(E + (size_t)pc.x * N + A + pc.y);
             }
             ev[u] = x;
           }
@@ -447,6 +457,7 @@ struct ElemGemmPlan {
   int ngroups = 0;
   int *slot_of_elem = nullptr, *elem_of_slot = nullptr, *group = nullptr, *pair_ab = nullptr, *pair_off = nullptr,
       *err = nullptr;
+  int2 *gtab = nullptr;  // [nen][nen]: packed slab of (min, max), and the column shift off(b) - off(a) when b < a
   void *Qv[2] = {nullptr, nullptr};  // BF16, TF32 operand buffers
   float *E = nullptr;
 };
@@ -472,7 +483,7 @@ static std::vector<int> dir_types(const Dir &D, std::vector<int> &rep) {
 }
 
 static void plan_free(ElemGemmPlan *P) {
-  void *ps[] = {P->slot_of_elem, P->elem_of_slot, P->group, P->pair_ab, P->pair_off, P->err, P->Qv[0], P->Qv[1], P->E};
+  void *ps[] = {P->slot_of_elem, P->elem_of_slot, P->group, P->pair_ab, P->pair_off, P->err, P->Qv[0], P->Qv[1], P->E, P->gtab};
   for (void *p : ps)
     if (p) cudaFree(p);
 }
@@ -556,6 +567,12 @@ static cudaError_t elem_gemm_prepare(iga_s *h) {
       poff.push_back(off(a));
       poff.push_back(off(b));
     }
+  std::vector<int2> gt((size_t)nen * nen);
+  for (int a = 0; a < nen; a++)
+    for (int b = 0; b < nen; b++) {
+      const int lo = std::min(a, b), hi = std::max(a, b);
+      gt[(size_t)a * nen + b] = make_int2(lo * nen - lo * (lo - 1) / 2 + (hi - lo), b < a ? off(b) - off(a) : 0);
+    }
   std::vector<int> eos((size_t)m_tiles * GT, -1);
   for (int64_t e = 0; e < h->nelem; e++) eos[slot[e]] = (int)e;
   const size_t slots_total = (size_t)m_tiles * GT;
@@ -568,6 +585,8 @@ static cudaError_t elem_gemm_prepare(iga_s *h) {
   if ((ce = cudaMemcpy(P->pair_ab, pairs.data(), pairs.size() * sizeof(int), cudaMemcpyHostToDevice))) return ce;
   if ((ce = cudaMalloc((void **)&P->pair_off, poff.size() * sizeof(int)))) return ce;
   if ((ce = cudaMemcpy(P->pair_off, poff.data(), poff.size() * sizeof(int), cudaMemcpyHostToDevice))) return ce;
+  if ((ce = cudaMalloc((void **)&P->gtab, gt.size() * sizeof(int2)))) return ce;
+  if ((ce = cudaMemcpy(P->gtab, gt.data(), gt.size() * sizeof(int2), cudaMemcpyHostToDevice))) return ce;
   if ((ce = cudaMalloc((void **)&P->elem_of_slot, eos.size() * sizeof(int)))) return ce;
   if ((ce = cudaMemcpy(P->elem_of_slot, eos.data(), eos.size() * sizeof(int), cudaMemcpyHostToDevice))) return ce;
   if ((ce = cudaMalloc((void **)&P->err, sizeof(int)))) return ce;
@@ -671,19 +690,21 @@ cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, in
   const unsigned grid = (unsigned)((int64_t)P->ngroups * P->n_tiles);
   if (op == EG_BF16) {
     cudaFuncSetAttribute(k_elem_gemm<EG_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    IGA_LAUNCH(h, KC_ELEM_TC, (k_elem_gemm<EG_BF16><<<grid, 128, smem, h->stream>>>(g)));
+    IGA_LAUNCH(h, KC_ELEM_TC, (k_elem_gemm<EG_BF16><<<grid, 256, smem, h->stream>>>(g)));
   } else {
     cudaFuncSetAttribute(k_elem_gemm<EG_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    IGA_LAUNCH(h, KC_ELEM_TC, (k_elem_gemm<EG_TF32><<<grid, 128, smem, h->stream>>>(g)));
+    IGA_LAUNCH(h, KC_ELEM_TC, (k_elem_gemm<EG_TF32><<<grid, 256, smem, h->stream>>>(g)));
   }
   if ((ce = cudaGetLastError())) return ce;
   IGA_LAUNCH(h, KC_ELEM_GATHER, EG_DISPATCH(h->dim, h->p, ({
     constexpr int RMAX = ipow3<D>(2 * PP + 1);
     constexpr int TPB = RMAX * 4 * 256 <= 96 * 1024 ? 256 : (RMAX * 4 * 128 <= 96 * 1024 ? 128 : (RMAX * 4 * 64 <= 96 * 1024 ? 64 : 32));
-    const size_t sm = (size_t)RMAX * TPB * sizeof(float);
+    constexpr int NENc = ipow3<D>(PP + 1);
+    const size_t sm = (size_t)RMAX * TPB * sizeof(float) + (NENc * NENc * 8 <= 8 * 1024 ? (size_t)NENc * NENc * 8 : 0);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_gather_rows<D, PP, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const unsigned gg = (unsigned)((h->N + TPB - 1) / TPB);
-    k_gather_rows<D, PP, TPB><<<gg, TPB, sm, h->stream>>>(a0, a1, a2, P->E, h->rowptr, h->weights, h->bnd, vals, h->N);
+    k_gather_rows<D, PP, TPB><<<gg, TPB, sm, h->stream>>>(a0, a1, a2, P->E, P->gtab, h->rowptr, h->weights, h->bnd, vals,
+                                                          h->N);
   })));
   return cudaGetLastError();
 }
