@@ -20,10 +20,13 @@
 //
 // k_elem_gemm, one CTA per (128 elements, 128 pairs) tile and group of element tiles,
 // 256 threads:
-//   - two threads per row copy an element row of the Qv chunk (cp.async, 16 B) and
-//     compute a pair row of the T chunk from the tile type's 1D tables, into the
-//     canonical K-major layout without swizzling (8-row x 16-byte core matrices,
-//     128 B apart along M/N, 2 KB apart along K), two stages;
+//   - the T tile of the CTA's pair range (all of K) comes from a per-mesh cache built
+//     once by the same kernel in build mode (when the cache takes at most 1 GB), else
+//     two threads per pair row compute it from the type's 1D tables; it stays in shared
+//     memory for the CTA's group of element tiles;
+//   - two threads per row copy an element row of each Qv chunk (cp.async, 16 B) into the
+//     canonical K-major layout without swizzling (8-row x 16-byte core matrices, 128 B
+//     apart along M/N, 2 KB apart along K), two stages;
 //   - thread 0 issues the chunk's four tcgen05.mma (32 bytes of K each) and commits
 //     them to the stage's barrier, which frees the stage two chunks later;
 //   - after the last chunk warp w reads accumulator rows 32 (w % 4) .. + 31 (half the
@@ -82,7 +85,10 @@ struct GemmArgs {
   int nel0, nel1;
   int64_t N, N0, N1;        // functions in all, along x, along y
   const float *tab[3];     // FP32 1D tables [nel][q][p+1][2]
-  const int *group;        // [ngroups][5]: first m-tile, m-tiles, element of the type per direction
+  const int *group;        // [ngroups][6]: first m-tile, m-tiles, element of the type per direction, type
+  const uint8_t *Tc;       // T tiles built once per mesh ([type][n_tile][tile_bytes]), or null
+  uint8_t *Tout;           // build mode: write the T tiles here and stop
+  int64_t tile_bytes;
   const int *pair_ab;      // [nsym]: a | b << 16, a <= b, row by row
   int dim, p, nq, nsym, nen, Kp, Np, n_tiles, m_tiles, general;
   int split;  // 1: T = T_hi + T_lo, both in the operand type (two MMAs per chunk on the same Qv)
@@ -126,7 +132,7 @@ __global__ void __launch_bounds__(256) k_elem_gemm(GemmArgs g) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int r128 = tid & 127, half = tid >> 7;  // operand row of this thread, and which half of its 8 16-byte chunks
   const int grp = blockIdx.x / g.n_tiles, n_tile = blockIdx.x % g.n_tiles;
-  const int m_first = g.group[grp * 5 + 0], m_count = g.group[grp * 5 + 1];
+  const int m_first = g.group[grp * 6 + 0], m_count = g.group[grp * 6 + 1];
   const int q = g.p + 1, n1 = g.p + 1;
   const int tsz = q * n1 * 2;
 
@@ -148,7 +154,7 @@ __global__ void __launch_bounds__(256) k_elem_gemm(GemmArgs g) {
   }
   for (int k = tid; k < 3 * tsz; k += blockDim.x) {
     const int ax = k / tsz, r = k - ax * tsz;
-    tab[k] = ax < g.dim ? g.tab[ax][(size_t)g.group[grp * 5 + 2 + ax] * tsz + r] : (r % 2 == 0 ? 1.f : 0.f);
+    tab[k] = ax < g.dim ? g.tab[ax][(size_t)g.group[grp * 6 + 2 + ax] * tsz + r] : (r % 2 == 0 ? 1.f : 0.f);
   }
   for (int c = tid; c < GT; c += blockDim.x) {
     const int n = n_tile * GT + c;
@@ -163,8 +169,14 @@ __global__ void __launch_bounds__(256) k_elem_gemm(GemmArgs g) {
   const int nslot = smu[15];
   const int KV = nslot * g.nq;
 
-  // ---- T tile of this pair range for the whole K, once per group ----
-  {
+  // ---- T tile of this pair range for the whole K: copied from the per-mesh cache, or
+  // built here (once per group) from the type's 1D tables ----
+  const int64_t tile_off = ((int64_t)g.group[grp * 6 + 5] * g.n_tiles + n_tile) * g.tile_bytes;
+  if (g.Tc) {
+    for (int64_t x = (int64_t)tid * 16; x < g.tile_bytes; x += 16 * (int64_t)blockDim.x) cp16(su32(Ts) + (uint32_t)x, g.Tc + tile_off + x, true);
+    cp_commit();
+    cp_wait<0>();
+  } else {
     const int npair = n_tile * GT + r128;
     int a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0;
     const bool pvalid = npair < g.nsym;
@@ -230,6 +242,10 @@ __global__ void __launch_bounds__(256) k_elem_gemm(GemmArgs g) {
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
+  if (g.Tout) {  // build mode: the tile goes to the per-mesh cache
+    for (int64_t x = (int64_t)tid * 16; x < g.tile_bytes; x += 16 * (int64_t)blockDim.x)
+      *reinterpret_cast<uint4 *>(g.Tout + tile_off + x) = *reinterpret_cast<const uint4 *>(Ts + x);
+  }
 
   const uint32_t idesc = (1u << 4) | ((OP == EG_BF16 ? 1u : 2u) << 7) | ((OP == EG_BF16 ? 1u : 2u) << 10) |
                          ((uint32_t)(GT >> 3) << 17) | ((uint32_t)(GT >> 4) << 24);
@@ -319,12 +335,12 @@ __global__ void __launch_bounds__(256) k_elem_gemm(GemmArgs g) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GT) : "memory");
 }
 
-// Qv[slot(e)][(s, q)] = Q_{mu nu}(e, q) in the operand type from the geometry record
-// and U: Q_00 = gSg - jw/W^2 lambda e^u (u~ interpolated and the exponential taken in
+// Qv[slot(e)][(s, q)] = Q_{mu nu}(e, q) in the operand type from the FP32 geometry
+// factors (geom32) and U: Q_00 = gSg - jw/W^2 lambda e^u (u~ interpolated and the exponential taken in
 // FP32), Q_0a = nSg_a, Q_ab = S_ab.  One thread per Gauss point, EB elements per block.
 template <int DIM, int P, int OP>
 __global__ void __launch_bounds__(128) k_qv(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ U,
-                                            const double *__restrict__ wts, const double *__restrict__ geom, GeomLayout gl,
+                                            const double *__restrict__ wts, const float *__restrict__ g32,
                                             float lambda, const int *__restrict__ slot_of_elem, void *__restrict__ Qv, int Kp,
                                             int general, int64_t nelem) {
   using IS = InterpF32<DIM, P>;
@@ -335,8 +351,9 @@ __global__ void __launch_bounds__(128) k_qv(DirArgs d0, DirArgs d1, DirArgs d2, 
   const int le = threadIdx.x / nq, qp = threadIdx.x - le * nq;
   const int64_t e = e_first + le;
   if (le >= IS::EB || e >= nelem) return;
-  const double *rec = geom + (size_t)e * gl.nf * nq + qp;
-  const float q00 = (float)rec[gl.gSg * nq] - (float)rec[gl.jwW2 * nq] * lambda * __expf(ut * (float)rec[gl.invW * nq]);
+  using GL = G32<DIM>;
+  const float *rec = g32 + (size_t)e * GL::NF * nq + qp;
+  const float q00 = rec[GL::GSG * nq] - rec[GL::JWW2 * nq] * lambda * __expf(ut * rec[GL::INVW * nq]);
   const Slots S = make_slots(DIM, general != 0);
   const size_t row = (size_t)slot_of_elem[e] * Kp;
 #pragma unroll
@@ -345,12 +362,12 @@ __global__ void __launch_bounds__(128) k_qv(DirArgs d0, DirArgs d1, DirArgs d2, 
     const int mu = S.mu[s], nu = S.nu[s];
     float v;
     if (mu == 0 && nu == 0) v = q00;
-    else if (mu == 0) v = (float)rec[(gl.Sg + nu - 1) * nq];
+    else if (mu == 0) v = rec[(GL::NSG + nu - 1) * nq];
     else {
       // S slots: 2D 00, 11, 01; 3D 00, 11, 22, 01, 02, 12
       const int i = mu - 1, j = nu - 1;
       const int si = (i == j) ? i : (DIM == 2 ? 2 : (i == 0 ? (j == 1 ? 3 : 4) : 5));
-      v = (float)rec[(gl.S + si) * nq];
+      v = rec[(GL::S + si) * nq];
     }
     const uint32_t bits = op_bits(v, OP);
     if (OP == EG_BF16) reinterpret_cast<uint16_t *>(Qv)[row + (size_t)s * nq + qp] = (uint16_t)bits;
@@ -454,7 +471,10 @@ __global__ void __launch_bounds__(TPB) k_gather_rows(DirArgs d0, DirArgs d1, Dir
 struct ElemGemmPlan {
   bool ok = false;
   int general = 0, nq = 0, nsym = 0, Kp = 0, Np = 0, n_tiles = 0, m_tiles = 0, es = 2;
-  int ngroups = 0;
+  int ngroups = 0, ntypes = 0;
+  int *tgroup = nullptr;                 // [ntypes][6]: build groups of the T-tile cache
+  uint8_t *Tc[2] = {nullptr, nullptr};   // T-tile cache per operand type (null: built in the GEMM)
+  bool tc_tried[2] = {false, false};
   int *slot_of_elem = nullptr, *elem_of_slot = nullptr, *group = nullptr, *pair_ab = nullptr, *pair_off = nullptr,
       *err = nullptr;
   int2 *gtab = nullptr;  // [nen][nen]: packed slab of (min, max), and the column shift off(b) - off(a) when b < a
@@ -483,7 +503,8 @@ static std::vector<int> dir_types(const Dir &D, std::vector<int> &rep) {
 }
 
 static void plan_free(ElemGemmPlan *P) {
-  void *ps[] = {P->slot_of_elem, P->elem_of_slot, P->group, P->pair_ab, P->pair_off, P->err, P->Qv[0], P->Qv[1], P->E, P->gtab};
+  void *ps[] = {P->slot_of_elem, P->elem_of_slot, P->group, P->pair_ab, P->pair_off, P->err, P->Qv[0], P->Qv[1], P->E, P->gtab,
+                P->tgroup, P->Tc[0], P->Tc[1]};
   for (void *p : ps)
     if (p) cudaFree(p);
 }
@@ -532,7 +553,7 @@ static cudaError_t elem_gemm_prepare(iga_s *h) {
   // tiles beyond four times the elements (knot vectors with few repeated spans): not worth it
   if (m_tiles * GT > 4 * h->nelem + 64 * GT) return cudaErrorNotSupported;
   P->m_tiles = (int)m_tiles;
-  std::vector<int> slot(h->nelem), groups;
+  std::vector<int> slot(h->nelem), groups, tgroups;
   std::vector<int64_t> next = first_slot;
   for (int64_t e = 0; e < h->nelem; e++) {
     const int64_t t = type_of(e);
@@ -552,9 +573,17 @@ static cudaError_t elem_gemm_prepare(iga_s *h) {
       groups.push_back(rep[0][t0]);
       groups.push_back(rep[1][t1]);
       groups.push_back(rep[2][t2]);
+      groups.push_back((int)t);
     }
+    tgroups.push_back(0);  // one group per type without element tiles: builds the type's T tiles
+    tgroups.push_back(0);
+    tgroups.push_back(rep[0][t0]);
+    tgroups.push_back(rep[1][t1]);
+    tgroups.push_back(rep[2][t2]);
+    tgroups.push_back((int)t);
   }
-  P->ngroups = (int)(groups.size() / 5);
+  P->ngroups = (int)(groups.size() / 6);
+  P->ntypes = (int)ntypes;
   std::vector<int> pairs, poff;
   const int64_t n0f = h->dir[0].n, n1f = h->dir[1].n;
   auto off = [&](int a) {
@@ -581,6 +610,8 @@ static cudaError_t elem_gemm_prepare(iga_s *h) {
   if ((ce = cudaMemcpy(P->slot_of_elem, slot.data(), slot.size() * sizeof(int), cudaMemcpyHostToDevice))) return ce;
   if ((ce = cudaMalloc((void **)&P->group, groups.size() * sizeof(int)))) return ce;
   if ((ce = cudaMemcpy(P->group, groups.data(), groups.size() * sizeof(int), cudaMemcpyHostToDevice))) return ce;
+  if ((ce = cudaMalloc((void **)&P->tgroup, tgroups.size() * sizeof(int)))) return ce;
+  if ((ce = cudaMemcpy(P->tgroup, tgroups.data(), tgroups.size() * sizeof(int), cudaMemcpyHostToDevice))) return ce;
   if ((ce = cudaMalloc((void **)&P->pair_ab, pairs.size() * sizeof(int)))) return ce;
   if ((ce = cudaMemcpy(P->pair_ab, pairs.data(), pairs.size() * sizeof(int), cudaMemcpyHostToDevice))) return ce;
   if ((ce = cudaMalloc((void **)&P->pair_off, poff.size() * sizeof(int)))) return ce;
@@ -653,10 +684,10 @@ cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, in
     using IS = InterpF32<D, PP>;
     const unsigned gq = (unsigned)((h->nelem + IS::EB - 1) / IS::EB);
     if (op == EG_BF16)
-      k_qv<D, PP, EG_BF16><<<gq, IS::THREADS, 0, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, (float)h->lambda,
+      k_qv<D, PP, EG_BF16><<<gq, IS::THREADS, 0, h->stream>>>(a0, a1, a2, U, h->weights, h->geom32, (float)h->lambda,
                                                               P->slot_of_elem, Qv, P->Kp, P->general, h->nelem);
     else
-      k_qv<D, PP, EG_TF32><<<gq, IS::THREADS, 0, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, (float)h->lambda,
+      k_qv<D, PP, EG_TF32><<<gq, IS::THREADS, 0, h->stream>>>(a0, a1, a2, U, h->weights, h->geom32, (float)h->lambda,
                                                               P->slot_of_elem, Qv, P->Kp, P->general, h->nelem);
   })));
   GemmArgs g;
@@ -687,12 +718,33 @@ cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, in
   const int nch = P->Kp * (op == EG_BF16 ? 2 : 4) / KB;
   g.split = eg_smem(nch, 1) <= 200 * 1024 ? 1 : 0;
   const size_t smem = eg_smem(nch, g.split);
+  g.tile_bytes = (int64_t)nch * (1 + g.split) * STAGE;
+  g.Tc = nullptr;
+  g.Tout = nullptr;
+  if (op == EG_BF16) cudaFuncSetAttribute(k_elem_gemm<EG_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  else cudaFuncSetAttribute(k_elem_gemm<EG_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the T tiles depend on the mesh only: built once (when they take at most 1 GB) and copied by the GEMM
+  if (!P->tc_tried[op]) {
+    P->tc_tried[op] = true;
+    const int64_t bytes = (int64_t)P->ntypes * P->n_tiles * g.tile_bytes;
+    if (bytes <= (int64_t)1 << 30 && cudaMalloc((void **)&P->Tc[op], bytes) == cudaSuccess) {
+      GemmArgs gb = g;
+      gb.group = P->tgroup;
+      gb.Tout = P->Tc[op];
+      const unsigned gridb = (unsigned)((int64_t)P->ntypes * P->n_tiles);
+      if (op == EG_BF16) IGA_LAUNCH(h, KC_ELEM_TC, (k_elem_gemm<EG_BF16><<<gridb, 256, smem, h->stream>>>(gb)));
+      else IGA_LAUNCH(h, KC_ELEM_TC, (k_elem_gemm<EG_TF32><<<gridb, 256, smem, h->stream>>>(gb)));
+      if ((ce = cudaGetLastError())) return ce;
+    } else {
+      cudaGetLastError();  // a failed allocation only means no cache
+      P->Tc[op] = nullptr;
+    }
+  }
+  g.Tc = P->Tc[op];
   const unsigned grid = (unsigned)((int64_t)P->ngroups * P->n_tiles);
   if (op == EG_BF16) {
-    cudaFuncSetAttribute(k_elem_gemm<EG_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     IGA_LAUNCH(h, KC_ELEM_TC, (k_elem_gemm<EG_BF16><<<grid, 256, smem, h->stream>>>(g)));
   } else {
-    cudaFuncSetAttribute(k_elem_gemm<EG_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     IGA_LAUNCH(h, KC_ELEM_TC, (k_elem_gemm<EG_TF32><<<grid, 256, smem, h->stream>>>(g)));
   }
   if ((ce = cudaGetLastError())) return ce;

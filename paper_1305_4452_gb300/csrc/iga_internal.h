@@ -39,6 +39,13 @@ struct GeomLayout {
 
 GeomLayout geom_layout(int dim);
 
+// FP32 copy of the geometry factors for the reduced-precision Jacobians (iga_s::geom32,
+// [e][slot][qp]): invW, gSg, jwW2, S (ns), nSg (dim)
+template <int DIM> struct G32 {
+  static constexpr int NS = DIM * (DIM + 1) / 2;
+  static constexpr int INVW = 0, GSG = 1, JWW2 = 2, S = 3, NSG = 3 + NS, NF = 3 + NS + DIM;
+};
+
 struct Dir {
   int p = 0, q = 0, nel = 0, n = 0;
   std::vector<double> knots;

@@ -25,11 +25,6 @@ namespace {
 template <int DIM> __host__ __device__ constexpr int ipow(int b) { return DIM == 2 ? b * b : b * b * b; }
 __host__ __device__ constexpr int rup(int x, int m) { return (x + m - 1) / m * m; }
 
-// FP32 geometry slots per Gauss point: invW, gSg, jwW2, S (ns), nSg (dim)
-template <int DIM> struct G32 {
-  static constexpr int NS = DIM * (DIM + 1) / 2;
-  static constexpr int INVW = 0, GSG = 1, JWW2 = 2, S = 3, NSG = 3 + NS, NF = 3 + NS + DIM;
-};
 
 template <int DIM, int P>
 __global__ void k_geom32(const double *__restrict__ geom, GeomLayout gl, float *__restrict__ g32, int64_t nelem) {
@@ -555,7 +550,11 @@ static cudaError_t mixed_prepare(iga_s *h) {
     if (ce) return ce;
     int64_t tot = h->nelem * nq;
     unsigned grid = (unsigned)((tot + 255) / 256);
-    IGA_LAUNCH(h, KC_GEOM, DISPATCH_TC(h->dim, h->p, (k_geom32<D, PP><<<grid, 256, 0, h->stream>>>(h->geom, h->gl, h->geom32, h->nelem))));
+    // every degree (the element GEMM takes 3D p = 4, which the per-element kernels do not)
+    if (h->dim == 3 && h->p == 4)
+      IGA_LAUNCH(h, KC_GEOM, (k_geom32<3, 4><<<grid, 256, 0, h->stream>>>(h->geom, h->gl, h->geom32, h->nelem)));
+    else
+      IGA_LAUNCH(h, KC_GEOM, DISPATCH_TC(h->dim, h->p, (k_geom32<D, PP><<<grid, 256, 0, h->stream>>>(h->geom, h->gl, h->geom32, h->nelem))));
     for (int ax = 0; ax < h->dim; ax++) {
       size_t n = h->dir[ax].tab.size();
       ce = cudaMalloc((void **)&h->tab32[ax], n * sizeof(float));
