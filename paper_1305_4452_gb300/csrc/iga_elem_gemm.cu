@@ -90,7 +90,7 @@ struct GemmArgs {
   uint8_t *Tout;           // build mode: write the T tiles here and stop
   int64_t tile_bytes;
   const int *pair_ab;      // [nsym]: a | b << 16, a <= b, row by row
-  int dim, p, nq, nsym, nen, Kp, Np, n_tiles, m_tiles, general;
+  int dim, p, nq, nsym, nen, Kp, n_tiles, m_tiles, general;
   int split;  // 1: T = T_hi + T_lo, both in the operand type (two MMAs per chunk on the same Qv)
   int *err;
 };
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(TPB) k_gather_rows(DirArgs d0, DirArgs d1, Dir
 // pair list, and the operand and result buffers.
 struct ElemGemmPlan {
   bool ok = false;
-  int general = 0, nq = 0, nsym = 0, Kp = 0, Np = 0, n_tiles = 0, m_tiles = 0, es = 2;
+  int general = 0, nq = 0, nsym = 0, Kp = 0, n_tiles = 0, m_tiles = 0;
   int ngroups = 0, ntypes = 0;
   int *tgroup = nullptr;                 // [ntypes][6]: build groups of the T-tile cache
   uint8_t *Tc[2] = {nullptr, nullptr};   // T-tile cache per operand type (null: built in the GEMM)
@@ -528,7 +528,6 @@ static cudaError_t elem_gemm_prepare(iga_s *h) {
   P->Kp = (S.n * P->nq + 63) / 64 * 64;
   P->nsym = nen * (nen + 1) / 2;  // the upper triangle a <= b, row by row
   P->n_tiles = (P->nsym + GT - 1) / GT;
-  P->Np = P->n_tiles * GT;
   // types and tiles
   std::vector<int> rep[3], ty[3];
   for (int ax = 0; ax < 3; ax++) {
@@ -710,7 +709,6 @@ cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, in
   g.nq = P->nq;
   g.nsym = P->nsym;
   g.Kp = P->Kp;
-  g.Np = P->Np;
   g.n_tiles = P->n_tiles;
   g.m_tiles = P->m_tiles;
   g.general = P->general;
