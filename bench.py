@@ -319,6 +319,12 @@ def run_ours(args):
     return 0
 
 
+# DRAM bytes (read + write) of one k_spmv_stencil launch on the 64^3 annulus, from one ncu
+# capture of this benchmark (profiles/k_spmv_stencil_annulus64_fp64_traffic.md); valid for
+# that workload and the kernel as captured.
+SPMV_DRAM_BYTES_ANNULUS64 = 803.45e6 + 4.97e6
+
+
 def roofline_entry(disc, cls, avg_ms, hbm_gbs, hbm_src):
     """Algorithmic work of one launch of the given kernel class on this workload."""
     N, nnz = disc.N, disc.nnz
@@ -335,8 +341,9 @@ def roofline_entry(disc, cls, avg_ms, hbm_gbs, hbm_src):
         t = avg_ms * 1e-3
         hbm_frac = bytes_ / t / 1e9 / hbm_gbs
         fp_frac = flops / t / 1e12 / FP64_PEAK_TFLOPS
+        traffic = SPMV_DRAM_BYTES_ANNULUS64 if NEL == 64 else None
         return {"kernel": "k_spmv_stencil (FP64 values, stencil columns)", "bound": "alu", "achieved": flops / t / 1e12,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": fp_frac, "traffic": None,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": fp_frac, "traffic": traffic,
                 "peak_source": "derived: 152 SM x 2 DFMA/clk x 2.07 GHz",
                 "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": bytes_,
                 "hbm": {"achieved_gbs": bytes_ / t / 1e9, "peak_gbs": hbm_gbs, "frac": hbm_frac, "peak_source": hbm_src}}
