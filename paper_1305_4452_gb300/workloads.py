@@ -21,6 +21,11 @@ assembly or solver arithmetic.
   control points on circles (radius at the radial Greville abscissae, angles
   2 pi j / n for the n wrapped angular functions), weights 1; optionally extruded in
   z.  A smooth closed approximation of the circle, positively oriented.
+* ``full_annulus``: the exact NURBS annulus (inner radius 1, outer 2) as a closed
+  curve of four rational quadratic quarter arcs (C^0 at the quarter points, knots of
+  multiplicity p there), raised to degree p and refined uniformly per quarter; its
+  angular direction is meant to be periodic with C^0 continuity across the seam
+  (k = 0, the last control points equal the first and are dropped).
 * ``grf_log_kappa``: a Gaussian random field with a separable squared-exponential
   covariance on the control grid's Greville abscissae, sampled by Cholesky.
 * ``batch_instances``: the draw of the heterogeneous batched workload.
@@ -168,6 +173,34 @@ def ring(nel_r, nel_t, p, r_in=1.0, r_out=2.0, nel_z=None, height=1.0):
     X[..., 1] = np.sin(th)[None, :, None] * r[None, None, :]
     X[..., 2] = z[:, None, None]
     return [kr, kt, kz], X.reshape(-1, 3)
+
+
+def full_annulus(nel_r, nel_q, p=2, r_in=1.0, r_out=2.0):
+    """Knot vectors (radial, angular; open) and control points (N, 2) with weights (N,)
+    of the exact annulus; nel_q elements per quarter of the angular direction.  The
+    angular control points are those of the wrapped periodic space (C^0 across the
+    seam: the closed curve's last control point, equal to its first, is left out)."""
+    s = math.sqrt(0.5)
+    quarter = np.array([[1.0, 0.0, 1.0], [s, s, s], [0.0, 1.0, 1.0]])  # homogeneous (w x, w y, w)
+    Ut, Pt = None, None
+    for j in range(4):
+        c, sn = math.cos(j * math.pi / 2), math.sin(j * math.pi / 2)
+        R = np.array([[c, -sn, 0.0], [sn, c, 0.0], [0.0, 0.0, 1.0]])
+        Uq, Pq = _refine_curve(quarter @ R.T, p, nel_q)  # one quarter, degree p, nel_q elements on [0, 1]
+        Uq = (Uq + j) / 4.0
+        if Ut is None:
+            Ut, Pt = Uq, Pq
+        else:  # join at the quarter point: knot of multiplicity p, shared end control point
+            Ut = np.concatenate([Ut[:-1], Uq[p + 1:]])
+            Pt = np.concatenate([Pt, Pq[1:]])
+    Pt = Pt[:-1]  # the last equals the first: the periodic space wraps it
+    Ur, Pr = _refine_curve(np.array([[r_in, 1.0], [r_out, 1.0]]), p, nel_r)
+    r = Pr[:, 0] / Pr[:, 1]
+    wt = Pt[:, 2]
+    ct = Pt[:, :2] / wt[:, None]
+    ctrl = (r[None, :, None] * ct[:, None, :]).reshape(-1, 2)   # [j][i][2], axis 0 (radius) fastest
+    weights = np.broadcast_to(wt[:, None], (len(wt), len(r))).reshape(-1).copy()
+    return [Ur, Ut], ctrl, weights
 
 
 def greville(U, p):

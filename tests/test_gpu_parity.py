@@ -680,3 +680,25 @@ def test_periodic_ring_geometry_matches_the_oracle(case):
     assert rep.status == 0
     assert np.linalg.norm(prob.residual(Us.cpu().numpy())) <= 1e-10 * (1 + 1e-12)
     disc.close()
+
+
+@pytest.mark.parametrize("p,nel_r,nel_q", [(2, 4, 3), (3, 3, 2)])
+def test_periodic_exact_full_annulus_matches_the_oracle(p, nel_r, nel_q):
+    """The exact NURBS annulus, periodic across the seam with C^0 continuity; Dirichlet
+    on the inner and outer circles: residual, Jacobian and Newton against the oracle."""
+    I = iga()
+    kn, ctrl, w = W.full_annulus(nel_r, nel_q, p)
+    bc = {(0, 0): 0.0, (0, 1): 0.0}
+    prob = O.Problem(kn, [p, p], ctrl=ctrl, weights=w, lam=1.0, dirichlet=bc, periodic={1: 0})
+    disc = I.Discretization(2, p, knots=kn, ctrl=ctrl, weights=w, lam=1.0, dirichlet=bc, periodic={1: 0})
+    assert disc.N == prob.N
+    rng = np.random.default_rng(31)
+    U0 = np.where(prob.dirichlet_mask(), 0.0, rng.uniform(-0.3, 0.3, prob.N))
+    U = torch.tensor(U0, device="cuda")
+    assert rel(disc.form_residual(U).cpu().numpy(), prob.residual(U0)) <= TOL
+    assert rel(disc.form_jacobian(U).cpu().numpy(), prob.jacobian(U0)) <= TOL
+    Us = torch.zeros_like(U)
+    rep = disc.solve_newton(Us, I.newton_defaults())
+    assert rep.status == 0
+    assert np.linalg.norm(prob.residual(Us.cpu().numpy())) <= 1e-10 * (1 + 1e-12)
+    disc.close()

@@ -639,3 +639,19 @@ def test_periodic_direction_with_x_independent_data_matches_natural_boundaries()
     assert np.abs(Up - Up[:, :1]).max() < 1e-13
     assert np.abs(Un - Un[:, :1]).max() < 1e-12
     assert np.abs(Up[:, 0] - Un[:, 0]).max() < 1e-12
+
+
+def test_exact_full_annulus_as_a_periodic_space():
+    """The closed annulus of four rational quarter arcs, periodic across the seam with
+    C^0 continuity (k = 0): every point lies on the circle of its radius, constants are in
+    the space, and the mass totals the area 3 pi (over-integrated rule)."""
+    for p, nq in ((2, 4), (3, 3)):
+        kn, ctrl, w = W.full_annulus(3, nq, p)
+        P = O.Problem(kn, [p, p], ctrl=ctrl, weights=w, lam=0.0, periodic={1: 0}, quad=[p + 3, p + 3])
+        rng = np.random.default_rng(p)
+        for xi in rng.uniform(0, 1, (20, 2)):
+            x, det = P.map_point(xi)
+            assert abs(math.hypot(*x) - (1 + xi[0])) < 1e-14 and det > 0
+        K = P.jacobian_csr(np.zeros(P.N))
+        assert np.abs(K @ np.ones(P.N)).max() < 1e-13
+        assert abs(P.mass().sum() - 3 * math.pi) < 1e-9
