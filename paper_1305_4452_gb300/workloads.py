@@ -21,6 +21,12 @@ assembly or solver arithmetic.
   control points on circles (radius at the radial Greville abscissae, angles
   2 pi j / n for the n wrapped angular functions), weights 1; optionally extruded in
   z.  A smooth closed approximation of the circle, positively oriented.
+* ``unclamp_curve``: Sec. 2.4's unclamping of a curve's control points (the task of
+  Algorithm 1): the knot vector is unclamped by Eqs. (unclamp-left)-(unclamp-right) and
+  the new control points are the unique ones that reproduce the curve on the parametric
+  domain -- here found by collocation (a linear solve at n+1 points of the domain), not by
+  the printed loop.  With a closed curve of C^k continuity across the seam, the first and
+  last k+1 unclamped control points coincide, and the periodic space keeps n-k of them.
 * ``full_annulus``: the exact NURBS annulus (inner radius 1, outer 2) as a closed
   curve of four rational quadratic quarter arcs (C^0 at the quarter points, knots of
   multiplicity p there), raised to degree p and refined uniformly per quarter; its
@@ -173,6 +179,47 @@ def ring(nel_r, nel_t, p, r_in=1.0, r_out=2.0, nel_z=None, height=1.0):
     X[..., 1] = np.sin(th)[None, :, None] * r[None, None, :]
     X[..., 2] = z[:, None, None]
     return [kr, kt, kz], X.reshape(-1, 3)
+
+
+def _unclamp_knots(U, p, k):
+    X = np.array(U, dtype=np.float64)
+    m = len(X) - 1
+    n = m - p - 1
+    for i in range(k + 1):
+        X[k - i] = X[p] - X[n + 1] + X[n - i]
+    for i in range(k + 1):
+        X[m - k + i] = X[n + 1] - X[p] + X[p + i + 1]
+    return X
+
+
+def _basis_row(U, p, nfun, xi):
+    """Values of the nfun B-splines of knot vector U at xi (Cox-de Boor, degree by degree),
+    xi strictly inside the domain [U_p, U_{nfun}]."""
+    N = np.zeros(len(U) - 1)
+    s = int(np.searchsorted(U, xi, side="right")) - 1
+    N[s] = 1.0
+    for d in range(1, p + 1):
+        M = np.zeros_like(N)
+        for i in range(len(U) - d - 1):
+            a = (xi - U[i]) / (U[i + d] - U[i]) * N[i] if U[i + d] > U[i] else 0.0
+            b = (U[i + d + 1] - xi) / (U[i + d + 1] - U[i + 1]) * N[i + 1] if U[i + d + 1] > U[i + 1] else 0.0
+            M[i] = a + b
+        N = M
+    return N[:nfun]
+
+
+def unclamp_curve(U, Pw, p, k):
+    """Unclamped knot vector and control points (homogeneous, rows of Pw) of the curve
+    sum_i N_i(xi; U) Pw_i, for C^k periodicity (Sec. 2.4): same curve on [U_p, U_{n+1}]."""
+    U = np.asarray(U, dtype=np.float64)
+    Pw = np.asarray(Pw, dtype=np.float64)
+    nfun = len(U) - p - 1
+    V = _unclamp_knots(U, p, k)
+    lo, hi = U[p], U[nfun]
+    xs = lo + (hi - lo) * (np.arange(nfun) + 0.5) / nfun  # interior collocation points
+    A = np.array([_basis_row(V, p, nfun, x) for x in xs])
+    C = np.array([_basis_row(U, p, nfun, x) @ Pw for x in xs])
+    return V, np.linalg.solve(A, C)
 
 
 def full_annulus(nel_r, nel_q, p=2, r_in=1.0, r_out=2.0):

@@ -655,3 +655,40 @@ def test_exact_full_annulus_as_a_periodic_space():
         K = P.jacobian_csr(np.zeros(P.N))
         assert np.abs(K @ np.ones(P.N)).max() < 1e-13
         assert abs(P.mass().sum() - 3 * math.pi) < 1e-9
+
+
+def test_unclamping_a_curve_keeps_it():
+    """Sec. 2.4 (Algorithm 1's task): a quarter arc of degree four, unclamped for C^0-C^3,
+    traces the same points on the parametric domain (evaluated with the oracle's
+    Cox-de Boor recursion on both knot vectors)."""
+    s = math.sqrt(0.5)
+    U, Pw = W._refine_curve(np.array([[1.0, 0, 1], [s, s, s], [0, 1, 1.0]]), 4, 3)
+    n = len(Pw)
+    for k in range(4):
+        V, Q = W.unclamp_curve(U, Pw, 4, k)
+        assert np.abs(V - O.unclamp_knots(U, 4, k)).max() < 1e-15
+        for xi in np.linspace(0.003, 0.997, 40):
+            a = sum(O.bspline(i, 4, U, xi) * Pw[i] for i in range(n))
+            b = sum(O.bspline(i, 4, V, xi) * Q[i] for i in range(n))
+            assert np.abs(a - b).max() < 1e-13, (k, xi)
+
+
+def test_unclamping_a_closed_curve_gives_periodic_control_points():
+    """A closed uniform C^(p-1) curve written on the clamped knot vector (control points by
+    least squares on the oracle's basis) unclamps to control points whose last p equal the
+    first p: the wrapped periodic space's control points."""
+    p, nel = 3, 8
+    th = 2 * math.pi * np.arange(nel) / nel
+    P = np.stack([np.cos(th), np.sin(th), np.ones(nel)], axis=1)   # periodic control points
+    Pext = np.concatenate([P, P[:p]])                               # unclamped numbering
+    U = O.open_uniform_knots(nel, p)
+    V = O.unclamp_knots(U, p, p - 1)
+    n = nel + p
+    xs = np.linspace(0.001, 0.999, 4 * n)
+    C = np.array([sum(O.bspline(i, p, V, x) * Pext[i] for i in range(n)) for x in xs])
+    B = np.array([[O.bspline(i, p, U, x) for i in range(n)] for x in xs])
+    Q = np.linalg.lstsq(B, C, rcond=None)[0]                         # the clamped description
+    V2, P2 = W.unclamp_curve(U, Q, p, p - 1)
+    assert np.abs(V2 - V).max() < 1e-15
+    assert np.abs(P2 - Pext).max() < 1e-11
+    assert np.abs(P2[-p:] - P2[:p]).max() < 1e-11
