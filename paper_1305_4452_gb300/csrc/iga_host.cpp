@@ -291,6 +291,9 @@ static iga_status build_dir(iga_s *h, const iga_desc *d, int ax, Dir &D) {
     }
     D.pair_T[k] = D.pair_off[j] + (i - D.l[j]);
   }
+  D.pair_c.clear();
+  for (size_t k = 0; k < D.pair_j.size(); k++)
+    if ((int)k <= D.pair_T[k]) D.pair_c.push_back((int)k);
   return IGA_OK;
 }
 

@@ -61,6 +61,7 @@ struct Dir {
   std::vector<int> pair_po;    // [P] offset into pair_val (in points)
   std::vector<double> pair_val;// [sum np][5]: B_i B_j, B'_i B_j, B_i B'_j, B'_i B'_j, B'_i B_j + B_i B'_j
   std::vector<int> pair_T;     // [P] index of the transposed pair (j, i)
+  std::vector<int> pair_c;     // canonical pairs (pair index <= that of its transpose), ascending
   std::vector<int> node_e0;    // [n] first element containing the function
   std::vector<int> node_ne;    // [n] number of elements containing it
   int npairs() const { return (int)pair_j.size(); }
@@ -75,6 +76,7 @@ struct DirDev {
   double *wq;
   int *l, *r;
   int *pair_off, *pair_i, *pair_j, *pair_x0, *pair_np, *pair_po, *pair_T;
+  int nc, *pair_c;
   double *pair_val;
   float *pair_val_f;  // FP32 copy for the mixed-precision stages
   int *node_e0, *node_ne;
@@ -87,6 +89,8 @@ struct DirArgs {  // passed by value to kernels
   const double *wq;
   const int *l, *r;
   const int *pair_off, *pair_i, *pair_j, *pair_x0, *pair_np, *pair_po, *pair_T;
+  int nc;
+  const int *pair_c;
   const double *pair_val;
   const float *pair_val_f;
   const int *node_e0, *node_ne;

@@ -11,8 +11,10 @@
 // pattern in the remaining directions are added, and Q's symmetry makes some
 // partial sums the pair-transposes of others, so the stiffness needs 10, 7 and 4
 // one-dimensional contractions per output in 3D (6 and 4 in 2D) instead of
-// 16, 9 and 4.  The reaction term alone (Q00 only) is one chain of single
-// contractions and can be added onto a previously assembled stiffness.
+// 16, 9 and 4; stage 1 also forms the transpose-invariant groups once per pair of
+// transposed 1D pairs.  On an identity map with unit weights (g = 0, S diagonal) the
+// counts drop to 4, 3 and 2 (2D: 3 and 2).  The reaction term alone (Q00 only) is one
+// chain of single contractions and can be added onto a previously assembled stiffness.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -22,7 +24,7 @@ namespace {
 
 template <int DIM> __host__ __device__ constexpr int ipow(int b) { return DIM == 2 ? b * b : b * b * b; }
 
-enum { PLAN_STIFF = 0, PLAN_MASS = 1 };
+enum { PLAN_STIFF = 0, PLAN_MASS = 1, PLAN_DIAG = 2 };
 
 struct CsrArgs {
   const int64_t *rowptr;
@@ -35,8 +37,8 @@ template <> __device__ __forceinline__ const double *ptab<double>(const DirArgs 
 template <> __device__ __forceinline__ const float *ptab<float>(const DirArgs &d) { return d.pair_val_f; }
 
 template <int PLAN, int DIM> struct Shape {
-  // Q slots read by stage 1; stored groups: stage 1 6 (3D) / 3 (2D), stage 2 3 (1 for PLAN_MASS)
-  static constexpr int NS = (PLAN == PLAN_MASS) ? 1 : (DIM == 3 ? 10 : 6);
+  // Q slots read by stage 1
+  static constexpr int NS = (PLAN == PLAN_MASS) ? 1 : (PLAN == PLAN_DIAG ? DIM + 1 : (DIM == 3 ? 10 : 6));
 };
 
 // Stage 1: one CTA per Gauss line (x1, x2); contract axis 0.
@@ -46,6 +48,14 @@ template <int PLAN, int DIM> struct Shape {
 //   3D: G0 (00,00)  G1 (10,00)  G2 (11,00)  G3 (00,10)  G4 (10,01)  G5 (00,11)
 //       [(01,00), (00,01), (01,10) are the pair-transposes of G1, G3, G4]
 //   2D: G0 (00)  G1 (10)  G2 (11)   [(01) is the transpose of G1]
+// G0, G2, G4 and G5 (2D: G0, G2) do not change when the axis-0 pair is transposed
+// (their 1D factors are B_i B_j, B'_i B'_j and B'_i B_j + B_i B'_j), so each thread
+// takes a canonical pair (i <= j in pair order), forms those once and writes them at
+// the pair and at its transpose; G1 and G3 are formed for both, with B_i B'_j for the
+// pair and B'_i B_j (the transpose's B_j B'_i) for the transpose.  The values are those
+// of the per-pair contraction: the same factors in the same order.
+// PLAN_DIAG (identity map, unit weights: g = 0 and S diagonal, so Q_0a and S_ab,
+// a != b, vanish): G0, G2, G5 only (2D: G0, G2), from Q00 and the three diagonal S.
 // The reaction-only plan has one contraction per output, so a CTA takes
 // STAGE1_MASS_LINES consecutive axis-1 lines to give its threads enough work.
 constexpr int STAGE1_MASS_LINES = 8;
@@ -53,6 +63,7 @@ constexpr int STAGE1_MASS_LINES = 8;
 template <typename T, int DIM, int P, int PLAN>
 __global__ void __launch_bounds__(256) k_stage1(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ geom,
                                                 const double *__restrict__ Q00, GeomLayout gl, T *__restrict__ out) {
+  const T *tab = ptab<T>(d0);
   if (PLAN == PLAN_MASS) {
     // lines x1 = blockIdx.x * LINES + l; each line's Q00 in shared memory
     constexpr int Q = P + 1, NQ = ipow<DIM>(Q), LINES = STAGE1_MASS_LINES;
@@ -68,9 +79,9 @@ __global__ void __launch_bounds__(256) k_stage1(DirArgs d0, DirArgs d1, DirArgs 
       lines[idx] = (T)Q00[(size_t)e * NQ + g0 + Q * (g1 + Q * g2)];
     }
     __syncthreads();
-    // one pair per thread, all lines at once: each table value serves LINES FMAs
-    const T *tab = ptab<T>(d0);
-    for (int pi = threadIdx.x; pi < d0.np; pi += blockDim.x) {
+    // one canonical pair per thread, all lines at once: each table value serves LINES FMAs
+    for (int c = threadIdx.x; c < d0.nc; c += blockDim.x) {
+      const int pi = d0.pair_c[c], piT = d0.pair_T[pi];
       const int xs = d0.pair_x0[pi], np = d0.pair_np[pi];
       const T *pv = tab + (size_t)d0.pair_po[pi] * IGA_PVS;
       T acc[LINES];
@@ -83,7 +94,11 @@ __global__ void __launch_bounds__(256) k_stage1(DirArgs d0, DirArgs d1, DirArgs 
       }
 #pragma unroll
       for (int l = 0; l < LINES; l++)
-        if (l < nl) out[((size_t)x2 * d1.X + x1a + l) * d0.np + pi] = acc[l];
+        if (l < nl) {
+          T *o = out + ((size_t)x2 * d1.X + x1a + l) * d0.np;
+          o[pi] = acc[l];
+          o[piT] = acc[l];
+        }
     }
     return;
   }
@@ -101,34 +116,43 @@ __global__ void __launch_bounds__(256) k_stage1(DirArgs d0, DirArgs d1, DirArgs 
     int qp = g0 + Q * (g1 + Q * g2);
     int f;
     if (s == 0) f = -1;
+    else if (PLAN == PLAN_DIAG) f = gl.S + (s - 1);
     else if (DIM == 3) f = (s <= 6) ? gl.S + (s - 1) : gl.Sg + (s - 7);
     else f = (s <= 3) ? gl.S + (s - 1) : gl.Sg + (s - 4);
     line[idx] = (T)((f < 0) ? Q00[(size_t)e * NQ + qp] : geom[((size_t)e * gl.nf + f) * NQ + qp]);
   }
   __syncthreads();
   const size_t plane = (size_t)d0.np * d1.X * (DIM == 3 ? d2.X : 1);
-  const size_t lineoff = ((size_t)x2 * d1.X + x1) * d0.np;
-  const T *tab = ptab<T>(d0);
-  for (int pi = threadIdx.x; pi < d0.np; pi += blockDim.x) {
+  T *const ol = out + ((size_t)x2 * d1.X + x1) * d0.np;
+  for (int c = threadIdx.x; c < d0.nc; c += blockDim.x) {
+    const int pi = d0.pair_c[c], piT = d0.pair_T[pi];
     const int xs = d0.pair_x0[pi], np = d0.pair_np[pi];
     const T *pv = tab + (size_t)d0.pair_po[pi] * IGA_PVS;
     const T *L = line + xs;
-    T a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
+    // a*: the pair's groups (G0..G5); b1, b3: G1, G3 of the transposed pair
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0, b1 = 0, b3 = 0;
     for (int k = 0; k < np; k++) {
-      const T p00 = pv[IGA_PVS * k + 0];
-      if (PLAN == PLAN_MASS) {
+      const T p00 = pv[IGA_PVS * k + 0], p11 = pv[IGA_PVS * k + 3];
+      if (PLAN == PLAN_DIAG) {
         a0 = fma(p00, L[k], a0);
+        a0 = fma(p11, L[1 * X0 + k], a0);
+        a2 = fma(p00, L[2 * X0 + k], a2);
+        if (DIM == 3) a5 = fma(p00, L[3 * X0 + k], a5);
       } else {
-        const T p01 = pv[IGA_PVS * k + 2], p11 = pv[IGA_PVS * k + 3], psym = pv[IGA_PVS * k + 4];
+        const T p10 = pv[IGA_PVS * k + 1], p01 = pv[IGA_PVS * k + 2], psym = pv[IGA_PVS * k + 4];
         if (DIM == 3) {
           a0 = fma(p00, L[k], a0);
           a0 = fma(psym, L[7 * X0 + k], a0);
           a0 = fma(p11, L[1 * X0 + k], a0);
           a1 = fma(p00, L[8 * X0 + k], a1);
           a1 = fma(p01, L[4 * X0 + k], a1);
+          b1 = fma(p00, L[8 * X0 + k], b1);
+          b1 = fma(p10, L[4 * X0 + k], b1);
           a2 = fma(p00, L[2 * X0 + k], a2);
           a3 = fma(p00, L[9 * X0 + k], a3);
           a3 = fma(p01, L[5 * X0 + k], a3);
+          b3 = fma(p00, L[9 * X0 + k], b3);
+          b3 = fma(p10, L[5 * X0 + k], b3);
           a4 = fma(p00, L[6 * X0 + k], a4);
           a5 = fma(p00, L[3 * X0 + k], a5);
         } else {
@@ -137,19 +161,27 @@ __global__ void __launch_bounds__(256) k_stage1(DirArgs d0, DirArgs d1, DirArgs 
           a0 = fma(p11, L[1 * X0 + k], a0);
           a1 = fma(p00, L[5 * X0 + k], a1);
           a1 = fma(p01, L[3 * X0 + k], a1);
+          b1 = fma(p00, L[5 * X0 + k], b1);
+          b1 = fma(p10, L[3 * X0 + k], b1);
           a2 = fma(p00, L[2 * X0 + k], a2);
         }
       }
     }
-    T *o = out + lineoff + pi;
-    o[0] = a0;
-    if (PLAN == PLAN_STIFF) {
-      o[plane] = a1;
+    // the transposed pair's slots; for a pair that is its own transpose b1, b3 equal a1, a3
+    const int pj[2] = {pi, piT};
+#pragma unroll
+    for (int t = 0; t < 2; t++) {
+      if (t == 1 && piT == pi) break;
+      T *o = ol + pj[t];
+      o[0] = a0;
       o[2 * plane] = a2;
+      if (PLAN == PLAN_STIFF) o[plane] = t ? b1 : a1;
       if (DIM == 3) {
-        o[3 * plane] = a3;
-        o[4 * plane] = a4;
         o[5 * plane] = a5;
+        if (PLAN == PLAN_STIFF) {
+          o[3 * plane] = t ? b3 : a3;
+          o[4 * plane] = a4;
+        }
       }
     }
   }
@@ -161,6 +193,7 @@ __global__ void __launch_bounds__(256) k_stage1(DirArgs d0, DirArgs d1, DirArgs 
 //   H2 (axis-2 pattern 11) = P^00 G5          [pattern 01 is the transpose of H1]
 // H0 and H2 are unchanged when both pairs are transposed, so they are formed only
 // for pi1 <= pi1T; the final stage reads them at (pi1T, pi0T) otherwise.
+// PLAN_DIAG: H0 = P^00 G0 + P^11 G2, H2 = P^00 G5 (G1, G3, G4 and so H1 vanish).
 template <typename T, int PLAN>
 __global__ void __launch_bounds__(128) k_stage2(DirArgs d0, DirArgs d1, DirArgs d2, const T *__restrict__ in,
                                                 T *__restrict__ out, int chunk) {
@@ -174,7 +207,7 @@ __global__ void __launch_bounds__(128) k_stage2(DirArgs d0, DirArgs d1, DirArgs 
   const T *tab = ptab<T>(d1);
   for (int pi1 = pa; pi1 < pb; pi1++) {
     const bool sym = pi1 <= d1.pair_T[pi1];  // uniform across the block
-    if (PLAN == PLAN_MASS && !sym) continue;
+    if (PLAN != PLAN_STIFF && !sym) continue;
     const int xs = d1.pair_x0[pi1], np = d1.pair_np[pi1];
     const T *pv = tab + (size_t)d1.pair_po[pi1] * IGA_PVS;
     T h0 = 0, h1 = 0, h2 = 0;
@@ -183,6 +216,10 @@ __global__ void __launch_bounds__(128) k_stage2(DirArgs d0, DirArgs d1, DirArgs 
       const T p00 = pv[IGA_PVS * k + 0];
       if (PLAN == PLAN_MASS) {
         h0 = fma(p00, in[row + pi0], h0);
+      } else if (PLAN == PLAN_DIAG) {
+        h0 = fma(p00, in[row + pi0], h0);
+        h0 = fma(pv[IGA_PVS * k + 3], in[2 * inplane + row + pi0], h0);
+        h2 = fma(p00, in[5 * inplane + row + pi0], h2);
       } else {
         const T p01 = pv[IGA_PVS * k + 2];
         if (sym) {
@@ -199,10 +236,8 @@ __global__ void __launch_bounds__(128) k_stage2(DirArgs d0, DirArgs d1, DirArgs 
     }
     T *o = out + ((size_t)x2 * d1.np + pi1) * d0.np + pi0;
     if (sym) o[0] = h0;
-    if (PLAN == PLAN_STIFF) {
-      o[outplane] = h1;
-      if (sym) o[2 * outplane] = h2;
-    }
+    if (PLAN == PLAN_STIFF) o[outplane] = h1;
+    if (PLAN != PLAN_MASS && sym) o[2 * outplane] = h2;
   }
 }
 
@@ -218,6 +253,7 @@ __device__ __forceinline__ bool on_dirichlet(const BndArgs &b, int dim, const in
 // Final stage: contract the last axis and write the CSR entries.
 //   3D: in = T2[g2][x2][pi1][pi0];  J = P^00 H0 + P^10 H1 + P^01 H1^T + P^11 H2
 //   2D: in = T1[g1][x1][pi0];       J = P^00 G0 + P^10 G1 + P^01 G1^T + P^11 G2
+//   PLAN_DIAG: the H1 (2D: G1) terms vanish.
 // vals = base + contribution (base optional).  fix = 1: entries in Dirichlet rows
 // or columns become those of an identity row and a zeroed column instead.
 // J is symmetric (Q is), so only the entries whose pair triple (pl, pmid, pi0)
@@ -265,6 +301,9 @@ __global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d
       const size_t rs = (DIM == 2 || mid_sym) ? r : rT;
       if (PLAN == PLAN_MASS) {
         acc = fma(p00, in[rs], acc);
+      } else if (PLAN == PLAN_DIAG) {
+        acc = fma(p00, in[rs], acc);
+        acc = fma(pv[IGA_PVS * k + 3], in[2 * plane + rs], acc);
       } else {
         const T p10 = pv[IGA_PVS * k + 1], p01 = pv[IGA_PVS * k + 2], p11 = pv[IGA_PVS * k + 3];
         acc = fma(p00, in[rs], acc);
@@ -365,6 +404,9 @@ cudaError_t jacobian(iga_s *h, const double *U, V *vals, int mode, const V *base
     return h->dim == 3 ? run_stages<T, V, 3, PLAN_MASS>(h, vals, base, 1) : run_stages<T, V, 2, PLAN_MASS>(h, vals, base, 1);
   }
   const int fix = (mode == 1 || mode == 3) ? 0 : 1;
+  // identity map with unit weights: the geometry factors are g = 0 and a diagonal S
+  if (!h->has_geom && !h->has_w)
+    return h->dim == 3 ? run_stages<T, V, 3, PLAN_DIAG>(h, vals, nullptr, fix) : run_stages<T, V, 2, PLAN_DIAG>(h, vals, nullptr, fix);
   return h->dim == 3 ? run_stages<T, V, 3, PLAN_STIFF>(h, vals, nullptr, fix) : run_stages<T, V, 2, PLAN_STIFF>(h, vals, nullptr, fix);
 }
 
