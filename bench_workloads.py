@@ -207,9 +207,17 @@ def batch512(torch, iga, W, clock):
             t = time.perf_counter()
             r = b.solve(U, o)
             best = min(best, time.perf_counter() - t)
+        us = r["solve_us"]
+        big = int(np.argmax(us))
         res[label] = {"ms": best * 1e3, "solves_per_s": 512 / best, "solved": int(r["solved"]),
                       "newton_its_total": int(r["newton_its"].sum()), "krylov_its_total": int(r["krylov_its"].sum()),
-                      "max_fnorm": float(r["fnorm"].max())}
+                      "max_fnorm": float(r["fnorm"].max()),
+                      # load balance: the longest instance against the sum of all over the SMs
+                      "instance_ms": {"max": float(us[big]) / 1e3, "sum": float(us.sum()) / 1e3,
+                                      "sum_over_sms": float(us.sum()) / 1e3 / torch.cuda.get_device_properties(0).multi_processor_count,
+                                      "longest": {"n": int(ins[big]["nel"]), "p": int(ins[big]["p"]),
+                                                  "newton_its": int(r["newton_its"][big]),
+                                                  "krylov_its": int(r["krylov_its"][big])}}}
     ck = clock.stop()
     b.close()
     import oracle as O

@@ -285,6 +285,8 @@ typedef struct {
   int *krylov_its;
   double *fnorm;
   int *status;      /* iga_status per instance */
+  double *solve_us; /* device time of each instance's solve in microseconds (%globaltimer
+                       from the first to the last step of the CTA that solved it), or NULL */
 } iga_batch_report;
 iga_status iga_batch_create(int count, const iga_desc *descs, const iga_bratu *params, void *stream,
                             iga_batch_t *out);

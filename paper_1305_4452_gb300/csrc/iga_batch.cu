@@ -43,8 +43,6 @@ struct BMesh {  // device data shared by instances with the same knots (square m
   const int *first, *node_e0, *node_ne, *l, *r;
   const int *pair_off, *pair_i, *pair_x0, *pair_np, *pair_po;
   const float *pair_val;  // [pts][5]
-  const int64_t *rowptr;
-  const int32_t *colidx;
 };
 
 struct BInst {
@@ -56,8 +54,20 @@ struct BInst {
   const float *ck32, *cr32;
   double *F, *dU, *Ut, *Ft, *dinv, *w, *V;  // V: (mmax+1) x N
   double *Fe;            // [nelem][nen]
-  float *J, *T1, *q00, *z32;
+  float *J;              // Jacobian values, sliced by 32 rows (see jslot)
+  float *T1, *q00, *z32;
 };
+
+// The batch Jacobian is stored by slices of 32 consecutive rows, slot-major within a
+// slice: slot s = (j1 - l(i1)) (2p+1) + (j0 - l(i0)) of row A = (i0, i1) is at
+// J[(A / 32) 32 (2p+1)^2 + 32 s + A % 32], so that a warp's loads of one slot for its 32
+// rows are one 128-byte access.  Slots outside a row's stencil stay zero.
+__host__ __device__ __forceinline__ int64_t jslot(int A, int s, int wf) {
+  return (int64_t)(A >> 5) * 32 * wf * wf + 32 * s + (A & 31);
+}
+__host__ __device__ __forceinline__ int64_t jsize(int N, int p) {
+  return (int64_t)((N + 31) / 32) * 32 * (2 * p + 1) * (2 * p + 1);
+}
 
 struct BArgs {
   double *U;
@@ -67,11 +77,19 @@ struct BArgs {
 struct BRep {
   int newton_its, krylov_its, status, pad;
   double fnorm0, fnorm;
+  uint64_t t0, t1;  // %globaltimer (ns) at the start and the end of the instance's solve
 };
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 struct Cta {
   int tid, nt, lane, warp, nw;
-  double *red;  // shared, >= 34 doubles
+  double *red;  // shared, >= 36 doubles
+  float *zs;    // shared FP32 operand vector of the operator products (N floats), or null
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -93,6 +111,37 @@ __device__ double cta_sum(const Cta &c, double v) {
   double r = c.red[33];
   __syncthreads();
   return r;
+}
+
+// two block sums at once (one pair of barriers fewer), each in the order of cta_sum
+__device__ void cta_sum2(const Cta &c, double &a, double &b) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if (c.lane == 0) {
+    c.red[c.warp] = a;
+    c.red[16 + c.warp] = b;
+  }
+  __syncthreads();
+  if (c.warp == 0) {
+    double r = (c.lane < c.nw) ? c.red[c.lane] : 0.0;
+    double t = (c.lane < c.nw) ? c.red[16 + c.lane] : 0.0;
+    r = warp_sum(r);
+    t = warp_sum(t);
+    if (c.lane == 0) {
+      c.red[34] = r;
+      c.red[35] = t;
+    }
+  }
+  __syncthreads();
+  a = c.red[34];
+  b = c.red[35];
+  __syncthreads();
+}
+
+// slot of the diagonal entry of row A
+__device__ __forceinline__ int diag_slot(const BMesh &M, int A, int wf) {
+  const int i0 = A % M.n, i1 = A / M.n;
+  return (i1 - M.l[i1]) * wf + (i0 - M.l[i0]);
 }
 
 __device__ __forceinline__ bool on_bnd(int i0, int i1, int n) { return i0 == 0 || i1 == 0 || i0 == n - 1 || i1 == n - 1; }
@@ -258,22 +307,40 @@ __device__ void b_jacobian(const BInst &I, const double *__restrict__ U, float *
     const int i0 = M.pair_i[p0], i1 = M.pair_i[p1];
     const int j0 = M.l[i0] + (p0 - M.pair_off[i0]), j1 = M.l[i1] + (p1 - M.pair_off[i1]);
     const int A = i0 + M.n * i1, B = j0 + M.n * j1;
-    const int w0 = M.r[i0] - M.l[i0] + 1;
     if (on_bnd(i0, i1, M.n) || on_bnd(j0, j1, M.n)) acc = (A == B) ? 1.f : 0.f;
-    J[M.rowptr[A] + (int64_t)(p1 - M.pair_off[i1]) * w0 + (p0 - M.pair_off[i0])] = acc;
+    J[jslot(A, (p1 - M.pair_off[i1]) * (2 * P + 1) + (p0 - M.pair_off[i0]), 2 * P + 1)] = acc;
   }
   __syncthreads();
 }
 
 // ------------------------------------------------------------------- GMRES --
-// y = J (dinv .* v) (scaled) or y = J v, with FP32 products; z32 holds the FP32 operand
+// y = J (dinv .* v) (scaled) or y = J v, with FP32 products.  The FP32 operand goes to
+// shared memory (c.zs; the global z32 when it does not fit).  Row A = (i0, i1) holds the
+// columns (j0, j1), j1 in [l(i1), r(i1)] outer and j0 in [l(i0), r(i0)] inner, so the
+// column indices follow from the 1D stencils and no index is loaded.  Every row runs the
+// same unrolled (2P+1)^2 slots: the thread of row A is lane A % 32 of the warp that owns
+// A's slice, so each slot is one coalesced load; a slot outside the row's stencil holds
+// zero and reads a column of the row (clamped), so it adds nothing and the sum is the one
+// over the row's own columns in their order.
+template <int P>
 __device__ void b_apply(const BInst &I, const double *__restrict__ v, double *__restrict__ y, bool scaled, const Cta &c) {
+  constexpr int WF = 2 * P + 1;
   const BMesh &M = I.m;
-  for (int r = c.tid; r < M.N; r += c.nt) I.z32[r] = (float)(scaled ? I.dinv[r] * v[r] : v[r]);
+  const int n = M.n, N = M.N;
+  float *z = c.zs ? c.zs : I.z32;
+  for (int r = c.tid; r < N; r += c.nt) z[r] = (float)(scaled ? I.dinv[r] * v[r] : v[r]);
   __syncthreads();
-  for (int r = c.tid; r < M.N; r += c.nt) {
+  for (int r = c.tid; r < N; r += c.nt) {
+    const int i0 = r % n, i1 = r / n;
+    const int l0 = M.l[i0], m0 = M.r[i0] - l0, l1 = M.l[i1], m1 = M.r[i1] - l1;
+    const float *Jr = I.J + jslot(r, 0, WF);
     float acc = 0.f;
-    for (int64_t k = M.rowptr[r]; k < M.rowptr[r + 1]; k++) acc = fmaf(I.J[k], I.z32[M.colidx[k]], acc);
+#pragma unroll
+    for (int b = 0; b < WF; b++) {
+      const float *zr = z + l0 + (int64_t)n * (l1 + min(b, m1));
+#pragma unroll
+      for (int a = 0; a < WF; a++) acc = fmaf(Jr[32 * (b * WF + a)], zr[min(a, m0)], acc);
+    }
     y[r] = (double)acc;
   }
   __syncthreads();
@@ -307,15 +374,14 @@ __device__ void b_cgs_pass(const BInst &I, double *__restrict__ w, int jp1, GmSh
 }
 
 // returns 0 converged, 1 cap reached, 2 breakdown/NaN
+template <int P>
 __device__ int b_gmres(const BInst &I, const double *__restrict__ b, double *__restrict__ x, double tol, int m, int maxit,
                        GmShared &s, const Cta &c, int *its) {
   const BMesh &M = I.m;
   const int N = M.N;
-  // Jacobi scaling from the diagonal (columns ascend: the diagonal is found by search)
+  // Jacobi scaling from the diagonal
   for (int r = c.tid; r < N; r += c.nt) {
-    double d = 0.0;
-    for (int64_t k = M.rowptr[r]; k < M.rowptr[r + 1]; k++)
-      if (M.colidx[k] == r) { d = (double)I.J[k]; break; }
+    const double d = (double)I.J[jslot(r, diag_slot(M, r, 2 * P + 1), 2 * P + 1)];
     I.dinv[r] = (d != 0.0) ? 1.0 / d : 1.0;
     x[r] = 0.0;
   }
@@ -329,7 +395,7 @@ __device__ int b_gmres(const BInst &I, const double *__restrict__ b, double *__r
       for (int r = c.tid; r < N; r += c.nt) V0[r] = b[r];
       __syncthreads();
     } else {
-      b_apply(I, x, I.w, false, c);  // x is in the unpreconditioned space: apply J itself
+      b_apply<P>(I, x, I.w, false, c);  // x is in the unpreconditioned space: apply J itself
       for (int r = c.tid; r < N; r += c.nt) V0[r] = b[r] - I.w[r];
       __syncthreads();
     }
@@ -350,7 +416,7 @@ __device__ int b_gmres(const BInst &I, const double *__restrict__ b, double *__r
     bool brk = false;
     for (int j = 0; j < m && total + j < maxit; j++) {
       double *w = I.w;
-      b_apply(I, I.V + (size_t)j * N, w, true, c);
+      b_apply<P>(I, I.V + (size_t)j * N, w, true, c);
       b_cgs_pass(I, w, j + 1, s, j, true, c);
       b_cgs_pass(I, w, j + 1, s, j, false, c);
       double ww = 0.0;
@@ -411,6 +477,7 @@ __device__ int b_gmres(const BInst &I, const double *__restrict__ b, double *__r
 
 // Jacobi-preconditioned conjugate gradients (the -ksp_type cg solve of App. B):
 // FP64 vectors and reductions, FP32 operator products.  0 converged, 1 cap, 2 breakdown.
+template <int P>
 __device__ int b_cg(const BInst &I, const double *__restrict__ b, double *__restrict__ x, double tol, int maxit, const Cta &c,
                     int *its) {
   const BMesh &M = I.m;
@@ -418,9 +485,7 @@ __device__ int b_cg(const BInst &I, const double *__restrict__ b, double *__rest
   double *r = I.w;  // residual (the GMRES work vector; p and q use the first two basis slots)
   double *p = I.V, *q = I.V + N;
   for (int i = c.tid; i < N; i += c.nt) {
-    double d = 0.0;
-    for (int64_t k = M.rowptr[i]; k < M.rowptr[i + 1]; k++)
-      if (M.colidx[k] == i) { d = (double)I.J[k]; break; }
+    const double d = (double)I.J[jslot(i, diag_slot(M, i, 2 * P + 1), 2 * P + 1)];
     I.dinv[i] = (d != 0.0) ? 1.0 / d : 1.0;
   }
   __syncthreads();
@@ -432,13 +497,12 @@ __device__ int b_cg(const BInst &I, const double *__restrict__ b, double *__rest
     rz = fma(b[i], p[i], rz);
     rr = fma(b[i], b[i], rr);
   }
-  rz = cta_sum(c, rz);
-  rr = cta_sum(c, rr);
+  cta_sum2(c, rz, rr);
   int it = 0, rc = 1;
   if (!isfinite(rr)) rc = 2;
   else if (sqrt(rr) <= tol) rc = 0;
   while (rc == 1 && it < maxit) {
-    b_apply(I, p, q, false, c);
+    b_apply<P>(I, p, q, false, c);
     double pq = 0.0;
     for (int i = c.tid; i < N; i += c.nt) pq = fma(p[i], q[i], pq);
     pq = cta_sum(c, pq);
@@ -452,8 +516,7 @@ __device__ int b_cg(const BInst &I, const double *__restrict__ b, double *__rest
       rr2 = fma(ri, ri, rr2);
       rz2 = fma(ri, I.dinv[i] * ri, rz2);
     }
-    rr2 = cta_sum(c, rr2);
-    rz2 = cta_sum(c, rz2);
+    cta_sum2(c, rr2, rz2);
     it++;
     if (!isfinite(rr2)) { rc = 2; break; }
     if (sqrt(rr2) <= tol) { rc = 0; break; }
@@ -490,8 +553,8 @@ __device__ void b_solve(const BInst &I, double *__restrict__ U, const iga_newton
     double tol = rtol * fn;
     if (tol < 0.5 * o.atol) tol = 0.5 * o.atol;
     int its = 0;
-    if (o.ksp == IGA_KSP_CG) b_cg(I, Ft, dU, tol, o.max_krylov, c, &its);
-    else b_gmres(I, Ft, dU, tol, m, o.max_krylov, s, c, &its);
+    if (o.ksp == IGA_KSP_CG) b_cg<P>(I, Ft, dU, tol, o.max_krylov, c, &its);
+    else b_gmres<P>(I, Ft, dU, tol, m, o.max_krylov, s, c, &its);
     kry += its;
     double alpha = 1.0, ft = 0.0;
     bool ok = false;
@@ -525,12 +588,15 @@ __device__ void b_solve(const BInst &I, double *__restrict__ U, const iga_newton
 }
 
 constexpr int BTHREADS = 256;  // threads per CTA of the persistent kernel
+constexpr int BZCAP_MAX = 40960;  // floats of dynamic shared memory at most (160 KB)
 
 // MINB = 1: up to 255 registers, one resident CTA per SM; MINB = 2: 128 registers,
 // two or more resident CTAs per SM (more spills, more latency hiding).
 template <int MINB>
 __global__ void __launch_bounds__(BTHREADS, MINB) k_batch(const BInst *__restrict__ insts, const int *__restrict__ order, int count,
-                                                const BArgs *__restrict__ args, int *__restrict__ counter, BRep *__restrict__ reps) {
+                                                const BArgs *__restrict__ args, int *__restrict__ counter, BRep *__restrict__ reps,
+                                                int zcap) {
+  extern __shared__ float zs_dyn[];  // [zcap]: the operand vector of instances with N <= zcap
   __shared__ double red[40];
   __shared__ GmShared s;
   __shared__ int cur;
@@ -541,6 +607,7 @@ __global__ void __launch_bounds__(BTHREADS, MINB) k_batch(const BInst *__restric
   c.warp = threadIdx.x >> 5;
   c.nw = blockDim.x >> 5;
   c.red = red;
+  c.zs = nullptr;
   const iga_newton_opts o = args->opts;
   for (;;) {
     if (c.tid == 0) cur = atomicAdd(counter, 1);
@@ -551,11 +618,14 @@ __global__ void __launch_bounds__(BTHREADS, MINB) k_batch(const BInst *__restric
     const int idx = order[k];
     const BInst I = insts[idx];
     double *U = args->U + I.uoff;
+    c.zs = I.m.N <= zcap ? zs_dyn : nullptr;
+    if (c.tid == 0) reps[idx].t0 = gtimer();
     switch (I.m.p) {
       case 1: b_solve<1>(I, U, o, s, reps + idx, c); break;
       case 2: b_solve<2>(I, U, o, s, reps + idx, c); break;
       default: b_solve<3>(I, U, o, s, reps + idx, c); break;
     }
+    if (c.tid == 0) reps[idx].t1 = gtimer();
   }
 }
 
@@ -616,6 +686,7 @@ struct iga_batch_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int graph_threads = 0, graph_ctas = 0;
+  int zcap = 0;                    // floats of dynamic shared memory for the operand vector
   std::string err;
   int mmax = 0;
 };
@@ -668,13 +739,6 @@ static iga_status build_mesh(iga_batch_s *b, const iga_desc *d, MeshHost &mh) {
   }
   std::vector<int64_t> rowptr;
   iga_rowptr(&tmp, rowptr);
-  std::vector<int32_t> colidx(rowptr.back());
-  for (int64_t A = 0; A < tmp.N; A++) {
-    int i0 = (int)(A % D.n), i1 = (int)(A / D.n);
-    int64_t k = rowptr[A];
-    for (int j1 = D.l[i1]; j1 <= D.r[i1]; j1++)
-      for (int j0 = D.l[i0]; j0 <= D.r[i0]; j0++) colidx[k++] = j0 + D.n * j1;
-  }
   BMesh &M = mh.dev;
   M.p = D.p; M.q = D.q; M.nel = D.nel; M.n = D.n; M.np = D.npairs(); M.N = (int)tmp.N; M.nnz = rowptr.back();
   std::vector<float> pv(D.pair_val.begin(), D.pair_val.end());
@@ -685,8 +749,7 @@ static iga_status build_mesh(iga_batch_s *b, const iga_desc *d, MeshHost &mh) {
       (ce = upload_v(mh.bufs, &M.r, D.r)) || (ce = upload_v(mh.bufs, &M.pair_off, D.pair_off)) ||
       (ce = upload_v(mh.bufs, &M.pair_i, D.pair_i)) || (ce = upload_v(mh.bufs, &M.pair_x0, D.pair_x0)) ||
       (ce = upload_v(mh.bufs, &M.pair_np, D.pair_np)) || (ce = upload_v(mh.bufs, &M.pair_po, D.pair_po)) ||
-      (ce = upload_v(mh.bufs, &M.pair_val, pv)) || (ce = upload_v(mh.bufs, &M.rowptr, rowptr)) ||
-      (ce = upload_v(mh.bufs, &M.colidx, colidx))) {
+      (ce = upload_v(mh.bufs, &M.pair_val, pv))) {
     b->err = iga_format("mesh upload: %s", cudaGetErrorString(ce));
     return ce == cudaErrorMemoryAllocation ? IGA_ENOMEM : IGA_ECUDA;
   }
@@ -743,17 +806,23 @@ static iga_status batch_create_impl(iga_batch_s *b, int count, const iga_desc *d
     const BMesh &M = b->meshes[mi[i]].dev;
     int64_t nelem = (int64_t)M.nel * M.nel, nq = (int64_t)M.q * M.q, nen = (int64_t)(M.p + 1) * (M.p + 1);
     b->uoff[i + 1] = b->uoff[i] + M.N;
+    b->zcap = std::max(b->zcap, M.N);
     dbl += 6 * (int64_t)M.N + (int64_t)(b->mmax + 1) * M.N + nelem * nen + 2 * nelem * nq + 8;
-    flt += M.nnz + 2 * (int64_t)M.nel * M.q * M.np + nelem * nq + M.N + 2 * nelem * nq + 8;
+    flt += jsize(M.N, M.p) + 32 + 2 * (int64_t)M.nel * M.q * M.np + nelem * nq + M.N + 2 * nelem * nq + 8;
     qpoff[i + 1] = qpoff[i] + nelem * nq;
   }
   qp_total = qpoff[count];
+  // the operand vector of the operator products lives in shared memory (up to 160 KB)
+  b->zcap = std::min(b->zcap, BZCAP_MAX);
+  for (auto kern : {k_batch<1>, k_batch<2>})
+    BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(b->zcap * sizeof(float))));
   double *dar = nullptr;
   float *far = nullptr;
   BCK(cudaMalloc((void **)&dar, dbl * sizeof(double)));
   b->bufs.push_back(dar);
   BCK(cudaMalloc((void **)&far, flt * sizeof(float)));
   b->bufs.push_back(far);
+  BCK(cudaMemset(far, 0, flt * sizeof(float)));  // the Jacobian slots outside the stencils stay zero
   std::vector<BInst> insts(count);
   double *dp = dar;
   float *fp = far;
@@ -775,7 +844,8 @@ static iga_status batch_create_impl(iga_batch_s *b, int count, const iga_desc *d
     I.w = dp; dp += M.N;
     I.V = dp; dp += (int64_t)(b->mmax + 1) * M.N;
     I.Fe = dp; dp += nelem * nen;
-    I.J = fp; fp += M.nnz;
+    fp = far + ((fp - far + 31) / 32) * 32;  // slices start on 128 bytes
+    I.J = fp; fp += jsize(M.N, M.p);
     I.T1 = fp; fp += 2 * (int64_t)M.nel * M.q * M.np;
     I.q00 = fp; fp += nelem * nq;
     I.z32 = fp; fp += M.N;
@@ -888,10 +958,11 @@ static cudaError_t batch_enqueue(iga_batch_s *b) {
   cudaMemcpyAsync(b->d_args, b->h_args, sizeof(BArgs), cudaMemcpyHostToDevice, b->stream);
   cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream);
   int grid = b->nsm * b->ctas_per_sm;
+  const size_t zb = (size_t)b->zcap * sizeof(float);
   if (b->ctas_per_sm == 1)
-    k_batch<1><<<grid, b->threads, 0, b->stream>>>(b->d_insts, b->d_order, b->count, b->d_args, b->d_counter, b->d_reps);
+    k_batch<1><<<grid, b->threads, zb, b->stream>>>(b->d_insts, b->d_order, b->count, b->d_args, b->d_counter, b->d_reps, b->zcap);
   else
-    k_batch<2><<<grid, b->threads, 0, b->stream>>>(b->d_insts, b->d_order, b->count, b->d_args, b->d_counter, b->d_reps);
+    k_batch<2><<<grid, b->threads, zb, b->stream>>>(b->d_insts, b->d_order, b->count, b->d_args, b->d_counter, b->d_reps, b->zcap);
   cudaMemcpyAsync(b->h_reps, b->d_reps, b->count * sizeof(BRep), cudaMemcpyDeviceToHost, b->stream);
   return cudaGetLastError();
 }
@@ -934,6 +1005,7 @@ extern "C" iga_status iga_batch_solve(iga_batch_t b, double *U, const iga_newton
       if (rep->krylov_its) rep->krylov_its[i] = b->h_reps[i].krylov_its;
       if (rep->fnorm) rep->fnorm[i] = b->h_reps[i].fnorm;
       if (rep->status) rep->status[i] = b->h_reps[i].status;
+      if (rep->solve_us) rep->solve_us[i] = 1e-3 * (double)(b->h_reps[i].t1 - b->h_reps[i].t0);
     }
   }
   if (solved != b->count) {

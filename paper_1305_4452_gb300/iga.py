@@ -344,7 +344,7 @@ def _wrap_device(ptr, n, dtype):
 # ------------------------------------------------------------------ batched ---
 class IgaBatchReport(ctypes.Structure):
     _fields_ = [("solved", ctypes.c_int), ("newton_its", ctypes.c_void_p), ("krylov_its", ctypes.c_void_p),
-                ("fnorm", ctypes.c_void_p), ("status", ctypes.c_void_p)]
+                ("fnorm", ctypes.c_void_p), ("status", ctypes.c_void_p), ("solve_us", ctypes.c_void_p)]
 
 
 def _batch_lib():
@@ -415,18 +415,21 @@ class Batch:
 
     def solve(self, U, opts=None, check=True):
         """U: torch CUDA float64 tensor of length self.total (in/out).  Returns a dict
-        of per-instance arrays (newton_its, krylov_its, fnorm, status) and 'solved'."""
+        of per-instance arrays (newton_its, krylov_its, fnorm, status, solve_us: device time
+        of each instance's solve) and 'solved'."""
         L = _batch_lib()
         o = opts if opts is not None else newton_defaults()
         nit = np.zeros(self.count, dtype=np.int32)
         kit = np.zeros(self.count, dtype=np.int32)
         fn = np.zeros(self.count)
         st = np.zeros(self.count, dtype=np.int32)
-        r = IgaBatchReport(0, nit.ctypes.data, kit.ctypes.data, fn.ctypes.data, st.ctypes.data)
+        us = np.zeros(self.count)
+        r = IgaBatchReport(0, nit.ctypes.data, kit.ctypes.data, fn.ctypes.data, st.ctypes.data, us.ctypes.data)
         rc = L.iga_batch_solve(self.h, ctypes.c_void_p(U.data_ptr()), ctypes.byref(o), ctypes.byref(r))
         if check and rc != IGA_OK:
             raise IgaError(rc, L.iga_batch_last_error(self.h).decode())
-        return {"solved": r.solved, "newton_its": nit, "krylov_its": kit, "fnorm": fn, "status": st, "rc": rc}
+        return {"solved": r.solved, "newton_its": nit, "krylov_its": kit, "fnorm": fn, "status": st, "solve_us": us,
+                "rc": rc}
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
