@@ -587,13 +587,15 @@ __device__ void b_solve(const BInst &I, double *__restrict__ U, const iga_newton
   __syncthreads();
 }
 
-constexpr int BTHREADS = 256;  // threads per CTA of the persistent kernel
 constexpr int BZCAP_MAX = 40960;  // floats of dynamic shared memory at most (160 KB)
 
-// MINB = 1: up to 255 registers, one resident CTA per SM; MINB = 2: 128 registers,
-// two or more resident CTAs per SM (more spills, more latency hiding).
-template <int MINB>
-__global__ void __launch_bounds__(BTHREADS, MINB) k_batch(const BInst *__restrict__ insts, const int *__restrict__ order, int count,
+// Launch shapes: NT threads per CTA, register budget for MINB resident CTAs per SM
+// (256 threads: 255 registers with MINB = 1, 128 with MINB = 2; 512: 128).  More
+// threads per instance give the memory-bound Krylov phases more loads in flight at the
+// price of register spills in the element kernels (at 1024 threads, 64 registers, the
+// spills cost more than the extra loads gain).
+template <int MINB, int NT>
+__global__ void __launch_bounds__(NT, MINB) k_batch(const BInst *__restrict__ insts, const int *__restrict__ order, int count,
                                                 const BArgs *__restrict__ args, int *__restrict__ counter, BRep *__restrict__ reps,
                                                 int zcap) {
   extern __shared__ float zs_dyn[];  // [zcap]: the operand vector of instances with N <= zcap
@@ -682,7 +684,7 @@ struct iga_batch_s {
   BArgs *d_args = nullptr, *h_args = nullptr;  // pinned host mirror
   BRep *d_reps = nullptr, *h_reps = nullptr;
   std::vector<int64_t> uoff;       // count + 1
-  int threads = 256, ctas_per_sm = 2, nsm = 0;
+  int threads = 512, ctas_per_sm = 1, nsm = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int graph_threads = 0, graph_ctas = 0;
@@ -814,7 +816,7 @@ static iga_status batch_create_impl(iga_batch_s *b, int count, const iga_desc *d
   qp_total = qpoff[count];
   // the operand vector of the operator products lives in shared memory (up to 160 KB)
   b->zcap = std::min(b->zcap, BZCAP_MAX);
-  for (auto kern : {k_batch<1>, k_batch<2>})
+  for (auto kern : {k_batch<1, 256>, k_batch<2, 256>, k_batch<1, 512>})
     BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(b->zcap * sizeof(float))));
   double *dar = nullptr;
   float *far = nullptr;
@@ -944,13 +946,14 @@ extern "C" iga_status iga_batch_offsets(iga_batch_t b, int64_t *offsets) {
   return IGA_OK;
 }
 
-extern "C" iga_status iga_batch_set_launch(iga_batch_t b, int ctas_per_sm) {
+extern "C" iga_status iga_batch_set_launch(iga_batch_t b, int ctas_per_sm, int threads_per_cta) {
   if (!b) return IGA_EINVAL;
-  if (ctas_per_sm < 1 || ctas_per_sm > 8) {
-    b->err = "ctas_per_sm must be in [1, 8]";
+  if ((threads_per_cta != 256 && threads_per_cta != 512) || ctas_per_sm < 1 || ctas_per_sm * threads_per_cta > 2048) {
+    b->err = "threads_per_cta must be 256 or 512 and ctas_per_sm * threads_per_cta at most 2048";
     return IGA_EINVAL;
   }
   b->ctas_per_sm = ctas_per_sm;
+  b->threads = threads_per_cta;
   return IGA_OK;
 }
 
@@ -959,10 +962,9 @@ static cudaError_t batch_enqueue(iga_batch_s *b) {
   cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream);
   int grid = b->nsm * b->ctas_per_sm;
   const size_t zb = (size_t)b->zcap * sizeof(float);
-  if (b->ctas_per_sm == 1)
-    k_batch<1><<<grid, b->threads, zb, b->stream>>>(b->d_insts, b->d_order, b->count, b->d_args, b->d_counter, b->d_reps, b->zcap);
-  else
-    k_batch<2><<<grid, b->threads, zb, b->stream>>>(b->d_insts, b->d_order, b->count, b->d_args, b->d_counter, b->d_reps, b->zcap);
+  auto kern = k_batch<1, 512>;
+  if (b->threads == 256) kern = b->ctas_per_sm == 1 ? k_batch<1, 256> : k_batch<2, 256>;
+  kern<<<grid, b->threads, zb, b->stream>>>(b->d_insts, b->d_order, b->count, b->d_args, b->d_counter, b->d_reps, b->zcap);
   cudaMemcpyAsync(b->h_reps, b->d_reps, b->count * sizeof(BRep), cudaMemcpyDeviceToHost, b->stream);
   return cudaGetLastError();
 }
@@ -981,7 +983,6 @@ extern "C" iga_status iga_batch_solve(iga_batch_t b, double *U, const iga_newton
   b->h_args->opts = o;
   // the caller's pending work (any stream) completes before the solve reads U
   BCK(cudaDeviceSynchronize());
-  b->threads = BTHREADS;
   if (!b->exec || b->graph_threads != b->threads || b->graph_ctas != b->ctas_per_sm) {
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }

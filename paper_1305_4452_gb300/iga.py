@@ -353,7 +353,7 @@ def _batch_lib():
         vp = ctypes.c_void_p
         L.iga_batch_create.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.POINTER(vp)]
         L.iga_batch_offsets.argtypes = [vp, vp]
-        L.iga_batch_set_launch.argtypes = [vp, ctypes.c_int]
+        L.iga_batch_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int]
         L.iga_batch_solve.argtypes = [vp, vp, ctypes.POINTER(IgaNewtonOpts), ctypes.POINTER(IgaBatchReport)]
         L.iga_batch_destroy.argtypes = [vp]
         L.iga_batch_destroy.restype = None
@@ -407,9 +407,11 @@ class Batch:
         self.offsets = off
         self.total = int(off[-1])
 
-    def set_launch(self, ctas_per_sm):
+    def set_launch(self, ctas_per_sm, threads=512):
+        """Launch shape of the persistent kernel: CTAs per SM and threads per CTA
+        (256 or 512)."""
         L = _batch_lib()
-        rc = L.iga_batch_set_launch(self.h, int(ctas_per_sm))
+        rc = L.iga_batch_set_launch(self.h, int(ctas_per_sm), int(threads))
         if rc != IGA_OK:
             raise IgaError(rc, L.iga_batch_last_error(self.h).decode())
 

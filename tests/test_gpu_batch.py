@@ -39,11 +39,11 @@ def oracle_problem(ins):
     return O.Problem([U, U], [ins["p"]] * 2, lam=ins["lam"], log_kappa=ins.get("log_kappa"), dirichlet=BC)
 
 
-@pytest.mark.parametrize("ctas", [1, 2])
-def test_batch_solves_every_instance_to_tolerance(I, ctas):
+@pytest.mark.parametrize("ctas,threads", [(1, 256), (2, 256), (1, 512), (4, 512)])
+def test_batch_solves_every_instance_to_tolerance(I, ctas, threads):
     ins = instances(24, seed=3, kappa_every=4)
     b = I.Batch(ins)
-    b.set_launch(ctas)
+    b.set_launch(ctas, threads)
     U = torch.zeros(b.total, dtype=torch.float64, device="cuda")
     rep = b.solve(U)
     assert rep["solved"] == len(ins)
@@ -116,4 +116,13 @@ def test_batch_cg_matches_gmres(I):
     rep = b.solve(Uc, o)
     assert rep["solved"] == len(ins)
     assert torch.abs(Ug - Uc).max().item() <= 1e-7
+    b.close()
+
+
+def test_batch_rejects_invalid_launch_shapes(I):
+    b = I.Batch(instances(2, seed=7))
+    for ctas, threads in ((1, 300), (0, 256), (1, 1024), (5, 512), (9, 256)):
+        with pytest.raises(I.IgaError):
+            b.set_launch(ctas, threads)
+    b.set_launch(4, 512)
     b.close()
