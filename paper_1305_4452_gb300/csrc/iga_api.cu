@@ -32,7 +32,7 @@ static cudaError_t upload(T **dst, const std::vector<T> &src) {
 
 static void free_dir(DirDev &d) {
   void *ps[] = {d.first, d.tab, d.wq, d.l, d.r, d.pair_off, d.pair_i, d.pair_j, d.pair_x0,
-                d.pair_np, d.pair_po, d.pair_T, d.pair_c, d.pair_val, d.pair_val_f, d.node_e0, d.node_ne};
+                d.pair_np, d.pair_po, d.pair_T, d.pair_c, d.pair_cs, d.pair_val, d.pair_val_f, d.node_e0, d.node_ne};
   for (void *p : ps)
     if (p) cudaFree(p);
   memset(&d, 0, sizeof d);
@@ -74,6 +74,7 @@ static iga_status upload_dir(iga_s *h, int ax) {
   CK(upload(&d.pair_po, D.pair_po));
   CK(upload(&d.pair_T, D.pair_T));
   CK(upload(&d.pair_c, D.pair_c));
+  CK(upload(&d.pair_cs, D.pair_cs));
   d.nc = (int)D.pair_c.size();
   CK(upload(&d.pair_val, D.pair_val));
   std::vector<float> pf(D.pair_val.begin(), D.pair_val.end());

@@ -22,7 +22,7 @@ DirArgs dir_args(const DirDev &d) {
   a.first = d.first; a.tab = d.tab; a.wq = d.wq; a.l = d.l; a.r = d.r;
   a.pair_off = d.pair_off; a.pair_i = d.pair_i; a.pair_j = d.pair_j;
   a.pair_x0 = d.pair_x0; a.pair_np = d.pair_np; a.pair_po = d.pair_po; a.pair_T = d.pair_T;
-  a.nc = d.nc; a.pair_c = d.pair_c;
+  a.nc = d.nc; a.pair_c = d.pair_c; a.pair_cs = d.pair_cs;
   a.pair_val = d.pair_val; a.pair_val_f = d.pair_val_f;
   a.node_e0 = d.node_e0; a.node_ne = d.node_ne;
   return a;

@@ -291,9 +291,14 @@ static iga_status build_dir(iga_s *h, const iga_desc *d, int ax, Dir &D) {
     }
     D.pair_T[k] = D.pair_off[j] + (i - D.l[j]);
   }
+  // canonical pairs in pair order, and ordered by overlap length (longest first) so
+  // that the threads of a warp in the pair loops of the Jacobian run the same number
+  // of Gauss points
   D.pair_c.clear();
   for (size_t k = 0; k < D.pair_j.size(); k++)
     if ((int)k <= D.pair_T[k]) D.pair_c.push_back((int)k);
+  D.pair_cs = D.pair_c;
+  std::stable_sort(D.pair_cs.begin(), D.pair_cs.end(), [&](int a, int b) { return D.pair_np[a] > D.pair_np[b]; });
   return IGA_OK;
 }
 

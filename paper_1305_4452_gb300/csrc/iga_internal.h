@@ -62,6 +62,7 @@ struct Dir {
   std::vector<double> pair_val;// [sum np][5]: B_i B_j, B'_i B_j, B_i B'_j, B'_i B'_j, B'_i B_j + B_i B'_j
   std::vector<int> pair_T;     // [P] index of the transposed pair (j, i)
   std::vector<int> pair_c;     // canonical pairs (pair index <= that of its transpose), ascending
+  std::vector<int> pair_cs;    // the same, longest overlap first
   std::vector<int> node_e0;    // [n] first element containing the function
   std::vector<int> node_ne;    // [n] number of elements containing it
   int npairs() const { return (int)pair_j.size(); }
@@ -76,7 +77,7 @@ struct DirDev {
   double *wq;
   int *l, *r;
   int *pair_off, *pair_i, *pair_j, *pair_x0, *pair_np, *pair_po, *pair_T;
-  int nc, *pair_c;
+  int nc, *pair_c, *pair_cs;
   double *pair_val;
   float *pair_val_f;  // FP32 copy for the mixed-precision stages
   int *node_e0, *node_ne;
@@ -90,7 +91,7 @@ struct DirArgs {  // passed by value to kernels
   const int *l, *r;
   const int *pair_off, *pair_i, *pair_j, *pair_x0, *pair_np, *pair_po, *pair_T;
   int nc;
-  const int *pair_c;
+  const int *pair_c, *pair_cs;
   const double *pair_val;
   const float *pair_val_f;
   const int *node_e0, *node_ne;

@@ -64,6 +64,9 @@ template <typename T, int DIM, int P, int PLAN>
 __global__ void __launch_bounds__(256) k_stage1(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ geom,
                                                 const double *__restrict__ Q00, GeomLayout gl, T *__restrict__ out) {
   const T *tab = ptab<T>(d0);
+  // FP64: DFMA-bound, so warps get pairs of equal overlap length; FP32: bound by memory
+  // traffic, so pairs stay in pair order (neighbouring stores)
+  const int *clist = sizeof(T) == 8 ? d0.pair_cs : d0.pair_c;
   if (PLAN == PLAN_MASS) {
     // lines x1 = blockIdx.x * LINES + l; each line's Q00 in shared memory
     constexpr int Q = P + 1, NQ = ipow<DIM>(Q), LINES = STAGE1_MASS_LINES;
@@ -81,7 +84,7 @@ __global__ void __launch_bounds__(256) k_stage1(DirArgs d0, DirArgs d1, DirArgs 
     __syncthreads();
     // one canonical pair per thread, all lines at once: each table value serves LINES FMAs
     for (int c = threadIdx.x; c < d0.nc; c += blockDim.x) {
-      const int pi = d0.pair_c[c], piT = d0.pair_T[pi];
+      const int pi = clist[c], piT = d0.pair_T[pi];
       const int xs = d0.pair_x0[pi], np = d0.pair_np[pi];
       const T *pv = tab + (size_t)d0.pair_po[pi] * IGA_PVS;
       T acc[LINES];
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(256) k_stage1(DirArgs d0, DirArgs d1, DirArgs 
   const size_t plane = (size_t)d0.np * d1.X * (DIM == 3 ? d2.X : 1);
   T *const ol = out + ((size_t)x2 * d1.X + x1) * d0.np;
   for (int c = threadIdx.x; c < d0.nc; c += blockDim.x) {
-    const int pi = d0.pair_c[c], piT = d0.pair_T[pi];
+    const int pi = clist[c], piT = d0.pair_T[pi];
     const int xs = d0.pair_x0[pi], np = d0.pair_np[pi];
     const T *pv = tab + (size_t)d0.pair_po[pi] * IGA_PVS;
     const T *L = line + xs;
@@ -195,7 +198,7 @@ __global__ void __launch_bounds__(256) k_stage1(DirArgs d0, DirArgs d1, DirArgs 
 // for pi1 <= pi1T; the final stage reads them at (pi1T, pi0T) otherwise.
 // PLAN_DIAG: H0 = P^00 G0 + P^11 G2, H2 = P^00 G5 (G1, G3, G4 and so H1 vanish).
 template <typename T, int PLAN>
-__global__ void __launch_bounds__(128) k_stage2(DirArgs d0, DirArgs d1, DirArgs d2, const T *__restrict__ in,
+__global__ void __launch_bounds__(128, 6) k_stage2(DirArgs d0, DirArgs d1, DirArgs d2, const T *__restrict__ in,
                                                 T *__restrict__ out, int chunk) {
   const int pi0 = blockIdx.x * blockDim.x + threadIdx.x;
   const int x2 = blockIdx.z;
@@ -211,27 +214,30 @@ __global__ void __launch_bounds__(128) k_stage2(DirArgs d0, DirArgs d1, DirArgs 
     const int xs = d1.pair_x0[pi1], np = d1.pair_np[pi1];
     const T *pv = tab + (size_t)d1.pair_po[pi1] * IGA_PVS;
     T h0 = 0, h1 = 0, h2 = 0;
-    for (int k = 0; k < np; k++) {
-      const size_t row = ((size_t)x2 * d1.X + xs + k) * d0.np;
+    // g: this thread's entry at Gauss point xs + k of axis 1 (gT: the transposed axis-0 pair)
+    const T *g = in + ((size_t)x2 * d1.X + xs) * d0.np + pi0;
+    const T *gT = g - pi0 + pi0T;
+#pragma unroll(sizeof(T) == 4 ? 4 : 1)
+    for (int k = 0; k < np; k++, g += d0.np, gT += d0.np) {
       const T p00 = pv[IGA_PVS * k + 0];
       if (PLAN == PLAN_MASS) {
-        h0 = fma(p00, in[row + pi0], h0);
+        h0 = fma(p00, g[0], h0);
       } else if (PLAN == PLAN_DIAG) {
-        h0 = fma(p00, in[row + pi0], h0);
-        h0 = fma(pv[IGA_PVS * k + 3], in[2 * inplane + row + pi0], h0);
-        h2 = fma(p00, in[5 * inplane + row + pi0], h2);
+        h0 = fma(p00, g[0], h0);
+        h0 = fma(pv[IGA_PVS * k + 3], g[2 * inplane], h0);
+        h2 = fma(p00, g[5 * inplane], h2);
       } else {
         const T p01 = pv[IGA_PVS * k + 2];
         if (sym) {
           const T p10 = pv[IGA_PVS * k + 1], p11 = pv[IGA_PVS * k + 3];
-          h0 = fma(p00, in[row + pi0], h0);
-          h0 = fma(p10, in[inplane + row + pi0], h0);
-          h0 = fma(p01, in[inplane + row + pi0T], h0);
-          h0 = fma(p11, in[2 * inplane + row + pi0], h0);
-          h2 = fma(p00, in[5 * inplane + row + pi0], h2);
+          h0 = fma(p00, g[0], h0);
+          h0 = fma(p10, g[inplane], h0);
+          h0 = fma(p01, gT[inplane], h0);
+          h0 = fma(p11, g[2 * inplane], h0);
+          h2 = fma(p00, g[5 * inplane], h2);
         }
-        h1 = fma(p00, in[3 * inplane + row + pi0], h1);
-        h1 = fma(p01, in[4 * inplane + row + pi0T], h1);
+        h1 = fma(p00, g[3 * inplane], h1);
+        h1 = fma(p01, gT[4 * inplane], h1);
       }
     }
     T *o = out + ((size_t)x2 * d1.np + pi1) * d0.np + pi0;
