@@ -468,9 +468,9 @@ def periodic64(torch, iga, W, clock, nel=64, p=3):
         solves[label] = {"ms": best * 1e3, "newton_its": rep.newton_its, "krylov_its": rep.krylov_its, "fnorm": rep.fnorm}
     ck = clock.stop()
     d.close()
-    tr, tj, nr, sec = _oracle_assembly_block(W, 3, p, 8, periodic=per)
+    otr, otj, nr, sec = _oracle_assembly_block(W, 3, p, 8, periodic=per)
     its = solves["fp64_gmres"]["newton_its"]
-    cb = _baseline(1.0 / ((its * (tr + tj) + tr) * nel ** 3), "solves/s", "oracle residual+Jacobian of an 8^3-element block "
+    cb = _baseline(1.0 / ((its * (otr + otj) + otr) * nel ** 3), "solves/s", "oracle residual+Jacobian of an 8^3-element block "
                    "periodic in x and y, per element x 64^3, times %d Newton steps; linear solves not counted" % its, nr, sec)
     return _line(1e3 / solves["fp64_gmres"]["ms"], "solves/s", "bratu3d_cube64_p3_periodic_xy_C2_lambda2_fp64", {
         "cpu_baseline": cb,
