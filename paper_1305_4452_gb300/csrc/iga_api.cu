@@ -42,7 +42,7 @@ void iga_release(iga_s *h) {
   periodic_release(h);
   elem_gemm_release(h);
   for (int ax = 0; ax < 3; ax++) free_dir(h->ddev[ax]);
-  void *ps[] = {h->rowptr, h->colidx, h->weights, h->geom, h->Fe, h->Q00, h->T1, h->T2, h->Kstiff, h->Kstiff_f, h->Ebuf64, h->ts_buf,
+  void *ps[] = {h->rowptr, h->rp_line, h->rp_p0, h->colidx, h->weights, h->geom, h->Fe, h->Q00, h->T1, h->T2, h->Kstiff, h->Kstiff_f, h->Ebuf64, h->ts_buf,
                 h->Mred, h->Mred_f, h->J64, h->J32, h->wk, h->V, h->red, h->ctl, h->Uhost_dev,
                 h->geom32, h->tab32[0], h->tab32[1], h->tab32[2], h->Ebuf, h->z32};
   for (void *p : ps)
@@ -124,6 +124,19 @@ iga_status iga_create_impl(iga_s *h, const iga_desc *d, const iga_bratu *b) {
   iga_rowptr(h, rowptr);
   h->nnz = rowptr[N];
   CK(upload(&h->rowptr, rowptr));
+  {
+    const Dir &D0 = h->dir[0];
+    std::vector<int64_t> line((size_t)(N / D0.n));
+    for (size_t L = 0; L < line.size(); L++) line[L] = rowptr[L * D0.n];
+    std::vector<int> p0(D0.n);
+    int acc = 0;
+    for (int i = 0; i < D0.n; i++) {
+      p0[i] = acc;
+      acc += D0.r[i] - D0.l[i] + 1;
+    }
+    CK(upload(&h->rp_line, line));
+    CK(upload(&h->rp_p0, p0));
+  }
   CK(cudaMalloc((void **)&h->colidx, (size_t)h->nnz * sizeof(int32_t)));
   CK(launch_colidx(h));
   // weights, geometry factors

@@ -171,6 +171,10 @@ struct iga_s {
 
   // device buffers owned by the library
   int64_t *rowptr = nullptr;
+  // rowptr of a tensor-product pattern: row (i0, line) starts at
+  // rp_line[line] + (stencil width of the line) * rp_p0[i0], line = i1 + n1 i2 (2D: i1)
+  int64_t *rp_line = nullptr;
+  int *rp_p0 = nullptr;
   int32_t *colidx = nullptr;
   double *weights = nullptr;   // [N] or null
   double *geom = nullptr;      // [nelem][nf][nq]

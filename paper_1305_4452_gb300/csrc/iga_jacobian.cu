@@ -28,7 +28,9 @@ enum { PLAN_STIFF = 0, PLAN_MASS = 1, PLAN_DIAG = 2 };
 
 struct CsrArgs {
   const int64_t *rowptr;
-  const double *wts;  // rational weights (J_AB carries w_A w_B) or null
+  const int64_t *rp_line;  // first CSR position of each line (i1, i2) of rows
+  const int *rp_p0;        // prefix sums of the axis-0 stencil widths
+  const double *wts;       // rational weights (J_AB carries w_A w_B) or null
   BndArgs bnd;
 };
 
@@ -287,6 +289,9 @@ __global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d
   }
   const T *tab = ptab<T>(dl);
   const bool mid_sym = pmid <= pmidT;  // 3D: where stage 2 stored H0 and H2
+  // CSR row starts: line start (the same for the whole block at a given pl) plus the
+  // row's offset within its line
+  const int64_t rA0 = (int64_t)w1 * csr.rp_p0[i0], rB0 = (int64_t)w1T * csr.rp_p0[j0];
   for (int pl = pa; pl < pb; pl++) {
     const int plT = dl.pair_T[pl];
     if (pl > plT || (pl == plT && (pmid > pmidT || (pmid == pmidT && pi0 > pi0T)))) continue;
@@ -326,14 +331,16 @@ __global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d
       I[0] = i0; I[1] = i1; I[2] = il; J[0] = j0; J[1] = j1; J[2] = jl;
       A = i0 + (int64_t)d0.n * (i1 + (int64_t)d1.n * il);
       B = j0 + (int64_t)d0.n * (j1 + (int64_t)d1.n * jl);
-      pos = csr.rowptr[A] + ((int64_t)ol * w1 + o1) * w0 + o0;
-      posT = csr.rowptr[B] + ((int64_t)olT * w1T + o1T) * w0T + o0T;
+      const int wl = dl.r[il] - dl.l[il] + 1, wlT = dl.r[jl] - dl.l[jl] + 1;
+      pos = csr.rp_line[i1 + (int64_t)d1.n * il] + wl * rA0 + ((int64_t)ol * w1 + o1) * w0 + o0;
+      posT = csr.rp_line[j1 + (int64_t)d1.n * jl] + wlT * rB0 + ((int64_t)olT * w1T + o1T) * w0T + o0T;
     } else {
       I[0] = i0; I[1] = il; J[0] = j0; J[1] = jl;
       A = i0 + (int64_t)d0.n * il;
       B = j0 + (int64_t)d0.n * jl;
-      pos = csr.rowptr[A] + (int64_t)ol * w0 + o0;
-      posT = csr.rowptr[B] + (int64_t)olT * w0T + o0T;
+      const int wl = dl.r[il] - dl.l[il] + 1, wlT = dl.r[jl] - dl.l[jl] + 1;
+      pos = csr.rp_line[il] + wl * rA0 + (int64_t)ol * w0 + o0;
+      posT = csr.rp_line[jl] + wlT * rB0 + (int64_t)olT * w0T + o0T;
     }
     double v = (double)acc;
     if (csr.wts) v *= csr.wts[A] * csr.wts[B];
@@ -378,7 +385,7 @@ cudaError_t run_stages(iga_s *h, V *vals, const V *base, int fix) {
   T *T1 = (T *)h->T1, *T2 = (T *)h->T2;
   cudaError_t ce = run_stage1<T, DIM, PLAN>(h, T1);
   if (ce) return ce;
-  CsrArgs csr{h->rowptr, h->weights, h->bnd};
+  CsrArgs csr{h->rowptr, h->rp_line, h->rp_p0, h->weights, h->bnd};
   const int chunk = 8;
   if (DIM == 3) {
     dim3 g2((a0.np + 127) / 128, (a1.np + chunk - 1) / chunk, a2.X);
