@@ -800,13 +800,125 @@ __global__ void __launch_bounds__(128) k_q00_f32(DirArgs d0, DirArgs d1, DirArgs
   Q00[(size_t)e * S::NQ + qp] = (double)v;
 }
 
+// The same Q00 for elements of at most 27 Gauss points (2D, or 3D with p <= 2), in two
+// phases per block of 128 elements: one thread per element computes u~ at its Gauss
+// points (weighted coefficients and FP32 1D tables in registers, the nested sums of
+// interp_u_block -- axis 0 innermost, then axis 1, then axis 2, each in function order --
+// with the partial sums shared between points) into shared memory; then one thread per
+// (element, Gauss point) of the block's contiguous range reads the geometry factors and
+// writes Q00, both coalesced.  The same operations per point as k_q00_f32.
+template <int DIM, int P>
+__global__ void __launch_bounds__(128) k_q00_f32e(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ U,
+                                                  const double *__restrict__ wts, const double *__restrict__ geom, GeomLayout gl,
+                                                  float lambda, float cs, float cr, float shift, double *__restrict__ Q00,
+                                                  int64_t nelem) {
+  constexpr int N1 = P + 1, Q = P + 1, EB = 128;
+  constexpr int N2 = DIM == 3 ? N1 : 1, Q2 = DIM == 3 ? Q : 1;
+  constexpr int NQ = Q * Q * Q2;
+  __shared__ float ut_s[EB * NQ];
+  const int64_t e_first = (int64_t)blockIdx.x * EB, e = e_first + threadIdx.x;
+  if (e < nelem) {
+    const int e0 = (int)(e % d0.nel), e1 = (int)((e / d0.nel) % d1.nel), e2 = DIM == 3 ? (int)(e / ((int64_t)d0.nel * d1.nel)) : 0;
+    float ut[Q2][Q][Q];
+    if (cr != 0.f && U) {
+      float B0[Q][N1], B1[Q][N1], B2[Q2][N2];
+#pragma unroll
+      for (int g = 0; g < Q; g++)
+#pragma unroll
+        for (int a = 0; a < N1; a++) {
+          B0[g][a] = (float)d0.tab[(((size_t)e0 * Q + g) * N1 + a) * 2];
+          B1[g][a] = (float)d1.tab[(((size_t)e1 * Q + g) * N1 + a) * 2];
+          if (DIM == 3) B2[g < Q2 ? g : 0][a < N2 ? a : 0] = (float)d2.tab[(((size_t)e2 * Q + g) * N1 + a) * 2];
+        }
+      const int64_t f0 = d0.first[e0], f1 = d1.first[e1], f2 = DIM == 3 ? d2.first[e2] : 0;
+      float t1[N2][Q][Q];  // [a2][g1][g0]
+#pragma unroll
+      for (int a2 = 0; a2 < N2; a2++) {
+        float t0[N1][Q];  // [a1][g0]
+#pragma unroll
+        for (int a1 = 0; a1 < N1; a1++) {
+          float uw[N1];
+#pragma unroll
+          for (int a0 = 0; a0 < N1; a0++) {
+            const int64_t G = (f0 + a0) + (int64_t)d0.n * ((f1 + a1) + (int64_t)d1.n * (f2 + a2));
+            uw[a0] = (float)(U[G] * (wts ? wts[G] : 1.0));
+          }
+#pragma unroll
+          for (int g0 = 0; g0 < Q; g0++) {
+            float s0 = 0.f;
+#pragma unroll
+            for (int a0 = 0; a0 < N1; a0++) s0 = fmaf(B0[g0][a0], uw[a0], s0);
+            t0[a1][g0] = s0;
+          }
+        }
+#pragma unroll
+        for (int g1 = 0; g1 < Q; g1++)
+#pragma unroll
+          for (int g0 = 0; g0 < Q; g0++) {
+            float s1 = 0.f;
+#pragma unroll
+            for (int a1 = 0; a1 < N1; a1++) s1 = fmaf(B1[g1][a1], t0[a1][g0], s1);
+            t1[a2][g1][g0] = s1;
+          }
+      }
+#pragma unroll
+      for (int g2 = 0; g2 < Q2; g2++)
+#pragma unroll
+        for (int g1 = 0; g1 < Q; g1++)
+#pragma unroll
+          for (int g0 = 0; g0 < Q; g0++) {
+            float u = 0.f;
+            if (DIM == 3) {
+#pragma unroll
+              for (int a2 = 0; a2 < N2; a2++) u = fmaf(B2[g2][a2], t1[a2][g1][g0], u);
+            } else {
+              u = t1[0][g1][g0];
+            }
+            ut[g2][g1][g0] = u;
+          }
+    } else {
+#pragma unroll
+      for (int g2 = 0; g2 < Q2; g2++)
+#pragma unroll
+        for (int g1 = 0; g1 < Q; g1++)
+#pragma unroll
+          for (int g0 = 0; g0 < Q; g0++) ut[g2][g1][g0] = 0.f;
+    }
+#pragma unroll
+    for (int qp = 0; qp < NQ; qp++) ut_s[threadIdx.x * NQ + qp] = ut[qp / (Q * Q)][(qp / Q) % Q][qp % Q];
+  }
+  __syncthreads();
+  const int nb = (int)min((int64_t)EB, nelem - e_first);
+  for (int k = threadIdx.x; k < nb * NQ; k += EB) {
+    const int le = k / NQ, qp = k - le * NQ;
+    const double *rec = geom + (size_t)(e_first + le) * gl.nf * NQ + qp;
+    float v = cs != 0.f ? cs * (float)rec[gl.gSg * NQ] : 0.f;
+    if (cr != 0.f) {
+      const float jw2 = (float)rec[gl.jwW2 * NQ];
+      v -= cr * jw2 * lambda * __expf(ut_s[k] * (float)rec[gl.invW * NQ]);
+      if (shift != 0.f) v += cr * shift * jw2;
+    }
+    Q00[(size_t)e_first * NQ + k] = (double)v;
+  }
+}
+
 cudaError_t launch_q00_f32(iga_s *h, const double *U, double cs, double cr) {
   DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
+  const float ts = h->ts_on ? (float)h->ts_a : 0.f;
+  if (h->dim == 2 || h->p <= 2) {
+    const unsigned grid = (unsigned)((h->nelem + 127) / 128);
+    IGA_LAUNCH(h, KC_Q00, DISPATCH_DP(h->dim, h->p, ({
+      constexpr int PE = (D == 2 || PP <= 2) ? PP : 2;  // 3D p > 2 does not reach this branch
+      k_q00_f32e<D, PE><<<grid, 128, 0, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, (float)h->lambda, (float)cs,
+                                                      (float)cr, ts, h->Q00, h->nelem);
+    })));
+    return cudaGetLastError();
+  }
   IGA_LAUNCH(h, KC_Q00, DISPATCH_DP(h->dim, h->p, ({
     using S = InterpF32<D, PP>;
     const unsigned grid = (unsigned)((h->nelem + S::EB - 1) / S::EB);
     k_q00_f32<D, PP><<<grid, S::THREADS, 0, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, (float)h->lambda, (float)cs,
-                                                         (float)cr, h->ts_on ? (float)h->ts_a : 0.f, h->Q00, h->nelem);
+                                                         (float)cr, ts, h->Q00, h->nelem);
   })));
   return cudaGetLastError();
 }
