@@ -375,6 +375,50 @@ __global__ void __launch_bounds__(128) k_qv(DirArgs d0, DirArgs d1, DirArgs d2, 
   }
 }
 
+// The same Qv for elements of at most 27 Gauss points (2D, or 3D with p <= 2), in two
+// phases per block of 128 elements: one thread per element forms u~ at its points
+// (interp_u_elem, the same operations per point as interp_u_block) into shared memory,
+// then one thread per (element, point) of the block's contiguous range reads the FP32
+// geometry factors (coalesced) and writes the element's Qv row entries.
+template <int DIM, int P, int OP>
+__global__ void __launch_bounds__(128) k_qv_e(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ U,
+                                              const double *__restrict__ wts, const float *__restrict__ g32,
+                                              float lambda, const int *__restrict__ slot_of_elem, void *__restrict__ Qv, int Kp,
+                                              int general, int64_t nelem) {
+  constexpr int Q = P + 1, EB = 128, nq = DIM == 3 ? Q * Q * Q : Q * Q;
+  __shared__ float ut_s[EB * nq];
+  const int64_t e_first = (int64_t)blockIdx.x * EB, e = e_first + threadIdx.x;
+  if (e < nelem) interp_u_elem<DIM, P>(d0, d1, d2, U, wts, e, ut_s + threadIdx.x * nq);
+  __syncthreads();
+  using GL = G32<DIM>;
+  const Slots S = make_slots(DIM, general != 0);
+  const int nb = (int)min((int64_t)EB, nelem - e_first);
+  for (int k = threadIdx.x; k < nb * nq; k += EB) {
+    const int le = k / nq, qp = k - le * nq;
+    const int64_t ee = e_first + le;
+    const float *rec = g32 + (size_t)ee * GL::NF * nq + qp;
+    const float q00 = rec[GL::GSG * nq] - rec[GL::JWW2 * nq] * lambda * __expf(ut_s[k] * rec[GL::INVW * nq]);
+    const size_t row = (size_t)slot_of_elem[ee] * Kp;
+#pragma unroll
+    for (int s = 0; s < (DIM == 3 ? 10 : 6); s++) {
+      if (s >= S.n) break;
+      const int mu = S.mu[s], nu = S.nu[s];
+      float v;
+      if (mu == 0 && nu == 0) v = q00;
+      else if (mu == 0) v = rec[(GL::NSG + nu - 1) * nq];
+      else {
+        // S slots: 2D 00, 11, 01; 3D 00, 11, 22, 01, 02, 12
+        const int i = mu - 1, j = nu - 1;
+        const int si = (i == j) ? i : (DIM == 2 ? 2 : (i == 0 ? (j == 1 ? 3 : 4) : 5));
+        v = rec[(GL::S + si) * nq];
+      }
+      const uint32_t bits = op_bits(v, OP);
+      if (OP == EG_BF16) reinterpret_cast<uint16_t *>(Qv)[row + (size_t)s * nq + qp] = (uint16_t)bits;
+      else reinterpret_cast<uint32_t *>(Qv)[row + (size_t)s * nq + qp] = bits;
+    }
+  }
+}
+
 template <int DIM> __host__ __device__ constexpr int ipow3(int b) { return DIM == 2 ? b * b : b * b * b; }
 
 // One thread per CSR row A (consecutive rows across a warp).  For every element e
@@ -682,7 +726,16 @@ cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, in
   IGA_LAUNCH(h, KC_Q00, EG_DISPATCH(h->dim, h->p, ({
     using IS = InterpF32<D, PP>;
     const unsigned gq = (unsigned)((h->nelem + IS::EB - 1) / IS::EB);
-    if (op == EG_BF16)
+    constexpr int PE = (D == 2 || PP <= 2) ? PP : 2;  // small elements: one thread per element
+    const unsigned ge = (unsigned)((h->nelem + 127) / 128);
+    if (D == 2 || PP <= 2) {
+      if (op == EG_BF16)
+        k_qv_e<D, PE, EG_BF16><<<ge, 128, 0, h->stream>>>(a0, a1, a2, U, h->weights, h->geom32, (float)h->lambda,
+                                                          P->slot_of_elem, Qv, P->Kp, P->general, h->nelem);
+      else
+        k_qv_e<D, PE, EG_TF32><<<ge, 128, 0, h->stream>>>(a0, a1, a2, U, h->weights, h->geom32, (float)h->lambda,
+                                                          P->slot_of_elem, Qv, P->Kp, P->general, h->nelem);
+    } else if (op == EG_BF16)
       k_qv<D, PP, EG_BF16><<<gq, IS::THREADS, 0, h->stream>>>(a0, a1, a2, U, h->weights, h->geom32, (float)h->lambda,
                                                               P->slot_of_elem, Qv, P->Kp, P->general, h->nelem);
     else

@@ -812,81 +812,10 @@ __global__ void __launch_bounds__(128) k_q00_f32e(DirArgs d0, DirArgs d1, DirArg
                                                   const double *__restrict__ wts, const double *__restrict__ geom, GeomLayout gl,
                                                   float lambda, float cs, float cr, float shift, double *__restrict__ Q00,
                                                   int64_t nelem) {
-  constexpr int N1 = P + 1, Q = P + 1, EB = 128;
-  constexpr int N2 = DIM == 3 ? N1 : 1, Q2 = DIM == 3 ? Q : 1;
-  constexpr int NQ = Q * Q * Q2;
+  constexpr int Q = P + 1, EB = 128, NQ = DIM == 3 ? Q * Q * Q : Q * Q;
   __shared__ float ut_s[EB * NQ];
   const int64_t e_first = (int64_t)blockIdx.x * EB, e = e_first + threadIdx.x;
-  if (e < nelem) {
-    const int e0 = (int)(e % d0.nel), e1 = (int)((e / d0.nel) % d1.nel), e2 = DIM == 3 ? (int)(e / ((int64_t)d0.nel * d1.nel)) : 0;
-    float ut[Q2][Q][Q];
-    if (cr != 0.f && U) {
-      float B0[Q][N1], B1[Q][N1], B2[Q2][N2];
-#pragma unroll
-      for (int g = 0; g < Q; g++)
-#pragma unroll
-        for (int a = 0; a < N1; a++) {
-          B0[g][a] = (float)d0.tab[(((size_t)e0 * Q + g) * N1 + a) * 2];
-          B1[g][a] = (float)d1.tab[(((size_t)e1 * Q + g) * N1 + a) * 2];
-          if (DIM == 3) B2[g < Q2 ? g : 0][a < N2 ? a : 0] = (float)d2.tab[(((size_t)e2 * Q + g) * N1 + a) * 2];
-        }
-      const int64_t f0 = d0.first[e0], f1 = d1.first[e1], f2 = DIM == 3 ? d2.first[e2] : 0;
-      float t1[N2][Q][Q];  // [a2][g1][g0]
-#pragma unroll
-      for (int a2 = 0; a2 < N2; a2++) {
-        float t0[N1][Q];  // [a1][g0]
-#pragma unroll
-        for (int a1 = 0; a1 < N1; a1++) {
-          float uw[N1];
-#pragma unroll
-          for (int a0 = 0; a0 < N1; a0++) {
-            const int64_t G = (f0 + a0) + (int64_t)d0.n * ((f1 + a1) + (int64_t)d1.n * (f2 + a2));
-            uw[a0] = (float)(U[G] * (wts ? wts[G] : 1.0));
-          }
-#pragma unroll
-          for (int g0 = 0; g0 < Q; g0++) {
-            float s0 = 0.f;
-#pragma unroll
-            for (int a0 = 0; a0 < N1; a0++) s0 = fmaf(B0[g0][a0], uw[a0], s0);
-            t0[a1][g0] = s0;
-          }
-        }
-#pragma unroll
-        for (int g1 = 0; g1 < Q; g1++)
-#pragma unroll
-          for (int g0 = 0; g0 < Q; g0++) {
-            float s1 = 0.f;
-#pragma unroll
-            for (int a1 = 0; a1 < N1; a1++) s1 = fmaf(B1[g1][a1], t0[a1][g0], s1);
-            t1[a2][g1][g0] = s1;
-          }
-      }
-#pragma unroll
-      for (int g2 = 0; g2 < Q2; g2++)
-#pragma unroll
-        for (int g1 = 0; g1 < Q; g1++)
-#pragma unroll
-          for (int g0 = 0; g0 < Q; g0++) {
-            float u = 0.f;
-            if (DIM == 3) {
-#pragma unroll
-              for (int a2 = 0; a2 < N2; a2++) u = fmaf(B2[g2][a2], t1[a2][g1][g0], u);
-            } else {
-              u = t1[0][g1][g0];
-            }
-            ut[g2][g1][g0] = u;
-          }
-    } else {
-#pragma unroll
-      for (int g2 = 0; g2 < Q2; g2++)
-#pragma unroll
-        for (int g1 = 0; g1 < Q; g1++)
-#pragma unroll
-          for (int g0 = 0; g0 < Q; g0++) ut[g2][g1][g0] = 0.f;
-    }
-#pragma unroll
-    for (int qp = 0; qp < NQ; qp++) ut_s[threadIdx.x * NQ + qp] = ut[qp / (Q * Q)][(qp / Q) % Q][qp % Q];
-  }
+  if (e < nelem) interp_u_elem<DIM, P>(d0, d1, d2, cr != 0.f ? U : nullptr, wts, e, ut_s + threadIdx.x * NQ);
   __syncthreads();
   const int nb = (int)min((int64_t)EB, nelem - e_first);
   for (int k = threadIdx.x; k < nb * NQ; k += EB) {
