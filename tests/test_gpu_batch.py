@@ -48,6 +48,7 @@ def test_batch_solves_every_instance_to_tolerance(I, ctas, threads):
     rep = b.solve(U)
     assert rep["solved"] == len(ins)
     assert np.all(rep["fnorm"] <= 1e-10)
+    assert np.all(rep["solve_us"] > 0) and np.all(np.isfinite(rep["solve_us"]))
     Uh = U.cpu().numpy()
     for i, x in enumerate(ins):
         Ui = Uh[b.offsets[i]:b.offsets[i + 1]]

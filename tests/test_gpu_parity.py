@@ -702,3 +702,33 @@ def test_periodic_exact_full_annulus_matches_the_oracle(p, nel_r, nel_q):
     assert rep.status == 0
     assert np.linalg.norm(prob.residual(Us.cpu().numpy())) <= 1e-10 * (1 + 1e-12)
     disc.close()
+
+
+@pytest.mark.parametrize("dim,p,nel,k", [(2, 2, (7, 6), None), (2, 3, (6, 5), 1), (3, 2, (5, 4, 3), None), (3, 3, (4, 3, 3), None)])
+def test_identity_map_plan_matches_the_general_plan(dim, p, nel, k):
+    """Without control points the Jacobian stages use the plan of an identity map with unit
+    weights (geometry factors g = 0, S diagonal); the same cube given its Greville points
+    as control points (x = xi by linear precision) takes the general plan.  Both equal the
+    oracle, and each other to rounding."""
+    I = iga()
+    knots = [W.uniform_open_knots(nel[d], p, k) for d in range(dim)]
+    n = [len(kk) - p - 1 for kk in knots]
+    g = [W.greville(knots[d], p) for d in range(dim)]
+    mesh = np.meshgrid(*g[::-1], indexing="ij")  # axis 0 fastest in the flattened order
+    ctrl = np.stack([m.reshape(-1) for m in mesh[::-1]], axis=1).copy()
+    bc = bc_all(dim)
+    plain = I.Discretization(dim, p, knots=knots, lam=1.3, dirichlet=bc)
+    mapped = I.Discretization(dim, p, knots=knots, ctrl=ctrl, lam=1.3, dirichlet=bc)
+    prob = O.Problem(knots, [p] * dim, lam=1.3, dirichlet=bc)
+    U0 = W.interior_field(n, 11)
+    U = torch.tensor(U0, device="cuda")
+    Jp = plain.form_jacobian(U).cpu().numpy()
+    Jm = mapped.form_jacobian(U).cpu().numpy()
+    Jo = prob.jacobian(U0)
+    assert rel(Jp, Jo) <= TOL and rel(Jm, Jo) <= TOL
+    assert rel(Jp, Jm) <= 1e-13
+    Jp32 = plain.form_jacobian(U, prec=I.IGA_JAC_FP32).cpu().numpy().astype(np.float64)
+    Jm32 = mapped.form_jacobian(U, prec=I.IGA_JAC_FP32).cpu().numpy().astype(np.float64)
+    assert rel(Jp32, Jo) <= 1e-5 and rel(Jm32, Jo) <= 1e-5
+    plain.close()
+    mapped.close()
