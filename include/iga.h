@@ -294,11 +294,12 @@ iga_status iga_batch_create(int count, const iga_desc *descs, const iga_bratu *p
  * concatenated solution array (natural order within an instance). */
 iga_status iga_batch_offsets(iga_batch_t batch, int64_t *offsets);
 /* Launch shape of the persistent kernel: CTAs per SM and threads per CTA (256 or 512;
- * ctas_per_sm * threads_per_cta <= 2048).  Default 1 x 512.  IGA_EINVAL otherwise.  The autotuner in paper_1305_4452_gb300/autotune.py chooses it. */
+ * ctas_per_sm * threads_per_cta <= 2048).  Default 1 x 512.  IGA_EINVAL otherwise.
+ * The autotuner in paper_1305_4452_gb300/autotune.py chooses it. */
 iga_status iga_batch_set_launch(iga_batch_t batch, int ctas_per_sm, int threads_per_cta);
 /* Solve every instance from the initial values in U (device, concatenated,
- * in/out) with Newton + GMRES(m, at most 64) + Jacobi, FP64 residual and norms,
- * FP32 sum-factorised Jacobian.  One graph launch (captured on the first call
+ * in/out) with Newton + GMRES(m, at most 64) + Jacobi (Jacobi CG with
+ * opts->ksp = IGA_KSP_CG), FP64 residual and norms, FP32 sum-factorised Jacobian.  One graph launch (captured on the first call
  * and replayed): argument copy, work-counter reset, the persistent kernel (each
  * CTA takes the next instance, largest first, until none is left) and the
  * report copy.  Synchronises the device.  Returns IGA_OK when every instance

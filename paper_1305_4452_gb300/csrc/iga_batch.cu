@@ -10,10 +10,11 @@
 //   residual  (FP64; Algorithm 3 with Eq. residual): one element per thread with
 //             sum factorisation, then a fixed-order gather per control variable;
 //   Jacobian  (FP32; Eq. jacobian): global sum factorisation over the instance's
-//             mesh, axis 0 then axis 1, each CSR entry written once;
+//             mesh, axis 0 then axis 1, each entry written once, into a layout
+//             sliced by 32 rows for the operator products (see jslot);
 //   GMRES(m)  with right Jacobi preconditioning; FP64 Krylov vectors and
 //             classical Gram-Schmidt applied twice (one warp per dot product,
-//             fixed-order warp reductions), FP32 operator products;
+//             fixed-order warp reductions), FP32 operator products; or Jacobi CG;
 //   Newton    with backtracking, as in iga_solve_newton.
 // There are no spin-waits: every loop is bounded by the Newton and Krylov caps.
 // The launch, the copy of its arguments and the read-back of the per-instance
