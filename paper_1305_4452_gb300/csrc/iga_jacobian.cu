@@ -274,7 +274,8 @@ __global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d
   if (pi0 >= d0.np) return;
   const DirArgs &dl = (DIM == 3) ? d2 : d1;
   const int pmid = (DIM == 3) ? blockIdx.z : 0;
-  const int pa = blockIdx.y * chunk, pb = min(pa + chunk, dl.np);
+  // the block's range of canonical last-axis pairs (pair index <= its transpose's)
+  const int pa = blockIdx.y * chunk, pb = min(pa + chunk, dl.nc);
   const size_t plane = (DIM == 3) ? (size_t)d0.np * d1.np * d2.X : (size_t)d0.np * d1.X;
   const int pi0T = d0.pair_T[pi0];
   const int i0 = d0.pair_i[pi0], j0 = d0.pair_j[pi0];
@@ -292,9 +293,9 @@ __global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d
   // CSR row starts: line start (the same for the whole block at a given pl) plus the
   // row's offset within its line
   const int64_t rA0 = (int64_t)w1 * csr.rp_p0[i0], rB0 = (int64_t)w1T * csr.rp_p0[j0];
-  for (int pl = pa; pl < pb; pl++) {
-    const int plT = dl.pair_T[pl];
-    if (pl > plT || (pl == plT && (pmid > pmidT || (pmid == pmidT && pi0 > pi0T)))) continue;
+  for (int c = pa; c < pb; c++) {
+    const int pl = dl.pair_c[c], plT = dl.pair_T[pl];
+    if (pl == plT && (pmid > pmidT || (pmid == pmidT && pi0 > pi0T))) continue;
     const int xs = dl.pair_x0[pl], np = dl.pair_np[pl];
     const T *pv = tab + (size_t)dl.pair_po[pl] * IGA_PVS;
     T acc = 0;
@@ -386,15 +387,15 @@ cudaError_t run_stages(iga_s *h, V *vals, const V *base, int fix) {
   cudaError_t ce = run_stage1<T, DIM, PLAN>(h, T1);
   if (ce) return ce;
   CsrArgs csr{h->rowptr, h->rp_line, h->rp_p0, h->weights, h->bnd};
-  const int chunk = 8;
+  const int chunk = 8, fchunk = 16;  // stage-2 pairs per block; final-stage canonical pairs per block
   if (DIM == 3) {
     dim3 g2((a0.np + 127) / 128, (a1.np + chunk - 1) / chunk, a2.X);
     IGA_LAUNCH(h, KC_STAGE2, (k_stage2<T, PLAN><<<g2, 128, 0, h->stream>>>(a0, a1, a2, T1, T2, chunk)));
-    dim3 g3((a0.np + 127) / 128, (a2.np + chunk - 1) / chunk, a1.np);
-    IGA_LAUNCH(h, KC_FINAL, (k_final<T, V, 3, PLAN><<<g3, 128, 0, h->stream>>>(a0, a1, a2, T2, csr, vals, base, chunk, fix)));
+    dim3 g3((a0.np + 127) / 128, (a2.nc + fchunk - 1) / fchunk, a1.np);
+    IGA_LAUNCH(h, KC_FINAL, (k_final<T, V, 3, PLAN><<<g3, 128, 0, h->stream>>>(a0, a1, a2, T2, csr, vals, base, fchunk, fix)));
   } else {
-    dim3 g3((a0.np + 127) / 128, (a1.np + chunk - 1) / chunk, 1);
-    IGA_LAUNCH(h, KC_FINAL, (k_final<T, V, 2, PLAN><<<g3, 128, 0, h->stream>>>(a0, a1, a2, T1, csr, vals, base, chunk, fix)));
+    dim3 g3((a0.np + 127) / 128, (a1.nc + fchunk - 1) / fchunk, 1);
+    IGA_LAUNCH(h, KC_FINAL, (k_final<T, V, 2, PLAN><<<g3, 128, 0, h->stream>>>(a0, a1, a2, T1, csr, vals, base, fchunk, fix)));
   }
   return cudaGetLastError();
 }
