@@ -72,9 +72,10 @@ def tune(batch, instances, U, opts=None, candidates=CANDIDATES, cache_path=None,
         U.copy_(U0)
         batch.solve(U, opts, check=False)  # first call captures the graph for this shape
         U.copy_(U0)
-        torch.cuda.synchronize()
+        if U.is_cuda:
+            torch.cuda.synchronize()
         t0 = time.perf_counter()
-        batch.solve(U, opts, check=False)
+        batch.solve(U, opts, check=False)  # synchronises (it reads the per-instance reports)
         times["%dx%d" % (c, t)] = 1e3 * (time.perf_counter() - t0)
     key = min(times, key=times.get)
     best = tuple(int(v) for v in key.split("x"))

@@ -15,3 +15,40 @@ def test_cache_roundtrip(tmp_path):
     assert autotune.load_cache(p) == {}
     autotune.save_cache({"k": {"ctas_per_sm": 2}}, p)
     assert autotune.load_cache(p)["k"]["ctas_per_sm"] == 2
+
+
+class _FakeBatch:
+    """Stands in for iga.Batch: a solve takes a fixed time per launch shape."""
+
+    def __init__(self, cost_ms):
+        self.cost_ms = cost_ms
+        self.shape = None
+        self.launches = []
+
+    def set_launch(self, ctas, threads=512):
+        self.shape = (ctas, threads)
+        self.launches.append(self.shape)
+
+    def solve(self, U, opts=None, check=True):
+        import time
+        time.sleep(self.cost_ms[self.shape] / 1e3)
+        U.add_(1.0)  # the solve changes U; the tuner restores it before each timing
+        return {}
+
+
+def test_tune_picks_the_fastest_shape_restores_u_and_caches_it(tmp_path):
+    torch = __import__("pytest").importorskip("torch")
+    cost = {s: 30.0 for s in autotune.CANDIDATES}
+    cost[(1, 512)] = 5.0
+    ins = [{"nel": 16, "p": 2, "lam": 1.0}] * 3
+    U = torch.zeros(4, dtype=torch.float64)
+    cache = str(tmp_path / "c.json")
+    b = _FakeBatch(cost)
+    r = autotune.tune(b, ins, U, cache_path=cache)
+    assert (r["ctas_per_sm"], r["threads"]) == (1, 512) and not r["cached"]
+    assert b.shape == (1, 512) and set(b.launches[:-1]) == set(autotune.CANDIDATES)
+    assert torch.equal(U, torch.zeros(4, dtype=torch.float64))
+    assert set(r["times_ms"]) == {"%dx%d" % s for s in autotune.CANDIDATES}
+    b2 = _FakeBatch(cost)
+    r2 = autotune.tune(b2, ins, U, cache_path=cache)
+    assert r2["cached"] and (r2["ctas_per_sm"], r2["threads"]) == (1, 512) and b2.launches == [(1, 512)]
