@@ -252,21 +252,36 @@ __global__ void __launch_bounds__(256) k_elem_gemm(GemmArgs g) {
   const uint32_t rowoff = (uint32_t)((r128 >> 3) * 128 + (r128 & 7) * 16);
   int it = 0;     // chunk counter over all m-tiles (stage it & 1)
   int last = -1;  // thread 0: the last chunk whose MMAs were committed
+  // copy chunk c of m-tile mt_ of the Qv operand into stage st_ (this thread's 64 bytes of
+  // its row), as one cp.async group
+  auto issue = [&](int mt_, int c_, int st_) {
+    const uint8_t *qr = reinterpret_cast<const uint8_t *>(g.Qv) + ((size_t)mt_ * GT + r128) * g.Kp * ES + (size_t)c_ * KB;
+    const uint32_t adst = su32(As + st_ * STAGE) + rowoff;
+#pragma unroll
+    for (int kc = half * 4; kc < half * 4 + 4; kc++) cp16(adst + kc * LBO, qr + kc * 16, true);
+    cp_commit();
+  };
+  // two stages in flight: the copy of the next chunk (the next m-tile's first chunk after a
+  // tile's last) is issued before the wait for the current one, and runs during the MMAs and
+  // the epilogue
+  if (m_count > 0) issue(m_first, 0, 0);
   for (int mi = 0; mi < m_count && !*abort_s; mi++) {
     const int mt = m_first + mi;
-    const uint8_t *qrow = reinterpret_cast<const uint8_t *>(g.Qv) + ((size_t)mt * GT + r128) * g.Kp * ES;
     for (int c = 0; c < nchunks; c++, it++) {
       const int st = it & 1;
-      if (it >= 2) {
-        if (tid == 0 && !mbar_wait(su32(done + st), ((it - 2) >> 1) & 1, abort_s)) *abort_s = 1;
-        __syncthreads();
-        if (*abort_s) break;
+      if ((c + 1 < nchunks) || (mi + 1 < m_count)) {
+        // the other stage is free once the MMAs of chunk it - 1, which read it, are complete
+        if (it >= 1) {
+          if (tid == 0 && !mbar_wait(su32(done + (st ^ 1)), ((it - 1) >> 1) & 1, abort_s)) *abort_s = 1;
+          __syncthreads();
+          if (*abort_s) break;
+        }
+        if (c + 1 < nchunks) issue(mt, c + 1, st ^ 1);
+        else issue(mt + 1, 0, st ^ 1);
+        cp_wait<1>();  // this chunk's copies have landed; the next chunk's may be in flight
+      } else {
+        cp_wait<0>();
       }
-      const uint32_t adst = su32(As + st * STAGE) + rowoff;
-#pragma unroll
-      for (int kc = half * 4; kc < half * 4 + 4; kc++) cp16(adst + kc * LBO, qrow + (size_t)c * KB + kc * 16, true);
-      cp_commit();
-      cp_wait<0>();
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (tid == 0) {
@@ -325,6 +340,7 @@ __global__ void __launch_bounds__(256) k_elem_gemm(GemmArgs g) {
     tc_fence_before();
     __syncthreads();  // the accumulator is read before the next m-tile's MMAs overwrite it
   }
+  cp_wait<0>();  // after a stop a prefetched chunk may still be in flight
   // after a stop, wait (bounded) for the last committed MMAs before freeing the tensor memory
   if (tid == 0 && *abort_s) {
     if (last >= 0) (void)mbar_wait(su32(done + (last & 1)), (last >> 1) & 1, nullptr);
