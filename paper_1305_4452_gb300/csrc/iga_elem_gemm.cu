@@ -26,7 +26,8 @@
 //     memory for the CTA's group of element tiles;
 //   - two threads per row copy an element row of each Qv chunk (cp.async, 16 B) into the
 //     canonical K-major layout without swizzling (8-row x 16-byte core matrices, 128 B
-//     apart along M/N, 2 KB apart along K), two stages;
+//     apart along M/N, 2 KB apart along K), two stages, the next chunk's copy issued
+//     before the wait for the current one;
 //   - thread 0 issues the chunk's four tcgen05.mma (32 bytes of K each) and commits
 //     them to the stage's barrier, which frees the stage two chunks later;
 //   - after the last chunk warp w reads accumulator rows 32 (w % 4) .. + 31 (half the
