@@ -266,7 +266,10 @@ __device__ __forceinline__ bool on_dirichlet(const BndArgs &b, int dim, const in
 // or columns become those of an identity row and a zeroed column instead.
 // J is symmetric (Q is), so only the entries whose pair triple (pl, pmid, pi0)
 // is not above its transpose (plT, pmidT, pi0T) in lexicographic order are
-// contracted; each value is written at (A, B) and at (B, A).
+// contracted; each value is written at (A, B) and at (B, A).  A block walks a range
+// of the canonical last-axis pairs (pl <= plT) for its pmid and 128 axis-0 pairs;
+// CSR row starts come from the start of the row's line (i1, i2) plus the line's
+// stencil width times the prefix sum of the axis-0 widths before i0.
 template <typename T, typename V, int DIM, int PLAN>
 __global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d2, const T *__restrict__ in, CsrArgs csr,
                                                V *__restrict__ vals, const V *__restrict__ base, int chunk, int fix) {
