@@ -149,16 +149,21 @@ iga_status iga_form_residual(iga_t iga, const double *U, double *F);
  * real-time loop cannot take an allocation's latency or failure): this call
  * allocates nothing.  The paper has no counterpart; it is a library-level
  * variant.  Its element-vector scratch is a fixed array of
- * IGA_NOALLOC_MAX_ELEMENT_VALUES doubles (16 MiB) in the library's device memory,
- * held on every GPU that loads the library until the process exits.
- *  - Problems with elements x (p+1)^dim above that limit are rejected with
+ * IGA_NOALLOC_MAX_ELEMENT_VALUES doubles (16 MiB) in the library's device memory.
+ *  - iga_create (non-periodic handles) looks the array's address up on the current
+ *    device; this loads the library code that holds the array and reserves its
+ *    16 MiB on that device, which keeps it until the process exits.  Should that
+ *    look-up fail at creation, the first call repeats it and may then be the one
+ *    that reserves the array: make that call before any stream capture.
+ *  - The current device must be the one that was current at iga_create
+ *    (IGA_EINVAL otherwise).
+ *  - Problems with elements x (p+1)^dim above the array's size are rejected with
  *    IGA_EINVAL (nothing is written); iga_form_residual has no such limit.
- *  - The first call on a device looks up the array's device address with that
- *    device current; make it before any stream capture.
  *  - All calls share the array: calls that overlap on the GPU race.  Nothing in
  *    it needs to start at zero (every entry read was written by the same call).
  * U and F: device double[n], caller-owned, distinct; stream-ordered like the other
- * calls; results are bit-identical to iga_form_residual. */
+ * calls; the kernels are those of iga_form_residual, so the results are
+ * bit-identical to it. */
 #define IGA_NOALLOC_MAX_ELEMENT_VALUES 2097152u
 iga_status iga_form_residual_noalloc(iga_t iga, const double *U, double *F);
 

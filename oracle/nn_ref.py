@@ -1,10 +1,10 @@
 """CPU FP64 reference of the convolutional neural operator (TEST INFRASTRUCTURE).
 
 Plain numpy: zero-padded dilated 3x3 convolutions written as nine shifted
-channel contractions, SiLU, a masked mean-squared error, and the backward pass
-written out by hand (chain rule per layer).  Parameters use the flat layout of
-the CUDA network: per layer W[cout][3][3][cin] then b[cout].  Never imported by
-the product path.
+channel contractions, SiLU, a masked mean-squared error, the backward pass
+written out by hand (chain rule per layer), and the Adam update of Kingma and Ba
+(2015, Algorithm 1).  Parameters use the flat layout of the CUDA network: per
+layer W[cout][3][3][cin] then b[cout].  Never imported by the product path.
 """
 import numpy as np
 
@@ -95,3 +95,29 @@ def loss_and_grad(params, shapes, x, tgt, mask, beta=0.0):
         grad[boff:boff + cout] = dz.sum(axis=(0, 1, 2))
         da = dxp[:, d:d + H, d:d + W, :]
     return loss, grad
+
+
+class AdamState:
+    """First and second moment estimates m, v (zero at the start) and the step count t."""
+
+    def __init__(self, n):
+        self.m = np.zeros(n)
+        self.v = np.zeros(n)
+        self.t = 0
+
+
+def adam_step(params, grad, state, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma and Ba 2015, Algorithm 1), elementwise:
+        t <- t + 1
+        m <- beta1 m + (1 - beta1) g          (biased first moment)
+        v <- beta2 v + (1 - beta2) g^2        (biased second raw moment)
+        m_hat = m / (1 - beta1^t),  v_hat = v / (1 - beta2^t)   (bias corrections)
+        theta <- theta - lr m_hat / (sqrt(v_hat) + eps)
+    Returns the new parameters; `state` is updated in place."""
+    g = np.asarray(grad, dtype=np.float64)
+    state.t += 1
+    state.m = beta1 * state.m + (1.0 - beta1) * g
+    state.v = beta2 * state.v + (1.0 - beta2) * g * g
+    m_hat = state.m / (1.0 - beta1 ** state.t)
+    v_hat = state.v / (1.0 - beta2 ** state.t)
+    return np.asarray(params, dtype=np.float64) - lr * m_hat / (np.sqrt(v_hat) + eps)

@@ -188,6 +188,7 @@ extern "C" iga_status iga_create(const iga_desc *d, const iga_bratu *b, void *st
   }
   iga_s *h = new iga_s();
   h->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&h->device) != cudaSuccess) h->device = -1;
   const bool periodic = d->periodic[0] || d->periodic[1] || (d->dim == 3 && d->periodic[2]);
   iga_status st = periodic ? iga_periodic_setup(h, d, b) : iga_create_impl(h, d, b);
   if (st != IGA_OK) {
@@ -196,6 +197,7 @@ extern "C" iga_status iga_create(const iga_desc *d, const iga_bratu *b, void *st
     delete h;
     return st;
   }
+  if (!periodic) noalloc_setup(h);
   *out = h;
   return IGA_OK;
 }

@@ -724,26 +724,12 @@ static cudaError_t launch_rate_term(iga_s *h, const double *U, double *Fe) {
 
 cudaError_t launch_residual(iga_s *h, const double *U, double *F) {
   if (h->inner) return periodic_residual(h, U, F);
-  DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
-  constexpr int NE = 4;
-  unsigned grid = (unsigned)((h->nelem + NE - 1) / NE);
-  IGA_LAUNCH(h, KC_RES_ELEM, DISPATCH_DP(h->dim, h->p, ({
-    size_t sm = res_smem<D, PP>(NE);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_residual<D, PP, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_residual<D, PP, NE><<<grid, 128, sm, h->stream>>>(a0, a1, a2, U, h->weights, h->geom, h->gl, h->lambda, h->Fe, h->nelem);
-  })));
-  cudaError_t ce = launch_rate_term(h, U, h->Fe);
-  if (ce) return ce;
-  unsigned g2 = (unsigned)((h->N + 255) / 256);
-  if (h->dim == 3)
-    IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<3><<<g2, 256, 0, h->stream>>>(a0, a1, a2, h->Fe, U, h->bnd, F, h->N, h->p + 1, nullptr)));
-  else
-    IGA_LAUNCH(h, KC_RES_GATHER, (k_gather_residual<2><<<g2, 256, 0, h->stream>>>(a0, a1, a2, h->Fe, U, h->bnd, F, h->N, h->p + 1, nullptr)));
-  return cudaGetLastError();
+  return launch_residual_into(h, U, F, h->Fe);
 }
 
-// The residual kernels of launch_residual, with the element-vector buffer supplied
-// by the caller instead of the handle's own (used by iga_form_residual_noalloc).
+// The residual kernels (element pass, rate term, row gather) with the element-vector
+// buffer supplied by the caller: the handle's own (launch_residual) or the fixed
+// array of iga_form_residual_noalloc, so both entry points run the same code.
 cudaError_t launch_residual_into(iga_s *h, const double *U, double *F, double *Fe) {
   DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
   constexpr int NE = 4;

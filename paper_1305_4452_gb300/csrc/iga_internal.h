@@ -163,6 +163,8 @@ struct iga_s {
   Dir dir[3];
   DirDev ddev[3];
   cudaStream_t stream = nullptr;
+  int device = -1;             // CUDA device current at iga_create
+  double *noalloc_scratch = nullptr;  // device address of the allocation-free residual's array
   double lambda = 0.0;
   bool has_geom = false, has_w = false, has_kappa = false;
   BndArgs bnd{};
@@ -236,6 +238,13 @@ DirArgs dir_args(const DirDev &d);
 cudaError_t launch_geometry(iga_s *h, const double *ctrl_dev, const double *logk_dev);
 cudaError_t launch_colidx(iga_s *h);
 cudaError_t launch_residual(iga_s *h, const double *U, double *F);
+// The residual kernels with the element-vector buffer Fe supplied by the caller
+// (launch_residual passes the handle's own; non-periodic handles only)
+cudaError_t launch_residual_into(iga_s *h, const double *U, double *F, double *Fe);
+// ---- allocation-free residual (iga_noalloc.cu) ----
+// Looks up, on the current device, the address of the fixed scratch array of
+// iga_form_residual_noalloc and keeps it in h->noalloc_scratch (left null on failure)
+void noalloc_setup(iga_s *h);
 // Q00 = cs * g^T S g - cr * jw/W^2 * lambda * exp(u) at every Gauss point (U may be null when cr == 0)
 cudaError_t launch_q00(iga_s *h, const double *U, double cs, double cr);
 // the same Q00 computed in FP32 arithmetic (stored as double), for the FP32 Jacobian

@@ -10,20 +10,22 @@
 // library's own device memory, so the call itself never allocates.
 //
 // The array is a file-scope __device__ variable of IGA_NOALLOC_MAX_ELEMENT_VALUES
-// doubles (16 MiB).  Every GPU that loads this code holds it until the process
-// exits.  Its device address is looked up once per device, on the first call made
-// with that device current (cudaGetSymbolAddress); make that first call outside
-// any stream capture.  All calls share the array, so calls that overlap on the GPU
-// (different streams or different handles at the same time) race on it; the
-// kernels overwrite every entry they later read, so no part of it has to start
-// at zero and stale contents from an earlier call are never used.
+// doubles (16 MiB).  CUDA loads the code of this file, and reserves the array on a
+// device, the first time its address is asked for on that device.  iga_create does
+// that (noalloc_setup, with the handle's device current), so a device holds the
+// array from its first handle's creation until the process exits, and the entry
+// point itself neither loads code nor reserves memory.  Should that look-up have
+// failed at creation, the first call on the handle repeats it (and may then be the
+// one that reserves the array); make that call outside any stream capture.  All
+// calls share the array, so calls that overlap on the GPU (different streams or
+// different handles at the same time) race on it; the kernels overwrite every entry
+// they later read, so no part of it has to start at zero and stale contents from an
+// earlier call are never used.
 #include <cuda_runtime.h>
 
 #include <mutex>
 
 #include "iga_internal.h"
-
-cudaError_t launch_residual_into(iga_s *h, const double *U, double *F, double *Fe);
 
 static __device__ __align__(256) double g_residual_scratch[IGA_NOALLOC_MAX_ELEMENT_VALUES];
 
@@ -33,6 +35,8 @@ std::mutex g_mu;
 double *g_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device (looked up once per device).
+// In host code g_residual_scratch names a host-side stand-in, not device memory: only
+// the address returned by cudaGetSymbolAddress may be handed to a kernel.
 cudaError_t scratch_address(double **out) {
   int dev = 0;
   cudaError_t ce = cudaGetDevice(&dev);
@@ -49,6 +53,12 @@ cudaError_t scratch_address(double **out) {
   return cudaSuccess;
 }
 }  // namespace
+
+void noalloc_setup(iga_s *h) {
+  double *p = nullptr;
+  h->noalloc_scratch = (scratch_address(&p) == cudaSuccess) ? p : nullptr;
+  cudaGetLastError();  // a failed look-up is retried by the first call; drop its error state here
+}
 
 extern "C" iga_status iga_form_residual_noalloc(iga_t h, const double *U, double *F) {
   if (!h) return IGA_EINVAL;
@@ -68,13 +78,22 @@ extern "C" iga_status iga_form_residual_noalloc(iga_t h, const double *U, double
                         need, (unsigned)IGA_NOALLOC_MAX_ELEMENT_VALUES);
     return IGA_EINVAL;
   }
-  double *scratch = nullptr;
-  cudaError_t ce = scratch_address(&scratch);
-  if (ce != cudaSuccess) {
-    h->err = iga_format("iga_form_residual_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(ce));
-    return IGA_ECUDA;
+  int dev = -1;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess || dev != h->device) {
+    h->err = iga_format("iga_form_residual_noalloc: current device %d is not the handle's device %d", dev, h->device);
+    return IGA_EINVAL;
   }
-  ce = launch_residual_into(h, U, F, scratch);
+  if (!h->noalloc_scratch) {
+    double *p = nullptr;
+    ce = scratch_address(&p);
+    if (ce != cudaSuccess) {
+      h->err = iga_format("iga_form_residual_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(ce));
+      return IGA_ECUDA;
+    }
+    h->noalloc_scratch = p;
+  }
+  ce = launch_residual_into(h, U, F, h->noalloc_scratch);
   if (ce != cudaSuccess) {
     h->err = iga_format("iga_form_residual_noalloc: %s", cudaGetErrorString(ce));
     return IGA_ECUDA;

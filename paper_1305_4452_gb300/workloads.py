@@ -90,6 +90,23 @@ def uniform_open_knots(nel, p, k=None):
     return np.asarray(U, dtype=np.float64)
 
 
+def graded_open_knots(nel, p, seed, k=None, extra=(), spread=0.6):
+    """Open knot vector on [0,1] with nel spans of seeded, unequal lengths (length of
+    span e proportional to 1 + spread * (2 u_e - 1), u_e from splitmix64(seed)); every
+    interior knot repeated p-k times, and the interior knots listed in `extra`
+    (1..nel-1) repeated once more each (a local drop of continuity)."""
+    if k is None or k < 0:
+        k = p - 1
+    h = 1.0 + spread * (2.0 * uniform(seed, nel) - 1.0)
+    x = np.concatenate([[0.0], np.cumsum(h)])
+    x /= x[-1]
+    U = [0.0] * (p + 1)
+    for e in range(1, nel):
+        U += [x[e]] * (p - k + (1 if e in extra else 0))
+    U += [1.0] * (p + 1)
+    return np.asarray(U, dtype=np.float64)
+
+
 # ---------------------------------------------------------------- geometry ---
 
 def _bezier_elevate(Pw, times):

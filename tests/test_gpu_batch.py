@@ -57,6 +57,26 @@ def test_batch_solves_every_instance_to_tolerance(I, ctas, threads):
     b.close()
 
 
+def test_batch_on_the_configurations_mesh_distribution(I):
+    """The batched configuration's own draw (square meshes n ~ U{16..128}, p ~ U{2,3},
+    lambda ~ U[0.5, 6]) plus its largest instance, 128^2 cubic: the largest instances take
+    the biggest shared-memory operand vectors and the longest GMRES cycles.  The oracle's
+    residual at every instance's solution meets the tolerance."""
+    ins = W.batch_instances(15, seed=0)
+    ins.append({"nel": 128, "p": 3, "lam": 5.5})
+    assert max(x["nel"] for x in ins) == 128 and min(x["nel"] for x in ins) < 48
+    b = I.Batch(ins)
+    U = torch.zeros(b.total, dtype=torch.float64, device="cuda")
+    rep = b.solve(U)
+    assert rep["solved"] == len(ins)
+    Uh = U.cpu().numpy()
+    for i, x in enumerate(ins):
+        Ui = Uh[b.offsets[i]:b.offsets[i + 1]]
+        F = oracle_problem(x).residual(Ui)
+        assert np.linalg.norm(F) <= 1.5e-10, (i, x, np.linalg.norm(F))
+    b.close()
+
+
 def test_batch_matches_single_problem_solver(I):
     ins = instances(8, seed=5)
     b = I.Batch(ins)

@@ -69,6 +69,33 @@ def test_loss_grad_is_deterministic(M):
     net.close()
 
 
+def test_adam_steps_match_the_cpu_reference(M):
+    """iga_nn_adam_step against Kingma and Ba's Algorithm 1 in FP64 (nn_ref.adam_step):
+    three steps, each on the gradient the network itself returns at its current
+    weights; the update of every parameter is compared element by element."""
+    net = M.Net(10, 9, hidden=16, dilations=(1, 2, 1), max_batch=2, seed=5)
+    rng = np.random.default_rng(3)
+    x = torch.tensor(rng.normal(0, 1, (2, 10, 9, 4)), dtype=torch.float32, device="cuda")
+    t = torch.tensor(rng.normal(0, 0.3, (2, 10, 9)), dtype=torch.float32, device="cuda")
+    st = R.AdamState(net.nparams)
+    g = torch.zeros(net.nparams, dtype=torch.float32, device="cuda")
+    for step, (lr, b1, b2, eps) in enumerate([(1e-3, 0.9, 0.999, 1e-8), (2e-3, 0.9, 0.999, 1e-8),
+                                              (5e-4, 0.8, 0.99, 1e-6)]):
+        w0 = net.get_params().astype(np.float64)
+        net.loss_grad(x, t, None, g)
+        gh = g.cpu().numpy().astype(np.float64)
+        net.adam_step(lr, b1, b2, eps)
+        w1 = net.get_params().astype(np.float64)
+        ref = R.adam_step(w0, gh, st, lr, b1, b2, eps)
+        # FP32 moments and weights: the step agrees to ~1e-6 of lr, the weights to
+        # their own rounding
+        err = np.abs((w1 - w0) - (ref - w0))
+        bound = 1e-5 * lr + 2.0 * np.finfo(np.float32).eps * np.abs(w0)
+        assert np.all(err <= bound), (step, float((err / bound).max()))
+        assert np.count_nonzero(gh) > 0.9 * net.nparams  # the comparison covers real updates
+    net.close()
+
+
 def test_trained_guess_reduces_newton_iterations(M):
     from paper_1305_4452_gb300 import iga
     nel = 16

@@ -37,12 +37,42 @@ def rel(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
+def graded_knots(dim, p, nel, k=None):
+    """Seeded unequal spans per direction; direction 0 also drops the continuity by one
+    at its second interior knot (a repeated knot) when that keeps k >= 0."""
+    out = []
+    for d in range(dim):
+        kk = p - 1 if k is None else k
+        extra = (2,) if d == 0 and kk >= 1 and nel[d] > 2 else ()
+        out.append(W.graded_open_knots(nel[d], p, 31 + d, k=k, extra=extra))
+    return out
+
+
+def perturbed_nurbs(knots, p, seed):
+    """A rational map near the identity on the given knots: Greville control points moved by
+    a smooth bump of amplitude 0.03 and weights drawn in [0.9, 1.1] (det J stays > 0)."""
+    dim = len(knots)
+    gr = [W.greville(kn, p) for kn in knots]
+    mesh = np.meshgrid(*gr[::-1], indexing="ij")[::-1]  # natural order: axis 0 fastest
+    X = np.stack([m.reshape(-1) for m in mesh], axis=1)
+    bump = np.prod(np.sin(np.pi * X), axis=1)
+    for d in range(dim):
+        X[:, d] += 0.03 * bump * (1.0 if d == 0 else -1.0)
+    return X, W.uniform(seed, X.shape[0], 0.9, 1.1)
+
+
 def make_pair(dim, p, nel, lam=1.0, k=None, geom=None, kappa_seed=None, bc=True, dirichlet=None):
-    """GPU discretisation and oracle problem on the same inputs."""
+    """GPU discretisation and oracle problem on the same inputs.  geom: None (identity map
+    on uniform knots), "annulus", "graded" (identity map, unequal spans and a repeated
+    knot) or "graded_nurbs" (the same knots under a rational map)."""
     I = iga()
     nel = [nel] * dim if np.isscalar(nel) else list(nel)
     ctrl = weights = knots = None
-    if geom == "annulus":
+    if geom in ("graded", "graded_nurbs"):
+        knots = graded_knots(dim, p, nel, k)
+        if geom == "graded_nurbs":
+            ctrl, weights = perturbed_nurbs(knots, p, 41)
+    elif geom == "annulus":
         kn, ctrl, weights = W.quarter_annulus(tuple(nel) if dim == 3 else (nel[0], nel[1], 1), p)
         if dim == 2:
             n0, n1 = len(kn[0]) - p - 1, len(kn[1]) - p - 1
@@ -75,6 +105,14 @@ SMALL = [
     (3, 3, (5, 6, 3), None, "annulus", None),
     (3, 1, (4, 3, 5), None, None, None),
     (3, 4, (3, 2, 3), 2, None, None),
+    # unequal spans (Sec. 2.1 allows any non-decreasing knot vector), a repeated interior knot
+    (2, 2, (9, 7), None, "graded", None),
+    (2, 3, (7, 6), None, "graded", 5),
+    (2, 4, (6, 5), None, "graded_nurbs", None),
+    (2, 3, (8, 6), 1, "graded", None),
+    (3, 2, (6, 5, 4), None, "graded", None),
+    (3, 3, (5, 4, 4), None, "graded_nurbs", None),
+    (3, 4, (4, 3, 3), None, "graded", None),
 ]
 
 
@@ -207,6 +245,17 @@ def test_full_size_annulus_64_cubed_sampled():
     Jg = np.concatenate([J[rp_h[r]:rp_h[r + 1]].cpu().numpy() for r in rows])
     jscale = torch.abs(J).max().item()
     assert np.abs(Jg - Jo).max() <= TOL * jscale
+    del J
+    # the benchmark's solve (U = 0, FP64 Jacobian, GMRES + Jacobi): the oracle's residual at
+    # the GPU's solution, on the sampled rows plus the rows next to every face
+    U.zero_()
+    rep = disc.solve_newton(U)
+    assert rep.status == 0 and rep.fnorm <= 1e-10
+    Us = U.cpu().numpy()
+    edge = np.flatnonzero(~W.boundary_mask(n) & (np.indices(n[::-1]).reshape(3, -1)[::-1] == 1).any(axis=0))
+    chk = np.unique(np.concatenate([rows, edge[(W.uniform(91, 64) * len(edge)).astype(np.int64)]]))
+    Fs = prob.residual_rows(Us, chk)
+    assert np.abs(Fs).max() <= 1e-10 * (1 + 1e-12), np.abs(Fs).max()
     disc.close()
 
 
@@ -345,7 +394,8 @@ def test_newton_split_residual_matches_oracle(case):
     disc.close()
 
 
-MF_CASES = [(2, 2, (9, 7), None, None, None), (2, 3, (7, 6), None, "annulus", None), (2, 2, (9, 7), None, None, 3),
+MF_CASES = [(2, 2, (9, 7), None, "graded", None), (3, 3, (5, 4, 4), None, "graded_nurbs", None),
+            (2, 2, (9, 7), None, None, None), (2, 3, (7, 6), None, "annulus", None), (2, 2, (9, 7), None, None, 3),
             (3, 3, (5, 4, 3), None, "annulus", None), (3, 2, (5, 4, 3), 0, None, None), (3, 4, (3, 2, 3), 2, None, None)]
 
 
@@ -432,7 +482,8 @@ def test_newton_with_fd_jacobian_reaches_the_oracle_solution():
 
 # ------------------------------------------- Sec. 4.2 time-dependent problems
 
-TS_CASES = [(2, 2, (9, 7), None, None, None), (2, 3, (7, 6), None, "annulus", None), (2, 2, (9, 7), None, None, 3),
+TS_CASES = [(2, 3, (7, 6), None, "graded_nurbs", None), (3, 2, (5, 4, 3), None, "graded", None),
+            (2, 2, (9, 7), None, None, None), (2, 3, (7, 6), None, "annulus", None), (2, 2, (9, 7), None, None, 3),
             (3, 3, (4, 5, 3), None, "annulus", None), (3, 2, (5, 4, 3), None, None, None), (2, 4, (5, 4), None, None, None)]
 
 

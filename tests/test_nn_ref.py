@@ -53,3 +53,40 @@ def test_backward_matches_finite_differences(beta):
         lm, _ = R.loss_and_grad(params - e, shapes, x, tgt, mask, beta)
         fd = (lp - lm) / (2 * h)
         assert abs(fd - grad[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, grad[i])
+
+
+# ---------------------------------------------- Adam (Kingma and Ba 2015, Alg. 1)
+
+def test_adam_first_step_moves_by_lr_times_the_sign():
+    # t = 1: m_hat = g and v_hat = g^2 exactly, so the step is lr g / (|g| + eps)
+    g = np.array([3.0, -0.5, 1e-3, -2e-6])
+    st = R.AdamState(4)
+    out = R.adam_step(np.zeros(4), g, st, lr=0.01, eps=1e-8)
+    assert np.allclose(out, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-14, atol=0)
+    assert st.t == 1
+
+
+def test_adam_constant_gradient_keeps_the_corrected_moments_exact():
+    # with g fixed, the bias corrections make m_hat = g and v_hat = g^2 at every t;
+    # without them the first steps would be about 3x too long
+    g = np.array([0.7, -1.3])
+    st = R.AdamState(2)
+    th = np.zeros(2)
+    for t in range(1, 6):
+        th = R.adam_step(th, g, st, lr=1e-2, beta1=0.9, beta2=0.999, eps=0.0)
+        assert np.allclose(th, -1e-2 * t * np.sign(g), rtol=1e-13, atol=0)
+
+
+def test_adam_alternating_gradient_closed_form():
+    # g, then -g: m_2 = -(1-b1)^2 g and v_2 = (1-b2)(1+b2) g^2, so m_hat_2 =
+    # -(1-b1)/(1+b1) g, v_hat_2 = g^2 and the second step is +lr (1-b1)/(1+b1) sign(g);
+    # swapping beta1 and beta2 changes the factor
+    b1, b2, lr = 0.9, 0.999, 1e-3
+    g = np.array([2.0, -0.25])
+    st = R.AdamState(2)
+    th1 = R.adam_step(np.zeros(2), g, st, lr, b1, b2, eps=0.0)
+    th2 = R.adam_step(th1, -g, st, lr, b1, b2, eps=0.0)
+    step2 = th2 - th1
+    assert np.allclose(step2, lr * (1 - b1) / (1 + b1) * np.sign(g), rtol=1e-12, atol=0)
+    assert np.allclose(st.m, -(1 - b1) ** 2 * g, rtol=1e-14)
+    assert np.allclose(st.v, (1 - b2) * (1 + b2) * g * g, rtol=1e-13)

@@ -692,3 +692,71 @@ def test_unclamping_a_closed_curve_gives_periodic_control_points():
     assert np.abs(V2 - V).max() < 1e-15
     assert np.abs(P2 - Pext).max() < 1e-11
     assert np.abs(P2[-p:] - P2[:p]).max() < 1e-11
+
+
+# ------------------------------------ row helpers against the whole assembly
+# or_residual_rows / or_jacobian_rows compute selected rows from the elements that
+# contain each row's function (Sec. 2.7: the support of N_A is p+1 spans per
+# direction).  They check the full-size GPU runs, so they are pinned here to the
+# whole-mesh element loop (Algorithm 3), row by row, on every face, edge and
+# corner and on rows next to repeated or unequal knots.
+
+def _boundary_and_sampled_rows(n, count, seed):
+    idx = np.indices(n[::-1]).reshape(len(n), -1)[::-1]
+    N = idx.shape[1]
+    pick = np.zeros(N, dtype=bool)
+    for d, nd in enumerate(n):
+        for v in (0, 1, nd - 2, nd - 1):  # faces and the layer next to them
+            pick |= idx[d] == v
+    sel = np.flatnonzero(pick)
+    rng = np.random.default_rng(seed)
+    extra = rng.choice(N, size=min(count, N), replace=False)
+    return np.unique(np.concatenate([sel, extra]))
+
+
+ROW_CASES = [
+    # (dim, p, knots factory, geometry, kappa, dirichlet)
+    (2, 1, lambda: [W.uniform_open_knots(6, 1), W.graded_open_knots(5, 1, 3)], None, False, True),
+    (2, 2, lambda: [W.graded_open_knots(6, 2, 1, extra=(2,)), W.graded_open_knots(5, 2, 2)], None, True, True),
+    (2, 3, lambda: [W.uniform_open_knots(5, 3, 1), W.graded_open_knots(6, 3, 4, extra=(1, 4))], None, False, False),
+    (2, 4, lambda: [W.graded_open_knots(4, 4, 5), W.uniform_open_knots(4, 4, 2)], None, False, True),
+    (2, 3, None, "annulus", False, True),
+    (3, 2, lambda: [W.graded_open_knots(4, 2, 6, extra=(2,)), W.uniform_open_knots(3, 2), W.graded_open_knots(3, 2, 7)],
+     None, False, True),
+    (3, 3, None, "annulus", True, True),
+    (3, 4, lambda: [W.uniform_open_knots(2, 4, 2)] * 2 + [W.graded_open_knots(3, 4, 8)], None, False, False),
+    (3, 1, lambda: [W.graded_open_knots(4, 1, 9), W.uniform_open_knots(3, 1), W.uniform_open_knots(3, 1)], None,
+     False, True),
+]
+
+
+@pytest.mark.parametrize("case", ROW_CASES, ids=lambda c: "d%dp%d_%s_kap%d_bc%d" % (c[0], c[1], c[3], c[4], c[5]))
+def test_row_helpers_equal_the_whole_mesh_assembly(case):
+    dim, p, knots_f, geom, kap, bc = case
+    ctrl = w = None
+    if geom == "annulus":
+        if dim == 3:
+            knots, ctrl, w = W.quarter_annulus((3, 4, 2), p)
+        else:
+            knots, ctrl, w = random_nurbs_2d(4, 3, p, 0)
+    else:
+        knots = knots_f()
+    n = [len(k) - p - 1 for k in knots]
+    N = int(np.prod(n))
+    lk = W.uniform(17, N, -0.5, 0.5) if kap else None
+    prob = O.Problem(knots, [p] * dim, ctrl=ctrl, weights=w, lam=1.9, log_kappa=lk,
+                     dirichlet=dirichlet_all(dim, 0.25) if bc else None)
+    U = W.uniform(23, N, -0.4, 0.4)
+    F = prob.residual(U)
+    J = prob.jacobian(U)
+    rowptr, _ = prob.pattern()
+    rows = _boundary_and_sampled_rows(n, 20, 5)
+    Fr = prob.residual_rows(U, rows)
+    Jr = prob.jacobian_rows(U, rows)
+    Jsel = np.concatenate([J[rowptr[r]:rowptr[r + 1]] for r in rows])
+    sf, sj = np.abs(F).max(), np.abs(J).max()
+    assert np.abs(Fr - F[rows]).max() <= 1e-14 * sf
+    assert np.abs(Jr - Jsel).max() <= 1e-14 * sj
+    # every row once, in a shuffled order: the helpers do not depend on the order asked
+    perm = np.random.default_rng(1).permutation(N)
+    assert np.abs(prob.residual_rows(U, perm) - F[perm]).max() <= 1e-14 * sf
