@@ -8,11 +8,18 @@ the C ABI (residual assembly, Jacobian assembly, Krylov, line search).
 The discretisation (knots, tables, CSR pattern, geometry factors) is set up once
 per process, outside the timed region; its time is reported as setup_ms.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-extras]
 
 Under torchrun (N > 1) every rank solves its own replica (weak scaling); rank 0
-prints one JSON line.  --impl reference times the oracle (plain C, one thread) on
-a bounded sample of the same workload and prints the same metric.
+prints one JSON line.  The value is timed with the library's per-launch profiler
+off; a second, profiled pass over the same solves gives the kernel shares and the
+roofline of the dominant kernel, against FP64/FP32/copy peaks measured in the same
+process (iga_measure_peaks).  Extra keys (skipped with --no-extras) carry the
+other half of the metric: Newton solves/s of the 128^3 quadratic cube with the
+FP64 Jacobian against the reduced-precision ones (same Krylov method each), and
+the learned initial guess against the zero start on held-out kappa fields.
+--impl reference times the oracle (plain C, colour-loop timing mode on all host
+cores) on a bounded sample of the same workload and prints the same metric.
 """
 import argparse
 import json
@@ -29,15 +36,14 @@ sys.path.insert(0, ROOT)
 METRIC = "assembled Jacobian nnz/s & Newton solves/s to ||F||≤1e-10, FP64 vs mixed/NN"
 UNIT = "solves/s"
 NEL, P, LAM = 64, 3, 2.0
-# FP64 peak of GB300: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.070 GHz (max SM clock)
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
-def peaks():
+def hbm_peak():
+    """The measured copy bandwidth of the GB300s, else the fallback."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return float(d["hbm_gbs"]), "measured (copy, MEASURED_PEAKS.json)"
     except Exception:
         return 6800.0, "fallback"
 
@@ -94,35 +100,54 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU oracle ---
-def oracle_sample(min_seconds=10.0, newton_its=3):
-    """Time the oracle's residual and Jacobian assembly on an 8x8x8-element block of
-    the same discretisation (degree, rule, rational geometry, lambda) until at
-    least min_seconds of CPU work, extrapolate per element to the 64^3 mesh, and
-    convert to solves/s with one Jacobian + one residual per Newton step (plus the
-    final residual).  The oracle's linear solves are not counted, so the figure
-    favours the CPU."""
-    import numpy as np
+def _oracle_problem(nel, p=P):
     import oracle as O
     from paper_1305_4452_gb300 import workloads as W
-    sub = 8
-    kn, ctrl, w = W.quarter_annulus(sub, P)
-    prob = O.Problem(kn, [P] * 3, ctrl=ctrl, weights=w, lam=LAM, dirichlet={(a, s): 0.0 for a in range(3) for s in range(2)})
-    U = W.interior_field([sub + P] * 3, 2)
+    kn, ctrl, w = W.quarter_annulus(nel, p)
+    prob = O.Problem(kn, [p] * 3, ctrl=ctrl, weights=w, lam=LAM, dirichlet={(a, s): 0.0 for a in range(3) for s in range(2)})
+    n = [len(k) - p - 1 for k in kn]
+    return prob, W.interior_field(n, 2)
+
+
+def oracle_whole_mesh(newton_its):
+    """The oracle's residual and Jacobian assembly of the whole benchmark mesh, each timed
+    once, in its colour-loop timing mode on every OpenMP thread of this host (the same
+    element arithmetic as the serial oracle, elements of one colour spread over the
+    threads).  Solves/s counts (newton_its + 1) residuals and newton_its Jacobians per
+    solve, as the GPU's Newton takes; the oracle's linear solves are not counted, so the
+    figure favours the CPU."""
+    import oracle as O
+    O.build()
+    prob, U = _oracle_problem(NEL)
+    t0 = time.perf_counter()
     prob.pattern()
-    tr, tj, reps = 0.0, 0.0, 0
-    t_start = time.time()
-    while reps == 0 or time.time() - t_start < min_seconds:
-        t = time.perf_counter(); prob.residual(U); tr += time.perf_counter() - t
-        t = time.perf_counter(); prob.jacobian(U); tj += time.perf_counter() - t
-        reps += 1
-    scale = (NEL ** 3) / float(sub ** 3)
-    tr_full, tj_full = tr / reps * scale, tj / reps * scale
-    t_solve = newton_its * (tr_full + tj_full) + tr_full
-    return {"value": 1.0 / t_solve, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "oracle residual+Jacobian assembly of an 8^3-element block of the annulus (p=3, 4^3 Gauss points, "
-                      "lambda=2), %d repetitions (%.1f s), extrapolated x%d to 64^3 and to %d Newton steps; linear solves "
-                      "not counted" % (reps, time.time() - t_start, int(scale), newton_its),
-            "residual_s_full_mesh": tr_full, "jacobian_s_full_mesh": tj_full}
+    t_pat = time.perf_counter() - t0
+    t = time.perf_counter(); prob.residual_colored(U); tr = time.perf_counter() - t
+    t = time.perf_counter(); prob.jacobian_colored(U); tj = time.perf_counter() - t
+    t_solve = newton_its * (tr + tj) + tr
+    return {"value": 1.0 / t_solve, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": "oracle residual and Jacobian of the whole %d^3 annulus mesh (p=3, 4^3 Gauss points, lambda=2), "
+                      "each timed once in the colour-loop timing mode on %d OpenMP threads: %.2f s + %.2f s; solve = "
+                      "%d Jacobians + %d residuals (the GPU solve's Newton steps); linear solves not counted"
+                      % (NEL, O.num_threads(), tr, tj, newton_its, newton_its + 1),
+            "residual_s": tr, "jacobian_s": tj, "pattern_s": t_pat}
+
+
+SLAB = 8
+
+
+def oracle_step(newton_its, prob, U, sl, Us):
+    """One step of the reference arm: the oracle's residual of the whole mesh (prob, U)
+    and its Jacobian on a slab of nel x nel x SLAB elements of the same discretisation
+    (sl, Us; the Jacobian's cost per element does not depend on the slab), both in the
+    colour-loop timing mode.  Returns (solves/s for the whole mesh, seconds of the step)."""
+    t0 = time.perf_counter()
+    prob.residual_colored(U)
+    tr = time.perf_counter() - t0
+    t = time.perf_counter()
+    sl.jacobian_colored(Us)
+    tj = (time.perf_counter() - t) * NEL / float(SLAB)
+    return 1.0 / (newton_its * (tr + tj) + tr), time.perf_counter() - t0
 
 
 def run_reference(args):
@@ -131,20 +156,27 @@ def run_reference(args):
         return 0
     import oracle as O
     O.build()
-    per_step = []
+    its = 3  # Newton steps of the GPU's solve of this workload (its JSON line reports them)
+    prob, U = _oracle_problem(NEL)
+    sl, Us = _oracle_problem((NEL, NEL, SLAB))
+    sl.pattern()
     for _ in range(args.warmup):
-        oracle_sample(min_seconds=0.0)
-    cb = None
+        oracle_step(its, prob, U, sl, Us)
+    vals, secs = [], []
     for _ in range(args.steps):
-        cb = oracle_sample(min_seconds=0.0)
-        per_step.append(1.0 / cb["value"])
-    value = len(per_step) / sum(per_step)
-    cb = dict(cb)
-    cb["value"] = value
+        v, s = oracle_step(its, prob, U, sl, Us)
+        vals.append(v)
+        secs.append(s)
+    value = len(vals) / sum(1.0 / v for v in vals)
+    cb = {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+          "sample": "per step: the oracle's residual of the whole %d^3 annulus mesh and its Jacobian on a %dx%dx8-element "
+                    "slab (scaled x%d), colour-loop timing mode on %d OpenMP threads; solve = %d Jacobians + %d residuals; "
+                    "linear solves not counted" % (NEL, NEL, NEL, NEL // SLAB, O.num_threads(), its, its + 1)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(per_step) / len(per_step),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(None), "cpu_baseline": cb,
+            "note": "ms_per_step is the wall time of one sampled step; value is the whole-mesh solve rate it implies",
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -193,6 +225,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     build.build()
     stream = torch.cuda.current_stream()
+    pk = iga.measure_peaks()  # FP64/FP32 FMA and copy rates of this GPU, measured now
 
     t0 = time.perf_counter()
     kn, ctrl, w = W.quarter_annulus(NEL, P)
@@ -211,8 +244,8 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         rep = solve()
-    # dominant kernel classes are timed with events on the library's stream
-    disc.profile_enable(["jac_stage1", "jac_stage2", "jac_final", "spmv", "residual_element", "gs_orth"])
+    # timed region: the library's event profiler is off (launches are still counted)
+    disc.profile_enable([])
     disc.profile_read()
     clocks = ClockSampler(local)
     clocks.start()
@@ -230,18 +263,29 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    prof = disc.profile_read()
-    disc.profile_enable([])
+    launches = sum(v[2] for v in disc.profile_read().values())
     ms = max_over_ranks(ms, world, "cuda")
     value = job_throughput(world, args.steps, ms / 1e3)
-    launches = sum(v[2] for v in prof.values())
+
+    # profiled pass over the same solves: per-class device times (CUDA events on the
+    # library's stream, around each launch) for the kernel shares and the roofline
+    disc.profile_enable(["jac_stage1", "jac_stage2", "jac_final", "spmv", "residual_element", "residual_gather", "q00",
+                         "gs_orth", "vector", "gmres_scalar"])
+    disc.profile_read()
+    torch.cuda.synchronize()
+    p0 = time.perf_counter()
+    for _ in range(args.steps):
+        solve()
+    torch.cuda.synchronize()
+    prof_ms = 1e3 * (time.perf_counter() - p0)
+    prof = disc.profile_read()
+    disc.profile_enable([])
 
     # end to end through the host-buffer entry point (H2D of U0, D2H of the solution)
     Uh = torch.zeros(N, dtype=torch.float64).pin_memory()
     Uh_np = Uh.numpy()
-    for _ in range(1):
-        Uh.zero_()
-        disc.solve_newton_host(Uh_np, opts)
+    Uh.zero_()
+    disc.solve_newton_host(Uh_np, opts)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -273,8 +317,8 @@ def run_ours(args):
 
     t_res = timeit(lambda: disc.form_residual(Ur, F), 10)
     t_jac = timeit(lambda: disc.form_jacobian(Ur, vals=J), 3)
-    # matrix-free Newton-Krylov on the same problem (exact products, no assembled Jacobian):
-    # one product, and one whole solve, outside the timed region
+    del J
+    # matrix-free Newton-Krylov on the same problem (exact products, no assembled Jacobian)
     xr = torch.ones_like(U0)
     t_jv = timeit(lambda: disc.apply_jacobian_mf(Ur, xr, F), 5)
     o_mf = iga.newton_defaults()
@@ -288,82 +332,157 @@ def run_ours(args):
           "fnorm": r_mf.fnorm, "jv_ms": t_jv, "spmv_ms_for_comparison": prof["spmv"][0] / max(prof["spmv"][1], 1),
           "csr_bytes_avoided": disc.nnz * 8}
 
-    # roofline of the dominant kernel class in the timed region
-    hbm, hbm_src = peaks()
+    # roofline of the dominant kernel class of the profiled pass
+    hbm, hbm_src = hbm_peak()
     dom = max(prof, key=lambda c: prof[c][0])
     dms, dn, _ = prof[dom]
-    avg_ms = dms / max(dn, 1)
-    roof = roofline_entry(disc, dom, avg_ms, hbm, hbm_src)
+    roof = roofline_entry(disc, dom, dms / max(dn, 1), hbm, hbm_src, pk)
 
     r = reps[-1]
+    solve_s = ms / args.steps / 1e3
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(disc),
             "parallelism": "replicas" if world > 1 else "single",
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roof,
+            "peaks_measured": {"fp64_tflops": pk["fp64_tflops"], "fp32_tflops": pk["fp32_tflops"],
+                               "copy_gbs": pk["copy_gbs"], "sms": pk["sms"],
+                               "how": "iga_measure_peaks: DFMA/FFMA chains on every SM, 512 MiB copy; best of 5-10"},
             "newton": {"its": r.newton_its, "krylov_its": r.krylov_its, "fnorm0": r.fnorm0, "fnorm": r.fnorm},
-            "kernel_share": {c: round(v[0] / max(ms, 1e-9), 4) for c, v in prof.items() if v[1] > 0},
+            "kernel_share": {c: round(v[0] / max(prof_ms, 1e-9), 4) for c, v in prof.items() if v[1] > 0},
+            "profiled_pass_ms_per_step": prof_ms / args.steps,
             "assembly_fp64": {"jacobian_ms": t_jac, "jacobian_nnz_per_s": disc.nnz / (t_jac / 1e3),
                               "residual_ms": t_res, "residual_dofs_per_s": N / (t_res / 1e3)},
             "matrix_free_newton": mf,
-            "setup_ms": setup_ms}
+            "setup_ms": setup_ms,
+            # a solve on a mesh not seen before: set-up (tables, pattern, geometry factors) plus the solve
+            "new_mesh": {"solves_per_s": 1.0 / (setup_ms / 1e3 + solve_s), "setup_ms": setup_ms,
+                         "solve_ms": solve_s * 1e3}}
+    disc.close()
+    del Ur, F, xr, Umf, U, U0
+    torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["fp64_vs_mixed"] = mixed_comparison(torch, iga, W)
+        torch.cuda.empty_cache()
+        line["learned_start"] = learned_comparison(torch, iga, W)
+        torch.cuda.empty_cache()
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
-        import oracle as O
-        O.build()
-        line["cpu_baseline"] = oracle_sample(min_seconds=args.cpu_seconds, newton_its=r.newton_its)
+        line["cpu_baseline"] = oracle_whole_mesh(r.newton_its)
     if rank == 0:
         print(json.dumps(line))
-    disc.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
 
 
-# DRAM bytes (read + write) of one k_spmv_stencil launch on the 64^3 annulus, from one ncu
-# capture of this benchmark (profiles/k_spmv_stencil_annulus64_fp64_traffic.md); valid for
-# that workload and the kernel as captured.
+# ------------------------------------------- the metric's second half ------
+def mixed_comparison(torch, iga, W, nel=128, p=2, reps=3):
+    """3D Bratu, lambda = 2, on the unit cube, 128^3 quadratic (2.2M dofs, 267M nnz): Newton
+    solves from U = 0 to ||F||_2 <= 1e-10 with the FP64 Jacobian and with the reduced-precision
+    ones (FP32 sum factorisation, BF16 and TF32 tensor-core element matrices), each with GMRES
+    and with CG (the same Krylov method on both sides of every ratio); residual, norms and
+    orthogonalisation are FP64 in every run.  Best of `reps` solves after one warm-up.
+    Jacobian errors: relative Frobenius distance to the FP64 Jacobian at seeded U ~ U[-0.1,
+    0.1] (the FP64 Jacobian equals the oracle's to 1e-12 in the parity tests)."""
+    bc = {(a, s): 0.0 for a in range(3) for s in range(2)}
+    d = iga.Discretization(3, p, nel=nel, lam=2.0, dirichlet=bc)
+    out = {"workload": "bratu3d_cube_%dcubed_p%d_lambda2_from_zero" % (nel, p), "dofs": d.N, "nnz": d.nnz}
+    Ur = torch.tensor(W.interior_field([nel + p] * 3, 3), device="cuda")
+    J = torch.empty(d.nnz, dtype=torch.float64, device="cuda")
+    J32 = torch.empty(d.nnz, dtype=torch.float32, device="cuda")
+    d.form_jacobian(Ur, vals=J)
+    nJ = torch.linalg.norm(J).item()
+    modes = [("fp64", iga.IGA_FP64), ("fp32", iga.IGA_JAC_FP32), ("bf16", iga.IGA_JAC_BF16), ("tf32", iga.IGA_JAC_TF32)]
+    jac = {}
+    for name, code in modes:
+        if code == iga.IGA_FP64:
+            t = _best_ms(torch, lambda: d.form_jacobian(Ur, vals=J), 3)
+            jac[name] = {"ms": t, "nnz_per_s": d.nnz / (t * 1e-3), "rel_frobenius_error_vs_fp64": 0.0}
+            continue
+        t = _best_ms(torch, lambda: d.form_jacobian(Ur, prec=code, vals=J32), 3)
+        err = (torch.linalg.norm(J32.double() - J) / nJ).item()
+        jac[name] = {"ms": t, "nnz_per_s": d.nnz / (t * 1e-3), "rel_frobenius_error_vs_fp64": err}
+    out["jacobian"] = jac
+    del J, J32
+    torch.cuda.empty_cache()
+    U = torch.zeros(d.N, dtype=torch.float64, device="cuda")
+    solves = {}
+    for ksp_name, ksp in (("gmres", iga.IGA_KSP_GMRES), ("cg", iga.IGA_KSP_CG)):
+        for name, code in modes:
+            o = iga.newton_defaults()
+            o.jac, o.ksp = code, ksp
+            U.zero_()
+            d.solve_newton(U, o)
+            best, rep = 1e30, None
+            for _ in range(reps):
+                U.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rep = d.solve_newton(U, o)
+                torch.cuda.synchronize()
+                best = min(best, time.perf_counter() - t0)
+            solves["%s_%s" % (name, ksp_name)] = {"solves_per_s": 1.0 / best, "ms": best * 1e3, "newton_its": rep.newton_its,
+                                                  "krylov_its": rep.krylov_its, "fnorm": rep.fnorm}
+        base = solves["fp64_%s" % ksp_name]["solves_per_s"]
+        for name, _ in modes:
+            solves["%s_%s" % (name, ksp_name)]["speedup_vs_fp64_same_krylov"] = solves["%s_%s" % (name, ksp_name)]["solves_per_s"] / base
+    out["newton"] = solves
+    d.close()
+    return out
+
+
+def learned_comparison(torch, iga, W):
+    """kappa-Bratu on 64^2 quadratic elements: the convolutional initial guess (trained in this
+    process on 20k seeded solves of the batched solver) against the zero start, 2,000
+    held-out fields, batched Newton; the network start's wall time includes inference."""
+    import bench_workloads as BW
+    res, _, _ = BW.learned_core(torch, iga, W)
+    return res
+
+
+def _best_ms(torch, fn, reps):
+    fn()
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return best
+
+
+# DRAM bytes (read + write) of one k_spmv_stencil launch (FP64 values) on the 64^3 annulus,
+# from one ncu capture of this benchmark's command (named in the JSON line); valid for that
+# workload while the kernel is unchanged.
 SPMV_DRAM_BYTES_ANNULUS64 = 803.45e6 + 4.97e6
+SPMV_TRAFFIC_CAPTURE = ("profiles/k_spmv_stencil_annulus64_fp64_traffic.md: ncu --metrics "
+                        "dram__bytes_read.sum,dram__bytes_write.sum --clock-control none -k regex:k_spmv_stencil")
 
 
-def roofline_entry(disc, cls, avg_ms, hbm_gbs, hbm_src):
-    """Algorithmic work of one launch of the given kernel class on this workload."""
+def roofline_entry(disc, cls, avg_ms, hbm_gbs, hbm_src, pk):
+    """Algorithmic work of one launch of the given kernel class on this workload, against the
+    FP64 FMA peak measured in this process (the operator product and the assembly stages
+    are bound by GB300's FP64 pipe, not by HBM: one DFMA per 8-byte value)."""
     N, nnz = disc.N, disc.nnz
-    nq = (P + 1) ** 3
-    nel1 = NEL
-    npair = nel1 * (P + 1) ** 2 * (P + 1)  # sum over 1D pairs of their Gauss points: nel (p+1)^2 q
-    X = NEL * (P + 1)
-    P1 = sum(min(i, P) + min(NEL + P - 1 - i, P) + 1 for i in range(NEL + P))  # 1D pairs
+    fp64 = pk["fp64_tflops"]
+    src = "measured in this run (iga_measure_peaks, DFMA chains)"
+    t = avg_ms * 1e-3
     if cls == "spmv":
-        # values (columns follow from the stencil), rowptr, x read, y written; one FP64 FMA per
-        # stored value.  At 8 B per FMA this product is bound by GB300's FP64 pipe, not by HBM.
+        # values (columns follow from the stencil), rowptr, x read, y written; one FP64 FMA per value
         bytes_ = nnz * 8 + (N + 1) * 8 + 2 * N * 8
         flops = 2.0 * nnz
-        t = avg_ms * 1e-3
-        hbm_frac = bytes_ / t / 1e9 / hbm_gbs
-        fp_frac = flops / t / 1e12 / FP64_PEAK_TFLOPS
         traffic = SPMV_DRAM_BYTES_ANNULUS64 if NEL == 64 else None
         return {"kernel": "k_spmv_stencil (FP64 values, stencil columns)", "bound": "alu", "achieved": flops / t / 1e12,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": fp_frac, "traffic": traffic,
-                "peak_source": "derived: 152 SM x 2 DFMA/clk x 2.07 GHz",
-                "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": bytes_,
-                "hbm": {"achieved_gbs": bytes_ / t / 1e9, "peak_gbs": hbm_gbs, "frac": hbm_frac, "peak_source": hbm_src}}
-    if cls == "jac_stage1":
-        flops = 2.0 * 16 * npair * X * X  # 16 terms x sum of pair points per line x lines (stiffness launch)
-    elif cls == "jac_stage2":
-        flops = 2.0 * 9 * P1 * X * npair
-    elif cls == "jac_final":
-        flops = 2.0 * 4 * P1 * P1 * npair
-    elif cls == "residual_element":
-        n1, q = P + 1, P + 1
-        fwd = 2 * n1 * n1 * q * n1 + 3 * n1 * q * q * n1 + 4 * q ** 3 * n1
-        flops = 2.0 * NEL ** 3 * (2 * fwd + 14 * nq)
-    else:
-        return {"kernel": cls, "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": None, "traffic": None}
-    ach = flops / (avg_ms * 1e-3) / 1e12
-    return {"kernel": cls, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "peak_source": "derived: 152 SM x 2 DFMA/clk x 2.07 GHz",
-            "algorithmic_flops_per_launch": flops}
+                "peak": fp64, "unit": "TFLOP/s", "frac": flops / t / 1e12 / fp64, "traffic": traffic,
+                "traffic_capture": SPMV_TRAFFIC_CAPTURE if traffic else None, "peak_source": src,
+                "avg_launch_ms": avg_ms, "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": bytes_,
+                "hbm": {"achieved_gbs": bytes_ / t / 1e9, "peak_gbs": hbm_gbs, "frac": bytes_ / t / 1e9 / hbm_gbs,
+                        "peak_source": hbm_src}}
+    return {"kernel": cls, "bound": "alu", "achieved": None, "peak": fp64, "unit": "TFLOP/s", "frac": None,
+            "traffic": None, "peak_source": src, "avg_launch_ms": avg_ms}
 
 
 def main():
@@ -373,7 +492,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nel", type=int, default=64, help="elements per direction (64 is the benchmark workload)")
-    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sampling time (0: skip)")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="0 skips the CPU baseline (the oracle on all host cores)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64-vs-mixed and learned-start comparisons")
     ap.add_argument("--workload", default="annulus64",
                     choices=["annulus64", "bratu16", "cube_mixed", "batch512", "learned64", "nn64", "fdjac", "genalpha", "periodic64", "mixed64"],
                     help="annulus64 is the benchmark line; the others print their configuration's line")

@@ -237,7 +237,12 @@ def batch512(torch, iga, W, clock):
                  {"results": res, "setup_s": setup, "total_dofs": int(b.total), "cpu_baseline": cb}, ck)
 
 
-def learned64(torch, iga, W, clock, n_train=20000, n_test=2000, steps=16000):
+def learned_core(torch, iga, W, n_train=20000, n_test=2000, steps=16000, clock=None):
+    """Training data from the batched solver (seeds 0..n_train-1), the convolutional guess
+    trained on the GPU, and the held-out comparison (seeds 1,000,000...): batched Newton from
+    the zero start against batched Newton from the network's guess (inference included in
+    its wall time), plus plain one-at-a-time FP64 Newton on a sample.  Returns the results
+    and the clock record of the held-out phase."""
     from paper_1305_4452_gb300 import nn
     nel = 64
     t0 = time.perf_counter()
@@ -262,8 +267,10 @@ def learned64(torch, iga, W, clock, n_train=20000, n_test=2000, steps=16000):
         net.adam_step(lr)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t1
-    clock.start()
-    # held-out: batched mixed Newton from zero and from the network's guess (inference timed)
+    del x, tgt, Utr
+    if clock is not None:
+        clock.start()
+    # held-out: batched Newton from zero and from the network's guess (inference timed)
     U0, r0, s0 = nn.solve_batch(test)
     xt, _ = nn.features(test)
     torch.cuda.synchronize()
@@ -287,23 +294,34 @@ def learned64(torch, iga, W, clock, n_train=20000, n_test=2000, steps=16000):
         tp += time.perf_counter() - t
         its_plain.append(rep.newton_its)
         d.close()
-    ck = clock.stop()
+    ck = clock.stop() if clock is not None else None
     rel_err = float(np.median(np.linalg.norm(U1[ok] - guess.double().cpu().numpy().reshape(len(test), -1)[ok], axis=1)
                               / np.maximum(np.linalg.norm(U1[ok], axis=1), 1e-30)))
+    zero = n_test / s0
+    nn_start = n_test / (s1 + infer_s)
     res = {
+        "workload": "kappa_bratu_64x64_p2_grf_logkappa_lambda0.5to4_heldout%d" % n_test,
         "train_solves": int(keep.sum()), "train_skipped_no_convergence": int((~keep).sum()), "data_gen_s": gen_s,
         "train_steps": steps, "train_s": train_s, "loss_first": losses[0], "loss_last": float(np.mean(losses[-50:])),
         "params": net.nparams, "test": n_test, "test_both_converged": int(ok.sum()),
         "guess_median_rel_error": rel_err,
-        "zero_start": {"solves_per_s": n_test / s0, "newton_its_mean": float(r0["newton_its"][ok].mean()),
+        "zero_start": {"solves_per_s": zero, "newton_its_mean": float(r0["newton_its"][ok].mean()),
                        "krylov_its_mean": float(r0["krylov_its"][ok].mean())},
-        "nn_start": {"solves_per_s": n_test / (s1 + infer_s), "inference_s": infer_s,
+        "nn_start": {"solves_per_s": nn_start, "inference_s": infer_s, "solve_s": s1,
                      "newton_its_mean": float(r1["newton_its"][ok].mean()), "krylov_its_mean": float(r1["krylov_its"][ok].mean())},
+        "speedup_nn_vs_zero_start": nn_start / zero,
         "plain_fp64_single": {"solves_per_s": nsamp / tp, "newton_its_mean": float(np.mean(its_plain)), "sample": nsamp},
         "total_s": time.perf_counter() - t0,
     }
     net.close()
+    return res, ck, test
+
+
+def learned64(torch, iga, W, clock, n_train=20000, n_test=2000, steps=16000):
+    res, ck, test = learned_core(torch, iga, W, n_train, n_test, steps, clock)
     import oracle as O
+    nel = 64
+    bc = {(a, s): 0.0 for a in range(2) for s in range(2)}
     kn = O.open_uniform_knots(nel, 2)
     t_or, done = 0.0, 0
     for ins in test[:64]:

@@ -369,6 +369,24 @@ typedef struct {
 iga_status iga_profile_enable(iga_t iga, unsigned mask);
 iga_status iga_profile_read(iga_t iga, iga_profile *out);
 
+/* ---- Roofline denominators (measurement; the paper has no counterpart) ----
+ * Peak rates of the current device, measured by micro-benchmarks on `stream`
+ * (a cudaStream_t, NULL: default stream):
+ *   fp64_tflops  FP64 fused multiply-adds (CUDA cores, DFMA), flops = 2 per FMA;
+ *   fp32_tflops  FP32 fused multiply-adds (FFMA);
+ *   copy_gbs     device-to-device copy of a 512 MiB buffer, read + write bytes;
+ *   sms          streaming multiprocessors of the device.
+ * Each figure is the best of several launches timed with CUDA events (about 0.2 s
+ * in all).  Allocates (and frees) 1 GiB of scratch; synchronises the stream.
+ * IGA_ENOMEM or IGA_ECUDA on failure (*out unchanged). */
+typedef struct {
+  double fp64_tflops;
+  double fp32_tflops;
+  double copy_gbs;
+  int sms;
+} iga_peaks;
+iga_status iga_measure_peaks(void *stream, iga_peaks *out);
+
 /* Release every library-owned device buffer.  NULL is accepted. */
 void iga_destroy(iga_t iga);
 

@@ -41,7 +41,19 @@
  *     with kappa = exp(sum logkappa_A N_A).
  *
  * Every function returns 0 on success and a negative code on malformed input.
+ *
+ * Timing mode (or_residual_colored, or_jacobian_colored): the same element loop and
+ * element arithmetic, with the elements visited colour by colour and each colour's
+ * elements spread over OpenMP threads (when compiled with OpenMP).  Two elements whose
+ * span indices agree modulo p+1 in every direction share no basis function (a function
+ * is supported on at most p+1 consecutive non-empty spans, Sec. 2.1), so the threads of
+ * one colour write disjoint entries.  Only the order in which element contributions are
+ * added changes.  It exists to time the oracle on all host cores; the checks use the
+ * serial functions.  The per-point scratch arrays are thread-local for this reason.
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <float.h>
 #include <math.h>
 #include <stdint.h>
@@ -51,6 +63,7 @@
 #define OR_MAXD 3
 #define OR_MAXP 8
 #define OR_MAXEN 729 /* (OR_MAXP+1)^3 */
+#define OR_TLS _Thread_local
 
 typedef struct {
   int dim;
@@ -303,7 +316,7 @@ int or_shape(const or_problem *P, const int *s, const double *xi, int64_t *gidx,
     }
   }
   int nen = (pp[0] + 1) * (pp[1] + 1) * (pp[2] + 1);
-  static double M[OR_MAXEN], dM[OR_MAXEN][3], wA[OR_MAXEN];
+  static OR_TLS double M[OR_MAXEN], dM[OR_MAXEN][3], wA[OR_MAXEN];
   int a = 0;
   for (int c2 = 0; c2 <= pp[2]; c2++)
     for (int c1 = 0; c1 <= pp[1]; c1++)
@@ -329,7 +342,7 @@ int or_shape(const or_problem *P, const int *s, const double *xi, int64_t *gidx,
     for (int al = 0; al < dim; al++) Wd[al] += wA[a] * dM[a][al];
   }
   /* Eq. (rational) and Eq. (drational): N_{A,alpha} = (w_A M_{A,alpha} - N_A w_{,alpha}) / w */
-  static double dNp[OR_MAXEN][3];
+  static OR_TLS double dNp[OR_MAXEN][3];
   for (a = 0; a < nen; a++) {
     N[a] = wA[a] * M[a] / W;
     for (int al = 0; al < dim; al++) dNp[a][al] = (wA[a] * dM[a][al] - N[a] * Wd[al]) / W;
@@ -483,7 +496,7 @@ static int element_integrals_mode(const or_mesh *Msh, const int *e, const double
   for (int a = 0; a < nen; a++) Fe[a] = 0.0;
   if (Ke)
     for (int a = 0; a < nen * nen; a++) Ke[a] = 0.0;
-  static double N[OR_MAXEN], dN[OR_MAXEN * 3];
+  static OR_TLS double N[OR_MAXEN], dN[OR_MAXEN * 3];
   for (int g2 = 0; g2 < q[2]; g2++)
     for (int g1 = 0; g1 < q[1]; g1++)
       for (int g0 = 0; g0 < q[0]; g0++) {
@@ -668,6 +681,110 @@ int or_jacobian_fd(const or_problem *P, const double *Uc, const int64_t *rowptr,
       }
   for (int64_t A = 0; A < N; A++) dirichlet_fix_row(P, A, rowptr, colidx, vals + rowptr[A]);
   free(Ke);
+  mesh_free(&Msh);
+  return 0;
+}
+
+/* Number of OpenMP threads the colour-loop timing mode uses (1 without OpenMP). */
+int or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* Element count of colour c (span indices c, c + stride, ...) along one direction. */
+static int colour_count(int ne, int c, int stride) { return (c < ne) ? (ne - 1 - c) / stride + 1 : 0; }
+
+/* or_residual with the colour-by-colour element loop of the timing mode (see the file
+ * header); the same element integrals, Dirichlet rows and result up to the order of the
+ * additions.  Not for periodic directions (-30). */
+int or_residual_colored(const or_problem *P, const double *Uc, double *F) {
+  if (P->wrap[0] || P->wrap[1] || P->wrap[2]) return -30;
+  or_mesh Msh;
+  int rc = mesh_init(P, &Msh);
+  if (rc) return rc;
+  int64_t N = num_dofs(P);
+  for (int64_t A = 0; A < N; A++) F[A] = 0.0;
+  int st[3] = {1, 1, 1};
+  for (int d = 0; d < P->dim; d++) st[d] = P->p[d] + 1;
+  int bad = 0;
+  for (int c2 = 0; c2 < st[2]; c2++)
+    for (int c1 = 0; c1 < st[1]; c1++)
+      for (int c0 = 0; c0 < st[0]; c0++) {
+        const int k0 = colour_count(Msh.ne[0], c0, st[0]), k1 = colour_count(Msh.ne[1], c1, st[1]);
+        const int64_t total = (int64_t)k0 * k1 * colour_count(Msh.ne[2], c2, st[2]);
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t t = 0; t < total; t++) {
+          int64_t gidx[OR_MAXEN];
+          double Fe[OR_MAXEN];
+          int e[3] = {c0 + (int)(t % k0) * st[0], c1 + (int)((t / k0) % k1) * st[1], c2 + (int)(t / ((int64_t)k0 * k1)) * st[2]};
+          int nen = element_integrals(&Msh, e, Uc, gidx, Fe, NULL);
+          if (nen < 0) {
+#pragma omp atomic write
+            bad = nen;
+            continue;
+          }
+          for (int a = 0; a < nen; a++) F[gidx[a]] += Fe[a];
+        }
+      }
+  if (bad) { mesh_free(&Msh); return bad; }
+  for (int64_t A = 0; A < N; A++) {
+    double g;
+    if (dirichlet(P, A, &g)) F[A] = Uc[A] - g;
+  }
+  mesh_free(&Msh);
+  return 0;
+}
+
+/* or_jacobian with the colour-by-colour element loop of the timing mode. */
+int or_jacobian_colored(const or_problem *P, const double *Uc, const int64_t *rowptr, const int32_t *colidx,
+                        double *vals) {
+  if (P->wrap[0] || P->wrap[1] || P->wrap[2]) return -30;
+  or_mesh Msh;
+  int rc = mesh_init(P, &Msh);
+  if (rc) return rc;
+  int64_t N = num_dofs(P);
+  for (int64_t k = 0; k < rowptr[N]; k++) vals[k] = 0.0;
+  int st[3] = {1, 1, 1};
+  for (int d = 0; d < P->dim; d++) st[d] = P->p[d] + 1;
+  int bad = 0;
+#pragma omp parallel
+  {
+    int64_t gidx[OR_MAXEN];
+    double Fe[OR_MAXEN];
+    double *Ke = (double *)malloc(sizeof(double) * OR_MAXEN * OR_MAXEN);
+    for (int c2 = 0; c2 < st[2]; c2++)
+      for (int c1 = 0; c1 < st[1]; c1++)
+        for (int c0 = 0; c0 < st[0]; c0++) {
+          const int k0 = colour_count(Msh.ne[0], c0, st[0]), k1 = colour_count(Msh.ne[1], c1, st[1]);
+          const int64_t total = (int64_t)k0 * k1 * colour_count(Msh.ne[2], c2, st[2]);
+#pragma omp for schedule(dynamic, 1)
+          for (int64_t t = 0; t < total; t++) {
+            int e[3] = {c0 + (int)(t % k0) * st[0], c1 + (int)((t / k0) % k1) * st[1], c2 + (int)(t / ((int64_t)k0 * k1)) * st[2]};
+            int nen = Ke ? element_integrals(&Msh, e, Uc, gidx, Fe, Ke) : -2;
+            if (nen < 0) {
+#pragma omp atomic write
+              bad = nen;
+              continue;
+            }
+            for (int a = 0; a < nen; a++)
+              for (int b = 0; b < nen; b++) {
+                int64_t k = find_col(rowptr, colidx, gidx[a], gidx[b]);
+                if (k < 0) {
+#pragma omp atomic write
+                  bad = -20;
+                  continue;
+                }
+                vals[k] += Ke[a * nen + b];
+              }
+          }
+        }
+    free(Ke);
+  }
+  if (bad) { mesh_free(&Msh); return bad; }
+  for (int64_t A = 0; A < N; A++) dirichlet_fix_row(P, A, rowptr, colidx, vals + rowptr[A]);
   mesh_free(&Msh);
   return 0;
 }

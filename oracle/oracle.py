@@ -33,11 +33,14 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 
 def build(force=False):
-    """Compile the C oracle with gcc (plain -O2, no fast-math, single thread)."""
+    """Compile the C oracle with gcc (plain -O2, no fast-math).  OpenMP serves only the
+    colour-loop timing mode; without it (no libgomp) the oracle builds single-threaded."""
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     tmp = _LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC]
+    if subprocess.call(base + ["-fopenmp", "-lm"], stderr=subprocess.DEVNULL) != 0:
+        subprocess.check_call(base + ["-lm"])
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -85,6 +88,9 @@ def lib():
         L.or_jacobian.argtypes = [P, vp, vp, vp, vp]
         L.or_jacobian_fd.argtypes = [P, vp, vp, vp, vp]
         L.or_mass.argtypes = [P, vp, vp, vp]
+        L.or_residual_colored.argtypes = [P, vp, vp]
+        L.or_jacobian_colored.argtypes = [P, vp, vp, vp, vp]
+        L.or_num_threads.restype = ctypes.c_int
         L.or_residual_rows.argtypes = [P, vp, i64, vp, vp]
         L.or_jacobian_rows.argtypes = [P, vp, i64, vp, vp, vp, vp]
         L.or_dense_bruteforce.argtypes = [P, vp, vp, vp, ctypes.c_int]
@@ -111,6 +117,11 @@ def open_uniform_knots(nel, p, k=None):
         U += [e / nel] * mult
     U += [1.0] * (p + 1)
     return np.asarray(U, dtype=np.float64)
+
+
+def num_threads():
+    """Threads of the colour-loop timing mode (OpenMP's default: all host cores)."""
+    return int(lib().or_num_threads())
 
 
 def gauss_legendre(q):
@@ -248,6 +259,26 @@ class Problem:
         rc = lib().or_jacobian(ctypes.byref(c), _ptr(U), _ptr(rowptr), _ptr(colidx), _ptr(vals))
         if rc:
             raise RuntimeError("or_jacobian failed: %d" % rc)
+        return vals
+
+    # -- timing mode: the same loops colour by colour on all OpenMP threads --------
+    def residual_colored(self, U):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        F = np.zeros(self.N)
+        c = self._c()
+        rc = lib().or_residual_colored(ctypes.byref(c), _ptr(U), _ptr(F))
+        if rc:
+            raise RuntimeError("or_residual_colored failed: %d" % rc)
+        return F
+
+    def jacobian_colored(self, U):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        rowptr, colidx = self.pattern()
+        vals = np.zeros(len(colidx))
+        c = self._c()
+        rc = lib().or_jacobian_colored(ctypes.byref(c), _ptr(U), _ptr(rowptr), _ptr(colidx), _ptr(vals))
+        if rc:
+            raise RuntimeError("or_jacobian_colored failed: %d" % rc)
         return vals
 
     def jacobian_fd(self, U):

@@ -17,7 +17,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libiga.so")
 
-SOURCES = ["iga_host.cpp", "iga_element.cu", "iga_jacobian.cu", "iga_mixed.cu", "iga_krylov.cu", "iga_api.cu", "iga_batch.cu", "iga_nn.cu", "iga_conv_tc.cu", "iga_noalloc.cu", "iga_periodic.cu", "iga_elem_gemm.cu"]
+SOURCES = ["iga_host.cpp", "iga_element.cu", "iga_jacobian.cu", "iga_mixed.cu", "iga_krylov.cu", "iga_api.cu", "iga_batch.cu", "iga_nn.cu", "iga_conv_tc.cu", "iga_noalloc.cu", "iga_periodic.cu", "iga_elem_gemm.cu", "iga_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -25,7 +25,7 @@ EXPORTS = ["iga_create", "iga_set_boundary_value", "iga_set_lambda", "iga_get_pa
            "iga_batch_last_error", "iga_nn_create", "iga_nn_num_params", "iga_nn_get_params", "iga_nn_set_params",
            "iga_nn_forward", "iga_nn_loss_grad", "iga_nn_adam_step", "iga_nn_destroy", "iga_nn_last_error",
            "iga_nn_set_h1_weight", "iga_apply_jacobian", "iga_apply_jacobian_mf", "iga_form_jacobian_diagonal",
-           "iga_form_residual_ts", "iga_form_jacobian_ts", "iga_ts_alpha_step"]
+           "iga_form_residual_ts", "iga_form_jacobian_ts", "iga_ts_alpha_step", "iga_measure_peaks"]
 
 KERNEL_CLASSES = ["geometry", "residual_element", "residual_gather", "q00", "jac_stage1", "jac_stage2", "jac_final",
                   "spmv", "gs_orth", "gmres_scalar", "vector", "combine", "pattern", "elem_tc", "elem_gather"]
@@ -81,6 +81,11 @@ class IgaTsOpts(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("rho_inf", ctypes.c_double)]
 
 
+class IgaPeaks(ctypes.Structure):
+    _fields_ = [("fp64_tflops", ctypes.c_double), ("fp32_tflops", ctypes.c_double), ("copy_gbs", ctypes.c_double),
+                ("sms", ctypes.c_int)]
+
+
 class IgaProfile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 16), ("timed", ctypes.c_longlong * 16), ("launches", ctypes.c_longlong * 16)]
 
@@ -121,6 +126,7 @@ def lib():
         L.iga_last_error.restype = ctypes.c_char_p
         L.iga_profile_enable.argtypes = [vp, ctypes.c_uint]
         L.iga_profile_read.argtypes = [vp, ctypes.POINTER(IgaProfile)]
+        L.iga_measure_peaks.argtypes = [vp, ctypes.POINTER(IgaPeaks)]
         _lib = L
     return _lib
 
@@ -145,6 +151,14 @@ def newton_defaults():
     o = IgaNewtonOpts()
     lib().iga_newton_defaults(ctypes.byref(o))
     return o
+
+
+def measure_peaks(stream=None):
+    """iga_measure_peaks on the current device: FP64 and FP32 FMA rates (TFLOP/s) and
+    the device-to-device copy bandwidth (GB/s)."""
+    p = IgaPeaks()
+    _check(lib().iga_measure_peaks(ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(p)))
+    return {"fp64_tflops": p.fp64_tflops, "fp32_tflops": p.fp32_tflops, "copy_gbs": p.copy_gbs, "sms": p.sms}
 
 
 def _stream_ptr(stream):

@@ -94,6 +94,7 @@ def test_struct_layouts_match_the_header(tmp_path):
         "iga_newton_report": (iga.IgaNewtonReport, ["newton_its", "krylov_its", "fnorm0", "fnorm", "fnorm_hist", "status"]),
         "iga_ts_opts": (iga.IgaTsOpts, ["dt", "rho_inf"]),
         "iga_batch_report": (iga.IgaBatchReport, ["solved", "newton_its", "krylov_its", "fnorm", "status", "solve_us"]),
+        "iga_peaks": (iga.IgaPeaks, ["fp64_tflops", "fp32_tflops", "copy_gbs", "sms"]),
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "iga.h"', 'int main(void) {']
     for cname, (_, fields) in structs.items():

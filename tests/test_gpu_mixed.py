@@ -17,8 +17,20 @@ from paper_1305_4452_gb300 import workloads as W
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-# relative Frobenius error bounds: ~10x the unit roundoff of the operand type
-FRO_TOL = {"bf16": 2e-2, "tf32": 5e-3}
+# Relative Frobenius error bounds per case, about 3x the errors these deterministic
+# kernels give on GB300 (measured: in the comments), so that a change that made an
+# error a few times larger fails.  For scale: the unit roundoff is 2^-9 = 2.0e-3 for
+# BF16 and 2^-11 = 4.9e-4 for TF32; the split constant operand (a rounded part plus its
+# rounded remainder) takes most cases far below it.
+FRO_TOL = {"bf16": 2e-3, "tf32": 3e-4}   # the loosest case of each type (3D p = 1, non-uniform knots)
+CASE_TOL = {  # case id -> (bf16, tf32)
+    "d2p2_16_None_False": (3e-4, 4e-5),            # measured 1.08e-4, 1.23e-5
+    "d2p3_(9, 7)_None_False": (5e-4, 2.5e-4),      # 1.80e-4, 7.66e-5
+    "d2p2_(12, 10)_None_True": (1.2e-3, 1.5e-4),   # 3.77e-4, 4.77e-5 (kappa field)
+    "d3p2_(6, 5, 4)_None_False": (2.5e-4, 4e-5),   # 7.50e-5, 1.37e-5
+    "d3p3_(5, 4, 4)_annulus_False": (1.5e-4, 2e-5),  # 4.82e-5, 6.52e-6
+    "d3p1_(5, 4, 3)_None_False": (4e-3, 3e-4),     # 1.22e-3, 8.73e-5 (p = 1: no split operand)
+}
 
 
 @pytest.fixture(scope="module")
@@ -68,7 +80,7 @@ def test_mixed_jacobian_error_and_exact_structure(I, case, prec):
     Jm = Jm.double().cpu().numpy()
     Jo = prob.jacobian(U0)
     err = np.linalg.norm(Jm - Jo) / np.linalg.norm(Jo)
-    assert err < FRO_TOL[prec], err
+    assert err < CASE_TOL["d%dp%d_%s_%s_%s" % case][0 if prec == "bf16" else 1], err
     # Dirichlet rows/columns are exact
     rowptr, colidx = prob.pattern()
     mask = prob.dirichlet_mask()
@@ -120,7 +132,7 @@ def test_bf16_element_gemm_quartic_3d(I):
     U0 = W.interior_field(n, seed=5, lo=-0.3, hi=0.3)
     Jm = disc.form_jacobian(torch.tensor(U0, device="cuda"), prec=I.IGA_JAC_BF16).double().cpu().numpy()
     Jo = prob.jacobian(U0)
-    assert np.linalg.norm(Jm - Jo) / np.linalg.norm(Jo) < FRO_TOL["bf16"]
+    assert np.linalg.norm(Jm - Jo) / np.linalg.norm(Jo) < 1.5e-4  # measured 4.34e-5
     disc.close()
 
 
@@ -140,7 +152,7 @@ def test_nonuniform_knots_use_the_per_element_contraction(I, prec):
     code = I.IGA_JAC_BF16 if prec == "bf16" else I.IGA_JAC_TF32
     Jm = disc.form_jacobian(torch.tensor(U0, device="cuda"), prec=code).double().cpu().numpy()
     Jo = prob.jacobian(U0)
-    assert np.linalg.norm(Jm - Jo) / np.linalg.norm(Jo) < FRO_TOL[prec]
+    assert np.linalg.norm(Jm - Jo) / np.linalg.norm(Jo) < FRO_TOL[prec]  # measured 7.44e-4, 1.01e-4
     disc.close()
 
 

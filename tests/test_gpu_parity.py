@@ -85,7 +85,8 @@ def make_pair(dim, p, nel, lam=1.0, k=None, geom=None, kappa_seed=None, bc=True,
     n = [len(kk) - p - 1 for kk in knots]
     lk = None
     if kappa_seed is not None:
-        lk = W.grf_log_kappa(n, p, nel, kappa_seed) if dim == 2 else W.uniform(kappa_seed, int(np.prod(n)), -0.5, 0.5)
+        grf = dim == 2 and geom not in ("graded", "graded_nurbs")  # the field generator assumes uniform knots
+        lk = W.grf_log_kappa(n, p, nel, kappa_seed) if grf else W.uniform(kappa_seed, int(np.prod(n)), -0.5, 0.5)
     if dirichlet is None:
         dirichlet = bc_all(dim) if bc else None
     disc = I.Discretization(dim, p, knots=knots, ctrl=ctrl, weights=weights, lam=lam, log_kappa=lk, dirichlet=dirichlet)
@@ -297,7 +298,7 @@ def test_full_size_cube_48_cubed_quartic_sampled():
     del J
     Jb = disc.form_jacobian(U, prec=I.IGA_JAC_BF16)
     Jbg = np.concatenate([Jb[rpo[r]:rpo[r + 1]].double().cpu().numpy() for r in rows])
-    assert np.linalg.norm(Jbg - Jo) <= 2e-2 * np.linalg.norm(Jo)
+    assert np.linalg.norm(Jbg - Jo) <= 1.5e-5 * np.linalg.norm(Jo)  # measured 3.6e-6
     disc.close()
 
 
@@ -314,7 +315,7 @@ def test_full_size_cube_128_cubed_bf16_element_gemm_sampled():
     rpo, _ = prob.pattern()
     Jbg = np.concatenate([Jb[rpo[r]:rpo[r + 1]].double().cpu().numpy() for r in rows])
     Jo = prob.jacobian_rows(U0, rows)
-    assert np.linalg.norm(Jbg - Jo) <= 2e-2 * np.linalg.norm(Jo)
+    assert np.linalg.norm(Jbg - Jo) <= 2e-5 * np.linalg.norm(Jo)  # measured 6.5e-6
     disc.close()
 
 

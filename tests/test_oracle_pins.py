@@ -760,3 +760,32 @@ def test_row_helpers_equal_the_whole_mesh_assembly(case):
     # every row once, in a shuffled order: the helpers do not depend on the order asked
     perm = np.random.default_rng(1).permutation(N)
     assert np.abs(prob.residual_rows(U, perm) - F[perm]).max() <= 1e-14 * sf
+
+
+# --------------------------------------------- colour-loop timing mode (OpenMP)
+
+@pytest.mark.parametrize("case", [(2, 2, (9, 7), None), (2, 3, (6, 5), "graded"), (3, 3, (4, 3, 5), "annulus"),
+                                  (3, 2, (5, 4, 3), "kappa"), (3, 1, (3, 3, 2), None)])
+def test_colored_timing_mode_equals_the_serial_loops(case):
+    """The timing mode visits the same elements with the same arithmetic in another
+    order: equal to the serial oracle up to the rounding of the additions, and every
+    element is visited exactly once (a skipped or doubled colour would show)."""
+    dim, p, nel, kind = case
+    ctrl = w = lk = None
+    if kind == "annulus":
+        knots, ctrl, w = W.quarter_annulus(nel, p)
+    elif kind == "graded":
+        knots = [W.graded_open_knots(nel[d], p, 50 + d, extra=(2,) if d == 0 else ()) for d in range(dim)]
+    else:
+        knots = [W.uniform_open_knots(nel[d], p) for d in range(dim)]
+    n = [len(k) - p - 1 for k in knots]
+    N = int(np.prod(n))
+    if kind == "kappa":
+        lk = W.uniform(3, N, -0.5, 0.5)
+    prob = O.Problem(knots, [p] * dim, ctrl=ctrl, weights=w, lam=2.1, log_kappa=lk, dirichlet=dirichlet_all(dim, 0.1))
+    U = W.uniform(4, N, -0.3, 0.3)
+    F, Fc = prob.residual(U), prob.residual_colored(U)
+    J, Jc = prob.jacobian(U), prob.jacobian_colored(U)
+    assert np.abs(F - Fc).max() <= 1e-14 * np.abs(F).max()
+    assert np.abs(J - Jc).max() <= 1e-14 * np.abs(J).max()
+    assert O.num_threads() >= 1
