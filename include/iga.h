@@ -131,6 +131,20 @@ iga_status iga_create(const iga_desc *desc, const iga_bratu *bratu, void *stream
  * axis 1 side 0, ...) gives the value.  A periodic axis has no faces: IGA_EINVAL. */
 iga_status iga_set_boundary_value(iga_t iga, int axis, int side, double value);
 
+/* Failure detection of the tensor-core Jacobian (a library facility; the paper has no
+ * counterpart).  Every wait of its pipeline on a shared-memory barrier is bounded: after
+ * `seconds` (default 2; accepted range (0, 60]) the kernel stops issuing copies and
+ * tensor-core operations, waits at most 2 s more for those it has issued, frees its
+ * tensor memory and returns, and the call (iga_form_jacobian, iga_solve_newton) reports
+ * IGA_ETIMEOUT.  The handle stays usable; the next call runs normally. */
+iga_status iga_set_wait_limit(iga_t iga, double seconds);
+
+/* Test hook of that path: the next BF16/TF32 element-GEMM Jacobian on this handle waits
+ * once, before issuing any work, on a barrier phase that nothing completes, so the wait
+ * gives up after the limit and the call returns IGA_ETIMEOUT.  Later calls are unaffected.
+ * Faults nothing: the give-up is the bounded wait's normal exit. */
+iga_status iga_inject_stall(iga_t iga);
+
 /* Change lambda after creation (used by the batched and learned-start drivers). */
 iga_status iga_set_lambda(iga_t iga, double lambda);
 
@@ -170,7 +184,9 @@ iga_status iga_form_residual_noalloc(iga_t iga, const double *U, double *F);
 /* Jacobian J(U) of Eq. (jacobian) into CSR values on the library's pattern.
  * vals: device memory, caller-owned, nnz entries of double (IGA_FP64, IGA_JAC_FD) or
  * float (IGA_JAC_TF32, IGA_JAC_BF16, IGA_JAC_FP32).  IGA_JAC_NONE is not a format:
- * IGA_EINVAL. */
+ * IGA_EINVAL.  IGA_JAC_TF32 / IGA_JAC_BF16 synchronise the stream at the end to read the
+ * tensor-core pipeline's give-up flag: IGA_ETIMEOUT (the values are then invalid) when
+ * a bounded wait gave up (see iga_set_wait_limit). */
 iga_status iga_form_jacobian(iga_t iga, const double *U, void *vals, iga_precision prec);
 
 /* y = J x for CSR values on the library's pattern (the operator product of the

@@ -44,7 +44,7 @@ void iga_release(iga_s *h) {
   for (int ax = 0; ax < 3; ax++) free_dir(h->ddev[ax]);
   void *ps[] = {h->rowptr, h->rp_line, h->rp_p0, h->colidx, h->weights, h->geom, h->Fe, h->Q00, h->T1, h->T2, h->Kstiff, h->Kstiff_f, h->Ebuf64, h->ts_buf,
                 h->Mred, h->Mred_f, h->J64, h->J32, h->wk, h->V, h->red, h->ctl, h->Uhost_dev,
-                h->geom32, h->tab32[0], h->tab32[1], h->tab32[2], h->Ebuf, h->z32};
+                h->geom32, h->tab32[0], h->tab32[1], h->tab32[2], h->Ebuf, h->z32, h->gsbar};
   for (void *p : ps)
     if (p) cudaFree(p);
   if (h->ctl_host) cudaFreeHost(h->ctl_host);
@@ -230,6 +230,22 @@ extern "C" iga_status iga_set_boundary_value(iga_t h, int axis, int side, double
   return IGA_OK;
 }
 
+extern "C" iga_status iga_set_wait_limit(iga_t h, double seconds) {
+  if (!h) return IGA_EINVAL;
+  if (!(seconds > 0.0) || seconds > 60.0) {
+    h->err = "the wait limit must be in (0, 60] seconds";
+    return IGA_EINVAL;
+  }
+  h->wait_limit_ns = (uint64_t)(seconds * 1e9);
+  return IGA_OK;
+}
+
+extern "C" iga_status iga_inject_stall(iga_t h) {
+  if (!h) return IGA_EINVAL;
+  h->stall_next = true;
+  return IGA_OK;
+}
+
 extern "C" iga_status iga_set_lambda(iga_t h, double lambda) {
   if (!h || !isfinite(lambda)) return IGA_EINVAL;
   h->lambda = lambda;
@@ -275,7 +291,13 @@ extern "C" iga_status iga_form_jacobian(iga_t h, const double *U, void *vals, ig
       return IGA_EINVAL;
     }
     if (prec == IGA_JAC_FD) CK(launch_jacobian_fd(h, U, (double *)vals));
-    else CK(launch_jacobian_mixed(h, U, (float *)vals, (int)prec));
+    else {
+      CK(launch_jacobian_mixed(h, U, (float *)vals, (int)prec));
+      if (elem_gemm_failed(h)) {
+        h->err = "a tensor-core pipeline wait gave up; the Jacobian values are invalid";
+        return IGA_ETIMEOUT;
+      }
+    }
   } else {
     h->err = "unknown precision";
     return IGA_EINVAL;
@@ -358,6 +380,10 @@ static iga_status ensure_workspace(iga_s *h, int m, bool f32, bool mf = false) {
   const int64_t N = h->N;
   if (!h->wk) CK(cudaMalloc((void **)&h->wk, (size_t)(8 * N + 64 + 2 * 1025) * sizeof(double)));
   if (!h->ctl_host) CK(cudaMallocHost((void **)&h->ctl_host, 16 * sizeof(double)));
+  if (!h->gsbar) {
+    CK(cudaMalloc((void **)&h->gsbar, 2 * sizeof(unsigned)));
+    CK(cudaMemsetAsync(h->gsbar, 0, 2 * sizeof(unsigned), h->stream));
+  }
   if (h->V_m != m) {
     if (h->V) cudaFree(h->V);
     if (h->red) cudaFree(h->red);
@@ -394,6 +420,10 @@ static iga_status newton_jacobian(iga_s *h, const double *U, bool f32, bool reus
   }
   if (f32 && prec != IGA_JAC_FP32) {  // tensor-core element matrices, assembled in full each step
     CK(launch_jacobian_mixed(h, U, h->J32, prec));
+    if (elem_gemm_failed(h)) {
+      h->err = "a tensor-core pipeline wait gave up";
+      return IGA_ETIMEOUT;
+    }
     return IGA_OK;
   }
   if (!reuse) {
@@ -489,8 +519,10 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
     // Newton tolerance: a linear residual under atol/2 already lets the step meet atol
     double rtol = o.krylov_rtol < fn ? o.krylov_rtol : fn;
     // with a reduced-precision Jacobian (and FP32 operator products) a linear solve
-    // tighter than the Jacobian's own error buys nothing
-    if (f32 && rtol < 1e-4) rtol = 1e-4;
+    // tighter than the Jacobian's own error buys nothing: the floor is about 20-50 times
+    // the relative Frobenius error of each type (BF16 ~2e-5, TF32 ~5e-6, FP32 ~3e-9)
+    const double floor_rtol = !f32 ? 0.0 : (o.jac == IGA_JAC_BF16 ? 1e-4 : (o.jac == IGA_JAC_TF32 ? 1e-6 : 1e-8));
+    if (rtol < floor_rtol) rtol = floor_rtol;
     double tol_abs = rtol * fn;
     if (tol_abs < 0.5 * o.atol) tol_abs = 0.5 * o.atol;
     if (tol_abs < 1e-14 * fn) tol_abs = 1e-14 * fn;
@@ -503,6 +535,10 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
     if (grc < 0) {
       h->err = iga_format("GMRES: %s", cudaGetErrorString(ce));
       return IGA_ECUDA;
+    }
+    if (grc == 3) {
+      h->err = "GMRES: a grid barrier of the fused orthogonalisation gave up";
+      return IGA_ETIMEOUT;
     }
     R.krylov_its += its;
     // backtracking on ||F||: halve the step until the norm decreases

@@ -94,6 +94,8 @@ struct GemmArgs {
   int dim, p, nq, nsym, nen, Kp, n_tiles, m_tiles, general;
   int split;  // 1: T = T_hi + T_lo, both in the operand type (two MMAs per chunk on the same Qv)
   int *err;
+  uint64_t limit_ns;  // bound of each pipeline wait (the drain after a stop keeps MBAR_LIMIT_NS)
+  int stall;          // failure-detection test: wait once on a barrier phase that nothing completes
 };
 
 __device__ __forceinline__ uint32_t op_bits(float x, int op) {
@@ -262,10 +264,17 @@ __global__ void __launch_bounds__(256) k_elem_gemm(GemmArgs g) {
     for (int kc = half * 4; kc < half * 4 + 4; kc++) cp16(adst + kc * LBO, qr + kc * 16, true);
     cp_commit();
   };
+  // failure-detection test: barrier 1's first phase completes only at the first commit to
+  // stage 1, which never comes before this wait, so the wait gives up after limit_ns and the
+  // kernel stops before it has issued any copy or MMA
+  if (g.stall) {
+    if (tid == 0 && !mbar_wait(su32(done + 1), 0, abort_s, 0, g.limit_ns)) *abort_s = 1;
+    __syncthreads();
+  }
   // two stages in flight: the copy of the next chunk (the next m-tile's first chunk after a
   // tile's last) is issued before the wait for the current one, and runs during the MMAs and
   // the epilogue
-  if (m_count > 0) issue(m_first, 0, 0);
+  if (m_count > 0 && !*abort_s) issue(m_first, 0, 0);
   for (int mi = 0; mi < m_count && !*abort_s; mi++) {
     const int mt = m_first + mi;
     for (int c = 0; c < nchunks; c++, it++) {
@@ -273,7 +282,7 @@ __global__ void __launch_bounds__(256) k_elem_gemm(GemmArgs g) {
       if ((c + 1 < nchunks) || (mi + 1 < m_count)) {
         // the other stage is free once the MMAs of chunk it - 1, which read it, are complete
         if (it >= 1) {
-          if (tid == 0 && !mbar_wait(su32(done + (st ^ 1)), ((it - 1) >> 1) & 1, abort_s)) *abort_s = 1;
+          if (tid == 0 && !mbar_wait(su32(done + (st ^ 1)), ((it - 1) >> 1) & 1, abort_s, 0, g.limit_ns)) *abort_s = 1;
           __syncthreads();
           if (*abort_s) break;
         }
@@ -313,7 +322,7 @@ __global__ void __launch_bounds__(256) k_elem_gemm(GemmArgs g) {
     }
     if (*abort_s) break;
     // this m-tile's accumulator is complete once its last commit has arrived
-    if (tid == 0 && !mbar_wait(su32(done + ((it - 1) & 1)), ((it - 1) >> 1) & 1, abort_s)) *abort_s = 1;
+    if (tid == 0 && !mbar_wait(su32(done + ((it - 1) & 1)), ((it - 1) >> 1) & 1, abort_s, 0, g.limit_ns)) *abort_s = 1;
     __syncthreads();
     if (*abort_s) break;
     tc_fence_after();
@@ -792,6 +801,8 @@ cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, in
   g.m_tiles = P->m_tiles;
   g.general = P->general;
   g.err = P->err;
+  g.limit_ns = h->wait_limit_ns;
+  g.stall = 0;
   const int nch = P->Kp * (op == EG_BF16 ? 2 : 4) / KB;
   g.split = eg_smem(nch, 1) <= 200 * 1024 ? 1 : 0;
   const size_t smem = eg_smem(nch, g.split);
@@ -818,6 +829,8 @@ cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, in
     }
   }
   g.Tc = P->Tc[op];
+  g.stall = h->stall_next ? 1 : 0;
+  h->stall_next = false;
   const unsigned grid = (unsigned)((int64_t)P->ngroups * P->n_tiles);
   if (op == EG_BF16) {
     IGA_LAUNCH(h, KC_ELEM_TC, (k_elem_gemm<EG_BF16><<<grid, 256, smem, h->stream>>>(g)));
@@ -838,10 +851,16 @@ cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, in
   return cudaGetLastError();
 }
 
-// Error flag of the element GEMM (a barrier wait that timed out); reading it synchronises.
+// Error flag of the element GEMM (a pipeline wait that gave up): read on the handle's
+// stream (which this synchronises) and cleared for the next launch.
 bool elem_gemm_failed(iga_s *h) {
   if (!h->egemm || !h->egemm->err) return false;
   int v = 0;
-  cudaMemcpy(&v, h->egemm->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (cudaMemcpyAsync(&v, h->egemm->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return false;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return false;
+  if (v) {
+    cudaMemsetAsync(h->egemm->err, 0, sizeof(int), h->stream);
+    cudaStreamSynchronize(h->stream);
+  }
   return v != 0;
 }

@@ -213,6 +213,8 @@ struct iga_s {
   double *Ebuf64 = nullptr;    // [nelem][nen][nen] FP64 element matrices (local numerical differentiation)
   float *z32 = nullptr;        // FP32 copy of the Krylov vector for the FP32 SpMV
   ElemGemmPlan *egemm = nullptr;  // element matrices as one GEMM across elements (iga_elem_gemm.cu)
+  uint64_t wait_limit_ns = 2000000000ull;  // bound of each pipeline wait of the tensor-core kernels
+  bool stall_next = false;     // failure-detection test: the next element GEMM waits on a barrier nothing completes
   // Newton / Krylov workspace
   double *J64 = nullptr;
   float *J32 = nullptr;
@@ -222,6 +224,7 @@ struct iga_s {
   double *red = nullptr;       // reduction partials
   double *ctl = nullptr;       // GMRES scalar control block (device)
   double *ctl_host = nullptr;  // pinned mirror
+  unsigned *gsbar = nullptr;   // grid barrier of the fused orthogonalisation (count, generation)
   int nblk_red = 0;
 };
 

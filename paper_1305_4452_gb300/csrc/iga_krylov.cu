@@ -8,6 +8,8 @@
 // order, so results do not depend on scheduling.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "iga_internal.h"
@@ -135,6 +137,53 @@ __global__ void __launch_bounds__(256) k_spmv_stencil(StencilRows S, const int64
   if (row < N && lane == 0) y[row] = (double)acc;
 }
 
+// y = A x with FP32 values and FP32 x, FP32 products and sums (the operator of the
+// reduced-precision Newton), one warp per row: lane t reads the 16-byte word t of the row
+// (the row's span rounded out to 16-byte words, so that every load is one aligned vector),
+// i.e. 128 values per warp and step, and forms the columns of its four entries from their
+// positions (e -> (e mod w0, (e / w0) mod w1, e / (w0 w1)), the quotients exact in FP32
+// for e < 2^12).  The tree over the lanes is in a fixed order.  Values outside the row,
+// and the words past the end of the array, are not used.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_spmv32_warp(StencilRows S, const int64_t *__restrict__ rowptr,
+                                                     const float *__restrict__ val, const float *__restrict__ x,
+                                                     double *__restrict__ y, int N, int64_t nnz,
+                                                     const double *__restrict__ done) {
+  if (done && done[0] != 0.0) return;
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5, stride = gridDim.x * wpb;
+  for (int row = blockIdx.x * wpb + (threadIdx.x >> 5); row < N; row += stride) {
+    const RowShape R = row_shape<DIM>(S, row);
+    const int64_t s = rowptr[row], t = rowptr[row + 1];
+    const float inv0 = 1.f / (float)R.w0, inv01 = 1.f / (float)(R.w0 * R.w1);
+    const int base_col = R.lo0 + R.lo1 * S.n0 + R.lo2 * S.n01;
+    float acc = 0.f;
+    for (int64_t b = (s & ~(int64_t)3) + 4 * lane; b < t; b += 128) {
+      float v[4];
+      if (b + 4 <= nnz) {
+        const float4 q = __ldcs(reinterpret_cast<const float4 *>(val + b));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; j++) v[j] = (b + j < nnz) ? val[b + j] : 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const int e = (int)(b + j - s);
+        if (e < 0 || b + j >= t) continue;
+        const int k = (int)(((float)e + 0.5f) * inv01);
+        const int r = e - k * R.w0 * R.w1;
+        const int jj = (int)(((float)r + 0.5f) * inv0);
+        const int ii = r - jj * R.w0;
+        acc = fmaf(v[j], __ldg(x + base_col + ii + jj * S.n0 + k * S.n01), acc);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[row] = (double)acc;
+  }
+}
+
 __global__ void k_cvt_f32(const double *__restrict__ x, float *__restrict__ y, int64_t N, const double *__restrict__ done) {
   if (done && done[0] != 0.0) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) y[i] = (float)x[i];
@@ -214,6 +263,43 @@ __device__ void block_sum_cols(const double *__restrict__ partial, int nb, int n
   __syncthreads();
 }
 
+// partial[i * gridDim.x + blockIdx.x] = sum over the block's rows r < cnt of V[i][a + r] ws[r],
+// i < jp1: items (column i, row chunk c), R chunks per column so that the warps are busy
+// even for few columns; chunk sums in shared memory (dp, one per warp), then per column in
+// order.  ws holds the block's rows of w; all threads of the block take part.
+__device__ void block_dots(const double *__restrict__ Vb, int64_t ld, int jp1, int64_t a, int cnt, const double *ws,
+                           double *dp, double *__restrict__ partial) {
+  const int T = blockDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
+  const int R = jp1 >= nw ? 1 : nw / jp1;
+  const int items = jp1 * R, clen = (cnt + R - 1) / R;
+  for (int base = 0; base < items; base += nw) {
+    const int it = base + warp;
+    if (it < items) {
+      const int i = it / R, c = it - i * R;
+      const int r0 = c * clen, r1 = min(cnt, r0 + clen);
+      const double *v = Vb + (size_t)i * ld + a;
+      double acc = 0.0;
+#pragma unroll 4
+      for (int r = r0 + lane; r < r1; r += 32) acc = fma(v[r], ws[r], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) dp[warp] = acc;
+    }
+    __syncthreads();
+    // columns completed in this round: items [base, base + nw)
+    if (threadIdx.x < nw) {
+      const int it0 = base + threadIdx.x;
+      if (it0 < items && (it0 % R) == 0) {
+        const int i = it0 / R;
+        double acc = 0.0;
+        for (int c = 0; c < R; c++) acc += dp[threadIdx.x + c];
+        partial[(size_t)i * gridDim.x + blockIdx.x] = acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <int PASS>
 __global__ void __launch_bounds__(GS_THREADS) k_gs_pass(const double *__restrict__ Vb, int64_t ld, int jp1,
                                                         const double *__restrict__ prev, double *__restrict__ Hj,
@@ -264,36 +350,7 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_pass(const double *__restrict
     return;
   }
   __syncthreads();
-  // dots: items (column i, row chunk c), R chunks per column so that the warps are
-  // busy even for few columns; chunk sums in shared memory, then per column in order
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
-  const int R = jp1 >= nw ? 1 : nw / jp1;
-  const int items = jp1 * R, clen = (cnt + R - 1) / R;
-  for (int base = 0; base < items; base += nw) {
-    const int it = base + warp;
-    if (it < items) {
-      const int i = it / R, c = it - i * R;
-      const int r0 = c * clen, r1 = min(cnt, r0 + clen);
-      const double *v = Vb + (size_t)i * ld + a;
-      double acc = 0.0;
-#pragma unroll 4
-      for (int r = r0 + lane; r < r1; r += 32) acc = fma(v[r], ws[r], acc);
-      acc = warp_sum(acc);
-      if (lane == 0) dp[warp] = acc;
-    }
-    __syncthreads();
-    // columns completed in this round: items [base, base + nw)
-    if (threadIdx.x < nw) {
-      const int it0 = base + threadIdx.x;
-      if (it0 < items && (it0 % R) == 0) {
-        const int i = it0 / R;
-        double acc = 0.0;
-        for (int c = 0; c < R; c++) acc += dp[threadIdx.x + c];
-        partial[(size_t)i * gridDim.x + blockIdx.x] = acc;
-      }
-    }
-    __syncthreads();
-  }
+  block_dots(Vb, ld, jp1, a, cnt, ws, dp, partial);
 }
 
 // v_next = w / hnorm ; z = dinv .* v_next   (skipped on breakdown)
@@ -391,6 +448,167 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_finish(const double *__restri
   }
 }
 
+// ---- one Arnoldi orthogonalisation in a single cooperative launch ----
+// Flag slots of the GMRES scalar block used by the fused kernel: 6 = a grid barrier gave
+// up (the solve reports IGA_ETIMEOUT).
+constexpr int GS_FLAG_TIMEOUT = 6;
+constexpr unsigned long long GS_BARRIER_NS = 1000000000ull;  // 1 s: far above any phase
+
+__device__ __forceinline__ unsigned long long gs_gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Barrier over the blocks of a cooperative launch (all resident): bar[0] counts the
+// arrivals, bar[1] is the generation; the last block to arrive resets the count and
+// advances the generation, the others wait for that (at most GS_BARRIER_NS, then false).
+// Every block's writes before the barrier are visible to every block after it.
+__device__ bool gs_grid_sync(unsigned *bar) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = gs_gtimer();
+      for (unsigned i = 1; *vgen == gen; i++)
+        if ((i & 255) == 0 && gs_gtimer() - t0 > GS_BARRIER_NS) {
+          ok = 0;
+          break;
+        }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// The three Gram-Schmidt passes and the end of the iteration (k_gs_pass<1..3> and
+// k_gs_finish) as one kernel: classical Gram-Schmidt applied twice to w = A z_j against
+// V_0..V_j, the new column of H, v_{j+1} = w / ||w||, z = dinv .* v_{j+1} and the Givens
+// step.  Blocks own the row ranges of gs_partition and keep their rows of w in shared
+// memory from the first phase to the last; the phases are separated by grid barriers.
+//   phase 1: partial1[i][b] = V_i . w over the block's rows
+//   phase 2: h1 = sum_b partial1 (same sums in every block); H[:, j] = h1; w -= V h1;
+//            partial2[i][b] = V_i . w, partial2[j+1][b] = w . w
+//   phase 3: h2 = sum_b partial2; H[:, j] += h2; w -= V h2 and, with s1 = ||w||^2 before
+//            this update, ||w||^2 = s1 - ||h2||^2 (Pythagoras: w - V h2 is orthogonal to
+//            V h2 up to rounding) -- unless that removes more than half of s1, when the
+//            norm is summed directly after one more barrier; then v_{j+1}, z, Givens.
+// The passes read V as the separate kernels do (4 (j+1) N values); w does not go back to
+// global memory.  All blocks take the same branches (their sums are identical).
+__global__ void __launch_bounds__(GS_THREADS) k_gs_fused(const double *__restrict__ Vb, int64_t ld, int j,
+                                                         const double *__restrict__ w, const double *__restrict__ dinv,
+                                                         double *__restrict__ z, double *__restrict__ P1,
+                                                         double *__restrict__ P2, int64_t N, int per, double *__restrict__ gm,
+                                                         int m, double tol, unsigned *bar) {
+  extern __shared__ double fs_sm[];
+  const int jp1 = j + 1;
+  double *ws = fs_sm;                  // [per]
+  double *hs = ws + per;               // [m + 2]: h1, then h1 + h2
+  double *h2 = hs + (m + 2);           // [m + 2]: h2 and s1
+  double *dp = h2 + (m + 2);           // [GS_THREADS / 32]
+  double *cs_s = dp + GS_THREADS / 32; // [m]
+  double *sn_s = cs_s + m;             // [m]
+  double *Hs = sn_s + m;               // [m + 2]
+  __shared__ double sh[32];
+  GmLayout L = gm_layout(m);
+  double *fl = gm + L.flags;
+  if (fl[0] != 0.0) return;
+  const int T = blockDim.x;
+  const int64_t a = (int64_t)blockIdx.x * per;
+  const int cnt = (int)max((int64_t)0, min((int64_t)per, N - a));
+  // phase 1
+  for (int r = threadIdx.x; r < cnt; r += T) ws[r] = w[a + r];
+  __syncthreads();
+  block_dots(Vb, ld, jp1, a, cnt, ws, dp, P1);
+  if (!gs_grid_sync(bar)) goto timeout;
+  // phase 2
+  block_sum_cols(P1, gridDim.x, jp1, hs);
+  {
+    double sq = 0.0;
+    for (int r = threadIdx.x; r < cnt; r += T) {
+      double v = ws[r];
+      const double *c = Vb + a + r;
+#pragma unroll 4
+      for (int i = 0; i < jp1; i++) v = fma(-hs[i], c[(size_t)i * ld], v);
+      ws[r] = v;
+      sq = fma(v, v, sq);
+    }
+    sq = block_sum(sq, sh);
+    if (threadIdx.x == 0) P2[(size_t)jp1 * gridDim.x + blockIdx.x] = sq;
+  }
+  __syncthreads();
+  block_dots(Vb, ld, jp1, a, cnt, ws, dp, P2);
+  if (!gs_grid_sync(bar)) goto timeout;
+  // phase 3
+  block_sum_cols(P2, gridDim.x, jp1 + 1, h2);
+  {
+    double s2 = h2[jp1];
+    for (int i = 0; i < jp1; i++) s2 = fma(-h2[i], h2[i], s2);
+    const bool direct = !(s2 > 0.5 * h2[jp1]);
+    double sq = 0.0;
+    for (int r = threadIdx.x; r < cnt; r += T) {
+      double v = ws[r];
+      const double *c = Vb + a + r;
+#pragma unroll 4
+      for (int i = 0; i < jp1; i++) v = fma(-h2[i], c[(size_t)i * ld], v);
+      ws[r] = v;
+      sq = fma(v, v, sq);
+    }
+    if (direct) {  // severe cancellation in the second pass: sum ||w||^2 itself
+      sq = block_sum(sq, sh);
+      if (threadIdx.x == 0) P1[blockIdx.x] = sq;
+      if (!gs_grid_sync(bar)) goto timeout;
+      if (threadIdx.x < 32) {
+        double acc = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) acc += P1[b];
+        acc = warp_sum(acc);
+        if (threadIdx.x == 0) sh[0] = acc;
+      }
+      __syncthreads();
+      s2 = sh[0];
+    }
+    const double hn = sqrt(fmax(s2, 0.0));
+    const double inv = (hn > 0.0) ? 1.0 / hn : 0.0;
+    double *vnext = const_cast<double *>(Vb) + (size_t)jp1 * ld;
+    for (int r = threadIdx.x; r < cnt; r += T) {
+      const double v = ws[r] * inv;
+      vnext[a + r] = v;
+      z[a + r] = dinv[a + r] * v;
+    }
+    if (blockIdx.x == 0) {
+      double *Hj = gm + L.H + (size_t)j * (m + 1);
+      for (int i = threadIdx.x; i < jp1; i += T) {
+        Hs[i] = hs[i] + h2[i];
+        Hj[i] = Hs[i];
+      }
+      for (int i = threadIdx.x; i < j; i += T) {
+        cs_s[i] = gm[L.cs + i];
+        sn_s[i] = gm[L.sn + i];
+      }
+      if (threadIdx.x == 0) Hs[jp1] = fmax(s2, 0.0);
+      __syncthreads();
+      if (threadIdx.x == 0) givens_step_sm(Hs, cs_s, sn_s, gm, m, j, tol);
+    }
+  }
+  return;
+timeout:
+  if (threadIdx.x == 0) {
+    fl[GS_FLAG_TIMEOUT] = 1.0;
+    fl[3] = 1.0;
+    fl[0] = 1.0;
+  }
+}
+
 // solve the k x k upper triangular system H y = g (one thread); k = fl[1]
 __global__ void k_trisolve(double *__restrict__ gm, int m) {
   GmLayout L = gm_layout(m);
@@ -482,7 +700,11 @@ static cudaError_t spmv_f32_launch(iga_s *h, const float *vals, const double *x,
   const StencilRows S = stencil_rows(h);
   const int N = (int)h->N;
   unsigned grid = (unsigned)(((int64_t)N * 8 + 255) / 256);
-  if (h->dim == 3)
+  if (h->dim == 3 && ((uintptr_t)vals & 15) == 0) {
+    // a warp per row with 16-byte loads; persistent warps, 8 blocks of 8 warps per SM
+    unsigned g3 = (unsigned)std::min<int64_t>(((int64_t)N + 7) / 8, 152 * 8);
+    IGA_LAUNCH(h, KC_SPMV, (k_spmv32_warp<3><<<g3, 256, 0, h->stream>>>(S, h->rowptr, vals, h->z32, y, N, h->nnz, done)));
+  } else if (h->dim == 3)
     IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<3, 8, float, float, float><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, h->z32, y, N, done)));
   else
     IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<2, 8, float, float, float><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, h->z32, y, N, done)));
@@ -556,7 +778,8 @@ cudaError_t launch_nan_check(iga_s *h, const double *x, double *out_dev) {
 
 // Restarted GMRES(m), right Jacobi preconditioning: solves A x = b from x = 0
 // until ||b - A x|| <= tol_abs or maxit iterations.  Returns 0 on convergence,
-// 1 when the cap was hit, 2 on breakdown/NaN, -1 on a CUDA error.
+// 1 when the cap was hit, 2 on breakdown/NaN, 3 when a grid barrier of the fused
+// orthogonalisation gave up, -1 on a CUDA error.
 // Operator of the Krylov solvers: FP64 values (kind 0), FP32 values (1) or the
 // matrix-free product J(U) x (2; vals unused, h->Q00 holds the reaction part at U)
 static void apply_op(iga_s *h, const void *vals, int kind, const double *x, double *y, const double *done) {
@@ -600,6 +823,19 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
       cudaFuncSetAttribute(k_gs_pass<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
     }
   }
+  // one cooperative launch per orthogonalisation when every block of the row partition
+  // can be resident at once (one 1024-thread block per SM), else the four kernels
+  const size_t fsmem = (size_t)(gs.per + 3 * (m + 2) + GS_THREADS / 32 + 2 * m) * sizeof(double);
+  bool fused = false;
+  if (h->gsbar && fsmem <= 227 * 1024) {
+    int dev = 0, coop = 0, nsm = 0, per_sm = 0;
+    if (fsmem > 48 * 1024) cudaFuncSetAttribute(k_gs_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gs_fused, GS_THREADS, fsmem) == cudaSuccess)
+      fused = coop && (int64_t)per_sm * nsm >= gs.nb;
+    cudaGetLastError();
+  }
   jacobi_scaling(h, vals, is_f32, dinv);
   IGA_LAUNCH(h, KC_VEC, (k_fill<<<eg, 256, 0, h->stream>>>(x, 0.0, N)));
   const int batch = 8;
@@ -626,6 +862,21 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
         const int jp1 = j + 1;
         const size_t smem = (size_t)(gs.per + jp1 + GS_THREADS / 32) * sizeof(double);
         double *P1 = h->red, *P2 = h->red + (size_t)(m + 1) * gs.nb, *P3 = h->red;
+        if (fused) {
+          const double *Vc = Vb;
+          const double *wc = w, *dc = dinv;
+          int jj = j, mm = m, per = gs.per;
+          int64_t NN = N, ldd = ld;
+          double tt = tol_abs;
+          unsigned *bar = h->gsbar;
+          void *args[] = {(void *)&Vc, (void *)&ldd, (void *)&jj, (void *)&wc, (void *)&dc, (void *)&z, (void *)&P1,
+                          (void *)&P2, (void *)&NN, (void *)&per, (void *)&gm, (void *)&mm, (void *)&tt, (void *)&bar};
+          cudaError_t le = cudaSuccess;
+          IGA_LAUNCH(h, KC_ORTH, (le = cudaLaunchCooperativeKernel((const void *)k_gs_fused, dim3(gs.nb), dim3(GS_THREADS), args,
+                                                                   fsmem, h->stream)));
+          if (le != cudaSuccess) { *cerr = le; return -1; }
+          continue;
+        }
         IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<1><<<gs.nb, GS_THREADS, smem, h->stream>>>(Vb, ld, jp1, nullptr, Hj, w, P1, N, gs.per, done)));
         IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<2><<<gs.nb, GS_THREADS, smem, h->stream>>>(Vb, ld, jp1, P1, Hj, w, P2, N, gs.per, done)));
         IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<3><<<gs.nb, GS_THREADS, smem, h->stream>>>(Vb, ld, jp1, P2, Hj, w, P3, N, gs.per, done)));
@@ -635,6 +886,12 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
       cudaMemcpyAsync(fl_host, gm + L.flags, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
       cudaError_t ce = cudaStreamSynchronize(h->stream);
       if (ce) { *cerr = ce; return -1; }
+      if (fl_host[GS_FLAG_TIMEOUT] != 0.0) {  // a grid barrier gave up: reset it and report
+        cudaMemsetAsync(h->gsbar, 0, 2 * sizeof(unsigned), h->stream);
+        cudaStreamSynchronize(h->stream);
+        *its = total + j;
+        return 3;
+      }
       if (fl_host[0] != 0.0 || j >= m) cycle_done = true;
     }
     int k = (int)fl_host[1];

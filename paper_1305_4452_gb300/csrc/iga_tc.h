@@ -38,16 +38,19 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
   return ok != 0;
 }
 
-// wait for the phase with the given parity to complete; false after ~2 s, or
-// at once when another role has given up (*abort set).  sleep_ns > 0 backs off
+constexpr uint64_t MBAR_LIMIT_NS = 2000000000ull;  // default bound of a pipeline wait: 2 s
+
+// wait for the phase with the given parity to complete; false after limit_ns (default
+// 2 s), or at once when another role has given up (*abort set).  sleep_ns > 0 backs off
 // between polls (for waits that are long by design).
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int *abort, unsigned sleep_ns = 0) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int *abort, unsigned sleep_ns = 0,
+                                          uint64_t limit_ns = MBAR_LIMIT_NS) {
   if (mbar_try(mbar, parity)) return true;
   const uint64_t t0 = gtimer();
   for (uint32_t i = 1;; i++) {
     if (sleep_ns) __nanosleep(sleep_ns);
     if (mbar_try(mbar, parity)) return true;
-    if ((i & 63) == 0 && ((abort && *abort) || gtimer() - t0 > 2000000000ull)) return false;
+    if ((i & 63) == 0 && ((abort && *abort) || gtimer() - t0 > limit_ns)) return false;
   }
 }
 

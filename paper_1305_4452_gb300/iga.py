@@ -25,7 +25,8 @@ EXPORTS = ["iga_create", "iga_set_boundary_value", "iga_set_lambda", "iga_get_pa
            "iga_batch_last_error", "iga_nn_create", "iga_nn_num_params", "iga_nn_get_params", "iga_nn_set_params",
            "iga_nn_forward", "iga_nn_loss_grad", "iga_nn_adam_step", "iga_nn_destroy", "iga_nn_last_error",
            "iga_nn_set_h1_weight", "iga_apply_jacobian", "iga_apply_jacobian_mf", "iga_form_jacobian_diagonal",
-           "iga_form_residual_ts", "iga_form_jacobian_ts", "iga_ts_alpha_step", "iga_measure_peaks"]
+           "iga_form_residual_ts", "iga_form_jacobian_ts", "iga_ts_alpha_step", "iga_measure_peaks",
+           "iga_set_wait_limit", "iga_inject_stall"]
 
 KERNEL_CLASSES = ["geometry", "residual_element", "residual_gather", "q00", "jac_stage1", "jac_stage2", "jac_final",
                   "spmv", "gs_orth", "gmres_scalar", "vector", "combine", "pattern", "elem_tc", "elem_gather"]
@@ -127,6 +128,8 @@ def lib():
         L.iga_profile_enable.argtypes = [vp, ctypes.c_uint]
         L.iga_profile_read.argtypes = [vp, ctypes.POINTER(IgaProfile)]
         L.iga_measure_peaks.argtypes = [vp, ctypes.POINTER(IgaPeaks)]
+        L.iga_set_wait_limit.argtypes = [vp, ctypes.c_double]
+        L.iga_inject_stall.argtypes = [vp]
         _lib = L
     return _lib
 

@@ -196,3 +196,32 @@ def test_element_gemm_newton_steps_on_a_fine_mesh(I, prec):
         steps[name] = rep.newton_its
         disc.close()
     assert steps[prec] <= steps["fp64"] + 1, steps
+
+
+def test_bounded_pipeline_wait_gives_up_and_the_next_call_is_correct(I):
+    """Failure detection in the allowed form: a bounded wait on a barrier that nothing
+    arrives on.  With the stall hook the element GEMM's wait gives up after the (short)
+    limit and the call reports IGA_ETIMEOUT; the kernel freed its tensor memory (the next
+    calls allocate it again in every CTA and complete), and their Jacobians are
+    bit-identical to one assembled before the stall."""
+    import ctypes
+    disc, prob, n = pair(I, 3, 2, 16, 1.5)  # a uniform mesh large enough for the element GEMM
+    U = torch.tensor(W.interior_field(n, seed=3, lo=-0.3, hi=0.3), device="cuda")
+    ref = disc.form_jacobian(U, prec=I.IGA_JAC_BF16).clone()
+    L = I.lib()
+    assert L.iga_set_wait_limit(disc.h, 0.02) == I.IGA_OK
+    assert L.iga_inject_stall(disc.h) == I.IGA_OK
+    vals = torch.full((disc.nnz,), float("nan"), dtype=torch.float32, device="cuda")
+    rc = L.iga_form_jacobian(disc.h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(vals.data_ptr()), I.IGA_JAC_BF16)
+    assert rc == I.IGA_ETIMEOUT, rc
+    assert b"gave up" in L.iga_last_error(disc.h)
+    assert L.iga_set_wait_limit(disc.h, 2.0) == I.IGA_OK
+    for _ in range(2):
+        assert torch.equal(disc.form_jacobian(U, prec=I.IGA_JAC_BF16), ref)
+    # a Newton solve on the same handle after the give-up
+    Us = torch.zeros(disc.N, dtype=torch.float64, device="cuda")
+    o = I.newton_defaults()
+    o.jac = I.IGA_JAC_BF16
+    assert disc.solve_newton(Us, o).status == 0
+    assert L.iga_set_wait_limit(disc.h, 0.0) == I.IGA_EINVAL
+    disc.close()
