@@ -398,7 +398,7 @@ static iga_status ensure_workspace(iga_s *h, int m, bool f32, bool mf = false) {
   }
   if (!f32 && !mf && !h->J64) CK(cudaMalloc((void **)&h->J64, h->nnz * sizeof(double)));
   if (f32 && !h->J32) CK(cudaMalloc((void **)&h->J32, h->nnz * sizeof(float)));
-  if (f32 && !h->z32) CK(cudaMalloc((void **)&h->z32, N * sizeof(float)));
+  if (f32 && !h->z32) CK(cudaMalloc((void **)&h->z32, 2 * N * sizeof(float)));  // (xh, xl) pairs
   return IGA_OK;
 }
 
