@@ -219,8 +219,9 @@ typedef struct {
   iga_precision jac;   /* Jacobian precision used to steer Newton (default IGA_FP64);
                           IGA_JAC_NONE: matrix-free (no assembled Jacobian) */
   int reuse_stiffness; /* 1: assemble the U-independent part K of J once per solve and add
-                          the reaction term each step (default 1); with an FP64 Jacobian every
-                          residual of the solve is then K U plus the reaction term (equal to
+                          the reaction term each step (default 1); every residual of the solve
+                          (FP64 with every Jacobian type, except matrix-free, local ND and periodic
+                          solves) is then the FP64 product K U plus the reaction term (equal to
                           Eq. (residual) up to rounding); 0: full assembly each step */
   int ksp;             /* Krylov method: IGA_KSP_GMRES (default) or IGA_KSP_CG (Jacobi-
                           preconditioned conjugate gradients, the -ksp_type cg run of App. B;

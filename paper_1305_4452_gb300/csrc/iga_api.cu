@@ -398,7 +398,7 @@ static iga_status ensure_workspace(iga_s *h, int m, bool f32, bool mf = false) {
   }
   if (!f32 && !mf && !h->J64) CK(cudaMalloc((void **)&h->J64, h->nnz * sizeof(double)));
   if (f32 && !h->J32) CK(cudaMalloc((void **)&h->J32, h->nnz * sizeof(float)));
-  if (f32 && !h->z32) CK(cudaMalloc((void **)&h->z32, 2 * N * sizeof(float)));  // (xh, xl) pairs
+  if (f32 && !h->z32) CK(cudaMalloc((void **)&h->z32, N * sizeof(float)));
   return IGA_OK;
 }
 
@@ -470,7 +470,9 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
   const bool mf = o.jac == IGA_JAC_NONE;  // matrix-free
   const bool fd = o.jac == IGA_JAC_FD;    // FP64 values by numerical differentiation
   const bool f32 = !mf && !fd && o.jac != IGA_FP64;
-  const bool split = !f32 && !mf && !fd && o.reuse_stiffness != 0 && !h->inner;
+  // the FP64 residual as K U + reaction(U) with the FP64 stiffness K assembled once per
+  // solve (also when a reduced-precision Jacobian steers Newton: the residual stays FP64)
+  const bool split = !mf && !fd && o.reuse_stiffness != 0 && !h->inner;
   iga_status st = ensure_workspace(h, o.gmres_restart, f32, mf);
   if (st != IGA_OK) return st;
   const int64_t N = h->N;

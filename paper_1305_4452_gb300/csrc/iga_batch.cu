@@ -35,6 +35,7 @@
 namespace {
 
 constexpr int BMAXM = 64;  // largest GMRES restart in the batched solver
+constexpr int BDOT_MAX = 16;  // largest number of row chunks per Gram-Schmidt dot
 
 struct BMesh {  // device data shared by instances with the same knots (square meshes: both axes identical)
   int p, q, nel, n, np, N;
@@ -73,6 +74,7 @@ __host__ __device__ __forceinline__ int64_t jsize(int N, int p) {
 struct BArgs {
   double *U;
   iga_newton_opts opts;
+  int dot_chunks;  // work unit of the Gram-Schmidt dots: row chunks per dot (0: as many as keep every warp busy)
 };
 
 struct BRep {
@@ -91,6 +93,7 @@ struct Cta {
   int tid, nt, lane, warp, nw;
   double *red;  // shared, >= 36 doubles
   float *zs;    // shared FP32 operand vector of the operator products (N floats), or null
+  int dot_chunks;  // row chunks per Gram-Schmidt dot (BArgs::dot_chunks)
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -349,20 +352,35 @@ __device__ void b_apply(const BInst &I, const double *__restrict__ v, double *__
 
 struct GmShared {
   double H[BMAXM + 1][BMAXM];
+  double part[BMAXM + 1][BDOT_MAX];  // chunk sums of the Gram-Schmidt dots
   double cs[BMAXM], sn[BMAXM], g[BMAXM + 1], y[BMAXM], h[BMAXM + 1];
   double scal[8];
   int flag[4];
 };
 
-// CGS pass: h_i = <V_i, w> (one warp per dot), then w -= sum h_i V_i; returns nothing; adds h into H[:, j]
+// CGS pass: h_i = <V_i, w>, then w -= sum h_i V_i; adds h into H[:, j].  Work unit of
+// the dots: (column i, row chunk) with R chunks of about N / R rows per column (R =
+// c.dot_chunks, or as many as keep every warp busy when it is 0), one warp per unit; the
+// chunk sums are added in chunk order, so the result depends on R but not on scheduling.
 __device__ void b_cgs_pass(const BInst &I, double *__restrict__ w, int jp1, GmShared &s, int j, bool first, const Cta &c) {
   const int N = I.m.N;
-  for (int i = c.warp; i < jp1; i += c.nw) {
+  int R = c.dot_chunks > 0 ? c.dot_chunks : max(1, c.nw / jp1);
+  R = min(R, BDOT_MAX);
+  const int items = jp1 * R, clen = (N + R - 1) / R;
+  for (int it = c.warp; it < items; it += c.nw) {
+    const int i = it / R, ch = it - i * R;
+    const int r0 = ch * clen, r1 = min(N, r0 + clen);
     const double *v = I.V + (size_t)i * N;
     double acc = 0.0;
-    for (int r = c.lane; r < N; r += 32) acc = fma(v[r], w[r], acc);
+    for (int r = r0 + c.lane; r < r1; r += 32) acc = fma(v[r], w[r], acc);
     acc = warp_sum(acc);
-    if (c.lane == 0) s.h[i] = acc;
+    if (c.lane == 0) s.part[i][ch] = acc;
+  }
+  __syncthreads();
+  if (c.tid < jp1) {
+    double h = s.part[c.tid][0];
+    for (int ch = 1; ch < R; ch++) h += s.part[c.tid][ch];
+    s.h[c.tid] = h;
   }
   __syncthreads();
   for (int r = c.tid; r < N; r += c.nt) {
@@ -611,6 +629,7 @@ __global__ void __launch_bounds__(NT, MINB) k_batch(const BInst *__restrict__ in
   c.nw = blockDim.x >> 5;
   c.red = red;
   c.zs = nullptr;
+  c.dot_chunks = args->dot_chunks;
   const iga_newton_opts o = args->opts;
   for (;;) {
     if (c.tid == 0) cur = atomicAdd(counter, 1);
@@ -686,6 +705,7 @@ struct iga_batch_s {
   BRep *d_reps = nullptr, *h_reps = nullptr;
   std::vector<int64_t> uoff;       // count + 1
   int threads = 512, ctas_per_sm = 1, nsm = 0;
+  int dot_chunks = 1;              // work unit of the Gram-Schmidt dots (iga_batch_set_tiles)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int graph_threads = 0, graph_ctas = 0;
@@ -955,6 +975,16 @@ extern "C" iga_status iga_batch_set_launch(iga_batch_t b, int ctas_per_sm, int t
   }
   b->ctas_per_sm = ctas_per_sm;
   b->threads = threads_per_cta;
+  return IGA_OK;
+}
+
+extern "C" iga_status iga_batch_set_tiles(iga_batch_t b, int dot_chunks) {
+  if (!b) return IGA_EINVAL;
+  if (dot_chunks < 0 || dot_chunks > BDOT_MAX) {
+    b->err = iga_format("dot_chunks must be in 0..%d", BDOT_MAX);
+    return IGA_EINVAL;
+  }
+  b->dot_chunks = dot_chunks;
   return IGA_OK;
 }
 

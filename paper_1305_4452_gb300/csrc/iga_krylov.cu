@@ -101,43 +101,33 @@ __device__ __forceinline__ RowShape row_shape(const StencilRows &S, int row) {
 }
 
 // y = A x over the stencil CSR, LPR lanes per row.  Lane t of a row takes the
-// row's entries t, t+LPR, ...  Rows whose stencil is complete in every direction
-// ((2p+1)^DIM columns, nearly all of them) read their column offsets from a table in
-// shared memory, so that a lane's loads are independent of one another; the other rows
-// advance the column incrementally (a run of w0 consecutive columns per (i1, i2)
-// offset).  Every lane reaches the shuffles.
-template <int DIM, int LPR, typename V, typename X, typename ACC>
+// row's entries t, t+LPR, ..., CH of them per round: the round's columns are formed
+// first (a run of w0 consecutive columns per (i1, i2) offset, advanced with integer
+// arithmetic only), then its CH value and x loads are issued together, then the FMAs,
+// in entry order -- so each lane has CH loads in flight rather than one, and the sum is
+// the same as entry by entry.  Every lane reaches the shuffles.
+template <int DIM, int LPR, int CH, typename V, typename X, typename ACC>
 __global__ void __launch_bounds__(256) k_spmv_stencil(StencilRows S, const int64_t *__restrict__ rowptr,
                                                       const V *__restrict__ val, const X *__restrict__ x,
-                                                      double *__restrict__ y, int N, int wf, const double *__restrict__ done) {
-  __shared__ int off_s[729];
+                                                      double *__restrict__ y, int N, const double *__restrict__ done) {
   if (done && done[0] != 0.0) return;
-  const int full = DIM == 3 ? wf * wf * wf : wf * wf;
-  for (int e = threadIdx.x; e < full; e += blockDim.x) {
-    const int i = e % wf, j = (e / wf) % wf, k = e / (wf * wf);
-    off_s[e] = i + j * S.n0 + k * S.n01;
-  }
-  __syncthreads();
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = gid / LPR, lane = gid % LPR;
   ACC acc = 0;
   if (row < N) {
     const RowShape R = row_shape<DIM>(S, row);
+    const int cnt = R.w0 * R.w1 * R.w2;
     const V *v = val + rowptr[row];
-    if (R.w0 == wf && R.w1 == wf && R.w2 == (DIM == 3 ? wf : 1)) {
-      const X *xb = x + (R.lo0 + R.lo1 * S.n0 + R.lo2 * S.n01);
-#pragma unroll 8
-      for (int e = lane; e < full; e += LPR) acc = fma((ACC)v[e], (ACC)xb[off_s[e]], acc);
-    } else {
-      const int cnt = R.w0 * R.w1 * R.w2;
-      int ii = lane, jj = 0, kk = 0;
-      while (ii >= R.w0) { ii -= R.w0; jj++; }
-      while (jj >= R.w1) { jj -= R.w1; kk++; }
-      int col = (R.lo0 + ii) + (R.lo1 + jj) * S.n0 + (R.lo2 + kk) * S.n01;
-      const int djj = S.n0 - R.w0, dkk = S.n01 - R.w1 * S.n0;
-#pragma unroll 4
-      for (int e = lane; e < cnt; e += LPR) {
-        acc = fma((ACC)v[e], (ACC)x[col], acc);
+    int ii = lane, jj = 0, kk = 0;
+    while (ii >= R.w0) { ii -= R.w0; jj++; }
+    while (jj >= R.w1) { jj -= R.w1; kk++; }
+    int col = (R.lo0 + ii) + (R.lo1 + jj) * S.n0 + (R.lo2 + kk) * S.n01;
+    const int djj = S.n0 - R.w0, dkk = S.n01 - R.w1 * S.n0;
+    for (int e0 = lane; e0 < cnt; e0 += CH * LPR) {
+      int cols[CH];
+#pragma unroll
+      for (int k = 0; k < CH; k++) {
+        cols[k] = col;
         ii += LPR;
         col += LPR;
         while (ii >= R.w0) {
@@ -146,6 +136,16 @@ __global__ void __launch_bounds__(256) k_spmv_stencil(StencilRows S, const int64
           if (++jj == R.w1) { jj = 0; col += dkk; }
         }
       }
+      V vv[CH];
+      X xv[CH];
+#pragma unroll
+      for (int k = 0; k < CH; k++) {
+        const bool in = e0 + k * LPR < cnt;  // past the row's end the column is not one of its own
+        vv[k] = in ? v[e0 + k * LPR] : (V)0;
+        xv[k] = in ? x[cols[k]] : (X)0;
+      }
+#pragma unroll
+      for (int k = 0; k < CH; k++) acc = fma((ACC)vv[k], (ACC)xv[k], acc);
     }
   }
 #pragma unroll
@@ -153,99 +153,11 @@ __global__ void __launch_bounds__(256) k_spmv_stencil(StencilRows S, const int64
   if (row < N && lane == 0) y[row] = (double)acc;
 }
 
-// Operator of the reduced-precision Newton: FP32 values, the FP64 vector x carried as an
-// unevaluated pair of floats (x = xh + xl, xh = fl32(x), xl = fl32(x - xh)), and every
-// product and sum in double-float arithmetic on the FP32 pipe:
-//   p + pe = v xh exactly (pe by fma), pe += v xl;  (hi, lo) += p by the error-free
-//   two-sum hi + p = s + e;  lo += e + pe.
-// The sum of a row is then exact to about 2^-44 of the sum of |v x| (with the given FP32
-// values), so the Krylov solve reaches the accuracy of an FP64 product while the
-// arithmetic runs at FP32 rates; an FP64 product of FP32 values would be bound by GB300's
-// FP64 pipe like the FP64 operator.  The operations that must not be contracted into FMAs
-// are written with explicitly rounded intrinsics.
-__device__ __forceinline__ void df_add(float &hi, float &lo, float b, float be) {
-  const float s = __fadd_rn(hi, b);
-  const float bb = __fsub_rn(s, hi);
-  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  hi = s;
-  lo = __fadd_rn(lo, __fadd_rn(e, be));
-}
-
-// LPR lanes per row as k_spmv_stencil.  Rows whose stencil is complete in every direction
-// ((2p+1)^DIM columns, nearly all of them) take their column offsets from a table in
-// shared memory, so the loads of a lane do not wait on the column arithmetic; the other
-// rows advance the column as k_spmv_stencil does.
-template <int DIM, int LPR>
-__global__ void __launch_bounds__(256) k_spmv_f32c(StencilRows S, const int64_t *__restrict__ rowptr,
-                                                   const float *__restrict__ val, const float2 *__restrict__ x,
-                                                   double *__restrict__ y, int N, int wf, const double *__restrict__ done) {
-  __shared__ int off_s[729];
+__global__ void k_cvt_f32(const double *__restrict__ x, float *__restrict__ y, int64_t N, const double *__restrict__ done) {
   if (done && done[0] != 0.0) return;
-  const int full = DIM == 3 ? wf * wf * wf : wf * wf;
-  for (int e = threadIdx.x; e < full; e += blockDim.x) {
-    const int i = e % wf, j = (e / wf) % wf, k = e / (wf * wf);
-    off_s[e] = i + j * S.n0 + k * S.n01;
-  }
-  __syncthreads();
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int row = gid / LPR, lane = gid % LPR;
-  float hi = 0.f, lo = 0.f;
-  if (row < N) {
-    const RowShape R = row_shape<DIM>(S, row);
-    const float *v = val + rowptr[row];
-    const int base = R.lo0 + R.lo1 * S.n0 + R.lo2 * S.n01;
-    if (R.w0 == wf && R.w1 == wf && R.w2 == (DIM == 3 ? wf : 1)) {
-#pragma unroll 8
-      for (int e = lane; e < full; e += LPR) {
-        const float a = __ldcs(v + e);
-        const float2 xx = __ldg(x + base + off_s[e]);
-        const float p = __fmul_rn(a, xx.x);
-        const float pe = fmaf(a, xx.y, fmaf(a, xx.x, -p));
-        df_add(hi, lo, p, pe);
-      }
-    } else {
-      const int cnt = R.w0 * R.w1 * R.w2;
-      int ii = lane, jj = 0, kk = 0;
-      while (ii >= R.w0) { ii -= R.w0; jj++; }
-      while (jj >= R.w1) { jj -= R.w1; kk++; }
-      int col = (R.lo0 + ii) + (R.lo1 + jj) * S.n0 + (R.lo2 + kk) * S.n01;
-      const int djj = S.n0 - R.w0, dkk = S.n01 - R.w1 * S.n0;
-      for (int e = lane; e < cnt; e += LPR) {
-        const float a = v[e];
-        const float2 xx = x[col];
-        const float p = __fmul_rn(a, xx.x);
-        const float pe = fmaf(a, xx.y, fmaf(a, xx.x, -p));
-        df_add(hi, lo, p, pe);
-        ii += LPR;
-        col += LPR;
-        while (ii >= R.w0) {
-          ii -= R.w0;
-          col += djj;
-          if (++jj == R.w1) { jj = 0; col += dkk; }
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int o = LPR / 2; o > 0; o >>= 1) {
-    const float h2 = __shfl_down_sync(0xffffffffu, hi, o, LPR), l2 = __shfl_down_sync(0xffffffffu, lo, o, LPR);
-    df_add(hi, lo, h2, l2);
-  }
-  if (row < N && lane == 0) y[row] = (double)hi + (double)lo;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) y[i] = (float)x[i];
 }
 
-// x -> (xh, xl) = (fl32(x), fl32(x - xh)) for k_spmv_f32c
-__global__ void k_cvt_f32x2(const double *__restrict__ x, float2 *__restrict__ y, int64_t N, const double *__restrict__ done) {
-  if (done && done[0] != 0.0) return;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = x[i];
-    const float h = __double2float_rn(v);
-    y[i] = make_float2(h, __double2float_rn(v - (double)h));
-  }
-}
-
-
-// dinv = 1 / diag(A); the diagonal's position in row A follows from the stencil
 template <int DIM, typename V>
 __global__ void k_diag_stencil(StencilRows S, const int64_t *__restrict__ rowptr, const V *__restrict__ val,
                                double *__restrict__ dinv, int N) {
@@ -746,22 +658,23 @@ static StencilRows stencil_rows(const iga_s *h) {
   return S;
 }
 
-// FP32-value operator product used by the mixed-precision Newton: x -> (xh, xl) float
-// pair, then the double-float product k_spmv_f32c (8 lanes x 4 B = one 32 B sector per
-// row and step)
+// FP32-value operator product used by the mixed-precision Newton: x -> FP32 copy,
+// FP32 SpMV with FP32 sums (8 lanes x 4 B = one 32 B sector per row and step).  The
+// operator only steers Newton (its values are rounded already); its FP32 sums limit the
+// linear residual to the FP32 level, which the forcing floor of the reduced-precision
+// Jacobians stays above.
 static cudaError_t spmv_f32_launch(iga_s *h, const float *vals, const double *x, double *y, const double *done) {
   if (h->inner) return periodic_spmv(h, vals, 1, x, y, done);
   int eg = (int)((h->N + 255) / 256);
   if (eg > 608) eg = 608;
-  float2 *x2 = reinterpret_cast<float2 *>(h->z32);
-  IGA_LAUNCH(h, KC_VEC, (k_cvt_f32x2<<<eg, 256, 0, h->stream>>>(x, x2, h->N, done)));
+  IGA_LAUNCH(h, KC_VEC, (k_cvt_f32<<<eg, 256, 0, h->stream>>>(x, h->z32, h->N, done)));
   const StencilRows S = stencil_rows(h);
-  const int N = (int)h->N, wf = 2 * h->p + 1;
+  const int N = (int)h->N;
   unsigned grid = (unsigned)(((int64_t)N * 8 + 255) / 256);
   if (h->dim == 3)
-    IGA_LAUNCH(h, KC_SPMV, (k_spmv_f32c<3, 8><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, x2, y, N, wf, done)));
+    IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<3, 8, 4, float, float, float><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, h->z32, y, N, done)));
   else
-    IGA_LAUNCH(h, KC_SPMV, (k_spmv_f32c<2, 8><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, x2, y, N, wf, done)));
+    IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<2, 8, 4, float, float, float><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, h->z32, y, N, done)));
   return cudaGetLastError();
 }
 
@@ -775,9 +688,9 @@ static cudaError_t spmv_launch(iga_s *h, const V *vals, const double *x, double 
   const int N = (int)h->N;
   unsigned grid = (unsigned)(((int64_t)N * 4 + 255) / 256);
   if (h->dim == 3)
-    IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<3, 4, V, double, double><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, x, y, N, 2 * h->p + 1, done)));
+    IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<3, 4, 4, V, double, double><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, x, y, N, done)));
   else
-    IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<2, 4, V, double, double><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, x, y, N, 2 * h->p + 1, done)));
+    IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<2, 4, 4, V, double, double><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, x, y, N, done)));
   return cudaGetLastError();
 }
 
