@@ -191,15 +191,14 @@ def batch512(torch, iga, W, clock):
     setup = time.perf_counter() - t0
     U = torch.zeros(b.total, dtype=torch.float64, device="cuda")
     from paper_1305_4452_gb300 import autotune
-    o = iga.newton_defaults()
-    o.ksp = iga.IGA_KSP_CG
-    tuned = autotune.tune(b, ins, U, o, retime=True)
-    res = {"autotune": tuned}
+    res = {"autotune": {}}
     clock.start()
     for label, ksp in (("cg", iga.IGA_KSP_CG), ("gmres30", iga.IGA_KSP_GMRES)):
         o = iga.newton_defaults()
         o.ksp = ksp
         o.gmres_restart = 30
+        # launch shape, and for GMRES the work unit of its Gram-Schmidt dots, for this mix
+        res["autotune"][label] = autotune.tune(b, ins, U, o, retime=True)
         best, r = 1e30, None
         for _ in range(3):
             U.zero_()
@@ -220,6 +219,7 @@ def batch512(torch, iga, W, clock):
                                                   "krylov_its": int(r["krylov_its"][big])}}}
     ck = clock.stop()
     b.close()
+    res["jacobian_2d_tensor_vs_sumfact"] = jacobian_2d_comparison(torch, iga, W)
     import oracle as O
     done, t_or, k = 0, 0.0, 0
     t0 = time.perf_counter()
@@ -235,6 +235,29 @@ def batch512(torch, iga, W, clock):
                    "one at a time" % done, done, t_or)
     return _line(res["cg"]["solves_per_s"], "solves/s", "batch512_2d_n16to128_p2or3_lambda0.5to6_fp64res_fp32jac",
                  {"results": res, "setup_s": setup, "total_dofs": int(b.total), "cpu_baseline": cb}, ck)
+
+
+def jacobian_2d_comparison(torch, iga, W, reps=5):
+    """The reduced-precision Jacobians the batched instances could use, on single 2D meshes
+    of the batch's range (identity map, lambda = 3, U ~ U[-0.1, 0.1]): FP32 global sum
+    factorisation on the CUDA cores (the batch's own kind) against the BF16 and TF32
+    tensor-core element matrices, best of `reps`; errors against the FP64 Jacobian."""
+    out = []
+    bc = {(a, s): 0.0 for a in range(2) for s in range(2)}
+    for nel, p in ((32, 2), (64, 2), (128, 2), (32, 3), (64, 3), (128, 3)):
+        d = iga.Discretization(2, p, nel=nel, lam=3.0, dirichlet=bc)
+        U = torch.tensor(W.interior_field([nel + p] * 2, 3), device="cuda")
+        J = d.form_jacobian(U)
+        nJ = torch.linalg.norm(J).item()
+        row = {"nel": nel, "p": p, "nnz": d.nnz}
+        J32 = torch.empty(d.nnz, dtype=torch.float32, device="cuda")
+        for name, code in (("fp32_sumfact", iga.IGA_JAC_FP32), ("bf16_tensor", iga.IGA_JAC_BF16), ("tf32_tensor", iga.IGA_JAC_TF32)):
+            t = _ev(torch, lambda: d.form_jacobian(U, prec=code, vals=J32), reps)
+            row[name] = {"us": t * 1e3, "rel_frobenius_error_vs_fp64": (torch.linalg.norm(J32.double() - J) / nJ).item()}
+        row["fastest"] = min(("fp32_sumfact", "bf16_tensor", "tf32_tensor"), key=lambda k: row[k]["us"])
+        out.append(row)
+        d.close()
+    return out
 
 
 def learned_core(torch, iga, W, n_train=20000, n_test=2000, steps=16000, clock=None):

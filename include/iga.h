@@ -319,6 +319,13 @@ iga_status iga_batch_offsets(iga_batch_t batch, int64_t *offsets);
  * ctas_per_sm * threads_per_cta <= 2048).  Default 1 x 512.  IGA_EINVAL otherwise.
  * The autotuner in paper_1305_4452_gb300/autotune.py chooses it. */
 iga_status iga_batch_set_launch(iga_batch_t batch, int ctas_per_sm, int threads_per_cta);
+/* Work-unit shape of the persistent kernel's Gram-Schmidt dot products: each of the
+ * j+1 dots of an orthogonalisation pass is split into dot_chunks row ranges, one warp
+ * per (dot, range), their sums added in range order (0: as many ranges as keep every
+ * warp busy, at most 16).  Default 1 (one warp per dot).  Results depend on the shape
+ * only through the order of additions.  0..16, else IGA_EINVAL.  The autotuner in
+ * paper_1305_4452_gb300/autotune.py chooses it with the launch shape. */
+iga_status iga_batch_set_tiles(iga_batch_t batch, int dot_chunks);
 /* Solve every instance from the initial values in U (device, concatenated,
  * in/out) with Newton + GMRES(m, at most 64) + Jacobi (Jacobi CG with
  * opts->ksp = IGA_KSP_CG), FP64 residual and norms, FP32 sum-factorised Jacobian.  One graph launch (captured on the first call

@@ -44,7 +44,7 @@ void iga_release(iga_s *h) {
   for (int ax = 0; ax < 3; ax++) free_dir(h->ddev[ax]);
   void *ps[] = {h->rowptr, h->rp_line, h->rp_p0, h->colidx, h->weights, h->geom, h->Fe, h->Q00, h->T1, h->T2, h->Kstiff, h->Kstiff_f, h->Ebuf64, h->ts_buf,
                 h->Mred, h->Mred_f, h->J64, h->J32, h->wk, h->V, h->red, h->ctl, h->Uhost_dev,
-                h->geom32, h->tab32[0], h->tab32[1], h->tab32[2], h->Ebuf, h->z32, h->gsbar};
+                h->geom32, h->tab32[0], h->tab32[1], h->tab32[2], h->Ebuf, h->z32, h->gsbar, h->J32s};
   for (void *p : ps)
     if (p) cudaFree(p);
   if (h->ctl_host) cudaFreeHost(h->ctl_host);
@@ -413,6 +413,7 @@ static iga_status norm_host(iga_s *h, const double *x, double *out) {
 
 // Assemble the Newton Jacobian at U into h->J64 / h->J32.
 static iga_status newton_jacobian(iga_s *h, const double *U, bool f32, bool reuse, int prec) {
+  h->J32s_valid = false;  // the sliced copy no longer matches once J32 is rewritten
   if (h->inner) reuse = false;  // periodic: full assembly on the unwrapped space, then the fold
   if (prec == IGA_JAC_FD) {  // local numerical differentiation, assembled in full each step
     CK(launch_jacobian_fd(h, U, h->J64));
@@ -515,6 +516,7 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
     } else {
       st = newton_jacobian(h, U, f32, o.reuse_stiffness != 0, (int)o.jac);
       if (st != IGA_OK) return st;
+      if (f32) CK(launch_slice32(h));  // the Krylov products run on the sliced copy
     }
     IGA_LAUNCH(h, KC_VEC, (k_neg<<<eg, 256, 0, h->stream>>>(F, Ft, N)));
     // forcing term min(rtol, ||F||) (quadratic Newton), but never below half the

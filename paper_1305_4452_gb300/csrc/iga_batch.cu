@@ -1012,6 +1012,7 @@ extern "C" iga_status iga_batch_solve(iga_batch_t b, double *U, const iga_newton
   if (o.gmres_restart > BMAXM) o.gmres_restart = BMAXM;
   b->h_args->U = U;
   b->h_args->opts = o;
+  b->h_args->dot_chunks = b->dot_chunks;  // read by the graph's argument copy at every replay
   // the caller's pending work (any stream) completes before the solve reads U
   BCK(cudaDeviceSynchronize());
   if (!b->exec || b->graph_threads != b->threads || b->graph_ctas != b->ctas_per_sm) {

@@ -218,6 +218,8 @@ struct iga_s {
   // Newton / Krylov workspace
   double *J64 = nullptr;
   float *J32 = nullptr;
+  float *J32s = nullptr;       // sliced copy of J32 for the FP32 operator products (launch_slice32)
+  bool J32s_valid = false;     // J32s holds the values now in J32
   double *wk = nullptr;        // vectors: F, dU, Utrial, Ftrial, diag, z, w, ...
   double *V = nullptr;         // GMRES basis (m+1) x N
   int V_m = 0;
@@ -304,6 +306,8 @@ struct GsPartition {
 GsPartition gs_partition(int64_t N);
 cudaError_t launch_spmv64(iga_s *h, const double *vals, const double *x, double *y);
 cudaError_t launch_spmv32(iga_s *h, const float *vals, const double *x, double *y);
+// sliced copy of h->J32 (rows in slices of 32, slot-major) for the FP32 Krylov products
+cudaError_t launch_slice32(iga_s *h);
 cudaError_t launch_diag_inv(iga_s *h, const void *vals, int is_f32, double *dinv);
 cudaError_t launch_norm2(iga_s *h, const double *x, double *out_dev);
 cudaError_t launch_nan_check(iga_s *h, const double *x, double *out_dev);

@@ -101,12 +101,9 @@ __device__ __forceinline__ RowShape row_shape(const StencilRows &S, int row) {
 }
 
 // y = A x over the stencil CSR, LPR lanes per row.  Lane t of a row takes the
-// row's entries t, t+LPR, ..., CH of them per round: the round's columns are formed
-// first (a run of w0 consecutive columns per (i1, i2) offset, advanced with integer
-// arithmetic only), then its CH value and x loads are issued together, then the FMAs,
-// in entry order -- so each lane has CH loads in flight rather than one, and the sum is
-// the same as entry by entry.  Every lane reaches the shuffles.
-template <int DIM, int LPR, int CH, typename V, typename X, typename ACC>
+// row's entries t, t+LPR, ...; the column is advanced incrementally (a run of w0
+// consecutive columns per (i1, i2) offset).  Every lane reaches the shuffles.
+template <int DIM, int LPR, typename V, typename X, typename ACC>
 __global__ void __launch_bounds__(256) k_spmv_stencil(StencilRows S, const int64_t *__restrict__ rowptr,
                                                       const V *__restrict__ val, const X *__restrict__ x,
                                                       double *__restrict__ y, int N, const double *__restrict__ done) {
@@ -123,34 +120,76 @@ __global__ void __launch_bounds__(256) k_spmv_stencil(StencilRows S, const int64
     while (jj >= R.w1) { jj -= R.w1; kk++; }
     int col = (R.lo0 + ii) + (R.lo1 + jj) * S.n0 + (R.lo2 + kk) * S.n01;
     const int djj = S.n0 - R.w0, dkk = S.n01 - R.w1 * S.n0;
-    for (int e0 = lane; e0 < cnt; e0 += CH * LPR) {
-      int cols[CH];
-#pragma unroll
-      for (int k = 0; k < CH; k++) {
-        cols[k] = col;
-        ii += LPR;
-        col += LPR;
-        while (ii >= R.w0) {
-          ii -= R.w0;
-          col += djj;
-          if (++jj == R.w1) { jj = 0; col += dkk; }
-        }
+#pragma unroll 4
+    for (int e = lane; e < cnt; e += LPR) {
+      acc = fma((ACC)v[e], (ACC)x[col], acc);
+      ii += LPR;
+      col += LPR;
+      while (ii >= R.w0) {
+        ii -= R.w0;
+        col += djj;
+        if (++jj == R.w1) { jj = 0; col += dkk; }
       }
-      V vv[CH];
-      X xv[CH];
-#pragma unroll
-      for (int k = 0; k < CH; k++) {
-        const bool in = e0 + k * LPR < cnt;  // past the row's end the column is not one of its own
-        vv[k] = in ? v[e0 + k * LPR] : (V)0;
-        xv[k] = in ? x[cols[k]] : (X)0;
-      }
-#pragma unroll
-      for (int k = 0; k < CH; k++) acc = fma((ACC)vv[k], (ACC)xv[k], acc);
     }
   }
 #pragma unroll
   for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, LPR);
   if (row < N && lane == 0) y[row] = (double)acc;
+}
+
+// Sliced copy of FP32 CSR values for the reduced-precision Krylov solves: rows in slices
+// of 32, slot-major within a slice.  Slot s = a + WF (b + WF c) of row A = (i0, i1, i2)
+// (WF = 2p+1, a < WF along axis 0, ...) holds the row's value for column
+// (l0 + a, l1 + b, l2 + c) when that is inside the row's stencil, else 0; it sits at
+// [(A / 32) 32 WF^DIM + 32 s + A % 32], so that one slot of a warp's 32 rows is one
+// 128-byte access.  One thread per (row, slot), the writes coalesced.
+__host__ __device__ __forceinline__ int64_t sl_index(int A, int s, int nslot) {
+  return (int64_t)(A >> 5) * 32 * nslot + 32 * s + (A & 31);
+}
+
+template <int DIM>
+__global__ void k_csr_to_sliced(StencilRows S, const int64_t *__restrict__ rowptr, const float *__restrict__ csr,
+                                float *__restrict__ sl, int N, int wf) {
+  const int nslot = DIM == 3 ? wf * wf * wf : wf * wf;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)((N + 31) / 32) * 32 * nslot;
+  if (t >= total) return;
+  const int slice = (int)(t / (32 * nslot)), rem = (int)(t % (32 * nslot));
+  const int s = rem / 32, A = slice * 32 + (rem & 31);
+  float v = 0.f;
+  if (A < N) {
+    const RowShape R = row_shape<DIM>(S, A);
+    const int a = s % wf, b = (s / wf) % wf, c = s / (wf * wf);
+    if (a < R.w0 && b < R.w1 && c < R.w2) v = csr[rowptr[A] + a + R.w0 * (b + R.w1 * c)];
+  }
+  sl[t] = v;
+}
+
+// y = A x on the sliced values, one thread per row, FP32 products and sums: each slot is
+// one coalesced load of the warp's 32 values and, for rows with complete stencils, of 32
+// consecutive x (the column of a slot is the row's own index plus a fixed offset).  A slot
+// outside a row's stencil holds 0 and reads a clamped column of the row, so it adds
+// nothing; the sum over the row's own columns runs in their CSR order.
+template <int DIM, int P>
+__global__ void __launch_bounds__(256) k_spmv_sliced(StencilRows S, const float *__restrict__ sl, const float *__restrict__ x,
+                                                     double *__restrict__ y, int N, const double *__restrict__ done) {
+  constexpr int WF = 2 * P + 1, NC = DIM == 3 ? WF : 1, NSLOT = WF * WF * NC;
+  if (done && done[0] != 0.0) return;
+  const int A = blockIdx.x * blockDim.x + threadIdx.x;
+  if (A >= N) return;
+  const RowShape R = row_shape<DIM>(S, A);
+  const float *v = sl + sl_index(A, 0, NSLOT);
+  float acc = 0.f;
+  for (int c = 0; c < NC; c++) {
+    const int cc = min(c, R.w2 - 1);
+#pragma unroll
+    for (int b = 0; b < WF; b++) {
+      const float *xr = x + R.lo0 + (int64_t)S.n0 * (R.lo1 + min(b, R.w1 - 1)) + (int64_t)S.n01 * (R.lo2 + cc);
+#pragma unroll
+      for (int a = 0; a < WF; a++) acc = fmaf(__ldcs(v + 32 * (a + WF * (b + WF * c))), xr[min(a, R.w0 - 1)], acc);
+    }
+  }
+  y[A] = (double)acc;
 }
 
 __global__ void k_cvt_f32(const double *__restrict__ x, float *__restrict__ y, int64_t N, const double *__restrict__ done) {
@@ -658,11 +697,12 @@ static StencilRows stencil_rows(const iga_s *h) {
   return S;
 }
 
-// FP32-value operator product used by the mixed-precision Newton: x -> FP32 copy,
-// FP32 SpMV with FP32 sums (8 lanes x 4 B = one 32 B sector per row and step).  The
-// operator only steers Newton (its values are rounded already); its FP32 sums limit the
-// linear residual to the FP32 level, which the forcing floor of the reduced-precision
-// Jacobians stays above.
+// FP32-value operator product used by the mixed-precision Newton: x -> FP32 copy, then
+// the product on the sliced copy of the values when one is current (h->J32s, made by
+// launch_slice32 for h->J32), else on the CSR values (8 lanes x 4 B = one 32 B sector
+// per row and step).  The operator only steers Newton (its values are rounded already);
+// its FP32 sums limit the linear residual to the FP32 level, which the forcing floor of
+// the reduced-precision Jacobians stays above.
 static cudaError_t spmv_f32_launch(iga_s *h, const float *vals, const double *x, double *y, const double *done) {
   if (h->inner) return periodic_spmv(h, vals, 1, x, y, done);
   int eg = (int)((h->N + 255) / 256);
@@ -670,12 +710,52 @@ static cudaError_t spmv_f32_launch(iga_s *h, const float *vals, const double *x,
   IGA_LAUNCH(h, KC_VEC, (k_cvt_f32<<<eg, 256, 0, h->stream>>>(x, h->z32, h->N, done)));
   const StencilRows S = stencil_rows(h);
   const int N = (int)h->N;
+  if (h->J32s && vals == h->J32 && h->J32s_valid) {
+    const unsigned gs = (unsigned)((N + 255) / 256);
+    if (h->dim == 3) {
+      switch (h->p) {
+        case 1: IGA_LAUNCH(h, KC_SPMV, (k_spmv_sliced<3, 1><<<gs, 256, 0, h->stream>>>(S, h->J32s, h->z32, y, N, done))); break;
+        case 2: IGA_LAUNCH(h, KC_SPMV, (k_spmv_sliced<3, 2><<<gs, 256, 0, h->stream>>>(S, h->J32s, h->z32, y, N, done))); break;
+        case 3: IGA_LAUNCH(h, KC_SPMV, (k_spmv_sliced<3, 3><<<gs, 256, 0, h->stream>>>(S, h->J32s, h->z32, y, N, done))); break;
+        default: IGA_LAUNCH(h, KC_SPMV, (k_spmv_sliced<3, 4><<<gs, 256, 0, h->stream>>>(S, h->J32s, h->z32, y, N, done))); break;
+      }
+    } else {
+      switch (h->p) {
+        case 1: IGA_LAUNCH(h, KC_SPMV, (k_spmv_sliced<2, 1><<<gs, 256, 0, h->stream>>>(S, h->J32s, h->z32, y, N, done))); break;
+        case 2: IGA_LAUNCH(h, KC_SPMV, (k_spmv_sliced<2, 2><<<gs, 256, 0, h->stream>>>(S, h->J32s, h->z32, y, N, done))); break;
+        case 3: IGA_LAUNCH(h, KC_SPMV, (k_spmv_sliced<2, 3><<<gs, 256, 0, h->stream>>>(S, h->J32s, h->z32, y, N, done))); break;
+        default: IGA_LAUNCH(h, KC_SPMV, (k_spmv_sliced<2, 4><<<gs, 256, 0, h->stream>>>(S, h->J32s, h->z32, y, N, done))); break;
+      }
+    }
+    return cudaGetLastError();
+  }
   unsigned grid = (unsigned)(((int64_t)N * 8 + 255) / 256);
   if (h->dim == 3)
-    IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<3, 8, 4, float, float, float><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, h->z32, y, N, done)));
+    IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<3, 8, float, float, float><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, h->z32, y, N, done)));
   else
-    IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<2, 8, 4, float, float, float><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, h->z32, y, N, done)));
+    IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<2, 8, float, float, float><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, h->z32, y, N, done)));
   return cudaGetLastError();
+}
+
+// h->J32s = the sliced copy of the FP32 CSR values in h->J32 (allocated on first use)
+cudaError_t launch_slice32(iga_s *h) {
+  h->J32s_valid = false;
+  if (h->inner) return cudaSuccess;
+  const int wf = 2 * h->p + 1, nslot = h->dim == 3 ? wf * wf * wf : wf * wf;
+  const int64_t total = (h->N + 31) / 32 * 32 * (int64_t)nslot;
+  if (!h->J32s) {
+    cudaError_t ce = cudaMalloc((void **)&h->J32s, total * sizeof(float));
+    if (ce) return ce;
+  }
+  const StencilRows S = stencil_rows(h);
+  const unsigned g = (unsigned)((total + 255) / 256);
+  if (h->dim == 3)
+    IGA_LAUNCH(h, KC_VEC, (k_csr_to_sliced<3><<<g, 256, 0, h->stream>>>(S, h->rowptr, h->J32, h->J32s, (int)h->N, wf)));
+  else
+    IGA_LAUNCH(h, KC_VEC, (k_csr_to_sliced<2><<<g, 256, 0, h->stream>>>(S, h->rowptr, h->J32, h->J32s, (int)h->N, wf)));
+  cudaError_t ce = cudaGetLastError();
+  if (!ce) h->J32s_valid = true;
+  return ce;
 }
 
 template <typename V>
@@ -688,9 +768,9 @@ static cudaError_t spmv_launch(iga_s *h, const V *vals, const double *x, double 
   const int N = (int)h->N;
   unsigned grid = (unsigned)(((int64_t)N * 4 + 255) / 256);
   if (h->dim == 3)
-    IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<3, 4, 4, V, double, double><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, x, y, N, done)));
+    IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<3, 4, V, double, double><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, x, y, N, done)));
   else
-    IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<2, 4, 4, V, double, double><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, x, y, N, done)));
+    IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<2, 4, V, double, double><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, x, y, N, done)));
   return cudaGetLastError();
 }
 

@@ -26,7 +26,7 @@ EXPORTS = ["iga_create", "iga_set_boundary_value", "iga_set_lambda", "iga_get_pa
            "iga_nn_forward", "iga_nn_loss_grad", "iga_nn_adam_step", "iga_nn_destroy", "iga_nn_last_error",
            "iga_nn_set_h1_weight", "iga_apply_jacobian", "iga_apply_jacobian_mf", "iga_form_jacobian_diagonal",
            "iga_form_residual_ts", "iga_form_jacobian_ts", "iga_ts_alpha_step", "iga_measure_peaks",
-           "iga_set_wait_limit", "iga_inject_stall"]
+           "iga_set_wait_limit", "iga_inject_stall", "iga_batch_set_tiles"]
 
 KERNEL_CLASSES = ["geometry", "residual_element", "residual_gather", "q00", "jac_stage1", "jac_stage2", "jac_final",
                   "spmv", "gs_orth", "gmres_scalar", "vector", "combine", "pattern", "elem_tc", "elem_gather"]
@@ -371,6 +371,7 @@ def _batch_lib():
         L.iga_batch_create.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.POINTER(vp)]
         L.iga_batch_offsets.argtypes = [vp, vp]
         L.iga_batch_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+        L.iga_batch_set_tiles.argtypes = [vp, ctypes.c_int]
         L.iga_batch_solve.argtypes = [vp, vp, ctypes.POINTER(IgaNewtonOpts), ctypes.POINTER(IgaBatchReport)]
         L.iga_batch_destroy.argtypes = [vp]
         L.iga_batch_destroy.restype = None
@@ -429,6 +430,14 @@ class Batch:
         (256 or 512)."""
         L = _batch_lib()
         rc = L.iga_batch_set_launch(self.h, int(ctas_per_sm), int(threads))
+        if rc != IGA_OK:
+            raise IgaError(rc, L.iga_batch_last_error(self.h).decode())
+
+    def set_tiles(self, dot_chunks):
+        """Work unit of the Gram-Schmidt dots: row chunks per dot (0: enough to keep every
+        warp busy; 1..16)."""
+        L = _batch_lib()
+        rc = L.iga_batch_set_tiles(self.h, int(dot_chunks))
         if rc != IGA_OK:
             raise IgaError(rc, L.iga_batch_last_error(self.h).decode())
 

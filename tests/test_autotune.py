@@ -18,20 +18,26 @@ def test_cache_roundtrip(tmp_path):
 
 
 class _FakeBatch:
-    """Stands in for iga.Batch: a solve takes a fixed time per launch shape."""
+    """Stands in for iga.Batch: a solve takes a fixed time per launch shape, minus a
+    saving per Gram-Schmidt dot shape."""
 
-    def __init__(self, cost_ms):
+    def __init__(self, cost_ms, dot_saving_ms=None):
         self.cost_ms = cost_ms
+        self.dot_saving_ms = dot_saving_ms or {}
         self.shape = None
+        self.dots = 1
         self.launches = []
 
     def set_launch(self, ctas, threads=512):
         self.shape = (ctas, threads)
         self.launches.append(self.shape)
 
+    def set_tiles(self, dots):
+        self.dots = dots
+
     def solve(self, U, opts=None, check=True):
         import time
-        time.sleep(self.cost_ms[self.shape] / 1e3)
+        time.sleep(max(0.0, self.cost_ms[self.shape] - self.dot_saving_ms.get(self.dots, 0.0)) / 1e3)
         U.add_(1.0)  # the solve changes U; the tuner restores it before each timing
         return {}
 
@@ -48,7 +54,21 @@ def test_tune_picks_the_fastest_shape_restores_u_and_caches_it(tmp_path):
     assert (r["ctas_per_sm"], r["threads"]) == (1, 512) and not r["cached"]
     assert b.shape == (1, 512) and set(b.launches[:-1]) == set(autotune.CANDIDATES)
     assert torch.equal(U, torch.zeros(4, dtype=torch.float64))
-    assert set(r["times_ms"]) == {"%dx%d" % s for s in autotune.CANDIDATES}
+    assert {"%dx%d/dots1" % s for s in autotune.CANDIDATES} <= set(r["times_ms"])
+    assert r["dot_chunks"] == 1 and b.dots == 1
     b2 = _FakeBatch(cost)
     r2 = autotune.tune(b2, ins, U, cache_path=cache)
     assert r2["cached"] and (r2["ctas_per_sm"], r2["threads"]) == (1, 512) and b2.launches == [(1, 512)]
+
+
+def test_tune_picks_the_dot_shape_on_the_best_launch_shape(tmp_path):
+    torch = __import__("pytest").importorskip("torch")
+    cost = {s: 40.0 for s in autotune.CANDIDATES}
+    cost[(2, 256)] = 20.0
+    ins = [{"nel": 24, "p": 3, "lam": 2.0}] * 2
+    U = torch.zeros(3, dtype=torch.float64)
+    b = _FakeBatch(cost, {4: 12.0})
+    r = autotune.tune(b, ins, U, cache_path=str(tmp_path / "c.json"))
+    assert (r["ctas_per_sm"], r["threads"], r["dot_chunks"]) == (2, 256, 4)
+    assert b.shape == (2, 256) and b.dots == 4
+    assert set(r["times_ms"]) >= {"2x256/dots%d" % d for d in autotune.DOT_CANDIDATES}
