@@ -495,7 +495,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="0 skips the CPU baseline (the oracle on all host cores)")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64-vs-mixed and learned-start comparisons")
     ap.add_argument("--workload", default="annulus64",
-                    choices=["annulus64", "bratu16", "cube_mixed", "batch512", "learned64", "nn64", "fdjac", "genalpha", "periodic64", "mixed64"],
+                    choices=["annulus64", "bratu16", "cube_mixed", "batch512", "learned64", "nn64", "fdjac", "genalpha", "periodic64",
+                             "mixed64", "newton64_mixed"],
                     help="annulus64 is the benchmark line; the others print their configuration's line")
     args = ap.parse_args()
     if args.workload != "annulus64" and args.impl == "ours":

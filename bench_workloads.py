@@ -1,6 +1,7 @@
 """Benchmark lines for the configurations other than the headline one.
 
-    python bench.py --workload {bratu16, cube_mixed, batch512, learned64, nn64, fdjac, genalpha, periodic64, mixed64}
+    python bench.py --workload {bratu16, cube_mixed, batch512, learned64, nn64, fdjac, genalpha, periodic64, mixed64,
+                                newton64_mixed}
 
 Each prints one JSON line with the keys of the headline line (metric, value,
 unit, config, clocks, e2e-style extras) for one configuration:
@@ -24,6 +25,8 @@ unit, config, clocks, e2e-style extras) for one configuration:
   periodic64  Sec. 2.4: 3D Bratu, lambda = 2, on the unit cube 64^3 cubic, C^2 periodic in
               x and y, Dirichlet faces in z: residual and Jacobian assembly (unwrapped
               space plus the fold onto the wrapped functions) and Newton solves.
+  newton64_mixed  Newton on the 64^3 quadratic cube with the FP64 and the reduced-precision
+              Jacobians, GMRES and CG (the main line's 128^3 comparison at a profiler size).
   mixed64     the reduced-precision Jacobians alone on the 64^3 quadratic cube (lambda = 2,
               U ~ U[-0.1, 0.1]): BF16 and TF32 element matrices (tcgen05 GEMM across
               elements) and the FP32 sum factorisation, per-kernel-class times, error
@@ -549,5 +552,40 @@ def mixed64(torch, iga, W, clock, nel=64, p=2):
                  dtype="bf16")
 
 
+def newton64_mixed(torch, iga, W, clock, nel=64, p=2, reps=3):
+    """Newton solves (lambda = 2, U = 0 to ||F|| <= 1e-10) of the 64^3 quadratic cube with the
+    FP64 Jacobian and with the FP32 / BF16 reduced-precision ones, GMRES and CG: the
+    128^3 comparison of the main line at a size a profiler capture can take (CSR values
+    136 MB FP32, above the 126 MB L2)."""
+    bc = {(a, s): 0.0 for a in range(3) for s in range(2)}
+    d = iga.Discretization(3, p, nel=nel, lam=2.0, dirichlet=bc)
+    U = torch.zeros(d.N, dtype=torch.float64, device="cuda")
+    out = {"dofs": d.N, "nnz": d.nnz}
+    clock.start()
+    for ksp_name, ksp in (("gmres", iga.IGA_KSP_GMRES), ("cg", iga.IGA_KSP_CG)):
+        for name, code in (("fp64", iga.IGA_FP64), ("fp32", iga.IGA_JAC_FP32), ("bf16", iga.IGA_JAC_BF16)):
+            o = iga.newton_defaults()
+            o.jac, o.ksp = code, ksp
+            U.zero_()
+            d.solve_newton(U, o)
+            best, rep = 1e30, None
+            for _ in range(reps):
+                U.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rep = d.solve_newton(U, o)
+                best = min(best, time.perf_counter() - t0)
+            out["%s_%s" % (name, ksp_name)] = {"ms": best * 1e3, "solves_per_s": 1.0 / best, "newton_its": rep.newton_its,
+                                               "krylov_its": rep.krylov_its, "fnorm": rep.fnorm}
+    ck = clock.stop()
+    d.close()
+    for ksp_name in ("gmres", "cg"):
+        for name in ("fp32", "bf16"):
+            k = "%s_%s" % (name, ksp_name)
+            out[k]["speedup_vs_fp64_same_krylov"] = out[k]["solves_per_s"] / out["fp64_%s" % ksp_name]["solves_per_s"]
+    return _line(out["fp32_cg"]["solves_per_s"], "solves/s", "bratu3d_cube_64cubed_p2_lambda2_newton_fp64_vs_mixed",
+                 {"cases": out}, ck)
+
+
 WORKLOADS = {"bratu16": bratu16, "cube_mixed": cube_mixed, "batch512": batch512, "learned64": learned64, "nn64": nn64, "fdjac": fdjac,
-             "genalpha": genalpha, "periodic64": periodic64, "mixed64": mixed64}
+             "genalpha": genalpha, "periodic64": periodic64, "mixed64": mixed64, "newton64_mixed": newton64_mixed}

@@ -697,6 +697,12 @@ static StencilRows stencil_rows(const iga_s *h) {
   return S;
 }
 
+// The sliced product runs one thread per row: it needs many rows to fill the GPU, and
+// its sequential FP32 row sums lose accuracy with long rows ((2p+1)^3 = 729 slots at
+// p = 4).  It serves p <= 2 and meshes of at least half a million rows; the CSR product
+// (8 lanes per row, a tree over the lanes) serves the rest.
+static bool slice_pays(const iga_s *h) { return h->p <= 2 || h->N >= 500000; }
+
 // FP32-value operator product used by the mixed-precision Newton: x -> FP32 copy, then
 // the product on the sliced copy of the values when one is current (h->J32s, made by
 // launch_slice32 for h->J32), else on the CSR values (8 lanes x 4 B = one 32 B sector
@@ -710,7 +716,7 @@ static cudaError_t spmv_f32_launch(iga_s *h, const float *vals, const double *x,
   IGA_LAUNCH(h, KC_VEC, (k_cvt_f32<<<eg, 256, 0, h->stream>>>(x, h->z32, h->N, done)));
   const StencilRows S = stencil_rows(h);
   const int N = (int)h->N;
-  if (h->J32s && vals == h->J32 && h->J32s_valid) {
+  if (h->J32s && vals == h->J32 && h->J32s_valid && slice_pays(h)) {
     const unsigned gs = (unsigned)((N + 255) / 256);
     if (h->dim == 3) {
       switch (h->p) {
@@ -740,7 +746,7 @@ static cudaError_t spmv_f32_launch(iga_s *h, const float *vals, const double *x,
 // h->J32s = the sliced copy of the FP32 CSR values in h->J32 (allocated on first use)
 cudaError_t launch_slice32(iga_s *h) {
   h->J32s_valid = false;
-  if (h->inner) return cudaSuccess;
+  if (h->inner || !slice_pays(h)) return cudaSuccess;
   const int wf = 2 * h->p + 1, nslot = h->dim == 3 ? wf * wf * wf : wf * wf;
   const int64_t total = (h->N + 31) / 32 * 32 * (int64_t)nslot;
   if (!h->J32s) {

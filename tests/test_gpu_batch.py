@@ -147,3 +147,29 @@ def test_batch_rejects_invalid_launch_shapes(I):
             b.set_launch(ctas, threads)
     b.set_launch(4, 512)
     b.close()
+
+
+def test_batch_dot_work_units_give_the_same_solutions(I):
+    """The work-unit shape of the Gram-Schmidt dots (row chunks per dot) changes only the
+    order of additions: every shape solves every instance, the solutions agree to the
+    Newton tolerance, each shape is deterministic, and out-of-range shapes are rejected."""
+    ins = instances(10, seed=13, nmin=12, nmax=40)
+    b = I.Batch(ins)
+    o = I.newton_defaults()
+    o.gmres_restart = 30
+    sols = {}
+    for dots in (1, 3, 0, 16):
+        b.set_tiles(dots)
+        U = torch.zeros(b.total, dtype=torch.float64, device="cuda")
+        rep = b.solve(U, o)
+        assert rep["solved"] == len(ins)
+        U2 = torch.zeros_like(U)
+        b.solve(U2, o)
+        assert torch.equal(U, U2)
+        sols[dots] = U
+    for dots in (3, 0, 16):
+        assert torch.abs(sols[dots] - sols[1]).max().item() <= 1e-7
+    for bad in (-1, 17):
+        with pytest.raises(I.IgaError):
+            b.set_tiles(bad)
+    b.close()
