@@ -18,12 +18,12 @@ def test_cache_roundtrip(tmp_path):
 
 
 class _FakeBatch:
-    """Stands in for iga.Batch: a solve takes a fixed time per launch shape, minus a
-    saving per Gram-Schmidt dot shape."""
+    """Stands in for iga.Batch: a solve takes a fixed time per launch shape, plus a
+    change per Gram-Schmidt dot shape (negative: a saving)."""
 
-    def __init__(self, cost_ms, dot_saving_ms=None):
+    def __init__(self, cost_ms, dot_delta_ms=None):
         self.cost_ms = cost_ms
-        self.dot_saving_ms = dot_saving_ms or {}
+        self.dot_delta_ms = dot_delta_ms if dot_delta_ms is not None else {0: 10.0, 2: 10.0, 4: 10.0}
         self.shape = None
         self.dots = 1
         self.launches = []
@@ -37,7 +37,7 @@ class _FakeBatch:
 
     def solve(self, U, opts=None, check=True):
         import time
-        time.sleep(max(0.0, self.cost_ms[self.shape] - self.dot_saving_ms.get(self.dots, 0.0)) / 1e3)
+        time.sleep(max(0.0, self.cost_ms[self.shape] + self.dot_delta_ms.get(self.dots, 0.0)) / 1e3)
         U.add_(1.0)  # the solve changes U; the tuner restores it before each timing
         return {}
 
@@ -67,7 +67,7 @@ def test_tune_picks_the_dot_shape_on_the_best_launch_shape(tmp_path):
     cost[(2, 256)] = 20.0
     ins = [{"nel": 24, "p": 3, "lam": 2.0}] * 2
     U = torch.zeros(3, dtype=torch.float64)
-    b = _FakeBatch(cost, {4: 12.0})
+    b = _FakeBatch(cost, {0: 5.0, 2: 5.0, 4: -12.0})
     r = autotune.tune(b, ins, U, cache_path=str(tmp_path / "c.json"))
     assert (r["ctas_per_sm"], r["threads"], r["dot_chunks"]) == (2, 256, 4)
     assert b.shape == (2, 256) and b.dots == 4
