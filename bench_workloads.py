@@ -201,6 +201,8 @@ def batch512(torch, iga, W, clock):
         o.ksp = ksp
         o.gmres_restart = 30
         # launch shape, and for GMRES the work unit of its Gram-Schmidt dots, for this mix
+        # (timed from the zero start, as the solves below)
+        U.zero_()
         res["autotune"][label] = autotune.tune(b, ins, U, o, retime=True)
         best, r = 1e30, None
         for _ in range(3):

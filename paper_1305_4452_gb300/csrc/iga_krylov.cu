@@ -286,10 +286,16 @@ __device__ void block_dots(const double *__restrict__ Vb, int64_t ld, int jp1, i
       const int i = it / R, c = it - i * R;
       const int r0 = c * clen, r1 = min(cnt, r0 + clen);
       const double *v = Vb + (size_t)i * ld + a;
-      double acc = 0.0;
-#pragma unroll 4
-      for (int r = r0 + lane; r < r1; r += 32) acc = fma(v[r], ws[r], acc);
-      acc = warp_sum(acc);
+      // two independent chains (rows r0+lane+64k and r0+lane+32+64k), added at the end
+      double acc = 0.0, acc2 = 0.0;
+      int r = r0 + lane;
+#pragma unroll 2
+      for (; r + 32 < r1; r += 64) {
+        acc = fma(v[r], ws[r], acc);
+        acc2 = fma(v[r + 32], ws[r + 32], acc2);
+      }
+      if (r < r1) acc = fma(v[r], ws[r], acc);
+      acc = warp_sum(acc + acc2);
       if (lane == 0) dp[warp] = acc;
     }
     __syncthreads();
@@ -498,6 +504,34 @@ __device__ bool gs_grid_sync(unsigned *bar) {
   return ok_s != 0;
 }
 
+// ws[r] -= sum_{i < jp1} h[i] V[i][a + r] for the block's rows r < cnt, two rows per
+// thread and step (two independent FMA chains sharing each h[i]); returns the thread's
+// sum of the updated ws[r]^2 (rows in the order visited).
+__device__ __forceinline__ double gs_update_rows(const double *__restrict__ Vb, int64_t ld, int jp1, int64_t a, int cnt,
+                                                 const double *h, double *ws) {
+  const int T = blockDim.x;
+  double sq = 0.0;
+  for (int r = threadIdx.x; r < cnt; r += 2 * T) {
+    const int r2 = r + T;
+    const bool two = r2 < cnt;
+    double v = ws[r], v2 = two ? ws[r2] : 0.0;
+    const double *c1 = Vb + a + r, *c2 = Vb + a + (two ? r2 : r);
+#pragma unroll 4
+    for (int i = 0; i < jp1; i++) {
+      const double hi = h[i];
+      v = fma(-hi, c1[(size_t)i * ld], v);
+      v2 = fma(-hi, c2[(size_t)i * ld], v2);
+    }
+    ws[r] = v;
+    sq = fma(v, v, sq);
+    if (two) {
+      ws[r2] = v2;
+      sq = fma(v2, v2, sq);
+    }
+  }
+  return sq;
+}
+
 // The three Gram-Schmidt passes and the end of the iteration (k_gs_pass<1..3> and
 // k_gs_finish) as one kernel: classical Gram-Schmidt applied twice to w = A z_j against
 // V_0..V_j, the new column of H, v_{j+1} = w / ||w||, z = dinv .* v_{j+1} and the Givens
@@ -541,15 +575,7 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_fused(const double *__restric
   // phase 2
   block_sum_cols(P1, gridDim.x, jp1, hs);
   {
-    double sq = 0.0;
-    for (int r = threadIdx.x; r < cnt; r += T) {
-      double v = ws[r];
-      const double *c = Vb + a + r;
-#pragma unroll 4
-      for (int i = 0; i < jp1; i++) v = fma(-hs[i], c[(size_t)i * ld], v);
-      ws[r] = v;
-      sq = fma(v, v, sq);
-    }
+    double sq = gs_update_rows(Vb, ld, jp1, a, cnt, hs, ws);
     sq = block_sum(sq, sh);
     if (threadIdx.x == 0) P2[(size_t)jp1 * gridDim.x + blockIdx.x] = sq;
   }
@@ -562,15 +588,7 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_fused(const double *__restric
     double s2 = h2[jp1];
     for (int i = 0; i < jp1; i++) s2 = fma(-h2[i], h2[i], s2);
     const bool direct = !(s2 > 0.5 * h2[jp1]);
-    double sq = 0.0;
-    for (int r = threadIdx.x; r < cnt; r += T) {
-      double v = ws[r];
-      const double *c = Vb + a + r;
-#pragma unroll 4
-      for (int i = 0; i < jp1; i++) v = fma(-h2[i], c[(size_t)i * ld], v);
-      ws[r] = v;
-      sq = fma(v, v, sq);
-    }
+    double sq = gs_update_rows(Vb, ld, jp1, a, cnt, h2, ws);
     if (direct) {  // severe cancellation in the second pass: sum ||w||^2 itself
       sq = block_sum(sq, sh);
       if (threadIdx.x == 0) P1[blockIdx.x] = sq;
