@@ -819,10 +819,11 @@ cudaError_t launch_diag_inv(iga_s *h, const void *vals, int is_f32, double *dinv
 GsPartition gs_partition(int64_t N) {
   // one block per SM (the passes re-sum the previous pass's per-block partials in
   // every block, so few blocks keep that cheap); more when a block would exceed
-  // 16384 rows (128 KB of shared memory for w)
+  // 16384 rows (128 KB of shared memory for w); fewer for small systems, so that a
+  // block keeps at least about one row per thread (a 16^2 mesh: one block)
   GsPartition g;
   int64_t nb = (N + 16383) / 16384;
-  if (nb < 152) nb = 152;
+  if (nb < 152) nb = std::min<int64_t>(152, std::max<int64_t>(nb, (N + 1023) / 1024));
   g.per = (int)((N + nb - 1) / nb);
   if (g.per < 1) g.per = 1;
   g.nb = (int)((N + g.per - 1) / g.per);

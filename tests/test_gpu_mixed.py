@@ -225,3 +225,24 @@ def test_bounded_pipeline_wait_gives_up_and_the_next_call_is_correct(I):
     assert disc.solve_newton(Us, o).status == 0
     assert L.iga_set_wait_limit(disc.h, 0.0) == I.IGA_EINVAL
     disc.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_newton_with_the_sliced_fp32_product_reaches_the_oracle_solution(I, prec):
+    """3D quadratic (p <= 2: the Krylov products run on the sliced copy of the FP32
+    Jacobian), rows on every face: Newton reaches ||F|| <= 1e-10 and the oracle's residual
+    at the GPU's solution meets it too; GMRES and CG agree."""
+    disc, prob, n = pair(I, 3, 2, (14, 11, 9), 2.5)
+    sols = []
+    for ksp in (I.IGA_KSP_GMRES, I.IGA_KSP_CG):
+        U = torch.zeros(disc.N, dtype=torch.float64, device="cuda")
+        o = I.newton_defaults()
+        o.jac = I.IGA_JAC_FP32 if prec == "fp32" else I.IGA_JAC_BF16
+        o.ksp = ksp
+        rep = disc.solve_newton(U, o)
+        assert rep.status == 0 and rep.fnorm <= 1e-10
+        Uh = U.cpu().numpy()
+        assert np.linalg.norm(prob.residual(Uh)) <= 1.5e-10
+        sols.append(Uh)
+    assert np.abs(sols[0] - sols[1]).max() <= 1e-8
+    disc.close()
