@@ -538,9 +538,7 @@ cudaError_t launch_wgrad(const WgradArgs &a, cudaStream_t stream) {
 // overhang the grid compute rows that the epilogue does not store.
 // ---------------------------------------------------------------------------
 constexpr int TMA_THREADS = 32 * (CONV_EPI_WARPS + 2);  // + producer warp + MMA warp
-constexpr int TMA_STAGES = 9;  // one per tap: a tile's nine boxes occupy the nine stages
-constexpr int TMA_GROUP = 3;   // taps per commit: the stages are released three at a time
-constexpr int TMA_NGROUPS = TMA_STAGES / TMA_GROUP;
+constexpr int TMA_STAGES = 8;
 constexpr int TMA_BX = 16, TMA_BY = 8;
 
 template <int NOUT>
@@ -551,7 +549,7 @@ struct TmaSmem {
   static constexpr uint32_t A0 = 0;                        // stages first (1024-aligned)
   static constexpr uint32_t W0 = TMA_STAGES * A_BYTES;
   static constexpr uint32_t BAR = W0 + W_BYTES;
-  static constexpr uint32_t BIAS = BAR + 8 * (TMA_STAGES + TMA_NGROUPS + 4) + 16;
+  static constexpr uint32_t BIAS = BAR + 8 * (2 * TMA_STAGES + 4) + 16;
   static constexpr uint32_t TOTAL = BIAS + 4 * NOUT + 1024;  // + alignment slack
   static constexpr uint32_t TMEM_COLS = 2 * NOUT < 32 ? 32 : 2 * NOUT;
 };
@@ -565,15 +563,14 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) k_conv_tma(const __grid_consta
   uint8_t *As = sm + SM::A0;
   uint8_t *Ws = sm + SM::W0;
   uint64_t *full = reinterpret_cast<uint64_t *>(sm + SM::BAR);
-  uint64_t *empty = full + S;  // one per group of TMA_GROUP stages
-  uint64_t *accf = empty + TMA_NGROUPS;
+  uint64_t *empty = full + S;
+  uint64_t *accf = empty + S;
   uint64_t *acce = accf + 2;
   uint32_t *slot = reinterpret_cast<uint32_t *>(acce + 2);
   volatile int *abort_s = reinterpret_cast<volatile int *>(slot + 1);
   float *bias_s = reinterpret_cast<float *>(sm + SM::BIAS);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int PRODUCER = CONV_EPI_WARPS, MMA = CONV_EPI_WARPS + 1;
-  static_assert(S == 9 && S % TMA_GROUP == 0, "one stage per tap, whole groups");
   const int TXN = (a.W + TMA_BX - 1) / TMA_BX, TYN = (a.H + TMA_BY - 1) / TMA_BY;
   const int nimg = a.P / (a.H * a.W);
   const int ntiles = nimg * TXN * TYN;
@@ -592,9 +589,10 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) k_conv_tma(const __grid_consta
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int i = 0; i < S; i++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(full + i)) : "memory");
-    for (int i = 0; i < TMA_NGROUPS; i++)
+    for (int i = 0; i < S; i++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(full + i)) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(empty + i)) : "memory");
+    }
     for (int i = 0; i < 2; i++) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(accf + i)) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(acce + i)), "n"(32 * CONV_EPI_WARPS) : "memory");
@@ -612,10 +610,8 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) k_conv_tma(const __grid_consta
   if (warp == PRODUCER) {
     if ((tid & 31) == 0) {
       for (int it = 0; it < total_it; it++) {
-        const int s = it % S;  // == the tap
-        // a group's three stages are free once the previous tile's MMAs of that group (one
-        // commit, the tl-th to the group's barrier) have completed
-        if (it >= S && s % TMA_GROUP == 0 && !mbar_wait(su32(empty + s / TMA_GROUP), ((it / S) - 1) & 1, abort_s)) {
+        const int s = it % S;
+        if (it >= S && !mbar_wait(su32(empty + s), ((it / S) - 1) & 1, abort_s)) {
           atomicExch(a.err, 1);
           *abort_s = 1;
           break;
@@ -639,7 +635,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) k_conv_tma(const __grid_consta
     if ((tid & 31) == 0) {
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NOUT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
       const uint64_t adesc0 = sdesc_sw128(su32(As)), bdesc0 = sdesc(su32(Ws), SM::LBO_W, 128);
-      int last = -1;  // last iteration whose MMAs were issued
+      int last = -1;
       for (int it = 0; it < total_it; it++) {
         const int s = it % S, tl = it / 9, tap = it - tl * 9, buf = tl & 1;
         if (tap == 0 && tl >= 2 && !mbar_wait(su32(acce + buf), ((tl / 2) - 1) & 1, abort_s)) {
@@ -666,26 +662,14 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) k_conv_tma(const __grid_consta
               "l"(ad0 + 2 * k), "l"(bd0 + (uint64_t)((k * 2 * SM::LBO_W) >> 4)), "r"(idesc), "r"(acc)
               : "memory");
         }
-        last = it;
-        // one commit per group of taps releases the group's stages
-        if (tap % TMA_GROUP == TMA_GROUP - 1)
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                           su32(empty + tap / TMA_GROUP))
-                       : "memory");
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(empty + s))
+                     : "memory");
         if (tap == 8)
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(accf + buf))
                        : "memory");
+        last = it;
       }
-      // after a failure, let the MMAs already issued finish before the memory is freed: the
-      // last issued tap's group gets its commit (if it has not had it) and that commit, which
-      // covers every earlier MMA, is waited for (bounded)
-      if (*abort_s && last >= 0) {
-        const int ltap = last % 9, ltl = last / 9, g = ltap / TMA_GROUP;
-        if (ltap % TMA_GROUP != TMA_GROUP - 1)
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(empty + g))
-                       : "memory");
-        mbar_wait(su32(empty + g), ltl & 1, nullptr);
-      }
+      if (*abort_s && last >= 0) mbar_wait(su32(empty + last % S), (last / S) & 1, nullptr);
     }
     __syncwarp();
   } else {
