@@ -59,3 +59,25 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
     assert bench.run_reference(argparse.Namespace(gpus=2, steps=1, warmup=0)) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_prints_one_measured_line():
+    """bench.py --impl reference on a tiny mesh (CPU): one JSON line with impl, value,
+    the oracle's thread count, an e2e entry and a step time that is the step's own wall
+    time (steps x ms_per_step fits in the run)."""
+    import json
+    import subprocess
+    import sys
+    import time
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    t0 = time.time()
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--nel", "4",
+                          "--steps", "2", "--warmup", "3"], capture_output=True, text=True, check=True, timeout=600)
+    wall = time.time() - t0
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "solves/s"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["steps"] * d["ms_per_step"] / 1e3 <= wall
