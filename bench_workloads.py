@@ -298,14 +298,24 @@ def learned_core(torch, iga, W, n_train=20000, n_test=2000, steps=16000, clock=N
     del x, tgt, Utr
     if clock is not None:
         clock.start()
-    # held-out: batched Newton from zero and from the network's guess (inference timed)
+    # held-out: batched Newton from zero and from the network's guess (inference timed).
+    # Inference runs the trained weights on all held-out fields in one call (a network
+    # handle sized for the whole set), one launch per layer instead of one per 64 fields.
     U0, r0, s0 = nn.solve_batch(test)
     xt, _ = nn.features(test)
+    inf = nn.Net(nel + 2, nel + 2, hidden=64, max_batch=len(test), seed=0)
+    inf.set_params(net.get_params())
+    inf.forward(xt[:64], mask)  # first call outside the clock (module load, tensor maps)
     torch.cuda.synchronize()
     ti = time.perf_counter()
-    guess = torch.cat([net.forward(xt[a:a + 64], mask) for a in range(0, len(test), 64)])
+    guess = inf.forward(xt, mask)
     torch.cuda.synchronize()
     infer_s = time.perf_counter() - ti
+    # the guess does not depend on the call's batch size (a field's convolutions read only
+    # its own pixels); checked against 64-field calls on the first 256 fields
+    g64 = torch.cat([net.forward(xt[a:a + 64], mask) for a in range(0, min(len(test), 256), 64)])
+    guess_batch_check = float(torch.abs(g64 - guess[:g64.shape[0]]).max().item())
+    inf.close()
     U1, r1, s1 = nn.solve_batch(test, U0=guess.double().cpu().numpy().reshape(len(test), -1))
     ok = (r0["status"] == 0) & (r1["status"] == 0)
     # one-at-a-time plain FP64 Newton (GMRES + Jacobi, zero start) on a sample of the test fields
@@ -336,6 +346,8 @@ def learned_core(torch, iga, W, n_train=20000, n_test=2000, steps=16000, clock=N
         "zero_start": {"solves_per_s": zero, "newton_its_mean": float(r0["newton_its"][ok].mean()),
                        "krylov_its_mean": float(r0["krylov_its"][ok].mean())},
         "nn_start": {"solves_per_s": nn_start, "inference_s": infer_s, "solve_s": s1,
+                     "inference": "one forward call over all %d fields" % n_test,
+                     "max_abs_diff_vs_64_field_calls": guess_batch_check,
                      "newton_its_mean": float(r1["newton_its"][ok].mean()), "krylov_its_mean": float(r1["krylov_its"][ok].mean())},
         "speedup_nn_vs_zero_start": nn_start / zero,
         "plain_fp64_single": {"solves_per_s": nsamp / tp, "newton_its_mean": float(np.mean(its_plain)), "sample": nsamp},
