@@ -463,82 +463,101 @@ __global__ void __launch_bounds__(TPB) k_gather_rows(DirArgs d0, DirArgs d1, Dir
                                                      int64_t N) {
   constexpr int N1 = P + 1, NEN = ipow3<DIM>(N1), RMAX = (2 * P + 1) * (2 * P + 1);
   constexpr int NB = N1 * N1;  // functions of an element in one axis-2 slice (2D: all)
+  constexpr int LD = TPB + 1;  // accumulator stride: conflict-free by thread and by column
   constexpr bool TAB_SMEM = NEN * NEN * 8 <= 8 * 1024;  // p = 2: small enough not to cost occupancy
-  extern __shared__ float acc_all[];  // [RMAX][TPB], then the (pk, column shift) table for p <= 3
+  extern __shared__ float acc_all[];  // [RMAX][TPB + 1], then the (pk, column shift) table for p <= 3
+  __shared__ int64_t r0_s[TPB];       // each row slice's first CSR position (-1: nothing to store)
+  __shared__ int len_s[TPB];
   const int t = threadIdx.x;
   const int2 *gtab = gtab_g;
   if (TAB_SMEM) {
-    int2 *st = reinterpret_cast<int2 *>(acc_all + RMAX * TPB);
+    int2 *st = reinterpret_cast<int2 *>(acc_all + RMAX * LD);
     for (int k = t; k < NEN * NEN; k += TPB) st[k] = gtab_g[k];
     __syncthreads();
     gtab = st;
   }
   const int64_t A = (int64_t)blockIdx.x * TPB + t;
-  if (A >= N) return;
   float *acc = acc_all + t;
-  const int I0 = (int)(A % d0.n), I1 = (int)((A / d0.n) % d1.n), I2 = (DIM == 3) ? (int)(A / ((int64_t)d0.n * d1.n)) : 0;
+  const int64_t Ac = A < N ? A : N - 1;
+  const int I0 = (int)(Ac % d0.n), I1 = (int)((Ac / d0.n) % d1.n), I2 = (DIM == 3) ? (int)(Ac / ((int64_t)d0.n * d1.n)) : 0;
   const int l0 = d0.l[I0], l1 = d1.l[I1], l2 = DIM == 3 ? d2.l[I2] : 0;
   const int w0 = d0.r[I0] - l0 + 1, w1 = d1.r[I1] - l1 + 1, w2 = DIM == 3 ? d2.r[I2] - l2 + 1 : 1;
   const int s2 = DIM == 3 ? (int)blockIdx.y : 0;
-  if (s2 >= w2) return;
+  const bool active = A < N && s2 < w2;  // no early return: the block stores together at the end
   const int J2 = l2 + s2;
   const int len = w0 * w1;
-  for (int k = 0; k < len; k++) acc[k * TPB] = 0.f;
-  const int lo2 = (DIM == 3) ? d2.node_e0[I2] : 0, hi2 = (DIM == 3) ? lo2 + d2.node_ne[I2] : 1;
-  const int lo1 = d1.node_e0[I1], hi1 = lo1 + d1.node_ne[I1];
-  const int lo0 = d0.node_e0[I0], hi0 = lo0 + d0.node_ne[I0];
-  for (int e2 = lo2; e2 < hi2; e2++) {
-    const int f2 = (DIM == 3) ? d2.first[e2] : 0;
-    const int b2 = J2 - f2;  // e's axis-2 function at column J2
-    if (DIM == 3 && (b2 < 0 || b2 > P)) continue;
-    for (int e1 = lo1; e1 < hi1; e1++) {
-      const int f1 = d1.first[e1];
-      for (int e0 = lo0; e0 < hi0; e0++) {
-        const int f0 = d0.first[e0];
-        const int a = (I0 - f0) + N1 * ((I1 - f1) + N1 * (I2 - f2));
-        const int base = (f1 - l1) * w0 + (f0 - l0);
-        const int2 *ga = gtab + a * NEN + (DIM == 3 ? b2 * NB : 0);
-        // the slice's values are loaded before any is added: independent loads in flight
-        constexpr int CH = NB <= 64 ? NB : 25;
-        for (int bc = 0; bc < NB; bc += CH) {
-          float ev[CH];
+  r0_s[t] = -1;
+  len_s[t] = 0;
+  if (active) {
+    for (int k = 0; k < len; k++) acc[k * LD] = 0.f;
+    const int lo2 = (DIM == 3) ? d2.node_e0[I2] : 0, hi2 = (DIM == 3) ? lo2 + d2.node_ne[I2] : 1;
+    const int lo1 = d1.node_e0[I1], hi1 = lo1 + d1.node_ne[I1];
+    const int lo0 = d0.node_e0[I0], hi0 = lo0 + d0.node_ne[I0];
+    for (int e2 = lo2; e2 < hi2; e2++) {
+      const int f2 = (DIM == 3) ? d2.first[e2] : 0;
+      const int b2 = J2 - f2;  // e's axis-2 function at column J2
+      if (DIM == 3 && (b2 < 0 || b2 > P)) continue;
+      for (int e1 = lo1; e1 < hi1; e1++) {
+        const int f1 = d1.first[e1];
+        for (int e0 = lo0; e0 < hi0; e0++) {
+          const int f0 = d0.first[e0];
+          const int a = (I0 - f0) + N1 * ((I1 - f1) + N1 * (I2 - f2));
+          const int base = (f1 - l1) * w0 + (f0 - l0);
+          const int2 *ga = gtab + a * NEN + (DIM == 3 ? b2 * NB : 0);
+          // the slice's values are loaded before any is added: independent loads in flight
+          constexpr int CH = NB <= 64 ? NB : 25;
+          for (int bc = 0; bc < NB; bc += CH) {
+            float ev[CH];
 #pragma unroll
-          for (int u = 0; u < CH; u++) {
-            const int b = bc + u;
-            float x = 0.f;
-            if (b < NB) {
-              const int2 pc = ga[b];  // packed slab of (min(a,b), max(a,b)); column shift off(b) - off(a) for b < a
-              x = __ldg(E + (size_t)pc.x * N + A + pc.y);
+            for (int u = 0; u < CH; u++) {
+              const int b = bc + u;
+              float x = 0.f;
+              if (b < NB) {
+                const int2 pc = ga[b];  // packed slab of (min(a,b), max(a,b)); column shift off(b) - off(a) for b < a
+                x = __ldg(E + (size_t)pc.x * N + A + pc.y);
+              }
+              ev[u] = x;
             }
-            ev[u] = x;
-          }
 #pragma unroll
-          for (int u = 0; u < CH; u++) {
-            const int b = bc + u;
-            if (b >= NB) break;
-            const int b0 = b % N1, b1 = b / N1;
-            acc[(base + b1 * w0 + b0) * TPB] += ev[u];
+            for (int u = 0; u < CH; u++) {
+              const int b = bc + u;
+              if (b >= NB) break;
+              const int b0 = b % N1, b1 = b / N1;
+              acc[(base + b1 * w0 + b0) * LD] += ev[u];
+            }
           }
         }
       }
     }
+    bool rowfix = (bnd.flag[0][0] && I0 == 0) || (bnd.flag[0][1] && I0 == d0.n - 1) || (bnd.flag[1][0] && I1 == 0) ||
+                  (bnd.flag[1][1] && I1 == d1.n - 1);
+    if (DIM == 3) rowfix |= (bnd.flag[2][0] && I2 == 0) || (bnd.flag[2][1] && I2 == d2.n - 1);
+    bool fix2 = false;  // the slice's axis-2 column is a Dirichlet one
+    if (DIM == 3) fix2 = (bnd.flag[2][0] && J2 == 0) || (bnd.flag[2][1] && J2 == d2.n - 1);
+    const float wA = wts ? (float)wts[A] : 1.f;
+    for (int k = 0; k < len; k++) {
+      const int J0 = l0 + k % w0, J1 = l1 + k / w0;
+      const int64_t B = J0 + (int64_t)d0.n * (J1 + (int64_t)d1.n * J2);
+      const bool colfix = fix2 || (bnd.flag[0][0] && J0 == 0) || (bnd.flag[0][1] && J0 == d0.n - 1) ||
+                          (bnd.flag[1][0] && J1 == 0) || (bnd.flag[1][1] && J1 == d1.n - 1);
+      float v = acc[k * LD];
+      if (wts) v *= wA * (float)wts[B];
+      if (rowfix || colfix) v = (A == B) ? 1.f : 0.f;
+      acc[k * LD] = v;
+    }
+    r0_s[t] = rowptr[A] + (int64_t)s2 * len;
+    len_s[t] = len;
   }
-  bool rowfix = (bnd.flag[0][0] && I0 == 0) || (bnd.flag[0][1] && I0 == d0.n - 1) || (bnd.flag[1][0] && I1 == 0) ||
-                (bnd.flag[1][1] && I1 == d1.n - 1);
-  if (DIM == 3) rowfix |= (bnd.flag[2][0] && I2 == 0) || (bnd.flag[2][1] && I2 == d2.n - 1);
-  bool fix2 = false;  // the slice's axis-2 column is a Dirichlet one
-  if (DIM == 3) fix2 = (bnd.flag[2][0] && J2 == 0) || (bnd.flag[2][1] && J2 == d2.n - 1);
-  const float wA = wts ? (float)wts[A] : 1.f;
-  const int64_t r0 = rowptr[A] + (int64_t)s2 * len;
-  for (int k = 0; k < len; k++) {
-    const int J0 = l0 + k % w0, J1 = l1 + k / w0;
-    const int64_t B = J0 + (int64_t)d0.n * (J1 + (int64_t)d1.n * J2);
-    const bool colfix = fix2 || (bnd.flag[0][0] && J0 == 0) || (bnd.flag[0][1] && J0 == d0.n - 1) ||
-                        (bnd.flag[1][0] && J1 == 0) || (bnd.flag[1][1] && J1 == d1.n - 1);
-    float v = acc[k * TPB];
-    if (wts) v *= wA * (float)wts[B];
-    if (rowfix || colfix) v = (A == B) ? 1.f : 0.f;
-    vals[r0 + k] = v;
+  __syncthreads();
+  // each row slice is a run of len consecutive CSR values: a warp stores the runs of its
+  // own 32 rows one after the other, a lane per value (coalesced)
+  const int lane = t & 31, w = t >> 5;
+  for (int rr = 0; rr < 32; rr++) {
+    const int tt = w * 32 + rr;
+    const int64_t r0 = r0_s[tt];
+    if (r0 < 0) continue;
+    const int n = len_s[tt];
+    for (int k = lane; k < n; k += 32) vals[r0 + k] = acc_all[k * LD + tt];
   }
 }
 
@@ -842,7 +861,7 @@ cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, in
     constexpr int RMAX = (2 * PP + 1) * (2 * PP + 1);  // columns of a thread's slice
     constexpr int TPB = 128;
     constexpr int NENc = ipow3<D>(PP + 1);
-    const size_t sm = (size_t)RMAX * TPB * sizeof(float) + (NENc * NENc * 8 <= 8 * 1024 ? (size_t)NENc * NENc * 8 : 0);
+    const size_t sm = (size_t)RMAX * (TPB + 1) * sizeof(float) + (NENc * NENc * 8 <= 8 * 1024 ? (size_t)NENc * NENc * 8 : 0);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_gather_rows<D, PP, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const dim3 gg((unsigned)((h->N + TPB - 1) / TPB), D == 3 ? 2 * PP + 1 : 1);
     k_gather_rows<D, PP, TPB><<<gg, TPB, sm, h->stream>>>(a0, a1, a2, P->E, P->gtab, h->rowptr, h->weights, h->bnd, vals,
