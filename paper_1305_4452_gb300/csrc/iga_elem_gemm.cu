@@ -464,14 +464,15 @@ __global__ void __launch_bounds__(TPB) k_gather_rows(DirArgs d0, DirArgs d1, Dir
   constexpr int N1 = P + 1, NEN = ipow3<DIM>(N1), RMAX = (2 * P + 1) * (2 * P + 1);
   constexpr int NB = N1 * N1;  // functions of an element in one axis-2 slice (2D: all)
   constexpr int LD = TPB + 1;  // accumulator stride: conflict-free by thread and by column
+  constexpr int TABOFF = (RMAX * LD + 1) / 2 * 2;  // the int2 table starts on an 8-byte boundary
   constexpr bool TAB_SMEM = NEN * NEN * 8 <= 8 * 1024;  // p = 2: small enough not to cost occupancy
-  extern __shared__ float acc_all[];  // [RMAX][TPB + 1], then the (pk, column shift) table for p <= 3
+  extern __shared__ float acc_all[];  // [RMAX][TPB + 1] (+ pad to 8 bytes), then the (pk, column shift) table
   __shared__ int64_t r0_s[TPB];       // each row slice's first CSR position (-1: nothing to store)
   __shared__ int len_s[TPB];
   const int t = threadIdx.x;
   const int2 *gtab = gtab_g;
   if (TAB_SMEM) {
-    int2 *st = reinterpret_cast<int2 *>(acc_all + RMAX * LD);
+    int2 *st = reinterpret_cast<int2 *>(acc_all + TABOFF);
     for (int k = t; k < NEN * NEN; k += TPB) st[k] = gtab_g[k];
     __syncthreads();
     gtab = st;
@@ -861,7 +862,8 @@ cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, in
     constexpr int RMAX = (2 * PP + 1) * (2 * PP + 1);  // columns of a thread's slice
     constexpr int TPB = 128;
     constexpr int NENc = ipow3<D>(PP + 1);
-    const size_t sm = (size_t)RMAX * (TPB + 1) * sizeof(float) + (NENc * NENc * 8 <= 8 * 1024 ? (size_t)NENc * NENc * 8 : 0);
+    const size_t sm = (size_t)((RMAX * (TPB + 1) + 1) / 2 * 2) * sizeof(float) +
+                      (NENc * NENc * 8 <= 8 * 1024 ? (size_t)NENc * NENc * 8 : 0);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_gather_rows<D, PP, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const dim3 gg((unsigned)((h->N + TPB - 1) / TPB), D == 3 ? 2 * PP + 1 : 1);
     k_gather_rows<D, PP, TPB><<<gg, TPB, sm, h->stream>>>(a0, a1, a2, P->E, P->gtab, h->rowptr, h->weights, h->bnd, vals,
