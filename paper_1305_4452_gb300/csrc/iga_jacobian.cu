@@ -249,15 +249,6 @@ __global__ void __launch_bounds__(128, 6) k_stage2(DirArgs d0, DirArgs d1, DirAr
   }
 }
 
-__device__ __forceinline__ bool on_dirichlet(const BndArgs &b, int dim, const int *i, const int *n) {
-  bool on = false;
-  for (int ax = 0; ax < dim; ax++) {
-    if (b.flag[ax][0] && i[ax] == 0) on = true;
-    if (b.flag[ax][1] && i[ax] == n[ax] - 1) on = true;
-  }
-  return on;
-}
-
 // Final stage: contract the last axis and write the CSR entries.
 //   3D: in = T2[g2][x2][pi1][pi0];  J = P^00 H0 + P^10 H1 + P^01 H1^T + P^11 H2
 //   2D: in = T1[g1][x1][pi0];       J = P^00 G0 + P^10 G1 + P^01 G1^T + P^11 G2
@@ -267,23 +258,30 @@ __device__ __forceinline__ bool on_dirichlet(const BndArgs &b, int dim, const in
 // J is symmetric (Q is), so only the entries whose pair triple (pl, pmid, pi0)
 // is not above its transpose (plT, pmidT, pi0T) in lexicographic order are
 // contracted; each value is written at (A, B) and at (B, A).  A block walks a range
-// of the canonical last-axis pairs (pl <= plT) for its pmid and 128 axis-0 pairs;
-// CSR row starts come from the start of the row's line (i1, i2) plus the line's
-// stencil width times the prefix sum of the axis-0 widths before i0.
+// of at most FINAL_CHUNK canonical last-axis pairs (pl <= plT) for its pmid and 128
+// axis-0 pairs; everything that depends only on the last-axis pair (its overlap, its
+// table rows, its functions, their Dirichlet flags, the CSR line starts of the row and
+// of the transposed row) is formed once per block in shared memory.  CSR row starts come
+// from the start of the row's line (i1, i2) plus the line's stencil width times the
+// prefix sum of the axis-0 widths before i0.
+constexpr int FINAL_CHUNK = 16;
+
+struct FinalPair {
+  int pl, skip_diag, xs, np, po, il, jl, ol, olT, wl, wlT, dirI, dirJ;
+  int64_t lineA, lineB;
+};
+
 template <typename T, typename V, int DIM, int PLAN>
 __global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d2, const T *__restrict__ in, CsrArgs csr,
                                                V *__restrict__ vals, const V *__restrict__ base, int chunk, int fix) {
+  __shared__ FinalPair fp[FINAL_CHUNK];
   const int pi0 = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pi0 >= d0.np) return;
+  const bool active = pi0 < d0.np;
   const DirArgs &dl = (DIM == 3) ? d2 : d1;
   const int pmid = (DIM == 3) ? blockIdx.z : 0;
   // the block's range of canonical last-axis pairs (pair index <= its transpose's)
   const int pa = blockIdx.y * chunk, pb = min(pa + chunk, dl.nc);
   const size_t plane = (DIM == 3) ? (size_t)d0.np * d1.np * d2.X : (size_t)d0.np * d1.X;
-  const int pi0T = d0.pair_T[pi0];
-  const int i0 = d0.pair_i[pi0], j0 = d0.pair_j[pi0];
-  const int o0 = pi0 - d0.pair_off[i0], w0 = d0.r[i0] - d0.l[i0] + 1;
-  const int o0T = pi0T - d0.pair_off[j0], w0T = d0.r[j0] - d0.l[j0] + 1;
   int i1 = 0, j1 = 0, o1 = 0, w1 = 1, pmidT = 0, o1T = 0, w1T = 1;
   if (DIM == 3) {
     i1 = d1.pair_i[pmid]; j1 = d1.pair_j[pmid];
@@ -291,16 +289,52 @@ __global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d
     pmidT = d1.pair_T[pmid];
     o1T = pmidT - d1.pair_off[j1]; w1T = d1.r[j1] - d1.l[j1] + 1;
   }
+  const int LAX = DIM - 1;  // the last axis
+  if ((int)threadIdx.x < pb - pa) {
+    FinalPair &f = fp[threadIdx.x];
+    const int pl = dl.pair_c[pa + threadIdx.x], plT = dl.pair_T[pl];
+    f.pl = pl;
+    f.skip_diag = pl == plT;  // a self-transposed pair: the triple order decides
+    f.xs = dl.pair_x0[pl];
+    f.np = dl.pair_np[pl];
+    f.po = dl.pair_po[pl];
+    const int il = dl.pair_i[pl], jl = dl.pair_j[pl];
+    f.il = il;
+    f.jl = jl;
+    f.ol = pl - dl.pair_off[il];
+    f.olT = plT - dl.pair_off[jl];
+    f.wl = dl.r[il] - dl.l[il] + 1;
+    f.wlT = dl.r[jl] - dl.l[jl] + 1;
+    f.dirI = (csr.bnd.flag[LAX][0] && il == 0) || (csr.bnd.flag[LAX][1] && il == dl.n - 1);
+    f.dirJ = (csr.bnd.flag[LAX][0] && jl == 0) || (csr.bnd.flag[LAX][1] && jl == dl.n - 1);
+    f.lineA = DIM == 3 ? csr.rp_line[i1 + (int64_t)d1.n * il] : csr.rp_line[il];
+    f.lineB = DIM == 3 ? csr.rp_line[j1 + (int64_t)d1.n * jl] : csr.rp_line[jl];
+  }
+  __syncthreads();
+  if (!active) return;
+  const int pi0T = d0.pair_T[pi0];
+  const int i0 = d0.pair_i[pi0], j0 = d0.pair_j[pi0];
+  const int o0 = pi0 - d0.pair_off[i0], w0 = d0.r[i0] - d0.l[i0] + 1;
+  const int o0T = pi0T - d0.pair_off[j0], w0T = d0.r[j0] - d0.l[j0] + 1;
   const T *tab = ptab<T>(dl);
   const bool mid_sym = pmid <= pmidT;  // 3D: where stage 2 stored H0 and H2
+  // Dirichlet flags of the row and column functions along the axes before the last
+  bool dirI = (csr.bnd.flag[0][0] && i0 == 0) || (csr.bnd.flag[0][1] && i0 == d0.n - 1);
+  bool dirJ = (csr.bnd.flag[0][0] && j0 == 0) || (csr.bnd.flag[0][1] && j0 == d0.n - 1);
+  if (DIM == 3) {
+    dirI = dirI || (csr.bnd.flag[1][0] && i1 == 0) || (csr.bnd.flag[1][1] && i1 == d1.n - 1);
+    dirJ = dirJ || (csr.bnd.flag[1][0] && j1 == 0) || (csr.bnd.flag[1][1] && j1 == d1.n - 1);
+  }
   // CSR row starts: line start (the same for the whole block at a given pl) plus the
   // row's offset within its line
   const int64_t rA0 = (int64_t)w1 * csr.rp_p0[i0], rB0 = (int64_t)w1T * csr.rp_p0[j0];
-  for (int c = pa; c < pb; c++) {
-    const int pl = dl.pair_c[c], plT = dl.pair_T[pl];
-    if (pl == plT && (pmid > pmidT || (pmid == pmidT && pi0 > pi0T))) continue;
-    const int xs = dl.pair_x0[pl], np = dl.pair_np[pl];
-    const T *pv = tab + (size_t)dl.pair_po[pl] * IGA_PVS;
+  const int64_t inA = ((int64_t)o1 * w0 + o0), inB = ((int64_t)o1T * w0T + o0T);  // 3D in-line offsets before ol
+  const bool skip_self = pmid > pmidT || (pmid == pmidT && pi0 > pi0T);
+  for (int c = 0; c < pb - pa; c++) {
+    const FinalPair &f = fp[c];
+    if (f.skip_diag && skip_self) continue;
+    const int xs = f.xs, np = f.np;
+    const T *pv = tab + (size_t)f.po * IGA_PVS;
     T acc = 0;
     for (int k = 0; k < np; k++) {
       const size_t xo = (size_t)(xs + k);
@@ -327,28 +361,21 @@ __global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d
         acc = fma(p11, in[2 * plane + rs], acc);
       }
     }
-    const int il = dl.pair_i[pl], jl = dl.pair_j[pl];
-    const int ol = pl - dl.pair_off[il], olT = plT - dl.pair_off[jl];
-    int I[3], J[3], n[3] = {d0.n, d1.n, d2.n};
     int64_t A, B, pos, posT;
     if (DIM == 3) {
-      I[0] = i0; I[1] = i1; I[2] = il; J[0] = j0; J[1] = j1; J[2] = jl;
-      A = i0 + (int64_t)d0.n * (i1 + (int64_t)d1.n * il);
-      B = j0 + (int64_t)d0.n * (j1 + (int64_t)d1.n * jl);
-      const int wl = dl.r[il] - dl.l[il] + 1, wlT = dl.r[jl] - dl.l[jl] + 1;
-      pos = csr.rp_line[i1 + (int64_t)d1.n * il] + wl * rA0 + ((int64_t)ol * w1 + o1) * w0 + o0;
-      posT = csr.rp_line[j1 + (int64_t)d1.n * jl] + wlT * rB0 + ((int64_t)olT * w1T + o1T) * w0T + o0T;
+      A = i0 + (int64_t)d0.n * (i1 + (int64_t)d1.n * f.il);
+      B = j0 + (int64_t)d0.n * (j1 + (int64_t)d1.n * f.jl);
+      pos = f.lineA + f.wl * rA0 + (int64_t)f.ol * w1 * w0 + inA;
+      posT = f.lineB + f.wlT * rB0 + (int64_t)f.olT * w1T * w0T + inB;
     } else {
-      I[0] = i0; I[1] = il; J[0] = j0; J[1] = jl;
-      A = i0 + (int64_t)d0.n * il;
-      B = j0 + (int64_t)d0.n * jl;
-      const int wl = dl.r[il] - dl.l[il] + 1, wlT = dl.r[jl] - dl.l[jl] + 1;
-      pos = csr.rp_line[il] + wl * rA0 + (int64_t)ol * w0 + o0;
-      posT = csr.rp_line[jl] + wlT * rB0 + (int64_t)olT * w0T + o0T;
+      A = i0 + (int64_t)d0.n * f.il;
+      B = j0 + (int64_t)d0.n * f.jl;
+      pos = f.lineA + f.wl * rA0 + (int64_t)f.ol * w0 + o0;
+      posT = f.lineB + f.wlT * rB0 + (int64_t)f.olT * w0T + o0T;
     }
     double v = (double)acc;
     if (csr.wts) v *= csr.wts[A] * csr.wts[B];
-    if (fix && (on_dirichlet(csr.bnd, DIM, I, n) || on_dirichlet(csr.bnd, DIM, J, n))) {
+    if (fix && (dirI || f.dirI || dirJ || f.dirJ)) {
       const V e = (V)(A == B ? 1.0 : 0.0);  // identity row, zeroed column
       vals[pos] = e;
       vals[posT] = e;
@@ -390,7 +417,7 @@ cudaError_t run_stages(iga_s *h, V *vals, const V *base, int fix) {
   cudaError_t ce = run_stage1<T, DIM, PLAN>(h, T1);
   if (ce) return ce;
   CsrArgs csr{h->rowptr, h->rp_line, h->rp_p0, h->weights, h->bnd};
-  const int chunk = 8, fchunk = 16;  // stage-2 pairs per block; final-stage canonical pairs per block
+  const int chunk = 8, fchunk = FINAL_CHUNK;  // stage-2 pairs per block; final-stage canonical pairs per block
   if (DIM == 3) {
     dim3 g2((a0.np + 127) / 128, (a1.np + chunk - 1) / chunk, a2.X);
     IGA_LAUNCH(h, KC_STAGE2, (k_stage2<T, PLAN><<<g2, 128, 0, h->stream>>>(a0, a1, a2, T1, T2, chunk)));
