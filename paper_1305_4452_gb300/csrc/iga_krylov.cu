@@ -988,7 +988,9 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
 // returns at once, so the host synchronises only every few iterations.
 // ---------------------------------------------------------------------------
 namespace {
-enum { CG_DONE = 0, CG_ITS, CG_RZ, CG_RR, CG_PQ, CG_ALPHA, CG_BETA, CG_RZ2, CG_RR2, CG_BRK, CG_NS };
+enum { CG_DONE = 0, CG_ITS, CG_RZ, CG_RR, CG_PQ, CG_ALPHA, CG_BETA, CG_RZ2, CG_RR2, CG_BRK, CG_RZB, CG_NS };
+// the two slots of <r,z>, alternating by iteration parity (CG_RZ holds the first one)
+__device__ __forceinline__ int cg_rz(int par) { return par ? CG_RZB : CG_RZ; }
 
 __global__ void __launch_bounds__(RED_THREADS) k_cg_init(const double *__restrict__ b, const double *__restrict__ dinv,
                                                          double *__restrict__ x, double *__restrict__ r, double *__restrict__ p,
@@ -1038,19 +1040,38 @@ __global__ void k_cg_check0(double *s, double tol) {
   else if (!(sqrt(s[CG_RR]) > tol)) s[CG_DONE] = 1.0;
 }
 
-__global__ void k_cg_alpha(double *s) {
-  if (s[CG_DONE] != 0.0) return;
-  double pq = s[CG_PQ];
-  if (!(pq > 0.0) || !isfinite(pq)) { s[CG_DONE] = 1.0; s[CG_BRK] = 1.0; return; }
-  s[CG_ALPHA] = s[CG_RZ] / pq;
+// Sum of partial[k * stride + off], k < nb, in a fixed order (the same in every block);
+// valid in every thread of the block
+__device__ double block_sum_strided(const double *__restrict__ partial, int nb, int stride, int off, double *sh) {
+  __shared__ double res;
+  double v = 0.0;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) v += partial[(size_t)k * stride + off];
+  v = block_sum(v, sh);
+  if (threadIdx.x == 0) res = v;
+  __syncthreads();
+  return res;
 }
 
+// One CG iteration after the operator product q = A p, in two kernels whose every block
+// forms the iteration's scalars from the previous kernel's per-block partials in the
+// same fixed order (so all blocks agree bit for bit) and block 0 records them:
+//   k_cg_xr: alpha = <r,z> / <p,q>; x += alpha p; r -= alpha q; partials of <r,z>, <r,r>
+//   k_cg_p:  converged when ||r|| <= tol; else beta = <r,z>_new / <r,z>; p = D^-1 r + beta p
+// <r,z> alternates between two slots by iteration parity: block 0 writes the new value
+// while the other blocks still read the old one.
 __global__ void __launch_bounds__(RED_THREADS) k_cg_xr(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
                                                        const double *__restrict__ q, const double *__restrict__ dinv,
-                                                       const double *__restrict__ s, double *__restrict__ partial, int64_t N) {
+                                                       double *__restrict__ s, const double *__restrict__ pq_part,
+                                                       double *__restrict__ partial, int nb, int par, int64_t N) {
   __shared__ double sh[32];
   if (s[CG_DONE] != 0.0) return;
-  const double alpha = s[CG_ALPHA];
+  const double pq = block_sum_strided(pq_part, nb, 1, 0, sh);
+  if (!(pq > 0.0) || !isfinite(pq)) {  // every block takes this branch
+    if (blockIdx.x == 0 && threadIdx.x == 0) { s[CG_DONE] = 1.0; s[CG_BRK] = 1.0; }
+    return;
+  }
+  const double alpha = s[cg_rz(par)] / pq;  // <r,z> of this iteration
+  if (blockIdx.x == 0 && threadIdx.x == 0) { s[CG_PQ] = pq; s[CG_ALPHA] = alpha; }
   int64_t per = (N + gridDim.x - 1) / gridDim.x;
   int64_t a = blockIdx.x * per, e = min(N, a + per);
   double rr = 0.0, rz = 0.0;
@@ -1069,21 +1090,24 @@ __global__ void __launch_bounds__(RED_THREADS) k_cg_xr(double *__restrict__ x, d
   }
 }
 
-__global__ void k_cg_beta(double *s, double tol) {
+__global__ void __launch_bounds__(RED_THREADS) k_cg_p(double *__restrict__ p, const double *__restrict__ r,
+                                                      const double *__restrict__ dinv, double *__restrict__ s,
+                                                      const double *__restrict__ partial, int nb, int par, double tol, int64_t N) {
+  __shared__ double sh[32];
   if (s[CG_DONE] != 0.0) return;
-  s[CG_ITS] += 1.0;
-  double rr = s[CG_RR2];
-  if (!isfinite(rr)) { s[CG_DONE] = 1.0; s[CG_BRK] = 1.0; return; }
-  s[CG_RR] = rr;
-  if (sqrt(rr) <= tol) { s[CG_DONE] = 1.0; return; }
-  s[CG_BETA] = s[CG_RZ2] / s[CG_RZ];
-  s[CG_RZ] = s[CG_RZ2];
-}
-
-__global__ void k_cg_p(double *__restrict__ p, const double *__restrict__ r, const double *__restrict__ dinv,
-                       const double *__restrict__ s, int64_t N) {
-  if (s[CG_DONE] != 0.0) return;
-  const double beta = s[CG_BETA];
+  const double rz_new = block_sum_strided(partial, nb, 2, 0, sh);
+  const double rr = block_sum_strided(partial, nb, 2, 1, sh);
+  const bool bad = !isfinite(rr), conv = !bad && sqrt(rr) <= tol;
+  const double beta = rz_new / s[cg_rz(par)];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    s[CG_ITS] += 1.0;
+    s[CG_RR] = rr;
+    s[CG_BETA] = beta;
+    s[cg_rz(par ^ 1)] = rz_new;  // the next iteration's <r,z>
+    if (bad) { s[CG_DONE] = 1.0; s[CG_BRK] = 1.0; }
+    else if (conv) s[CG_DONE] = 1.0;
+  }
+  if (bad || conv) return;  // every block takes the same branch
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = fma(beta, p[i], dinv[i] * r[i]);
 }
@@ -1106,14 +1130,13 @@ int cg_solve(iga_s *h, const void *vals, int is_f32, const double *b, double *x,
   int enq = 0;
   while (enq < maxit) {
     for (int k = 0; k < batch && enq < maxit; k++, enq++) {
+      const int par = enq & 1;  // <r,z> slot of this iteration
+      double *pq_part = h->red, *rz_part = h->red + RED_BLOCKS;
       apply_op(h, vals, is_f32, p, q, done);
-      IGA_LAUNCH(h, KC_VEC, (k_dot_partial<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(p, q, h->red, N, done)));
-      IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce_rows<<<1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, s + CG_PQ, 0, done)));
-      IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_cg_alpha<<<1, 1, 0, h->stream>>>(s)));
-      IGA_LAUNCH(h, KC_VEC, (k_cg_xr<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(x, r, p, q, dinv, s, h->red, N)));
-      IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_reduce2<<<1, RED_THREADS, 0, h->stream>>>(h->red, RED_BLOCKS, s + CG_RZ2, s + CG_RR2, done)));
-      IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_cg_beta<<<1, 1, 0, h->stream>>>(s, tol_abs)));
-      IGA_LAUNCH(h, KC_VEC, (k_cg_p<<<eg, 256, 0, h->stream>>>(p, r, dinv, s, N)));
+      IGA_LAUNCH(h, KC_VEC, (k_dot_partial<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(p, q, pq_part, N, done)));
+      IGA_LAUNCH(h, KC_VEC, (k_cg_xr<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(x, r, p, q, dinv, s, pq_part, rz_part, RED_BLOCKS,
+                                                                                  par, N)));
+      IGA_LAUNCH(h, KC_VEC, (k_cg_p<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(p, r, dinv, s, rz_part, RED_BLOCKS, par, tol_abs, N)));
     }
     cudaMemcpyAsync(h->ctl_host, s, CG_NS * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     cudaError_t ce = cudaStreamSynchronize(h->stream);
