@@ -18,7 +18,6 @@ namespace {
 
 constexpr int RED_THREADS = 256;
 constexpr int RED_BLOCKS = 304;  // 2 x 152 SMs
-constexpr int CG_THREADS = 1024;  // the CG vector kernels: 2 blocks of 32 warps per SM
 constexpr int GS_THREADS = 1024;  // Gram-Schmidt passes: one block of 32 warps per SM
 
 // GMRES scalar block layout (doubles) for restart m
@@ -213,7 +212,7 @@ __global__ void k_diag_stencil(StencilRows S, const int64_t *__restrict__ rowptr
 }
 
 // partial[blk] = sum over the block's fixed row range of x*y
-__global__ void __launch_bounds__(CG_THREADS) k_dot_partial(const double *__restrict__ x, const double *__restrict__ y,
+__global__ void __launch_bounds__(RED_THREADS) k_dot_partial(const double *__restrict__ x, const double *__restrict__ y,
                                                              double *__restrict__ partial, int64_t N, const double *__restrict__ done) {
   __shared__ double sh[32];
   if (done && done[0] != 0.0) return;
@@ -1060,7 +1059,7 @@ __device__ double block_sum_strided(const double *__restrict__ partial, int nb, 
 //   k_cg_p:  converged when ||r|| <= tol; else beta = <r,z>_new / <r,z>; p = D^-1 r + beta p
 // <r,z> alternates between two slots by iteration parity: block 0 writes the new value
 // while the other blocks still read the old one.
-__global__ void __launch_bounds__(CG_THREADS) k_cg_xr(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+__global__ void __launch_bounds__(RED_THREADS) k_cg_xr(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
                                                        const double *__restrict__ q, const double *__restrict__ dinv,
                                                        double *__restrict__ s, const double *__restrict__ pq_part,
                                                        double *__restrict__ partial, int nb, int par, int64_t N) {
@@ -1091,7 +1090,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_xr(double *__restrict__ x, do
   }
 }
 
-__global__ void __launch_bounds__(CG_THREADS) k_cg_p(double *__restrict__ p, const double *__restrict__ r,
+__global__ void __launch_bounds__(RED_THREADS) k_cg_p(double *__restrict__ p, const double *__restrict__ r,
                                                       const double *__restrict__ dinv, double *__restrict__ s,
                                                       const double *__restrict__ partial, int nb, int par, double tol, int64_t N) {
   __shared__ double sh[32];
@@ -1134,10 +1133,10 @@ int cg_solve(iga_s *h, const void *vals, int is_f32, const double *b, double *x,
       const int par = enq & 1;  // <r,z> slot of this iteration
       double *pq_part = h->red, *rz_part = h->red + RED_BLOCKS;
       apply_op(h, vals, is_f32, p, q, done);
-      IGA_LAUNCH(h, KC_VEC, (k_dot_partial<<<RED_BLOCKS, CG_THREADS, 0, h->stream>>>(p, q, pq_part, N, done)));
-      IGA_LAUNCH(h, KC_VEC, (k_cg_xr<<<RED_BLOCKS, CG_THREADS, 0, h->stream>>>(x, r, p, q, dinv, s, pq_part, rz_part, RED_BLOCKS,
-                                                                                 par, N)));
-      IGA_LAUNCH(h, KC_VEC, (k_cg_p<<<RED_BLOCKS, CG_THREADS, 0, h->stream>>>(p, r, dinv, s, rz_part, RED_BLOCKS, par, tol_abs, N)));
+      IGA_LAUNCH(h, KC_VEC, (k_dot_partial<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(p, q, pq_part, N, done)));
+      IGA_LAUNCH(h, KC_VEC, (k_cg_xr<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(x, r, p, q, dinv, s, pq_part, rz_part, RED_BLOCKS,
+                                                                                  par, N)));
+      IGA_LAUNCH(h, KC_VEC, (k_cg_p<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(p, r, dinv, s, rz_part, RED_BLOCKS, par, tol_abs, N)));
     }
     cudaMemcpyAsync(h->ctl_host, s, CG_NS * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     cudaError_t ce = cudaStreamSynchronize(h->stream);
