@@ -373,13 +373,20 @@ __global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d
       pos = f.lineA + f.wl * rA0 + (int64_t)f.ol * w0 + o0;
       posT = f.lineB + f.wlT * rB0 + (int64_t)f.olT * w0T + o0T;
     }
-    double v = (double)acc;
-    if (csr.wts) v *= csr.wts[A] * csr.wts[B];
     if (fix && (dirI || f.dirI || dirJ || f.dirJ)) {
       const V e = (V)(A == B ? 1.0 : 0.0);  // identity row, zeroed column
       vals[pos] = e;
       vals[posT] = e;
+    } else if constexpr (sizeof(V) == 4) {
+      // FP32 values: the sum with the base in FP32 (one correctly rounded addition), no
+      // FP64 operations on GB300's narrow FP64 pipe except the rational weights' product
+      float v = (float)acc;
+      if (csr.wts) v *= (float)(csr.wts[A] * csr.wts[B]);
+      vals[pos] = base ? (V)(base[pos] + v) : (V)v;
+      if (posT != pos) vals[posT] = base ? (V)(base[posT] + v) : (V)v;
     } else {
+      double v = (double)acc;
+      if (csr.wts) v *= csr.wts[A] * csr.wts[B];
       vals[pos] = base ? (V)((double)base[pos] + v) : (V)v;
       if (posT != pos) vals[posT] = base ? (V)((double)base[posT] + v) : (V)v;
     }
