@@ -336,7 +336,11 @@ def run_ours(args):
     hbm, hbm_src = hbm_peak()
     dom = max(prof, key=lambda c: prof[c][0])
     dms, dn, _ = prof[dom]
-    roof = roofline_entry(disc, dom, dms / max(dn, 1), hbm, hbm_src, pk)
+    used = None
+    if dom == "spmv":
+        used = fixed_product_entries(torch, disc, [len(k) - P - 1 for k in kn], list(bc))
+        torch.cuda.empty_cache()
+    roof = roofline_entry(disc, dom, dms / max(dn, 1), hbm, hbm_src, pk, used)
 
     r = reps[-1]
     solve_s = ms / args.steps / 1e3
@@ -454,28 +458,55 @@ def _best_ms(torch, fn, reps):
     return best
 
 
-# DRAM bytes (read + write) of one k_spmv_stencil launch (FP64 values) on the 64^3 annulus,
-# from one ncu capture of this benchmark's command (named in the JSON line); valid for that
-# workload while the kernel is unchanged.
-SPMV_DRAM_BYTES_ANNULUS64 = 803.45e6 + 4.97e6
-SPMV_TRAFFIC_CAPTURE = ("profiles/k_spmv_stencil_annulus64_fp64_traffic.md: ncu --metrics "
-                        "dram__bytes_read.sum,dram__bytes_write.sum --clock-control none -k regex:k_spmv_stencil")
+# DRAM bytes (read + write) of one Krylov operator product (k_spmv_fixed, FP64 values) on
+# the 64^3 annulus, from one ncu capture of this benchmark's command (named in the JSON
+# line); valid for that workload while the kernel is unchanged (None: not captured).
+SPMV_DRAM_BYTES_ANNULUS64 = None
+SPMV_TRAFFIC_CAPTURE = ("profiles/k_spmv_fixed_annulus64_fp64_traffic.md: ncu --metrics "
+                        "dram__bytes_read.sum,dram__bytes_write.sum --clock-control none -k regex:k_spmv_fixed")
 
 
-def roofline_entry(disc, cls, avg_ms, hbm_gbs, hbm_src, pk):
+def fixed_product_entries(torch, disc, n, faces):
+    """Stored CSR entries that the product with the Dirichlet-fixed Newton Jacobian
+    (k_spmv_fixed) multiplies: those of rows off the Dirichlet faces, less the columns on
+    a Dirichlet face of the last axis (a contiguous part of each row, which the kernel
+    skips); the Dirichlet rows are copied.  Returns (entries, Dirichlet rows)."""
+    rp, ci = disc.pattern()
+    idx = torch.arange(disc.N, device="cuda")
+    ijk = [idx % n[0], (idx // n[0]) % n[1], idx // (n[0] * n[1])]
+    dmask = torch.zeros(disc.N, dtype=torch.bool, device="cuda")
+    last = torch.zeros(disc.N, dtype=torch.bool, device="cuda")
+    for ax, side in faces:
+        on = ijk[ax] == (0 if side == 0 else n[ax] - 1)
+        dmask |= on
+        if ax == len(n) - 1:
+            last |= on
+    rows = torch.repeat_interleave(idx, rp[1:] - rp[:-1])
+    keep = ~dmask[rows]
+    del rows
+    keep &= ~last[ci.long()]
+    return int(keep.sum().item()), int(dmask.sum().item())
+
+
+def roofline_entry(disc, cls, avg_ms, hbm_gbs, hbm_src, pk, used=None):
     """Algorithmic work of one launch of the given kernel class on this workload, against the
     FP64 FMA peak measured in this process (the operator product and the assembly stages
-    are bound by GB300's FP64 pipe, not by HBM: one DFMA per 8-byte value)."""
+    are bound by GB300's FP64 pipe, not by HBM: one DFMA per 8-byte value).  used: for the
+    Krylov product, (entries it multiplies, Dirichlet rows it copies)."""
     N, nnz = disc.N, disc.nnz
     fp64 = pk["fp64_tflops"]
     src = "measured in this run (iga_measure_peaks, DFMA chains)"
     t = avg_ms * 1e-3
     if cls == "spmv":
-        # values (columns follow from the stencil), rowptr, x read, y written; one FP64 FMA per value
-        bytes_ = nnz * 8 + (N + 1) * 8 + 2 * N * 8
-        flops = 2.0 * nnz
+        # the product with the Dirichlet-fixed Jacobian: one FP64 FMA and one 8-byte value per
+        # entry off the Dirichlet rows and columns; rowptr, x read, y written
+        ent, ndir = used if used else (nnz, 0)
+        bytes_ = ent * 8 + (N + 1) * 8 + 2 * N * 8
+        flops = 2.0 * ent
         traffic = SPMV_DRAM_BYTES_ANNULUS64 if NEL == 64 else None
-        return {"kernel": "k_spmv_stencil (FP64 values, stencil columns)", "bound": "alu", "achieved": flops / t / 1e12,
+        return {"kernel": "k_spmv_fixed (FP64 values, stencil columns, Dirichlet rows copied, zero columns of the last axis's Dirichlet faces skipped)",
+                "bound": "alu", "achieved": flops / t / 1e12, "entries_multiplied": ent, "stored_entries": nnz,
+                "dirichlet_rows": ndir,
                 "peak": fp64, "unit": "TFLOP/s", "frac": flops / t / 1e12 / fp64, "traffic": traffic,
                 "traffic_capture": SPMV_TRAFFIC_CAPTURE if traffic else None, "peak_source": src,
                 "avg_launch_ms": avg_ms, "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": bytes_,

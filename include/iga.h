@@ -319,13 +319,19 @@ iga_status iga_batch_offsets(iga_batch_t batch, int64_t *offsets);
  * ctas_per_sm * threads_per_cta <= 2048).  Default 1 x 512.  IGA_EINVAL otherwise.
  * The autotuner in paper_1305_4452_gb300/autotune.py chooses it. */
 iga_status iga_batch_set_launch(iga_batch_t batch, int ctas_per_sm, int threads_per_cta);
-/* Work-unit shape of the persistent kernel's Gram-Schmidt dot products: each of the
- * j+1 dots of an orthogonalisation pass is split into dot_chunks row ranges, one warp
- * per (dot, range), their sums added in range order (0: as many ranges as keep every
- * warp busy, at most 16).  Default 1 (one warp per dot).  Results depend on the shape
- * only through the order of additions.  0..16, else IGA_EINVAL.  The autotuner in
- * paper_1305_4452_gb300/autotune.py chooses it with the launch shape. */
-iga_status iga_batch_set_tiles(iga_batch_t batch, int dot_chunks);
+/* Work-unit and tile shapes of the persistent kernel.
+ * dot_chunks: each of the j+1 Gram-Schmidt dot products of an orthogonalisation pass is
+ *   split into dot_chunks row ranges, one warp per (dot, range), their sums added in
+ *   range order (0: as many ranges as keep every warp busy, at most 16).  Default 1 (one
+ *   warp per dot).  Results depend on it only through the order of additions.
+ * jac_lines: element tile of the Jacobian's first sum-factorisation stage (Eq. jacobian,
+ *   axis 0): Gauss lines whose Q00 and kappa values are staged in shared memory at once,
+ *   each pair-table value then serving that many lines (1, 2, 4 or 8; fewer when the
+ *   lines of a large instance do not fit).  Default 4.  The Jacobian does not depend on
+ *   it (same terms, same order).
+ * Out-of-range values return IGA_EINVAL and change nothing.  The autotuner in
+ * paper_1305_4452_gb300/autotune.py chooses both with the launch shape. */
+iga_status iga_batch_set_tiles(iga_batch_t batch, int dot_chunks, int jac_lines);
 /* Solve every instance from the initial values in U (device, concatenated,
  * in/out) with Newton + GMRES(m, at most 64) + Jacobi (Jacobi CG with
  * opts->ksp = IGA_KSP_CG), FP64 residual and norms, FP32 sum-factorised Jacobian.  One graph launch (captured on the first call
@@ -378,13 +384,14 @@ const char *iga_nn_last_error(iga_nn_t nn);
  *   u at Gauss points, 4 Jacobian stage 1, 5 Jacobian stage 2, 6 Jacobian final
  *   stage, 7 SpMV, 8 Gram-Schmidt multi-dot/update, 9 GMRES scalar kernels,
  *   10 vector kernels, 11 stiffness + reaction combine, 12 CSR pattern,
- *   13 tensor-core element matrices, 14 element-matrix gather.
+ *   13 tensor-core element matrices, 14 element-matrix gather, 15 the stiffness
+ *   product K U of the split residual (class 7 is then the Krylov products alone).
  * iga_profile_enable(iga, mask): classes whose bit is set get a CUDA event pair
  * recorded around each launch on the library's stream (mask 0: timing off;
  * launches are always counted).  iga_profile_read synchronises the stream,
  * returns the totals since the last read (ms[c], timed[c] = timed launches,
  * launches[c] = all launches) and resets them. */
-#define IGA_NCLASS 15
+#define IGA_NCLASS 16
 typedef struct {
   double ms[16];
   long long timed[16];
@@ -410,6 +417,14 @@ typedef struct {
   int sms;
 } iga_peaks;
 iga_status iga_measure_peaks(void *stream, iga_peaks *out);
+
+/* y[i] = e^x[i], i < n, with the FP64 exponential that the residual, Q00 and reaction
+ * kernels evaluate at the Gauss points (the Bratu term lambda e^u of Eq. residual and
+ * Eq. jacobian): the table-driven method of Tang (ACM TOMS 1989), about one unit in the
+ * last place.  x and y are device arrays of n doubles (caller-owned; they may be the same
+ * array); stream-ordered on `stream`, no synchronisation.  n = 0 does nothing;
+ * n < 0 or a NULL array with n > 0 returns IGA_EINVAL. */
+iga_status iga_exp_eval(void *stream, const double *x, double *y, int64_t n);
 
 /* Release every library-owned device buffer.  NULL is accepted. */
 void iga_destroy(iga_t iga);

@@ -1,19 +1,23 @@
-"""Autotuner for the batched solver's launch and work-unit shapes.
+"""Autotuner for the batched solver's launch, element-tile and work-unit shapes.
 
 The persistent batched kernel is compiled for several launch shapes: 256 threads
 per CTA (one resident CTA per SM with up to 255 registers, or two or more with
 128) and 512 (128 registers), on a grid of SMs x CTAs per SM.  More threads per
 instance put more loads in flight in the memory-bound Krylov phases; fewer
-registers spill more in the element kernels.  The Gram-Schmidt dots of its GMRES
-have a work-unit shape too: each dot split into R row chunks, one warp per
-(dot, chunk) -- one chunk leaves most warps idle while the basis is short, many
-chunks add partial sums.  ``tune(batch, U, opts)`` first times one solve per
-launch shape, then, on the fastest one, one solve per dot shape (with GMRES; CG
-has no such dots), keeps the fastest pair, applies it with
+registers spill more in the element kernels.  The Jacobian's first
+sum-factorisation stage runs on element tiles of L Gauss lines staged in shared
+memory: a larger L reuses each pair-table value over more lines but gives fewer
+tiles to spread over the CTA and more registers per thread.  The Gram-Schmidt dots
+of its GMRES have a work-unit shape too: each dot split into R row chunks, one warp
+per (dot, chunk) -- one chunk leaves most warps idle while the basis is short, many
+chunks add partial sums.  ``tune(batch, U, opts)`` times one solve per launch shape,
+then, on the fastest one, one solve per element tile L, then (with GMRES; CG has no
+such dots) one per dot shape, keeps the fastest combination, applies it with
 ``iga_batch_set_launch`` / ``iga_batch_set_tiles`` and records it in a JSON cache
-keyed by a signature of the batch (instance count and the histogram of mesh
-sizes and degrees), so a later batch with the same mix starts from the cached
-shapes without re-timing.
+keyed by a signature of the batch (instance count and the histogram of mesh sizes
+and degrees), so a later batch with the same mix starts from the cached shapes
+without re-timing.  A shape other than the default replaces it only when it is at
+least 3 % faster, so that timing noise does not pick between equal shapes.
 """
 import hashlib
 import json
@@ -22,6 +26,8 @@ import time
 
 # (CTAs per SM, threads per CTA)
 CANDIDATES = ((1, 256), (2, 256), (4, 256), (1, 512))
+# Gauss lines per element tile of the Jacobian's first stage (the first is the default)
+LINE_CANDIDATES = (4, 1, 2, 8)
 # row chunks per Gram-Schmidt dot (0: enough chunks to keep every warp busy)
 DOT_CANDIDATES = (1, 2, 4, 0)
 
@@ -72,13 +78,20 @@ def _time_solve(batch, U, U0, opts):
     return 1e3 * (time.perf_counter() - t0)
 
 
-def tune(batch, instances, U, opts=None, candidates=CANDIDATES, dot_candidates=DOT_CANDIDATES, cache_path=None,
-         retime=False):
-    """Choose the launch shape and the Gram-Schmidt dot shape of `batch` (an iga.Batch
-    built from `instances`) by timing one solve per candidate from the initial values in U
-    (restored before each timing): every (CTAs per SM, threads per CTA) first, then every
-    row-chunk count of the dots on the fastest launch shape (when opts selects GMRES).
-    Returns {"ctas_per_sm": c, "threads": t, "dot_chunks": r, "times_ms": {...},
+def _pick(times, default_key):
+    """The fastest key, unless it is within 3 % of the default's time."""
+    best = min(times, key=times.get)
+    return best if times[best] < 0.97 * times[default_key] else default_key
+
+
+def tune(batch, instances, U, opts=None, candidates=CANDIDATES, line_candidates=LINE_CANDIDATES,
+         dot_candidates=DOT_CANDIDATES, cache_path=None, retime=False):
+    """Choose the launch shape, the element tile of the Jacobian and the Gram-Schmidt dot
+    shape of `batch` (an iga.Batch built from `instances`) by timing one solve per
+    candidate from the initial values in U (restored before each timing): every (CTAs per
+    SM, threads per CTA) first, then every element tile on the fastest launch shape, then
+    every row-chunk count of the dots (when opts selects GMRES).  Returns
+    {"ctas_per_sm": c, "threads": t, "jac_lines": L, "dot_chunks": r, "times_ms": {...},
     "cached": bool}."""
     sig = signature(instances)
     gmres = opts is None or int(getattr(opts, "ksp", 0)) == 0
@@ -87,34 +100,41 @@ def tune(batch, instances, U, opts=None, candidates=CANDIDATES, dot_candidates=D
     if not retime and key_sig in cache and "threads" in cache[key_sig]:
         e = cache[key_sig]
         best = (int(e["ctas_per_sm"]), int(e["threads"]))
+        lines, dots = int(e.get("jac_lines", line_candidates[0])), int(e.get("dot_chunks", 1))
         batch.set_launch(*best)
-        batch.set_tiles(int(e.get("dot_chunks", 1)))
-        return {"ctas_per_sm": best[0], "threads": best[1], "dot_chunks": int(e.get("dot_chunks", 1)),
+        batch.set_tiles(dots, lines)
+        return {"ctas_per_sm": best[0], "threads": best[1], "jac_lines": lines, "dot_chunks": dots,
                 "times_ms": e.get("times_ms", {}), "cached": True}
     U0 = U.clone()
     times = {}
-    batch.set_tiles(1)
+    lines0 = line_candidates[0]
+    batch.set_tiles(1, lines0)
     for c, t in candidates:
         batch.set_launch(c, t)
-        times["%dx%d/dots1" % (c, t)] = _time_solve(batch, U, U0, opts)
+        times["%dx%d/lines%d/dots1" % (c, t, lines0)] = _time_solve(batch, U, U0, opts)
     key = min(times, key=times.get)
     best = tuple(int(v) for v in key.split("/")[0].split("x"))
     batch.set_launch(*best)
+    pre = "%dx%d" % best
+    # element tile of the Jacobian's first stage, on the fastest launch shape
+    for L in line_candidates[1:]:
+        batch.set_tiles(1, L)
+        times["%s/lines%d/dots1" % (pre, L)] = _time_solve(batch, U, U0, opts)
+    alt = {L: times["%s/lines%d/dots1" % (pre, L)] for L in line_candidates}
+    lines = _pick(alt, lines0)
     dots = 1
     if gmres:
-        base = times["%dx%d/dots1" % best]
         for r in dot_candidates:
             if r == 1:
                 continue
-            batch.set_tiles(r)
-            times["%dx%d/dots%d" % (best[0], best[1], r)] = _time_solve(batch, U, U0, opts)
-        # another dot shape replaces one chunk per dot only when it is clearly faster (3 %)
-        alt = {int(k.split("/dots")[1]): v for k, v in times.items() if k.startswith("%dx%d/" % best)}
-        r_best = min(alt, key=alt.get)
-        if alt[r_best] < 0.97 * base:
-            dots = r_best
-    batch.set_tiles(dots)
+            batch.set_tiles(r, lines)
+            times["%s/lines%d/dots%d" % (pre, lines, r)] = _time_solve(batch, U, U0, opts)
+        alt = {r: times["%s/lines%d/dots%d" % (pre, lines, r)] for r in dot_candidates}
+        dots = _pick(alt, 1)
+    batch.set_tiles(dots, lines)
     U.copy_(U0)
-    cache[key_sig] = {"ctas_per_sm": best[0], "threads": best[1], "dot_chunks": dots, "times_ms": times}
+    cache[key_sig] = {"ctas_per_sm": best[0], "threads": best[1], "jac_lines": lines, "dot_chunks": dots,
+                      "times_ms": times}
     save_cache(cache, cache_path)
-    return {"ctas_per_sm": best[0], "threads": best[1], "dot_chunks": dots, "times_ms": times, "cached": False}
+    return {"ctas_per_sm": best[0], "threads": best[1], "jac_lines": lines, "dot_chunks": dots, "times_ms": times,
+            "cached": False}

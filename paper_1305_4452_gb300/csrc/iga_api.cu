@@ -435,7 +435,13 @@ static iga_status newton_jacobian(iga_s *h, const double *U, bool f32, bool reus
   // J(U) = K + reaction(U): the stiffness K does not depend on U or lambda
   if (f32) {
     if (!h->Kstiff_f) CK(cudaMalloc((void **)&h->Kstiff_f, h->nnz * sizeof(float)));
-    if (!h->K_valid_f) { CK(launch_jacobian32(h, nullptr, h->Kstiff_f, 1, nullptr)); h->K_valid_f = true; }
+    if (!h->K_valid_f) {
+      // the FP64 stiffness of the split residual, rounded once, is a closer FP32 stiffness
+      // than an FP32 assembly and costs one pass over the values instead of three stages
+      if (h->K_valid) CK(launch_round_f32(h, h->Kstiff, h->Kstiff_f, h->nnz));
+      else CK(launch_jacobian32(h, nullptr, h->Kstiff_f, 1, nullptr));
+      h->K_valid_f = true;
+    }
     CK(launch_jacobian32(h, U, h->J32, 2, h->Kstiff_f));
   } else {
     if (!h->Kstiff) CK(cudaMalloc((void **)&h->Kstiff, h->nnz * sizeof(double)));
@@ -533,7 +539,9 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
     int its = 0;
     cudaError_t ce = cudaSuccess;
     const void *Jv = mf ? nullptr : (f32 ? (const void *)h->J32 : (const void *)h->J64);
-    const int kind = mf ? 2 : (f32 ? 1 : 0);
+    // the FP64 Jacobian carries the exact Dirichlet fix: its product skips the fixed rows
+    // and the zero columns
+    const int kind = mf ? 2 : (f32 ? 1 : (o.jac == IGA_FP64 ? 3 : 0));
     int grc = (o.ksp == IGA_KSP_CG) ? cg_solve(h, Jv, kind, Ft, dU, tol_abs, o.max_krylov, &its, &ce)
                                     : gmres_solve(h, Jv, kind, Ft, dU, tol_abs, o.gmres_restart, o.max_krylov, &its, &ce);
     if (grc < 0) {

@@ -11,7 +11,8 @@
 //             sum factorisation, then a fixed-order gather per control variable;
 //   Jacobian  (FP32; Eq. jacobian): global sum factorisation over the instance's
 //             mesh, axis 0 then axis 1, each entry written once, into a layout
-//             sliced by 32 rows for the operator products (see jslot);
+//             sliced by 32 rows for the operator products (see jslot); axis 0 runs
+//             on tiles of Gauss lines staged in shared memory (see b_stage1);
 //   GMRES(m)  with right Jacobi preconditioning; FP64 Krylov vectors and
 //             classical Gram-Schmidt applied twice (one warp per dot product,
 //             fixed-order warp reductions), FP32 operator products; or Jacobi CG;
@@ -30,6 +31,7 @@
 #include <string>
 #include <vector>
 
+#include "iga_exp.h"
 #include "iga_internal.h"
 
 namespace {
@@ -53,11 +55,12 @@ struct BInst {
   int64_t uoff;          // offset of this instance's U in the caller's array
   const double *ck;      // [nelem][nq] kappa * jw
   const double *cr;      // [nelem][nq] jw
-  const float *ck32, *cr32;
+  const float *ck32, *cr32;  // kappa jw, line-major [x1][x0]; jw, element-major [e][qp]
   double *F, *dU, *Ut, *Ft, *dinv, *w, *V;  // V: (mmax+1) x N
   double *Fe;            // [nelem][nen]
   float *J;              // Jacobian values, sliced by 32 rows (see jslot)
-  float *T1, *q00, *z32;
+  float *T1;             // stage-1 groups G0, G2: [2][x1][slot s0 < 2p+1][i0]
+  float *q00, *z32;      // q00: [x1][x0], line-major (x = e q + g)
 };
 
 // The batch Jacobian is stored by slices of 32 consecutive rows, slot-major within a
@@ -75,6 +78,7 @@ struct BArgs {
   double *U;
   iga_newton_opts opts;
   int dot_chunks;  // work unit of the Gram-Schmidt dots: row chunks per dot (0: as many as keep every warp busy)
+  int jac_lines;   // element tile of the Jacobian's first stage: Gauss lines per shared-memory tile (1, 2, 4, 8)
 };
 
 struct BRep {
@@ -93,7 +97,10 @@ struct Cta {
   int tid, nt, lane, warp, nw;
   double *red;  // shared, >= 36 doubles
   float *zs;    // shared FP32 operand vector of the operator products (N floats), or null
+  float *tile;  // the same dynamic shared memory (tile_cap floats), for the Jacobian's line tiles
+  int tile_cap;
   int dot_chunks;  // row chunks per Gram-Schmidt dot (BArgs::dot_chunks)
+  int jac_lines;   // Gauss lines per stage-1 tile (BArgs::jac_lines)
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -193,7 +200,7 @@ __device__ void b_residual(const BInst &I, const double *__restrict__ U, double 
         }
         const int qp = g1 * Q + g0;
         const double ck = I.ck[(size_t)e * NQ + qp], cr = I.cr[(size_t)e * NQ + qp];
-        vs[qp] = -cr * lam * exp(u);
+        vs[qp] = -cr * lam * iga_exp(u);
         v0[qp] = ck * d0;
         v1[qp] = ck * d1;
       }
@@ -244,13 +251,64 @@ __device__ void b_residual(const BInst &I, const double *__restrict__ U, double 
 }
 
 // ---------------------------------------------------------------- Jacobian --
+// Stage 1 (axis 0) on tiles of L Gauss lines x1: the tile's Q00 and kappa jw lines are
+// copied to shared memory (contiguous, line-major), then each work item, a 1D pair
+// (i0, slot s0) of axis 0, forms G0 = sum P00 Q00 + P11 kappa jw and G2 = sum P00 kappa jw
+// over the pair's common Gauss points for all L lines at once, so that each pair-table
+// value serves L lines.  L is the element-tile shape the autotuner chooses (Cta::jac_lines);
+// it changes neither the terms nor their order, only the reuse.
+template <int P, int L>
+__device__ void b_stage1(const BInst &I, const Cta &c) {
+  constexpr int Q = P + 1, WF = 2 * P + 1;
+  const BMesh &M = I.m;
+  const int X = M.nel * Q, n = M.n;
+  const size_t plane = (size_t)X * WF * n;
+  float *lq = c.tile, *lk = c.tile + L * X;  // [L][X] each
+  for (int x1a = 0; x1a < X; x1a += L) {
+    const int nl = min(L, X - x1a);
+    for (int idx = c.tid; idx < nl * X; idx += c.nt) {
+      lq[idx] = I.q00[(size_t)x1a * X + idx];
+      lk[idx] = I.ck32[(size_t)x1a * X + idx];
+    }
+    __syncthreads();
+    for (int it = c.tid; it < WF * n; it += c.nt) {
+      const int s0 = it / n, i0 = it - s0 * n;
+      if (s0 > M.r[i0] - M.l[i0]) continue;
+      const int pi = M.pair_off[i0] + s0;
+      const int xs = M.pair_x0[pi], cnt = M.pair_np[pi];
+      const float *pv = M.pair_val + (size_t)M.pair_po[pi] * IGA_PVS;
+      float g0[L], g2[L];
+#pragma unroll
+      for (int l = 0; l < L; l++) g0[l] = g2[l] = 0.f;
+      for (int k = 0; k < cnt; k++) {
+        const float p00 = pv[IGA_PVS * k + 0], p11 = pv[IGA_PVS * k + 3];
+#pragma unroll
+        for (int l = 0; l < L; l++) {
+          const float q = lq[l * X + xs + k], ck = lk[l * X + xs + k];
+          g0[l] = fmaf(p00, q, g0[l]);
+          g0[l] = fmaf(p11, ck, g0[l]);
+          g2[l] = fmaf(p00, ck, g2[l]);
+        }
+      }
+#pragma unroll
+      for (int l = 0; l < L; l++)
+        if (l < nl) {
+          const size_t o = ((size_t)(x1a + l) * WF + s0) * n + i0;
+          I.T1[o] = g0[l];
+          I.T1[plane + o] = g2[l];
+        }
+    }
+    __syncthreads();
+  }
+}
+
 template <int P>
 __device__ void b_jacobian(const BInst &I, const double *__restrict__ U, float *__restrict__ J, const Cta &c) {
-  constexpr int N1 = P + 1, Q = P + 1, NQ = Q * Q;
+  constexpr int N1 = P + 1, Q = P + 1, NQ = Q * Q, WF = 2 * P + 1;
   const BMesh &M = I.m;
-  const int nel = M.nel, X = nel * Q, np = M.np;
+  const int nel = M.nel, X = nel * Q, np = M.np, n = M.n;
   const float lam = (float)I.lambda;
-  // Q00 = -jw lambda e^u at every Gauss point (u interpolated in FP32)
+  // Q00 = -jw lambda e^u at every Gauss point (u interpolated in FP32), line-major
   for (int e = c.tid; e < nel * nel; e += c.nt) {
     const int e0 = e % nel, e1 = e / nel;
     const double *B0 = M.tab + (size_t)e0 * Q * N1 * 2, *B1 = M.tab + (size_t)e1 * Q * N1 * 2;
@@ -273,46 +331,40 @@ __device__ void b_jacobian(const BInst &I, const double *__restrict__ U, float *
 #pragma unroll
         for (int a1 = 0; a1 < N1; a1++) u = fmaf((float)B1[(g1 * N1 + a1) * 2], T[a1][g0], u);
         const int qp = g1 * Q + g0;
-        I.q00[(size_t)e * NQ + qp] = -I.cr32[(size_t)e * NQ + qp] * lam * expf(u);
+        I.q00[(size_t)(e1 * Q + g1) * X + e0 * Q + g0] = -I.cr32[(size_t)e * NQ + qp] * lam * expf(u);
       }
   }
   __syncthreads();
-  // stage 1 (axis 0): G0 = sum P00 Q00 + P11 ck ;  G2 = sum P00 ck
-  const size_t plane = (size_t)X * np;
-  for (int wi = c.tid; wi < X * np; wi += c.nt) {
-    const int x1 = wi / np, pi = wi % np;
-    const int e1 = x1 / Q, g1 = x1 % Q;
-    const int xs = M.pair_x0[pi], cnt = M.pair_np[pi];
-    const float *pv = M.pair_val + (size_t)M.pair_po[pi] * IGA_PVS;
-    float g0a = 0.f, g2a = 0.f;
-    for (int k = 0; k < cnt; k++) {
-      const int x0 = xs + k, e0 = x0 / Q, gg0 = x0 % Q;
-      const size_t o = (size_t)(e1 * nel + e0) * NQ + g1 * Q + gg0;
-      const float ck = I.ck32[o];
-      g0a = fmaf(pv[IGA_PVS * k + 0], I.q00[o], g0a);
-      g0a = fmaf(pv[IGA_PVS * k + 3], ck, g0a);
-      g2a = fmaf(pv[IGA_PVS * k + 0], ck, g2a);
-    }
-    I.T1[(size_t)x1 * np + pi] = g0a;
-    I.T1[plane + (size_t)x1 * np + pi] = g2a;
+  // stage 1 (axis 0), on tiles of L lines that fit the shared memory
+  int L = c.jac_lines;
+  while (L > 1 && 2 * L * X > c.tile_cap) L >>= 1;
+  switch (L) {
+    case 8: b_stage1<P, 8>(I, c); break;
+    case 4: b_stage1<P, 4>(I, c); break;
+    case 2: b_stage1<P, 2>(I, c); break;
+    default: b_stage1<P, 1>(I, c); break;
   }
-  __syncthreads();
-  // final stage (axis 1): J = sum P1^00 G0 + P1^11 G2, one entry per work item
-  for (int wi = c.tid; wi < np * np; wi += c.nt) {
-    const int p1 = wi / np, p0 = wi % np;
+  // final stage (axis 1): J = sum P1^00 G0 + P1^11 G2, one entry per work item; items
+  // (axis-1 pair, slot s0, i0) with i0 fastest, so that a warp reads consecutive G values
+  // and writes consecutive rows of one slot of the sliced layout
+  const size_t plane = (size_t)X * WF * n;
+  for (int wi = c.tid; wi < np * WF * n; wi += c.nt) {
+    const int p1 = wi / (WF * n), rem = wi - p1 * (WF * n);
+    const int s0 = rem / n, i0 = rem - s0 * n;
+    if (s0 > M.r[i0] - M.l[i0]) continue;
+    const int i1 = M.pair_i[p1], s1 = p1 - M.pair_off[i1];
     const int xs = M.pair_x0[p1], cnt = M.pair_np[p1];
     const float *pv = M.pair_val + (size_t)M.pair_po[p1] * IGA_PVS;
     float acc = 0.f;
     for (int k = 0; k < cnt; k++) {
-      const size_t o = (size_t)(xs + k) * np + p0;
+      const size_t o = ((size_t)(xs + k) * WF + s0) * n + i0;
       acc = fmaf(pv[IGA_PVS * k + 0], I.T1[o], acc);
       acc = fmaf(pv[IGA_PVS * k + 3], I.T1[plane + o], acc);
     }
-    const int i0 = M.pair_i[p0], i1 = M.pair_i[p1];
-    const int j0 = M.l[i0] + (p0 - M.pair_off[i0]), j1 = M.l[i1] + (p1 - M.pair_off[i1]);
-    const int A = i0 + M.n * i1, B = j0 + M.n * j1;
-    if (on_bnd(i0, i1, M.n) || on_bnd(j0, j1, M.n)) acc = (A == B) ? 1.f : 0.f;
-    J[jslot(A, (p1 - M.pair_off[i1]) * (2 * P + 1) + (p0 - M.pair_off[i0]), 2 * P + 1)] = acc;
+    const int j0 = M.l[i0] + s0, j1 = M.l[i1] + s1;
+    const int A = i0 + n * i1, B = j0 + n * j1;
+    if (on_bnd(i0, i1, n) || on_bnd(j0, j1, n)) acc = (A == B) ? 1.f : 0.f;
+    J[jslot(A, s1 * WF + s0, WF)] = acc;
   }
   __syncthreads();
 }
@@ -629,7 +681,10 @@ __global__ void __launch_bounds__(NT, MINB) k_batch(const BInst *__restrict__ in
   c.nw = blockDim.x >> 5;
   c.red = red;
   c.zs = nullptr;
+  c.tile = zs_dyn;
+  c.tile_cap = zcap;
   c.dot_chunks = args->dot_chunks;
+  c.jac_lines = args->jac_lines;
   const iga_newton_opts o = args->opts;
   for (;;) {
     if (c.tid == 0) cur = atomicAdd(counter, 1);
@@ -682,7 +737,9 @@ __global__ void k_batch_coeffs(const BInst *__restrict__ insts, int count, const
   }
   ck_all[t] = kappa * jw;
   cr_all[t] = jw;
-  ck32_all[t] = (float)(kappa * jw);
+  // the FP32 kappa jw of the Jacobian's line tiles: line-major [x1][x0], x = e q + g
+  const int X = M.nel * Q;
+  ck32_all[eoff[lo] + (int64_t)(e1 * Q + g1) * X + e0 * Q + g0] = (float)(kappa * jw);
   cr32_all[t] = (float)jw;
 }
 
@@ -706,6 +763,7 @@ struct iga_batch_s {
   std::vector<int64_t> uoff;       // count + 1
   int threads = 512, ctas_per_sm = 1, nsm = 0;
   int dot_chunks = 1;              // work unit of the Gram-Schmidt dots (iga_batch_set_tiles)
+  int jac_lines = 4;               // Gauss lines per stage-1 tile of the Jacobian (iga_batch_set_tiles)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int graph_threads = 0, graph_ctas = 0;
@@ -828,10 +886,15 @@ static iga_status batch_create_impl(iga_batch_s *b, int count, const iga_desc *d
   for (int i = 0; i < count; i++) {
     const BMesh &M = b->meshes[mi[i]].dev;
     int64_t nelem = (int64_t)M.nel * M.nel, nq = (int64_t)M.q * M.q, nen = (int64_t)(M.p + 1) * (M.p + 1);
+    // one Gauss line of Q00 and one of kappa jw must fit the shared-memory tile
+    if (2 * (int64_t)M.nel * M.q > BZCAP_MAX) {
+      b->err = iga_format("instance %d: %d elements per direction exceed the batched solver's line tile", i, M.nel);
+      return IGA_EINVAL;
+    }
     b->uoff[i + 1] = b->uoff[i] + M.N;
     b->zcap = std::max(b->zcap, M.N);
     dbl += 6 * (int64_t)M.N + (int64_t)(b->mmax + 1) * M.N + nelem * nen + 2 * nelem * nq + 8;
-    flt += jsize(M.N, M.p) + 32 + 2 * (int64_t)M.nel * M.q * M.np + nelem * nq + M.N + 2 * nelem * nq + 8;
+    flt += jsize(M.N, M.p) + 32 + 2 * (int64_t)M.nel * M.q * (2 * M.p + 1) * M.n + nelem * nq + M.N + 2 * nelem * nq + 8;
     qpoff[i + 1] = qpoff[i] + nelem * nq;
   }
   qp_total = qpoff[count];
@@ -869,7 +932,7 @@ static iga_status batch_create_impl(iga_batch_s *b, int count, const iga_desc *d
     I.Fe = dp; dp += nelem * nen;
     fp = far + ((fp - far + 31) / 32) * 32;  // slices start on 128 bytes
     I.J = fp; fp += jsize(M.N, M.p);
-    I.T1 = fp; fp += 2 * (int64_t)M.nel * M.q * M.np;
+    I.T1 = fp; fp += 2 * (int64_t)M.nel * M.q * (2 * M.p + 1) * M.n;
     I.q00 = fp; fp += nelem * nq;
     I.z32 = fp; fp += M.N;
   }
@@ -978,13 +1041,18 @@ extern "C" iga_status iga_batch_set_launch(iga_batch_t b, int ctas_per_sm, int t
   return IGA_OK;
 }
 
-extern "C" iga_status iga_batch_set_tiles(iga_batch_t b, int dot_chunks) {
+extern "C" iga_status iga_batch_set_tiles(iga_batch_t b, int dot_chunks, int jac_lines) {
   if (!b) return IGA_EINVAL;
   if (dot_chunks < 0 || dot_chunks > BDOT_MAX) {
     b->err = iga_format("dot_chunks must be in 0..%d", BDOT_MAX);
     return IGA_EINVAL;
   }
+  if (jac_lines != 1 && jac_lines != 2 && jac_lines != 4 && jac_lines != 8) {
+    b->err = "jac_lines must be 1, 2, 4 or 8";
+    return IGA_EINVAL;
+  }
   b->dot_chunks = dot_chunks;
+  b->jac_lines = jac_lines;
   return IGA_OK;
 }
 
@@ -1013,6 +1081,7 @@ extern "C" iga_status iga_batch_solve(iga_batch_t b, double *U, const iga_newton
   b->h_args->U = U;
   b->h_args->opts = o;
   b->h_args->dot_chunks = b->dot_chunks;  // read by the graph's argument copy at every replay
+  b->h_args->jac_lines = b->jac_lines;
   // the caller's pending work (any stream) completes before the solve reads U
   BCK(cudaDeviceSynchronize());
   if (!b->exec || b->graph_threads != b->threads || b->graph_ctas != b->ctas_per_sm) {

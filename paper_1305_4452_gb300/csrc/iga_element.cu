@@ -13,6 +13,9 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
+#include "iga_exp.h"
 #include "iga_internal.h"
 #include "iga_interp.h"
 
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(128) k_residual(DirArgs d0, DirArgs d1, DirArg
       s = q00[(size_t)e * NQ + qp] * ut;
     } else {
       double u = ut * rec[gl.invW * NQ];
-      s = -rec[gl.jwW * NQ] * lambda * exp(u);
+      s = -rec[gl.jwW * NQ] * lambda * iga_exp(u);
     }
     for (int a = 0; a < DIM; a++) s -= rec[(gl.g + a) * NQ] * v[a];
     X[qp] = s;
@@ -553,7 +556,7 @@ __global__ void __launch_bounds__(128) k_q00(DirArgs d0, DirArgs d1, DirArgs d2,
       continue;
     }
     if (RES) {
-      const double lex = lambda * exp(ut * rec[gl.invW * NQ]);
+      const double lex = lambda * iga_exp(ut * rec[gl.invW * NQ]);
       (base + SM::TAB + NEN)[qp] = -rec[gl.jwW * NQ] * lex;
       // the reaction part of Q00 at the same point, for the next Jacobian
       if (q00_out) {
@@ -566,7 +569,7 @@ __global__ void __launch_bounds__(128) k_q00(DirArgs d0, DirArgs d1, DirArgs d2,
     double v = 0.0;
     if (cs != 0.0) v = cs * rec[gl.gSg * NQ];
     if (cr != 0.0) {
-      v -= cr * rec[gl.jwW2 * NQ] * lambda * exp(ut * rec[gl.invW * NQ]);
+      v -= cr * rec[gl.jwW2 * NQ] * lambda * iga_exp(ut * rec[gl.invW * NQ]);
       if (shift != 0.0) v += cr * shift * rec[gl.jwW2 * NQ];
     }
     Q00[(size_t)e * NQ + qp] = v;
@@ -840,7 +843,7 @@ cudaError_t launch_q00_f32(iga_s *h, const double *U, double cs, double cr) {
 
 cudaError_t launch_residual_split(iga_s *h, const double *U, double *F, const double *K, double *KU) {
   DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
-  cudaError_t ce = launch_spmv64(h, K, U, KU);
+  cudaError_t ce = launch_spmv64_residual(h, K, U, KU);
   if (ce) return ce;
   constexpr int NE = 4;
   unsigned grid = (unsigned)((h->nelem + NE - 1) / NE);
@@ -968,4 +971,19 @@ cudaError_t launch_colidx(iga_s *h) {
   unsigned g = (unsigned)((h->N + 255) / 256);
   IGA_LAUNCH(h, KC_PATTERN, (k_colidx<<<g, 256, 0, h->stream>>>(a0, a1, a2, h->dim, h->rowptr, h->colidx, h->N)));
   return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_exp_eval(const double *__restrict__ x, double *__restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = iga_exp(x[i]);
+}
+}  // namespace
+
+extern "C" iga_status iga_exp_eval(void *stream, const double *x, double *y, int64_t n) {
+  if (n < 0 || (n > 0 && (!x || !y))) return IGA_EINVAL;
+  if (n == 0) return IGA_OK;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 8);
+  k_exp_eval<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(x, y, n);
+  return cudaGetLastError() == cudaSuccess ? IGA_OK : IGA_ECUDA;
 }

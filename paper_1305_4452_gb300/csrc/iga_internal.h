@@ -128,7 +128,7 @@ struct PerArgs {
 // Kernel classes for launch counting and event timing (iga_profile_*).
 enum KClass {
   KC_GEOM = 0, KC_RES_ELEM, KC_RES_GATHER, KC_Q00, KC_STAGE1, KC_STAGE2, KC_FINAL, KC_SPMV, KC_ORTH,
-  KC_GMRES_SCALAR, KC_VEC, KC_COMBINE, KC_PATTERN, KC_ELEM_TC, KC_ELEM_GATHER, KC_N
+  KC_GMRES_SCALAR, KC_VEC, KC_COMBINE, KC_PATTERN, KC_ELEM_TC, KC_ELEM_GATHER, KC_RES_SPMV, KC_N
 };
 
 struct ProfRec {
@@ -282,6 +282,8 @@ void iga_release(iga_s *h);
 // 3: full Jacobian without the Dirichlet fix
 cudaError_t launch_jacobian64(iga_s *h, const double *U, double *vals, int mode, const double *base);
 cudaError_t launch_jacobian32(iga_s *h, const double *U, float *vals, int mode, const float *base);
+// y = x rounded to FP32 (nnz-sized value arrays)
+cudaError_t launch_round_f32(iga_s *h, const double *x, float *y, int64_t n);
 size_t jacobian_t1_groups(int dim);
 // ---- mixed-precision Jacobian (iga_mixed.cu) ----
 bool mixed_supported(int dim, int p);
@@ -305,6 +307,10 @@ struct GsPartition {
 };
 GsPartition gs_partition(int64_t N);
 cudaError_t launch_spmv64(iga_s *h, const double *vals, const double *x, double *y);
+// the same product, counted and timed as the split residual's stiffness product
+cudaError_t launch_spmv64_residual(iga_s *h, const double *vals, const double *x, double *y);
+// y = J x for a Dirichlet-fixed Jacobian (rows e_A, zero columns skipped)
+cudaError_t launch_spmv64_fixed(iga_s *h, const double *vals, const double *x, double *y);
 cudaError_t launch_spmv32(iga_s *h, const float *vals, const double *x, double *y);
 // sliced copy of h->J32 (rows in slices of 32, slot-major) for the FP32 Krylov products
 cudaError_t launch_slice32(iga_s *h);

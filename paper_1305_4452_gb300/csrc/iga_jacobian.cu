@@ -16,6 +16,8 @@
 // counts drop to 4, 3 and 2 (2D: 3 and 2).  The reaction term alone (Q00 only) is one
 // chain of single contractions and can be added onto a previously assembled stiffness.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "iga_internal.h"
@@ -469,6 +471,31 @@ size_t jacobian_t2_groups(int dim) { return dim == 3 ? 3 : 0; }
 cudaError_t launch_jacobian64(iga_s *h, const double *U, double *vals, int mode, const double *base) {
   if (h->inner) return mode == 0 ? periodic_jacobian64(h, U, vals) : cudaErrorInvalidValue;
   return jacobian<double, double>(h, U, vals, mode, base);
+}
+
+namespace {
+// y = fl32(x), two values per thread and step (nnz-sized arrays: bound by HBM)
+__global__ void __launch_bounds__(256) k_round_f32(const double *__restrict__ x, float *__restrict__ y, int64_t n) {
+  const int64_t n2 = n / 2, stride = (int64_t)gridDim.x * blockDim.x;
+  const double2 *x2 = reinterpret_cast<const double2 *>(x);
+  float2 *y2 = reinterpret_cast<float2 *>(y);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += stride) {
+    const double2 v = x2[i];
+    y2[i] = make_float2((float)v.x, (float)v.y);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) y[n - 1] = (float)x[n - 1];
+}
+}  // namespace
+
+cudaError_t launch_round_f32(iga_s *h, const double *x, float *y, int64_t n) {
+  if (n <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (n / 2 + 255) / 256;
+  const int grid = (int)std::min<int64_t>(want > 0 ? want : 1, (int64_t)(sms > 0 ? sms : 1) * 8);
+  IGA_LAUNCH(h, KC_VEC, (k_round_f32<<<grid, 256, 0, h->stream>>>(x, y, n)));
+  return cudaGetLastError();
 }
 
 cudaError_t launch_jacobian32(iga_s *h, const double *U, float *vals, int mode, const float *base) {

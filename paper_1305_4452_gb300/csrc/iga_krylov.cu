@@ -137,6 +137,82 @@ __global__ void __launch_bounds__(256) k_spmv_stencil(StencilRows S, const int64
   if (row < N && lane == 0) y[row] = (double)acc;
 }
 
+// y = J x for an assembled Newton Jacobian after the Dirichlet fix: a Dirichlet row is
+// e_A and a Dirichlet column is zero off the diagonal.  A row of a Dirichlet function
+// gives y_A = x_A; every other row runs k_spmv_stencil's loop over a contiguous part of
+// its stored values: the planes of its stencil along the last axis that hold Dirichlet
+// columns (a Dirichlet face of that axis: bit 2 (DIM-1) + side of dmask) are skipped by
+// starting or ending the loop there.  The Dirichlet columns of the other axes are
+// interleaved with the rest and are multiplied as the exact zeros they are (skipping them
+// would make the value index depend on the column walk and serialise the value loads).
+// The sum runs over the same values less exact zeros; rows away from the Dirichlet faces
+// of the last axis take them in k_spmv_stencil's lanes and order.
+template <int DIM, int LPR>
+__global__ void __launch_bounds__(256) k_spmv_fixed(StencilRows S, const int64_t *__restrict__ rowptr,
+                                                    const double *__restrict__ val, const double *__restrict__ x,
+                                                    double *__restrict__ y, int N, const double *__restrict__ done, int dmask) {
+  if (done && done[0] != 0.0) return;
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = gid / LPR, lane = gid % LPR;
+  double acc = 0.0;
+  bool dir_row = false;
+  if (row < N) {
+    int i0, i1, i2 = 0, n1, n2 = 1;
+    if (DIM == 3) {
+      i2 = row / S.n01;
+      const int t = row - i2 * S.n01;
+      i1 = t / S.n0;
+      i0 = t - i1 * S.n0;
+      n1 = S.n01 / S.n0;
+      n2 = N / S.n01;
+    } else {
+      i1 = row / S.n0;
+      i0 = row - i1 * S.n0;
+      n1 = N / S.n0;
+    }
+    dir_row = ((dmask & 1) && i0 == 0) || ((dmask & 2) && i0 == S.n0 - 1) || ((dmask & 4) && i1 == 0) ||
+              ((dmask & 8) && i1 == n1 - 1) || (DIM == 3 && (((dmask & 16) && i2 == 0) || ((dmask & 32) && i2 == n2 - 1)));
+    if (!dir_row) {
+      const RowShape R = row_shape<DIM>(S, row);
+      // stencil planes along the last axis: [lo, lo + w) clipped to the non-Dirichlet ones
+      const int lo = DIM == 3 ? R.lo2 : R.lo1, w = DIM == 3 ? R.w2 : R.w1, nl = DIM == 3 ? n2 : n1;
+      const int fl = DIM == 3 ? 16 : 4, fh = DIM == 3 ? 32 : 8;
+      const int p0 = ((dmask & fl) && lo == 0) ? 1 : 0;
+      const int p1 = ((dmask & fh) && lo + w - 1 == nl - 1) ? w - 1 : w;
+      const int plane = DIM == 3 ? R.w0 * R.w1 : R.w0;
+      const int e0 = p0 * plane, e1 = p1 * plane;
+      const double *v = val + rowptr[row];
+      int ii = lane, jj = 0, kk = 0;
+      while (ii >= R.w0) { ii -= R.w0; jj++; }
+      if (DIM == 3) {
+        while (jj >= R.w1) { jj -= R.w1; kk++; }
+        kk += p0;
+      } else {
+        jj += p0;
+      }
+      int col = (R.lo0 + ii) + (R.lo1 + jj) * S.n0 + (R.lo2 + kk) * S.n01;
+      const int djj = S.n0 - R.w0, dkk = S.n01 - R.w1 * S.n0;
+#pragma unroll 4
+      for (int e = e0 + lane; e < e1; e += LPR) {
+        acc = fma(v[e], x[col], acc);
+        ii += LPR;
+        col += LPR;
+        while (ii >= R.w0) {
+          ii -= R.w0;
+          col += djj;
+          if (++jj == R.w1) {
+            jj = 0;
+            col += dkk;
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, LPR);
+  if (row < N && lane == 0) y[row] = dir_row ? x[row] : acc;
+}
+
 // Sliced copy of FP32 CSR values for the reduced-precision Krylov solves: rows in slices
 // of 32, slot-major within a slice.  Slot s = a + WF (b + WF c) of row A = (i0, i1, i2)
 // (WF = 2p+1, a < WF along axis 0, ...) holds the row's value for column
@@ -783,7 +859,7 @@ cudaError_t launch_slice32(iga_s *h) {
 }
 
 template <typename V>
-static cudaError_t spmv_launch(iga_s *h, const V *vals, const double *x, double *y, const double *done) {
+static cudaError_t spmv_launch(iga_s *h, const V *vals, const double *x, double *y, const double *done, int cls = KC_SPMV) {
   // Few lanes per row: the cross-lane reduction costs log2(LPR) FP64 adds on every
   // lane of the group, which on GB300's narrow FP64 pipe is not free; 4 lanes keep
   // the loads sector-efficient (4 x 8 B contiguous per row and step).
@@ -792,13 +868,37 @@ static cudaError_t spmv_launch(iga_s *h, const V *vals, const double *x, double 
   const int N = (int)h->N;
   unsigned grid = (unsigned)(((int64_t)N * 4 + 255) / 256);
   if (h->dim == 3)
-    IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<3, 4, V, double, double><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, x, y, N, done)));
+    IGA_LAUNCH(h, cls, (k_spmv_stencil<3, 4, V, double, double><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, x, y, N, done)));
   else
-    IGA_LAUNCH(h, KC_SPMV, (k_spmv_stencil<2, 4, V, double, double><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, x, y, N, done)));
+    IGA_LAUNCH(h, cls, (k_spmv_stencil<2, 4, V, double, double><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, x, y, N, done)));
   return cudaGetLastError();
 }
 
+// the product with an assembled, Dirichlet-fixed FP64 Newton Jacobian (k_spmv_fixed)
+static cudaError_t spmv_fixed_launch(iga_s *h, const double *vals, const double *x, double *y, const double *done) {
+  if (h->inner) return periodic_spmv(h, vals, false, x, y, done);
+  int dmask = 0;
+  for (int d = 0; d < h->dim; d++)
+    for (int s = 0; s < 2; s++)
+      if (h->bnd.flag[d][s]) dmask |= 1 << (2 * d + s);
+  const StencilRows S = stencil_rows(h);
+  const int N = (int)h->N;
+  unsigned grid = (unsigned)(((int64_t)N * 4 + 255) / 256);
+  if (h->dim == 3)
+    IGA_LAUNCH(h, KC_SPMV, (k_spmv_fixed<3, 4><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, x, y, N, done, dmask)));
+  else
+    IGA_LAUNCH(h, KC_SPMV, (k_spmv_fixed<2, 4><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, x, y, N, done, dmask)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spmv64_fixed(iga_s *h, const double *vals, const double *x, double *y) {
+  return spmv_fixed_launch(h, vals, x, y, nullptr);
+}
+
 cudaError_t launch_spmv64(iga_s *h, const double *vals, const double *x, double *y) { return spmv_launch<double>(h, vals, x, y, nullptr); }
+cudaError_t launch_spmv64_residual(iga_s *h, const double *vals, const double *x, double *y) {
+  return spmv_launch<double>(h, vals, x, y, nullptr, KC_RES_SPMV);
+}
 cudaError_t launch_spmv32(iga_s *h, const float *vals, const double *x, double *y) { return spmv_launch<float>(h, vals, x, y, nullptr); }
 
 cudaError_t launch_diag_inv(iga_s *h, const void *vals, int is_f32, double *dinv) {
@@ -852,11 +952,13 @@ cudaError_t launch_nan_check(iga_s *h, const double *x, double *out_dev) {
 // until ||b - A x|| <= tol_abs or maxit iterations.  Returns 0 on convergence,
 // 1 when the cap was hit, 2 on breakdown/NaN, 3 when a grid barrier of the fused
 // orthogonalisation gave up, -1 on a CUDA error.
-// Operator of the Krylov solvers: FP64 values (kind 0), FP32 values (1) or the
-// matrix-free product J(U) x (2; vals unused, h->Q00 holds the reaction part at U)
+// Operator of the Krylov solvers: FP64 values (kind 0), FP32 values (1), the
+// matrix-free product J(U) x (2; vals unused, h->Q00 holds the reaction part at U) or
+// FP64 values of a Jacobian with the Dirichlet fix (3: rows e_A, zero columns skipped)
 static void apply_op(iga_s *h, const void *vals, int kind, const double *x, double *y, const double *done) {
   if (kind == 2) launch_jv(h, x, y, done);
   else if (kind == 1) spmv_f32_launch(h, (const float *)vals, x, y, done);
+  else if (kind == 3) spmv_fixed_launch(h, (const double *)vals, x, y, done);
   else spmv_launch<double>(h, (const double *)vals, x, y, done);
 }
 
@@ -870,7 +972,7 @@ static void jacobi_scaling(iga_s *h, const void *vals, int kind, double *dinv) {
     launch_jacobian_diagonal(h, dinv);
     IGA_LAUNCH(h, KC_VEC, (k_invert_diag<<<grid_for(h->N, 256, 4 * 152), 256, 0, h->stream>>>(dinv, h->N)));
   } else {
-    launch_diag_inv(h, vals, kind, dinv);
+    launch_diag_inv(h, vals, kind == 1, dinv);
   }
 }
 

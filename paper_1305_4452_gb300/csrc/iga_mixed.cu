@@ -18,6 +18,7 @@
 #include <float.h>
 #include <stdint.h>
 
+#include "iga_exp.h"
 #include "iga_internal.h"
 
 namespace {
@@ -436,7 +437,7 @@ __global__ void __launch_bounds__(FdShape<DIM, P>::THREADS) k_elem_fd(DirArgs d0
       v[1] = s01 * r[0] + s11 * r[1] + s12 * r[2];
       v[2] = s02 * r[0] + s12 * r[1] + s22 * r[2];
     }
-    sv = -rec[gl.jwW * NQ] * lambda * exp(u * rec[gl.invW * NQ]);
+    sv = -rec[gl.jwW * NQ] * lambda * iga_exp(u * rec[gl.invW * NQ]);
     for (int a = 0; a < DIM; a++) sv -= rec[(gl.g + a) * NQ] * v[a];
   };
   for (int q = tid; q < NQ; q += blockDim.x) {

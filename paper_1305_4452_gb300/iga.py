@@ -26,10 +26,11 @@ EXPORTS = ["iga_create", "iga_set_boundary_value", "iga_set_lambda", "iga_get_pa
            "iga_nn_forward", "iga_nn_loss_grad", "iga_nn_adam_step", "iga_nn_destroy", "iga_nn_last_error",
            "iga_nn_set_h1_weight", "iga_apply_jacobian", "iga_apply_jacobian_mf", "iga_form_jacobian_diagonal",
            "iga_form_residual_ts", "iga_form_jacobian_ts", "iga_ts_alpha_step", "iga_measure_peaks",
-           "iga_set_wait_limit", "iga_inject_stall", "iga_batch_set_tiles"]
+           "iga_set_wait_limit", "iga_inject_stall", "iga_batch_set_tiles", "iga_exp_eval"]
 
 KERNEL_CLASSES = ["geometry", "residual_element", "residual_gather", "q00", "jac_stage1", "jac_stage2", "jac_final",
-                  "spmv", "gs_orth", "gmres_scalar", "vector", "combine", "pattern", "elem_tc", "elem_gather"]
+                  "spmv", "gs_orth", "gmres_scalar", "vector", "combine", "pattern", "elem_tc", "elem_gather",
+                  "residual_spmv"]
 
 
 class IgaDesc(ctypes.Structure):
@@ -130,6 +131,7 @@ def lib():
         L.iga_measure_peaks.argtypes = [vp, ctypes.POINTER(IgaPeaks)]
         L.iga_set_wait_limit.argtypes = [vp, ctypes.c_double]
         L.iga_inject_stall.argtypes = [vp]
+        L.iga_exp_eval.argtypes = [vp, vp, vp, ctypes.c_int64]
         _lib = L
     return _lib
 
@@ -154,6 +156,17 @@ def newton_defaults():
     o = IgaNewtonOpts()
     lib().iga_newton_defaults(ctypes.byref(o))
     return o
+
+
+def exp_eval(x, y=None, stream=None):
+    """y = e^x (device FP64 tensors) with the library's Gauss-point exponential."""
+    import torch
+    if y is None:
+        y = torch.empty_like(x)
+    assert x.is_cuda and x.dtype == torch.float64 and x.is_contiguous() and y.shape == x.shape
+    _check(lib().iga_exp_eval(ctypes.c_void_p(_stream_ptr(stream)), ctypes.c_void_p(x.data_ptr()),
+                              ctypes.c_void_p(y.data_ptr()), x.numel()))
+    return y
 
 
 def measure_peaks(stream=None):
@@ -371,7 +384,7 @@ def _batch_lib():
         L.iga_batch_create.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.POINTER(vp)]
         L.iga_batch_offsets.argtypes = [vp, vp]
         L.iga_batch_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int]
-        L.iga_batch_set_tiles.argtypes = [vp, ctypes.c_int]
+        L.iga_batch_set_tiles.argtypes = [vp, ctypes.c_int, ctypes.c_int]
         L.iga_batch_solve.argtypes = [vp, vp, ctypes.POINTER(IgaNewtonOpts), ctypes.POINTER(IgaBatchReport)]
         L.iga_batch_destroy.argtypes = [vp]
         L.iga_batch_destroy.restype = None
@@ -420,6 +433,7 @@ class Batch:
             raise IgaError(rc, L.iga_batch_last_error(None).decode())
         self.h = h
         self.count = n
+        self.dot_chunks, self.jac_lines = 1, 4  # the library's defaults
         off = np.zeros(n + 1, dtype=np.int64)
         L.iga_batch_offsets(self.h, off.ctypes.data)
         self.offsets = off
@@ -433,13 +447,17 @@ class Batch:
         if rc != IGA_OK:
             raise IgaError(rc, L.iga_batch_last_error(self.h).decode())
 
-    def set_tiles(self, dot_chunks):
+    def set_tiles(self, dot_chunks, jac_lines=None):
         """Work unit of the Gram-Schmidt dots: row chunks per dot (0: enough to keep every
-        warp busy; 1..16)."""
+        warp busy; 1..16); element tile of the Jacobian's first stage: Gauss lines per
+        shared-memory tile (1, 2, 4, 8; None keeps the current value)."""
         L = _batch_lib()
-        rc = L.iga_batch_set_tiles(self.h, int(dot_chunks))
+        if jac_lines is None:
+            jac_lines = self.jac_lines
+        rc = L.iga_batch_set_tiles(self.h, int(dot_chunks), int(jac_lines))
         if rc != IGA_OK:
             raise IgaError(rc, L.iga_batch_last_error(self.h).decode())
+        self.dot_chunks, self.jac_lines = int(dot_chunks), int(jac_lines)
 
     def solve(self, U, opts=None, check=True):
         """U: torch CUDA float64 tensor of length self.total (in/out).  Returns a dict

@@ -173,3 +173,30 @@ def test_batch_dot_work_units_give_the_same_solutions(I):
         with pytest.raises(I.IgaError):
             b.set_tiles(bad)
     b.close()
+
+
+def test_batch_element_tiles_give_identical_jacobians_and_solutions(I):
+    """The element tile of the Jacobian's first stage (Gauss lines per shared-memory tile)
+    changes only the reuse of the pair tables, not the terms or their order: every tile
+    gives bit-identical solutions and iteration counts.  Out-of-range tiles are refused."""
+    ins = instances(9, seed=17, nmin=10, nmax=48, kappa_every=3)
+    ins.append({"nel": 128, "p": 3, "lam": 4.0})  # 512 Gauss points per line
+    b = I.Batch(ins)
+    o = I.newton_defaults()
+    o.ksp = I.IGA_KSP_CG
+    ref = None
+    for lines in (1, 2, 4, 8):
+        b.set_tiles(1, lines)
+        U = torch.zeros(b.total, dtype=torch.float64, device="cuda")
+        rep = b.solve(U, o)
+        assert rep["solved"] == len(ins)
+        if ref is None:
+            ref = (U, rep["newton_its"].copy(), rep["krylov_its"].copy())
+        else:
+            assert torch.equal(U, ref[0]), lines
+            assert np.array_equal(rep["newton_its"], ref[1]) and np.array_equal(rep["krylov_its"], ref[2])
+    for bad in (0, 3, 16, -1):
+        with pytest.raises(I.IgaError):
+            b.set_tiles(1, bad)
+    assert b.jac_lines == 8
+    b.close()
