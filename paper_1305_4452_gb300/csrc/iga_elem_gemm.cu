@@ -20,10 +20,14 @@
 //
 // k_elem_gemm, one CTA per (128 elements, 128 pairs) tile and group of element tiles,
 // 256 threads:
-//   - the T tile of the CTA's pair range (all of K) comes from a per-mesh cache built
-//     once by the same kernel in build mode (when the cache takes at most 1 GB), else
-//     two threads per pair row compute it from the type's 1D tables; it stays in shared
-//     memory for the CTA's group of element tiles;
+//   - the T tile of the CTA's pair range comes from a per-mesh cache built once by the
+//     same kernel in build mode (when the cache takes at most 1 GB), else two threads per
+//     pair row compute it from the type's 1D tables; it stays in shared memory for the
+//     CTA's group of element tiles.  When the T tile of the whole K does not fit (TF32 at
+//     p = 4, general maps at p = 4), K runs in passes of at most EG_PASS_CHUNKS chunks:
+//     the group (at most EG_PASS_GROUP element tiles) keeps one accumulator per tile in
+//     tensor memory, each pass loads its part of T and adds its chunks' MMAs to every
+//     tile's accumulator, and the epilogues follow the last pass;
 //   - two threads per row copy an element row of each Qv chunk (cp.async, 16 B) into the
 //     canonical K-major layout without swizzling (8-row x 16-byte core matrices, 128 B
 //     apart along M/N, 2 KB apart along K), two stages, the next chunk's copy issued
@@ -59,6 +63,8 @@ constexpr int KB = 128;          // bytes of K per chunk and row
 constexpr int STAGE = GT * KB;   // bytes of one operand chunk
 constexpr uint32_t LBO = 16 * 128;  // next 16 bytes of K: 16 row groups of 128 B
 constexpr int EG_GROUP_MAX = 32;    // m-tiles per CTA at most (one T tile computed per CTA)
+constexpr int EG_PASS_CHUNKS = 10;  // T chunks resident per K pass when the whole K does not fit
+constexpr int EG_PASS_GROUP = 4;    // m-tiles per CTA with K passes: 4 accumulators of 128 columns
 
 enum { EG_BF16 = 0, EG_TF32 = 1 };
 
@@ -93,6 +99,7 @@ struct GemmArgs {
   const int *pair_ab;      // [nsym]: a | b << 16, a <= b, row by row
   int dim, p, nq, nsym, nen, Kp, n_tiles, m_tiles, general;
   int split;  // 1: T = T_hi + T_lo, both in the operand type (two MMAs per chunk on the same Qv)
+  int npass;  // K passes (1: the T tile of the whole K is resident)
   int *err;
   uint64_t limit_ns;  // bound of each pipeline wait (the drain after a stop keeps MBAR_LIMIT_NS)
   int stall;          // failure-detection test: wait once on a barrier phase that nothing completes
@@ -122,10 +129,11 @@ __global__ void __launch_bounds__(256) k_elem_gemm(GemmArgs g) {
   constexpr int KC = KB / ES;                // K values per chunk
   constexpr int PER = 16 / ES;               // values per 16 bytes
   const int nchunks = g.Kp / KC;
+  const int npass = g.npass, pcs = (nchunks + npass - 1) / npass;  // K passes, chunks per pass
   extern __shared__ __align__(128) uint8_t sm[];
-  uint8_t *Ts = sm;                                    // [nchunks][STAGE]  T rounded
-  uint8_t *Tl = sm + (size_t)nchunks * STAGE;          // [nchunks][STAGE]  remainder (split)
-  uint8_t *As = sm + (size_t)nchunks * (1 + g.split) * STAGE;  // [2][STAGE]
+  uint8_t *Ts = sm;                                    // [pcs][STAGE]  T rounded (this pass's chunks)
+  uint8_t *Tl = sm + (size_t)pcs * STAGE;              // [pcs][STAGE]  remainder (split, one pass only)
+  uint8_t *As = sm + (size_t)pcs * (1 + g.split) * STAGE;  // [2][STAGE]
   float *tab = reinterpret_cast<float *>(As + 2 * STAGE);  // [3][q][p+1][2]
   int *smu = reinterpret_cast<int *>(tab + 3 * 5 * 5 * 2), *snu = smu + 16;
   int *spair = smu + 32;  // [GT][3]: this pair tile's (a | b << 16, offset of a, offset of b)
@@ -139,8 +147,10 @@ __global__ void __launch_bounds__(256) k_elem_gemm(GemmArgs g) {
   const int q = g.p + 1, n1 = g.p + 1;
   const int tsz = q * n1 * 2;
 
+  // tensor memory: one 128-column accumulator, or one per m-tile of the group with K passes
+  const uint32_t tcols = npass > 1 ? (uint32_t)(EG_PASS_GROUP * GT) : (uint32_t)GT;
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)), "r"(GT) : "memory");
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)), "r"(tcols) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
@@ -172,11 +182,17 @@ __global__ void __launch_bounds__(256) k_elem_gemm(GemmArgs g) {
   const int nslot = smu[15];
   const int KV = nslot * g.nq;
 
-  // ---- T tile of this pair range for the whole K: copied from the per-mesh cache, or
-  // built here (once per group) from the type's 1D tables ----
+  // ---- T tile of this pair range for chunks [c_lo, c_hi) of K (all of K in one pass):
+  // copied from the per-mesh cache, or built here (once per group and pass) from the
+  // type's 1D tables ----
   const int64_t tile_off = ((int64_t)g.group[grp * 6 + 5] * g.n_tiles + n_tile) * g.tile_bytes;
+  auto load_T = [&](int c_lo, int c_hi) {
   if (g.Tc) {
-    for (int64_t x = (int64_t)tid * 16; x < g.tile_bytes; x += 16 * (int64_t)blockDim.x) cp16(su32(Ts) + (uint32_t)x, g.Tc + tile_off + x, true);
+    // one pass: the whole cached tile (with the remainder part when split); passes: this
+    // pass's chunks of the rounded part
+    const int64_t x0 = (int64_t)c_lo * STAGE, x1 = npass > 1 ? (int64_t)c_hi * STAGE : g.tile_bytes;
+    for (int64_t x = x0 + (int64_t)tid * 16; x < x1; x += 16 * (int64_t)blockDim.x)
+      cp16(su32(Ts) + (uint32_t)(x - x0), g.Tc + tile_off + x, true);
     cp_commit();
     cp_wait<0>();
   } else {
@@ -195,8 +211,8 @@ __global__ void __launch_bounds__(256) k_elem_gemm(GemmArgs g) {
     }
 #define TB(ax, gq, aa, s) tab[(((ax) * q + (gq)) * n1 + (aa)) * 2 + (s)]
     const uint32_t rowoff = (uint32_t)((r128 >> 3) * 128 + (r128 & 7) * 16);
-    for (int c = 0; c < nchunks; c++) {
-      const uint32_t bdst = su32(Ts + (size_t)c * STAGE) + rowoff, ldst = su32(Tl + (size_t)c * STAGE) + rowoff;
+    for (int c = c_lo; c < c_hi; c++) {
+      const uint32_t bdst = su32(Ts + (size_t)(c - c_lo) * STAGE) + rowoff, ldst = su32(Tl + (size_t)(c - c_lo) * STAGE) + rowoff;
       for (int kc = half * 4; kc < half * 4 + 4; kc++) {
         int k = c * KC + kc * PER, sl = k / g.nq, qp = k - sl * g.nq;  // K index, its slot and Gauss point
         uint32_t w[4] = {0u, 0u, 0u, 0u}, wl[4] = {0u, 0u, 0u, 0u};
@@ -245,10 +261,13 @@ __global__ void __launch_bounds__(256) k_elem_gemm(GemmArgs g) {
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
-  if (g.Tout) {  // build mode: the tile goes to the per-mesh cache
-    for (int64_t x = (int64_t)tid * 16; x < g.tile_bytes; x += 16 * (int64_t)blockDim.x)
-      *reinterpret_cast<uint4 *>(g.Tout + tile_off + x) = *reinterpret_cast<const uint4 *>(Ts + x);
+  if (g.Tout) {  // build mode: the tile (this pass's part of it) goes to the per-mesh cache
+    const int64_t x0 = (int64_t)c_lo * STAGE, x1 = npass > 1 ? (int64_t)c_hi * STAGE : g.tile_bytes;
+    for (int64_t x = x0 + (int64_t)tid * 16; x < x1; x += 16 * (int64_t)blockDim.x)
+      *reinterpret_cast<uint4 *>(g.Tout + tile_off + x) = *reinterpret_cast<const uint4 *>(Ts + (x - x0));
+    __syncthreads();  // the next pass rebuilds Ts
   }
+  };
 
   const uint32_t idesc = (1u << 4) | ((OP == EG_BF16 ? 1u : 2u) << 7) | ((OP == EG_BF16 ? 1u : 2u) << 10) |
                          ((uint32_t)(GT >> 3) << 17) | ((uint32_t)(GT >> 4) << 24);
@@ -271,64 +290,11 @@ __global__ void __launch_bounds__(256) k_elem_gemm(GemmArgs g) {
     if (tid == 0 && !mbar_wait(su32(done + 1), 0, abort_s, 0, g.limit_ns)) *abort_s = 1;
     __syncthreads();
   }
-  // two stages in flight: the copy of the next chunk (the next m-tile's first chunk after a
-  // tile's last) is issued before the wait for the current one, and runs during the MMAs and
-  // the epilogue
-  if (m_count > 0 && !*abort_s) issue(m_first, 0, 0);
-  for (int mi = 0; mi < m_count && !*abort_s; mi++) {
-    const int mt = m_first + mi;
-    for (int c = 0; c < nchunks; c++, it++) {
-      const int st = it & 1;
-      if ((c + 1 < nchunks) || (mi + 1 < m_count)) {
-        // the other stage is free once the MMAs of chunk it - 1, which read it, are complete
-        if (it >= 1) {
-          if (tid == 0 && !mbar_wait(su32(done + (st ^ 1)), ((it - 1) >> 1) & 1, abort_s, 0, g.limit_ns)) *abort_s = 1;
-          __syncthreads();
-          if (*abort_s) break;
-        }
-        if (c + 1 < nchunks) issue(mt, c + 1, st ^ 1);
-        else issue(mt + 1, 0, st ^ 1);
-        cp_wait<1>();  // this chunk's copies have landed; the next chunk's may be in flight
-      } else {
-        cp_wait<0>();
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid == 0) {
-        tc_fence_after();
-        const uint64_t ad = sdesc(su32(As + st * STAGE), LBO, 128);
-        for (int part = 0; part <= g.split; part++) {
-          const uint64_t bd = sdesc(su32((part ? Tl : Ts) + (size_t)c * STAGE), LBO, 128);
-#pragma unroll
-          for (int kk = 0; kk < 4; kk++) {
-            const uint32_t acc = (c > 0 || kk > 0 || part > 0) ? 1u : 0u;
-            const uint64_t a_k = ad + (uint64_t)((kk * 2 * LBO) >> 4), b_k = bd + (uint64_t)((kk * 2 * LBO) >> 4);
-            if constexpr (OP == EG_BF16)
-              asm volatile(
-                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                  "l"(a_k), "l"(b_k), "r"(idesc), "r"(acc)
-                  : "memory");
-            else
-              asm volatile(
-                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                  "l"(a_k), "l"(b_k), "r"(idesc), "r"(acc)
-                  : "memory");
-          }
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(done + st))
-                     : "memory");
-        last = it;
-      }
-    }
-    if (*abort_s) break;
-    // this m-tile's accumulator is complete once its last commit has arrived
-    if (tid == 0 && !mbar_wait(su32(done + ((it - 1) & 1)), ((it - 1) >> 1) & 1, abort_s, 0, g.limit_ns)) *abort_s = 1;
-    __syncthreads();
-    if (*abort_s) break;
+  // E_ab (a <= b) goes to slab pk(a, b) at column A(e, a): for consecutive elements
+  // along x the lanes write consecutive floats; warp w reads tensor-memory lanes
+  // 32 (w % 4) .. + 31, columns 64 (w / 4) .. + 63 of the m-tile's accumulator
+  auto epilogue = [&](int mt, uint32_t acc_tm) {
     tc_fence_after();
-    // E_ab (a <= b) goes to slab pk(a, b) at column A(e, a): for consecutive elements
-    // along x the lanes write consecutive floats
-    // warp w reads tensor-memory lanes 32 (w % 4) .. + 31, columns 64 (w / 4) .. + 63
     const int quarter = warp & 3, ch = warp >> 2;
     const int row = quarter * 32 + lane;
     const int e = g.elem_of_slot[(size_t)mt * GT + row];
@@ -339,7 +305,7 @@ __global__ void __launch_bounds__(256) k_elem_gemm(GemmArgs g) {
     }
     for (int c0 = ch * (GT / 2); c0 < (ch + 1) * (GT / 2); c0 += 16) {
       float v[16];
-      tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
+      tmem_ld16(acc_tm + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
       if (e < 0) continue;
 #pragma unroll
       for (int u = 0; u < 16; u++) {
@@ -348,7 +314,82 @@ __global__ void __launch_bounds__(256) k_elem_gemm(GemmArgs g) {
       }
     }
     tc_fence_before();
-    __syncthreads();  // the accumulator is read before the next m-tile's MMAs overwrite it
+    __syncthreads();  // the accumulator is read before later MMAs overwrite it
+  };
+  // K in npass passes; within a pass two stages in flight: the copy of the next chunk (the
+  // next m-tile's first chunk of the pass after a tile's last) is issued before the wait for
+  // the current one, and runs during the MMAs and the epilogue
+  for (int h = 0; h < npass && !*abort_s; h++) {
+    const int c_lo = h * pcs, c_hi = min(nchunks, c_lo + pcs);
+    if (h > 0) {
+      // the previous pass's MMAs read Ts: its last commit precedes the rebuild
+      if (tid == 0 && last >= 0 && !mbar_wait(su32(done + (last & 1)), (last >> 1) & 1, abort_s, 0, g.limit_ns)) *abort_s = 1;
+      __syncthreads();
+      if (*abort_s) break;
+    }
+    load_T(c_lo, c_hi);
+    if (m_count > 0 && !*abort_s) issue(m_first, c_lo, it & 1);
+    for (int mi = 0; mi < m_count && !*abort_s; mi++) {
+      const int mt = m_first + mi;
+      const uint32_t acc_tm = tmem + (npass > 1 ? (uint32_t)(mi * GT) : 0u);
+      for (int c = c_lo; c < c_hi; c++, it++) {
+        const int st = it & 1;
+        if ((c + 1 < c_hi) || (mi + 1 < m_count)) {
+          // the other stage is free once the MMAs of chunk it - 1, which read it, are complete
+          if (it >= 1) {
+            if (tid == 0 && !mbar_wait(su32(done + (st ^ 1)), ((it - 1) >> 1) & 1, abort_s, 0, g.limit_ns)) *abort_s = 1;
+            __syncthreads();
+            if (*abort_s) break;
+          }
+          if (c + 1 < c_hi) issue(mt, c + 1, st ^ 1);
+          else issue(mt + 1, c_lo, st ^ 1);
+          cp_wait<1>();  // this chunk's copies have landed; the next chunk's may be in flight
+        } else {
+          cp_wait<0>();
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+          tc_fence_after();
+          const uint64_t ad = sdesc(su32(As + st * STAGE), LBO, 128);
+          for (int part = 0; part <= g.split; part++) {
+            const uint64_t bd = sdesc(su32((part ? Tl : Ts) + (size_t)(c - c_lo) * STAGE), LBO, 128);
+#pragma unroll
+            for (int kk = 0; kk < 4; kk++) {
+              const uint32_t acc = (c > 0 || kk > 0 || part > 0) ? 1u : 0u;
+              const uint64_t a_k = ad + (uint64_t)((kk * 2 * LBO) >> 4), b_k = bd + (uint64_t)((kk * 2 * LBO) >> 4);
+              if constexpr (OP == EG_BF16)
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_tm),
+                    "l"(a_k), "l"(b_k), "r"(idesc), "r"(acc)
+                    : "memory");
+              else
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_tm),
+                    "l"(a_k), "l"(b_k), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(done + st))
+                       : "memory");
+          last = it;
+        }
+      }
+      if (*abort_s) break;
+      if (npass == 1) {
+        // this m-tile's accumulator is complete once its last commit has arrived
+        if (tid == 0 && !mbar_wait(su32(done + ((it - 1) & 1)), ((it - 1) >> 1) & 1, abort_s, 0, g.limit_ns)) *abort_s = 1;
+        __syncthreads();
+        if (*abort_s) break;
+        epilogue(mt, acc_tm);
+      }
+    }
+  }
+  if (npass > 1 && m_count > 0 && !*abort_s) {
+    // every accumulator of the group is complete once the last pass's last commit has arrived
+    if (tid == 0 && !mbar_wait(su32(done + ((it - 1) & 1)), ((it - 1) >> 1) & 1, abort_s, 0, g.limit_ns)) *abort_s = 1;
+    __syncthreads();
+    for (int mi = 0; mi < m_count && !*abort_s; mi++) epilogue(m_first + mi, tmem + (uint32_t)(mi * GT));
   }
   cp_wait<0>();  // after a stop a prefetched chunk may still be in flight
   // after a stop, wait (bounded) for the last committed MMAs before freeing the tensor memory
@@ -358,7 +399,7 @@ __global__ void __launch_bounds__(256) k_elem_gemm(GemmArgs g) {
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GT) : "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
 }
 
 // Qv[slot(e)][(s, q)] = Q_{mu nu}(e, q) in the operand type from the FP32 geometry
@@ -576,6 +617,8 @@ struct ElemGemmPlan {
   bool tc_tried[2] = {false, false};
   int *slot_of_elem = nullptr, *elem_of_slot = nullptr, *group = nullptr, *pair_ab = nullptr, *pair_off = nullptr,
       *err = nullptr;
+  int *group4 = nullptr;                 // [ngroups4][6]: groups of at most EG_PASS_GROUP m-tiles (K passes)
+  int ngroups4 = 0;
   int2 *gtab = nullptr;  // [nen][nen]: packed slab of (min, max), and the column shift off(b) - off(a) when b < a
   void *Qv[2] = {nullptr, nullptr};  // BF16, TF32 operand buffers
   float *E = nullptr;
@@ -603,7 +646,7 @@ static std::vector<int> dir_types(const Dir &D, std::vector<int> &rep) {
 
 static void plan_free(ElemGemmPlan *P) {
   void *ps[] = {P->slot_of_elem, P->elem_of_slot, P->group, P->pair_ab, P->pair_off, P->err, P->Qv[0], P->Qv[1], P->E, P->gtab,
-                P->tgroup, P->Tc[0], P->Tc[1]};
+                P->tgroup, P->Tc[0], P->Tc[1], P->group4};
   for (void *p : ps)
     if (p) cudaFree(p);
 }
@@ -651,7 +694,7 @@ static cudaError_t elem_gemm_prepare(iga_s *h) {
   // tiles beyond four times the elements (knot vectors with few repeated spans): not worth it
   if (m_tiles * GT > 4 * h->nelem + 64 * GT) return cudaErrorNotSupported;
   P->m_tiles = (int)m_tiles;
-  std::vector<int> slot(h->nelem), groups, tgroups;
+  std::vector<int> slot(h->nelem), groups, groups4, tgroups;
   std::vector<int64_t> next = first_slot;
   for (int64_t e = 0; e < h->nelem; e++) {
     const int64_t t = type_of(e);
@@ -673,6 +716,14 @@ static cudaError_t elem_gemm_prepare(iga_s *h) {
       groups.push_back(rep[2][t2]);
       groups.push_back((int)t);
     }
+    for (int64_t m = m0; m < m1; m += EG_PASS_GROUP) {
+      groups4.push_back((int)m);
+      groups4.push_back((int)std::min<int64_t>(EG_PASS_GROUP, m1 - m));
+      groups4.push_back(rep[0][t0]);
+      groups4.push_back(rep[1][t1]);
+      groups4.push_back(rep[2][t2]);
+      groups4.push_back((int)t);
+    }
     tgroups.push_back(0);  // one group per type without element tiles: builds the type's T tiles
     tgroups.push_back(0);
     tgroups.push_back(rep[0][t0]);
@@ -681,6 +732,7 @@ static cudaError_t elem_gemm_prepare(iga_s *h) {
     tgroups.push_back((int)t);
   }
   P->ngroups = (int)(groups.size() / 6);
+  P->ngroups4 = (int)(groups4.size() / 6);
   P->ntypes = (int)ntypes;
   std::vector<int> pairs, poff;
   const int64_t n0f = h->dir[0].n, n1f = h->dir[1].n;
@@ -708,6 +760,8 @@ static cudaError_t elem_gemm_prepare(iga_s *h) {
   if ((ce = cudaMemcpy(P->slot_of_elem, slot.data(), slot.size() * sizeof(int), cudaMemcpyHostToDevice))) return ce;
   if ((ce = cudaMalloc((void **)&P->group, groups.size() * sizeof(int)))) return ce;
   if ((ce = cudaMemcpy(P->group, groups.data(), groups.size() * sizeof(int), cudaMemcpyHostToDevice))) return ce;
+  if ((ce = cudaMalloc((void **)&P->group4, groups4.size() * sizeof(int)))) return ce;
+  if ((ce = cudaMemcpy(P->group4, groups4.data(), groups4.size() * sizeof(int), cudaMemcpyHostToDevice))) return ce;
   if ((ce = cudaMalloc((void **)&P->tgroup, tgroups.size() * sizeof(int)))) return ce;
   if ((ce = cudaMemcpy(P->tgroup, tgroups.data(), tgroups.size() * sizeof(int), cudaMemcpyHostToDevice))) return ce;
   if ((ce = cudaMalloc((void **)&P->pair_ab, pairs.size() * sizeof(int)))) return ce;
@@ -759,11 +813,21 @@ static cudaError_t qv_buffer(iga_s *h, int op, void **out) {
     }                                                       \
   } while (0)
 
-// The plan exists and the T tile of the whole K fits in shared memory for the operand type.
+// K passes of the element GEMM for an operand type: one when the T tile of the whole K
+// fits in shared memory, else as few as keep EG_PASS_CHUNKS chunks resident.
+static int eg_passes(int nch) {
+  if (eg_smem(nch, 0) <= 200 * 1024) return 1;
+  return (nch + EG_PASS_CHUNKS - 1) / EG_PASS_CHUNKS;
+}
+
+// The element-type plan exists (knot vectors whose spans repeat enough) and either the T
+// tile of the whole K fits in shared memory for the operand type, or it does not and the
+// per-element contraction (iga_mixed.cu: 2D p <= 4, 3D p <= 3) cannot take the case: then
+// K runs in passes (3D p = 4 in TF32, and with a general map in BF16 too).
 bool elem_gemm_supported(iga_s *h, int prec) {
   if (elem_gemm_prepare(h) != cudaSuccess) return false;
   const int es = prec == IGA_JAC_BF16 ? 2 : 4;
-  return eg_smem(h->egemm->Kp * es / KB, 0) <= 200 * 1024;
+  return eg_passes(h->egemm->Kp * es / KB) == 1 || !mixed_supported(h->dim, h->p);
 }
 
 // vals (FP32, CSR) = the Jacobian with BF16 (prec IGA_JAC_BF16) or TF32 element
@@ -824,8 +888,10 @@ cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, in
   g.limit_ns = h->wait_limit_ns;
   g.stall = 0;
   const int nch = P->Kp * (op == EG_BF16 ? 2 : 4) / KB;
-  g.split = eg_smem(nch, 1) <= 200 * 1024 ? 1 : 0;
-  const size_t smem = eg_smem(nch, g.split);
+  g.npass = eg_passes(nch);
+  const int pcs = (nch + g.npass - 1) / g.npass;
+  g.split = (g.npass == 1 && eg_smem(nch, 1) <= 200 * 1024) ? 1 : 0;
+  const size_t smem = eg_smem(pcs, g.split);
   g.tile_bytes = (int64_t)nch * (1 + g.split) * STAGE;
   g.Tc = nullptr;
   g.Tout = nullptr;
@@ -851,7 +917,9 @@ cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, in
   g.Tc = P->Tc[op];
   g.stall = h->stall_next ? 1 : 0;
   h->stall_next = false;
-  const unsigned grid = (unsigned)((int64_t)P->ngroups * P->n_tiles);
+  // with K passes a CTA keeps one accumulator per m-tile: groups of at most EG_PASS_GROUP
+  if (g.npass > 1) g.group = P->group4;
+  const unsigned grid = (unsigned)((int64_t)(g.npass > 1 ? P->ngroups4 : P->ngroups) * P->n_tiles);
   if (op == EG_BF16) {
     IGA_LAUNCH(h, KC_ELEM_TC, (k_elem_gemm<EG_BF16><<<grid, 256, smem, h->stream>>>(g)));
   } else {
