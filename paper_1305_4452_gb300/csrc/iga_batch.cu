@@ -95,7 +95,7 @@ __device__ __forceinline__ uint64_t gtimer() {
 
 struct Cta {
   int tid, nt, lane, warp, nw;
-  double *red;  // shared, >= 36 doubles
+  double *red;  // shared, >= 38 doubles (cta_sum: 0..33; scalars shared by thread 0: 35..37)
   float *zs;    // shared FP32 operand vector of the operator products (N floats), or null
   float *tile;  // the same dynamic shared memory (tile_cap floats), for the Jacobian's line tiles
   int tile_cap;
@@ -473,10 +473,17 @@ __device__ int b_gmres(const BInst &I, const double *__restrict__ b, double *__r
     first_cycle = false;
     double ss = 0.0;
     for (int r = c.tid; r < N; r += c.nt) ss = fma(V0[r], V0[r], ss);
-    const double beta = sqrt(cta_sum(c, ss));
+    ss = cta_sum(c, ss);
+    if (c.tid == 0) {
+      const double bt = sqrt(ss);
+      c.red[35] = bt;
+      c.red[36] = 1.0 / bt;
+    }
+    __syncthreads();
+    const double beta = c.red[35], binv = c.red[36];
     if (!isfinite(beta)) { rc = 2; break; }
     if (beta <= tol) { rc = 0; break; }
-    for (int r = c.tid; r < N; r += c.nt) V0[r] /= beta;
+    for (int r = c.tid; r < N; r += c.nt) V0[r] *= binv;
     if (c.tid == 0) {
       s.g[0] = beta;
       for (int i = 1; i <= m; i++) s.g[i] = 0.0;
@@ -492,8 +499,12 @@ __device__ int b_gmres(const BInst &I, const double *__restrict__ b, double *__r
       b_cgs_pass(I, w, j + 1, s, j, false, c);
       double ww = 0.0;
       for (int r = c.tid; r < N; r += c.nt) ww = fma(w[r], w[r], ww);
-      const double hn = sqrt(cta_sum(c, ww));
+      ww = cta_sum(c, ww);
       if (c.tid == 0) {
+        // ||w||, its reciprocal and the Givens step by thread 0, shared after the barrier
+        const double hn = sqrt(ww);
+        s.scal[1] = hn;
+        s.scal[2] = 1.0 / hn;
         s.H[j + 1][j] = hn;
         for (int i = 0; i < j; i++) {
           double a = s.H[i][j], bb = s.H[i + 1][j];
@@ -514,11 +525,12 @@ __device__ int b_gmres(const BInst &I, const double *__restrict__ b, double *__r
       }
       __syncthreads();
       res = s.scal[0];
+      const double hn = s.scal[1];
       k = j + 1;
       if (!(hn > 1e-300) || !isfinite(res)) { brk = true; break; }
       if (res <= tol) break;
       double *vn = I.V + (size_t)(j + 1) * N;
-      const double inv = 1.0 / hn;
+      const double inv = s.scal[2];
       for (int r = c.tid; r < N; r += c.nt) vn[r] = w[r] * inv;
       __syncthreads();
     }
@@ -578,7 +590,11 @@ __device__ int b_cg(const BInst &I, const double *__restrict__ b, double *__rest
     for (int i = c.tid; i < N; i += c.nt) pq = fma(p[i], q[i], pq);
     pq = cta_sum(c, pq);
     if (!(pq > 0.0) || !isfinite(pq)) { rc = 2; break; }
-    const double alpha = rz / pq;
+    // the iteration's scalars by thread 0, shared: a FP64 division or square root in every
+    // thread would cost the SM's narrow FP64 pipe as much as a pass over a vector
+    if (c.tid == 0) c.red[35] = rz / pq;
+    __syncthreads();
+    const double alpha = c.red[35];
     double rr2 = 0.0, rz2 = 0.0;
     for (int i = c.tid; i < N; i += c.nt) {
       x[i] = fma(alpha, p[i], x[i]);
@@ -590,8 +606,13 @@ __device__ int b_cg(const BInst &I, const double *__restrict__ b, double *__rest
     cta_sum2(c, rr2, rz2);
     it++;
     if (!isfinite(rr2)) { rc = 2; break; }
-    if (sqrt(rr2) <= tol) { rc = 0; break; }
-    const double beta = rz2 / rz;
+    if (c.tid == 0) {
+      c.red[36] = sqrt(rr2) <= tol ? 1.0 : 0.0;
+      c.red[37] = rz2 / rz;
+    }
+    __syncthreads();
+    if (c.red[36] != 0.0) { rc = 0; break; }
+    const double beta = c.red[37];
     rz = rz2;
     for (int i = c.tid; i < N; i += c.nt) p[i] = fma(beta, p[i], I.dinv[i] * r[i]);
     __syncthreads();

@@ -446,8 +446,10 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_pass(const double *__restrict
 __global__ void k_normalize(const double *w, const double *__restrict__ hn, double *vnext,
                             const double *__restrict__ dinv, double *__restrict__ z, int64_t N, const double *__restrict__ done) {
   if (done[0] != 0.0) return;
-  double s = hn[0];
-  double inv = (s > 0.0) ? 1.0 / s : 0.0;
+  __shared__ double inv_s;  // 1 / ||w|| once per block, not per thread
+  if (threadIdx.x == 0) inv_s = (hn[0] > 0.0) ? 1.0 / hn[0] : 0.0;
+  __syncthreads();
+  const double inv = inv_s;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x) {
     double v = w[r] * inv;
     vnext[r] = v;
@@ -467,13 +469,17 @@ __device__ void givens_step_sm(double *Hs, const double *cs_s, const double *sn_
   double *Hj = gm + L.H + (size_t)j * (m + 1);
   const double hn = sqrt(Hs[j + 1]);
   Hs[j + 1] = hn;
+  // the previous rotations, the running component t carried in a register: one dependent
+  // FMA per rotation (single-thread FP64 latency on GB300's narrow pipe is the cost here)
+  double t = Hs[0];
   for (int i = 0; i < j; i++) {
-    const double c = cs_s[i], s = sn_s[i];
-    const double a = Hs[i], b = Hs[i + 1];
-    Hs[i] = c * a + s * b;
-    Hs[i + 1] = -s * a + c * b;
+    const double c = cs_s[i], s = sn_s[i], b = Hs[i + 1];
+    const double cb = c * b, sb = s * b;
+    Hs[i] = fma(c, t, sb);
+    t = fma(-s, t, cb);
   }
-  const double a = Hs[j], b = Hs[j + 1];
+  Hs[j] = t;
+  const double a = t, b = Hs[j + 1];
   const double r = hypot(a, b);
   const double c = (r > 0.0) ? a / r : 1.0, s = (r > 0.0) ? b / r : 0.0;
   gm[L.cs + j] = c;
@@ -637,6 +643,7 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_fused(const double *__restric
   double *sn_s = cs_s + m;             // [m]
   double *Hs = sn_s + m;               // [m + 2]
   __shared__ double sh[32];
+  __shared__ double sc[4];
   GmLayout L = gm_layout(m);
   double *fl = gm + L.flags;
   if (fl[0] != 0.0) return;
@@ -661,11 +668,26 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_fused(const double *__restric
   // phase 3
   block_sum_cols(P2, gridDim.x, jp1 + 1, h2);
   {
-    double s2 = h2[jp1];
-    for (int i = 0; i < jp1; i++) s2 = fma(-h2[i], h2[i], s2);
-    const bool direct = !(s2 > 0.5 * h2[jp1]);
+    // the block's scalars once, by warp 0 (fixed order), not by every thread: on GB300 a
+    // FP64 instruction costs the narrow pipe the same for one active lane as for 32
+    //   sc[0] = s2 = ||w1||^2 - ||h2||^2, sc[1] = direct, sc[2] = 1 / sqrt(s2)
+    if (threadIdx.x < 32) {
+      double t = 0.0;
+      for (int i = threadIdx.x; i < jp1; i += 32) t = fma(h2[i], h2[i], t);
+      t = warp_sum(t);
+      if (threadIdx.x == 0) {
+        const double s2 = h2[jp1] - t;
+        const bool direct = !(s2 > 0.5 * h2[jp1]);
+        const double hn = sqrt(fmax(s2, 0.0));
+        sc[0] = s2;
+        sc[1] = direct ? 1.0 : 0.0;
+        sc[2] = (hn > 0.0) ? 1.0 / hn : 0.0;
+      }
+    }
+    __syncthreads();
+    double s2 = sc[0];
     double sq = gs_update_rows(Vb, ld, jp1, a, cnt, h2, ws);
-    if (direct) {  // severe cancellation in the second pass: sum ||w||^2 itself
+    if (sc[1] != 0.0) {  // severe cancellation in the second pass: sum ||w||^2 itself
       sq = block_sum(sq, sh);
       if (threadIdx.x == 0) P1[blockIdx.x] = sq;
       if (!gs_grid_sync(bar)) goto timeout;
@@ -673,20 +695,21 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_fused(const double *__restric
         double acc = 0.0;
         for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) acc += P1[b];
         acc = warp_sum(acc);
-        if (threadIdx.x == 0) sh[0] = acc;
+        if (threadIdx.x == 0) {
+          const double hn = sqrt(fmax(acc, 0.0));
+          sc[0] = acc;
+          sc[2] = (hn > 0.0) ? 1.0 / hn : 0.0;
+        }
       }
       __syncthreads();
-      s2 = sh[0];
+      s2 = sc[0];
     }
-    const double hn = sqrt(fmax(s2, 0.0));
-    const double inv = (hn > 0.0) ? 1.0 / hn : 0.0;
+    const double inv = sc[2];
     double *vnext = const_cast<double *>(Vb) + (size_t)jp1 * ld;
-    for (int r = threadIdx.x; r < cnt; r += T) {
-      const double v = ws[r] * inv;
-      vnext[a + r] = v;
-      z[a + r] = dinv[a + r] * v;
-    }
+    int r0 = threadIdx.x, rs = T;
     if (blockIdx.x == 0) {
+      // block 0: the new column of H, and the Givens step by thread 0 while warps 1..
+      // normalise the block's rows
       double *Hj = gm + L.H + (size_t)j * (m + 1);
       for (int i = threadIdx.x; i < jp1; i += T) {
         Hs[i] = hs[i] + h2[i];
@@ -699,7 +722,15 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_fused(const double *__restric
       if (threadIdx.x == 0) Hs[jp1] = fmax(s2, 0.0);
       __syncthreads();
       if (threadIdx.x == 0) givens_step_sm(Hs, cs_s, sn_s, gm, m, j, tol);
+      r0 = threadIdx.x - 32;
+      rs = T - 32;
     }
+    if (r0 >= 0)
+      for (int r = r0; r < cnt; r += rs) {
+        const double v = ws[r] * inv;
+        vnext[a + r] = v;
+        z[a + r] = dinv[a + r] * v;
+      }
   }
   return;
 timeout:
@@ -1172,7 +1203,12 @@ __global__ void __launch_bounds__(RED_THREADS) k_cg_xr(double *__restrict__ x, d
     if (blockIdx.x == 0 && threadIdx.x == 0) { s[CG_DONE] = 1.0; s[CG_BRK] = 1.0; }
     return;
   }
-  const double alpha = s[cg_rz(par)] / pq;  // <r,z> of this iteration
+  // alpha = <r,z> / <p,q> once per block (a FP64 division in every thread would cost the
+  // narrow FP64 pipe as much as a vector pass)
+  __shared__ double alpha_s;
+  if (threadIdx.x == 0) alpha_s = s[cg_rz(par)] / pq;  // <r,z> of this iteration
+  __syncthreads();
+  const double alpha = alpha_s;
   if (blockIdx.x == 0 && threadIdx.x == 0) { s[CG_PQ] = pq; s[CG_ALPHA] = alpha; }
   int64_t per = (N + gridDim.x - 1) / gridDim.x;
   int64_t a = blockIdx.x * per, e = min(N, a + per);
@@ -1199,8 +1235,16 @@ __global__ void __launch_bounds__(RED_THREADS) k_cg_p(double *__restrict__ p, co
   if (s[CG_DONE] != 0.0) return;
   const double rz_new = block_sum_strided(partial, nb, 2, 0, sh);
   const double rr = block_sum_strided(partial, nb, 2, 1, sh);
-  const bool bad = !isfinite(rr), conv = !bad && sqrt(rr) <= tol;
-  const double beta = rz_new / s[cg_rz(par)];
+  // the convergence test and beta once per block (thread 0), shared
+  __shared__ double beta_s;
+  __shared__ int conv_s;
+  if (threadIdx.x == 0) {
+    conv_s = isfinite(rr) && sqrt(rr) <= tol;
+    beta_s = rz_new / s[cg_rz(par)];
+  }
+  __syncthreads();
+  const bool bad = !isfinite(rr), conv = conv_s != 0;
+  const double beta = beta_s;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     s[CG_ITS] += 1.0;
     s[CG_RR] = rr;
