@@ -586,14 +586,14 @@ __device__ bool gs_grid_sync(unsigned *bar) {
   return ok_s != 0;
 }
 
-// ws[r] -= sum_{i < jp1} h[i] V[i][a + r] for the block's rows r < cnt, two rows per
-// thread and step (two independent FMA chains sharing each h[i]); returns the thread's
-// sum of the updated ws[r]^2 (rows in the order visited).
+// ws[r] -= sum_{i < jp1} h[i] V[i][a + r] for the block's rows r < cnt, taken by T threads
+// numbered t0 (the rows t0 + k T), two rows per thread and step (two independent FMA
+// chains sharing each h[i]); returns the thread's sum of the updated ws[r]^2 (rows in the
+// order visited).
 __device__ __forceinline__ double gs_update_rows(const double *__restrict__ Vb, int64_t ld, int jp1, int64_t a, int cnt,
-                                                 const double *h, double *ws) {
-  const int T = blockDim.x;
+                                                 const double *h, double *ws, int t0, int T) {
   double sq = 0.0;
-  for (int r = threadIdx.x; r < cnt; r += 2 * T) {
+  for (int r = t0; r < cnt; r += 2 * T) {
     const int r2 = r + T;
     const bool two = r2 < cnt;
     double v = ws[r], v2 = two ? ws[r2] : 0.0;
@@ -658,7 +658,7 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_fused(const double *__restric
   // phase 2
   block_sum_cols(P1, gridDim.x, jp1, hs);
   {
-    double sq = gs_update_rows(Vb, ld, jp1, a, cnt, hs, ws);
+    double sq = gs_update_rows(Vb, ld, jp1, a, cnt, hs, ws, threadIdx.x, T);
     sq = block_sum(sq, sh);
     if (threadIdx.x == 0) P2[(size_t)jp1 * gridDim.x + blockIdx.x] = sq;
   }
@@ -686,8 +686,36 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_fused(const double *__restric
     }
     __syncthreads();
     double s2 = sc[0];
-    double sq = gs_update_rows(Vb, ld, jp1, a, cnt, h2, ws);
-    if (sc[1] != 0.0) {  // severe cancellation in the second pass: sum ||w||^2 itself
+    const bool direct = sc[1] != 0.0;
+    double *vnext = const_cast<double *>(Vb) + (size_t)jp1 * ld;
+    // rows of this block's update and normalisation: every thread, except in block 0, whose
+    // warp 0 assembles the new column of H and runs the Givens step (thread 0, a serial
+    // chain of dependent FP64 operations) while warps 1.. update and normalise the rows
+    int r0 = threadIdx.x, rs = T;
+    auto givens_block0 = [&]() {
+      double *Hj = gm + L.H + (size_t)j * (m + 1);
+      for (int i = threadIdx.x; i < jp1; i += 32) {
+        Hs[i] = hs[i] + h2[i];
+        Hj[i] = Hs[i];
+      }
+      for (int i = threadIdx.x; i < j; i += 32) {
+        cs_s[i] = gm[L.cs + i];
+        sn_s[i] = gm[L.sn + i];
+      }
+      __syncwarp();
+      if (threadIdx.x == 0) {
+        Hs[jp1] = fmax(s2, 0.0);
+        givens_step_sm(Hs, cs_s, sn_s, gm, m, j, tol);
+      }
+    };
+    if (blockIdx.x == 0 && !direct) {
+      if (threadIdx.x < 32) givens_block0();
+      r0 = threadIdx.x - 32;
+      rs = T - 32;
+    }
+    double sq = 0.0;
+    if (r0 >= 0) sq = gs_update_rows(Vb, ld, jp1, a, cnt, h2, ws, r0, rs);
+    if (direct) {  // severe cancellation in the second pass: sum ||w||^2 itself (all threads updated)
       sq = block_sum(sq, sh);
       if (threadIdx.x == 0) P1[blockIdx.x] = sq;
       if (!gs_grid_sync(bar)) goto timeout;
@@ -703,28 +731,14 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_fused(const double *__restric
       }
       __syncthreads();
       s2 = sc[0];
+      if (blockIdx.x == 0) {
+        if (threadIdx.x < 32) givens_block0();
+        r0 = threadIdx.x - 32;
+        rs = T - 32;
+      }
     }
     const double inv = sc[2];
-    double *vnext = const_cast<double *>(Vb) + (size_t)jp1 * ld;
-    int r0 = threadIdx.x, rs = T;
-    if (blockIdx.x == 0) {
-      // block 0: the new column of H, and the Givens step by thread 0 while warps 1..
-      // normalise the block's rows
-      double *Hj = gm + L.H + (size_t)j * (m + 1);
-      for (int i = threadIdx.x; i < jp1; i += T) {
-        Hs[i] = hs[i] + h2[i];
-        Hj[i] = Hs[i];
-      }
-      for (int i = threadIdx.x; i < j; i += T) {
-        cs_s[i] = gm[L.cs + i];
-        sn_s[i] = gm[L.sn + i];
-      }
-      if (threadIdx.x == 0) Hs[jp1] = fmax(s2, 0.0);
-      __syncthreads();
-      if (threadIdx.x == 0) givens_step_sm(Hs, cs_s, sn_s, gm, m, j, tol);
-      r0 = threadIdx.x - 32;
-      rs = T - 32;
-    }
+    // a thread normalises the rows it updated (the same r0, rs), so no barrier between
     if (r0 >= 0)
       for (int r = r0; r < cnt; r += rs) {
         const double v = ws[r] * inv;
