@@ -461,7 +461,7 @@ def _best_ms(torch, fn, reps):
 # DRAM bytes (read + write) of one Krylov operator product (k_spmv_fixed, FP64 values) on
 # the 64^3 annulus, from one ncu capture of this benchmark's command (named in the JSON
 # line); valid for that workload while the kernel is unchanged (None: not captured).
-SPMV_DRAM_BYTES_ANNULUS64 = None
+SPMV_DRAM_BYTES_ANNULUS64 = 751.95e6 + 2.02e6
 SPMV_TRAFFIC_CAPTURE = ("profiles/k_spmv_fixed_annulus64_fp64_traffic.md: ncu --metrics "
                         "dram__bytes_read.sum,dram__bytes_write.sum --clock-control none -k regex:k_spmv_fixed")
 

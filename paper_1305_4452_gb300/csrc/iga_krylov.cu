@@ -325,19 +325,32 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_rows(const double *__res
 // block-local sums of the partials make the separate reduction launches
 // unnecessary.  Every sum has a fixed shape and order.
 
-// out_sh[i] = sum_{b < nb} partial[i * nb + b], i < n: eight lanes per i, lane t
-// summing b = t, t+8, ... in order, then a fixed 3-level shuffle tree (the same
-// result in every block); all loads of a thread are independent
+// out_sh[i] = sum_{b < nb} partial[i * nb + b], i < n: eight lanes per i, lane t summing
+// b = t + 8 (4 q + k) into four accumulators k (short chains of dependent FP64 adds: their
+// latency, not their count, bounds this step), added as (a0 + a1) + (a2 + a3), then a fixed
+// 3-level shuffle tree (the same result in every block); warps whose four columns are all
+// past n skip the step, since an idle lane's FP64 add costs the narrow pipe as much as a
+// busy one's
 __device__ void block_sum_cols(const double *__restrict__ partial, int nb, int n, double *out_sh) {
   const int g = threadIdx.x >> 3, t = threadIdx.x & 7, ng = blockDim.x >> 3;
   for (int i0 = 0; i0 < n; i0 += ng) {
     const int i = i0 + g;
-    double acc = 0.0;
+    if (i0 + ((threadIdx.x >> 5) << 2) >= n) continue;  // the whole warp's columns are past n
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     if (i < n) {
       const double *pi = partial + (size_t)i * nb;
-#pragma unroll 4
-      for (int b = t; b < nb; b += 8) acc += pi[b];
+      int b = t;
+      for (; b + 24 < nb; b += 32) {
+        a0 += pi[b];
+        a1 += pi[b + 8];
+        a2 += pi[b + 16];
+        a3 += pi[b + 24];
+      }
+      if (b < nb) a0 += pi[b];
+      if (b + 8 < nb) a1 += pi[b + 8];
+      if (b + 16 < nb) a2 += pi[b + 16];
     }
+    double acc = (a0 + a1) + (a2 + a3);
     acc += __shfl_down_sync(0xffffffffu, acc, 4, 8);
     acc += __shfl_down_sync(0xffffffffu, acc, 2, 8);
     acc += __shfl_down_sync(0xffffffffu, acc, 1, 8);
