@@ -223,22 +223,33 @@ __host__ __device__ __forceinline__ int64_t sl_index(int A, int s, int nslot) {
   return (int64_t)(A >> 5) * 32 * nslot + 32 * s + (A & 31);
 }
 
-template <int DIM>
-__global__ void k_csr_to_sliced(StencilRows S, const int64_t *__restrict__ rowptr, const float *__restrict__ csr,
-                                float *__restrict__ sl, int N, int wf) {
-  const int nslot = DIM == 3 ? wf * wf * wf : wf * wf;
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t total = (int64_t)((N + 31) / 32) * 32 * nslot;
-  if (t >= total) return;
-  const int slice = (int)(t / (32 * nslot)), rem = (int)(t % (32 * nslot));
-  const int s = rem / 32, A = slice * 32 + (rem & 31);
-  float v = 0.f;
-  if (A < N) {
-    const RowShape R = row_shape<DIM>(S, A);
-    const int a = s % wf, b = (s / wf) % wf, c = s / (wf * wf);
-    if (a < R.w0 && b < R.w1 && c < R.w2) v = csr[rowptr[A] + a + R.w0 * (b + R.w1 * c)];
+template <int DIM, int P>
+__global__ void __launch_bounds__(256) k_csr_to_sliced(StencilRows S, const int64_t *__restrict__ rowptr,
+                                                       const float *__restrict__ csr, float *__restrict__ sl, int N) {
+  // one thread per row: it reads its own CSR row front to back (each 32-byte sector serves
+  // eight consecutive values through L1) and writes its slot values, which the warp's 32
+  // rows of one slice store as one 128-byte line per slot
+  constexpr int WF = 2 * P + 1, NC = DIM == 3 ? WF : 1, NSLOT = WF * WF * NC;
+  const int A = blockIdx.x * blockDim.x + threadIdx.x;
+  if (A >= (N + 31) / 32 * 32) return;
+  float *o = sl + sl_index(A, 0, NSLOT);
+  if (A >= N) {  // the last slice's padding rows
+    for (int s = 0; s < NSLOT; s++) o[32 * s] = 0.f;
+    return;
   }
-  sl[t] = v;
+  const RowShape R = row_shape<DIM>(S, A);
+  const float *v = csr + rowptr[A];
+  int k = 0;  // the next stored value of the row: slots run in the row's column order
+  for (int c = 0; c < NC; c++)
+    for (int b = 0; b < WF; b++) {
+      const bool line = b < R.w1 && c < R.w2;
+#pragma unroll
+      for (int a = 0; a < WF; a++) {
+        float x = 0.f;
+        if (line && a < R.w0) x = v[k++];
+        o[32 * (a + WF * (b + WF * c))] = x;
+      }
+    }
 }
 
 // y = A x on the sliced values, one thread per row, FP32 products and sums: each slot is
@@ -900,17 +911,31 @@ cudaError_t launch_slice32(iga_s *h) {
   h->J32s_valid = false;
   if (h->inner || !slice_pays(h)) return cudaSuccess;
   const int wf = 2 * h->p + 1, nslot = h->dim == 3 ? wf * wf * wf : wf * wf;
-  const int64_t total = (h->N + 31) / 32 * 32 * (int64_t)nslot;
+  const int64_t total = (h->N + 31) / 32 * 32 * (int64_t)nslot;  // floats of the sliced copy
   if (!h->J32s) {
     cudaError_t ce = cudaMalloc((void **)&h->J32s, total * sizeof(float));
     if (ce) return ce;
   }
   const StencilRows S = stencil_rows(h);
-  const unsigned g = (unsigned)((total + 255) / 256);
-  if (h->dim == 3)
-    IGA_LAUNCH(h, KC_VEC, (k_csr_to_sliced<3><<<g, 256, 0, h->stream>>>(S, h->rowptr, h->J32, h->J32s, (int)h->N, wf)));
-  else
-    IGA_LAUNCH(h, KC_VEC, (k_csr_to_sliced<2><<<g, 256, 0, h->stream>>>(S, h->rowptr, h->J32, h->J32s, (int)h->N, wf)));
+  const unsigned g = (unsigned)(((h->N + 31) / 32 * 32 + 255) / 256);
+  const int N = (int)h->N;
+  IGA_LAUNCH(h, KC_VEC, ({
+    if (h->dim == 3) {
+      switch (h->p) {
+        case 1: k_csr_to_sliced<3, 1><<<g, 256, 0, h->stream>>>(S, h->rowptr, h->J32, h->J32s, N); break;
+        case 2: k_csr_to_sliced<3, 2><<<g, 256, 0, h->stream>>>(S, h->rowptr, h->J32, h->J32s, N); break;
+        case 3: k_csr_to_sliced<3, 3><<<g, 256, 0, h->stream>>>(S, h->rowptr, h->J32, h->J32s, N); break;
+        default: k_csr_to_sliced<3, 4><<<g, 256, 0, h->stream>>>(S, h->rowptr, h->J32, h->J32s, N); break;
+      }
+    } else {
+      switch (h->p) {
+        case 1: k_csr_to_sliced<2, 1><<<g, 256, 0, h->stream>>>(S, h->rowptr, h->J32, h->J32s, N); break;
+        case 2: k_csr_to_sliced<2, 2><<<g, 256, 0, h->stream>>>(S, h->rowptr, h->J32, h->J32s, N); break;
+        case 3: k_csr_to_sliced<2, 3><<<g, 256, 0, h->stream>>>(S, h->rowptr, h->J32, h->J32s, N); break;
+        default: k_csr_to_sliced<2, 4><<<g, 256, 0, h->stream>>>(S, h->rowptr, h->J32, h->J32s, N); break;
+      }
+    }
+  }));
   cudaError_t ce = cudaGetLastError();
   if (!ce) h->J32s_valid = true;
   return ce;
