@@ -338,29 +338,25 @@ __global__ void __launch_bounds__(128) k_final(DirArgs d0, DirArgs d1, DirArgs d
     const int xs = f.xs, np = f.np;
     const T *pv = tab + (size_t)f.po * IGA_PVS;
     T acc = 0;
-    for (int k = 0; k < np; k++) {
-      const size_t xo = (size_t)(xs + k);
-      const T p00 = pv[IGA_PVS * k + 0];
-      size_t r, rT;
-      if (DIM == 3) {
-        r = (xo * d1.np + pmid) * d0.np + pi0;
-        rT = (xo * d1.np + pmidT) * d0.np + pi0T;
-      } else {
-        r = xo * d0.np + pi0;
-        rT = xo * d0.np + pi0T;
-      }
-      const size_t rs = (DIM == 2 || mid_sym) ? r : rT;
+    // the stage-2 entries of this pair at its first common Gauss point; the next points
+    // are one line (step) further (the same indices as r, rT = ((xs + k) n1 + pmid) n0 + pi0)
+    const size_t step = (DIM == 3) ? (size_t)d1.np * d0.np : (size_t)d0.np;
+    const T *ir = in + (DIM == 3 ? ((size_t)xs * d1.np + pmid) * d0.np + pi0 : (size_t)xs * d0.np + pi0);
+    const T *irT = in + (DIM == 3 ? ((size_t)xs * d1.np + pmidT) * d0.np + pi0T : (size_t)xs * d0.np + pi0T);
+    const T *irs = (DIM == 2 || mid_sym) ? ir : irT;
+    for (int k = 0; k < np; k++, pv += IGA_PVS, ir += step, irT += step, irs += step) {
+      const T p00 = pv[0];
       if (PLAN == PLAN_MASS) {
-        acc = fma(p00, in[rs], acc);
+        acc = fma(p00, irs[0], acc);
       } else if (PLAN == PLAN_DIAG) {
-        acc = fma(p00, in[rs], acc);
-        acc = fma(pv[IGA_PVS * k + 3], in[2 * plane + rs], acc);
+        acc = fma(p00, irs[0], acc);
+        acc = fma(pv[3], irs[2 * plane], acc);
       } else {
-        const T p10 = pv[IGA_PVS * k + 1], p01 = pv[IGA_PVS * k + 2], p11 = pv[IGA_PVS * k + 3];
-        acc = fma(p00, in[rs], acc);
-        acc = fma(p10, in[plane + r], acc);
-        acc = fma(p01, in[plane + rT], acc);
-        acc = fma(p11, in[2 * plane + rs], acc);
+        const T p10 = pv[1], p01 = pv[2], p11 = pv[3];
+        acc = fma(p00, irs[0], acc);
+        acc = fma(p10, ir[plane], acc);
+        acc = fma(p01, irT[plane], acc);
+        acc = fma(p11, irs[2 * plane], acc);
       }
     }
     int64_t A, B, pos, posT;
