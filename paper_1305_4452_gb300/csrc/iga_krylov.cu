@@ -151,6 +151,9 @@ template <int DIM, int LPR>
 __global__ void __launch_bounds__(256) k_spmv_fixed(StencilRows S, const int64_t *__restrict__ rowptr,
                                                     const double *__restrict__ val, const double *__restrict__ x,
                                                     double *__restrict__ y, int N, const double *__restrict__ done, int dmask) {
+  // launched as a programmatic dependent of the orthogonalisation (see spmv_fixed_launch):
+  // its blocks may be resident before that grid ends; nothing is read before it has
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   if (done && done[0] != 0.0) return;
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int row = gid / LPR, lane = gid % LPR;
@@ -658,6 +661,9 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_fused(const double *__restric
                                                          double *__restrict__ P2, int64_t N, int per, double *__restrict__ gm,
                                                          int m, double tol, unsigned *bar) {
   extern __shared__ double fs_sm[];
+  // the operator product that follows may start launching its blocks now; they wait for
+  // this grid's end before reading (griddepcontrol.wait in k_spmv_fixed)
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int jp1 = j + 1;
   double *ws = fs_sm;                  // [per]
   double *hs = ws + per;               // [m + 2]: h1, then h1 + h2
@@ -966,12 +972,25 @@ static cudaError_t spmv_fixed_launch(iga_s *h, const double *vals, const double 
       if (h->bnd.flag[d][s]) dmask |= 1 << (2 * d + s);
   const StencilRows S = stencil_rows(h);
   const int N = (int)h->N;
-  unsigned grid = (unsigned)(((int64_t)N * 4 + 255) / 256);
+  // a programmatic dependent launch: when the preceding kernel (the orthogonalisation)
+  // signals early, the product's blocks become resident beside it and start the moment it
+  // ends, instead of after a full launch latency
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(((int64_t)N * 4 + 255) / 256));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = h->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t le = cudaSuccess;
   if (h->dim == 3)
-    IGA_LAUNCH(h, KC_SPMV, (k_spmv_fixed<3, 4><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, x, y, N, done, dmask)));
+    IGA_LAUNCH(h, KC_SPMV, (le = cudaLaunchKernelEx(&cfg, k_spmv_fixed<3, 4>, S, h->rowptr, vals, x, y, N, done, dmask)));
   else
-    IGA_LAUNCH(h, KC_SPMV, (k_spmv_fixed<2, 4><<<grid, 256, 0, h->stream>>>(S, h->rowptr, vals, x, y, N, done, dmask)));
-  return cudaGetLastError();
+    IGA_LAUNCH(h, KC_SPMV, (le = cudaLaunchKernelEx(&cfg, k_spmv_fixed<2, 4>, S, h->rowptr, vals, x, y, N, done, dmask)));
+  return le != cudaSuccess ? le : cudaGetLastError();
 }
 
 cudaError_t launch_spmv64_fixed(iga_s *h, const double *vals, const double *x, double *y) {
