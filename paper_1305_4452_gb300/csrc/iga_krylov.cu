@@ -785,15 +785,29 @@ timeout:
   }
 }
 
-// solve the k x k upper triangular system H y = g (one thread); k = fl[1]
+// solve the k x k upper triangular system H y = g (k = fl[1]) by columns, one warp: from
+// i = k - 1 down, y_i = g_i / H_ii (0 for a zero pivot), then g_c -= H_ci y_i for the rows
+// c < i, the lanes taking the rows (on a shared copy of g).  A single thread summing each
+// row took the FP64 latency of every product in turn; here a row costs one division and one
+// FMA per lane.
 __global__ void k_trisolve(double *__restrict__ gm, int m) {
   GmLayout L = gm_layout(m);
-  int k = (int)gm[L.flags + 1];
+  __shared__ double sg[1024];
+  const int k = (int)gm[L.flags + 1];
+  const int lane = threadIdx.x;
+  for (int i = lane; i < k; i += 32) sg[i] = gm[L.g + i];
+  __syncwarp();
   for (int i = k - 1; i >= 0; i--) {
-    double s = gm[L.g + i];
-    for (int c = i + 1; c < k; c++) s -= gm[L.H + (size_t)c * (m + 1) + i] * gm[L.y + c];
-    double d = gm[L.H + (size_t)i * (m + 1) + i];
-    gm[L.y + i] = (d != 0.0) ? s / d : 0.0;
+    const double *Hi = gm + L.H + (size_t)i * (m + 1);  // column i of H: H_ci, c <= i
+    double yi = 0.0;
+    if (lane == 0) {
+      const double d = Hi[i];
+      yi = (d != 0.0) ? sg[i] / d : 0.0;
+      gm[L.y + i] = yi;
+    }
+    yi = __shfl_sync(0xffffffffu, yi, 0);
+    for (int c = lane; c < i; c += 32) sg[c] -= Hi[c] * yi;
+    __syncwarp();
   }
 }
 
@@ -820,8 +834,10 @@ __global__ void k_residual_vec(const double *__restrict__ b, const double *__res
 // start a cycle: beta = sqrt(sumsq); V0 = r / beta; z = dinv V0; g = (beta, 0..); flags reset
 __global__ void k_cycle_init_scalars(double *__restrict__ gm, int m, const double *__restrict__ sumsq, double tol) {
   GmLayout L = gm_layout(m);
+  for (int i = threadIdx.x; i < L.size; i += blockDim.x) gm[i] = 0.0;  // the whole block clears
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   double beta = sqrt(sumsq[0]);
-  for (int i = 0; i < L.size; i++) gm[i] = 0.0;
   gm[L.g] = beta;
   gm[L.flags + 2] = beta;
   gm[L.flags + 4] = beta;
@@ -1124,7 +1140,7 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
       IGA_LAUNCH(h, KC_VEC, (k_residual_vec<<<eg, 256, 0, h->stream>>>(b, tmp, Vb, N)));
     }
     sumsq(h, Vb, scal);
-    IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_cycle_init_scalars<<<1, 1, 0, h->stream>>>(gm, m, scal, tol_abs)));
+    IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_cycle_init_scalars<<<1, 256, 0, h->stream>>>(gm, m, scal, tol_abs)));
     IGA_LAUNCH(h, KC_VEC, (k_normalize<<<eg, 256, 0, h->stream>>>(Vb, gm + L.flags + 4, Vb, dinv, z, N, gm + L.flags + 5)));  // flags[5] stays 0
     int j = 0;
     bool cycle_done = false;
@@ -1173,7 +1189,7 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
     int k = (int)fl_host[1];
     total += k;
     if (k > 0) {
-      IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_trisolve<<<1, 1, 0, h->stream>>>(gm, m)));
+      IGA_LAUNCH(h, KC_GMRES_SCALAR, (k_trisolve<<<1, 32, 0, h->stream>>>(gm, m)));
       IGA_LAUNCH(h, KC_VEC, (k_update_x<<<eg, 256, 0, h->stream>>>(Vb, ld, gm, m, dinv, x, N)));
     }
     if (fl_host[3] != 0.0) { rc = (fl_host[2] <= tol_abs) ? 0 : 2; break; }

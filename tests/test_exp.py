@@ -1,8 +1,8 @@
 """The FP64 exponential of the Gauss-point kernels (csrc/iga_exp.h: Tang's table-driven
 method, ACM TOMS 1989).
 
-CPU: its constants are the doubles nearest to the values the method defines (32/ln2,
-ln2/32 split into two parts, 2^(j/32), 1/k!), recomputed here at 60 digits.
+CPU: its constants are the doubles nearest to the values the method defines (64/ln2,
+ln2/64 split into two parts, 2^(j/64), 1/k!), recomputed here at 60 digits.
 GPU: against the host libm exp and CUDA's exp (through torch) on a million arguments
 and the special values; at most 2 units in the last place from the host exp.
 """
@@ -23,29 +23,31 @@ def test_table_and_constants_are_the_nearest_doubles():
     mp = pytest.importorskip("mpmath")
     mp.mp.dps = 60
     src = open(HDR).read()
-    tab_src = src[src.index("iga_exp_tab[32]"):src.index("};")]
+    tab_src = src[src.index("iga_exp_tab[64]"):src.index("};")]
     tab = _hex_literals(tab_src)
-    assert len(tab) == 32
+    assert len(tab) == 64
     for j, t in enumerate(tab):
-        assert t == float(mp.power(2, mp.mpf(j) / 32)), j
+        assert t == float(mp.power(2, mp.mpf(j) / 64)), j
     body = src[src.index("double iga_exp("):]
     consts = dict(re.findall(r"const double (\w+) = (0x1\.[0-9a-f]+p[+-]\d+)", body))
     ln2 = mp.log(2)
-    assert float.fromhex(consts["inv_l"]) == float(32 / ln2)
+    assert float.fromhex(consts["inv_l"]) == float(64 / ln2)
     l1, l2 = float.fromhex(consts["l1"]), float.fromhex(consts["l2"])
-    assert l1 == float(ln2 / 32) and l2 == float(ln2 / 32 - mp.mpf(l1))
-    assert abs(mp.mpf(l1) + mp.mpf(l2) - ln2 / 32) < mp.mpf(2) ** -110
-    # Taylor coefficients 1/6! ... 1/2! in the order of the Horner steps
+    assert l1 == float(ln2 / 64) and l2 == float(ln2 / 64 - mp.mpf(l1))
+    assert abs(mp.mpf(l1) + mp.mpf(l2) - ln2 / 64) < mp.mpf(2) ** -110
+    # Taylor coefficients 1/5! ... 1/2! in the order of the Horner steps
     coeffs = [float.fromhex(h) for h in re.findall(r"fma\(r, (?:q|0x1\.[0-9a-f]+p[+-]\d+), (0x1\.[0-9a-f]+p[+-]\d+)\)", body)]
     first = float.fromhex(re.search(r"fma\(r, (0x1\.[0-9a-f]+p[+-]\d+),", body).group(1))
-    assert first == float(1 / mp.factorial(6))
-    assert coeffs == [float(1 / mp.factorial(k)) for k in (5, 4, 3, 2)]
+    assert first == float(1 / mp.factorial(5))
+    assert coeffs == [float(1 / mp.factorial(k)) for k in (4, 3, 2)]
+    # the range test: the high word of 700.0
+    assert int(re.search(r"< (0x[0-9A-Fa-f]+)u", body).group(1), 16) == (int.from_bytes(__import__("struct").pack(">d", 700.0), "big") >> 32)
 
 
 def test_truncation_bound_of_the_polynomial():
-    # |r| <= ln2/64 after the reduction; the dropped Taylor terms are below r^7/7! e^|r|
-    r = np.log(2) / 64
-    assert r ** 7 / 5040 * np.exp(r) < 4e-18
+    # |r| <= ln2/128 after the reduction; the dropped Taylor terms are below r^6/6! e^|r|
+    r = np.log(2) / 128
+    assert r ** 6 / 720 * np.exp(r) < 4e-17
 
 
 @pytest.mark.gpu
@@ -57,8 +59,9 @@ def test_gpu_exp_within_two_ulp_of_the_host_exp():
     build.build()
     rng = np.random.default_rng(7)
     x = np.concatenate([rng.uniform(-20, 20, 600_000), rng.uniform(-700, 700, 300_000),
-                        rng.normal(0, 1e-3, 100_000), [0.0, -0.0, 1e-300, -1e-300, 700.0, -700.0],
-                        np.log(2) / 64 * np.arange(-64, 65)])
+                        rng.normal(0, 1e-3, 100_000), [0.0, -0.0, 1e-300, -1e-300, 700.0, -700.0,
+                                                       np.nextafter(700.0, 0.0), np.nextafter(-700.0, 0.0)],
+                        np.log(2) / 128 * np.arange(-128, 129)])
     xd = torch.tensor(x, dtype=torch.float64, device="cuda")
     y = iga.exp_eval(xd).cpu().numpy()
     ref = np.exp(x)
