@@ -145,6 +145,13 @@ iga_status iga_set_wait_limit(iga_t iga, double seconds);
  * Faults nothing: the give-up is the bounded wait's normal exit. */
 iga_status iga_inject_stall(iga_t iga);
 
+/* Form of the GMRES orthogonalisation (a library facility): fused = 1 (default) runs each
+ * Arnoldi step's Gram-Schmidt passes, norm and Givens step as one cooperative launch when
+ * the row partition fits the GPU's resident blocks (up to about 2.5M unknowns), else as
+ * separate pass kernels; fused = 0 always takes the separate kernels (the same arithmetic
+ * up to the norm's summation order).  Other values: IGA_EINVAL. */
+iga_status iga_set_gmres_fused(iga_t iga, int fused);
+
 /* Change lambda after creation (used by the batched and learned-start drivers). */
 iga_status iga_set_lambda(iga_t iga, double lambda);
 
@@ -226,9 +233,20 @@ typedef struct {
   int ksp;             /* Krylov method: IGA_KSP_GMRES (default) or IGA_KSP_CG (Jacobi-
                           preconditioned conjugate gradients, the -ksp_type cg run of App. B;
                           valid because the Jacobian with symmetric Dirichlet rows is symmetric) */
+  int gmres_cgs_refine; /* second classical Gram-Schmidt pass of each GMRES (Arnoldi) step:
+                          IGA_CGS_REFINE_NEVER (default: one pass, the default refinement type
+                          of PETSc's GMRES, the solver behind the paper's SNESSolve),
+                          IGA_CGS_REFINE_ALWAYS (classical Gram-Schmidt twice) or
+                          IGA_CGS_REFINE_IFNEEDED (a second pass only when the first removes
+                          at least half of ||w||^2, i.e. ||w - V h|| <= ||w|| / sqrt(2)); other
+                          values: IGA_EINVAL.  Where the orthogonalisation runs as separate
+                          pass kernels (iga_set_gmres_fused) IFNEEDED refines always. */
 } iga_newton_opts;
 #define IGA_KSP_GMRES 0
 #define IGA_KSP_CG 1
+#define IGA_CGS_REFINE_NEVER 0
+#define IGA_CGS_REFINE_IFNEEDED 1
+#define IGA_CGS_REFINE_ALWAYS 2
 
 typedef struct {
   int newton_its;         /* Newton steps taken */

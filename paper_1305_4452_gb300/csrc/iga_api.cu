@@ -246,6 +246,16 @@ extern "C" iga_status iga_inject_stall(iga_t h) {
   return IGA_OK;
 }
 
+extern "C" iga_status iga_set_gmres_fused(iga_t h, int fused) {
+  if (!h) return IGA_EINVAL;
+  if (fused != 0 && fused != 1) {
+    h->err = "fused must be 0 or 1";
+    return IGA_EINVAL;
+  }
+  h->gs_unfused = fused == 0;
+  return IGA_OK;
+}
+
 extern "C" iga_status iga_set_lambda(iga_t h, double lambda) {
   if (!h || !isfinite(lambda)) return IGA_EINVAL;
   h->lambda = lambda;
@@ -364,6 +374,7 @@ extern "C" void iga_newton_defaults(iga_newton_opts *o) {
   o->jac = IGA_FP64;
   o->reuse_stiffness = 1;
   o->ksp = IGA_KSP_GMRES;
+  o->gmres_cgs_refine = IGA_CGS_REFINE_NEVER;
 }
 
 // ---- small vector kernels of the Newton driver ----
@@ -466,6 +477,7 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
     return IGA_EINVAL;
   }
   if (!U || o.gmres_restart < 1 || o.gmres_restart > 1000 || o.max_newton < 0 || !(o.atol >= 0.0) ||
+      o.gmres_cgs_refine < IGA_CGS_REFINE_NEVER || o.gmres_cgs_refine > IGA_CGS_REFINE_ALWAYS ||
       (o.jac != IGA_FP64 && o.jac != IGA_JAC_TF32 && o.jac != IGA_JAC_BF16 && o.jac != IGA_JAC_FP32 &&
        o.jac != IGA_JAC_NONE && o.jac != IGA_JAC_FD)) {
     h->err = "bad Newton options or NULL U";
@@ -543,7 +555,8 @@ extern "C" iga_status iga_solve_newton(iga_t h, double *U, const iga_newton_opts
     // and the zero columns
     const int kind = mf ? 2 : (f32 ? 1 : (o.jac == IGA_FP64 ? 3 : 0));
     int grc = (o.ksp == IGA_KSP_CG) ? cg_solve(h, Jv, kind, Ft, dU, tol_abs, o.max_krylov, &its, &ce)
-                                    : gmres_solve(h, Jv, kind, Ft, dU, tol_abs, o.gmres_restart, o.max_krylov, &its, &ce);
+                                    : gmres_solve(h, Jv, kind, Ft, dU, tol_abs, o.gmres_restart, o.max_krylov,
+                                                  o.gmres_cgs_refine, &its, &ce);
     if (grc < 0) {
       h->err = iga_format("GMRES: %s", cudaGetErrorString(ce));
       return IGA_ECUDA;

@@ -14,8 +14,9 @@
 //             sliced by 32 rows for the operator products (see jslot); axis 0 runs
 //             on tiles of Gauss lines staged in shared memory (see b_stage1);
 //   GMRES(m)  with right Jacobi preconditioning; FP64 Krylov vectors and
-//             classical Gram-Schmidt applied twice (one warp per dot product,
-//             fixed-order warp reductions), FP32 operator products; or Jacobi CG;
+//             classical Gram-Schmidt, once or twice as gmres_cgs_refine says (one
+//             warp per dot product, fixed-order warp reductions), FP32 operator
+//             products; or Jacobi CG;
 //   Newton    with backtracking, as in iga_solve_newton.
 // There are no spin-waits: every loop is bounded by the Newton and Krylov caps.
 // The launch, the copy of its arguments and the read-back of the per-instance
@@ -447,7 +448,7 @@ __device__ void b_cgs_pass(const BInst &I, double *__restrict__ w, int jp1, GmSh
 // returns 0 converged, 1 cap reached, 2 breakdown/NaN
 template <int P>
 __device__ int b_gmres(const BInst &I, const double *__restrict__ b, double *__restrict__ x, double tol, int m, int maxit,
-                       GmShared &s, const Cta &c, int *its) {
+                       int refine, GmShared &s, const Cta &c, int *its) {
   const BMesh &M = I.m;
   const int N = M.N;
   // Jacobi scaling from the diagonal
@@ -495,8 +496,25 @@ __device__ int b_gmres(const BInst &I, const double *__restrict__ b, double *__r
     for (int j = 0; j < m && total + j < maxit; j++) {
       double *w = I.w;
       b_apply<P>(I, I.V + (size_t)j * N, w, true, c);
+      // classical Gram-Schmidt once, twice, or twice where the first pass removes more than
+      // half of ||w||^2 (the modes of gmres_cgs_refine)
+      double w0 = 0.0;
+      if (refine == IGA_CGS_REFINE_IFNEEDED) {
+        for (int r = c.tid; r < N; r += c.nt) w0 = fma(w[r], w[r], w0);
+        w0 = cta_sum(c, w0);
+      }
       b_cgs_pass(I, w, j + 1, s, j, true, c);
-      b_cgs_pass(I, w, j + 1, s, j, false, c);
+      bool twice = refine == IGA_CGS_REFINE_ALWAYS;
+      if (refine == IGA_CGS_REFINE_IFNEEDED) {
+        if (c.tid == 0) {
+          double t = 0.0;
+          for (int i = 0; i <= j; i++) t = fma(s.H[i][j], s.H[i][j], t);
+          s.flag[1] = (w0 - t > 0.5 * w0) ? 0 : 1;
+        }
+        __syncthreads();
+        twice = s.flag[1] != 0;
+      }
+      if (twice) b_cgs_pass(I, w, j + 1, s, j, false, c);
       double ww = 0.0;
       for (int r = c.tid; r < N; r += c.nt) ww = fma(w[r], w[r], ww);
       ww = cta_sum(c, ww);
@@ -646,7 +664,7 @@ __device__ void b_solve(const BInst &I, double *__restrict__ U, const iga_newton
     if (tol < 0.5 * o.atol) tol = 0.5 * o.atol;
     int its = 0;
     if (o.ksp == IGA_KSP_CG) b_cg<P>(I, Ft, dU, tol, o.max_krylov, c, &its);
-    else b_gmres<P>(I, Ft, dU, tol, m, o.max_krylov, s, c, &its);
+    else b_gmres<P>(I, Ft, dU, tol, m, o.max_krylov, o.gmres_cgs_refine, s, c, &its);
     kry += its;
     double alpha = 1.0, ft = 0.0;
     bool ok = false;
@@ -1094,7 +1112,8 @@ extern "C" iga_status iga_batch_solve(iga_batch_t b, double *U, const iga_newton
   iga_newton_opts o;
   iga_newton_defaults(&o);
   if (opts_in) o = *opts_in;
-  if (!U || o.gmres_restart < 1 || o.max_newton < 0 || !(o.atol >= 0.0)) {
+  if (!U || o.gmres_restart < 1 || o.max_newton < 0 || !(o.atol >= 0.0) || o.gmres_cgs_refine < IGA_CGS_REFINE_NEVER ||
+      o.gmres_cgs_refine > IGA_CGS_REFINE_ALWAYS) {
     b->err = "bad options or NULL U";
     return IGA_EINVAL;
   }

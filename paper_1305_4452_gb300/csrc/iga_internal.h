@@ -214,6 +214,7 @@ struct iga_s {
   float *z32 = nullptr;        // FP32 copy of the Krylov vector for the FP32 SpMV
   ElemGemmPlan *egemm = nullptr;  // element matrices as one GEMM across elements (iga_elem_gemm.cu)
   uint64_t wait_limit_ns = 2000000000ull;  // bound of each pipeline wait of the tensor-core kernels
+  bool gs_unfused = false;     // GMRES orthogonalisation by the separate pass kernels only
   bool stall_next = false;     // failure-detection test: the next element GEMM waits on a barrier nothing completes
   // Newton / Krylov workspace
   double *J64 = nullptr;
@@ -320,6 +321,6 @@ cudaError_t launch_nan_check(iga_s *h, const double *x, double *out_dev);
 int cg_solve(iga_s *h, const void *vals, int is_f32, const double *b, double *x, double tol_abs, int maxit, int *its,
              cudaError_t *cerr);
 int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double *x, double rtol_abs,
-                int m, int maxit, int *its, cudaError_t *cerr);
+                int m, int maxit, int refine, int *its, cudaError_t *cerr);
 
 std::string iga_format(const char *fmt, ...);

@@ -1,6 +1,6 @@
 // Krylov kernels of libiga: CSR SpMV, Jacobi scaling, deterministic dot
 // products and norms, and restarted GMRES(m) with right Jacobi preconditioning
-// and classical Gram-Schmidt applied twice, all in FP64.  The scalar GMRES
+// and classical Gram-Schmidt applied once or twice, all in FP64.  The scalar GMRES
 // bookkeeping (Givens rotations, residual estimate, triangular solve) runs in
 // one-thread kernels on the device; every kernel of an iteration returns at
 // once when the device "done" flag is set, so the host enqueues several
@@ -195,9 +195,12 @@ __global__ void __launch_bounds__(256) k_spmv_fixed(StencilRows S, const int64_t
       }
       int col = (R.lo0 + ii) + (R.lo1 + jj) * S.n0 + (R.lo2 + kk) * S.n01;
       const int djj = S.n0 - R.w0, dkk = S.n01 - R.w1 * S.n0;
+      // the values stream through once per product: loaded evict-first (__ldcs), so that
+      // they do not push x and the Krylov basis, which the orthogonalisation re-reads every
+      // iteration, out of L2
 #pragma unroll 4
       for (int e = e0 + lane; e < e1; e += LPR) {
-        acc = fma(v[e], x[col], acc);
+        acc = fma(__ldcs(v + e), x[col], acc);
         ii += LPR;
         col += LPR;
         while (ii >= R.w0) {
@@ -334,6 +337,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_rows(const double *__res
 //            order); H[:, j] = h1 (block 0); w -= V h1; partial2[i][b] = V[i] . w
 //   pass 3:  h2 = sum_b partial2; H[:, j] += h2 (block 0); w -= V h2;
 //            partial3[b] = sum of w[r]^2
+//   pass 4:  (one pass, no refinement, in place of passes 2 and 3) h1 = sum_b partial1;
+//            H[:, j] = h1 (block 0); w -= V h1; partial3[b] = sum of w[r]^2
 // followed by k_gs_finish (norm, Givens step, next basis vector).  Dots use one
 // warp per basis vector over the block's rows with w in shared memory; the
 // block-local sums of the partials make the separate reduction launches
@@ -389,16 +394,22 @@ __device__ void block_dots(const double *__restrict__ Vb, int64_t ld, int jp1, i
       const int i = it / R, c = it - i * R;
       const int r0 = c * clen, r1 = min(cnt, r0 + clen);
       const double *v = Vb + (size_t)i * ld + a;
-      // two independent chains (rows r0+lane+64k and r0+lane+32+64k), added at the end
-      double acc = 0.0, acc2 = 0.0;
+      // four independent chains (rows r0 + lane + 32 q + 128 k, q < 4), added at the end as
+      // (acc0 + acc1) + (acc2 + acc3): four loads of V in flight per lane and step, since
+      // the basis comes from HBM and few warps share an SM's FP64 pipe here
+      double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
       int r = r0 + lane;
-#pragma unroll 2
-      for (; r + 32 < r1; r += 64) {
-        acc = fma(v[r], ws[r], acc);
-        acc2 = fma(v[r + 32], ws[r + 32], acc2);
+      for (; r + 96 < r1; r += 128) {
+        const double x0 = v[r], x1 = v[r + 32], x2 = v[r + 64], x3 = v[r + 96];
+        acc0 = fma(x0, ws[r], acc0);
+        acc1 = fma(x1, ws[r + 32], acc1);
+        acc2 = fma(x2, ws[r + 64], acc2);
+        acc3 = fma(x3, ws[r + 96], acc3);
       }
-      if (r < r1) acc = fma(v[r], ws[r], acc);
-      acc = warp_sum(acc + acc2);
+      if (r < r1) acc0 = fma(v[r], ws[r], acc0);
+      if (r + 32 < r1) acc1 = fma(v[r + 32], ws[r + 32], acc1);
+      if (r + 64 < r1) acc2 = fma(v[r + 64], ws[r + 64], acc2);
+      double acc = warp_sum((acc0 + acc1) + (acc2 + acc3));
       if (lane == 0) dp[warp] = acc;
     }
     __syncthreads();
@@ -432,7 +443,7 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_pass(const double *__restrict
   if (PASS >= 2) {
     block_sum_cols(prev, gridDim.x, jp1, hs);
     if (blockIdx.x == 0)
-      for (int i = threadIdx.x; i < jp1; i += blockDim.x) Hj[i] = (PASS == 2) ? hs[i] : Hj[i] + hs[i];
+      for (int i = threadIdx.x; i < jp1; i += blockDim.x) Hj[i] = (PASS == 3) ? Hj[i] + hs[i] : hs[i];
   }
   double sq = 0.0;
   // two rows per thread and step: two independent FMA chains, their loads interleaved
@@ -452,7 +463,7 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_pass(const double *__restrict
       w[a + r] = v;
       if (two) w[a + r2] = v2;
     }
-    if (PASS == 3) {
+    if (PASS >= 3) {
       sq = fma(v, v, sq);
       if (two) sq = fma(v2, v2, sq);
     } else {
@@ -460,7 +471,7 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_pass(const double *__restrict
       if (two) ws[r2] = v2;
     }
   }
-  if (PASS == 3) {
+  if (PASS >= 3) {
     sq = block_sum(sq, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = sq;
     return;
@@ -484,20 +495,15 @@ __global__ void k_normalize(const double *w, const double *__restrict__ hn, doub
   }
 }
 
-// Givens step for column j of H (one thread)
 // Givens step for column j of H, on a copy of the column and of the previous
-// rotations in shared memory (Hs[0..j+1], cs_s[0..j), sn_s[0..j)); one thread.
-// H[j+1][j] arrives in Hs[j+1] as a sum of squares.  Writes the rotated column,
-// the new rotation, g and the flags back to gm.
-__device__ void givens_step_sm(double *Hs, const double *cs_s, const double *sn_s, double *__restrict__ gm, int m, int j,
-                               double tol) {
-  GmLayout L = gm_layout(m);
-  double *fl = gm + L.flags;
-  double *Hj = gm + L.H + (size_t)j * (m + 1);
-  const double hn = sqrt(Hs[j + 1]);
-  Hs[j + 1] = hn;
-  // the previous rotations, the running component t carried in a register: one dependent
-  // FMA per rotation (single-thread FP64 latency on GB300's narrow pipe is the cost here)
+// rotations in shared memory (Hs[0..j+1], cs_s[0..j), sn_s[0..j)), one thread, in two
+// parts: givens_apply_prev rotates Hs[0..j] by the previous rotations (it needs only the
+// Gram-Schmidt coefficients, so it can run before ||w|| is known) and returns the rotated
+// last component t; givens_new forms the new rotation from t and H[j+1][j] = sqrt(hn2),
+// writes the rotated column, the rotation, g (gj = g[j] on entry) and the flags to gm.
+__device__ double givens_apply_prev(double *Hs, const double *cs_s, const double *sn_s, int j) {
+  // the running component t carried in a register: one dependent FMA per rotation
+  // (single-thread FP64 latency on GB300's narrow pipe is the cost here)
   double t = Hs[0];
   for (int i = 0; i < j; i++) {
     const double c = cs_s[i], s = sn_s[i], b = Hs[i + 1];
@@ -505,8 +511,16 @@ __device__ void givens_step_sm(double *Hs, const double *cs_s, const double *sn_
     Hs[i] = fma(c, t, sb);
     t = fma(-s, t, cb);
   }
-  Hs[j] = t;
-  const double a = t, b = Hs[j + 1];
+  return t;
+}
+
+__device__ void givens_new(double *Hs, double t, double hn2, double gj, double *__restrict__ gm, int m, int j,
+                           double tol) {
+  GmLayout L = gm_layout(m);
+  double *fl = gm + L.flags;
+  double *Hj = gm + L.H + (size_t)j * (m + 1);
+  const double hn = sqrt(hn2);
+  const double a = t, b = hn;
   const double r = hypot(a, b);
   const double c = (r > 0.0) ? a / r : 1.0, s = (r > 0.0) ? b / r : 0.0;
   gm[L.cs + j] = c;
@@ -514,7 +528,6 @@ __device__ void givens_step_sm(double *Hs, const double *cs_s, const double *sn_
   Hs[j] = r;
   Hs[j + 1] = 0.0;
   for (int i = 0; i <= j + 1; i++) Hj[i] = Hs[i];
-  const double gj = gm[L.g + j];
   gm[L.g + j] = c * gj;
   gm[L.g + j + 1] = -s * gj;
   const double res = fabs(s * gj);
@@ -524,6 +537,15 @@ __device__ void givens_step_sm(double *Hs, const double *cs_s, const double *sn_
   if (breakdown) fl[3] = 1.0;
   if (res <= tol || breakdown || j + 1 == m) fl[0] = 1.0;
   fl[4] = hn;
+}
+
+// H[j+1][j] arrives in Hs[j+1] as a sum of squares.
+__device__ void givens_step_sm(double *Hs, const double *cs_s, const double *sn_s, double *__restrict__ gm, int m, int j,
+                               double tol) {
+  GmLayout L = gm_layout(m);
+  const double gj = gm[L.g + j];
+  const double t = givens_apply_prev(Hs, cs_s, sn_s, j);
+  givens_new(Hs, t, Hs[j + 1], gj, gm, m, j, tol);
 }
 
 // End of a GMRES iteration: ||w||^2 = sum of the pass-3 partials (every block,
@@ -641,32 +663,37 @@ __device__ __forceinline__ double gs_update_rows(const double *__restrict__ Vb, 
   return sq;
 }
 
-// The three Gram-Schmidt passes and the end of the iteration (k_gs_pass<1..3> and
-// k_gs_finish) as one kernel: classical Gram-Schmidt applied twice to w = A z_j against
-// V_0..V_j, the new column of H, v_{j+1} = w / ||w||, z = dinv .* v_{j+1} and the Givens
-// step.  Blocks own the row ranges of gs_partition and keep their rows of w in shared
-// memory from the first phase to the last; the phases are separated by grid barriers.
-//   phase 1: partial1[i][b] = V_i . w over the block's rows
-//   phase 2: h1 = sum_b partial1 (same sums in every block); H[:, j] = h1; w -= V h1;
+// The Gram-Schmidt passes and the end of the iteration (k_gs_pass<1..4> and k_gs_finish)
+// as one kernel: classical Gram-Schmidt applied once or twice (refine, the modes of
+// gmres_cgs_refine) to w = A z_j against V_0..V_j, the new column of H, v_{j+1} = w / ||w||,
+// z = dinv .* v_{j+1} and the Givens step.  Blocks own the row ranges of gs_partition and
+// keep their rows of w in shared memory from the first phase to the last; the phases are
+// separated by grid barriers.
+//   phase 1: partial1[i][b] = V_i . w over the block's rows (and, unless refine is
+//            ALWAYS, partial1[j+1][b] = w . w)
+//   phase 2 (second pass: always, or if needed when the first pass would remove more than
+//            half of ||w||^2): h1 = sum_b partial1 (same sums in every block); w -= V h1;
 //            partial2[i][b] = V_i . w, partial2[j+1][b] = w . w
-//   phase 3: h2 = sum_b partial2; H[:, j] += h2; w -= V h2 and, with s1 = ||w||^2 before
-//            this update, ||w||^2 = s1 - ||h2||^2 (Pythagoras: w - V h2 is orthogonal to
-//            V h2 up to rounding) -- unless that removes more than half of s1, when the
-//            norm is summed directly after one more barrier; then v_{j+1}, z, Givens.
-// The passes read V as the separate kernels do (4 (j+1) N values); w does not go back to
-// global memory.  All blocks take the same branches (their sums are identical).
+//   phase 3: h2 = sum_b partial2 (with one pass: h2 = h1, and the h1 of phase 2 taken as 0);
+//            H[:, j] = h1 + h2; w -= V h2 and, with s1 = ||w||^2 before this update,
+//            ||w||^2 = s1 - ||h2||^2 (Pythagoras: w - V h2 is orthogonal to V h2 up to
+//            rounding and the basis's loss of orthogonality) -- unless that removes more than
+//            half of s1, when the norm is summed directly after one more barrier; then
+//            v_{j+1}, z, Givens.
+// The passes read V as the separate kernels do (2 or 4 (j+1) N values); w does not go back
+// to global memory.  All blocks take the same branches (their sums are identical).
 __global__ void __launch_bounds__(GS_THREADS) k_gs_fused(const double *__restrict__ Vb, int64_t ld, int j,
                                                          const double *__restrict__ w, const double *__restrict__ dinv,
                                                          double *__restrict__ z, double *__restrict__ P1,
                                                          double *__restrict__ P2, int64_t N, int per, double *__restrict__ gm,
-                                                         int m, double tol, unsigned *bar) {
+                                                         int m, double tol, unsigned *bar, int refine) {
   extern __shared__ double fs_sm[];
   // the operator product that follows may start launching its blocks now; they wait for
   // this grid's end before reading (griddepcontrol.wait in k_spmv_fixed)
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int jp1 = j + 1;
   double *ws = fs_sm;                  // [per]
-  double *hs = ws + per;               // [m + 2]: h1, then h1 + h2
+  double *hs = ws + per;               // [m + 2]: h1 (0 with one pass)
   double *h2 = hs + (m + 2);           // [m + 2]: h2 and s1
   double *dp = h2 + (m + 2);           // [GS_THREADS / 32]
   double *cs_s = dp + GS_THREADS / 32; // [m]
@@ -680,23 +707,56 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_fused(const double *__restric
   const int T = blockDim.x;
   const int64_t a = (int64_t)blockIdx.x * per;
   const int cnt = (int)max((int64_t)0, min((int64_t)per, N - a));
+  bool twice = refine == IGA_CGS_REFINE_ALWAYS;
+  // the partials of the direct norm: a buffer that no block still reads
+  double *Pd = P2;
   // phase 1
-  for (int r = threadIdx.x; r < cnt; r += T) ws[r] = w[a + r];
+  if (twice) {
+    for (int r = threadIdx.x; r < cnt; r += T) ws[r] = w[a + r];
+  } else {
+    double sq = 0.0;
+    for (int r = threadIdx.x; r < cnt; r += T) {
+      const double v = w[a + r];
+      ws[r] = v;
+      sq = fma(v, v, sq);
+    }
+    sq = block_sum(sq, sh);
+    if (threadIdx.x == 0) P1[(size_t)jp1 * gridDim.x + blockIdx.x] = sq;
+  }
   __syncthreads();
   block_dots(Vb, ld, jp1, a, cnt, ws, dp, P1);
   if (!gs_grid_sync(bar)) goto timeout;
   // phase 2
-  block_sum_cols(P1, gridDim.x, jp1, hs);
-  {
-    double sq = gs_update_rows(Vb, ld, jp1, a, cnt, hs, ws, threadIdx.x, T);
-    sq = block_sum(sq, sh);
-    if (threadIdx.x == 0) P2[(size_t)jp1 * gridDim.x + blockIdx.x] = sq;
+  if (!twice) {
+    block_sum_cols(P1, gridDim.x, jp1 + 1, h2);  // h1 and s1 = ||w||^2
+    if (refine == IGA_CGS_REFINE_IFNEEDED) {
+      if (threadIdx.x < 32) {
+        double t = 0.0;
+        for (int i = threadIdx.x; i < jp1; i += 32) t = fma(h2[i], h2[i], t);
+        t = warp_sum(t);
+        if (threadIdx.x == 0) sc[3] = (h2[jp1] - t > 0.5 * h2[jp1]) ? 0.0 : 1.0;
+      }
+      __syncthreads();
+      twice = sc[3] != 0.0;
+    }
+    for (int i = threadIdx.x; i < jp1; i += T) hs[i] = twice ? h2[i] : 0.0;
+    __syncthreads();
+  } else {
+    block_sum_cols(P1, gridDim.x, jp1, hs);
   }
-  __syncthreads();
-  block_dots(Vb, ld, jp1, a, cnt, ws, dp, P2);
-  if (!gs_grid_sync(bar)) goto timeout;
+  if (twice) {
+    Pd = P1;
+    {
+      double sq = gs_update_rows(Vb, ld, jp1, a, cnt, hs, ws, threadIdx.x, T);
+      sq = block_sum(sq, sh);
+      if (threadIdx.x == 0) P2[(size_t)jp1 * gridDim.x + blockIdx.x] = sq;
+    }
+    __syncthreads();
+    block_dots(Vb, ld, jp1, a, cnt, ws, dp, P2);
+    if (!gs_grid_sync(bar)) goto timeout;
+    block_sum_cols(P2, gridDim.x, jp1 + 1, h2);
+  }
   // phase 3
-  block_sum_cols(P2, gridDim.x, jp1 + 1, h2);
   {
     // the block's scalars once, by warp 0 (fixed order), not by every thread: on GB300 a
     // FP64 instruction costs the narrow pipe the same for one active lane as for 32
@@ -719,39 +779,37 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_fused(const double *__restric
     const bool direct = sc[1] != 0.0;
     double *vnext = const_cast<double *>(Vb) + (size_t)jp1 * ld;
     // rows of this block's update and normalisation: every thread, except in block 0, whose
-    // warp 0 assembles the new column of H and runs the Givens step (thread 0, a serial
-    // chain of dependent FP64 operations) while warps 1.. update and normalise the rows
+    // warp 0 assembles the new column of H and applies the previous rotations to it (thread
+    // 0, a serial chain of dependent FP64 operations) while warps 1.. update the rows; the
+    // new rotation follows at once when ||w|| is known, else after the direct norm
     int r0 = threadIdx.x, rs = T;
-    auto givens_block0 = [&]() {
-      double *Hj = gm + L.H + (size_t)j * (m + 1);
-      for (int i = threadIdx.x; i < jp1; i += 32) {
-        Hs[i] = hs[i] + h2[i];
-        Hj[i] = Hs[i];
+    double gt = 0.0, gj = 0.0;  // thread 0 of block 0: the rotated last component and g[j]
+    if (blockIdx.x == 0) {
+      if (threadIdx.x < 32) {
+        if (threadIdx.x == 0) gj = gm[L.g + j];
+        for (int i = threadIdx.x; i < jp1; i += 32) Hs[i] = hs[i] + h2[i];
+        for (int i = threadIdx.x; i < j; i += 32) {
+          cs_s[i] = gm[L.cs + i];
+          sn_s[i] = gm[L.sn + i];
+        }
+        __syncwarp();
+        if (threadIdx.x == 0) {
+          gt = givens_apply_prev(Hs, cs_s, sn_s, j);
+          if (!direct) givens_new(Hs, gt, fmax(s2, 0.0), gj, gm, m, j, tol);
+        }
       }
-      for (int i = threadIdx.x; i < j; i += 32) {
-        cs_s[i] = gm[L.cs + i];
-        sn_s[i] = gm[L.sn + i];
-      }
-      __syncwarp();
-      if (threadIdx.x == 0) {
-        Hs[jp1] = fmax(s2, 0.0);
-        givens_step_sm(Hs, cs_s, sn_s, gm, m, j, tol);
-      }
-    };
-    if (blockIdx.x == 0 && !direct) {
-      if (threadIdx.x < 32) givens_block0();
       r0 = threadIdx.x - 32;
       rs = T - 32;
     }
     double sq = 0.0;
     if (r0 >= 0) sq = gs_update_rows(Vb, ld, jp1, a, cnt, h2, ws, r0, rs);
-    if (direct) {  // severe cancellation in the second pass: sum ||w||^2 itself (all threads updated)
+    if (direct) {  // severe cancellation: sum ||w||^2 itself
       sq = block_sum(sq, sh);
-      if (threadIdx.x == 0) P1[blockIdx.x] = sq;
+      if (threadIdx.x == 0) Pd[blockIdx.x] = sq;
       if (!gs_grid_sync(bar)) goto timeout;
       if (threadIdx.x < 32) {
         double acc = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) acc += P1[b];
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) acc += Pd[b];
         acc = warp_sum(acc);
         if (threadIdx.x == 0) {
           const double hn = sqrt(fmax(acc, 0.0));
@@ -761,11 +819,7 @@ __global__ void __launch_bounds__(GS_THREADS) k_gs_fused(const double *__restric
       }
       __syncthreads();
       s2 = sc[0];
-      if (blockIdx.x == 0) {
-        if (threadIdx.x < 32) givens_block0();
-        r0 = threadIdx.x - 32;
-        rs = T - 32;
-      }
+      if (blockIdx.x == 0 && threadIdx.x == 0) givens_new(Hs, gt, fmax(s2, 0.0), gj, gm, m, j, tol);
     }
     const double inv = sc[2];
     // a thread normalises the rows it updated (the same r0, rs), so no barrier between
@@ -1095,7 +1149,7 @@ static void jacobi_scaling(iga_s *h, const void *vals, int kind, double *dinv) {
 }
 
 int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double *x, double tol_abs, int m, int maxit,
-                int *its, cudaError_t *cerr) {
+                int refine, int *its, cudaError_t *cerr) {
   const int64_t N = h->N, ld = N;
   GmLayout L = gm_layout(m);
   double *gm = h->ctl;
@@ -1119,7 +1173,7 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
   // can be resident at once (one 1024-thread block per SM), else the four kernels
   const size_t fsmem = (size_t)(gs.per + 3 * (m + 2) + GS_THREADS / 32 + 2 * m) * sizeof(double);
   bool fused = false;
-  if (h->gsbar && fsmem <= 227 * 1024) {
+  if (h->gsbar && !h->gs_unfused && fsmem <= 227 * 1024) {
     int dev = 0, coop = 0, nsm = 0, per_sm = 0;
     if (fsmem > 48 * 1024) cudaFuncSetAttribute(k_gs_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
     if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess &&
@@ -1150,7 +1204,7 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
         const double *done = gm + L.flags;
         double *Hj = gm + L.H + (size_t)j * (m + 1);
         apply_op(h, vals, is_f32, z, w, done);
-        // classical Gram-Schmidt, applied twice (three passes), then norm + Givens + next vector
+        // classical Gram-Schmidt, once or twice, then norm + Givens + next vector
         const int jp1 = j + 1;
         const size_t smem = (size_t)(gs.per + jp1 + GS_THREADS / 32) * sizeof(double);
         double *P1 = h->red, *P2 = h->red + (size_t)(m + 1) * gs.nb, *P3 = h->red;
@@ -1161,17 +1215,25 @@ int gmres_solve(iga_s *h, const void *vals, int is_f32, const double *b, double 
           int64_t NN = N, ldd = ld;
           double tt = tol_abs;
           unsigned *bar = h->gsbar;
+          int rf = refine;
           void *args[] = {(void *)&Vc, (void *)&ldd, (void *)&jj, (void *)&wc, (void *)&dc, (void *)&z, (void *)&P1,
-                          (void *)&P2, (void *)&NN, (void *)&per, (void *)&gm, (void *)&mm, (void *)&tt, (void *)&bar};
+                          (void *)&P2, (void *)&NN, (void *)&per, (void *)&gm, (void *)&mm, (void *)&tt, (void *)&bar,
+                          (void *)&rf};
           cudaError_t le = cudaSuccess;
           IGA_LAUNCH(h, KC_ORTH, (le = cudaLaunchCooperativeKernel((const void *)k_gs_fused, dim3(gs.nb), dim3(GS_THREADS), args,
                                                                    fsmem, h->stream)));
           if (le != cudaSuccess) { *cerr = le; return -1; }
           continue;
         }
+        // unfused: IFNEEDED refines always (the test would need the sums on the host)
         IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<1><<<gs.nb, GS_THREADS, smem, h->stream>>>(Vb, ld, jp1, nullptr, Hj, w, P1, N, gs.per, done)));
-        IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<2><<<gs.nb, GS_THREADS, smem, h->stream>>>(Vb, ld, jp1, P1, Hj, w, P2, N, gs.per, done)));
-        IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<3><<<gs.nb, GS_THREADS, smem, h->stream>>>(Vb, ld, jp1, P2, Hj, w, P3, N, gs.per, done)));
+        if (refine == IGA_CGS_REFINE_NEVER) {  // the norm's partials in P2: P1 is still being read
+          P3 = P2;
+          IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<4><<<gs.nb, GS_THREADS, smem, h->stream>>>(Vb, ld, jp1, P1, Hj, w, P3, N, gs.per, done)));
+        } else {
+          IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<2><<<gs.nb, GS_THREADS, smem, h->stream>>>(Vb, ld, jp1, P1, Hj, w, P2, N, gs.per, done)));
+          IGA_LAUNCH(h, KC_ORTH, (k_gs_pass<3><<<gs.nb, GS_THREADS, smem, h->stream>>>(Vb, ld, jp1, P2, Hj, w, P3, N, gs.per, done)));
+        }
         IGA_LAUNCH(h, KC_VEC, (k_gs_finish<<<gs.nb, GS_THREADS, (size_t)(3 * m + 2) * sizeof(double), h->stream>>>(
                                   P3, gs.nb, w, Vb + (size_t)(j + 1) * ld, dinv, z, N, gs.per, gm, m, j, tol_abs)));
       }

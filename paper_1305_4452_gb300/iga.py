@@ -26,7 +26,8 @@ EXPORTS = ["iga_create", "iga_set_boundary_value", "iga_set_lambda", "iga_get_pa
            "iga_nn_forward", "iga_nn_loss_grad", "iga_nn_adam_step", "iga_nn_destroy", "iga_nn_last_error",
            "iga_nn_set_h1_weight", "iga_apply_jacobian", "iga_apply_jacobian_mf", "iga_form_jacobian_diagonal",
            "iga_form_residual_ts", "iga_form_jacobian_ts", "iga_ts_alpha_step", "iga_measure_peaks",
-           "iga_set_wait_limit", "iga_inject_stall", "iga_batch_set_tiles", "iga_exp_eval"]
+           "iga_set_wait_limit", "iga_inject_stall", "iga_batch_set_tiles", "iga_exp_eval",
+           "iga_set_gmres_fused"]
 
 KERNEL_CLASSES = ["geometry", "residual_element", "residual_gather", "q00", "jac_stage1", "jac_stage2", "jac_final",
                   "spmv", "gs_orth", "gmres_scalar", "vector", "combine", "pattern", "elem_tc", "elem_gather",
@@ -62,10 +63,12 @@ class IgaNewtonOpts(ctypes.Structure):
         ("jac", ctypes.c_int),
         ("reuse_stiffness", ctypes.c_int),
         ("ksp", ctypes.c_int),
+        ("gmres_cgs_refine", ctypes.c_int),
     ]
 
 
 IGA_KSP_GMRES, IGA_KSP_CG = 0, 1
+IGA_CGS_REFINE_NEVER, IGA_CGS_REFINE_IFNEEDED, IGA_CGS_REFINE_ALWAYS = 0, 1, 2
 
 
 class IgaNewtonReport(ctypes.Structure):
@@ -131,6 +134,7 @@ def lib():
         L.iga_measure_peaks.argtypes = [vp, ctypes.POINTER(IgaPeaks)]
         L.iga_set_wait_limit.argtypes = [vp, ctypes.c_double]
         L.iga_inject_stall.argtypes = [vp]
+        L.iga_set_gmres_fused.argtypes = [vp, ctypes.c_int]
         L.iga_exp_eval.argtypes = [vp, vp, vp, ctypes.c_int64]
         _lib = L
     return _lib
@@ -256,6 +260,9 @@ class Discretization:
 
     def set_lambda(self, lam):
         _check(lib().iga_set_lambda(self.h, float(lam)), self.h)
+
+    def set_gmres_fused(self, fused):
+        _check(lib().iga_set_gmres_fused(self.h, int(fused)), self.h)
 
     def pattern(self):
         """Copy the device CSR pattern into torch tensors (rowptr int64, colidx int32)."""

@@ -66,6 +66,7 @@ def test_invalid_descriptions_rejected_before_any_device_work(lib, kwargs, needl
 def test_newton_defaults(lib):
     o = lib.newton_defaults()
     assert o.atol == 1e-10 and o.max_newton == 50 and o.gmres_restart > 0 and o.jac == lib.IGA_FP64
+    assert o.gmres_cgs_refine == lib.IGA_CGS_REFINE_NEVER
 
 
 @pytest.mark.parametrize("cin,hidden", [(4, 24), (17, 64), (4, 128), (0, 32)])
@@ -90,7 +91,7 @@ def test_struct_layouts_match_the_header(tmp_path):
                                    "periodic"]),
         "iga_bratu": (iga.IgaBratu, [("lam", "lambda"), "log_kappa"]),
         "iga_newton_opts": (iga.IgaNewtonOpts, ["atol", "max_newton", "gmres_restart", "max_krylov", "krylov_rtol", "jac",
-                                                "reuse_stiffness", "ksp"]),
+                                                "reuse_stiffness", "ksp", "gmres_cgs_refine"]),
         "iga_newton_report": (iga.IgaNewtonReport, ["newton_its", "krylov_its", "fnorm0", "fnorm", "fnorm_hist", "status"]),
         "iga_ts_opts": (iga.IgaTsOpts, ["dt", "rho_inf"]),
         "iga_batch_report": (iga.IgaBatchReport, ["solved", "newton_its", "krylov_its", "fnorm", "status", "solve_us"]),
