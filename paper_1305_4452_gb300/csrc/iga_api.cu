@@ -164,6 +164,7 @@ iga_status iga_create_impl(iga_s *h, const iga_desc *d, const iga_bratu *b) {
     return IGA_EINVAL;
   }
   CK(ge);
+  if (h->has_geom || h->has_w) CK(classify_stiffness_plan(h));
   CK(cudaMalloc((void **)&h->Fe, (size_t)h->nelem * nen * sizeof(double)));
   CK(cudaMalloc((void **)&h->Q00, (size_t)h->nelem * nq * sizeof(double)));
   // stage intermediates (sized for FP64)

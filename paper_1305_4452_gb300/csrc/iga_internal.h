@@ -38,6 +38,8 @@ struct GeomLayout {
 };
 
 GeomLayout geom_layout(int dim);
+struct iga_s;
+cudaError_t classify_stiffness_plan(iga_s *h);
 
 // FP32 copy of the geometry factors for the reduced-precision Jacobians (iga_s::geom32,
 // [e][slot][qp]): invW, gSg, jwW2, S (ns), nSg (dim)
@@ -167,6 +169,11 @@ struct iga_s {
   double *noalloc_scratch = nullptr;  // device address of the allocation-free residual's array
   double lambda = 0.0;
   bool has_geom = false, has_w = false, has_kappa = false;
+  // stiffness plan of a mapped or rational geometry (classify_stiffness_plan): S diagonal at
+  // every Gauss point (an orthogonal parametrisation, such as the annulus), and which
+  // weight-gradient terms (S g)_a are nonzero (bit a)
+  bool plan_diag_s = false;
+  int plan_gmask = 7;
   BndArgs bnd{};
   GeomLayout gl{};
   std::string err;

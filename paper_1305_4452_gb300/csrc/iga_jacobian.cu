@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstring>
 #include <stdint.h>
 
 #include "iga_internal.h"
@@ -26,7 +28,7 @@ namespace {
 
 template <int DIM> __host__ __device__ constexpr int ipow(int b) { return DIM == 2 ? b * b : b * b * b; }
 
-enum { PLAN_STIFF = 0, PLAN_MASS = 1, PLAN_DIAG = 2 };
+enum { PLAN_STIFF = 0, PLAN_MASS = 1, PLAN_DIAG = 2, PLAN_DIAGS = 3 };
 
 struct CsrArgs {
   const int64_t *rowptr;
@@ -60,13 +62,19 @@ template <int PLAN, int DIM> struct Shape {
 // of the per-pair contraction: the same factors in the same order.
 // PLAN_DIAG (identity map, unit weights: g = 0 and S diagonal, so Q_0a and S_ab,
 // a != b, vanish): G0, G2, G5 only (2D: G0, G2), from Q00 and the three diagonal S.
+// PLAN_DIAGS (S diagonal at every Gauss point -- an orthogonal parametrisation such as the
+// annulus, whose radial and angular directions are perpendicular and whose height is
+// separate -- with rational weights): S_ab, a != b, vanish, so G4 vanishes and G1, G3 reduce
+// to the weight-gradient terms B_i B_j (S g)_a, which do not change when the pair is
+// transposed; gmask bit a says whether (S g)_a is nonzero (the others are skipped).
 // The reaction-only plan has one contraction per output, so a CTA takes
 // STAGE1_MASS_LINES consecutive axis-1 lines to give its threads enough work.
 constexpr int STAGE1_MASS_LINES = 8;
 
 template <typename T, int DIM, int P, int PLAN>
 __global__ void __launch_bounds__(256) k_stage1(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ geom,
-                                                const double *__restrict__ Q00, GeomLayout gl, T *__restrict__ out) {
+                                                const double *__restrict__ Q00, GeomLayout gl, T *__restrict__ out,
+                                                int gmask) {
   const T *tab = ptab<T>(d0);
   // FP64: DFMA-bound, so warps get pairs of equal overlap length; FP32: bound by memory
   // traffic, so pairs stay in pair order (neighbouring stores)
@@ -145,6 +153,18 @@ __global__ void __launch_bounds__(256) k_stage1(DirArgs d0, DirArgs d1, DirArgs 
         a0 = fma(p11, L[1 * X0 + k], a0);
         a2 = fma(p00, L[2 * X0 + k], a2);
         if (DIM == 3) a5 = fma(p00, L[3 * X0 + k], a5);
+      } else if (PLAN == PLAN_DIAGS) {
+        // the STIFF terms less those of the off-diagonal S (and of zero (S g)_a), in the
+        // same order
+        a0 = fma(p00, L[k], a0);
+        if (gmask & 1) a0 = fma(pv[IGA_PVS * k + 4], L[(DIM == 3 ? 7 : 4) * X0 + k], a0);
+        a0 = fma(p11, L[1 * X0 + k], a0);
+        if (gmask & 2) a1 = fma(p00, L[(DIM == 3 ? 8 : 5) * X0 + k], a1);
+        a2 = fma(p00, L[2 * X0 + k], a2);
+        if (DIM == 3) {
+          if (gmask & 4) a3 = fma(p00, L[9 * X0 + k], a3);
+          a5 = fma(p00, L[3 * X0 + k], a5);
+        }
       } else {
         const T p10 = pv[IGA_PVS * k + 1], p01 = pv[IGA_PVS * k + 2], psym = pv[IGA_PVS * k + 4];
         if (DIM == 3) {
@@ -183,12 +203,14 @@ __global__ void __launch_bounds__(256) k_stage1(DirArgs d0, DirArgs d1, DirArgs 
       o[0] = a0;
       o[2 * plane] = a2;
       if (PLAN == PLAN_STIFF) o[plane] = t ? b1 : a1;
+      if (PLAN == PLAN_DIAGS && (gmask & 2)) o[plane] = a1;
       if (DIM == 3) {
         o[5 * plane] = a5;
         if (PLAN == PLAN_STIFF) {
           o[3 * plane] = t ? b3 : a3;
           o[4 * plane] = a4;
         }
+        if (PLAN == PLAN_DIAGS && (gmask & 4)) o[3 * plane] = a3;
       }
     }
   }
@@ -201,9 +223,12 @@ __global__ void __launch_bounds__(256) k_stage1(DirArgs d0, DirArgs d1, DirArgs 
 // H0 and H2 are unchanged when both pairs are transposed, so they are formed only
 // for pi1 <= pi1T; the final stage reads them at (pi1T, pi0T) otherwise.
 // PLAN_DIAG: H0 = P^00 G0 + P^11 G2, H2 = P^00 G5 (G1, G3, G4 and so H1 vanish).
+// PLAN_DIAGS: G1 and G3 are transpose-invariant and G4 = 0, so
+//   H0 = P^00 G0 + (P^10 + P^01) G1 + P^11 G2, H1 = P^00 G3, H2 = P^00 G5,
+// with the G1 term only when (S g)_1 is nonzero and H1 only when (S g)_2 is (gmask).
 template <typename T, int PLAN>
 __global__ void __launch_bounds__(128, 6) k_stage2(DirArgs d0, DirArgs d1, DirArgs d2, const T *__restrict__ in,
-                                                T *__restrict__ out, int chunk) {
+                                                T *__restrict__ out, int chunk, int gmask) {
   const int pi0 = blockIdx.x * blockDim.x + threadIdx.x;
   const int x2 = blockIdx.z;
   const int pa = blockIdx.y * chunk, pb = min(pa + chunk, d1.np);
@@ -214,7 +239,9 @@ __global__ void __launch_bounds__(128, 6) k_stage2(DirArgs d0, DirArgs d1, DirAr
   const T *tab = ptab<T>(d1);
   for (int pi1 = pa; pi1 < pb; pi1++) {
     const bool sym = pi1 <= d1.pair_T[pi1];  // uniform across the block
-    if (PLAN != PLAN_STIFF && !sym) continue;
+    // a non-canonical pair has only H1 to form
+    const bool h1_on = PLAN == PLAN_STIFF || (PLAN == PLAN_DIAGS && (gmask & 4));
+    if (!sym && !h1_on) continue;
     const int xs = d1.pair_x0[pi1], np = d1.pair_np[pi1];
     const T *pv = tab + (size_t)d1.pair_po[pi1] * IGA_PVS;
     T h0 = 0, h1 = 0, h2 = 0;
@@ -230,6 +257,14 @@ __global__ void __launch_bounds__(128, 6) k_stage2(DirArgs d0, DirArgs d1, DirAr
         h0 = fma(p00, g[0], h0);
         h0 = fma(pv[IGA_PVS * k + 3], g[2 * inplane], h0);
         h2 = fma(p00, g[5 * inplane], h2);
+      } else if (PLAN == PLAN_DIAGS) {
+        if (sym) {
+          h0 = fma(p00, g[0], h0);
+          if (gmask & 2) h0 = fma(pv[IGA_PVS * k + 4], g[inplane], h0);
+          h0 = fma(pv[IGA_PVS * k + 3], g[2 * inplane], h0);
+          h2 = fma(p00, g[5 * inplane], h2);
+        }
+        if (gmask & 4) h1 = fma(p00, g[3 * inplane], h1);
       } else {
         const T p01 = pv[IGA_PVS * k + 2];
         if (sym) {
@@ -246,7 +281,7 @@ __global__ void __launch_bounds__(128, 6) k_stage2(DirArgs d0, DirArgs d1, DirAr
     }
     T *o = out + ((size_t)x2 * d1.np + pi1) * d0.np + pi0;
     if (sym) o[0] = h0;
-    if (PLAN == PLAN_STIFF) o[outplane] = h1;
+    if (h1_on) o[outplane] = h1;
     if (PLAN != PLAN_MASS && sym) o[2 * outplane] = h2;
   }
 }
@@ -410,7 +445,7 @@ cudaError_t run_stage1(iga_s *h, T *T1) {
   IGA_LAUNCH(h, KC_STAGE1, DISPATCH_P(h->p, ({
     auto kern = k_stage1<T, DIM, PP, PLAN>;
     if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    kern<<<grid, 256, sm, h->stream>>>(a0, a1, a2, h->geom, h->Q00, h->gl, T1);
+    kern<<<grid, 256, sm, h->stream>>>(a0, a1, a2, h->geom, h->Q00, h->gl, T1, h->plan_gmask);
   })));
   return cudaGetLastError();
 }
@@ -423,14 +458,25 @@ cudaError_t run_stages(iga_s *h, V *vals, const V *base, int fix) {
   if (ce) return ce;
   CsrArgs csr{h->rowptr, h->rp_line, h->rp_p0, h->weights, h->bnd};
   const int chunk = 8, fchunk = FINAL_CHUNK;  // stage-2 pairs per block; final-stage canonical pairs per block
+  // the final stage of PLAN_DIAGS is that of PLAN_DIAG when the last axis's weight-gradient
+  // term vanishes (no H1; 2D: no G1) and that of PLAN_STIFF otherwise (its H1 and H1^T
+  // reads find the transpose-invariant values at both pairs)
+  const bool diag_final = PLAN == PLAN_DIAGS && !((h->plan_gmask >> (DIM - 1)) & 1);
+  constexpr int FPLAN = PLAN == PLAN_DIAGS ? PLAN_STIFF : PLAN;
   if (DIM == 3) {
     dim3 g2((a0.np + 127) / 128, (a1.np + chunk - 1) / chunk, a2.X);
-    IGA_LAUNCH(h, KC_STAGE2, (k_stage2<T, PLAN><<<g2, 128, 0, h->stream>>>(a0, a1, a2, T1, T2, chunk)));
+    IGA_LAUNCH(h, KC_STAGE2, (k_stage2<T, PLAN><<<g2, 128, 0, h->stream>>>(a0, a1, a2, T1, T2, chunk, h->plan_gmask)));
     dim3 g3((a0.np + 127) / 128, (a2.nc + fchunk - 1) / fchunk, a1.np);
-    IGA_LAUNCH(h, KC_FINAL, (k_final<T, V, 3, PLAN><<<g3, 128, 0, h->stream>>>(a0, a1, a2, T2, csr, vals, base, fchunk, fix)));
+    if (diag_final)
+      IGA_LAUNCH(h, KC_FINAL, (k_final<T, V, 3, PLAN_DIAG><<<g3, 128, 0, h->stream>>>(a0, a1, a2, T2, csr, vals, base, fchunk, fix)));
+    else
+      IGA_LAUNCH(h, KC_FINAL, (k_final<T, V, 3, FPLAN><<<g3, 128, 0, h->stream>>>(a0, a1, a2, T2, csr, vals, base, fchunk, fix)));
   } else {
     dim3 g3((a0.np + 127) / 128, (a1.nc + fchunk - 1) / fchunk, 1);
-    IGA_LAUNCH(h, KC_FINAL, (k_final<T, V, 2, PLAN><<<g3, 128, 0, h->stream>>>(a0, a1, a2, T1, csr, vals, base, fchunk, fix)));
+    if (diag_final)
+      IGA_LAUNCH(h, KC_FINAL, (k_final<T, V, 2, PLAN_DIAG><<<g3, 128, 0, h->stream>>>(a0, a1, a2, T1, csr, vals, base, fchunk, fix)));
+    else
+      IGA_LAUNCH(h, KC_FINAL, (k_final<T, V, 2, FPLAN><<<g3, 128, 0, h->stream>>>(a0, a1, a2, T1, csr, vals, base, fchunk, fix)));
   }
   return cudaGetLastError();
 }
@@ -456,10 +502,92 @@ cudaError_t jacobian(iga_s *h, const double *U, V *vals, int mode, const V *base
   // identity map with unit weights: the geometry factors are g = 0 and a diagonal S
   if (!h->has_geom && !h->has_w)
     return h->dim == 3 ? run_stages<T, V, 3, PLAN_DIAG>(h, vals, nullptr, fix) : run_stages<T, V, 2, PLAN_DIAG>(h, vals, nullptr, fix);
+  // a diagonal S at every Gauss point (classify_stiffness_plan)
+  if (h->plan_diag_s)
+    return h->dim == 3 ? run_stages<T, V, 3, PLAN_DIAGS>(h, vals, nullptr, fix) : run_stages<T, V, 2, PLAN_DIAGS>(h, vals, nullptr, fix);
   return h->dim == 3 ? run_stages<T, V, 3, PLAN_STIFF>(h, vals, nullptr, fix) : run_stages<T, V, 2, PLAN_STIFF>(h, vals, nullptr, fix);
 }
 
 }  // namespace
+
+namespace {
+// max |f| over every element and Gauss point for the fields S_ab and (S g)_a of the
+// geometry cache: out[i] for field i of fld (as the bits of a non-negative double, whose
+// integer order is the numeric one)
+constexpr int CLS_MAXF = 9;
+__global__ void __launch_bounds__(256) k_geom_absmax(const double *__restrict__ geom, int nf, int nq, int64_t nelem,
+                                                     const int *__restrict__ fld, int nfld,
+                                                     unsigned long long *__restrict__ out) {
+  __shared__ unsigned long long m_s[CLS_MAXF];
+  if (threadIdx.x < CLS_MAXF) m_s[threadIdx.x] = 0ull;
+  __syncthreads();
+  double m[CLS_MAXF];
+  for (int i = 0; i < CLS_MAXF; i++) m[i] = 0.0;
+  const int64_t tot = nelem * nq;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = t / nq;
+    const int qp = (int)(t - e * nq);
+    const double *rec = geom + (size_t)e * nf * nq + qp;
+    for (int i = 0; i < nfld; i++) m[i] = fmax(m[i], fabs(rec[(size_t)fld[i] * nq]));
+  }
+  for (int i = 0; i < nfld; i++) atomicMax(&m_s[i], (unsigned long long)__double_as_longlong(m[i]));
+  __syncthreads();
+  if (threadIdx.x < nfld) atomicMax(&out[threadIdx.x], m_s[threadIdx.x]);
+}
+}  // namespace
+
+// The stiffness plan of a mapped or rational geometry, from the geometry cache: S is
+// taken as diagonal when every off-diagonal S_ab is below 5e-13 times the largest |S_aa|,
+// and (S g)_a as zero when it is below 5e-13 times the largest |S_bb| and |(S g)_b|.  An
+// orthogonal parametrisation (the annulus: radial and angular directions perpendicular,
+// the height separate, the weights a function of the angle alone) has these terms zero
+// in exact arithmetic and at rounding level in the cache: the map's derivatives are sums
+// of B-spline derivatives of size p/h that cancel, so the level grows with refinement
+// (64^3 cubic annulus: off-diagonal S at 1.6e-13 of the diagonal, (S g)_0 and (S g)_2 at
+// 1e-14 and 6e-14; 8^3: 1.5e-14).  Dropping terms of that relative size changes the
+// Jacobian by a comparable fraction of its largest entry, below its 1e-12 FP64 parity
+// tolerance; the terms the exact map has are kept.  Synchronises the stream.
+cudaError_t classify_stiffness_plan(iga_s *h) {
+  const int dim = h->dim, ns = dim * (dim + 1) / 2;
+  const int nq = dim == 3 ? h->q * h->q * h->q : h->q * h->q;
+  int fld[CLS_MAXF], nfld = 0;
+  for (int i = 0; i < ns; i++) fld[nfld++] = h->gl.S + i;  // diagonal first, then S01 (, S02, S12)
+  for (int a = 0; a < dim; a++) fld[nfld++] = h->gl.Sg + a;
+  int *fld_d = nullptr;
+  unsigned long long *out_d = nullptr;
+  cudaError_t ce = cudaMalloc((void **)&fld_d, sizeof(fld));
+  if (!ce) ce = cudaMalloc((void **)&out_d, CLS_MAXF * sizeof(unsigned long long));
+  if (!ce) ce = cudaMemcpyAsync(fld_d, fld, sizeof(fld), cudaMemcpyHostToDevice, h->stream);
+  if (!ce) ce = cudaMemsetAsync(out_d, 0, CLS_MAXF * sizeof(unsigned long long), h->stream);
+  unsigned long long m[CLS_MAXF] = {0};
+  if (!ce) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (h->nelem * nq + 255) / 256;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)(sms > 0 ? sms : 1) * 4));
+    k_geom_absmax<<<grid, 256, 0, h->stream>>>(h->geom, h->gl.nf, nq, h->nelem, fld_d, nfld, out_d);
+    ce = cudaGetLastError();
+  }
+  if (!ce) ce = cudaMemcpyAsync(m, out_d, sizeof(m), cudaMemcpyDeviceToHost, h->stream);
+  if (!ce) ce = cudaStreamSynchronize(h->stream);
+  if (fld_d) cudaFree(fld_d);
+  if (out_d) cudaFree(out_d);
+  if (ce) return ce;
+  double v[CLS_MAXF];
+  for (int i = 0; i < nfld; i++) memcpy(&v[i], &m[i], sizeof(double));
+  double sdiag = 0.0, sg = 0.0, soff = 0.0;
+  for (int i = 0; i < dim; i++) sdiag = std::max(sdiag, v[i]);
+  for (int i = dim; i < ns; i++) soff = std::max(soff, v[i]);
+  for (int a = 0; a < dim; a++) sg = std::max(sg, v[ns + a]);
+  const double tau = 5e-13;
+  h->plan_diag_s = std::isfinite(sdiag) && sdiag > 0.0 && soff <= tau * sdiag;
+  const double gscale = std::max(sdiag, sg);
+  h->plan_gmask = 0;
+  for (int a = 0; a < dim; a++)
+    if (!(v[ns + a] <= tau * gscale)) h->plan_gmask |= 1 << a;
+  return cudaSuccess;
+}
 
 size_t jacobian_t1_groups(int dim) { return dim == 3 ? 6 : 3; }
 size_t jacobian_t2_groups(int dim) { return dim == 3 ? 3 : 0; }
