@@ -123,6 +123,27 @@ def bratu16(torch, iga, W, clock):
         t = time.perf_counter()
         rep = d.solve_newton(Us, o)
         times.append(time.perf_counter() - t)
+    # the same problem as a one-instance batch: the persistent solver runs the whole Newton
+    # solve in one graph-captured launch (FP64 residual, FP32 Jacobian), so the 16x16 solve
+    # is no longer bound by launch latency and host synchronisations
+    B = iga.Batch([{"nel": 16, "p": 2, "lam": 1.0}])
+    Ub = torch.empty(B.total, dtype=torch.float64, device="cuda")
+    btimes, brep = [], None
+    for _ in range(23):
+        Ub.copy_(U)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        brep = B.solve(Ub)
+        btimes.append(time.perf_counter() - t0)
+    btimes = btimes[3:]
+    Us = U.clone()
+    d.solve_newton(Us, o)
+    batch1 = {"solves_per_s": 1.0 / min(btimes), "ms_per_solve": 1e3 * min(btimes),
+              "ms_median": 1e3 * float(np.median(btimes)), "newton_its": int(brep["newton_its"][0]),
+              "krylov_its": int(brep["krylov_its"][0]), "fnorm": float(brep["fnorm"][0]),
+              "max_abs_diff_vs_fp64_newton": (Ub - Us).abs().max().item(),
+              "how": "iga_batch_solve on one instance (wall time of the call, copy of the reports included)"}
+    B.close()
     ck = clock.stop()
     t = min(times)
     import oracle as O
@@ -135,7 +156,7 @@ def bratu16(torch, iga, W, clock):
     return _line(1.0 / t, "solves/s", "bratu2d_16x16_p2_lambda1_fp64", {
         "residual_us": tr * 1e3, "jacobian_us": tj * 1e3, "jacobian_nnz_per_s": d.nnz / (tj * 1e-3),
         "newton": {"its": rep.newton_its, "krylov_its": rep.krylov_its, "fnorm": rep.fnorm},
-        "ms_per_solve": t * 1e3, "dofs": d.N, "nnz": d.nnz, "cpu_baseline": cb}, ck)
+        "ms_per_solve": t * 1e3, "dofs": d.N, "nnz": d.nnz, "one_instance_batch": batch1, "cpu_baseline": cb}, ck)
 
 
 def cube_mixed(torch, iga, W, clock):
