@@ -76,9 +76,23 @@ static iga_status upload_dir(iga_s *h, int ax) {
   CK(upload(&d.pair_c, D.pair_c));
   CK(upload(&d.pair_cs, D.pair_cs));
   d.nc = (int)D.pair_c.size();
-  CK(upload(&d.pair_val, D.pair_val));
-  std::vector<float> pf(D.pair_val.begin(), D.pair_val.end());
-  CK(upload(&d.pair_val_f, pf));
+  if (h->w_folded) {
+    // the pair tables times w_ax[i] w_ax[j] (the axis's factor of w_A w_B)
+    std::vector<double> pv(D.pair_val);
+    const std::vector<double> &w = h->wsep[ax];
+    for (size_t k = 0; k < D.pair_i.size(); k++) {
+      const double f = w[D.pair_i[k]] * w[D.pair_j[k]];
+      double *v = pv.data() + (size_t)D.pair_po[k] * IGA_PVS;
+      for (int t = 0; t < D.pair_np[k] * IGA_PVS; t++) v[t] *= f;
+    }
+    CK(upload(&d.pair_val, pv));
+    std::vector<float> pf(pv.begin(), pv.end());
+    CK(upload(&d.pair_val_f, pf));
+  } else {
+    CK(upload(&d.pair_val, D.pair_val));
+    std::vector<float> pf(D.pair_val.begin(), D.pair_val.end());
+    CK(upload(&d.pair_val_f, pf));
+  }
   CK(upload(&d.node_e0, D.node_e0));
   CK(upload(&d.node_ne, D.node_ne));
   return IGA_OK;
@@ -115,6 +129,25 @@ iga_status iga_create_impl(iga_s *h, const iga_desc *d, const iga_bratu *b) {
         h->err = "log-kappa coefficients must be finite";
         return IGA_EINVAL;
       }
+  // weights that factor by axis (the annulus: a function of the angle alone), to within a
+  // few units of rounding: w0[i] = w(i, 0, 0), w_a[j] = w(0, .., j, .., 0) / w(0, 0, 0)
+  h->w_folded = false;
+  if (h->has_w && !h->unclamped) {
+    const int n0 = h->dir[0].n, n1 = h->dir[1].n, n2 = h->dim == 3 ? h->dir[2].n : 1;
+    const double *w = d->weights;
+    for (int a = 0; a < 3; a++) h->wsep[a].assign(a < h->dim ? h->dir[a].n : 1, 1.0);
+    for (int i = 0; i < n0; i++) h->wsep[0][i] = w[i];
+    for (int j = 0; j < n1; j++) h->wsep[1][j] = w[(int64_t)j * n0] / w[0];
+    if (h->dim == 3)
+      for (int k = 0; k < n2; k++) h->wsep[2][k] = w[(int64_t)k * n0 * n1] / w[0];
+    bool sep = true;
+    for (int64_t A = 0; A < N && sep; A++) {
+      const int i = (int)(A % n0), j = (int)((A / n0) % n1), k = (int)(A / ((int64_t)n0 * n1));
+      const double f = h->wsep[0][i] * h->wsep[1][j] * h->wsep[2][k];
+      sep = fabs(f - w[A]) <= 8.0 * 2.220446049250313e-16 * w[A];
+    }
+    h->w_folded = sep;
+  }
   for (int ax = 0; ax < 3; ax++) {
     st = upload_dir(h, ax);
     if (st != IGA_OK) return st;

@@ -174,6 +174,11 @@ struct iga_s {
   // weight-gradient terms (S g)_a are nonzero (bit a)
   bool plan_diag_s = false;
   int plan_gmask = 7;
+  // rational weights that factor by axis, w_A = w0[i0] w1[i1] w2[i2]: the products w_A w_B of
+  // the Jacobian are folded into the device pair tables (w_d[i] w_d[j] per pair) and the
+  // final stage multiplies by nothing
+  bool w_folded = false;
+  std::vector<double> wsep[3];
   BndArgs bnd{};
   GeomLayout gl{};
   std::string err;

@@ -456,7 +456,8 @@ cudaError_t run_stages(iga_s *h, V *vals, const V *base, int fix) {
   T *T1 = (T *)h->T1, *T2 = (T *)h->T2;
   cudaError_t ce = run_stage1<T, DIM, PLAN>(h, T1);
   if (ce) return ce;
-  CsrArgs csr{h->rowptr, h->rp_line, h->rp_p0, h->weights, h->bnd};
+  // weights folded into the pair tables: nothing left to multiply in the final stage
+  CsrArgs csr{h->rowptr, h->rp_line, h->rp_p0, h->w_folded ? nullptr : h->weights, h->bnd};
   const int chunk = 8, fchunk = FINAL_CHUNK;  // stage-2 pairs per block; final-stage canonical pairs per block
   // the final stage of PLAN_DIAGS is that of PLAN_DIAG when the last axis's weight-gradient
   // term vanishes (no H1; 2D: no G1) and that of PLAN_STIFF otherwise (its H1 and H1^T
