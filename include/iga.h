@@ -152,6 +152,13 @@ iga_status iga_inject_stall(iga_t iga);
  * up to the norm's summation order).  Other values: IGA_EINVAL. */
 iga_status iga_set_gmres_fused(iga_t iga, int fused);
 
+/* Plan of the sum-factorised stiffness (a library facility): general = 0 (default) lets
+ * create-time classification pick the diagonal-S plan where every off-diagonal S_ab of the
+ * geometry cache is below 5e-13 of the diagonal (an orthogonal parametrisation such as the
+ * annulus: those terms are zero in exact arithmetic); general = 1 always contracts every
+ * term.  Other values: IGA_EINVAL. */
+iga_status iga_set_jacobian_plan(iga_t iga, int general);
+
 /* Change lambda after creation (used by the batched and learned-start drivers). */
 iga_status iga_set_lambda(iga_t iga, double lambda);
 

@@ -280,6 +280,18 @@ extern "C" iga_status iga_inject_stall(iga_t h) {
   return IGA_OK;
 }
 
+extern "C" iga_status iga_set_jacobian_plan(iga_t h, int general) {
+  if (!h) return IGA_EINVAL;
+  if (general != 0 && general != 1) {
+    h->err = "general must be 0 or 1";
+    return IGA_EINVAL;
+  }
+  h->plan_general = general == 1;
+  h->K_valid = false;  // the kept stiffness was assembled under the other plan
+  h->K_valid_f = false;
+  return IGA_OK;
+}
+
 extern "C" iga_status iga_set_gmres_fused(iga_t h, int fused) {
   if (!h) return IGA_EINVAL;
   if (fused != 0 && fused != 1) {

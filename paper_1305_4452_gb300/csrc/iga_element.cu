@@ -35,48 +35,29 @@ template <int DIM> __host__ __device__ constexpr int ipow(int b) { return DIM ==
 
 // ---------------------------------------------------------------------------
 // Geometry factors (Sec. 2.3 Eqs. 6-7, drational; Appendix A Eqs. identity,
-// dspatial): one thread per (element, Gauss point).  Run once per iga_create.
+// dspatial).  Run once per iga_create.
+//
+// The rational map and its derivatives at a Gauss point are sums over the element's
+// (p+1)^DIM functions of w_a, w_a X_a (and w_a log kappa_a) times the tensor products of
+// the 1D values and first derivatives.  They are formed by sum factorisation, one axis
+// at a time, for NE elements per CTA in shared memory:
+//   axis 0:  S1[f][a2][a1][g0] = sum_a0 B0(g0, a0) C[f][a], and with B0' (2 results)
+//   axis 1:  from S1: B1 * S1_B, B1' * S1_B, B1 * S1_B'               (3 results)
+//   axis 2 (per point): V = B2 * S2_BB, D2 = B2' * S2_BB, D1 = B2 * S2_B'B, D0 = B2 * S2_BB'
+// (2D stops after axis 0 and contracts axis 1 per point) -- about 36 FMAs per field and
+// point at p = 3 instead of 30 per function and point; then geometry_point forms
+// F = dx/dxi (Eq. drational), its inverse and determinant and the cached factors.
 // ---------------------------------------------------------------------------
-template <int DIM, int P>
-__global__ void __launch_bounds__(128) k_geometry(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ ctrl,
-                                                  const double *__restrict__ wts, const double *__restrict__ logk,
-                                                  GeomLayout gl, double *__restrict__ geom, int64_t nelem,
-                                                  int *__restrict__ err) {
-  constexpr int N1 = P + 1, Q = P + 1, NQ = ipow<DIM>(Q), NEN = ipow<DIM>(N1);
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= nelem * NQ) return;
-  int64_t e = t / NQ;
-  int qp = (int)(t % NQ);
-  int g0 = qp % Q, g1 = (qp / Q) % Q, g2 = (DIM == 3) ? qp / (Q * Q) : 0;
-  int e0 = (int)(e % d0.nel), e1 = (int)((e / d0.nel) % d1.nel), e2 = (DIM == 3) ? (int)(e / ((int64_t)d0.nel * d1.nel)) : 0;
-  const double *T0 = d0.tab + ((size_t)e0 * Q + g0) * N1 * 2;
-  const double *T1 = d1.tab + ((size_t)e1 * Q + g1) * N1 * 2;
-  const double *T2 = (DIM == 3) ? d2.tab + ((size_t)e2 * Q + g2) * N1 * 2 : nullptr;
-  int f0 = d0.first[e0], f1 = d1.first[e1], f2 = (DIM == 3) ? d2.first[e2] : 0;
-  double W = 0.0, Wd[3] = {0.0, 0.0, 0.0}, Pc[3] = {0, 0, 0}, Pd[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, L = 0.0;
-  for (int a = 0; a < NEN; a++) {
-    int a0 = a % N1, a1 = (a / N1) % N1, a2 = (DIM == 3) ? a / (N1 * N1) : 0;
-    double b0 = T0[a0 * 2], db0 = T0[a0 * 2 + 1], b1 = T1[a1 * 2], db1 = T1[a1 * 2 + 1];
-    double b2 = (DIM == 3) ? T2[a2 * 2] : 1.0, db2 = (DIM == 3) ? T2[a2 * 2 + 1] : 0.0;
-    int64_t G = (f0 + a0) + (int64_t)d0.n * ((f1 + a1) + (int64_t)d1.n * (f2 + a2));
-    double M = b0 * b1 * b2;
-    double dM[3] = {db0 * b1 * b2, b0 * db1 * b2, b0 * b1 * db2};
-    double w = wts ? wts[G] : 1.0;
-    W += w * M;
-    for (int al = 0; al < DIM; al++) Wd[al] += w * dM[al];
-    if (ctrl)
-      for (int i = 0; i < DIM; i++) {
-        double xw = w * ctrl[G * DIM + i];
-        Pc[i] += xw * M;
-        for (int al = 0; al < DIM; al++) Pd[i][al] += xw * dM[al];
-      }
-    if (logk) L += w * logk[G] * M;
-  }
-  double invW = 1.0 / W;
+template <int DIM>
+__device__ __forceinline__ void geometry_point(const double *V, const double (*D)[3], bool has_ctrl, bool has_logk, double wq,
+                                               GeomLayout gl, double *rec, int NQ, int *__restrict__ err) {
+  // V[0] = W, V[1..DIM] = sum w X_i, V[DIM+1] = sum w log kappa; D[f][al] their derivatives
+  const double W = V[0];
+  const double invW = 1.0 / W;
   double F[3][3];
   for (int i = 0; i < DIM; i++)
     for (int al = 0; al < DIM; al++)
-      F[i][al] = ctrl ? (Pd[i][al] - Pc[i] * invW * Wd[al]) * invW : (i == al ? 1.0 : 0.0);
+      F[i][al] = has_ctrl ? (D[1 + i][al] - V[1 + i] * invW * D[0][al]) * invW : (i == al ? 1.0 : 0.0);
   double det, X[3][3];  // X[alpha][i] = xi_{alpha,i}
   if (DIM == 2) {
     det = F[0][0] * F[1][1] - F[0][1] * F[1][0];
@@ -98,10 +79,9 @@ __global__ void __launch_bounds__(128) k_geometry(DirArgs d0, DirArgs d1, DirArg
     X[2][2] = (F[0][0] * F[1][1] - F[0][1] * F[1][0]) * id;
   }
   if (!(det > 0.0)) atomicExch(err, 1);  // inverted or degenerate geometry (status only)
-  double wq = d0.wq[(size_t)e0 * Q + g0] * d1.wq[(size_t)e1 * Q + g1] * ((DIM == 3) ? d2.wq[(size_t)e2 * Q + g2] : 1.0);
   double jw = det * wq;
-  double kappa = logk ? exp(L * invW) : 1.0;
-  double g[3] = {Wd[0] * invW, Wd[1] * invW, Wd[2] * invW};
+  double kappa = has_logk ? exp(V[DIM + 1] * invW) : 1.0;
+  double g[3] = {D[0][0] * invW, D[0][1] * invW, DIM == 3 ? D[0][2] * invW : 0.0};
   double S[3][3];
   double sc = kappa * jw * invW * invW;
   for (int al = 0; al < DIM; al++)
@@ -110,7 +90,6 @@ __global__ void __launch_bounds__(128) k_geometry(DirArgs d0, DirArgs d1, DirArg
       for (int i = 0; i < DIM; i++) c += X[al][i] * X[be][i];
       S[al][be] = sc * c;
     }
-  double *rec = geom + (size_t)e * gl.nf * NQ + qp;
   rec[gl.invW * NQ] = invW;
   for (int al = 0; al < DIM; al++) rec[(gl.g + al) * NQ] = g[al];
   if (DIM == 2) {
@@ -129,6 +108,140 @@ __global__ void __launch_bounds__(128) k_geometry(DirArgs d0, DirArgs d1, DirArg
   }
   rec[gl.gSg * NQ] = gSg;
   rec[gl.jwW2 * NQ] = jw * invW * invW;
+}
+
+template <int DIM, int P> struct GeoSmem {
+  static constexpr int N1 = P + 1, Q = P + 1;
+  static constexpr int NEN = ipow<DIM>(N1), NQ = ipow<DIM>(Q);
+  static constexpr int NF = DIM + 2;  // w, w X_i, w log kappa
+  static constexpr int NE = NQ >= 128 ? 1 : 128 / NQ;
+  static constexpr int TAB = DIM * Q * N1 * 2;
+  static constexpr int C = NF * NEN;
+  static constexpr int S1 = NF * ipow<DIM>(N1) / N1 * Q * 2;               // [f][a2][a1][g0][2] (2D: [f][a1][g0][2])
+  static constexpr int S2 = DIM == 3 ? NF * N1 * Q * Q * 3 : 0;           // [f][a2][g1][g0][3]
+  static constexpr int PER = TAB + C + S1 + S2;
+};
+
+template <int DIM, int P>
+__global__ void __launch_bounds__(128) k_geometry(DirArgs d0, DirArgs d1, DirArgs d2, const double *__restrict__ ctrl,
+                                                  const double *__restrict__ wts, const double *__restrict__ logk,
+                                                  GeomLayout gl, double *__restrict__ geom, int64_t nelem,
+                                                  int *__restrict__ err) {
+  using SM = GeoSmem<DIM, P>;
+  constexpr int N1 = SM::N1, Q = SM::Q, NQ = SM::NQ, NEN = SM::NEN, NF = SM::NF, NE = SM::NE;
+  extern __shared__ double gsm[];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int64_t ebase = (int64_t)blockIdx.x * NE;
+  const bool has_ctrl = ctrl != nullptr, has_logk = logk != nullptr;
+  // tables and the weighted coefficients of the block's elements
+  for (int idx = tid; idx < NE * (SM::TAB + SM::C); idx += nt) {
+    const int le = idx / (SM::TAB + SM::C), k = idx % (SM::TAB + SM::C);
+    const int64_t e = ebase + le;
+    double *base = gsm + (size_t)le * SM::PER;
+    if (e >= nelem) { base[k] = 0.0; continue; }
+    const int e0 = (int)(e % d0.nel), e1 = (int)((e / d0.nel) % d1.nel), e2 = (DIM == 3) ? (int)(e / ((int64_t)d0.nel * d1.nel)) : 0;
+    if (k < SM::TAB) {
+      const int ax = k / (Q * N1 * 2), r = k % (Q * N1 * 2);
+      const DirArgs &d = ax == 0 ? d0 : (ax == 1 ? d1 : d2);
+      const int ee = ax == 0 ? e0 : (ax == 1 ? e1 : e2);
+      base[k] = d.tab[(size_t)ee * Q * N1 * 2 + r];
+    } else {
+      const int f = (k - SM::TAB) / NEN, a = (k - SM::TAB) % NEN;
+      const int a0 = a % N1, a1 = (a / N1) % N1, a2 = (DIM == 3) ? a / (N1 * N1) : 0;
+      const int64_t G = (d0.first[e0] + a0) + (int64_t)d0.n * ((d1.first[e1] + a1) + (int64_t)d1.n * ((DIM == 3 ? d2.first[e2] : 0) + a2));
+      const double w = wts ? wts[G] : 1.0;
+      double x = 0.0;
+      if (f == 0) x = w;
+      else if (f <= DIM) x = has_ctrl ? w * ctrl[G * DIM + (f - 1)] : 0.0;
+      else x = has_logk ? w * logk[G] : 0.0;
+      base[k] = x;
+    }
+  }
+  __syncthreads();
+#define GTB(base, ax, g, a, dv) (base)[(((ax) * Q + (g)) * N1 + (a)) * 2 + (dv)]
+  // axis 0: value and derivative of B0
+  constexpr int L1 = SM::S1 / (NF * Q * 2);  // lines (a2, a1) (2D: a1)
+  for (int idx = tid; idx < NE * NF * L1 * Q; idx += nt) {
+    const int le = idx / (NF * L1 * Q), r = idx % (NF * L1 * Q);
+    const int f = r / (L1 * Q), line = (r / Q) % L1, g0 = r % Q;
+    double *base = gsm + (size_t)le * SM::PER;
+    const double *C = base + SM::TAB + f * NEN + line * N1;
+    double v = 0.0, dv = 0.0;
+#pragma unroll
+    for (int a0 = 0; a0 < N1; a0++) {
+      v = fma(GTB(base, 0, g0, a0, 0), C[a0], v);
+      dv = fma(GTB(base, 0, g0, a0, 1), C[a0], dv);
+    }
+    double *o = base + SM::TAB + SM::C + ((size_t)(f * L1 + line) * Q + g0) * 2;
+    o[0] = v;
+    o[1] = dv;
+  }
+  __syncthreads();
+  if (DIM == 3) {
+    // axis 1: (B1, S1_B), (B1', S1_B), (B1, S1_B')
+    for (int idx = tid; idx < NE * NF * N1 * Q * Q; idx += nt) {
+      const int le = idx / (NF * N1 * Q * Q), r = idx % (NF * N1 * Q * Q);
+      const int f = r / (N1 * Q * Q), a2 = (r / (Q * Q)) % N1, g1 = (r / Q) % Q, g0 = r % Q;
+      double *base = gsm + (size_t)le * SM::PER;
+      const double *S1 = base + SM::TAB + SM::C + (size_t)f * L1 * Q * 2;
+      double bb = 0.0, db = 0.0, bd = 0.0;
+#pragma unroll
+      for (int a1 = 0; a1 < N1; a1++) {
+        const double *s = S1 + ((size_t)(a2 * N1 + a1) * Q + g0) * 2;
+        const double b1 = GTB(base, 1, g1, a1, 0), d1v = GTB(base, 1, g1, a1, 1);
+        bb = fma(b1, s[0], bb);
+        db = fma(d1v, s[0], db);
+        bd = fma(b1, s[1], bd);
+      }
+      double *o = base + SM::TAB + SM::C + SM::S1 + ((size_t)((f * N1 + a2) * Q + g1) * Q + g0) * 3;
+      o[0] = bb;
+      o[1] = db;
+      o[2] = bd;
+    }
+    __syncthreads();
+  }
+  // the last axis per point, then the factors
+  for (int idx = tid; idx < NE * NQ; idx += nt) {
+    const int le = idx / NQ, qp = idx % NQ;
+    const int64_t e = ebase + le;
+    if (e >= nelem) continue;
+    const double *base = gsm + (size_t)le * SM::PER;
+    const int g0 = qp % Q, g1 = (qp / Q) % Q, g2 = (DIM == 3) ? qp / (Q * Q) : 0;
+    double V[NF], D[NF][3];
+    for (int f = 0; f < NF; f++) {
+      double v = 0.0, dl = 0.0, dm = 0.0, dn = 0.0;
+      if (DIM == 3) {
+        const double *S2 = base + SM::TAB + SM::C + SM::S1;
+#pragma unroll
+        for (int a2 = 0; a2 < N1; a2++) {
+          const double *s = S2 + ((size_t)((f * N1 + a2) * Q + g1) * Q + g0) * 3;
+          const double b2 = GTB(base, 2, g2, a2, 0), d2v = GTB(base, 2, g2, a2, 1);
+          v = fma(b2, s[0], v);    // B0 B1 B2
+          dn = fma(d2v, s[0], dn); // B0 B1 B2'
+          dm = fma(b2, s[1], dm);  // B0 B1' B2
+          dl = fma(b2, s[2], dl);  // B0' B1 B2
+        }
+      } else {
+        const double *S1 = base + SM::TAB + SM::C + (size_t)f * L1 * Q * 2;
+#pragma unroll
+        for (int a1 = 0; a1 < N1; a1++) {
+          const double *s = S1 + ((size_t)a1 * Q + g0) * 2;
+          const double b1 = GTB(base, 1, g1, a1, 0), d1v = GTB(base, 1, g1, a1, 1);
+          v = fma(b1, s[0], v);
+          dm = fma(d1v, s[0], dm);
+          dl = fma(b1, s[1], dl);
+        }
+      }
+      V[f] = v;
+      D[f][0] = dl;
+      D[f][1] = dm;
+      D[f][2] = dn;
+    }
+#undef GTB
+    const int e0 = (int)(e % d0.nel), e1 = (int)((e / d0.nel) % d1.nel), e2 = (DIM == 3) ? (int)(e / ((int64_t)d0.nel * d1.nel)) : 0;
+    const double wq = d0.wq[(size_t)e0 * Q + g0] * d1.wq[(size_t)e1 * Q + g1] * ((DIM == 3) ? d2.wq[(size_t)e2 * Q + g2] : 1.0);
+    geometry_point<DIM>(V, D, has_ctrl, has_logk, wq, gl, geom + (size_t)e * gl.nf * NQ + qp, NQ, err);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -693,10 +806,13 @@ cudaError_t launch_geometry(iga_s *h, const double *ctrl_dev, const double *logk
   if (ce) return ce;
   cudaMemsetAsync(err, 0, sizeof(int), h->stream);
   DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
-  int NQ = (h->dim == 3) ? h->q * h->q * h->q : h->q * h->q;
-  int64_t tot = h->nelem * NQ;
-  unsigned grid = (unsigned)((tot + 127) / 128);
-  IGA_LAUNCH(h, KC_GEOM, DISPATCH_DP(h->dim, h->p, (k_geometry<D, PP><<<grid, 128, 0, h->stream>>>(a0, a1, a2, ctrl_dev, h->weights, logk_dev, h->gl, h->geom, h->nelem, err))));
+  IGA_LAUNCH(h, KC_GEOM, DISPATCH_DP(h->dim, h->p, ({
+    using GS = GeoSmem<D, PP>;
+    const size_t sm = (size_t)GS::NE * GS::PER * sizeof(double);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_geometry<D, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const unsigned grid = (unsigned)((h->nelem + GS::NE - 1) / GS::NE);
+    k_geometry<D, PP><<<grid, 128, sm, h->stream>>>(a0, a1, a2, ctrl_dev, h->weights, logk_dev, h->gl, h->geom, h->nelem, err);
+  })));
   int herr = 0;
   cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   ce = cudaStreamSynchronize(h->stream);

@@ -173,6 +173,7 @@ struct iga_s {
   // every Gauss point (an orthogonal parametrisation, such as the annulus), and which
   // weight-gradient terms (S g)_a are nonzero (bit a)
   bool plan_diag_s = false;
+  bool plan_general = false;   // iga_set_jacobian_plan(h, 1): every term, whatever the classification
   int plan_gmask = 7;
   // rational weights that factor by axis, w_A = w0[i0] w1[i1] w2[i2]: the products w_A w_B of
   // the Jacobian are folded into the device pair tables (w_d[i] w_d[j] per pair) and the

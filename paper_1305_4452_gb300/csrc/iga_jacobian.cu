@@ -504,7 +504,7 @@ cudaError_t jacobian(iga_s *h, const double *U, V *vals, int mode, const V *base
   if (!h->has_geom && !h->has_w)
     return h->dim == 3 ? run_stages<T, V, 3, PLAN_DIAG>(h, vals, nullptr, fix) : run_stages<T, V, 2, PLAN_DIAG>(h, vals, nullptr, fix);
   // a diagonal S at every Gauss point (classify_stiffness_plan)
-  if (h->plan_diag_s)
+  if (h->plan_diag_s && !h->plan_general)
     return h->dim == 3 ? run_stages<T, V, 3, PLAN_DIAGS>(h, vals, nullptr, fix) : run_stages<T, V, 2, PLAN_DIAGS>(h, vals, nullptr, fix);
   return h->dim == 3 ? run_stages<T, V, 3, PLAN_STIFF>(h, vals, nullptr, fix) : run_stages<T, V, 2, PLAN_STIFF>(h, vals, nullptr, fix);
 }

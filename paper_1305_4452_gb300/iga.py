@@ -27,7 +27,7 @@ EXPORTS = ["iga_create", "iga_set_boundary_value", "iga_set_lambda", "iga_get_pa
            "iga_nn_set_h1_weight", "iga_apply_jacobian", "iga_apply_jacobian_mf", "iga_form_jacobian_diagonal",
            "iga_form_residual_ts", "iga_form_jacobian_ts", "iga_ts_alpha_step", "iga_measure_peaks",
            "iga_set_wait_limit", "iga_inject_stall", "iga_batch_set_tiles", "iga_exp_eval",
-           "iga_set_gmres_fused"]
+           "iga_set_gmres_fused", "iga_set_jacobian_plan"]
 
 KERNEL_CLASSES = ["geometry", "residual_element", "residual_gather", "q00", "jac_stage1", "jac_stage2", "jac_final",
                   "spmv", "gs_orth", "gmres_scalar", "vector", "combine", "pattern", "elem_tc", "elem_gather",
@@ -135,6 +135,7 @@ def lib():
         L.iga_set_wait_limit.argtypes = [vp, ctypes.c_double]
         L.iga_inject_stall.argtypes = [vp]
         L.iga_set_gmres_fused.argtypes = [vp, ctypes.c_int]
+        L.iga_set_jacobian_plan.argtypes = [vp, ctypes.c_int]
         L.iga_exp_eval.argtypes = [vp, vp, vp, ctypes.c_int64]
         _lib = L
     return _lib
@@ -263,6 +264,9 @@ class Discretization:
 
     def set_gmres_fused(self, fused):
         _check(lib().iga_set_gmres_fused(self.h, int(fused)), self.h)
+
+    def set_jacobian_plan(self, general):
+        _check(lib().iga_set_jacobian_plan(self.h, int(general)), self.h)
 
     def pattern(self):
         """Copy the device CSR pattern into torch tensors (rowptr int64, colidx int32)."""

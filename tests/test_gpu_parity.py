@@ -364,6 +364,35 @@ def test_gmres_cgs_refinement_modes_reach_the_oracle_solution(refine, fused, nel
     disc.close()
 
 
+@pytest.mark.parametrize("dim,p,nel", [(3, 3, (10, 9, 8)), (3, 2, (9, 8, 7)), (2, 3, (12, 10))])
+def test_diagonal_s_plan_equals_the_general_plan(dim, p, nel):
+    """The annulus's orthogonal parametrisation (radial and angular directions perpendicular,
+    the height separate, weights a function of the angle) selects the diagonal-S plan, which
+    drops the off-diagonal S and the zero weight-gradient terms that the geometry cache holds
+    at rounding level.  Its FP64 and FP32 Jacobians agree with the general plan's to that
+    level (a dropped term that is not zero would show at 1e-3 or more), they differ from them
+    in the last bits (so the other plan did run), and the FP64 one equals the oracle's at
+    1e-12."""
+    I = iga()
+    disc, prob, n = make_pair(dim, p, nel, lam=2.0, geom="annulus")
+    U0 = W.interior_field(n, seed=5)
+    U = torch.tensor(U0, device="cuda")
+    Ja = disc.form_jacobian(U)
+    Ja32 = disc.form_jacobian(U, prec=I.IGA_JAC_FP32)
+    disc.set_jacobian_plan(1)
+    Jg = disc.form_jacobian(U)
+    Jg32 = disc.form_jacobian(U, prec=I.IGA_JAC_FP32)
+    disc.set_jacobian_plan(0)
+    scale = torch.abs(Jg).max().item()
+    assert torch.abs(Ja - Jg).max().item() <= 5e-13 * scale
+    assert not torch.equal(Ja, Jg)
+    assert torch.abs(Ja32.double() - Jg32.double()).max().item() <= 1e-6 * scale
+    assert rel(Ja.cpu().numpy(), prob.jacobian(U0)) <= TOL
+    with pytest.raises(I.IgaError):
+        disc.set_jacobian_plan(2)
+    disc.close()
+
+
 def test_gmres_option_rejections():
     I = iga()
     disc, prob, n = make_pair(2, 2, (6, 6), lam=1.0)
