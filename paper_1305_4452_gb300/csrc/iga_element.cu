@@ -868,8 +868,29 @@ cudaError_t launch_residual_into(iga_s *h, const double *U, double *F, double *F
   return cudaGetLastError();
 }
 
+// Q00 = cs gSg (no reaction term: the stiffness alone), straight from the geometry cache
+__global__ static void k_q00_geom(const double *__restrict__ geom, GeomLayout gl, int nq, int64_t nelem, double cs,
+                                  double *__restrict__ Q00) {
+  const int64_t tot = nelem * nq;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = t / nq;
+    const int qp = (int)(t - e * nq);
+    Q00[t] = cs * geom[((size_t)e * gl.nf + gl.gSg) * nq + qp];
+  }
+}
+
 cudaError_t launch_q00(iga_s *h, const double *U, double cs, double cr) {
   DirArgs a0 = dir_args(h->ddev[0]), a1 = dir_args(h->ddev[1]), a2 = dir_args(h->ddev[2]);
+  if (cr == 0.0) {  // the U-independent stiffness: no interpolation, no exponential
+    const int nq = h->dim == 3 ? h->q * h->q * h->q : h->q * h->q;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (h->nelem * nq + 255) / 256;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)(sms > 0 ? sms : 1) * 8));
+    IGA_LAUNCH(h, KC_Q00, (k_q00_geom<<<grid, 256, 0, h->stream>>>(h->geom, h->gl, nq, h->nelem, cs, h->Q00)));
+    return cudaGetLastError();
+  }
   constexpr int NE = 8;  // value-only interpolation: more elements per CTA
   unsigned grid = (unsigned)((h->nelem + NE - 1) / NE);
   IGA_LAUNCH(h, KC_Q00, DISPATCH_DP(h->dim, h->p, ({
