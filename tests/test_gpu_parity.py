@@ -114,6 +114,15 @@ SMALL = [
     (3, 2, (6, 5, 4), None, "graded", None),
     (3, 3, (5, 4, 4), None, "graded_nurbs", None),
     (3, 4, (4, 3, 3), None, "graded", None),
+    # the sum-factorised geometry at the degrees where its per-block element count changes
+    # (p = 1: 16 elements per block, p = 4: one), under a rational map; the diagonal-S plan
+    # with a kappa field folded into S (annulus), and the general plan with kappa
+    (3, 4, (3, 3, 2), None, "graded_nurbs", None),
+    (3, 1, (4, 3, 3), None, "graded_nurbs", None),
+    (2, 1, (6, 5), None, "graded_nurbs", None),
+    (3, 3, (5, 4, 3), None, "annulus", 7),
+    (2, 2, (8, 7), None, "annulus", 9),
+    (3, 2, (4, 4, 3), None, "graded_nurbs", 11),
 ]
 
 
