@@ -501,7 +501,7 @@ template <int DIM, int P, int TPB>
 __global__ void __launch_bounds__(TPB) k_gather_rows(DirArgs d0, DirArgs d1, DirArgs d2, const float *__restrict__ E,
                                                      const int2 *__restrict__ gtab_g, const int64_t *__restrict__ rowptr,
                                                      const double *__restrict__ wts, BndArgs bnd, float *__restrict__ vals,
-                                                     int64_t N) {
+                                                     int64_t N, int slice_major) {
   constexpr int N1 = P + 1, NEN = ipow3<DIM>(N1), RMAX = (2 * P + 1) * (2 * P + 1);
   constexpr int NB = N1 * N1;  // functions of an element in one axis-2 slice (2D: all)
   constexpr int LD = TPB + 1;  // accumulator stride: conflict-free by thread and by column
@@ -518,13 +518,16 @@ __global__ void __launch_bounds__(TPB) k_gather_rows(DirArgs d0, DirArgs d1, Dir
     __syncthreads();
     gtab = st;
   }
-  const int64_t A = (int64_t)blockIdx.x * TPB + t;
+  // slice_major: blockIdx.x is the axis-2 slice and blockIdx.y the row chunk, so that the
+  // slices of a row chunk run together and the mirrored reads of the element matrices
+  // (rows a few axis-2 layers apart) find them in L2
+  const int64_t A = (int64_t)(slice_major ? blockIdx.y : blockIdx.x) * TPB + t;
   float *acc = acc_all + t;
   const int64_t Ac = A < N ? A : N - 1;
   const int I0 = (int)(Ac % d0.n), I1 = (int)((Ac / d0.n) % d1.n), I2 = (DIM == 3) ? (int)(Ac / ((int64_t)d0.n * d1.n)) : 0;
   const int l0 = d0.l[I0], l1 = d1.l[I1], l2 = DIM == 3 ? d2.l[I2] : 0;
   const int w0 = d0.r[I0] - l0 + 1, w1 = d1.r[I1] - l1 + 1, w2 = DIM == 3 ? d2.r[I2] - l2 + 1 : 1;
-  const int s2 = DIM == 3 ? (int)blockIdx.y : 0;
+  const int s2 = DIM == 3 ? (int)(slice_major ? blockIdx.x : blockIdx.y) : 0;
   const bool active = A < N && s2 < w2;  // no early return: the block stores together at the end
   const int J2 = l2 + s2;
   const int len = w0 * w1;
@@ -933,9 +936,11 @@ cudaError_t launch_jacobian_elem_gemm(iga_s *h, const double *U, float *vals, in
     const size_t sm = (size_t)((RMAX * (TPB + 1) + 1) / 2 * 2) * sizeof(float) +
                       (NENc * NENc * 8 <= 8 * 1024 ? (size_t)NENc * NENc * 8 : 0);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_gather_rows<D, PP, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    const dim3 gg((unsigned)((h->N + TPB - 1) / TPB), D == 3 ? 2 * PP + 1 : 1);
+    const unsigned chunks = (unsigned)((h->N + TPB - 1) / TPB);
+    const int slice_major = (D == 3 && chunks <= 65535u) ? 1 : 0;
+    const dim3 gg = slice_major ? dim3(2 * PP + 1, chunks) : dim3(chunks, D == 3 ? 2 * PP + 1 : 1);
     k_gather_rows<D, PP, TPB><<<gg, TPB, sm, h->stream>>>(a0, a1, a2, P->E, P->gtab, h->rowptr, h->weights, h->bnd, vals,
-                                                          h->N);
+                                                          h->N, slice_major);
   })));
   return cudaGetLastError();
 }
