@@ -345,6 +345,44 @@ def test_annulus_geometry():
     assert np.allclose(x, [0, 2, 1], atol=1e-14)
 
 
+def test_annulus_parametrisation_is_orthogonal_and_its_weights_depend_on_the_angle():
+    """The premise of the diagonal-S stiffness plan (reading 18): on the quarter annulus the
+    three parametric directions of the map are mutually perpendicular at every point (radial,
+    angular, height), so F^T F is diagonal and so is S = det F F^-1 F^-T; and the rational
+    weights depend on the angle's index alone, so grad W is along xi_1 and (S g)_0 = (S g)_2 = 0.
+    Checked on the oracle's map by central differences (their error, about 1e-9 of the column
+    norms, is the tolerance) and on the control net exactly; a perturbed map fails the first."""
+    kn, ctrl, w = W.quarter_annulus(6, 3)
+    n = [len(k) - 4 for k in kn]
+    Wn = w.reshape(n[2], n[1], n[0])
+    assert np.array_equal(Wn, np.broadcast_to(Wn[:1, :, :1], Wn.shape))
+    P = O.Problem(kn, [3] * 3, ctrl=ctrl, weights=w)
+    rng = np.random.default_rng(7)
+    h = 1e-6
+
+    def columns(prob, xi):
+        cols = []
+        for a in range(3):
+            e = np.zeros(3)
+            e[a] = h
+            xp, _ = prob.map_point(np.clip(xi + e, 0.0, 1.0))
+            xm, _ = prob.map_point(np.clip(xi - e, 0.0, 1.0))
+            cols.append((np.asarray(xp) - np.asarray(xm)) / (2 * h))
+        return cols
+
+    for xi in 0.05 + 0.9 * rng.random((12, 3)):
+        c = columns(P, xi)
+        for a in range(3):
+            for b in range(a + 1, 3):
+                assert abs(np.dot(c[a], c[b])) <= 1e-8 * np.linalg.norm(c[a]) * np.linalg.norm(c[b]), (xi, a, b)
+    # the test can fail: a sheared copy of the same net is not orthogonal
+    sheared = ctrl.copy()
+    sheared[:, 0] += 0.2 * sheared[:, 2]
+    Ps = O.Problem(kn, [3] * 3, ctrl=sheared, weights=w)
+    c = columns(Ps, np.array([0.4, 0.3, 0.6]))
+    assert abs(np.dot(c[0], c[2])) > 1e-3 * np.linalg.norm(c[0]) * np.linalg.norm(c[2])
+
+
 def test_dirichlet_rows_and_columns():
     U = O.open_uniform_knots(3, 2)
     P = O.Problem([U, U], [2, 2], lam=1.0, dirichlet={(0, 0): 0.5, (1, 1): -0.25})
